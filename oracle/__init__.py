@@ -1,0 +1,319 @@
+"""CPU oracle for LUDVIG uplifting and graph diffusion (arXiv 2410.14462).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the library's compute path imports,
+links or runs this package; only ``tests/``, ``__graft_entry__.smoke()`` and
+the benchmark's CPU-baseline / reference leg use it.  It shares no code with
+the CUDA library: the two meet only through the seeded input generators.
+
+* ``ludvig_oracle.c`` (plain C, float64 values, float32 decision track):
+  projection, tile lists, per-pixel compositing (Eq. 1), uplift sums
+  (Eq. 3 / Eq. 5), exact kNN on Gaussian centres (Sec. 3.3).
+* this module (numpy / scipy): the similarity graph (Eq. 7 and the edge
+  weight of the diffusion workload), row normalisation, and the power
+  iteration g_{t+1} = A g_t / ||g_t||_2 (Eq. 8).
+
+Parity pins live in ``tests/test_oracle_*.py``.  "Parity unpinned": absolute
+agreement with the paper's own rasteriser (no code or printed values exist)
+and every task metric (no datasets).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ludvig_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MODE_HYBRID = 32   # float32 decisions (the kernel's precision), float64 values
+MODE_FP64 = 64     # every decision in float64
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` with gcc (no contraction of a*b+c into fma)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            i64, i32, f32 = ctypes.c_int64, ctypes.c_int32, ctypes.c_float
+            p = ctypes.c_void_p
+            L.orc_exp32.argtypes = [f32]
+            L.orc_exp32.restype = f32
+            L.orc_project.argtypes = [i64, p, p, p, p, p, i32, i32, p, p, p, p, i32]
+            L.orc_project.restype = i32
+            L.orc_tile_lists.argtypes = [i64, p, p, p, p, p, i32, i32, i32, p, i64, p, i32]
+            L.orc_tile_lists.restype = i64
+            L.orc_view_uplift.argtypes = [i64, p, p, p, p, p, i32, i32, p, i32, i32, p, p, p, p,
+                                          i64, p, p, p, p, i32]
+            L.orc_view_uplift.restype = i64
+            L.orc_normalise.argtypes = [i64, i32, p, p, p]
+            L.orc_normalise.restype = None
+            L.orc_knn.argtypes = [i64, p, i32, i64, p, p, p, i32]
+            L.orc_knn.restype = i32
+            _lib = L
+    return _lib
+
+
+def default_threads() -> int:
+    return max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count() or 1)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _scene_arrays(scene):
+    return (_c(scene.means, np.float32), _c(scene.scales, np.float32),
+            _c(scene.quats, np.float32), _c(scene.opacity, np.float32))
+
+
+# ---------------------------------------------------------------------------
+# rasteriser pieces
+# ---------------------------------------------------------------------------
+
+def exp32(x) -> np.ndarray:
+    """The float32 exponential of the decision track, elementwise."""
+    L = lib()
+    x = np.asarray(x, dtype=np.float32)
+    return np.array([L.orc_exp32(float(v)) for v in x.ravel()], dtype=np.float32).reshape(x.shape)
+
+
+def project(scene, cam_params, width, height, nthreads=None):
+    """Per-Gaussian projection of one view.
+
+    Returns dict: ``p32`` [N,8] (mx,my,z,ca,cb,cc,opacity,radius),
+    ``rect`` [N,4] (x0,y0,x1,y1 tiles, half-open), ``p64`` [N,8]
+    (mx,my,z,ca,cb,cc,radius,visible), ``visible`` [N] (float32 track).
+    """
+    m, s, q, o = _scene_arrays(scene)
+    n = m.shape[0]
+    cam = _c(cam_params, np.float32)
+    out32 = np.zeros((n, 8), np.float32)
+    rect = np.zeros((n, 4), np.int32)
+    out64 = np.zeros((n, 8), np.float64)
+    vis = np.zeros(n, np.uint8)
+    rc = lib().orc_project(n, _ptr(m), _ptr(s), _ptr(q), _ptr(o), _ptr(cam), width, height,
+                           _ptr(out32), _ptr(rect), _ptr(out64), _ptr(vis),
+                           nthreads or default_threads())
+    if rc != 0:
+        raise RuntimeError(f"orc_project failed: {rc}")
+    return {"p32": out32, "rect": rect, "p64": out64, "visible": vis.astype(bool)}
+
+
+def tile_lists(scene, cam_params, width, height, mode=MODE_HYBRID, nthreads=None):
+    """Depth-ordered candidate list of every 16x16 tile: (ranges [T,2], list)."""
+    m, s, q, o = _scene_arrays(scene)
+    n = m.shape[0]
+    cam = _c(cam_params, np.float32)
+    ntiles = ((width + 15) // 16) * ((height + 15) // 16)
+    ranges = np.zeros((ntiles, 2), np.int64)
+    L = lib()
+    args = (n, _ptr(m), _ptr(s), _ptr(q), _ptr(o), _ptr(cam), width, height, mode, _ptr(ranges))
+    total = L.orc_tile_lists(*args, 0, None, nthreads or default_threads())
+    if total < 0:
+        raise RuntimeError(f"orc_tile_lists failed: {total}")
+    lst = np.zeros(max(total, 1), np.int32)
+    L.orc_tile_lists(*args, total, _ptr(lst), nthreads or default_threads())
+    return ranges, lst[:total]
+
+
+def view_uplift(scene, cam_params, width, height, feats=None, num=None, den=None,
+                mode=MODE_HYBRID, want=None, t_final=False, triplets=False, nthreads=None):
+    """Adds one view's contribution to ``num`` [N,D] / ``den`` [N] (float64).
+
+    ``feats``: [H,W,D] float32 (or None).  Returns a dict with the number of
+    contributions and, on request, ``t_final`` [H,W] and the sparse weight
+    triplets (pixel, gaussian, w64, w32).
+    """
+    m, s, q, o = _scene_arrays(scene)
+    n = m.shape[0]
+    cam = _c(cam_params, np.float32)
+    d = 0
+    fptr = None
+    if feats is not None:
+        feats = _c(feats, np.float32)
+        d = feats.shape[-1]
+        fptr = _ptr(feats)
+    if num is not None:
+        assert num.dtype == np.float64 and num.flags.c_contiguous and num.shape == (n, d)
+    if den is not None:
+        assert den.dtype == np.float64 and den.flags.c_contiguous and den.shape == (n,)
+    wmask = None if want is None else _c(want, np.uint8)
+    tf = np.zeros((height, width), np.float64) if t_final else None
+    L = lib()
+    nt = nthreads or default_threads()
+    res = {}
+
+    def call(cap, tp, tg, tw, tw32):
+        return L.orc_view_uplift(n, _ptr(m), _ptr(s), _ptr(q), _ptr(o), _ptr(cam), width, height,
+                                 fptr, d, mode, _ptr(wmask), _ptr(num), _ptr(den), _ptr(tf),
+                                 cap, _ptr(tp), _ptr(tg), _ptr(tw), _ptr(tw32), nt)
+
+    if triplets:
+        # count the contributions first (no accumulation), then run for real
+        total = L.orc_view_uplift(n, _ptr(m), _ptr(s), _ptr(q), _ptr(o), _ptr(cam), width,
+                                  height, None, 0, mode, _ptr(wmask), None, None, None,
+                                  0, None, None, None, None, nt)
+        if total < 0:
+            raise RuntimeError(f"orc_view_uplift failed: {total}")
+        tp = np.zeros(max(total, 1), np.int32)
+        tg = np.zeros(max(total, 1), np.int32)
+        tw = np.zeros(max(total, 1), np.float64)
+        tw32 = np.zeros(max(total, 1), np.float32)
+        total2 = call(total, tp, tg, tw, tw32)
+        assert total2 == total
+        res.update(pix=tp[:total], gid=tg[:total], w64=tw[:total], w32=tw32[:total])
+    else:
+        total = call(0, None, None, None, None)
+        if total < 0:
+            raise RuntimeError(f"orc_view_uplift failed: {total}")
+    res["count"] = int(total)
+    if t_final:
+        res["t_final"] = tf
+    return res
+
+
+def normalise(num: np.ndarray, den: np.ndarray) -> np.ndarray:
+    """f_i = num_i / beta_i, and 0 where beta_i = 0 (Eq. 3)."""
+    out = np.zeros_like(num)
+    pos = den > 0
+    out[pos] = num[pos] / den[pos, None]
+    return out
+
+
+def uplift(scene, cams, features, views=None, mode=MODE_HYBRID, want=None, nthreads=None):
+    """Uplift over ``views`` (default all): returns (f [N,D], beta [N]) in float64.
+
+    ``features(v)`` returns the [H,W,D] float32 map of view v (numpy or torch).
+    """
+    views = range(cams.v) if views is None else views
+    num = den = None
+    for v in views:
+        F = features(v)
+        F = F.cpu().numpy() if hasattr(F, "cpu") else np.asarray(F)
+        F = _c(F, np.float32)
+        if num is None:
+            num = np.zeros((scene.n, F.shape[-1]), np.float64)
+            den = np.zeros(scene.n, np.float64)
+        view_uplift(scene, cams.params[v], cams.width, cams.height, F, num, den, mode=mode,
+                    want=want, nthreads=nthreads)
+    return normalise(num, den), den
+
+
+# ---------------------------------------------------------------------------
+# graph diffusion (Sec. 3.3)
+# ---------------------------------------------------------------------------
+
+def knn(means, k, queries=None, nthreads=None):
+    """Exact k nearest neighbours (float32 squared distances, ties to the lower
+    index, self excluded).  Returns (idx [m,k] int32, d2 [m,k] float32)."""
+    m = _c(means, np.float32)
+    n = m.shape[0]
+    q = None if queries is None else _c(queries, np.int64)
+    mq = n if q is None else q.shape[0]
+    idx = np.zeros((mq, k), np.int32)
+    d2 = np.zeros((mq, k), np.float32)
+    rc = lib().orc_knn(n, _ptr(m), k, mq, _ptr(q), _ptr(idx), _ptr(d2), nthreads or default_threads())
+    if rc != 0:
+        raise RuntimeError("orc_knn failed")
+    return idx, d2
+
+
+def union_edges(nbr: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Undirected edge set {i,j}: j in N(i) or i in N(j), no self loops.
+    Returns (rows, cols) of the symmetric pattern sorted by (row, col)."""
+    n, k = nbr.shape
+    r = np.repeat(np.arange(n, dtype=np.int64), k)
+    c = nbr.reshape(-1).astype(np.int64)
+    ok = (c >= 0) & (c != r)
+    r, c = r[ok], c[ok]
+    rows = np.concatenate([r, c])
+    cols = np.concatenate([c, r])
+    key = np.unique(rows * n + cols)
+    return key // n, key % n
+
+
+def edge_weights_spatial_cos(means, feats, rows, cols, h=0.01):
+    """Diffusion-workload edge weight exp(-||x_i-x_j||^2/h) * max(0, cos(f_i,f_j))
+    in float64 (a zero feature vector has cosine 0)."""
+    x = np.asarray(means, np.float64)
+    f = np.asarray(feats, np.float64)
+    d2 = np.sum((x[rows] - x[cols]) ** 2, axis=1)
+    nf = np.linalg.norm(f, axis=1)
+    dot = np.sum(f[rows] * f[cols], axis=1)
+    den = nf[rows] * nf[cols]
+    cos = np.where(den > 0, dot / np.where(den > 0, den, 1.0), 0.0)
+    return np.exp(-d2 / h) * np.maximum(0.0, cos)
+
+
+def edge_weights_rbf_unary(feats, rows, cols, bandwidth, s_f, unary=None):
+    """Eq. 7 with the RBF similarity of the appendix:
+    A_ij = exp(-||f^_i - f^_j||^2 / (b s_f^2)) * sqrt(P_i) sqrt(P_j), with f^ the
+    l2-normalised features and P the unary term (1 when omitted)."""
+    f = np.asarray(feats, np.float64)
+    nf = np.linalg.norm(f, axis=1, keepdims=True)
+    fh = np.where(nf > 0, f / np.where(nf > 0, nf, 1.0), 0.0)
+    d2 = np.sum((fh[rows] - fh[cols]) ** 2, axis=1)
+    w = np.exp(-d2 / (bandwidth * s_f * s_f))
+    if unary is not None:
+        p = np.sqrt(np.asarray(unary, np.float64))
+        w = w * p[rows] * p[cols]
+    return w
+
+
+def csr(n, rows, cols, vals, row_normalize=True, binarize=0.0):
+    """scipy CSR matrix of the graph.  With ``binarize`` > 0 every weight above
+    the threshold becomes 1 and the rest 0 (the segmentation variant of Sec. 4.1
+    thresholds A at 1e-5); with ``row_normalize`` each row is then divided by
+    its sum (rows summing to 0 stay 0)."""
+    import scipy.sparse as sp
+    vals = np.asarray(vals, np.float64)
+    if binarize > 0:
+        vals = (vals > binarize).astype(np.float64)
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    A.sum_duplicates()
+    if row_normalize:
+        s = np.asarray(A.sum(axis=1)).ravel()
+        inv = np.where(s > 0, 1.0 / np.where(s > 0, s, 1.0), 0.0)
+        A = sp.diags(inv) @ A
+        A = A.tocsr()
+    return A
+
+
+def diffuse(A, x0, iters):
+    """Power iteration of Eq. 8 on each column: g_{t+1} = A (g_t / ||g_t||_2).
+    A column whose norm reaches 0 stays 0.  Returns g_iters (float64)."""
+    g = np.array(x0, dtype=np.float64, copy=True)
+    squeeze = g.ndim == 1
+    if squeeze:
+        g = g[:, None]
+    for _ in range(iters):
+        nrm = np.linalg.norm(g, axis=0)
+        scale = np.where(nrm > 0, 1.0 / np.where(nrm > 0, nrm, 1.0), 0.0)
+        g = A @ (g * scale[None, :])
+    return g[:, 0] if squeeze else g
