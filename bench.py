@@ -1,0 +1,296 @@
+"""Throughput of the LUDVIG hot path on GB300: uplift views*channels per second.
+
+One step = one pass of the whole path over the paper-scale synthetic
+workload: uplift of 150 views (980x546, D=384 float32 features, 1M clustered
+Gaussians) -> kNN graph (k=16) with exp(-d^2/0.01) * max(0, cos) weights on
+the uplifted features -> 100 row-normalised diffusion steps of a mask.
+Inputs (scene and all 123 GB of features) are resident in HBM before the timed
+region and larger than L2, so no explicit flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle on
+bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "uplift views*ch/s"
+UNIT = "views*ch/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["paper", "small"], default="paper")
+    ap.add_argument("--dtype", choices=["f32", "bf16"], default="f32")
+    ap.add_argument("--e2e-views", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="uplift only (not a full step)")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_2410_14462_gb300 import inputs
+    if name == "paper":
+        return inputs.paper_scale_workload()
+    return inputs.paper_scale_workload(n=100_000, views=12, d=64, width=490, height=273)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    wl = workload(args.workload)
+    oracle.build()
+    cams = wl.cams
+    nthreads = oracle.default_threads()
+    # bounded sample per step: one view, every Gaussian, all D channels
+    times = []
+    feats = {}
+    for s in range(args.warmup + args.steps):
+        v = s % cams.v
+        if v not in feats:
+            feats[v] = wl.features(v).numpy()
+        num = np.zeros((wl.scene.n, wl.d))
+        den = np.zeros(wl.scene.n)
+        t0 = time.perf_counter()
+        oracle.view_uplift(wl.scene, cams.params[v], cams.width, cams.height, feats[v], num, den,
+                           nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    t = float(np.mean(times))
+    value = wl.d / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "sample": "1 view per step (uplift only), all Gaussians"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                             "sample": f"1 of {cams.v} views per step, D={wl.d}, N={wl.scene.n}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def cpu_baseline(wl):
+    import oracle
+    oracle.build()
+    nthreads = oracle.default_threads()
+    v = 0
+    F = wl.features(v).numpy()
+    num = np.zeros((wl.scene.n, wl.d))
+    den = np.zeros(wl.scene.n)
+    t0 = time.perf_counter()
+    oracle.view_uplift(wl.scene, wl.cams.params[v], wl.cams.width, wl.cams.height, F, num, den,
+                       nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return {"value": wl.d / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"uplift of view 0 of {wl.cams.v} (D={wl.d}, N={wl.scene.n}), {dt:.1f} s"}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2410_14462_gb300 import build, inputs, ludvig
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    L = ludvig.load()
+
+    wl = workload(args.workload)
+    W, H, V, D = wl.cams.width, wl.cams.height, wl.cams.v, wl.d
+    fdt = torch.float32 if args.dtype == "f32" else torch.bfloat16
+    esize = 4 if args.dtype == "f32" else 2
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    feats = torch.empty((V, H, W, D), dtype=fdt, device="cuda")
+    for v in range(V):
+        feats[v] = wl.features(v, device="cuda", dtype=fdt)
+    out = torch.empty((sc.n, D), dtype=torch.float32, device="cuda")
+    beta = torch.empty((sc.n,), dtype=torch.float32, device="cuda")
+    centre = inputs.cluster_centres(wl.seed)[0]
+    x0 = torch.from_numpy((np.linalg.norm(wl.scene.means - centre, axis=1) < 0.15).astype(np.float32)).cuda()
+    g_out = torch.empty_like(x0)
+    torch.cuda.synchronize()
+
+    def step():
+        ludvig.uplift(sc, wl.cams.params, W, H, feats, out, beta)
+        if not args.no_graph:
+            g = ludvig.Graph(sc, 16, out, spatial_h=0.01)
+            g.diffuse(x0, 100, out=g_out)
+            g.close()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    ludvig.trace_read(reset=True)
+    ludvig.trace_enable(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    ludvig.trace_enable(False)
+    tr = ludvig.trace_read(reset=True)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * V * D / (ms / 1e3)
+
+    # roofline of the dominant kernel (composite + aggregate)
+    peak, peak_kind = peaks()
+    comp_ms = tr["ms"]["composite"] / max(1, tr["calls"]["composite"])
+    launches_per_step = tr["calls"]["composite"] / args.steps
+    alg_bytes_step = V * H * W * D * esize + sc.n * 44 + sc.n * (D + 1) * 4
+    alg_per_launch = alg_bytes_step / max(1.0, launches_per_step)
+    achieved = alg_per_launch / (comp_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_composite", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+            "alg_bytes_per_launch": alg_per_launch, "launch_ms": comp_ms}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": wl.name, "n_gaussians": sc.n, "views": V, "width": W, "height": H,
+                       "d": D, "step": ("uplift" if args.no_graph else
+                                        "uplift + kNN(k=16) graph + 100 diffusion steps"),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs (features) larger than L2; no flush"},
+            "stages_ms_per_step": {k: v / args.steps for k, v in tr["ms"].items()},
+            "gpu_launches": tr["kernel_launches"],
+            "roofline": roof, "clocks": clk}
+
+    if rank == 0 and not args.no_e2e:
+        nv = min(args.e2e_views, V)
+        hf = feats[:nv].cpu().pin_memory()
+        ludvig.uplift_host(sc, wl.cams.params[:nv], W, H, hf)   # warm-up
+        ts = []
+        for _ in range(max(1, min(3, args.steps))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ludvig.uplift_host(sc, wl.cams.params[:nv], W, H, hf)
+            ts.append(time.perf_counter() - t0)
+        te = float(np.median(ts))
+        line["e2e"] = {"value": nv * D / te, "unit": UNIT, "h2d_bytes_per_step": int(hf.numel() * esize),
+                       "d2h_bytes_per_step": int(sc.n * (D + 1) * 4),
+                       "sample": f"views 0-{nv - 1} of {V} through ludvig_uplift_host (uplift only)"}
+        del hf
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,234 @@
+/*
+ * ludvig.h -- C ABI of libludvig, a GB300 (sm_103a) implementation of the
+ * uplifting and graph-diffusion hot path of LUDVIG (Marrie et al., "LUDVIG:
+ * Learning-free Uplifting of 2D Visual features to Gaussian Splatting
+ * scenes", arXiv 2410.14462).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers documented as "device" are CUDA device pointers owned by the
+ *    caller; the library never frees them.  "host" pointers are ordinary
+ *    host memory.  Arrays are dense, row-major, without padding.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued asynchronously on it; argument errors are
+ *    reported synchronously before anything is enqueued.  A call returns
+ *    LUDVIG_ERR_CUDA if a CUDA runtime call fails; the message is then in
+ *    ludvig_last_error().
+ *  - Outputs are written only when the call returns LUDVIG_OK.
+ *  - A scene (and a graph) may be used by one stream at a time: calls on the
+ *    same scene from different streams must be ordered by the caller.
+ *  - The library keeps a per-scene device workspace that grows on demand
+ *    (cudaMalloc) and is reused; the first call at a new size allocates.
+ *
+ * Geometry conventions (the paper fixes none; these are the 3D Gaussian
+ * Splatting rasteriser's, which the paper uses, Sec. 5):
+ *  - camera: world point X maps to x = R X + t (OpenCV axes: x right, y down,
+ *    z forward) and to pixel coordinates (fx x/z + cx, fy y/z + cy); pixel
+ *    (u,v) is sampled at its centre (u+0.5, v+0.5).
+ *  - Gaussian i: mean mu_i, covariance Sigma_i = R(q_i) diag(s_i)^2 R(q_i)^T
+ *    with q_i = (w,x,y,z) normalised inside the library, s_i the LINEAR
+ *    per-axis standard deviations, opacity o_i in (0,1) (post-sigmoid).
+ *  - 2D footprint: EWA covariance J R Sigma R^T J^T + 0.3 I (Jacobian taken at
+ *    the mean with x/z, y/z clamped to 1.3 x the half field of view), near
+ *    plane z > 0.2, radius ceil(3 sqrt(lambda_max)), 16x16 pixel tiles.
+ *  - weights (Sec. 3.1, Eq. 1): along each pixel's depth-ordered list
+ *    (ties: lower index first) alpha = min(0.99, o * exp(-0.5 d^T C d)); a
+ *    Gaussian with alpha < 1/255 is skipped; the walk stops before the
+ *    Gaussian that would take the transmittance below 1e-4;
+ *    w = alpha * T.
+ */
+#ifndef LUDVIG_H
+#define LUDVIG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LUDVIG_ABI_VERSION 1
+
+typedef enum {
+    LUDVIG_OK = 0,
+    LUDVIG_ERR_ARG = 1,          /* invalid argument (nothing enqueued) */
+    LUDVIG_ERR_OOM = 2,          /* device allocation failed */
+    LUDVIG_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    LUDVIG_ERR_TIMEOUT = 4,      /* a bounded wait expired */
+    LUDVIG_ERR_INTERNAL = 5,     /* a device-side consistency check failed */
+    LUDVIG_ERR_UNSUPPORTED = 6   /* valid request this build does not implement */
+} ludvig_status;
+
+typedef enum {
+    LUDVIG_F32 = 0,              /* float32 features, CUDA-core FFMA aggregation */
+    LUDVIG_BF16 = 1              /* bfloat16 features, tensor-core aggregation */
+} ludvig_dtype;
+
+/* Pinhole camera, host memory.  R: row-major world->camera rotation. */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+} ludvig_camera;
+
+typedef struct ludvig_scene* ludvig_scene_t;
+typedef struct ludvig_graph* ludvig_graph_t;
+
+/* ABI version of the loaded library (LUDVIG_ABI_VERSION it was built with). */
+int32_t ludvig_abi_version(void);
+
+/* Thread-local message describing the last failed call on this thread. */
+const char* ludvig_last_error(void);
+
+/* Creates a scene from n Gaussians (Sec. 3.1: mean, covariance from scale and
+ * rotation, opacity).  All inputs are device arrays and are COPIED:
+ *   means [n,3], scales [n,3] (linear standard deviations, > 0),
+ *   quats [n,4] (w,x,y,z; any non-zero norm), opacity [n] (in (0,1)).
+ * n may be 0.  The per-Gaussian 3D covariance is precomputed on `stream`.
+ * *out receives the handle; destroy it with ludvig_scene_destroy. */
+ludvig_status ludvig_scene_create(const float* means, const float* scales, const float* quats,
+                                  const float* opacity, int64_t n, void* stream,
+                                  ludvig_scene_t* out);
+
+/* Frees the scene and its workspace (synchronises the device). */
+ludvig_status ludvig_scene_destroy(ludvig_scene_t scene);
+
+/* Number of Gaussians of a scene. */
+int64_t ludvig_scene_size(ludvig_scene_t scene);
+
+/* Uplifting, accumulation half (Sec. 3.2, Eq. 3; matrix form Eq. 5):
+ *   num[i,:] += sum_{v,p} w_i(v,p) F_v[p,:]      den[i] += sum_{v,p} w_i(v,p)
+ * over the n_views cameras `cams` (host [n_views]) of one image size
+ * width x height (each <= 65535*16), with features `feats`
+ * (device [n_views, height, width, d], channels-last, dtype `dtype`;
+ * d % 4 == 0 for LUDVIG_F32 unless d < 4, d % 8 == 0 for LUDVIG_BF16).
+ * num (device [n,d] float32) and den (device [n] float32) are ADDED to, so
+ * partial sums over disjoint view sets can be merged by addition (view
+ * sharding, checkpoint/resume).  Summation order on the GPU is not fixed
+ * (atomics), so results are reproducible only to rounding. */
+ludvig_status ludvig_uplift_accumulate(ludvig_scene_t scene, const ludvig_camera* cams,
+                                       int32_t n_views, int32_t width, int32_t height,
+                                       const void* feats, int32_t dtype, int32_t d,
+                                       float* num, float* den, void* stream);
+
+/* Uplifting, normalisation half (Eq. 3, D^-1 of Eq. 5):
+ *   out[i,:] = num[i,:] / den[i] if den[i] > 0 else 0;  beta[i] = den[i].
+ * num/out may alias (in place); beta may be NULL.  Device arrays. */
+ludvig_status ludvig_uplift_finalize(int64_t n, int32_t d, const float* num, const float* den,
+                                     float* out, float* beta, void* stream);
+
+/* Full uplift f = D^-1 W^T F (Eq. 5): zeroes out (used as the numerator),
+ * accumulates every view and normalises in place.  out: device [n,d] float32;
+ * beta: device [n] float32 (beta_i = sum of weights, the importance score of
+ * Sec. 3.2 "Gaussian filtering") or NULL. */
+ludvig_status ludvig_uplift(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
+                            int32_t width, int32_t height, const void* feats, int32_t dtype,
+                            int32_t d, float* out, float* beta, void* stream);
+
+/* The same uplift from HOST memory: feats is host [n_views,height,width,d]
+ * (pinned memory gives full copy bandwidth), out host [n,d] and beta host [n]
+ * or NULL.  Views are streamed to the device in chunks through a double
+ * buffer that overlaps copies with compute; the call returns after the
+ * results are back in host memory. */
+ludvig_status ludvig_uplift_host(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
+                                 int32_t width, int32_t height, const void* feats, int32_t dtype,
+                                 int32_t d, float* out, float* beta, void* stream);
+
+/* ---- tracing ------------------------------------------------------------ */
+
+/* Stages of the path, as reported by ludvig_trace_read. */
+typedef enum {
+    LUDVIG_STAGE_PROJECT = 0,     /* EWA projection, depth keys, tile rectangles */
+    LUDVIG_STAGE_DEPTH_SORT = 1,  /* radix sort of depths per view */
+    LUDVIG_STAGE_BIN = 2,         /* tiles-touched scan and pair emission */
+    LUDVIG_STAGE_TILE_SORT = 3,   /* radix sort of (view, tile) pairs and tile ranges */
+    LUDVIG_STAGE_COMPOSITE = 4,   /* compositing weights + aggregation (the hot kernel) */
+    LUDVIG_STAGE_NORMALISE = 5,
+    LUDVIG_STAGE_KNN = 6,
+    LUDVIG_STAGE_GRAPH = 7,       /* union edges, weights, normalisation */
+    LUDVIG_STAGE_DIFFUSE = 8,
+    LUDVIG_STAGE_COUNT = 9
+} ludvig_stage;
+
+typedef struct {
+    double ms[16];              /* summed device time per stage (CUDA events) */
+    int64_t calls[16];          /* timed intervals per stage */
+    int64_t kernel_launches;    /* kernels launched by the library */
+} ludvig_trace;
+
+/* Turns stage tracing on or off for the whole process (off by default).
+ * While on, every stage is bracketed by CUDA events recorded on the stream
+ * the stage runs on; the launch counter always runs. */
+ludvig_status ludvig_trace_enable(int32_t on);
+
+/* Waits for the recorded events, adds their durations into *out and, if
+ * reset != 0, clears the trace and the launch counter. */
+ludvig_status ludvig_trace_read(ludvig_trace* out, int32_t reset);
+
+/* ---- inspection entry points (used by the parity tests) ---------------- */
+
+/* Per-Gaussian float32 projection of one view (device outputs):
+ *   rec [n,8]: mean2d.x, mean2d.y, depth, conic a, b, c, opacity, radius
+ *   rect [n,4]: tile rectangle x0,y0,x1,y1 (half-open; all 0 when culled). */
+ludvig_status ludvig_debug_project(ludvig_scene_t scene, const ludvig_camera* cam, int32_t width,
+                                   int32_t height, float* rec, int32_t* rect, void* stream);
+
+/* Depth-ordered per-tile lists of one view.  pruned = 0: every Gaussian whose
+ * tile rectangle covers the tile (the 3DGS binning rule); pruned = 1: the
+ * lists the uplift walks, which additionally drop Gaussians whose
+ * alpha >= 1/255 ellipse cannot reach any pixel centre of the tile (such a
+ * Gaussian is skipped at every pixel of the tile, so no weight changes).
+ * ranges: device [ntiles,2] int64 [start,end) into list; list: device int32
+ * [cap].  *total (host) receives the list length; the list is written only
+ * when total <= cap.  Synchronises `stream`. */
+ludvig_status ludvig_debug_tile_lists(ludvig_scene_t scene, const ludvig_camera* cam,
+                                      int32_t width, int32_t height, int32_t pruned,
+                                      int64_t* ranges, int32_t* list, int64_t cap, int64_t* total,
+                                      void* stream);
+
+/* Per-pixel float32 transmittance after the compositing walk of one view
+ * (device [height,width]) and the number of contributors (device int32). */
+ludvig_status ludvig_debug_transmittance(ludvig_scene_t scene, const ludvig_camera* cam,
+                                         int32_t width, int32_t height, float* t_final,
+                                         int32_t* n_contrib, void* stream);
+
+/* ---- graph diffusion (Sec. 3.3) ----------------------------------------- */
+
+/* Exact k nearest neighbours of every Gaussian centre (Euclidean; the point
+ * itself excluded; squared distances on float32 as (dx*dx+dy*dy)+dz*dz with
+ * d = x_j - x_i; equal distances to the lower index; missing neighbours -1).
+ * nbr: device [n,k] int32.  1 <= k <= 64. */
+ludvig_status ludvig_knn(ludvig_scene_t scene, int32_t k, int32_t* nbr, void* stream);
+
+/* Builds the diffusion graph: the union edge set {i,j : j in N_k(i) or
+ * i in N_k(j)} (Sec. 3.3) with weight
+ *   A_ij = exp(-||mu_i - mu_j||^2 / spatial_h) * max(0, cos(f_i, f_j))
+ * (f: device [n,df] float32 per-Gaussian features, e.g. uplifted DINOv2;
+ * a zero vector has cosine 0), optionally row-normalised (A <- D_A^-1 A, rows
+ * summing to 0 stay 0).  If binarize > 0 weights above it become 1 and the
+ * others 0 before normalisation.  The graph (CSR, float32) lives on the
+ * device until ludvig_graph_destroy. */
+ludvig_status ludvig_graph_build(ludvig_scene_t scene, int32_t k, const float* feats, int32_t df,
+                                 float spatial_h, float binarize, int32_t row_normalize,
+                                 void* stream, ludvig_graph_t* out);
+
+ludvig_status ludvig_graph_destroy(ludvig_graph_t graph);
+
+/* Number of stored (directed) edges of the graph. Synchronises nothing. */
+int64_t ludvig_graph_nnz(ludvig_graph_t graph);
+
+/* Copies the CSR arrays to device buffers: row_ptr [n+1] int64, col [nnz]
+ * int32, val [nnz] float32 (columns sorted within each row). */
+ludvig_status ludvig_graph_export(ludvig_graph_t graph, int64_t* row_ptr, int32_t* col, float* val,
+                                  void* stream);
+
+/* Graph diffusion (Sec. 3.3, Eq. 8) on every column of x0 (device [n,dx]):
+ *   g_0 = x0,  g_{t+1} = A (g_t / ||g_t||_2),  t < iters.
+ * out: device [n,dx]; must not alias x0.  A column whose norm is 0 stays 0.
+ * 1 <= dx <= 32. */
+ludvig_status ludvig_diffuse(ludvig_graph_t graph, const float* x0, int32_t dx, int32_t iters,
+                             float* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LUDVIG_H */

@@ -1,0 +1,147 @@
+// Internal declarations shared by the libludvig translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <unordered_map>
+
+#include "ludvig.h"
+
+namespace ludvig {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+
+// ---------------------------------------------------------------- tracing
+void count_launch();
+bool trace_on();
+int trace_begin(int stage, cudaStream_t st);   // returns a slot or -1
+void trace_end(int slot, cudaStream_t st);
+
+// Brackets a scope with stage events when tracing is on.
+struct StageScope {
+    int slot;
+    cudaStream_t st;
+    StageScope(int stage, cudaStream_t s) : slot(trace_on() ? trace_begin(stage, s) : -1), st(s) {}
+    ~StageScope() {
+        if (slot >= 0) trace_end(slot, st);
+    }
+};
+
+#define LV_CUDA(expr)                                                                      \
+    do {                                                                                   \
+        cudaError_t _e = (expr);                                                           \
+        if (_e != cudaSuccess) {                                                           \
+            ::ludvig::set_error("%s:%d %s: %s", __FILE__, __LINE__, #expr,                  \
+                                cudaGetErrorString(_e));                                   \
+            return _e == cudaErrorMemoryAllocation ? LUDVIG_ERR_OOM : LUDVIG_ERR_CUDA;      \
+        }                                                                                  \
+    } while (0)
+
+#define LV_LAUNCH()                                                                        \
+    do {                                                                                   \
+        ::ludvig::count_launch();                                                          \
+        cudaError_t _e = cudaGetLastError();                                               \
+        if (_e != cudaSuccess) {                                                           \
+            ::ludvig::set_error("%s:%d kernel launch: %s", __FILE__, __LINE__,              \
+                                cudaGetErrorString(_e));                                   \
+            return LUDVIG_ERR_CUDA;                                                        \
+        }                                                                                  \
+    } while (0)
+
+#define LV_TRY(expr)                                                                       \
+    do {                                                                                   \
+        ludvig_status _s = (expr);                                                         \
+        if (_s != LUDVIG_OK) return _s;                                                    \
+    } while (0)
+
+#define LV_ARG(cond, ...)                                                                  \
+    do {                                                                                   \
+        if (!(cond)) {                                                                     \
+            ::ludvig::set_error(__VA_ARGS__);                                              \
+            return LUDVIG_ERR_ARG;                                                         \
+        }                                                                                  \
+    } while (0)
+
+// ---------------------------------------------------------------- workspace
+// Grow-only named device buffers.  A buffer keeps its contents only until the
+// next call that grows it; callers treat workspace as scratch.
+class Arena {
+  public:
+    ~Arena();
+    // Returns a device buffer of at least `bytes` bytes (256-byte aligned).
+    ludvig_status get(const char* name, size_t bytes, void** out);
+    template <class T>
+    ludvig_status get(const char* name, size_t count, T** out) {
+        void* p = nullptr;
+        ludvig_status s = get(name, count * sizeof(T), &p);
+        *out = static_cast<T*>(p);
+        return s;
+    }
+    ludvig_status pinned(const char* name, size_t bytes, void** out);   // host, page-locked
+    void release();
+
+  private:
+    struct Buf {
+        void* ptr = nullptr;
+        size_t bytes = 0;
+    };
+    std::unordered_map<std::string, Buf> dev_, host_;
+};
+
+}  // namespace ludvig
+
+// The opaque scene: a device copy of the Gaussians with the view-independent
+// 3D covariance precomputed.
+struct ludvig_scene {
+    int64_t n = 0;
+    int device = 0;
+    float4* geo = nullptr;     // [n] (mean.x, mean.y, mean.z, opacity)
+    float4* cov_a = nullptr;   // [n] (S00, S01, S02, S11)
+    float2* cov_b = nullptr;   // [n] (S12, S22)
+    float* means = nullptr;    // [n,3] copy (kNN, graph)
+    cudaStream_t copy_stream = nullptr;   // host-feature uploads (created on first use)
+    cudaEvent_t ev_ready[2] = {nullptr, nullptr};
+    cudaEvent_t ev_free[2] = {nullptr, nullptr};
+    ludvig::Arena ws;
+};
+
+struct ludvig_graph {
+    int64_t n = 0;
+    int64_t nnz = 0;
+    int device = 0;
+    int64_t* row_ptr = nullptr;   // [n+1]
+    int32_t* col = nullptr;       // [nnz]
+    float* val = nullptr;         // [nnz]
+    ludvig::Arena ws;
+};
+
+namespace ludvig {
+
+// ---------------------------------------------------------------- primitives
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 16;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;   // keys per sort block
+
+// Exclusive prefix sum of n uint32 values (in-place allowed).  *total_dev
+// (device, may be null) receives the exact 64-bit sum; the uint32 prefixes are
+// meaningful only while that sum stays below 2^32.
+ludvig_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* total_dev,
+                                 Arena& ws, cudaStream_t st);
+
+// Stable LSD radix sort of (key, value) pairs on key bits [0, nbits), applied
+// independently to nseg consecutive segments of seg_len entries each
+// (seg_len % kRadixTile == 0).  Sorted data ends in (*keys, *vals), which may
+// be swapped with (keys_alt, vals_alt).
+ludvig_status radix_sort_pairs(uint32_t** keys, uint32_t** vals, uint32_t* keys_alt,
+                               uint32_t* vals_alt, int64_t nseg, int64_t seg_len, int nbits,
+                               Arena& ws, cudaStream_t st);
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }
+
+}  // namespace ludvig

@@ -1,0 +1,716 @@
+// Graph diffusion over the Gaussians (Sec. 3.3): exact kNN of the centres,
+// the union edge set with similarity weights (Eq. 7 / the diffusion
+// workload's spatial x cosine weight), and the power iteration of Eq. 8.
+//
+// kNN: points are bucketed in a uniform grid (cells sorted by the radix sort);
+// one thread per query scans cells ring by ring (Chebyshev distance r around
+// its own cell) and stops once the k-th best squared distance is below the
+// squared gap r*cell to the unvisited rings.  Squared distances are float32
+// (dx*dx + dy*dy) + dz*dz with d = x_j - x_i and ties go to the lower index,
+// so the result is exact and independent of the scan order.
+//
+// Graph: own neighbours plus reverse edges per row, one warp sorts and
+// de-duplicates each row, then weights are computed per edge from the two
+// feature rows and optionally thresholded and row-normalised.
+//
+// Diffusion: one kernel per step computes y = A x * (1/||x||) row by row and
+// accumulates ||y||^2 (float64) for the next step's scaling.
+#include <algorithm>
+#include <cfloat>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ludvig {
+
+namespace {
+
+unsigned grid_for(int64_t work, int threads) { return (unsigned)ceil_div(work, threads); }
+
+// ------------------------------------------------------------ bounding box
+__global__ void k_bbox(const float* __restrict__ x, int64_t n, float* __restrict__ out6) {
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fminf(lo[a], x[3 * i + a]);
+            hi[a] = fmaxf(hi[a], x[3 * i + a]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            // order-preserving integer encoding of floats for atomicMin/Max
+            const int l = __float_as_int(lo[a]), h = __float_as_int(hi[a]);
+            atomicMin(reinterpret_cast<int*>(out6) + a, l >= 0 ? l : l ^ 0x7fffffff);
+            atomicMax(reinterpret_cast<int*>(out6) + 3 + a, h >= 0 ? h : h ^ 0x7fffffff);
+        }
+    }
+}
+
+struct Grid {
+    float lo[3];
+    float cell;
+    float inv_cell;
+    int g[3];
+};
+
+__device__ __forceinline__ int cell_coord(float x, float lo, float inv, int g) {
+    int c = (int)floorf((x - lo) * inv);
+    return c < 0 ? 0 : (c >= g ? g - 1 : c);
+}
+
+__global__ void k_cell_keys(const float* __restrict__ x, int64_t n, int64_t npad, Grid gr,
+                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npad) return;
+    if (i >= n) {
+        keys[i] = 0xffffffffu;
+        vals[i] = 0xffffffffu;
+        return;
+    }
+    const int cx = cell_coord(x[3 * i], gr.lo[0], gr.inv_cell, gr.g[0]);
+    const int cy = cell_coord(x[3 * i + 1], gr.lo[1], gr.inv_cell, gr.g[1]);
+    const int cz = cell_coord(x[3 * i + 2], gr.lo[2], gr.inv_cell, gr.g[2]);
+    keys[i] = (uint32_t)(((int64_t)cz * gr.g[1] + cy) * gr.g[0] + cx);
+    vals[i] = (uint32_t)i;
+}
+
+__global__ void k_cell_ranges(const uint32_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const uint32_t k = keys[j];
+    if (j == 0 || keys[j - 1] != k) ranges[k].x = (uint32_t)j;
+    if (j == n - 1 || keys[j + 1] != k) ranges[k].y = (uint32_t)(j + 1);
+}
+
+__device__ __forceinline__ bool closer(float d, uint32_t i, float bd, uint32_t bi) {
+    return d < bd || (d == bd && i < bi);
+}
+
+// Points sorted by cell are stored as float4 (x, y, z, index) in cell order.
+__global__ void k_gather_sorted(const float* __restrict__ x, const uint32_t* __restrict__ order,
+                                int64_t n, float4* __restrict__ pts) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const uint32_t i = order[j];
+    pts[j] = make_float4(x[3 * i], x[3 * i + 1], x[3 * i + 2], __uint_as_float(i));
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) k_knn(const float4* __restrict__ pts, int64_t n, Grid gr,
+                                             const uint2* __restrict__ cells, int k,
+                                             int32_t* __restrict__ out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const float4 q = pts[j];
+    const uint32_t qi = __float_as_uint(q.w);
+    float bd[K];
+    uint32_t bi[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        bd[t] = FLT_MAX;
+        bi[t] = 0xffffffffu;
+    }
+    int have = 0;
+    const int cx = cell_coord(q.x, gr.lo[0], gr.inv_cell, gr.g[0]);
+    const int cy = cell_coord(q.y, gr.lo[1], gr.inv_cell, gr.g[1]);
+    const int cz = cell_coord(q.z, gr.lo[2], gr.inv_cell, gr.g[2]);
+    const int rmax = max(gr.g[0], max(gr.g[1], gr.g[2]));
+    for (int r = 0; r <= rmax; ++r) {
+        for (int dz = -r; dz <= r; ++dz) {
+            const int z = cz + dz;
+            if (z < 0 || z >= gr.g[2]) continue;
+            for (int dy = -r; dy <= r; ++dy) {
+                const int y = cy + dy;
+                if (y < 0 || y >= gr.g[1]) continue;
+                const bool face = (dz == -r || dz == r || dy == -r || dy == r);
+                const int step = face ? 1 : 2 * r;
+                for (int dx = -r; dx <= r; dx += (step > 0 ? step : 1)) {
+                    const int x = cx + dx;
+                    if (x < 0 || x >= gr.g[0]) continue;
+                    const uint2 rg = cells[((int64_t)z * gr.g[1] + y) * gr.g[0] + x];
+                    for (uint32_t p = rg.x; p < rg.y; ++p) {
+                        const float4 c = pts[p];
+                        const uint32_t ci = __float_as_uint(c.w);
+                        if (ci == qi) continue;
+                        const float ex = __fsub_rn(c.x, q.x), ey = __fsub_rn(c.y, q.y),
+                                    ez = __fsub_rn(c.z, q.z);
+                        const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)),
+                                                   __fmul_rn(ez, ez));
+                        if (!closer(d2, ci, bd[K - 1], bi[K - 1])) continue;
+                        float cd = d2;
+                        uint32_t cidx = ci;
+#pragma unroll
+                        for (int t = 0; t < K; ++t) {
+                            if (closer(cd, cidx, bd[t], bi[t])) {
+                                const float td = bd[t];
+                                const uint32_t ti = bi[t];
+                                bd[t] = cd;
+                                bi[t] = cidx;
+                                cd = td;
+                                cidx = ti;
+                            }
+                        }
+                        ++have;
+                    }
+                }
+            }
+        }
+        // every point outside the visited (2r+1)^3 block is at least r cells away
+        if (have >= k) {
+            const float gap = (float)r * gr.cell;
+            // 0.1% margin: rounding can put a point next to a cell border in the neighbour cell
+            const float bound = gap * gap * 0.999f;
+            float kth = 0.f;
+#pragma unroll
+            for (int t = 0; t < K; ++t)
+                if (t == k - 1) kth = bd[t];
+            if (kth < bound) break;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < K; ++t)
+        if (t < k) out[(int64_t)qi * k + t] = bi[t] == 0xffffffffu ? -1 : (int32_t)bi[t];
+}
+
+// ------------------------------------------------------------ graph build
+__global__ void k_own_and_indegree(const int32_t* __restrict__ nbr, int64_t n, int k,
+                                   uint32_t* __restrict__ own, uint32_t* __restrict__ indeg) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t c = 0;
+    for (int t = 0; t < k; ++t) {
+        const int32_t j = nbr[i * k + t];
+        if (j >= 0 && j != i) {
+            ++c;
+            atomicAdd(&indeg[j], 1u);
+        }
+    }
+    own[i] = c;
+}
+
+__global__ void k_row_counts(const uint32_t* __restrict__ own, const uint32_t* __restrict__ indeg,
+                             int64_t n, uint32_t* __restrict__ cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cnt[i] = own[i] + indeg[i];
+}
+
+__global__ void k_fill_rows(const int32_t* __restrict__ nbr, int64_t n, int k,
+                            const uint32_t* __restrict__ ptr, const uint32_t* __restrict__ own,
+                            uint32_t* __restrict__ cursor, uint32_t* __restrict__ tcol) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t o = ptr[i];
+    for (int t = 0; t < k; ++t) {
+        const int32_t j = nbr[i * k + t];
+        if (j >= 0 && j != i) {
+            tcol[o++] = (uint32_t)j;
+            const uint32_t pos = atomicAdd(&cursor[j], 1u);
+            tcol[ptr[j] + own[j] + pos] = (uint32_t)i;
+        }
+    }
+}
+
+// One warp per row: sort the row's column indices (insertion sort through
+// shared memory for short rows, a serial heap sort in place for long ones),
+// then count the distinct values.
+constexpr int kRowSmem = 256;
+__global__ void __launch_bounds__(256) k_sort_unique_rows(uint32_t* __restrict__ tcol,
+                                                         const uint32_t* __restrict__ ptr,
+                                                         const uint32_t* __restrict__ cnt, int64_t n,
+                                                         uint32_t* __restrict__ ucnt) {
+    __shared__ uint32_t buf[8][kRowSmem];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+    if (i >= n) return;
+    uint32_t* row = tcol + ptr[i];
+    const uint32_t c = cnt[i];
+    uint32_t* b = buf[warp];
+    if (c <= kRowSmem) {
+        for (uint32_t t = lane; t < c; t += 32) b[t] = row[t];
+        __syncwarp();
+        // rank sort: each element's position = number of smaller elements
+        // (+ equal elements before it), which is a stable sort of the row
+        for (uint32_t t = lane; t < c; t += 32) {
+            const uint32_t v = b[t];
+            uint32_t pos = 0;
+            for (uint32_t u = 0; u < c; ++u) {
+                const uint32_t w = b[u];
+                pos += (w < v) || (w == v && u < t);
+            }
+            row[pos] = v;
+        }
+        __syncwarp();
+    } else if (lane == 0) {
+        // heap sort in place
+        auto sift = [&](uint32_t start, uint32_t end) {
+            uint32_t root = start;
+            while (2 * root + 1 < end) {
+                uint32_t child = 2 * root + 1;
+                if (child + 1 < end && row[child] < row[child + 1]) ++child;
+                if (row[root] < row[child]) {
+                    const uint32_t t = row[root];
+                    row[root] = row[child];
+                    row[child] = t;
+                    root = child;
+                } else {
+                    break;
+                }
+            }
+        };
+        for (int64_t s = (int64_t)c / 2 - 1; s >= 0; --s) sift((uint32_t)s, c);
+        for (uint32_t e = c - 1; e > 0; --e) {
+            const uint32_t t = row[0];
+            row[0] = row[e];
+            row[e] = t;
+            sift(0, e);
+        }
+    }
+    __syncwarp();
+    uint32_t u = 0;
+    for (uint32_t t = lane; t < c; t += 32) u += (t == 0 || row[t] != row[t - 1]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+    if (lane == 0) ucnt[i] = u;
+}
+
+__global__ void k_norms(const float* __restrict__ f, int64_t n, int df, float* __restrict__ nrm) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (i >= n) return;
+    float s = 0.f;
+    for (int c = lane; c < df; c += 32) {
+        const float v = f[i * df + c];
+        s = fmaf(v, v, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) nrm[i] = sqrtf(s);
+}
+
+// One warp per row: compact the distinct columns, weight every edge, then
+// threshold / normalise the row.
+__global__ void __launch_bounds__(256) k_weights(const uint32_t* __restrict__ tcol,
+                                                const uint32_t* __restrict__ tptr,
+                                                const uint32_t* __restrict__ tcnt,
+                                                const int64_t* __restrict__ row_ptr,
+                                                const float* __restrict__ x, const float* __restrict__ f,
+                                                const float* __restrict__ nrm, int64_t n, int df,
+                                                float inv_h, float binarize, int row_normalize,
+                                                int32_t* __restrict__ col, float* __restrict__ val) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+    if (i >= n) return;
+    const uint32_t* row = tcol + tptr[i];
+    const uint32_t c = tcnt[i];
+    const int64_t o0 = row_ptr[i];
+    const float xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
+    const float ni = nrm[i];
+    const float* fi = f + i * df;
+    int64_t o = o0;
+    float rsum = 0.f;
+    for (uint32_t t = 0; t < c; ++t) {
+        const uint32_t j = row[t];
+        if (t > 0 && row[t - 1] == j) continue;   // duplicate (mutual neighbours)
+        float dot = 0.f;
+        const float* fj = f + (int64_t)j * df;
+        for (int ch = lane; ch < df; ch += 32) dot = fmaf(fi[ch], fj[ch], dot);
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, s);
+        if (lane == 0) {
+            const float ex = x[3 * j] - xi, ey = x[3 * j + 1] - yi, ez = x[3 * j + 2] - zi;
+            const float d2 = ex * ex + ey * ey + ez * ez;
+            const float den = ni * nrm[j];
+            const float cs = den > 0.f ? dot / den : 0.f;
+            float w = expf(-d2 * inv_h) * fmaxf(0.f, cs);
+            if (binarize > 0.f) w = w > binarize ? 1.f : 0.f;
+            col[o] = (int32_t)j;
+            val[o] = w;
+            rsum += w;
+        }
+        ++o;
+    }
+    if (row_normalize && lane == 0) {
+        const float inv = rsum > 0.f ? 1.0f / rsum : 0.f;
+        for (int64_t e = o0; e < o; ++e) val[e] *= inv;
+    }
+}
+
+__global__ void k_ucnt_to_u64(const uint32_t* __restrict__ u, int64_t n, int64_t* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = u[i];
+}
+
+// exclusive scan into int64 row pointers (u32 scan + widening is enough while nnz < 2^32)
+__global__ void k_widen_ptr(const uint32_t* __restrict__ p, int64_t n, const uint64_t* __restrict__ total,
+                            int64_t* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = p[i];
+    if (i == n) out[n] = (int64_t)*total;
+}
+
+// ------------------------------------------------------------ diffusion
+__global__ void k_colnorm2(const float* __restrict__ x, int64_t n, int dx, double* __restrict__ acc) {
+    __shared__ double part[32][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = 0; c < dx; ++c) {
+        double v = 0.0;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const double t = x[i * dx + c];
+            v += t * t;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) part[warp][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < dx) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += part[w][threadIdx.x];
+        atomicAdd(acc + threadIdx.x, v);
+    }
+}
+
+// y = A (x / ||x||).  dx == 1: groups of kLanes lanes per row over a
+// grid-stride range of rows; dx > 1: warp per row, lane = column.  ||y||^2 per
+// column is reduced in the block and added once per block (float64).
+template <int kLanes>
+__global__ void __launch_bounds__(256) k_spmv_scaled(const int64_t* __restrict__ rp,
+                                                    const int32_t* __restrict__ col,
+                                                    const float* __restrict__ val,
+                                                    const float* __restrict__ x, int64_t n, int dx,
+                                                    const double* __restrict__ n2_in,
+                                                    float* __restrict__ y, double* __restrict__ n2_out) {
+    __shared__ double part[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (kLanes == 1) {
+        double mine = 0.0;
+        const double nn = lane < dx ? n2_in[lane] : 0.0;
+        const float s = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.f;
+        for (int64_t i = (int64_t)blockIdx.x * 8 + warp; i < n; i += (int64_t)gridDim.x * 8) {
+            if (lane < dx) {
+                float acc = 0.f;
+                for (int64_t e = rp[i]; e < rp[i + 1]; ++e) acc = fmaf(val[e], x[(int64_t)col[e] * dx + lane], acc);
+                acc *= s;
+                y[i * dx + lane] = acc;
+                mine += (double)acc * acc;
+            }
+        }
+        part[warp][lane] = mine;
+        __syncthreads();
+        if (threadIdx.x < dx) {
+            double t = 0.0;
+            for (int w = 0; w < 8; ++w) t += part[w][threadIdx.x];
+            atomicAdd(n2_out + threadIdx.x, t);
+        }
+    } else {
+        const int sub = lane % kLanes;
+        const double nn = n2_in[0];
+        const float s = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.f;
+        double mine = 0.0;
+        const int64_t groups = (int64_t)gridDim.x * (blockDim.x / kLanes);
+        const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kLanes;
+        for (int64_t base = 0; base < n; base += groups) {
+            const int64_t i = base + g0;
+            float acc = 0.f;
+            if (i < n)
+                for (int64_t e = rp[i] + sub; e < rp[i + 1]; e += kLanes) acc = fmaf(val[e], x[col[e]], acc);
+#pragma unroll
+            for (int o = kLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (i < n && sub == 0) {
+                acc *= s;
+                y[i] = acc;
+                mine += (double)acc * acc;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+        if (lane == 0) part[warp][0] = mine;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < 8; ++w) t += part[w][0];
+            atomicAdd(n2_out, t);
+        }
+    }
+}
+
+ludvig_status knn_impl(ludvig_scene* s, int k, int32_t* nbr, cudaStream_t st) {
+    Arena& ws = s->ws;
+    const int64_t n = s->n;
+    float* bb;
+    LV_TRY(ws.get("knn.bbox", 8, &bb));
+    {
+        const int init[6] = {0x7fffffff, 0x7fffffff, 0x7fffffff, (int)0x80000000, (int)0x80000000,
+                             (int)0x80000000};
+        void* h;
+        LV_TRY(ws.pinned("knn.bbox_h", 64, &h));
+        std::memcpy(h, init, sizeof(init));
+        LV_CUDA(cudaMemcpyAsync(bb, h, sizeof(init), cudaMemcpyHostToDevice, st));
+        k_bbox<<<(unsigned)std::min<int64_t>(1024, ceil_div(n, 256)), 256, 0, st>>>(s->means, n, bb);
+        LV_LAUNCH();
+        LV_CUDA(cudaMemcpyAsync(static_cast<char*>(h) + 32, bb, 24, cudaMemcpyDeviceToHost, st));
+        LV_CUDA(cudaStreamSynchronize(st));
+        int enc[6];
+        std::memcpy(enc, static_cast<char*>(h) + 32, 24);
+        float lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            int l = enc[a] >= 0 ? enc[a] : enc[a] ^ 0x7fffffff;
+            int hh = enc[3 + a] >= 0 ? enc[3 + a] : enc[3 + a] ^ 0x7fffffff;
+            std::memcpy(&lo[a], &l, 4);
+            std::memcpy(&hi[a], &hh, 4);
+        }
+        Grid gr;
+        double ext[3], vol = 1.0;
+        for (int a = 0; a < 3; ++a) {
+            ext[a] = std::max(1e-6, (double)hi[a] - (double)lo[a]);
+            vol *= ext[a];
+        }
+        // about two points per cell on average, at most 2^24 cells
+        double cell = std::cbrt(vol * 2.0 / (double)std::max<int64_t>(n, 1));
+        for (;;) {
+            int64_t tot = 1;
+            for (int a = 0; a < 3; ++a) tot *= (int64_t)(ext[a] / cell) + 1;
+            if (tot <= ((int64_t)1 << 24)) break;
+            cell *= 1.25;
+        }
+        for (int a = 0; a < 3; ++a) {
+            gr.lo[a] = lo[a];
+            gr.g[a] = (int)(ext[a] / cell) + 1;
+        }
+        gr.cell = (float)cell;
+        gr.inv_cell = (float)(1.0 / cell);
+        const int64_t ncell = (int64_t)gr.g[0] * gr.g[1] * gr.g[2];
+        const int64_t npad = round_up(n, kRadixTile);
+        uint32_t *keys, *vals, *keys2, *vals2;
+        LV_TRY(ws.get("knn.keys", (size_t)npad, &keys));
+        LV_TRY(ws.get("knn.vals", (size_t)npad, &vals));
+        LV_TRY(ws.get("knn.keys2", (size_t)npad, &keys2));
+        LV_TRY(ws.get("knn.vals2", (size_t)npad, &vals2));
+        k_cell_keys<<<grid_for(npad, 256), 256, 0, st>>>(s->means, n, npad, gr, keys, vals);
+        LV_LAUNCH();
+        int nbits = 1;
+        while (((int64_t)1 << nbits) <= ncell) ++nbits;
+        uint32_t *sk = keys, *sv = vals;
+        LV_TRY(radix_sort_pairs(&sk, &sv, keys2, vals2, 1, npad, nbits, ws, st));
+        uint2* cells;
+        LV_TRY(ws.get("knn.cells", (size_t)ncell, &cells));
+        LV_CUDA(cudaMemsetAsync(cells, 0, sizeof(uint2) * (size_t)ncell, st));
+        k_cell_ranges<<<grid_for(n, 256), 256, 0, st>>>(sk, n, cells);
+        LV_LAUNCH();
+        float4* pts;
+        LV_TRY(ws.get("knn.pts", (size_t)n, &pts));
+        k_gather_sorted<<<grid_for(n, 256), 256, 0, st>>>(s->means, sv, n, pts);
+        LV_LAUNCH();
+        const unsigned g = grid_for(n, 128);
+        if (k <= 8) k_knn<8><<<g, 128, 0, st>>>(pts, n, gr, cells, k, nbr);
+        else if (k <= 16) k_knn<16><<<g, 128, 0, st>>>(pts, n, gr, cells, k, nbr);
+        else if (k <= 32) k_knn<32><<<g, 128, 0, st>>>(pts, n, gr, cells, k, nbr);
+        else k_knn<64><<<g, 128, 0, st>>>(pts, n, gr, cells, k, nbr);
+        LV_LAUNCH();
+    }
+    return LUDVIG_OK;
+}
+
+}  // namespace
+
+}  // namespace ludvig
+
+using namespace ludvig;
+
+extern "C" ludvig_status ludvig_knn(ludvig_scene_t scene, int32_t k, int32_t* nbr, void* stream) {
+    LV_ARG(scene != nullptr && nbr != nullptr, "NULL argument");
+    LV_ARG(k >= 1 && k <= 64, "k must be in [1, 64]");
+    if (scene->n == 0) return LUDVIG_OK;
+    StageScope scope(LUDVIG_STAGE_KNN, static_cast<cudaStream_t>(stream));
+    return knn_impl(scene, k, nbr, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" ludvig_status ludvig_graph_build(ludvig_scene_t scene, int32_t k, const float* feats, int32_t df,
+                                            float spatial_h, float binarize, int32_t row_normalize,
+                                            void* stream, ludvig_graph_t* out) {
+    LV_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    LV_ARG(scene != nullptr, "scene is NULL");
+    LV_ARG(k >= 1 && k <= 64, "k must be in [1, 64]");
+    LV_ARG(df >= 1 && feats != nullptr, "features required (df >= 1)");
+    LV_ARG(spatial_h > 0.f, "spatial_h must be positive");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ludvig_graph* g = new ludvig_graph();
+    g->n = scene->n;
+    LV_CUDA(cudaGetDevice(&g->device));
+    const int64_t n = scene->n;
+    Arena& ws = scene->ws;
+    auto fail = [&](ludvig_status s) {
+        ludvig_graph_destroy(g);
+        return s;
+    };
+    ludvig_status r;
+    if (cudaMalloc(&g->row_ptr, sizeof(int64_t) * (size_t)(n + 1)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("graph allocation failed");
+        return fail(LUDVIG_ERR_OOM);
+    }
+    if (n == 0) {
+        if (cudaMemsetAsync(g->row_ptr, 0, sizeof(int64_t), st) != cudaSuccess) return fail(LUDVIG_ERR_CUDA);
+        *out = g;
+        return LUDVIG_OK;
+    }
+    int32_t* nbr;
+    uint32_t *own, *indeg, *cnt, *tptr, *cursor, *ucnt, *uptr;
+    uint64_t *tot_d, *utot_d;
+    float* nrm;
+#define GB_TRY(expr)                   \
+    do {                               \
+        r = (expr);                    \
+        if (r != LUDVIG_OK) return fail(r); \
+    } while (0)
+    GB_TRY(ws.get("g.nbr", (size_t)n * k, &nbr));
+    GB_TRY(ws.get("g.own", (size_t)n, &own));
+    GB_TRY(ws.get("g.indeg", (size_t)n, &indeg));
+    GB_TRY(ws.get("g.cnt", (size_t)n, &cnt));
+    GB_TRY(ws.get("g.tptr", (size_t)n, &tptr));
+    GB_TRY(ws.get("g.cursor", (size_t)n, &cursor));
+    GB_TRY(ws.get("g.ucnt", (size_t)n, &ucnt));
+    GB_TRY(ws.get("g.uptr", (size_t)n, &uptr));
+    GB_TRY(ws.get("g.tot", 2, &tot_d));
+    utot_d = tot_d + 1;
+    GB_TRY(ws.get("g.nrm", (size_t)n, &nrm));
+    {
+        StageScope scope(LUDVIG_STAGE_KNN, st);
+        GB_TRY(knn_impl(scene, k, nbr, st));
+    }
+    StageScope gscope(LUDVIG_STAGE_GRAPH, st);
+    if (cudaMemsetAsync(indeg, 0, sizeof(uint32_t) * n, st) != cudaSuccess ||
+        cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * n, st) != cudaSuccess)
+        return fail(LUDVIG_ERR_CUDA);
+    k_own_and_indegree<<<grid_for(n, 256), 256, 0, st>>>(nbr, n, k, own, indeg);
+    count_launch();
+    k_row_counts<<<grid_for(n, 256), 256, 0, st>>>(own, indeg, n, cnt);
+    count_launch();
+    GB_TRY(scan_exclusive_u32(cnt, tptr, n, tot_d, ws, st));
+    void* hbuf;
+    GB_TRY(ws.pinned("g.tot_h", 16, &hbuf));
+    uint64_t* tot_h = static_cast<uint64_t*>(hbuf);
+    if (cudaMemcpyAsync(tot_h, tot_d, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return fail(LUDVIG_ERR_CUDA);
+    const int64_t tnnz = (int64_t)tot_h[0];
+    if (tnnz >= ((int64_t)1 << 32)) {
+        set_error("graph too large");
+        return fail(LUDVIG_ERR_UNSUPPORTED);
+    }
+    uint32_t* tcol;
+    GB_TRY(ws.get("g.tcol", (size_t)std::max<int64_t>(tnnz, 1), &tcol));
+    k_fill_rows<<<grid_for(n, 256), 256, 0, st>>>(nbr, n, k, tptr, own, cursor, tcol);
+    count_launch();
+    k_sort_unique_rows<<<grid_for(n, 8), 256, 0, st>>>(tcol, tptr, cnt, n, ucnt);
+    count_launch();
+    GB_TRY(scan_exclusive_u32(ucnt, uptr, n, utot_d, ws, st));
+    k_widen_ptr<<<grid_for(n + 1, 256), 256, 0, st>>>(uptr, n, utot_d, g->row_ptr);
+    count_launch();
+    k_norms<<<grid_for(n, 8), 256, 0, st>>>(feats, n, df, nrm);
+    count_launch();
+    if (cudaMemcpyAsync(tot_h + 1, utot_d, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return fail(LUDVIG_ERR_CUDA);
+    g->nnz = (int64_t)tot_h[1];
+    if (cudaMalloc(&g->col, sizeof(int32_t) * (size_t)std::max<int64_t>(g->nnz, 1)) != cudaSuccess ||
+        cudaMalloc(&g->val, sizeof(float) * (size_t)std::max<int64_t>(g->nnz, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("graph allocation failed");
+        return fail(LUDVIG_ERR_OOM);
+    }
+    k_weights<<<grid_for(n, 8), 256, 0, st>>>(tcol, tptr, cnt, g->row_ptr, scene->means, feats, nrm, n,
+                                              df, 1.0f / spatial_h, binarize, row_normalize, g->col, g->val);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) {
+        set_error("graph kernels failed to launch");
+        return fail(LUDVIG_ERR_CUDA);
+    }
+#undef GB_TRY
+    *out = g;
+    return LUDVIG_OK;
+}
+
+extern "C" ludvig_status ludvig_graph_destroy(ludvig_graph_t g) {
+    if (!g) return LUDVIG_OK;
+    cudaDeviceSynchronize();
+    cudaFree(g->row_ptr);
+    cudaFree(g->col);
+    cudaFree(g->val);
+    g->ws.release();
+    delete g;
+    return LUDVIG_OK;
+}
+
+extern "C" int64_t ludvig_graph_nnz(ludvig_graph_t g) { return g ? g->nnz : -1; }
+
+extern "C" ludvig_status ludvig_graph_export(ludvig_graph_t g, int64_t* row_ptr, int32_t* col, float* val,
+                                             void* stream) {
+    LV_ARG(g != nullptr, "graph is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (row_ptr) LV_CUDA(cudaMemcpyAsync(row_ptr, g->row_ptr, sizeof(int64_t) * (g->n + 1), cudaMemcpyDeviceToDevice, st));
+    if (g->nnz > 0) {
+        if (col) LV_CUDA(cudaMemcpyAsync(col, g->col, sizeof(int32_t) * g->nnz, cudaMemcpyDeviceToDevice, st));
+        if (val) LV_CUDA(cudaMemcpyAsync(val, g->val, sizeof(float) * g->nnz, cudaMemcpyDeviceToDevice, st));
+    }
+    return LUDVIG_OK;
+}
+
+extern "C" ludvig_status ludvig_diffuse(ludvig_graph_t g, const float* x0, int32_t dx, int32_t iters,
+                                        float* out, void* stream) {
+    LV_ARG(g != nullptr, "graph is NULL");
+    LV_ARG(dx >= 1 && dx <= 32, "dx must be in [1, 32]");
+    LV_ARG(iters >= 0, "iters must be >= 0");
+    LV_ARG(x0 != nullptr && out != nullptr, "NULL buffer");
+    LV_ARG(x0 != out, "out must not alias x0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t n = g->n;
+    if (n == 0) return LUDVIG_OK;
+    const size_t bytes = sizeof(float) * (size_t)n * dx;
+    if (iters == 0) {
+        LV_CUDA(cudaMemcpyAsync(out, x0, bytes, cudaMemcpyDeviceToDevice, st));
+        return LUDVIG_OK;
+    }
+    float* tmp;
+    double* n2;
+    LV_TRY(g->ws.get("d.tmp", (size_t)n * dx, &tmp));
+    // n2[t*32 + c] = ||column c of g_t||^2, every step's slot zeroed up front
+    LV_TRY(g->ws.get("d.n2", (size_t)(iters + 1) * 32, &n2));
+    // ping-pong so that the last step writes `out`
+    float* bufs[2] = {(iters % 2 == 1) ? out : tmp, (iters % 2 == 1) ? tmp : out};
+    StageScope scope(LUDVIG_STAGE_DIFFUSE, st);
+    LV_CUDA(cudaMemsetAsync(n2, 0, sizeof(double) * 32 * (size_t)(iters + 1), st));
+    k_colnorm2<<<(unsigned)std::min<int64_t>(592, ceil_div(n, 256)), 256, 0, st>>>(x0, n, dx, n2);
+    LV_LAUNCH();
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, ceil_div(n, 32)));
+    const float* xin = x0;
+    for (int t = 0; t < iters; ++t) {
+        float* y = bufs[t & 1];
+        if (dx == 1)
+            k_spmv_scaled<8><<<blocks, 256, 0, st>>>(g->row_ptr, g->col, g->val, xin, n, 1, n2 + 32 * t, y,
+                                                     n2 + 32 * (t + 1));
+        else
+            k_spmv_scaled<1><<<blocks, 256, 0, st>>>(g->row_ptr, g->col, g->val, xin, n, dx, n2 + 32 * t, y,
+                                                     n2 + 32 * (t + 1));
+        LV_LAUNCH();
+        xin = y;
+    }
+    return LUDVIG_OK;
+}

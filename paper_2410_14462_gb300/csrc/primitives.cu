@@ -1,0 +1,256 @@
+// Device-wide exclusive scan and stable LSD radix sort (reduce-then-scan).
+//
+// The radix sort orders (key, value) pairs by 8-bit digits, least significant
+// first.  Each pass: (1) every block histograms the digits of its 4096-key
+// tile, (2) one exclusive scan over the histograms laid out
+// [segment][digit][block] gives every (block, digit) its output base, (3)
+// every block re-reads its tile in order and scatters each key to
+// base + (number of equal digits before it in the tile), found with warp
+// match/popc and a per-digit prefix over the warps.  Segment-major histogram
+// order keeps equal-length segments apart, so one launch sorts many views.
+#include "common.cuh"
+
+namespace ludvig {
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* out_excl) {
+    __shared__ uint32_t warp_tot[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    uint32_t incl = warp_incl_scan(v);
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = lane < nwarps ? warp_tot[lane] : 0u;
+        t = warp_incl_scan(t);
+        warp_tot[lane] = t;   // inclusive over warps
+    }
+    __syncthreads();
+    const uint32_t before = warp > 0 ? warp_tot[warp - 1] : 0u;
+    *out_excl = before + incl - v;
+    const uint32_t total = warp_tot[nwarps - 1];
+    __syncthreads();
+    return total;
+}
+
+__device__ __forceinline__ unsigned long long warp_incl_scan64(unsigned long long v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// 64-bit block sum (a tile of 4096 counts may exceed 32 bits).
+__device__ __forceinline__ unsigned long long block_sum64(unsigned long long v) {
+    __shared__ unsigned long long part[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) part[warp] = v;
+    __syncthreads();
+    unsigned long long t = 0;
+    if (warp == 0) {
+        t = lane < (int)((blockDim.x + 31) >> 5) ? part[lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    __syncthreads();
+    return t;   // valid in warp 0
+}
+
+__global__ void k_scan_reduce(const uint32_t* __restrict__ in, int64_t n,
+                              unsigned long long* __restrict__ sums) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    unsigned long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < n) s += in[base + i];
+    const unsigned long long tot = block_sum64(s);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Single block: exclusive scan of the block sums in place, carrying across chunks.
+__global__ void k_scan_sums(unsigned long long* __restrict__ sums, int64_t nb,
+                            unsigned long long* __restrict__ total) {
+    __shared__ unsigned long long wt[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    unsigned long long carry = 0;
+    for (int64_t c0 = 0; c0 < nb; c0 += blockDim.x) {
+        const int64_t i = c0 + threadIdx.x;
+        const unsigned long long v = i < nb ? sums[i] : 0ull;
+        const unsigned long long incl = warp_incl_scan64(v);
+        if (lane == 31) wt[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long t = lane < nwarps ? wt[lane] : 0ull;
+            wt[lane] = warp_incl_scan64(t);
+        }
+        __syncthreads();
+        const unsigned long long before = warp > 0 ? wt[warp - 1] : 0ull;
+        if (i < nb) sums[i] = carry + before + incl - v;
+        carry += wt[nwarps - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void k_scan_apply(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n,
+                             const unsigned long long* __restrict__ sums) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = base + i < n ? in[base + i] : 0u;
+        s += v[i];
+    }
+    uint32_t excl;
+    block_excl_scan(s, &excl);
+    uint32_t run = (uint32_t)sums[blockIdx.x] + excl;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+}
+
+// ------------------------------------------------------------------ radix
+
+__global__ void __launch_bounds__(kRadixThreads)
+k_radix_upsweep(const uint32_t* __restrict__ keys, int shift, uint32_t* __restrict__ hist, int64_t bps) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+#pragma unroll 4
+    for (int i = 0; i < kRadixItems; ++i) {
+        const uint32_t k = keys[base + i * kRadixThreads + threadIdx.x];
+        atomicAdd(&h[(k >> shift) & 0xffu], 1u);
+    }
+    __syncthreads();
+    const int64_t seg = blockIdx.x / bps, b = blockIdx.x % bps;
+    hist[(seg * 256 + threadIdx.x) * bps + b] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRadixThreads)
+k_radix_downsweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                  uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int shift,
+                  const uint32_t* __restrict__ hist, int64_t bps) {
+    __shared__ uint32_t base_off[256];
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t wcnt[kRadixThreads / 32][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t seg = blockIdx.x / bps, b = blockIdx.x % bps;
+    base_off[tid] = hist[(seg * 256 + tid) * bps + b];
+    run[tid] = 0;
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (int i = 0; i < kRadixItems; ++i) {
+#pragma unroll
+        for (int w = 0; w < kRadixThreads / 32; ++w) wcnt[w][tid] = 0;
+        __syncthreads();
+        const int64_t idx = base + i * kRadixThreads + tid;
+        const uint32_t k = kin[idx];
+        const uint32_t v = vin[idx];
+        const uint32_t d = (k >> shift) & 0xffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & lt_mask);
+        if (rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t s = run[tid];
+#pragma unroll
+            for (int w = 0; w < kRadixThreads / 32; ++w) {
+                const uint32_t c = wcnt[w][tid];
+                wcnt[w][tid] = s;
+                s += c;
+            }
+            run[tid] = s;
+        }
+        __syncthreads();
+        const uint32_t pos = base_off[d] + wcnt[warp][d] + rank;
+        kout[pos] = k;
+        vout[pos] = v;
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+ludvig_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* total_dev,
+                                 Arena& ws, cudaStream_t st) {
+    if (n <= 0) {
+        if (total_dev) LV_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(uint64_t), st));
+        return LUDVIG_OK;
+    }
+    const int64_t nb = ceil_div(n, kScanTile);
+    unsigned long long* sums = nullptr;
+    LV_TRY(ws.get("scan.sums", (size_t)nb, &sums));
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums);
+    LV_LAUNCH();
+    k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, nb, reinterpret_cast<unsigned long long*>(total_dev));
+    LV_LAUNCH();
+    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums);
+    LV_LAUNCH();
+    return LUDVIG_OK;
+}
+
+ludvig_status radix_sort_pairs(uint32_t** keys, uint32_t** vals, uint32_t* keys_alt,
+                               uint32_t* vals_alt, int64_t nseg, int64_t seg_len, int nbits,
+                               Arena& ws, cudaStream_t st) {
+    if (nseg <= 0 || seg_len <= 0 || nbits <= 0) return LUDVIG_OK;
+    if (seg_len % kRadixTile != 0) {
+        set_error("radix_sort_pairs: segment length %lld not a multiple of %d", (long long)seg_len,
+                  kRadixTile);
+        return LUDVIG_ERR_INTERNAL;
+    }
+    const int64_t bps = seg_len / kRadixTile;
+    const int64_t nblocks = bps * nseg;
+    if (nblocks > 0x7fffffff) {
+        set_error("radix_sort_pairs: too many blocks");
+        return LUDVIG_ERR_ARG;
+    }
+    const int64_t nh = nseg * 256 * bps;
+    uint32_t* hist = nullptr;
+    LV_TRY(ws.get("radix.hist", (size_t)nh, &hist));
+    uint32_t *kin = *keys, *vin = *vals, *kout = keys_alt, *vout = vals_alt;
+    for (int shift = 0; shift < nbits; shift += 8) {
+        k_radix_upsweep<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(kin, shift, hist, bps);
+        LV_LAUNCH();
+        LV_TRY(scan_exclusive_u32(hist, hist, nh, nullptr, ws, st));
+        k_radix_downsweep<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(kin, vin, kout, vout, shift,
+                                                                       hist, bps);
+        LV_LAUNCH();
+        uint32_t* t = kin;
+        kin = kout;
+        kout = t;
+        t = vin;
+        vin = vout;
+        vout = t;
+    }
+    *keys = kin;
+    *vals = vin;
+    return LUDVIG_OK;
+}
+
+}  // namespace ludvig

@@ -1,0 +1,314 @@
+"""Thin ctypes binding of libludvig (include/ludvig.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Torch tensors are passed by data pointer together with the current
+CUDA stream.  There is no fallback: if ``libludvig.so`` is missing or fails to
+load, or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libludvig.so")
+
+F32 = 0
+BF16 = 1
+
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT", 5: "ERR_INTERNAL",
+          6: "ERR_UNSUPPORTED"}
+
+# function name -> (restype, argtypes); mirrors include/ludvig.h
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_F = ctypes.c_float
+SIGNATURES = {
+    "ludvig_abi_version": (_I32, []),
+    "ludvig_last_error": (ctypes.c_char_p, []),
+    "ludvig_scene_create": (_I32, [_P, _P, _P, _P, _I64, _P, ctypes.POINTER(_P)]),
+    "ludvig_scene_destroy": (_I32, [_P]),
+    "ludvig_scene_size": (_I64, [_P]),
+    "ludvig_uplift_accumulate": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
+    "ludvig_uplift_finalize": (_I32, [_I64, _I32, _P, _P, _P, _P, _P]),
+    "ludvig_uplift": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
+    "ludvig_uplift_host": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
+    "ludvig_trace_enable": (_I32, [_I32]),
+    "ludvig_trace_read": (_I32, [_P, _I32]),
+    "ludvig_debug_project": (_I32, [_P, _P, _I32, _I32, _P, _P, _P]),
+    "ludvig_debug_tile_lists": (_I32, [_P, _P, _I32, _I32, _I32, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
+    "ludvig_debug_transmittance": (_I32, [_P, _P, _I32, _I32, _P, _P, _P]),
+    "ludvig_knn": (_I32, [_P, _I32, _P, _P]),
+    "ludvig_graph_build": (_I32, [_P, _I32, _P, _I32, _F, _F, _I32, _P, ctypes.POINTER(_P)]),
+    "ludvig_graph_destroy": (_I32, [_P]),
+    "ludvig_graph_nnz": (_I64, [_P]),
+    "ludvig_graph_export": (_I32, [_P, _P, _P, _P, _P]),
+    "ludvig_diffuse": (_I32, [_P, _P, _I32, _I32, _P, _P]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class LudvigError(RuntimeError):
+    pass
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libludvig.so (raises if it is missing: no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise LudvigError(f"{path} not found: build it with "
+                                  "`python -m paper_2410_14462_gb300.build`")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        msg = load().ludvig_last_error().decode(errors="replace")
+        raise LudvigError(f"{what}: {STATUS.get(rc, rc)}: {msg}")
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype=None, name="tensor"):
+    if not t.is_cuda:
+        raise LudvigError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise LudvigError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise LudvigError(f"{name} must be {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class CameraArray(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+
+
+def cameras_struct(params: np.ndarray):
+    """[V,16] float32 (R, t, fx, fy, cx, cy) -> ludvig_camera[V] (host memory)."""
+    p = np.ascontiguousarray(params, dtype=np.float32).reshape(-1, 16)
+    arr = (CameraArray * max(1, p.shape[0]))()
+    ctypes.memmove(arr, p.ctypes.data, p.nbytes)
+    return arr, p.shape[0]
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.bfloat16:
+        return BF16
+    raise LudvigError(f"features must be float32 or bfloat16, got {t.dtype}")
+
+
+class Scene:
+    """A device-resident Gaussian scene (ludvig_scene_create)."""
+
+    def __init__(self, means, scales, quats, opacity, stream=None):
+        L = load()
+        dev = torch.device("cuda")
+        t = [torch.as_tensor(a, dtype=torch.float32).to(dev).contiguous()
+             for a in (means, scales, quats, opacity)]
+        self.n = int(t[0].shape[0])
+        h = ctypes.c_void_p()
+        _check(L.ludvig_scene_create(_dev(t[0]), _dev(t[1]), _dev(t[2]), _dev(t[3]), self.n,
+                                     _stream(stream), ctypes.byref(h)), "ludvig_scene_create")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        self._h = h
+
+    @classmethod
+    def from_inputs(cls, scene, stream=None):
+        return cls(scene.means, scene.scales, scene.quats, scene.opacity, stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ludvig_scene_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def uplift(scene: Scene, cams_params, width, height, feats: torch.Tensor, out=None, beta=None,
+           stream=None):
+    """f = D^-1 W^T F on the device.  feats: [V,H,W,D] float32/bfloat16 CUDA tensor."""
+    L = load()
+    cams, nv = cameras_struct(cams_params)
+    d = int(feats.shape[-1])
+    if out is None:
+        out = torch.empty((scene.n, d), dtype=torch.float32, device=feats.device)
+    if beta is None:
+        beta = torch.empty((scene.n,), dtype=torch.float32, device=feats.device)
+    _check(L.ludvig_uplift(scene.handle, cams, nv, width, height, _dev(feats, name="feats"),
+                           _dtype_code(feats), d, _dev(out, torch.float32, "out"),
+                           _dev(beta, torch.float32, "beta"), _stream(stream)), "ludvig_uplift")
+    return out, beta
+
+
+def uplift_accumulate(scene: Scene, cams_params, width, height, feats, num, den, stream=None):
+    L = load()
+    cams, nv = cameras_struct(cams_params)
+    _check(L.ludvig_uplift_accumulate(scene.handle, cams, nv, width, height, _dev(feats, name="feats"),
+                                      _dtype_code(feats), int(feats.shape[-1]),
+                                      _dev(num, torch.float32, "num"), _dev(den, torch.float32, "den"),
+                                      _stream(stream)), "ludvig_uplift_accumulate")
+
+
+def uplift_finalize(num, den, out=None, beta=None, stream=None):
+    L = load()
+    n, d = num.shape
+    out = num if out is None else out
+    _check(L.ludvig_uplift_finalize(n, d, _dev(num), _dev(den), _dev(out),
+                                    None if beta is None else _dev(beta), _stream(stream)),
+           "ludvig_uplift_finalize")
+    return out
+
+
+def uplift_host(scene: Scene, cams_params, width, height, feats: torch.Tensor, stream=None):
+    """The same uplift from host (CPU, ideally pinned) features; returns CPU tensors."""
+    L = load()
+    if feats.is_cuda or not feats.is_contiguous():
+        raise LudvigError("feats must be a contiguous CPU tensor")
+    cams, nv = cameras_struct(cams_params)
+    d = int(feats.shape[-1])
+    out = torch.empty((scene.n, d), dtype=torch.float32, pin_memory=True)
+    beta = torch.empty((scene.n,), dtype=torch.float32, pin_memory=True)
+    _check(L.ludvig_uplift_host(scene.handle, cams, nv, width, height, ctypes.c_void_p(feats.data_ptr()),
+                                _dtype_code(feats), d, ctypes.c_void_p(out.data_ptr()),
+                                ctypes.c_void_p(beta.data_ptr()), _stream(stream)), "ludvig_uplift_host")
+    return out, beta
+
+
+STAGES = ["project", "depth_sort", "bin", "tile_sort", "composite", "normalise", "knn", "graph", "diffuse"]
+
+
+class TraceStruct(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 16), ("calls", ctypes.c_int64 * 16),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+def trace_enable(on: bool = True):
+    _check(load().ludvig_trace_enable(int(on)), "ludvig_trace_enable")
+
+
+def trace_read(reset: bool = True) -> dict:
+    """Per-stage device milliseconds, interval counts and the kernel launch count."""
+    t = TraceStruct()
+    _check(load().ludvig_trace_read(ctypes.byref(t), int(reset)), "ludvig_trace_read")
+    return {"ms": {s: t.ms[i] for i, s in enumerate(STAGES)},
+            "calls": {s: t.calls[i] for i, s in enumerate(STAGES)},
+            "kernel_launches": int(t.kernel_launches)}
+
+
+def debug_project(scene: Scene, cam_params, width, height, stream=None):
+    L = load()
+    cams, _ = cameras_struct(cam_params)
+    rec = torch.zeros((scene.n, 8), dtype=torch.float32, device="cuda")
+    rect = torch.zeros((scene.n, 4), dtype=torch.int32, device="cuda")
+    _check(L.ludvig_debug_project(scene.handle, cams, width, height, _dev(rec), _dev(rect), _stream(stream)),
+           "ludvig_debug_project")
+    return rec, rect
+
+
+def debug_tile_lists(scene: Scene, cam_params, width, height, pruned=False, stream=None):
+    L = load()
+    cams, _ = cameras_struct(cam_params)
+    ntiles = ((width + 15) // 16) * ((height + 15) // 16)
+    ranges = torch.zeros((ntiles, 2), dtype=torch.int64, device="cuda")
+    total = ctypes.c_int64(0)
+    _check(L.ludvig_debug_tile_lists(scene.handle, cams, width, height, int(pruned), _dev(ranges), None, 0,
+                                     ctypes.byref(total), _stream(stream)), "ludvig_debug_tile_lists")
+    lst = torch.zeros((max(1, total.value),), dtype=torch.int32, device="cuda")
+    _check(L.ludvig_debug_tile_lists(scene.handle, cams, width, height, int(pruned), _dev(ranges), _dev(lst),
+                                     lst.numel(), ctypes.byref(total), _stream(stream)), "ludvig_debug_tile_lists")
+    return ranges, lst[: total.value]
+
+
+def debug_transmittance(scene: Scene, cam_params, width, height, stream=None):
+    L = load()
+    cams, _ = cameras_struct(cam_params)
+    t = torch.empty((height, width), dtype=torch.float32, device="cuda")
+    c = torch.empty((height, width), dtype=torch.int32, device="cuda")
+    _check(L.ludvig_debug_transmittance(scene.handle, cams, width, height, _dev(t), _dev(c), _stream(stream)),
+           "ludvig_debug_transmittance")
+    return t, c
+
+
+def knn(scene: Scene, k: int, stream=None):
+    L = load()
+    nbr = torch.empty((scene.n, k), dtype=torch.int32, device="cuda")
+    _check(L.ludvig_knn(scene.handle, k, _dev(nbr), _stream(stream)), "ludvig_knn")
+    return nbr
+
+
+class Graph:
+    """Diffusion graph on the device (ludvig_graph_build)."""
+
+    def __init__(self, scene: Scene, k: int, feats: torch.Tensor, spatial_h: float = 0.01,
+                 binarize: float = 0.0, row_normalize: bool = True, stream=None):
+        L = load()
+        h = ctypes.c_void_p()
+        _check(L.ludvig_graph_build(scene.handle, k, _dev(feats, torch.float32, "feats"), int(feats.shape[1]),
+                                    spatial_h, binarize, int(row_normalize), _stream(stream), ctypes.byref(h)),
+               "ludvig_graph_build")
+        self._h = h
+        self.n = scene.n
+
+    @property
+    def nnz(self) -> int:
+        return int(load().ludvig_graph_nnz(self._h))
+
+    def export(self, stream=None):
+        L = load()
+        rp = torch.empty((self.n + 1,), dtype=torch.int64, device="cuda")
+        col = torch.empty((max(1, self.nnz),), dtype=torch.int32, device="cuda")
+        val = torch.empty((max(1, self.nnz),), dtype=torch.float32, device="cuda")
+        _check(L.ludvig_graph_export(self._h, _dev(rp), _dev(col), _dev(val), _stream(stream)),
+               "ludvig_graph_export")
+        return rp, col[: self.nnz], val[: self.nnz]
+
+    def diffuse(self, x0: torch.Tensor, iters: int, out=None, stream=None):
+        L = load()
+        x0 = x0.contiguous()
+        dx = 1 if x0.dim() == 1 else int(x0.shape[1])
+        if out is None:
+            out = torch.empty_like(x0)
+        _check(L.ludvig_diffuse(self._h, _dev(x0, torch.float32, "x0"), dx, iters,
+                                _dev(out, torch.float32, "out"), _stream(stream)), "ludvig_diffuse")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ludvig_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,253 @@
+"""GPU parity of the uplift path (Sec. 3.2, Eq. 3 / Eq. 5) against the CPU
+oracle, through the C ABI.
+
+Bars: projection records, tile rectangles, tile lists, contributor counts are
+bit-exact (integer decisions taken by both sides on the same float32 rules);
+uplifted features within 1e-5 relative L2 of the float64 oracle (float32
+path); the error is printed for every case."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2410_14462_gb300 import inputs, ludvig
+from tests.gpu_util import device_features, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2410_14462_gb300 import build
+    build.build()
+    ludvig.load()
+
+
+def _workloads():
+    return {
+        "tiny": inputs.tiny_mask_workload(),
+        "ragged": inputs.small_field_workload(n=20_000, views=4, d=48, width=100, height=75),
+    }
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged"])
+def test_projection_bitexact(name):
+    wl = _workloads()[name]
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    for v in range(min(3, wl.cams.v)):
+        rec, rect = ludvig.debug_project(sc, wl.cams.params[v], wl.cams.width, wl.cams.height)
+        pr = oracle.project(wl.scene, wl.cams.params[v], wl.cams.width, wl.cams.height)
+        vis = pr["visible"]
+        rect = rect.cpu().numpy()
+        rec = rec.cpu().numpy()
+        assert np.array_equal(rect, pr["rect"]), f"view {v}: tile rectangles differ"
+        ref = pr["p32"][vis]
+        got = rec[vis]
+        assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), f"view {v}: records differ"
+        assert (rec[~vis] == 0).all()
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged"])
+def test_tile_lists_bitexact(name):
+    wl = _workloads()[name]
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    for v in range(min(3, wl.cams.v)):
+        ranges, lst = ludvig.debug_tile_lists(sc, wl.cams.params[v], wl.cams.width, wl.cams.height)
+        r_ref, l_ref = oracle.tile_lists(wl.scene, wl.cams.params[v], wl.cams.width, wl.cams.height)
+        ranges = ranges.cpu().numpy()
+        lst = lst.cpu().numpy()
+        # empty tiles: GPU reports [0,0); compare lengths and contents tile by tile
+        assert np.array_equal(ranges[:, 1] - ranges[:, 0], r_ref[:, 1] - r_ref[:, 0])
+        assert lst.shape == l_ref.shape
+        for t in range(r_ref.shape[0]):
+            a = lst[ranges[t, 0]:ranges[t, 1]]
+            b = l_ref[r_ref[t, 0]:r_ref[t, 1]]
+            assert np.array_equal(a, b), f"view {v} tile {t}"
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged"])
+def test_pruned_lists_keep_every_contributor(name):
+    """The lists the uplift walks are the binning-rule lists minus Gaussians
+    that cannot reach alpha >= 1/255 in the tile: a sub-sequence of the oracle's
+    list that still holds every Gaussian with a non-zero weight in the tile."""
+    wl = _workloads()[name]
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    W, H = wl.cams.width, wl.cams.height
+    TX = (W + 15) // 16
+    for v in range(min(2, wl.cams.v)):
+        ranges, lst = ludvig.debug_tile_lists(sc, wl.cams.params[v], W, H, pruned=True)
+        r_ref, l_ref = oracle.tile_lists(wl.scene, wl.cams.params[v], W, H)
+        res = oracle.view_uplift(wl.scene, wl.cams.params[v], W, H, triplets=True)
+        tile_of = (res["pix"] // W // 16) * TX + (res["pix"] % W) // 16
+        ranges, lst = ranges.cpu().numpy(), lst.cpu().numpy()
+        kept = 0
+        for t in range(r_ref.shape[0]):
+            a = lst[ranges[t, 0]:ranges[t, 1]]
+            b = l_ref[r_ref[t, 0]:r_ref[t, 1]]
+            pos = {g: k for k, g in enumerate(b.tolist())}
+            idx = [pos[g] for g in a.tolist()]
+            assert idx == sorted(idx) and len(set(idx)) == len(idx), f"view {v} tile {t}"
+            need = set(res["gid"][tile_of == t].tolist())
+            assert need <= set(a.tolist()), f"view {v} tile {t}: contributor pruned"
+            kept += len(a)
+        print(f"{name} view {v}: pruned lists keep {kept} of {len(l_ref)} entries")
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged"])
+def test_transmittance_and_contributors(name):
+    wl = _workloads()[name]
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    W, H = wl.cams.width, wl.cams.height
+    for v in range(min(2, wl.cams.v)):
+        t, c = ludvig.debug_transmittance(sc, wl.cams.params[v], W, H)
+        res = oracle.view_uplift(wl.scene, wl.cams.params[v], W, H, triplets=True, t_final=True)
+        cnt = np.bincount(res["pix"], minlength=W * H).reshape(H, W)
+        assert np.array_equal(c.cpu().numpy(), cnt)
+        # T_gpu is a float32 running product over up to ~150 factors (1 - alpha)
+        # whose alphas come from the float32 projection (relative error a few
+        # 1e-7 each); T <= 1, so |T_gpu - T_oracle| stays below ~150 * 1e-7.
+        err = np.abs(t.cpu().numpy() - res["t_final"]).max()
+        print(f"{name} view {v}: max |T_gpu - T_oracle| = {err:.2e}")
+        assert err < 2e-5
+
+
+def _gpu_uplift(wl, views, dtype=torch.float32):
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    F = device_features(wl, views, dtype)
+    out, beta = ludvig.uplift(sc, wl.cams.params[views], wl.cams.width, wl.cams.height, F)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), beta.cpu().numpy(), F
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged"])
+def test_uplift_f32_matches_oracle(name):
+    wl = _workloads()[name]
+    views = list(range(wl.cams.v))
+    out, beta, _ = _gpu_uplift(wl, views)
+    f_ref, b_ref = oracle.uplift(wl.scene, wl.cams, lambda v: wl.features(v))
+    pos = b_ref > 0
+    assert np.array_equal(beta > 0, pos)
+    e_f = rel_l2(out, f_ref, pos)
+    e_b = rel_l2(beta, b_ref)
+    print(f"{name}: float32 uplift rel L2 vs float64 oracle: f {e_f:.2e}  beta {e_b:.2e}")
+    assert e_f <= 1e-5 and e_b <= 1e-5
+    assert (out[~pos] == 0).all()
+
+
+def test_uplift_scalar_channels_and_bf16():
+    base = inputs.small_field_workload(n=8000, views=3, d=3, width=61, height=45)
+    out, beta, F = _gpu_uplift(base, [0, 1, 2])
+    f_ref, b_ref = oracle.uplift(base.scene, base.cams, lambda v: base.features(v))
+    pos = b_ref > 0
+    assert rel_l2(out, f_ref, pos) <= 1e-5
+    # bfloat16 features: compare with the oracle run on the same bf16 values
+    wl = inputs.small_field_workload(n=8000, views=3, d=40, width=61, height=45)
+    out, beta, F = _gpu_uplift(wl, [0, 1, 2], dtype=torch.bfloat16)
+    Fh = F.float().cpu().numpy()
+    f_ref, b_ref = oracle.uplift(wl.scene, wl.cams, lambda v: Fh[v])
+    pos = b_ref > 0
+    e = rel_l2(out, f_ref, pos)
+    print(f"bf16 features: rel L2 vs oracle on the bf16 values {e:.2e}")
+    assert e <= 1e-5
+
+
+def test_accumulate_split_equals_whole_and_host_path():
+    wl = inputs.small_field_workload(n=10_000, views=5, d=16)
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    F = device_features(wl, range(5))
+    W, H = wl.cams.width, wl.cams.height
+    whole, beta = ludvig.uplift(sc, wl.cams.params, W, H, F)
+    num = torch.zeros((sc.n, 16), device="cuda")
+    den = torch.zeros((sc.n,), device="cuda")
+    ludvig.uplift_accumulate(sc, wl.cams.params[:2], W, H, F[:2].contiguous(), num, den)
+    ludvig.uplift_accumulate(sc, wl.cams.params[2:], W, H, F[2:].contiguous(), num, den)
+    out = ludvig.uplift_finalize(num, den)
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), whole.cpu().numpy()) < 1e-6
+    hout, hbeta = ludvig.uplift_host(sc, wl.cams.params, W, H, F.cpu().pin_memory())
+    assert rel_l2(hout.numpy(), whole.cpu().numpy()) < 1e-6
+    assert rel_l2(hbeta.numpy(), beta.cpu().numpy()) < 1e-6
+
+
+def test_edge_cases():
+    wl = inputs.tiny_mask_workload()
+    W, H = wl.cams.width, wl.cams.height
+    # empty scene
+    empty = inputs.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32),
+                         np.zeros((0, 4), np.float32), np.zeros((0,), np.float32))
+    sc0 = ludvig.Scene.from_inputs(empty)
+    F = device_features(wl, [0])
+    out, beta = ludvig.uplift(sc0, wl.cams.params[:1], W, H, F)
+    assert out.shape == (0, 1)
+    # zero views: output zeros
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    out, beta = ludvig.uplift(sc, wl.cams.params[:0], W, H, F[:0])
+    torch.cuda.synchronize()
+    assert (out == 0).all() and (beta == 0).all()
+    # every Gaussian behind the camera: nothing contributes
+    cam = wl.cams.params[:1].copy()
+    cam[0, 9:12] = [0, 0, -50.0]
+    out, beta = ludvig.uplift(sc, cam, W, H, F)
+    torch.cuda.synchronize()
+    assert (beta == 0).all() and (out == 0).all()
+    # one-pixel image and an image narrower than a tile
+    for (w, h) in [(1, 1), (5, 37)]:
+        cams = inputs.cameras_orbit(2, 3.0, w, h, 120.0, hemisphere=False)
+        Fs = torch.rand((2, h, w, 4), device="cuda")
+        out, beta = ludvig.uplift(sc, cams.params, w, h, Fs)
+        Fh = Fs.cpu().numpy()
+        f_ref, b_ref = oracle.uplift(wl.scene, cams, lambda v: Fh[v])
+        torch.cuda.synchronize()
+        pos = b_ref > 0
+        assert np.array_equal(beta.cpu().numpy() > 0, pos)
+        if pos.any():
+            assert rel_l2(out.cpu().numpy(), f_ref, pos) <= 1e-5
+
+
+def test_dense_stack_overflows_store():
+    """Many large coincident splats: long tile lists, batches that flush the
+    shared-memory weight store several times per tile."""
+    rng = np.random.default_rng(0)
+    n = 3000
+    means = (rng.normal(size=(n, 3)) * 0.05).astype(np.float32)
+    scales = np.full((n, 3), 0.2, np.float32)
+    q = rng.normal(size=(n, 4)).astype(np.float32)
+    op = np.full(n, 0.02, np.float32)
+    sc_in = inputs.Scene(means, scales, q, op)
+    cams = inputs.cameras_orbit(2, 3.0, 96, 64, 100.0, hemisphere=True)
+    Fs = torch.rand((2, 64, 96, 36), device="cuda")
+    sc = ludvig.Scene.from_inputs(sc_in)
+    out, beta = ludvig.uplift(sc, cams.params, 96, 64, Fs)
+    Fh = Fs.cpu().numpy()
+    f_ref, b_ref = oracle.uplift(sc_in, cams, lambda v: Fh[v])
+    torch.cuda.synchronize()
+    pos = b_ref > 0
+    assert pos.sum() > 1000
+    assert rel_l2(out.cpu().numpy(), f_ref, pos) <= 1e-5
+
+
+def test_many_small_rows_overflow_row_table():
+    """Thousands of sub-pixel splats in one tile region: more contributing
+    Gaussians per tile than the per-flush row table holds."""
+    rng = np.random.default_rng(1)
+    n = 6000
+    means = np.stack([rng.uniform(-0.05, 0.05, n), rng.uniform(-0.05, 0.05, n), rng.uniform(-0.5, 0.5, n)], 1)
+    sc_in = inputs.Scene(means.astype(np.float32), np.full((n, 3), 0.0005, np.float32),
+                         np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)), np.full(n, 0.3, np.float32))
+    cam = np.zeros((1, 16), np.float32)
+    cam[0, [0, 4, 8]] = 1
+    cam[0, 9:12] = [0, 0, 3.0]
+    cam[0, 12:16] = [300.0, 300.0, 16.0, 16.0]
+    Fs = torch.rand((1, 32, 32, 8), device="cuda")
+    sc = ludvig.Scene.from_inputs(sc_in)
+    out, beta = ludvig.uplift(sc, cam, 32, 32, Fs)
+    Fh = Fs.cpu().numpy()
+    cams = inputs.Cameras(cam, 32, 32)
+    f_ref, b_ref = oracle.uplift(sc_in, cams, lambda v: Fh[v])
+    torch.cuda.synchronize()
+    pos = b_ref > 0
+    assert pos.sum() > 2000
+    assert np.array_equal(beta.cpu().numpy() > 0, pos)
+    assert rel_l2(out.cpu().numpy(), f_ref, pos) <= 1e-5
