@@ -59,7 +59,8 @@ typedef enum {
 
 typedef enum {
     LUDVIG_F32 = 0,              /* float32 features, CUDA-core FFMA aggregation */
-    LUDVIG_BF16 = 1              /* bfloat16 features, tensor-core aggregation */
+    LUDVIG_BF16 = 1              /* bfloat16 features; tensor-core aggregation (tcgen05) when
+                                    d is a multiple of 64 up to 512, CUDA cores otherwise */
 } ludvig_dtype;
 
 /* Pinhole camera, host memory.  R: row-major world->camera rotation. */
@@ -189,6 +190,13 @@ ludvig_status ludvig_debug_tile_lists(ludvig_scene_t scene, const ludvig_camera*
 ludvig_status ludvig_debug_transmittance(ludvig_scene_t scene, const ludvig_camera* cam,
                                          int32_t width, int32_t height, float* t_final,
                                          int32_t* n_contrib, void* stream);
+
+/* Tensor-core product used by the bfloat16 aggregation, on one 16x16 tile:
+ *   out[r, c] = sum_{p < 256} a[r, p] * f[p, c]      (r < 128, c < d)
+ * a: device [128,256] bfloat16 row-major (a W tile: Gaussian x pixel),
+ * f: device [16,16,d] bfloat16 (a feature tile, pixel p = 16*y + x),
+ * out: device [128,d] float32; d in {64, 128, ..., 512}.  Synchronises. */
+ludvig_status ludvig_debug_mma_bf16(const void* a, const void* f, int32_t d, float* out, void* stream);
 
 /* ---- graph diffusion (Sec. 3.3) ----------------------------------------- */
 

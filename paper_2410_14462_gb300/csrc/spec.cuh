@@ -205,25 +205,45 @@ __device__ __forceinline__ float alpha_at(float mx, float my, float ca, float cb
 // rectangle is 0 when the mean lies inside, otherwise the smallest of the
 // four edge minima (each a clamped 1D minimisation).  The 0.1% + 1e-3 slack
 // covers the float32 rounding of the per-pixel test, so a Gaussian this
-// returns false for is skipped at every pixel of the rectangle anyway.
-__device__ __forceinline__ bool reaches_rect(float mx, float my, float ca, float cb, float cc, float op,
+// returns false for is skipped at every pixel of the rectangle anyway.  Every
+// rounding is explicit: the projection and the pair emission evaluate the
+// same decisions and must agree exactly.
+struct Reach {
+    float thr, inv_ca, inv_cc, cb2;
+    bool possible;
+};
+
+__device__ __forceinline__ Reach reach_prep(float ca, float cb, float cc, float op) {
+    Reach r;
+    r.possible = !(op < kAlphaMin);   // alpha <= opacity < 1/255 everywhere otherwise
+    r.thr = __fadd_rn(__fmul_rn(__fmul_rn(2.0f, __logf(__fmul_rn(255.0f, op))), 1.001f), 1e-3f);
+    r.inv_ca = __frcp_rn(ca);
+    r.inv_cc = __frcp_rn(cc);
+    r.cb2 = __fmul_rn(2.0f, cb);
+    return r;
+}
+
+__device__ __forceinline__ bool reaches_rect(const Reach& R, float mx, float my, float ca, float cb, float cc,
                                              float xa, float xb, float ya, float yb) {
-    // explicit roundings: the same decision is re-evaluated by several kernels
-    if (op < kAlphaMin) return false;   // alpha <= opacity < 1/255 everywhere
-    const float thr = __fadd_rn(__fmul_rn(__fmul_rn(2.0f, __logf(__fmul_rn(255.0f, op))), 1.001f), 1e-3f);
+    if (!R.possible) return false;
     const float dx1 = __fsub_rn(mx, xb), dx0 = __fsub_rn(mx, xa);
     const float dy1 = __fsub_rn(my, yb), dy0 = __fsub_rn(my, ya);
     if (dx1 <= 0.f && dx0 >= 0.f && dy1 <= 0.f && dy0 >= 0.f) return true;
     auto q = [&](float dx, float dy) {
-        return __fadd_rn(__fadd_rn(__fmul_rn(ca, __fmul_rn(dx, dx)), __fmul_rn(__fmul_rn(2.f, cb), __fmul_rn(dx, dy))),
+        return __fadd_rn(__fadd_rn(__fmul_rn(ca, __fmul_rn(dx, dx)), __fmul_rn(R.cb2, __fmul_rn(dx, dy))),
                          __fmul_rn(cc, __fmul_rn(dy, dy)));
     };
     auto cl = [](float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); };
-    float best = q(dx0, cl(__fdiv_rn(-__fmul_rn(cb, dx0), cc), dy1, dy0));
-    best = fminf(best, q(dx1, cl(__fdiv_rn(-__fmul_rn(cb, dx1), cc), dy1, dy0)));
-    best = fminf(best, q(cl(__fdiv_rn(-__fmul_rn(cb, dy0), ca), dx1, dx0), dy0));
-    best = fminf(best, q(cl(__fdiv_rn(-__fmul_rn(cb, dy1), ca), dx1, dx0), dy1));
-    return best <= thr;
+    float best = q(dx0, cl(__fmul_rn(-__fmul_rn(cb, dx0), R.inv_cc), dy1, dy0));
+    best = fminf(best, q(dx1, cl(__fmul_rn(-__fmul_rn(cb, dx1), R.inv_cc), dy1, dy0)));
+    best = fminf(best, q(cl(__fmul_rn(-__fmul_rn(cb, dy0), R.inv_ca), dx1, dx0), dy0));
+    best = fminf(best, q(cl(__fmul_rn(-__fmul_rn(cb, dy1), R.inv_ca), dx1, dx0), dy1));
+    return best <= R.thr;
+}
+
+__device__ __forceinline__ bool reaches_rect(float mx, float my, float ca, float cb, float cc, float op,
+                                             float xa, float xb, float ya, float yb) {
+    return reaches_rect(reach_prep(ca, cb, cc, op), mx, my, ca, cb, cc, xa, xb, ya, yb);
 }
 
 }  // namespace ludvig

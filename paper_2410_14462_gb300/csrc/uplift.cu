@@ -31,6 +31,11 @@ namespace ludvig {
 
 constexpr int kMaxViews = 16;
 
+bool tc_supported(int dtype, int d);
+ludvig_status composite_tc(const float4* rec_a, const float2* rec_b, int64_t n, const uint2* ranges,
+                           const uint32_t* list, int nv, int width, int height, const void* feats, int d,
+                           float* num, float* den, Arena& ws, int* status, cudaStream_t st);
+
 struct CamBatch {
     Cam cam[kMaxViews];
 };
@@ -60,13 +65,10 @@ __global__ void k_scene_init(const float* __restrict__ means, const float* __res
 // Whether the Gaussian's alpha >= 1/255 region can reach a pixel centre of
 // tile (tx, ty); a Gaussian that cannot is skipped at every pixel of the tile,
 // so leaving it out of the tile's list changes no weight.
-__device__ __forceinline__ bool tile_reached(float mx, float my, float ca, float cb, float cc, float op,
+__device__ __forceinline__ bool tile_reached(const Reach& R, float mx, float my, float ca, float cb, float cc,
                                              int tx, int ty) {
     const float xa = (float)(tx * kTile) + 0.5f, ya = (float)(ty * kTile) + 0.5f;
-    return reaches_rect(mx, my, ca, cb, cc, op, xa, xa + 15.0f, ya, ya + 15.0f);
-}
-__device__ __forceinline__ bool tile_reached(const Projected& P, float op, int tx, int ty) {
-    return tile_reached(P.mx, P.my, P.ca, P.cb, P.cc, op, tx, ty);
+    return reaches_rect(R, mx, my, ca, cb, cc, xa, xa + 15.0f, ya, ya + 15.0f);
 }
 
 // ------------------------------------------------------------ 1. project
@@ -103,9 +105,10 @@ __global__ void k_project(const float4* __restrict__ geo, const float4* __restri
     if (P.visible) {
         if (prune) {
             // only tiles that the alpha >= 1/255 ellipse can reach
+            const Reach R = reach_prep(P.ca, P.cb, P.cc, g.w);
             for (int ty = P.y0; ty < P.y1; ++ty)
                 for (int tx = P.x0; tx < P.x1; ++tx)
-                    count += tile_reached(P, g.w, tx, ty) ? 1u : 0u;
+                    count += tile_reached(R, P.mx, P.my, P.ca, P.cb, P.cc, tx, ty) ? 1u : 0u;
         } else {
             count = (uint32_t)((P.x1 - P.x0) * (P.y1 - P.y0));
         }
@@ -155,12 +158,13 @@ __global__ void k_emit_pairs(const uint32_t* __restrict__ svals, const uint32_t*
     const int x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff, y1 = r.y >> 16;
     const float4 ra = rec_a[v * n + i];
     const float2 rb = rec_b[v * n + i];
+    const Reach R = reach_prep(ra.z, ra.w, rb.x, rb.y);
     uint32_t o = off[idx];
     const uint32_t end = o + cnt[idx];   // never write past the counted slots
     const uint32_t base = (uint32_t)(v * ntiles);
     for (int ty = y0; ty < y1 && o < end; ++ty)
         for (int tx = x0; tx < x1 && o < end; ++tx) {
-            if (prune && !tile_reached(ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, tx, ty)) continue;
+            if (prune && !tile_reached(R, ra.x, ra.y, ra.z, ra.w, rb.x, tx, ty)) continue;
             pkey[o] = base + (uint32_t)(ty * TX + tx);
             pval[o] = i;
             ++o;
@@ -625,6 +629,11 @@ ludvig_status run_chunk(ludvig_scene* s, const ludvig_camera* cams, int nv, int 
     const int64_t nitems = (int64_t)nv * ntiles;
     const bool vec = (d % 4 == 0);
     StageScope scope(LUDVIG_STAGE_COMPOSITE, st);
+    if (tc_supported(dtype, d)) {
+        int* status;
+        LV_TRY(ws.get("tc.status", 1, &status));
+        return composite_tc(rec_a, rec_b, n, ranges, spv, nv, width, height, feats, d, num, den, ws, status, st);
+    }
     if (dtype == LUDVIG_F32) {
         if (vec) return launch_composite<float, true>(args, nitems, st);
         return launch_composite<float, false>(args, nitems, st);
@@ -649,6 +658,11 @@ ludvig_status accumulate(ludvig_scene* s, const ludvig_camera* cams, int32_t n_v
                          float* den, cudaStream_t st, const ChunkDebug* dbg) {
     const size_t esize = dtype == LUDVIG_F32 ? 4 : 2;
     const int64_t view_elems = (int64_t)width * height * d;
+    int* status = nullptr;
+    if (tc_supported(dtype, d)) {
+        LV_TRY(s->ws.get("tc.status", 1, &status));
+        LV_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+    }
     int v0 = 0;
     int vc = std::min<int>(kMaxViews, std::max<int>(1, n_views));
     // keep the per-chunk Gaussian scratch (about 80 bytes per Gaussian and view) near 2 GB
@@ -668,6 +682,18 @@ ludvig_status accumulate(ludvig_scene* s, const ludvig_camera* cams, int32_t n_v
             continue;
         }
         v0 += nv;
+    }
+    if (status) {
+        // device-side status of the tensor-core kernel (bounded waits)
+        void* h;
+        LV_TRY(s->ws.pinned("tc.status_h", 16, &h));
+        LV_CUDA(cudaMemcpyAsync(h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LV_CUDA(cudaStreamSynchronize(st));
+        const int code = *static_cast<int*>(h);
+        if (code != 0) {
+            set_error("tensor-core aggregation reported status %d (a bounded wait expired)", code);
+            return (ludvig_status)code;
+        }
     }
     return LUDVIG_OK;
 }

@@ -43,6 +43,7 @@ SIGNATURES = {
     "ludvig_debug_project": (_I32, [_P, _P, _I32, _I32, _P, _P, _P]),
     "ludvig_debug_tile_lists": (_I32, [_P, _P, _I32, _I32, _I32, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "ludvig_debug_transmittance": (_I32, [_P, _P, _I32, _I32, _P, _P, _P]),
+    "ludvig_debug_mma_bf16": (_I32, [_P, _P, _I32, _P, _P]),
     "ludvig_knn": (_I32, [_P, _I32, _P, _P]),
     "ludvig_graph_build": (_I32, [_P, _I32, _P, _I32, _F, _F, _I32, _P, ctypes.POINTER(_P)]),
     "ludvig_graph_destroy": (_I32, [_P]),
@@ -257,6 +258,16 @@ def debug_transmittance(scene: Scene, cam_params, width, height, stream=None):
     _check(L.ludvig_debug_transmittance(scene.handle, cams, width, height, _dev(t), _dev(c), _stream(stream)),
            "ludvig_debug_transmittance")
     return t, c
+
+
+def debug_mma_bf16(a: torch.Tensor, f: torch.Tensor, stream=None):
+    """out[128,d] = a[128,256] @ f[256,d] through the uplift's tensor-core path."""
+    L = load()
+    d = int(f.shape[-1])
+    out = torch.zeros((128, d), dtype=torch.float32, device="cuda")
+    _check(L.ludvig_debug_mma_bf16(_dev(a, torch.bfloat16, "a"), _dev(f, torch.bfloat16, "f"), d, _dev(out),
+                                   _stream(stream)), "ludvig_debug_mma_bf16")
+    return out
 
 
 def knn(scene: Scene, k: int, stream=None):
