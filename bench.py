@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="uplift only (not a full step)")
+    ap.add_argument("--no-precision", action="store_true", help="skip the bf16 precision-form line")
     return ap.parse_args()
 
 
@@ -171,6 +172,57 @@ def cpu_baseline(wl):
             "sample": f"uplift of view 0 of {wl.cams.v} (D={wl.d}, N={wl.scene.n}), {dt:.1f} s"}
 
 
+def precision_form(sc, wl):
+    """bfloat16 features with D=512 on the same scene and cameras (tensor-core
+    aggregation), timed over the full uplift; its error is stated against the
+    float32 path on the first 8 views."""
+    import torch
+    from paper_2410_14462_gb300 import ludvig
+    V, H, W = wl.cams.v, wl.cams.height, wl.cams.width
+    D = 512
+    fb = torch.empty((V, H, W, D), dtype=torch.bfloat16, device="cuda")
+    for v in range(V):
+        fb[v] = wl.features_d(v, D, device="cuda", dtype=torch.bfloat16)
+    out = torch.empty((sc.n, D), dtype=torch.float32, device="cuda")
+    beta = torch.empty((sc.n,), dtype=torch.float32, device="cuda")
+    ludvig.uplift(sc, wl.cams.params, W, H, fb, out, beta)
+    torch.cuda.synchronize()
+    ludvig.trace_read(reset=True)
+    ludvig.trace_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        ludvig.uplift(sc, wl.cams.params, W, H, fb, out, beta)
+    e1.record()
+    torch.cuda.synchronize()
+    ludvig.trace_enable(False)
+    tr = ludvig.trace_read(reset=True)
+    ms = e0.elapsed_time(e1) / reps
+    # error vs the float32 path on views 0..7 (same D=512 field)
+    nv = 8
+    f32 = torch.stack([wl.features_d(v, D, device="cuda") for v in range(nv)]).contiguous()
+    o32, b32 = ludvig.uplift(sc, wl.cams.params[:nv], W, H, f32)
+    obf, bbf = ludvig.uplift(sc, wl.cams.params[:nv], W, H, fb[:nv].contiguous())
+    torch.cuda.synchronize()
+    pos = b32 > 0
+    err = float((obf[pos] - o32[pos]).norm() / o32[pos].norm())
+    comp_ms = tr["ms"]["composite"] / max(1, tr["calls"]["composite"])
+    launches = tr["calls"]["composite"] / reps
+    alg = V * H * W * D * 2 + sc.n * 44 + sc.n * (D + 1) * 4
+    peak, kind = peaks()
+    achieved = alg / max(1.0, launches) / (comp_ms / 1e3) / 1e9
+    del fb, f32
+    torch.cuda.empty_cache()
+    return {"value": V * D / (ms / 1e3), "unit": UNIT, "ms_per_uplift": ms, "dtype": "bf16",
+            "config": {"workload": wl.name.replace("-d384", "-d512"), "d": D, "step": "uplift only",
+                       "aggregation": "tcgen05 kind::f16, bf16 weights, fp32 accumulation"},
+            "rel_l2_vs_f32_path": err, "err_views": nv,
+            "roofline": {"bound": "hbm", "kernel": "k_composite_tc", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_kind": kind},
+            "stages_ms_per_uplift": {k: v / reps for k, v in tr["ms"].items() if v > 0}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -276,6 +328,11 @@ def run_ours(args):
                        "d2h_bytes_per_step": int(sc.n * (D + 1) * 4),
                        "sample": f"views 0-{nv - 1} of {V} through ludvig_uplift_host (uplift only)"}
         del hf
+    if rank == 0 and not args.no_precision and args.workload == "paper":
+        del feats
+        torch.cuda.empty_cache()
+        line["precision_form"] = precision_form(sc, wl)
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:

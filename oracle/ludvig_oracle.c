@@ -310,8 +310,10 @@ static inline void rect_of(const orc_proj* p, int mode, int* x0, int* y0, int* x
     else { *x0 = p->x0; *y0 = p->y0; *x1 = p->x1; *y1 = p->y1; }
 }
 
-/* Builds offsets[ntiles+1] and list[offsets[ntiles]] (caller frees). */
-static int build_lists(int64_t n, const orc_proj* P, int mode, int TX, int TY,
+/* Builds offsets[ntiles+1] and list[offsets[ntiles]] (caller frees).  Only
+ * the tiles with sort_tile[t] != 0 are put in depth order (all of them when
+ * sort_tile is NULL); the others keep index order and must not be walked. */
+static int build_lists(int64_t n, const orc_proj* P, int mode, int TX, int TY, const uint8_t* sort_tile,
                        int64_t** offsets_out, int32_t** list_out)
 {
     int64_t ntiles = (int64_t)TX * TY;
@@ -341,6 +343,7 @@ static int build_lists(int64_t n, const orc_proj* P, int mode, int TX, int TY,
     g_sort.mode = mode;
     for (int64_t t = 0; t < ntiles; ++t) {
         int64_t len = off[t + 1] - off[t];
+        if (sort_tile && !sort_tile[t]) continue;
         if (len > 1) qsort(list + off[t], (size_t)len, sizeof(int32_t), mode == 64 ? cmp_depth64 : cmp_depth32);
     }
     *offsets_out = off;
@@ -446,7 +449,7 @@ int64_t orc_tile_lists(int64_t n, const float* means, const float* scales, const
     project_all(n, means, scales, quats, opac, cam, width, height, P, nthreads > 0 ? nthreads : 1);
     int64_t* off;
     int32_t* lst;
-    if (build_lists(n, P, mode, TX, TY, &off, &lst)) { free(P); return -2; }
+    if (build_lists(n, P, mode, TX, TY, NULL, &off, &lst)) { free(P); return -2; }
     int64_t ntiles = (int64_t)TX * TY, total = off[ntiles];
     for (int64_t t = 0; t < ntiles; ++t) { ranges[2 * t] = off[t]; ranges[2 * t + 1] = off[t + 1]; }
     if (list && total <= cap) memcpy(list, lst, sizeof(int32_t) * (size_t)total);
@@ -478,15 +481,20 @@ int64_t orc_view_uplift(int64_t n, const float* means, const float* scales, cons
     project_all(n, means, scales, quats, opac, cam, width, height, P, nthreads);
     int64_t* off;
     int32_t* lst;
-    if (build_lists(n, P, mode, TX, TY, &off, &lst)) { free(P); return -2; }
-
-    /* which tiles to composite */
+    /* which tiles to composite: all, or those whose list holds a wanted Gaussian */
     uint8_t* tile_on = (uint8_t*)calloc((size_t)ntiles, 1);
-    for (int64_t t = 0; t < ntiles; ++t) {
-        if (!want) { tile_on[t] = 1; continue; }
-        for (int64_t k = off[t]; k < off[t + 1]; ++k)
-            if (want[lst[k]]) { tile_on[t] = 1; break; }
+    if (!want) {
+        memset(tile_on, 1, (size_t)ntiles);
+    } else {
+        for (int64_t i = 0; i < n; ++i) {
+            if (!want[i] || !vis_of(&P[i], mode)) continue;
+            int x0, y0, x1, y1;
+            rect_of(&P[i], mode, &x0, &y0, &x1, &y1);
+            for (int ty = y0; ty < y1; ++ty)
+                for (int tx = x0; tx < x1; ++tx) tile_on[(int64_t)ty * TX + tx] = 1;
+        }
     }
+    if (build_lists(n, P, mode, TX, TY, tile_on, &off, &lst)) { free(P); free(tile_on); return -2; }
     /* composite every pixel of every selected tile; contributions kept per
      * tile in pixel (row-major) then depth order */
     orc_contrib** tc = (orc_contrib**)calloc((size_t)ntiles, sizeof(orc_contrib*));

@@ -192,6 +192,31 @@ extern "C" ludvig_status ludvig_scene_destroy(ludvig_scene_t s) {
 
 extern "C" int64_t ludvig_scene_size(ludvig_scene_t s) { return s ? s->n : -1; }
 
+namespace ludvig {
+namespace {
+std::atomic<int64_t> g_opt_f32_tc{1};
+}
+bool option_f32_tensor_cores() { return g_opt_f32_tc.load() != 0; }
+}  // namespace ludvig
+
+extern "C" ludvig_status ludvig_set_option(int32_t option, int64_t value) {
+    switch (option) {
+        case LUDVIG_OPT_F32_TENSOR_CORES:
+            g_opt_f32_tc.store(value != 0);
+            return LUDVIG_OK;
+        default:
+            set_error("unknown option %d", option);
+            return LUDVIG_ERR_ARG;
+    }
+}
+
+extern "C" int64_t ludvig_get_option(int32_t option) {
+    switch (option) {
+        case LUDVIG_OPT_F32_TENSOR_CORES: return g_opt_f32_tc.load();
+        default: return -1;
+    }
+}
+
 extern "C" ludvig_status ludvig_trace_enable(int32_t on) {
     g_trace.store(on != 0);
     return LUDVIG_OK;

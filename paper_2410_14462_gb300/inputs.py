@@ -235,6 +235,10 @@ class Workload:
     seed: int
     kind: str          # "mask" or "field"
 
+    def features_d(self, view: int, d: int, device="cpu", dtype=None):
+        """The same smooth field with another channel count (precision form)."""
+        return feature_field(self.seed, view, d, self.cams.height, self.cams.width, device=device, dtype=dtype)
+
     def features(self, view: int, device="cpu", dtype=None):
         """Feature map [H,W,D] of one view as a torch tensor."""
         import torch

@@ -38,6 +38,8 @@ SIGNATURES = {
     "ludvig_uplift_finalize": (_I32, [_I64, _I32, _P, _P, _P, _P, _P]),
     "ludvig_uplift": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
     "ludvig_uplift_host": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
+    "ludvig_set_option": (_I32, [_I32, _I64]),
+    "ludvig_get_option": (_I64, [_I32]),
     "ludvig_trace_enable": (_I32, [_I32]),
     "ludvig_trace_read": (_I32, [_P, _I32]),
     "ludvig_debug_project": (_I32, [_P, _P, _I32, _I32, _P, _P, _P]),
@@ -203,6 +205,17 @@ def uplift_host(scene: Scene, cams_params, width, height, feats: torch.Tensor, s
                                 _dtype_code(feats), d, ctypes.c_void_p(out.data_ptr()),
                                 ctypes.c_void_p(beta.data_ptr()), _stream(stream)), "ludvig_uplift_host")
     return out, beta
+
+
+OPT_F32_TENSOR_CORES = 0
+
+
+def set_option(option: int, value: int):
+    _check(load().ludvig_set_option(option, int(value)), "ludvig_set_option")
+
+
+def get_option(option: int) -> int:
+    return int(load().ludvig_get_option(option))
 
 
 STAGES = ["project", "depth_sort", "bin", "tile_sort", "composite", "normalise", "knn", "graph", "diffuse"]

@@ -251,3 +251,25 @@ def test_many_small_rows_overflow_row_table():
     assert pos.sum() > 2000
     assert np.array_equal(beta.cpu().numpy() > 0, pos)
     assert rel_l2(out.cpu().numpy(), f_ref, pos) <= 1e-5
+
+
+@pytest.mark.parametrize("d", [32, 96, 384])
+def test_f32_tensor_core_and_cuda_core_paths(d):
+    """Float32 features: the split-bfloat16 tensor-core kernel (default for
+    d >= 32) and the CUDA-core FFMA kernel both meet the 1e-5 gate."""
+    wl = inputs.small_field_workload(n=20_000, views=3, d=d, width=100, height=75)
+    f_ref, b_ref = oracle.uplift(wl.scene, wl.cams, lambda v: wl.features(v))
+    pos = b_ref > 0
+    errs = {}
+    try:
+        for opt in (1, 0):
+            ludvig.set_option(ludvig.OPT_F32_TENSOR_CORES, opt)
+            out, beta, _ = _gpu_uplift(wl, [0, 1, 2])
+            assert np.array_equal(beta > 0, pos)
+            errs[opt] = (rel_l2(out, f_ref, pos), rel_l2(beta, b_ref))
+    finally:
+        ludvig.set_option(ludvig.OPT_F32_TENSOR_CORES, 1)
+    print(f"d={d}: tensor-core f {errs[1][0]:.2e} beta {errs[1][1]:.2e}; "
+          f"cuda-core f {errs[0][0]:.2e} beta {errs[0][1]:.2e}")
+    for e in errs.values():
+        assert e[0] <= 1e-5 and e[1] <= 1e-5
