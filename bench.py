@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="uplift only (not a full step)")
     ap.add_argument("--no-precision", action="store_true", help="skip the bf16 precision-form line")
+    ap.add_argument("--profile-case", choices=["tc2views"], default=None,
+                    help="run a small fixed case for an ncu capture and exit (no JSON line)")
     return ap.parse_args()
 
 
@@ -342,8 +344,29 @@ def run_ours(args):
     return 0
 
 
+def profile_case(name):
+    """Uplift of views 0-1 of the paper-scale workload, D=384, twice with float32
+    features and twice with the same field in bfloat16 (ncu captures)."""
+    import torch
+    from paper_2410_14462_gb300 import build, inputs, ludvig
+    build.build()
+    ludvig.load()
+    wl = inputs.paper_scale_workload(views=2, d=384)
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    W, H = wl.cams.width, wl.cams.height
+    F = torch.stack([wl.features(v, device="cuda") for v in range(2)]).contiguous()
+    Fb = F.to(torch.bfloat16)
+    for _ in range(2):
+        ludvig.uplift(sc, wl.cams.params, W, H, F)
+        ludvig.uplift(sc, wl.cams.params, W, H, Fb)
+    torch.cuda.synchronize()
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        return profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
