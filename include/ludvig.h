@@ -251,6 +251,25 @@ ludvig_status ludvig_graph_export(ludvig_graph_t graph, int64_t* row_ptr, int32_
 ludvig_status ludvig_diffuse(ludvig_graph_t graph, const float* x0, int32_t dx, int32_t iters,
                              float* out, void* stream);
 
+/* Graph diffusion that allocates no memory (the paper has no counterpart: this
+ * is a service entry point).  It computes exactly what ludvig_diffuse
+ * computes, for callers that must not allocate device memory: a request loop
+ * that runs under a strict no-allocation policy once it is warm, a process
+ * whose device memory is already handed out to another allocator, or code
+ * that records its work into a CUDA graph.  Its scratch (the ping-pong vector
+ * and the per-step norms) lives in statically allocated device memory of the
+ * library: at most 1,048,576 elements (n * dx) and at most 1024 steps; larger
+ * requests fail with LUDVIG_ERR_ARG before anything is enqueued.  Every GPU
+ * that loads the library holds this scratch (about 4.3 MB) until the process
+ * exits.  The first call on a device translates the scratch's address for
+ * that device (once per device, with the device current); make that first
+ * call before any stream capture.  All calls share the one scratch area, so
+ * calls whose work overlaps on the GPU (different streams, or different host
+ * threads without ordering) race; the call clears the norm slots it uses.
+ * Arguments, layouts and results are those of ludvig_diffuse. */
+ludvig_status ludvig_diffuse_noalloc(ludvig_graph_t graph, const float* x0, int32_t dx, int32_t iters,
+                                     float* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -699,6 +700,90 @@ extern "C" ludvig_status ludvig_diffuse(ludvig_graph_t g, const float* x0, int32
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, ceil_div(n, 32)));
+    const float* xin = x0;
+    for (int t = 0; t < iters; ++t) {
+        float* y = bufs[t & 1];
+        if (dx == 1)
+            k_spmv_scaled<8><<<blocks, 256, 0, st>>>(g->row_ptr, g->col, g->val, xin, n, 1, n2 + 32 * t, y,
+                                                     n2 + 32 * (t + 1));
+        else
+            k_spmv_scaled<1><<<blocks, 256, 0, st>>>(g->row_ptr, g->col, g->val, xin, n, dx, n2 + 32 * t, y,
+                                                     n2 + 32 * (t + 1));
+        LV_LAUNCH();
+        xin = y;
+    }
+    return LUDVIG_OK;
+}
+
+// ---------------------------------------------------------------- diffusion without allocation
+// Scratch of ludvig_diffuse_noalloc in statically allocated device memory:
+// the ping-pong vector (at most kNoAllocMaxElems = n * dx floats, 4 MiB) and
+// the per-step column norms (at most kNoAllocMaxIters steps, 32 columns,
+// float64).  Every GPU that loads the library holds these 4.3 MB until the
+// process exits.  All calls share them, so calls that overlap on the GPU race.
+static constexpr int64_t kNoAllocMaxElems = (int64_t)1 << 20;
+static constexpr int32_t kNoAllocMaxIters = 1024;
+static constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) float g_noalloc_tmp[kNoAllocMaxElems];
+static __device__ __align__(256) double g_noalloc_norm2[(kNoAllocMaxIters + 1) * 32];
+
+namespace {
+std::mutex g_noalloc_mu;
+float* g_noalloc_tmp_ptr[kNoAllocMaxDevices] = {};
+double* g_noalloc_norm2_ptr[kNoAllocMaxDevices] = {};
+
+// Device addresses of the static scratch for the current device.  In host code
+// the array names are host-side stand-ins, not device addresses, so they are
+// translated once per device with cudaGetSymbolAddress.
+ludvig_status noalloc_scratch(float** tmp, double** norm2) {
+    int dev = 0;
+    LV_CUDA(cudaGetDevice(&dev));
+    LV_ARG(dev >= 0 && dev < kNoAllocMaxDevices, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_tmp_ptr[dev]) {
+        void* a = nullptr;
+        void* b = nullptr;
+        LV_CUDA(cudaGetSymbolAddress(&a, g_noalloc_tmp));
+        LV_CUDA(cudaGetSymbolAddress(&b, g_noalloc_norm2));
+        g_noalloc_tmp_ptr[dev] = static_cast<float*>(a);
+        g_noalloc_norm2_ptr[dev] = static_cast<double*>(b);
+    }
+    *tmp = g_noalloc_tmp_ptr[dev];
+    *norm2 = g_noalloc_norm2_ptr[dev];
+    return LUDVIG_OK;
+}
+}  // namespace
+
+extern "C" ludvig_status ludvig_diffuse_noalloc(ludvig_graph_t g, const float* x0, int32_t dx, int32_t iters,
+                                                float* out, void* stream) {
+    LV_ARG(g != nullptr, "graph is NULL");
+    LV_ARG(dx >= 1 && dx <= 32, "dx must be in [1, 32]");
+    LV_ARG(iters >= 0 && iters <= kNoAllocMaxIters, "iters must be in [0, %d] for the allocation-free call",
+           kNoAllocMaxIters);
+    LV_ARG(x0 != nullptr && out != nullptr, "NULL buffer");
+    LV_ARG(x0 != out, "out must not alias x0");
+    const int64_t n = g->n;
+    LV_ARG(n * dx <= kNoAllocMaxElems, "n * dx = %lld exceeds the allocation-free limit of %lld elements",
+           (long long)(n * dx), (long long)kNoAllocMaxElems);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n == 0) return LUDVIG_OK;
+    const size_t bytes = sizeof(float) * (size_t)n * dx;
+    if (iters == 0) {
+        LV_CUDA(cudaMemcpyAsync(out, x0, bytes, cudaMemcpyDeviceToDevice, st));
+        return LUDVIG_OK;
+    }
+    float* tmp;
+    double* n2;
+    LV_TRY(noalloc_scratch(&tmp, &n2));
+    float* bufs[2] = {(iters % 2 == 1) ? out : tmp, (iters % 2 == 1) ? tmp : out};
+    // the norm accumulators keep the previous call's sums: clear the slots used
+    LV_CUDA(cudaMemsetAsync(n2, 0, sizeof(double) * 32 * (size_t)(iters + 1), st));
+    k_colnorm2<<<(unsigned)std::min<int64_t>(592, ceil_div(n, 256)), 256, 0, st>>>(x0, n, dx, n2);
+    LV_LAUNCH();
+    int dev = 0, sms = 152;
+    LV_CUDA(cudaGetDevice(&dev));
+    LV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, ceil_div(n, 32)));
     const float* xin = x0;
     for (int t = 0; t < iters; ++t) {

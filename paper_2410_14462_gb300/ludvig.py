@@ -52,6 +52,7 @@ SIGNATURES = {
     "ludvig_graph_nnz": (_I64, [_P]),
     "ludvig_graph_export": (_I32, [_P, _P, _P, _P, _P]),
     "ludvig_diffuse": (_I32, [_P, _P, _I32, _I32, _P, _P]),
+    "ludvig_diffuse_noalloc": (_I32, [_P, _P, _I32, _I32, _P, _P]),
 }
 
 _lib = None
@@ -324,6 +325,16 @@ class Graph:
             out = torch.empty_like(x0)
         _check(L.ludvig_diffuse(self._h, _dev(x0, torch.float32, "x0"), dx, iters,
                                 _dev(out, torch.float32, "out"), _stream(stream)), "ludvig_diffuse")
+        return out
+
+    def diffuse_noalloc(self, x0: torch.Tensor, iters: int, out: torch.Tensor, stream=None):
+        """ludvig_diffuse_noalloc: the same diffusion with the library's static
+        scratch; `out` must be supplied (nothing is allocated)."""
+        L = load()
+        dx = 1 if x0.dim() == 1 else int(x0.shape[1])
+        _check(L.ludvig_diffuse_noalloc(self._h, _dev(x0, torch.float32, "x0"), dx, iters,
+                                        _dev(out, torch.float32, "out"), _stream(stream)),
+               "ludvig_diffuse_noalloc")
         return out
 
     def close(self):
