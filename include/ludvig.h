@@ -58,19 +58,18 @@ typedef enum {
 } ludvig_status;
 
 typedef enum {
-    LUDVIG_F32 = 0,              /* float32 features.  d >= 32: tensor-core aggregation with
-                                    weights and features split into two bfloat16 terms each
-                                    (float32-level accuracy); otherwise, or with
-                                    LUDVIG_OPT_F32_TENSOR_CORES = 0, CUDA-core FFMA */
-    LUDVIG_BF16 = 1              /* bfloat16 features; tensor-core aggregation with bfloat16
-                                    weights when d is a multiple of 64 up to 512, CUDA cores
-                                    otherwise */
+    LUDVIG_F32 = 0,              /* float32 features.  32 <= d <= 512, d % 8 == 0: tensor-core
+                                    aggregation with features and weights split into two
+                                    bfloat16 terms each (float32-level accuracy); otherwise, or
+                                    with LUDVIG_OPT_F32_TENSOR_CORES = 0, CUDA-core FFMA */
+    LUDVIG_BF16 = 1              /* bfloat16 features.  32 <= d <= 512, d % 8 == 0: tensor-core
+                                    aggregation with bfloat16 weights; otherwise CUDA cores */
 } ludvig_dtype;
 
 /* Process-wide options (ludvig_set_option / ludvig_get_option). */
 typedef enum {
     LUDVIG_OPT_F32_TENSOR_CORES = 0   /* 1 (default): float32 features use the split-bfloat16
-                                         tensor-core kernel when d >= 32; 0: CUDA-core FFMA */
+                                         tensor-core kernel where it applies; 0: CUDA-core FFMA */
 } ludvig_option;
 
 /* Sets an option; LUDVIG_ERR_ARG for an unknown option. */

@@ -32,26 +32,20 @@ namespace ludvig {
 constexpr int kMaxViews = 16;
 
 bool tc_supported(int dtype, int d);
-bool tc32_supported(int dtype, int d);
 bool option_f32_tensor_cores();
-ludvig_status composite_tc32(const float4* rec_a, const float2* rec_b, int64_t n, const uint2* ranges,
-                             const uint32_t* list, int nv, int width, int height, const float* feats, int d,
-                             float* num, float* den, Arena& ws, int* status, cudaStream_t st);
-
-// Which aggregation kernel a request uses.
-enum class AggPath { kCudaCore, kTensorBf16, kTensorF32 };
-AggPath agg_path(int dtype, int d) {
-    if (tc_supported(dtype, d)) return AggPath::kTensorBf16;
-    if (tc32_supported(dtype, d) && option_f32_tensor_cores()) return AggPath::kTensorF32;
-    return AggPath::kCudaCore;
-}
 ludvig_status composite_tc(const float4* rec_a, const float2* rec_b, int64_t n, const uint2* ranges,
-                           const uint32_t* list, int nv, int width, int height, const void* feats, int d,
+                           const uint32_t* list, int nv, int width, int height, const void* feats, int dtype, int d,
                            float* num, float* den, Arena& ws, int* status, cudaStream_t st);
 
 struct CamBatch {
     Cam cam[kMaxViews];
 };
+
+// Whether a request's aggregation runs on the tensor cores (else CUDA cores).
+bool use_tensor_cores(int dtype, int d) {
+    if (!tc_supported(dtype, d)) return false;
+    return dtype == LUDVIG_BF16 || option_f32_tensor_cores();
+}
 
 namespace {
 
@@ -642,14 +636,11 @@ ludvig_status run_chunk(ludvig_scene* s, const ludvig_camera* cams, int nv, int 
     const int64_t nitems = (int64_t)nv * ntiles;
     const bool vec = (d % 4 == 0);
     StageScope scope(LUDVIG_STAGE_COMPOSITE, st);
-    const AggPath path = agg_path(dtype, d);
-    if (path != AggPath::kCudaCore) {
+    if (use_tensor_cores(dtype, d)) {
         int* status;
         LV_TRY(ws.get("tc.status", 1, &status));
-        if (path == AggPath::kTensorBf16)
-            return composite_tc(rec_a, rec_b, n, ranges, spv, nv, width, height, feats, d, num, den, ws, status, st);
-        return composite_tc32(rec_a, rec_b, n, ranges, spv, nv, width, height, static_cast<const float*>(feats), d,
-                              num, den, ws, status, st);
+        return composite_tc(rec_a, rec_b, n, ranges, spv, nv, width, height, feats, dtype, d, num, den, ws, status,
+                            st);
     }
     if (dtype == LUDVIG_F32) {
         if (vec) return launch_composite<float, true>(args, nitems, st);
@@ -676,7 +667,7 @@ ludvig_status accumulate(ludvig_scene* s, const ludvig_camera* cams, int32_t n_v
     const size_t esize = dtype == LUDVIG_F32 ? 4 : 2;
     const int64_t view_elems = (int64_t)width * height * d;
     int* status = nullptr;
-    if (agg_path(dtype, d) != AggPath::kCudaCore) {
+    if (use_tensor_cores(dtype, d)) {
         LV_TRY(s->ws.get("tc.status", 1, &status));
         LV_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
     }

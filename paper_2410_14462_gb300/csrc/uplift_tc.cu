@@ -1,23 +1,29 @@
-// Tensor-core aggregation for bfloat16 features (the precision form of the
-// uplift, Sec. 3.2 Eq. 3): num[i,:] += sum_p w_i(p) F[p,:] computed per 16x16
-// tile as the dense product W_tile^T F_tile on the 5th-generation tensor cores.
+// Tensor-core aggregation of the uplift (Sec. 3.2, Eq. 3):
+// num[i,:] += sum_p w_i(p) F[p,:] per 16x16 tile as the dense product
+// W_tile^T F_tile on the 5th-generation tensor cores, for bfloat16 features
+// (NT = 1) and float32 features (NT = 2, float32-level accuracy).
+//
+// NT = 2: the float32 features are split beforehand into two bfloat16 arrays
+// F = F1 + F2 (k_split_f32) and the weights into w = W1 + W2; the product keeps
+// W1 F1 + W2 F1 + W1 F2 (16 significant bits per operand, the dropped W2 F2 and
+// the residuals are below 2^-16 relative).  beta sums the same W terms, so each
+// f_i stays a convex combination of the features.
 //
 // One persistent CTA per SM (8 warps = 256 pixels) takes (view, tile) items
-// from an atomic counter and, for each item:
-//   * walks the tile's depth-ordered list in batches of 32 Gaussians (the same
-//     float32 rules as the CUDA-core path: alpha, 1/255 skip, 1e-4 stop);
-//   * appends every Gaussian with a non-zero weight in the tile as one row of
-//     a 128 x 256 bfloat16 W tile in shared memory (K-major, 128-byte
-//     swizzle); beta_i sums the same bfloat16-rounded weights, so each f_i stays
-//     a convex combination of the features;
-//   * when the W tile is full (or the list ends) one thread streams the tile's
-//     features channel block by channel block (256 pixels x 64 channels, TMA,
-//     4-stage ring, MN-major 128-byte swizzle) and issues tcgen05.mma
-//     (kind::f16, M=128, N=64, K=16) into a 128 x D float32 accumulator in
-//     tensor memory;
-//   * all warps read the accumulator back (tcgen05.ld) and add each Gaussian's
-//     row into num with vector reductions.
-// Every mbarrier wait is bounded; on expiry the kernel records
+// from an atomic counter.  For each item it
+//   * walks the tile's depth-ordered list in batches of 32 Gaussians (float32
+//     rules of Eq. 1: alpha, 1/255 skip, 1e-4 stop), one 8x4 pixel block per
+//     warp, with the next batch's records and culling constants prefetched;
+//   * appends every Gaussian with a non-zero weight in the tile as a row of a
+//     128 x 256 W tile per term in shared memory (K-major, 128-byte swizzle);
+//   * when the tile cannot take another batch (or the list ends) thread 0
+//     streams the feature tile through a TMA ring (256 pixels x 64 channels
+//     per stage, MN-major 128-byte swizzle, zero fill past the image and past
+//     d) and issues tcgen05.mma (kind::f16, M = 128, N = 64, K = 16) into a
+//     128 x 64*DB float32 accumulator in tensor memory;
+//   * all warps read the accumulator back (tcgen05.ld) and add each row into
+//     num with vector reductions.
+// Every mbarrier wait is bounded: on expiry the kernel records
 // LUDVIG_ERR_TIMEOUT, drains what it issued (bounded), frees tensor memory and
 // returns.
 #include <cuda.h>
@@ -38,30 +44,35 @@ using namespace tc;
 
 constexpr int kTcThreads = 256;
 constexpr int kTcRows = 128;                       // MMA M: Gaussians per W tile
-constexpr int kTcStages = 4;                       // feature channel-block ring
 constexpr int kTcBatch = 32;                       // Gaussians composited per step
-constexpr uint32_t kWBytes = kTcRows * 256 * 2;    // 64 KB
+constexpr uint32_t kWBytes = kTcRows * 256 * 2;    // 64 KB per bfloat16 term
 constexpr uint32_t kFBlockBytes = 256 * 64 * 2;    // 32 KB: 256 pixels x 64 channels
 
+template <int NT>
 struct TcSmem {
-    uint8_t W[kWBytes];                            // offset 0 (1024-aligned)
-    uint8_t F[kTcStages][kFBlockBytes];            // 1024-aligned stages
-    uint64_t full[kTcStages];
-    uint64_t empty[kTcStages];
+    static constexpr int kStages = NT == 1 ? 4 : 2;
+    uint8_t W[NT][kWBytes];                        // offset 0 (1024-aligned)
+    uint8_t F[kStages][kFBlockBytes];              // 1024-aligned stages
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
     uint64_t mma_done;
-    float4 ra[kTcBatch];
-    float2 rb[kTcBatch];
-    uint32_t gid[kTcBatch];
+    float4 ra[2][kTcBatch];                        // [buffer][j]
+    float2 rb[2][kTcBatch];
+    float4 rr[2][kTcBatch];                        // culling constants: thr, 1/a, 1/c, possible
+    uint32_t gid[2][kTcBatch];
     uint32_t row_gid[kTcRows];
     float row_den[kTcRows];
     float denpart[8][kTcBatch];
-    uint32_t rowmask;
+    uint32_t rowmask[2];
     uint32_t tmem_base;
     int item;
     int abort_flag;
 };
 
-constexpr size_t kTcSmemBytes = sizeof(TcSmem) + 1024;   // + alignment slack
+template <int NT>
+constexpr size_t tc_smem_bytes() {
+    return sizeof(TcSmem<NT>) + 1024;   // + alignment slack
+}
 
 // kind::f16 instruction descriptor: D float32, A and B bfloat16, A K-major,
 // B MN-major, M = 128, N = 64.
@@ -90,64 +101,70 @@ struct TcArgs {
     int store_mode;   // debug GEMM: plain stores of the accumulator, no list
 };
 
-// Producer + MMA issue for one W tile (thread 0 only).  Returns false on a
-// timed-out wait.
-template <int DB>
-__device__ bool issue_tile(TcSmem& S, const CUtensorMap* fmap, uint32_t& fcount, int tx, int ty, int v) {
-    const uint32_t w_base = saddr(S.W);
-    const uint32_t tmem = S.tmem_base;
-    auto issue = [&](int cb) -> bool {
-        const uint32_t k = fcount + cb, s = k % kTcStages;
-        if (k >= (uint32_t)kTcStages && !mbar_wait(&S.empty[s], ((k / kTcStages) - 1) & 1u)) return false;
+template <int NT>
+__device__ __forceinline__ void fail(TcSmem<NT>& S, int* status) {
+    S.abort_flag = 1;
+    atomicExch(status, (int)LUDVIG_ERR_TIMEOUT);
+}
+
+// TMA loads + MMA issue for one W tile (thread 0 only).  `fcount` counts the
+// feature blocks loaded so far (ring position); false on a timed-out wait.
+template <int DB, int NT>
+__device__ bool issue_tile(TcSmem<NT>& S, const CUtensorMap* f1, const CUtensorMap* f2, uint32_t& fcount, int tx,
+                           int ty, int v) {
+    constexpr int kS = TcSmem<NT>::kStages;
+    constexpr int kLoads = DB * NT;   // F1 block cb, then F2 block cb (NT = 2)
+    auto issue = [&](int l) -> bool {
+        const uint32_t k = fcount + l, s = k % kS;
+        if (k >= (uint32_t)kS && !mbar_wait(&S.empty[s], ((k / kS) - 1) & 1u)) return false;
         mbar_expect_tx(&S.full[s], kFBlockBytes);
-        tma_load_4d(S.F[s], fmap, &S.full[s], 64 * cb, tx * kTile, ty * kTile, v);
+        const int cb = l / NT, term = l % NT;
+        tma_load_4d(S.F[s], term == 0 ? f1 : f2, &S.full[s], 64 * cb, tx * kTile, ty * kTile, v);
         return true;
     };
-    for (int cb = 0; cb < DB && cb < kTcStages; ++cb)
-        if (!issue(cb)) return false;
+    for (int l = 0; l < kLoads && l < kS; ++l)
+        if (!issue(l)) return false;
     tc_fence_after();
-    for (int cb = 0; cb < DB; ++cb) {
-        const uint32_t k = fcount + cb, s = k % kTcStages;
-        if (!mbar_wait(&S.full[s], (k / kTcStages) & 1u)) return false;
+    const uint32_t tmem = S.tmem_base;
+    for (int l = 0; l < kLoads; ++l) {
+        const uint32_t k = fcount + l, s = k % kS;
+        const int cb = l / NT, term = l % NT;
+        if (!mbar_wait(&S.full[s], (k / kS) & 1u)) return false;
         tc_fence_after();
         const uint32_t f_base = saddr(S.F[s]);
+        // term 0 (F1): W1 F1 (+ W2 F1); term 1 (F2): W1 F2
 #pragma unroll
         for (int ks = 0; ks < 16; ++ks) {
-            const uint64_t ad = sw128_desc(w_base + (ks >> 2) * (kTcRows * 128) + (ks & 3) * 32, 16, 1024);
             const uint64_t bd = sw128_desc(f_base + ks * 2048, 1024, 1024);
-            mma_bf16(tmem + 64 * cb, ad, bd, kIdesc, ks > 0 ? 1u : 0u);
+            const uint32_t koff = (ks >> 2) * (kTcRows * 128) + (ks & 3) * 32;
+            const uint32_t acc = (ks > 0 || term > 0) ? 1u : 0u;
+            mma_bf16(tmem + 64 * cb, sw128_desc(saddr(S.W[0]) + koff, 16, 1024), bd, kIdesc, acc);
+            if (NT == 2 && term == 0)
+                mma_bf16(tmem + 64 * cb, sw128_desc(saddr(S.W[NT - 1]) + koff, 16, 1024), bd, kIdesc, 1u);
         }
         mma_commit(&S.empty[s]);
-        // refill the stage of the previous block (its MMAs are queued ahead)
-        if (cb >= 1 && cb - 1 + kTcStages < DB)
-            if (!issue(cb - 1 + kTcStages)) return false;
+        // refill the stage of the previous load (its MMAs are queued ahead)
+        if (l >= 1 && l - 1 + kS < kLoads)
+            if (!issue(l - 1 + kS)) return false;
     }
     mma_commit(&S.mma_done);
-    fcount += DB;
+    fcount += kLoads;
     return true;
 }
 
-// Flush of the W tile: MMA over all channel blocks, then read back the
-// accumulator rows [0, nrows) and add them into num (or store them in debug
-// mode).  Called by all threads.
-template <int DB>
-__device__ void flush_tile(TcSmem& S, const TcArgs& a, const CUtensorMap* fmap, int nrows, uint32_t& fcount,
-                           uint32_t& mma_phase, int tx, int ty, int v) {
+// Flush of the W tile rows [0, nrows): MMA over every channel block, then the
+// accumulator rows are added into num (or stored, in debug mode).  All threads.
+template <int DB, int NT>
+__device__ __noinline__ void flush_tile(TcSmem<NT>& S, const TcArgs& a, const CUtensorMap* f1,
+                                        const CUtensorMap* f2, int nrows, uint32_t& fcount, uint32_t& mma_phase,
+                                        int tx, int ty, int v) {
     fence_proxy_async();   // W written with generic stores, read by the tensor core
     __syncthreads();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        if (!issue_tile<DB>(S, fmap, fcount, tx, ty, v)) {
-            S.abort_flag = 1;
-            atomicExch(a.status, (int)LUDVIG_ERR_TIMEOUT);
-        }
-    }
+    if (tid == 0 && !issue_tile<DB, NT>(S, f1, f2, fcount, tx, ty, v)) fail(S, a.status);
     __syncthreads();
     if (S.abort_flag) return;
-    if (!mbar_wait(&S.mma_done, mma_phase)) {
-        S.abort_flag = 1;
-        atomicExch(a.status, (int)LUDVIG_ERR_TIMEOUT);
-    }
+    if (!mbar_wait(&S.mma_done, mma_phase)) fail(S, a.status);
     mma_phase ^= 1u;
     __syncthreads();
     if (S.abort_flag) return;
@@ -165,10 +182,13 @@ __device__ void flush_tile(TcSmem& S, const TcArgs& a, const CUtensorMap* fmap, 
             float* dst = a.num + (int64_t)g * d + 32 * u;
             if (a.store_mode) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) dst[i] = val[i];
+                for (int i = 0; i < 32; ++i)
+                    if (32 * u + i < d) dst[i] = val[i];
             } else {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) red_add_v4(dst + 4 * i, val[4 * i], val[4 * i + 1], val[4 * i + 2], val[4 * i + 3]);
+                for (int i = 0; i < 8; ++i)
+                    if (32 * u + 4 * i < d)
+                        red_add_v4(dst + 4 * i, val[4 * i], val[4 * i + 1], val[4 * i + 2], val[4 * i + 3]);
             }
         }
     }
@@ -177,16 +197,18 @@ __device__ void flush_tile(TcSmem& S, const TcArgs& a, const CUtensorMap* fmap, 
     __syncthreads();
 }
 
-template <int DB>
-__global__ void __launch_bounds__(kTcThreads, 1) k_composite_tc(TcArgs a, const __grid_constant__ CUtensorMap fmap) {
+template <int DB, int NT>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_composite_tc(TcArgs a, const __grid_constant__ CUtensorMap fmap1, const __grid_constant__ CUtensorMap fmap2) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const uint32_t pad = (1024u - (saddr(smem_raw) & 1023u)) & 1023u;
-    TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw + pad);
+    TcSmem<NT>& S = *reinterpret_cast<TcSmem<NT>*>(smem_raw + pad);
+    constexpr int kS = TcSmem<NT>::kStages;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
 
     if (tid == 0) {
-        for (int s = 0; s < kTcStages; ++s) {
+        for (int s = 0; s < kS; ++s) {
             mbar_init(&S.full[s], 1);
             mbar_init(&S.empty[s], 1);
         }
@@ -202,14 +224,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_composite_tc(TcArgs a, const 
     uint32_t fcount = 0, mma_phase = 0;
 
     if (a.store_mode) {
-        // debug GEMM: W rows come from a.num's companion buffer a.list (bf16 [128][256])
+        // debug GEMM: W rows come from a.list reinterpreted as bf16 [128][256]
         const __nv_bfloat16* Ain = reinterpret_cast<const __nv_bfloat16*>(a.list);
         for (int e = tid; e < kTcRows * 256; e += kTcThreads) {
             const int r = e >> 8, k = e & 255;
-            *reinterpret_cast<__nv_bfloat16*>(S.W + w_offset(r, k)) = Ain[e];
+            *reinterpret_cast<__nv_bfloat16*>(S.W[0] + w_offset(r, k)) = Ain[e];
         }
         if (tid < kTcRows) S.row_gid[tid] = tid;
-        flush_tile<DB>(S, a, &fmap, kTcRows, fcount, mma_phase, 0, 0, 0);
+        flush_tile<DB, NT>(S, a, &fmap1, &fmap2, kTcRows, fcount, mma_phase, 0, 0, 0);
     } else {
         // warp w covers the 8x4 pixel block ((w & 1) * 8, (w >> 1) * 4) of the tile
         const int bx = (warp & 1) * 8, by = (warp >> 1) * 4;
@@ -229,27 +251,59 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_composite_tc(TcArgs a, const 
             const uint2 range = a.ranges[item];
             const float4* rec_a = a.rec_a + (int64_t)v * a.n;
             const float2* rec_b = a.rec_b + (int64_t)v * a.n;
+            if (tid < kTcBatch && range.x + tid < range.y) {
+                const uint32_t g0 = a.list[range.x + tid];
+                const float4 ra = rec_a[g0];
+                const float2 rb = rec_b[g0];
+                const Reach R = reach_prep(ra.z, ra.w, rb.x, rb.y);
+                S.gid[0][tid] = g0;
+                S.ra[0][tid] = ra;
+                S.rb[0][tid] = rb;
+                S.rr[0][tid] = make_float4(R.thr, R.inv_ca, R.inv_cc, R.possible ? 1.f : 0.f);
+            }
+            if (tid == 0) {
+                S.rowmask[0] = 0u;
+                S.rowmask[1] = 0u;
+            }
+            __syncthreads();
             float T = 1.0f;
             bool done = !inside;
             int nrows = 0;
-            for (uint32_t b0 = range.x; b0 < range.y; b0 += kTcBatch) {
+            int buf = 0;
+            for (uint32_t b0 = range.x; b0 < range.y; b0 += kTcBatch, buf ^= 1) {
                 if (__syncthreads_count(!done) == 0) break;
-                const int cnt = (int)min((uint32_t)kTcBatch, range.y - b0);
-                if (tid < cnt) {
-                    const uint32_t g = a.list[b0 + tid];
-                    S.gid[tid] = g;
-                    S.ra[tid] = rec_a[g];
-                    S.rb[tid] = rec_b[g];
+                // room for up to 32 new rows, before any weight is live in registers
+                if (nrows + kTcBatch > kTcRows) {
+                    flush_tile<DB, NT>(S, a, &fmap1, &fmap2, nrows, fcount, mma_phase, tx, ty, v);
+                    nrows = 0;
+                    if (S.abort_flag) break;
                 }
-                if (tid == 0) S.rowmask = 0u;
-                __syncthreads();
+                const int cnt = (int)min((uint32_t)kTcBatch, range.y - b0);
+                // prefetch the next batch's records (stored at the end of this batch)
+                const uint32_t nb0 = b0 + kTcBatch;
+                const bool pf = tid < kTcBatch && nb0 + tid < range.y;
+                uint32_t pg = 0;
+                float4 pra = make_float4(0.f, 0.f, 0.f, 0.f);
+                float2 prb = make_float2(0.f, 0.f);
+                if (pf) {
+                    pg = a.list[nb0 + tid];
+                    pra = rec_a[pg];
+                    prb = rec_b[pg];
+                }
                 uint32_t rel;
                 {
                     bool rr = false;
                     if (lane < cnt) {
-                        const float4 ra = S.ra[lane];
-                        const float2 rb = S.rb[lane];
-                        rr = reaches_rect(ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, bxa, bxa + 7.0f, bya, bya + 3.0f);
+                        const float4 ra = S.ra[buf][lane];
+                        const float2 rb = S.rb[buf][lane];
+                        const float4 c4 = S.rr[buf][lane];
+                        Reach R;
+                        R.thr = c4.x;
+                        R.inv_ca = c4.y;
+                        R.inv_cc = c4.z;
+                        R.possible = c4.w != 0.f;
+                        R.cb2 = __fmul_rn(2.0f, ra.w);
+                        rr = reaches_rect(R, ra.x, ra.y, ra.z, ra.w, rb.x, bxa, bxa + 7.0f, bya, bya + 3.0f);
                     }
                     rel = __ballot_sync(0xffffffffu, rr);
                     if (!__any_sync(0xffffffffu, !done)) rel = 0u;
@@ -259,22 +313,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_composite_tc(TcArgs a, const 
                 for (int j = 0; j < kTcBatch; ++j) {
                     w[j] = 0.f;
                     if (((rel >> j) & 1u) && !done) {
-                        const float4 ra = S.ra[j];
-                        const float2 rb = S.rb[j];
+                        const float4 ra = S.ra[buf][j];
+                        const float2 rb = S.rb[buf][j];
                         const float al = alpha_at(ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, pxf, pyf);
                         if (al > 0.f) {
                             const float Tn = __fmul_rn(T, __fsub_rn(1.0f, al));
                             if (Tn < kTransMin) {
                                 done = true;
                             } else {
-                                w[j] = __bfloat162float(__float2bfloat16_rn(__fmul_rn(al, T)));
+                                w[j] = __fmul_rn(al, T);
                                 T = Tn;
                             }
                         }
                     }
                 }
-                // Gaussians with a non-zero weight somewhere in the tile, and their
-                // per-warp weight sums (beta uses the same rounded weights)
+                // Gaussians with a non-zero weight somewhere in the tile and their
+                // per-warp sums of the W terms (beta uses the same rounded weights)
                 uint32_t mine = 0u;
 #pragma unroll
                 for (int j = 0; j < kTcBatch; ++j) {
@@ -282,27 +336,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_composite_tc(TcArgs a, const 
                     float sj = 0.f;
                     if (m) {
                         mine |= 1u << j;
-                        sj = w[j];
+                        const __nv_bfloat16 h1 = __float2bfloat16_rn(w[j]);
+                        sj = __bfloat162float(h1);
+                        if (NT == 2) sj += __bfloat162float(__float2bfloat16_rn(w[j] - __bfloat162float(h1)));
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o);
                     }
                     if (lane == 0) S.denpart[warp][j] = sj;
                 }
-                if (lane == 0 && mine) atomicOr(&S.rowmask, mine);
+                if (lane == 0 && mine) atomicOr(&S.rowmask[buf], mine);
+                if (tid == 0) S.rowmask[buf ^ 1] = 0u;
                 __syncthreads();
-                const uint32_t rowmask = S.rowmask;
+                const uint32_t rowmask = S.rowmask[buf];
                 const int nnew = __popc(rowmask);
                 if (nnew) {
-                    if (nrows + nnew > kTcRows) {
-                        flush_tile<DB>(S, a, &fmap, nrows, fcount, mma_phase, tx, ty, v);
-                        nrows = 0;
-                        if (S.abort_flag) break;
-                    }
 #pragma unroll
                     for (int j = 0; j < kTcBatch; ++j) {
                         if ((rowmask >> j) & 1u) {
                             const int slot = nrows + __popc(rowmask & ((1u << j) - 1u));
-                            *reinterpret_cast<__nv_bfloat16*>(S.W + w_offset(slot, pix)) = __float2bfloat16_rn(w[j]);
+                            const uint32_t o = w_offset(slot, pix);
+                            const __nv_bfloat16 h1 = __float2bfloat16_rn(w[j]);
+                            *reinterpret_cast<__nv_bfloat16*>(S.W[0] + o) = h1;
+                            if (NT == 2)
+                                *reinterpret_cast<__nv_bfloat16*>(S.W[NT - 1] + o) =
+                                    __float2bfloat16_rn(w[j] - __bfloat162float(h1));
                         }
                     }
                     if (tid < kTcBatch && ((rowmask >> tid) & 1u)) {
@@ -310,28 +367,48 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_composite_tc(TcArgs a, const 
                         float s = 0.f;
 #pragma unroll
                         for (int wi = 0; wi < 8; ++wi) s += S.denpart[wi][tid];
-                        S.row_gid[slot] = S.gid[tid];
+                        S.row_gid[slot] = S.gid[buf][tid];
                         S.row_den[slot] = s;
                     }
                     nrows += nnew;
                 }
+                if (pf) {
+                    const Reach R = reach_prep(pra.z, pra.w, prb.x, prb.y);
+                    S.gid[buf ^ 1][tid] = pg;
+                    S.ra[buf ^ 1][tid] = pra;
+                    S.rb[buf ^ 1][tid] = prb;
+                    S.rr[buf ^ 1][tid] = make_float4(R.thr, R.inv_ca, R.inv_cc, R.possible ? 1.f : 0.f);
+                }
                 __syncthreads();
             }
             if (S.abort_flag) break;
-            if (nrows > 0) flush_tile<DB>(S, a, &fmap, nrows, fcount, mma_phase, tx, ty, v);
+            if (nrows > 0) flush_tile<DB, NT>(S, a, &fmap1, &fmap2, nrows, fcount, mma_phase, tx, ty, v);
             if (S.abort_flag) break;
             __syncthreads();   // every thread has read S.item before thread 0 takes the next one
         }
     }
     __syncthreads();
-    if (S.abort_flag && tid == 0) {
-        // drain: wait (bounded) for whatever was committed last
-        mbar_wait(&S.mma_done, mma_phase);
-    }
+    if (S.abort_flag && tid == 0) mbar_wait(&S.mma_done, mma_phase);   // drain (bounded)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0) tmem_dealloc(S.tmem_base, 512);
+}
+
+// float32 features -> two bfloat16 arrays with f = hi + lo to 16 significant bits.
+__global__ void k_split_f32(const float4* __restrict__ f, uint2* __restrict__ hi, uint2* __restrict__ lo,
+                            int64_t n4) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 x = f[i];
+        const __nv_bfloat16 a = __float2bfloat16_rn(x.x), b = __float2bfloat16_rn(x.y);
+        const __nv_bfloat16 c = __float2bfloat16_rn(x.z), e = __float2bfloat16_rn(x.w);
+        auto pk = [](__nv_bfloat16 l, __nv_bfloat16 h) {
+            return (uint32_t)__bfloat16_as_ushort(l) | ((uint32_t)__bfloat16_as_ushort(h) << 16);
+        };
+        hi[i] = make_uint2(pk(a, b), pk(c, e));
+        lo[i] = make_uint2(pk(__float2bfloat16_rn(x.x - __bfloat162float(a)), __float2bfloat16_rn(x.y - __bfloat162float(b))),
+                           pk(__float2bfloat16_rn(x.z - __bfloat162float(c)), __float2bfloat16_rn(x.w - __bfloat162float(e))));
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -350,7 +427,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // Tensor map over features [nv, H, W, d] bfloat16: box of 64 channels x 16 x 16
-// pixels of one view, 128-byte swizzle, zero fill outside the image.
+// pixels of one view, 128-byte swizzle, zero fill outside the image and past d.
 ludvig_status make_feature_map(CUtensorMap* map, const void* feats, int nv, int width, int height, int d) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) {
@@ -371,50 +448,72 @@ ludvig_status make_feature_map(CUtensorMap* map, const void* feats, int nv, int 
     return LUDVIG_OK;
 }
 
-template <int DB>
-ludvig_status launch_tc(const TcArgs& args, const CUtensorMap& map, int grid, cudaStream_t st) {
+template <int DB, int NT>
+ludvig_status launch_tc(const TcArgs& args, const CUtensorMap& m1, const CUtensorMap& m2, int grid, cudaStream_t st) {
     static bool configured = false;
     if (!configured) {
-        LV_CUDA(cudaFuncSetAttribute(k_composite_tc<DB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kTcSmemBytes));
+        LV_CUDA(cudaFuncSetAttribute(k_composite_tc<DB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tc_smem_bytes<NT>()));
         configured = true;
     }
-    k_composite_tc<DB><<<grid, kTcThreads, kTcSmemBytes, st>>>(args, map);
+    k_composite_tc<DB, NT><<<grid, kTcThreads, tc_smem_bytes<NT>(), st>>>(args, m1, m2);
     LV_LAUNCH();
     return LUDVIG_OK;
 }
 
-ludvig_status dispatch_tc(const TcArgs& args, const CUtensorMap& map, int grid, cudaStream_t st) {
-    switch (args.d / 64) {
-        case 1: return launch_tc<1>(args, map, grid, st);
-        case 2: return launch_tc<2>(args, map, grid, st);
-        case 3: return launch_tc<3>(args, map, grid, st);
-        case 4: return launch_tc<4>(args, map, grid, st);
-        case 5: return launch_tc<5>(args, map, grid, st);
-        case 6: return launch_tc<6>(args, map, grid, st);
-        case 7: return launch_tc<7>(args, map, grid, st);
-        case 8: return launch_tc<8>(args, map, grid, st);
-        default: set_error("tensor-core path needs d = 64..512 in steps of 64"); return LUDVIG_ERR_INTERNAL;
+template <int NT>
+ludvig_status dispatch_tc(const TcArgs& args, const CUtensorMap& m1, const CUtensorMap& m2, int grid,
+                          cudaStream_t st) {
+    switch ((args.d + 63) / 64) {
+        case 1: return launch_tc<1, NT>(args, m1, m2, grid, st);
+        case 2: return launch_tc<2, NT>(args, m1, m2, grid, st);
+        case 3: return launch_tc<3, NT>(args, m1, m2, grid, st);
+        case 4: return launch_tc<4, NT>(args, m1, m2, grid, st);
+        case 5: return launch_tc<5, NT>(args, m1, m2, grid, st);
+        case 6: return launch_tc<6, NT>(args, m1, m2, grid, st);
+        case 7: return launch_tc<7, NT>(args, m1, m2, grid, st);
+        case 8: return launch_tc<8, NT>(args, m1, m2, grid, st);
+        default: set_error("tensor-core path needs 32 <= d <= 512"); return LUDVIG_ERR_INTERNAL;
     }
 }
 
 }  // namespace
 
-bool tc_supported(int dtype, int d) { return dtype == LUDVIG_BF16 && d % 64 == 0 && d >= 64 && d <= 512; }
+// Tensor-core aggregation applies to d in [32, 512] with d % 8 == 0 (16-byte
+// rows for TMA); bfloat16 features always, float32 unless disabled.
+bool tc_supported(int dtype, int d) {
+    return (dtype == LUDVIG_BF16 || dtype == LUDVIG_F32) && d >= 32 && d <= 512 && d % 8 == 0;
+}
 
 // Composite + tensor-core aggregation of one chunk of views (stage 6 of the
 // uplift pipeline).  `status` receives LUDVIG_ERR_TIMEOUT if a wait expired.
 ludvig_status composite_tc(const float4* rec_a, const float2* rec_b, int64_t n, const uint2* ranges,
-                           const uint32_t* list, int nv, int width, int height, const void* feats, int d,
+                           const uint32_t* list, int nv, int width, int height, const void* feats, int dtype, int d,
                            float* num, float* den, Arena& ws, int* status, cudaStream_t st) {
-    CUtensorMap map;
-    LV_TRY(make_feature_map(&map, feats, nv, width, height, d));
-    int* counter;
-    LV_TRY(ws.get("tc.counter", 1, &counter));
-    LV_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
+    CUtensorMap m1, m2;
+    const void* f1 = feats;
+    const void* f2 = feats;
     int dev = 0, sms = 148;
     LV_CUDA(cudaGetDevice(&dev));
     LV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (dtype == LUDVIG_F32) {
+        // split the chunk's float32 features into two bfloat16 arrays
+        const int64_t count = (int64_t)nv * width * height * d;
+        void *hi, *lo;
+        LV_TRY(ws.get("tc.f_hi", (size_t)count * 2, &hi));
+        LV_TRY(ws.get("tc.f_lo", (size_t)count * 2, &lo));
+        k_split_f32<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, ceil_div(count / 4, 256))), 256,
+                      0, st>>>(static_cast<const float4*>(feats), static_cast<uint2*>(hi), static_cast<uint2*>(lo),
+                               count / 4);
+        LV_LAUNCH();
+        f1 = hi;
+        f2 = lo;
+    }
+    LV_TRY(make_feature_map(&m1, f1, nv, width, height, d));
+    LV_TRY(make_feature_map(&m2, f2, nv, width, height, d));
+    int* counter;
+    LV_TRY(ws.get("tc.counter", 1, &counter));
+    LV_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
     const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
     TcArgs a;
     a.rec_a = rec_a;
@@ -433,7 +532,9 @@ ludvig_status composite_tc(const float4* rec_a, const float2* rec_b, int64_t n, 
     a.counter = counter;
     a.status = status;
     a.store_mode = 0;
-    return dispatch_tc(a, map, std::min(sms, a.nitems), st);
+    const int grid = std::min(sms, a.nitems);
+    if (dtype == LUDVIG_F32) return dispatch_tc<2>(a, m1, m2, grid, st);
+    return dispatch_tc<1>(a, m1, m2, grid, st);
 }
 
 }  // namespace ludvig
@@ -455,7 +556,7 @@ extern "C" ludvig_status ludvig_debug_mma_bf16(const void* a, const void* f, int
     args.num = out;
     args.status = status;
     args.store_mode = 1;
-    LV_TRY(dispatch_tc(args, map, 1, st));
+    LV_TRY(dispatch_tc<1>(args, map, map, 1, st));
     int h = 0;
     LV_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     LV_CUDA(cudaStreamSynchronize(st));
