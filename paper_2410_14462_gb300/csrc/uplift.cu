@@ -363,23 +363,30 @@ __global__ void __launch_bounds__(256, 2) k_composite(CompositeArgs a) {
             rel = __ballot_sync(0xffffffffu, r);
             if (!__any_sync(0xffffffffu, !done)) rel = 0u;
         }
+        // alphas of the batch first (independent chains the scheduler can
+        // overlap), then the sequential transmittance recursion
         float w[kBatch];
 #pragma unroll
         for (int j = 0; j < kBatch; ++j) {
             w[j] = 0.f;
-            if (((rel >> j) & 1u) && !done) {
+            if ((rel >> j) & 1u) {
                 const float4 ra = sm.ra[j];
                 const float2 rb = sm.rb[j];
-                const float al = alpha_at(ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, pxf, pyf);
-                if (al > 0.f) {
-                    const float Tn = __fmul_rn(T, __fsub_rn(1.0f, al));
-                    if (Tn < kTransMin) {
-                        done = true;
-                    } else {
-                        w[j] = __fmul_rn(al, T);
-                        T = Tn;
-                        ++ncontrib;
-                    }
+                w[j] = alpha_at(ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, pxf, pyf);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const float al = w[j];
+            w[j] = 0.f;
+            if (al > 0.f && !done) {
+                const float Tn = __fmul_rn(T, __fsub_rn(1.0f, al));
+                if (Tn < kTransMin) {
+                    done = true;
+                } else {
+                    w[j] = __fmul_rn(al, T);
+                    T = Tn;
+                    ++ncontrib;
                 }
             }
         }

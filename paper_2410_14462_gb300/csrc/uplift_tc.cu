@@ -61,8 +61,6 @@ struct TcSmem {
     float4 rr[2][kTcBatch];                        // culling constants: thr, 1/a, 1/c, possible
     uint32_t gid[2][kTcBatch];
     uint32_t row_gid[kTcRows];
-    float row_den[kTcRows];
-    float denpart[8][kTcBatch];
     uint32_t rowmask[2];
     uint32_t tmem_base;
     int item;
@@ -192,8 +190,35 @@ __device__ __noinline__ void flush_tile(TcSmem<NT>& S, const TcArgs& a, const CU
             }
         }
     }
-    if (!a.store_mode && tid < nrows) atomicAdd(a.den + S.row_gid[tid], S.row_den[tid]);
+    if (!a.store_mode && tid < nrows) {
+        // beta partial of row tid: the sum of its W terms over the 256 pixels
+        float sden = 0.f;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const uint8_t* row = S.W[t] + tid * 128;
+#pragma unroll 4
+            for (int ka = 0; ka < 4; ++ka) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const uint4 v4 = *reinterpret_cast<const uint4*>(row + ka * (kTcRows * 128) + c * 16);
+                    const uint32_t wv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        sden += __uint_as_float(wv[e] << 16);
+                        sden += __uint_as_float(wv[e] & 0xffff0000u);
+                    }
+                }
+            }
+        }
+        atomicAdd(a.den + S.row_gid[tid], sden);
+    }
     tc_fence_before();
+    __syncthreads();
+    // the MMA has read the W tiles: clear them for the next rows
+    for (int t = 0; t < NT; ++t) {
+        uint4* w4 = reinterpret_cast<uint4*>(S.W[t]);
+        for (int e = tid; e < (int)(kWBytes / 16); e += kTcThreads) w4[e] = make_uint4(0u, 0u, 0u, 0u);
+    }
     __syncthreads();
 }
 
@@ -222,6 +247,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
 
     uint32_t fcount = 0, mma_phase = 0;
+    for (int t = 0; t < NT; ++t) {
+        uint4* w4 = reinterpret_cast<uint4*>(S.W[t]);
+        for (int e = tid; e < (int)(kWBytes / 16); e += kTcThreads) w4[e] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncthreads();
 
     if (a.store_mode) {
         // debug GEMM: W rows come from a.list reinterpreted as bf16 [128][256]
@@ -290,8 +320,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     pra = rec_a[pg];
                     prb = rec_b[pg];
                 }
-                uint32_t rel;
-                {
+                // Gaussians of the batch that can reach this warp's pixel block
+                const bool warp_active = __any_sync(0xffffffffu, !done);
+                uint32_t lm = 0u;   // this lane's non-zero weights (bit j = Gaussian j)
+                float w[kTcBatch];
+#pragma unroll
+                for (int j = 0; j < kTcBatch; ++j) w[j] = 0.f;
+                if (warp_active) {
                     bool rr = false;
                     if (lane < cnt) {
                         const float4 ra = S.ra[buf][lane];
@@ -305,54 +340,43 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         R.cb2 = __fmul_rn(2.0f, ra.w);
                         rr = reaches_rect(R, ra.x, ra.y, ra.z, ra.w, rb.x, bxa, bxa + 7.0f, bya, bya + 3.0f);
                     }
-                    rel = __ballot_sync(0xffffffffu, rr);
-                    if (!__any_sync(0xffffffffu, !done)) rel = 0u;
-                }
-                float w[kTcBatch];
+                    const uint32_t rel = __ballot_sync(0xffffffffu, rr);
+                    // alphas first (independent chains), then the transmittance recursion
 #pragma unroll
-                for (int j = 0; j < kTcBatch; ++j) {
-                    w[j] = 0.f;
-                    if (((rel >> j) & 1u) && !done) {
-                        const float4 ra = S.ra[buf][j];
-                        const float2 rb = S.rb[buf][j];
-                        const float al = alpha_at(ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, pxf, pyf);
-                        if (al > 0.f) {
+                    for (int j = 0; j < kTcBatch; ++j) {
+                        if ((rel >> j) & 1u) {
+                            const float4 ra = S.ra[buf][j];
+                            const float2 rb = S.rb[buf][j];
+                            w[j] = alpha_at(ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, pxf, pyf);
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < kTcBatch; ++j) {
+                        const float al = w[j];
+                        w[j] = 0.f;
+                        if (al > 0.f && !done) {
                             const float Tn = __fmul_rn(T, __fsub_rn(1.0f, al));
                             if (Tn < kTransMin) {
                                 done = true;
                             } else {
                                 w[j] = __fmul_rn(al, T);
                                 T = Tn;
+                                lm |= 1u << j;
                             }
                         }
                     }
+                    const uint32_t mine = __reduce_or_sync(0xffffffffu, lm);
+                    if (lane == 0 && mine) atomicOr(&S.rowmask[buf], mine);
                 }
-                // Gaussians with a non-zero weight somewhere in the tile and their
-                // per-warp sums of the W terms (beta uses the same rounded weights)
-                uint32_t mine = 0u;
-#pragma unroll
-                for (int j = 0; j < kTcBatch; ++j) {
-                    const uint32_t m = __ballot_sync(0xffffffffu, w[j] != 0.f);
-                    float sj = 0.f;
-                    if (m) {
-                        mine |= 1u << j;
-                        const __nv_bfloat16 h1 = __float2bfloat16_rn(w[j]);
-                        sj = __bfloat162float(h1);
-                        if (NT == 2) sj += __bfloat162float(__float2bfloat16_rn(w[j] - __bfloat162float(h1)));
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o);
-                    }
-                    if (lane == 0) S.denpart[warp][j] = sj;
-                }
-                if (lane == 0 && mine) atomicOr(&S.rowmask[buf], mine);
                 if (tid == 0) S.rowmask[buf ^ 1] = 0u;
                 __syncthreads();
                 const uint32_t rowmask = S.rowmask[buf];
                 const int nnew = __popc(rowmask);
-                if (nnew) {
+                if (lm) {
+                    // only non-zero weights are written: the W tiles are cleared after each flush
 #pragma unroll
                     for (int j = 0; j < kTcBatch; ++j) {
-                        if ((rowmask >> j) & 1u) {
+                        if ((lm >> j) & 1u) {
                             const int slot = nrows + __popc(rowmask & ((1u << j) - 1u));
                             const uint32_t o = w_offset(slot, pix);
                             const __nv_bfloat16 h1 = __float2bfloat16_rn(w[j]);
@@ -362,16 +386,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                     __float2bfloat16_rn(w[j] - __bfloat162float(h1));
                         }
                     }
-                    if (tid < kTcBatch && ((rowmask >> tid) & 1u)) {
-                        const int slot = nrows + __popc(rowmask & lt_mask);
-                        float s = 0.f;
-#pragma unroll
-                        for (int wi = 0; wi < 8; ++wi) s += S.denpart[wi][tid];
-                        S.row_gid[slot] = S.gid[buf][tid];
-                        S.row_den[slot] = s;
-                    }
-                    nrows += nnew;
                 }
+                if (tid < kTcBatch && ((rowmask >> tid) & 1u))
+                    S.row_gid[nrows + __popc(rowmask & lt_mask)] = S.gid[buf][tid];
+                nrows += nnew;
                 if (pf) {
                     const Reach R = reach_prep(pra.z, pra.w, prb.x, prb.y);
                     S.gid[buf ^ 1][tid] = pg;
@@ -379,7 +397,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     S.rb[buf ^ 1][tid] = prb;
                     S.rr[buf ^ 1][tid] = make_float4(R.thr, R.inv_ca, R.inv_cc, R.possible ? 1.f : 0.f);
                 }
-                __syncthreads();
+                // no barrier here: the next batch's counting barrier orders these stores
             }
             if (S.abort_flag) break;
             if (nrows > 0) flush_tile<DB, NT>(S, a, &fmap1, &fmap2, nrows, fcount, mma_phase, tx, ty, v);
