@@ -107,6 +107,7 @@ struct ludvig_scene {
     cudaStream_t copy_stream = nullptr;   // host-feature uploads (created on first use)
     cudaEvent_t ev_ready[2] = {nullptr, nullptr};
     cudaEvent_t ev_free[2] = {nullptr, nullptr};
+    int64_t tc_chunk_cap = 0;             // tensor-core path: weight chunks kept in ws
     ludvig::Arena ws;
 };
 

@@ -198,6 +198,20 @@ __device__ __forceinline__ float alpha_at(float mx, float my, float ca, float cb
     return al < kAlphaMin ? 0.0f : al;
 }
 
+// alpha_at without branches (same roundings, same result), for evaluating
+// several Gaussians side by side.
+__device__ __forceinline__ float alpha_at_nb(float mx, float my, float ca, float cb, float cc, float op,
+                                             float pxf, float pyf) {
+    const float dx = __fsub_rn(mx, pxf), dy = __fsub_rn(my, pyf);
+    const float pw = __fsub_rn(
+        __fmul_rn(-0.5f, __fadd_rn(__fmul_rn(ca, __fmul_rn(dx, dx)), __fmul_rn(cc, __fmul_rn(dy, dy)))),
+        __fmul_rn(cb, __fmul_rn(dx, dy)));
+    float al = __fmul_rn(op, exp_neg(pw > 0.0f ? 0.0f : pw));
+    al = al > kAlphaMax ? kAlphaMax : al;
+    al = al < kAlphaMin ? 0.0f : al;
+    return pw > 0.0f ? 0.0f : al;
+}
+
 // Conservative test: can a projected Gaussian reach alpha >= 1/255 at some
 // pixel centre of the rectangle [xa, xb] x [ya, yb]?  It can only if
 //   Q_min = min over the rectangle of  a dx^2 + 2 b dx dy + c dy^2  <=  2 ln(255 o)
@@ -245,5 +259,40 @@ __device__ __forceinline__ bool reaches_rect(float mx, float my, float ca, float
                                              float xa, float xb, float ya, float yb) {
     return reaches_rect(reach_prep(ca, cb, cc, op), mx, my, ca, cb, cc, xa, xb, ya, yb);
 }
+
+// The compositing kernels give each warp the 8x4 pixel block w of a 16x16
+// tile, at offset ((w & 1) * 8, (w >> 1) * 4).  Bit w of block_mask is set
+// when the Gaussian can reach alpha >= 1/255 somewhere in block w.
+__device__ __forceinline__ float block_x0(int tx, int w) { return (float)(tx * kTile + (w & 1) * 8) + 0.5f; }
+__device__ __forceinline__ float block_y0(int ty, int w) { return (float)(ty * kTile + (w >> 1) * 4) + 0.5f; }
+
+__device__ __forceinline__ uint32_t block_mask(const Reach& R, float mx, float my, float ca, float cb, float cc,
+                                               int tx, int ty) {
+    uint32_t m = 0u;
+#pragma unroll 1
+    for (int w = 0; w < 8; ++w) {
+        const float xa = block_x0(tx, w), ya = block_y0(ty, w);
+        if (reaches_rect(R, mx, my, ca, cb, cc, xa, xa + 7.0f, ya, ya + 3.0f)) m |= 1u << w;
+    }
+    return m;
+}
+
+// A (Gaussian, tile) pair is kept when the Gaussian can reach alpha >= 1/255
+// at some pixel centre of the tile; a Gaussian that cannot is skipped at every
+// pixel of the tile, so leaving it out of the tile's list changes no weight.
+__device__ __forceinline__ bool tile_used(const Reach& R, float mx, float my, float ca, float cb, float cc, int tx,
+                                          int ty) {
+    const float xa = (float)(tx * kTile) + 0.5f, ya = (float)(ty * kTile) + 0.5f;
+    return reaches_rect(R, mx, my, ca, cb, cc, xa, xa + 15.0f, ya, ya + 15.0f);
+}
+
+// One entry of a tile's depth-ordered list as the compositing kernels read it:
+// the projected Gaussian (mean, conic, opacity), its index and its block mask.
+struct __align__(16) PairRec {
+    float mx, my, ca, cb;
+    float cc, op;
+    uint32_t gid, mask;
+};
+static_assert(sizeof(PairRec) == 32, "PairRec is 32 bytes");
 
 }  // namespace ludvig

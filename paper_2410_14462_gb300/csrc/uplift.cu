@@ -11,7 +11,9 @@
 //                  (view*tiles + tile, index) pair per touched tile
 //   4. tile sort   stable radix sort of the pairs by (view, tile): every
 //                  tile's list stays in (depth, index) order
-//   5. ranges      [start, end) of every (view, tile) list
+//   5. ranges      [start, end) of every (view, tile) list, and the lists
+//                  rewritten as 32-byte records (projected Gaussian, index,
+//                  8x4 block mask) that the compositing kernels stream
 //   6. composite + aggregate, one CTA (256 threads = 16x16 pixels) per
 //                  (view, tile): walk the list in batches of 32 Gaussians,
 //                  form w = alpha T per pixel, keep the non-zero weights of
@@ -33,9 +35,9 @@ constexpr int kMaxViews = 16;
 
 bool tc_supported(int dtype, int d);
 bool option_f32_tensor_cores();
-ludvig_status composite_tc(const float4* rec_a, const float2* rec_b, int64_t n, const uint2* ranges,
-                           const uint32_t* list, int nv, int width, int height, const void* feats, int dtype, int d,
-                           float* num, float* den, Arena& ws, int* status, cudaStream_t st);
+ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, int width, int height,
+                           const void* feats, int dtype, int d, float* num, float* den, Arena& ws, int* status,
+                           int64_t* chunk_cap, cudaStream_t st);
 
 struct CamBatch {
     Cam cam[kMaxViews];
@@ -67,15 +69,6 @@ __global__ void k_scene_init(const float* __restrict__ means, const float* __res
     means_copy[3 * i] = m[0];
     means_copy[3 * i + 1] = m[1];
     means_copy[3 * i + 2] = m[2];
-}
-
-// Whether the Gaussian's alpha >= 1/255 region can reach a pixel centre of
-// tile (tx, ty); a Gaussian that cannot is skipped at every pixel of the tile,
-// so leaving it out of the tile's list changes no weight.
-__device__ __forceinline__ bool tile_reached(const Reach& R, float mx, float my, float ca, float cb, float cc,
-                                             int tx, int ty) {
-    const float xa = (float)(tx * kTile) + 0.5f, ya = (float)(ty * kTile) + 0.5f;
-    return reaches_rect(R, mx, my, ca, cb, cc, xa, xa + 15.0f, ya, ya + 15.0f);
 }
 
 // ------------------------------------------------------------ 1. project
@@ -111,11 +104,11 @@ __global__ void k_project(const float4* __restrict__ geo, const float4* __restri
     uint32_t count = 0;
     if (P.visible) {
         if (prune) {
-            // only tiles that the alpha >= 1/255 ellipse can reach
+            // only tiles (and 8x4 blocks) that the alpha >= 1/255 ellipse can reach
             const Reach R = reach_prep(P.ca, P.cb, P.cc, g.w);
             for (int ty = P.y0; ty < P.y1; ++ty)
                 for (int tx = P.x0; tx < P.x1; ++tx)
-                    count += tile_reached(R, P.mx, P.my, P.ca, P.cb, P.cc, tx, ty) ? 1u : 0u;
+                    count += tile_used(R, P.mx, P.my, P.ca, P.cb, P.cc, tx, ty) ? 1u : 0u;
         } else {
             count = (uint32_t)((P.x1 - P.x0) * (P.y1 - P.y0));
         }
@@ -171,7 +164,7 @@ __global__ void k_emit_pairs(const uint32_t* __restrict__ svals, const uint32_t*
     const uint32_t base = (uint32_t)(v * ntiles);
     for (int ty = y0; ty < y1 && o < end; ++ty)
         for (int tx = x0; tx < x1 && o < end; ++tx) {
-            if (prune && !tile_reached(R, ra.x, ra.y, ra.z, ra.w, rb.x, tx, ty)) continue;
+            if (prune && !tile_used(R, ra.x, ra.y, ra.z, ra.w, rb.x, tx, ty)) continue;
             pkey[o] = base + (uint32_t)(ty * TX + tx);
             pval[o] = i;
             ++o;
@@ -198,6 +191,30 @@ __global__ void k_ranges(const uint32_t* __restrict__ pkey, int64_t P, uint32_t 
     if (j == P - 1 || pkey[j + 1] != k) ranges[k].y = (uint32_t)(j + 1);
 }
 
+// The sorted lists as the compositing kernels stream them: one 32-byte record
+// per entry, in list order, with the entry's 8x4 block mask.
+__global__ void k_pair_records(const uint32_t* __restrict__ pkey, const uint32_t* __restrict__ pval, int64_t P,
+                               int ntiles, int TX, int64_t n, const float4* __restrict__ rec_a,
+                               const float2* __restrict__ rec_b, PairRec* __restrict__ out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P) return;
+    const uint32_t key = pkey[j], g = pval[j];
+    const uint32_t v = key / (uint32_t)ntiles, tile = key - v * (uint32_t)ntiles;
+    const int tx = (int)(tile % (uint32_t)TX), ty = (int)(tile / (uint32_t)TX);
+    const float4 ra = rec_a[(int64_t)v * n + g];
+    const float2 rb = rec_b[(int64_t)v * n + g];
+    PairRec r;
+    r.mx = ra.x;
+    r.my = ra.y;
+    r.ca = ra.z;
+    r.cb = ra.w;
+    r.cc = rb.x;
+    r.op = rb.y;
+    r.gid = g;
+    r.mask = block_mask(reach_prep(ra.z, ra.w, rb.x, rb.y), ra.x, ra.y, ra.z, ra.w, rb.x, tx, ty);
+    out[j] = r;
+}
+
 // ------------------------------------------------------------ 6. composite + aggregate
 constexpr int kBatch = 32;        // Gaussians composited per step
 constexpr int kStoreCap = 12288;  // non-zero weights kept per flush
@@ -214,11 +231,8 @@ __device__ __forceinline__ float to_f32(float x) { return x; }
 __device__ __forceinline__ float to_f32(__nv_bfloat16 x) { return __bfloat162float(x); }
 
 struct CompositeArgs {
-    const float4* rec_a;
-    const float2* rec_b;
-    int64_t n;
+    const PairRec* pairs;   // list records in list order
     const uint2* ranges;
-    const uint32_t* list;
     int ntiles, TX, width, height;
     const void* feats;      // chunk's first view
     int d;
@@ -232,6 +246,7 @@ struct CompositeSmem {
     float4 ra[kBatch];
     float2 rb[kBatch];
     uint32_t gid[kBatch];
+    uint32_t bmask[kBatch];
     uint32_t wcnt[8][kBatch];
     uint32_t rtot[kBatch];
     uint32_t rbase[kBatch];
@@ -326,15 +341,15 @@ __global__ void __launch_bounds__(256, 2) k_composite(CompositeArgs a) {
     const int px = tx * kTile + lx, py = ty * kTile + ly;
     const bool inside = px < a.width && py < a.height;
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
-    const float bxa = (float)(tx * kTile + bx) + 0.5f, bya = (float)(ty * kTile + by) + 0.5f;
     const uint2 range = a.ranges[item];
     const TIn* fv = reinterpret_cast<const TIn*>(a.feats) + (int64_t)v * a.height * a.width * a.d;
-    const float4* rec_a = a.rec_a + (int64_t)v * a.n;
-    const float2* rec_b = a.rec_b + (int64_t)v * a.n;
     if (tid == 0) {
         sm.nstore = 0;
         sm.nrows = 0;
     }
+    // records of the next batch, loaded one batch ahead
+    PairRec nxt{};
+    if (tid < kBatch && range.x + tid < range.y) nxt = a.pairs[range.x + tid];
     float T = 1.0f;
     bool done = !inside;
     int ncontrib = 0;
@@ -345,24 +360,16 @@ __global__ void __launch_bounds__(256, 2) k_composite(CompositeArgs a) {
         if (sm.nstore + kBatch * 256 > kStoreCap || sm.nrows + kBatch > kRowCap)
             flush_store<TIn, kVec>(sm, a, fv, tx, ty);
         if (tid < cnt) {
-            const uint32_t g = a.list[b0 + tid];
-            sm.gid[tid] = g;
-            sm.ra[tid] = rec_a[g];
-            sm.rb[tid] = rec_b[g];
+            sm.gid[tid] = nxt.gid;
+            sm.bmask[tid] = nxt.mask;
+            sm.ra[tid] = make_float4(nxt.mx, nxt.my, nxt.ca, nxt.cb);
+            sm.rb[tid] = make_float2(nxt.cc, nxt.op);
         }
+        if (tid < kBatch && b0 + kBatch + tid < range.y) nxt = a.pairs[b0 + kBatch + tid];
         __syncthreads();
         // Gaussians of the batch that can reach this warp's pixel block
-        uint32_t rel;
-        {
-            bool r = false;
-            if (lane < cnt) {
-                const float4 ra = sm.ra[lane];
-                const float2 rb = sm.rb[lane];
-                r = reaches_rect(ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, bxa, bxa + 7.0f, bya, bya + 3.0f);
-            }
-            rel = __ballot_sync(0xffffffffu, r);
-            if (!__any_sync(0xffffffffu, !done)) rel = 0u;
-        }
+        uint32_t rel = __ballot_sync(0xffffffffu, lane < cnt && ((sm.bmask[lane] >> warp) & 1u));
+        if (!__any_sync(0xffffffffu, !done)) rel = 0u;
         // alphas of the batch first (independent chains the scheduler can
         // overlap), then the sequential transmittance recursion
         float w[kBatch];
@@ -624,12 +631,18 @@ ludvig_status run_chunk(ludvig_scene* s, const ludvig_camera* cams, int nv, int 
     }
     if (dbg && dbg->stop_after_sort) return LUDVIG_OK;
 
+    PairRec* pairs;
+    LV_TRY(ws.get("up.pairs", (size_t)std::max<int64_t>(P, 1), &pairs));
+    tslot = trace_on() ? trace_begin(LUDVIG_STAGE_TILE_SORT, st) : -1;
+    if (P > 0) {
+        k_pair_records<<<grid_for(P, 256), 256, 0, st>>>(spk, spv, P, ntiles, TX, n, rec_a, rec_b, pairs);
+        LV_LAUNCH();
+    }
+    trace_end(tslot, st);
+
     CompositeArgs args;
-    args.rec_a = rec_a;
-    args.rec_b = rec_b;
-    args.n = n;
+    args.pairs = pairs;
     args.ranges = ranges;
-    args.list = spv;
     args.ntiles = ntiles;
     args.TX = TX;
     args.width = width;
@@ -646,8 +659,8 @@ ludvig_status run_chunk(ludvig_scene* s, const ludvig_camera* cams, int nv, int 
     if (use_tensor_cores(dtype, d)) {
         int* status;
         LV_TRY(ws.get("tc.status", 1, &status));
-        return composite_tc(rec_a, rec_b, n, ranges, spv, nv, width, height, feats, dtype, d, num, den, ws, status,
-                            st);
+        return composite_tc(pairs, ranges, nv, width, height, feats, dtype, d, num, den, ws, status,
+                            &s->tc_chunk_cap, st);
     }
     if (dtype == LUDVIG_F32) {
         if (vec) return launch_composite<float, true>(args, nitems, st);
