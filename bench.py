@@ -174,6 +174,25 @@ def cpu_baseline(wl):
             "sample": f"uplift of view 0 of {wl.cams.v} (D={wl.d}, N={wl.scene.n}), {dt:.1f} s"}
 
 
+def roofline(tr, steps, alg_bytes_step):
+    """HBM roofline of the kernel that reads the features: the tensor-core
+    aggregation (k_aggregate_tc) when it ran, else the CUDA-core composite.
+    Algorithmic bytes per step: the features once, 44 B per Gaussian, and
+    num/den once (4 N (D + 1)); per launch, that over the launches of a step
+    (one per chunk of up to 16 views).  Time: CUDA events around each launch
+    on the stream it runs on."""
+    stage = "aggregate" if tr["calls"].get("aggregate", 0) > 0 else "composite"
+    kernel = "k_aggregate_tc" if stage == "aggregate" else "k_composite"
+    launch_ms = tr["ms"][stage] / max(1, tr["calls"][stage])
+    launches = tr["calls"][stage] / steps
+    alg_per_launch = alg_bytes_step / max(1.0, launches)
+    peak, peak_kind = peaks()
+    achieved = alg_per_launch / (launch_ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+            "alg_bytes_per_launch": alg_per_launch, "launch_ms": launch_ms}
+
+
 def precision_form(sc, wl):
     """bfloat16 features with D=512 on the same scene and cameras (tensor-core
     aggregation), timed over the full uplift; its error is stated against the
@@ -209,19 +228,14 @@ def precision_form(sc, wl):
     torch.cuda.synchronize()
     pos = b32 > 0
     err = float((obf[pos] - o32[pos]).norm() / o32[pos].norm())
-    comp_ms = tr["ms"]["composite"] / max(1, tr["calls"]["composite"])
-    launches = tr["calls"]["composite"] / reps
-    alg = V * H * W * D * 2 + sc.n * 44 + sc.n * (D + 1) * 4
-    peak, kind = peaks()
-    achieved = alg / max(1.0, launches) / (comp_ms / 1e3) / 1e9
+    roof = roofline(tr, reps, V * H * W * D * 2 + sc.n * 44 + sc.n * (D + 1) * 4)
     del fb, f32
     torch.cuda.empty_cache()
     return {"value": V * D / (ms / 1e3), "unit": UNIT, "ms_per_uplift": ms, "dtype": "bf16",
             "config": {"workload": wl.name.replace("-d384", "-d512"), "d": D, "step": "uplift only",
                        "aggregation": "tcgen05 kind::f16, bf16 weights, fp32 accumulation"},
             "rel_l2_vs_f32_path": err, "err_views": nv,
-            "roofline": {"bound": "hbm", "kernel": "k_composite_tc", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "peak_kind": kind},
+            "roofline": roof,
             "stages_ms_per_uplift": {k: v / reps for k, v in tr["ms"].items() if v > 0}}
 
 
@@ -292,16 +306,7 @@ def run_ours(args):
         ms = float(t.item())
     value = world * V * D / (ms / 1e3)
 
-    # roofline of the dominant kernel (composite + aggregate)
-    peak, peak_kind = peaks()
-    comp_ms = tr["ms"]["composite"] / max(1, tr["calls"]["composite"])
-    launches_per_step = tr["calls"]["composite"] / args.steps
-    alg_bytes_step = V * H * W * D * esize + sc.n * 44 + sc.n * (D + 1) * 4
-    alg_per_launch = alg_bytes_step / max(1.0, launches_per_step)
-    achieved = alg_per_launch / (comp_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": "k_composite", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-            "alg_bytes_per_launch": alg_per_launch, "launch_ms": comp_ms}
+    roof = roofline(tr, args.steps, V * H * W * D * esize + sc.n * 44 + sc.n * (D + 1) * 4)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

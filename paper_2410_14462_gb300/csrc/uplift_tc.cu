@@ -665,6 +665,7 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
         void *hi, *lo;
         LV_TRY(ws.get("tc.f_hi", (size_t)count * 2, &hi));
         LV_TRY(ws.get("tc.f_lo", (size_t)count * 2, &lo));
+        StageScope split_scope(LUDVIG_STAGE_SPLIT, st);
         k_split_f32<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, ceil_div(count / 4, 256))), 256,
                       0, st>>>(static_cast<const float4*>(feats), static_cast<uint2*>(hi), static_cast<uint2*>(lo),
                                count / 4);
@@ -711,11 +712,13 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
         w.chunk_counter = counter;
         w.cap = (int)cap;
         w.status = status;
+        const int tslot = trace_on() ? trace_begin(LUDVIG_STAGE_WEIGHTS, st) : -1;
         if (NT == 2)
             k_weights<2><<<nitems, 256, 0, st>>>(w);
         else
             k_weights<1><<<nitems, 256, 0, st>>>(w);
         LV_LAUNCH();
+        trace_end(tslot, st);
         LV_CUDA(cudaMemcpyAsync(host, counter, sizeof(int), cudaMemcpyDeviceToHost, st));
         LV_CUDA(cudaMemcpyAsync(host + 1, status, sizeof(int), cudaMemcpyDeviceToHost, st));
         LV_CUDA(cudaStreamSynchronize(st));
@@ -753,6 +756,7 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
     g.status = status;
     g.store_mode = 0;
     const int grid = std::min(sms, count);
+    StageScope agg_scope(LUDVIG_STAGE_AGGREGATE, st);
     if (NT == 2) return dispatch_agg<2>(g, maps, grid, st);
     return dispatch_agg<1>(g, maps, grid, st);
 }

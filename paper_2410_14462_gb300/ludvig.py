@@ -219,7 +219,8 @@ def get_option(option: int) -> int:
     return int(load().ludvig_get_option(option))
 
 
-STAGES = ["project", "depth_sort", "bin", "tile_sort", "composite", "normalise", "knn", "graph", "diffuse"]
+STAGES = ["project", "depth_sort", "bin", "tile_sort", "composite", "normalise", "knn", "graph", "diffuse",
+          "split", "weights", "aggregate"]
 
 
 class TraceStruct(ctypes.Structure):
