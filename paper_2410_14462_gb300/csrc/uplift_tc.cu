@@ -19,10 +19,11 @@
 //  ahead.  The batch's weights go to 32 staging rows in shared memory; the
 //  Gaussians with a non-zero weight somewhere in the tile are then appended,
 //  as dense bfloat16 rows of 256 pixels, to the tile's "chunks" of 128 rows in
-//  global memory (chunk ids from an atomic counter; tile, row count and
-//  Gaussian ids recorded per chunk).
+//  global memory (chunk ids from an atomic counter; row count, Gaussian ids
+//  and the tile's next chunk recorded per chunk, the first chunk per tile).
 //
-//  k_aggregate_tc (one persistent CTA per SM, warp-specialised):
+//  k_aggregate_tc (one persistent CTA per SM, warp-specialised, tiles taken
+//  round-robin with each tile's chunks back to back):
 //    warp 0     TMA producer: the chunk's W rows (4 x 16 KB per term, 128-byte
 //               swizzle, K-major) and the tile's feature blocks (256 pixels x
 //               64 channels, MN-major) into rings of stages;
@@ -79,8 +80,9 @@ struct WeightsArgs {
     uint8_t* wg1;           // [cap][128][256] bfloat16: W (NT = 1) or W1
     uint8_t* wg2;           // W2 (NT = 2)
     uint32_t* chunk_gid;    // [cap][128]
-    int* chunk_item;        // [cap]
     int* chunk_rows;        // [cap]
+    int* chunk_next;        // [cap]: the tile's next chunk, or -1
+    int* item_first;        // [nitems]: the tile's first chunk, or -1 (set to -1 before the launch)
     int* chunk_counter;
     int cap;
     int* status;
@@ -96,10 +98,10 @@ struct WeightsSmem {
     int abort_flag;
 };
 
-__device__ __forceinline__ void finish_chunk(const WeightsArgs& a, int c, int rows, int item) {
+__device__ __forceinline__ void finish_chunk(const WeightsArgs& a, int c, int rows, int next) {
     if (c >= 0 && c < a.cap) {
         a.chunk_rows[c] = rows;
-        a.chunk_item[c] = item;
+        a.chunk_next[c] = next;
     }
 }
 
@@ -163,14 +165,19 @@ __global__ void __launch_bounds__(256, 4) k_weights(WeightsArgs a) {
         // every thread is past batch k-1: its slot takes batch k + kRing - 1
         if (k + kRing - 1 < nb) issue_records(k + kRing - 1);
         if (tid == 0) {
-            // rows [nrows, nrows + 32) must have chunks
+            // rows [nrows, nrows + 32) must have chunks; a chunk filled to
+            // exactly 128 rows may not have its successor yet
             if (nrows >= S.cur_start + kCRows) {
-                finish_chunk(a, S.cur_chunk, kCRows, item);
+                if (S.next_chunk < 0) S.next_chunk = atomicAdd(a.chunk_counter, 1);
+                finish_chunk(a, S.cur_chunk, kCRows, S.next_chunk);
                 S.cur_chunk = S.next_chunk;
                 S.cur_start += kCRows;
                 S.next_chunk = -1;
             }
-            if (S.cur_chunk < 0) S.cur_chunk = atomicAdd(a.chunk_counter, 1);
+            if (S.cur_chunk < 0) {
+                S.cur_chunk = atomicAdd(a.chunk_counter, 1);
+                a.item_first[item] = S.cur_chunk;
+            }
             if (nrows + kTcBatch > S.cur_start + kCRows && S.next_chunk < 0)
                 S.next_chunk = atomicAdd(a.chunk_counter, 1);
         }
@@ -261,26 +268,26 @@ __global__ void __launch_bounds__(256, 4) k_weights(WeightsArgs a) {
         if (!mbar_wait(&S.rec_full[k % kRing], (k / kRing) & 1u)) break;
     __syncthreads();
     if (tid == 0) {
-        if (S.cur_chunk >= 0 && nrows >= S.cur_start + kCRows) {
-            finish_chunk(a, S.cur_chunk, kCRows, item);
-            S.cur_chunk = S.next_chunk;
-            S.cur_start += kCRows;
-            S.next_chunk = -1;
+        const int cur = S.cur_chunk, cstart = S.cur_start, nxt = S.next_chunk;
+        if (nrows > cstart + kCRows) {   // the last batch spilled into nxt
+            finish_chunk(a, cur, kCRows, nxt);
+            finish_chunk(a, nxt, nrows - cstart - kCRows, -1);
+        } else {
+            finish_chunk(a, cur, nrows - cstart, -1);
+            finish_chunk(a, nxt, 0, -1);   // allocated, never used
         }
-        finish_chunk(a, S.cur_chunk, nrows - S.cur_start, item);
-        finish_chunk(a, S.next_chunk, 0, item);
     }
 }
 
 // ------------------------------------------------------------ aggregation
 
 struct AggArgs {
-    const int* chunk_counter;
     int cap;
-    const int* chunk_item;
     const int* chunk_rows;
+    const int* chunk_next;
+    const int* item_first;
     const uint32_t* chunk_gid;
-    int ntiles, TX, d;
+    int nitems, ntiles, TX, d;
     float* num;
     float* den;
     int* status;
@@ -305,6 +312,27 @@ template <int NT>
 constexpr size_t agg_smem_bytes() {
     return sizeof(AggSmem<NT>) + 1024;   // + alignment slack
 }
+
+// The chunks a CTA aggregates: those of tiles blockIdx.x, blockIdx.x + gridDim.x,
+// ... in order, each tile's chunks back to back (so its feature blocks are
+// still in L2 for the second chunk).  Every role walks the same sequence.
+struct ChunkWalk {
+    int item, c;
+    __device__ ChunkWalk() : item((int)blockIdx.x - (int)gridDim.x), c(-1) {}
+    // next non-empty chunk (its tile in item), or -1 at the end
+    __device__ int next(const AggArgs& a) {
+        for (;;) {
+            if (c >= 0) c = a.chunk_next[c];
+            while (c < 0) {
+                item += gridDim.x;
+                if (item >= a.nitems) return -1;
+                c = a.item_first[item];
+            }
+            if (c >= a.cap) return -1;   // never with a complete weights pass
+            if (a.chunk_rows[c] > 0) return c;
+        }
+    }
+};
 
 __device__ __forceinline__ bool agg_wait(volatile int* abort_flag, int* status, uint64_t* bar, uint32_t parity) {
     if (mbar_wait(bar, parity)) return true;
@@ -344,15 +372,14 @@ __global__ void __launch_bounds__(kAggThreads, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const int nchunks = min(*a.chunk_counter, a.cap);
 
     if (warp == 0) {
         if (lane == 0) {
             // ---- TMA producer
             uint32_t wc = 0, fc = 0;
-            for (int c = blockIdx.x; c < nchunks && !*abort_flag; c += gridDim.x) {
-                if (a.chunk_rows[c] <= 0) continue;
-                const int item = a.chunk_item[c];
+            ChunkWalk walk;
+            for (int c = walk.next(a); c >= 0 && !*abort_flag; c = walk.next(a)) {
+                const int item = walk.item;
                 const int v = item / a.ntiles, tile = item - v * a.ntiles;
                 const int tx = tile % a.TX, ty = tile / a.TX;
                 const uint32_t ws = wc % Sm::kWS;
@@ -394,8 +421,8 @@ __global__ void __launch_bounds__(kAggThreads, 1)
             // ---- MMA issuer
             uint32_t wc = 0, fc = 0, uc = 0;
             bool ok = true;
-            for (int c = blockIdx.x; c < nchunks && ok && !*abort_flag; c += gridDim.x) {
-                if (a.chunk_rows[c] <= 0) continue;
+            ChunkWalk walk;
+            for (int c = walk.next(a); c >= 0 && ok && !*abort_flag; c = walk.next(a)) {
                 const uint32_t ws = wc % Sm::kWS;
                 if (!agg_wait(abort_flag, a.status, &S.w_full[ws], (wc / Sm::kWS) & 1u)) break;
                 tc_fence_after();
@@ -446,9 +473,9 @@ __global__ void __launch_bounds__(kAggThreads, 1)
         const int r = 32 * q + lane;
         const int d = a.d;
         uint32_t wc = 0, uc = 0;
-        for (int c = blockIdx.x; c < nchunks && !*abort_flag; c += gridDim.x) {
+        ChunkWalk walk;
+        for (int c = walk.next(a); c >= 0 && !*abort_flag; c = walk.next(a)) {
             const int rows = a.chunk_rows[c];
-            if (rows <= 0) continue;
             const bool valid = r < rows;
             const uint32_t g = valid ? a.chunk_gid[(size_t)c * kCRows + r] : 0u;
             const uint32_t ws = wc % Sm::kWS;
@@ -685,7 +712,8 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
     int count = 0;
     uint8_t *wg1 = nullptr, *wg2 = nullptr;
     uint32_t* cgid = nullptr;
-    int *citem = nullptr, *crows = nullptr;
+    int *crows = nullptr, *cnext = nullptr, *ifirst = nullptr;
+    LV_TRY(ws.get("tc.item_first", (size_t)nitems, &ifirst));
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (cap > 0x7fffffff / kCRows) {
             set_error("tile weights need %lld chunks of 128 rows", (long long)cap);
@@ -694,9 +722,10 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
         LV_TRY(ws.get("tc.w1", (size_t)cap * kChunkBytes, &wg1));
         if (NT == 2) LV_TRY(ws.get("tc.w2", (size_t)cap * kChunkBytes, &wg2));
         LV_TRY(ws.get("tc.chunk_gid", (size_t)cap * kCRows, &cgid));
-        LV_TRY(ws.get("tc.chunk_item", (size_t)cap, &citem));
         LV_TRY(ws.get("tc.chunk_rows", (size_t)cap, &crows));
+        LV_TRY(ws.get("tc.chunk_next", (size_t)cap, &cnext));
         LV_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
+        LV_CUDA(cudaMemsetAsync(ifirst, 0xff, sizeof(int) * (size_t)nitems, st));
         WeightsArgs w{};
         w.pairs = pairs;
         w.ranges = ranges;
@@ -707,8 +736,9 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
         w.wg1 = wg1;
         w.wg2 = NT == 2 ? wg2 : wg1;
         w.chunk_gid = cgid;
-        w.chunk_item = citem;
         w.chunk_rows = crows;
+        w.chunk_next = cnext;
+        w.item_first = ifirst;
         w.chunk_counter = counter;
         w.cap = (int)cap;
         w.status = status;
@@ -743,11 +773,12 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
     LV_TRY(make_feature_map(&maps[2], f1, nv, width, height, d));
     LV_TRY(make_feature_map(&maps[3], f2, nv, width, height, d));
     AggArgs g{};
-    g.chunk_counter = counter;
     g.cap = (int)cap;
-    g.chunk_item = citem;
     g.chunk_rows = crows;
+    g.chunk_next = cnext;
+    g.item_first = ifirst;
     g.chunk_gid = cgid;
+    g.nitems = nitems;
     g.ntiles = TX * TY;
     g.TX = TX;
     g.d = d;
@@ -755,7 +786,7 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
     g.den = den;
     g.status = status;
     g.store_mode = 0;
-    const int grid = std::min(sms, count);
+    const int grid = std::min(sms, nitems);
     StageScope agg_scope(LUDVIG_STAGE_AGGREGATE, st);
     if (NT == 2) return dispatch_agg<2>(g, maps, grid, st);
     return dispatch_agg<1>(g, maps, grid, st);
@@ -771,14 +802,14 @@ extern "C" ludvig_status ludvig_debug_mma_bf16(const void* a, const void* f, int
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // one chunk of 128 rows (row r -> output row r) over a single 16x16 tile
     struct Meta {
-        int counter, item, rows, status;
+        int first, next, rows, status;
         uint32_t gid[kCRows];
     };
     static Meta* meta = nullptr;
     if (!meta) LV_CUDA(cudaMalloc(&meta, sizeof(Meta)));
     static Meta h{};
-    h.counter = 1;
-    h.item = 0;
+    h.first = 0;
+    h.next = -1;
     h.rows = kCRows;
     h.status = 0;
     for (int r = 0; r < kCRows; ++r) h.gid[r] = (uint32_t)r;
@@ -789,11 +820,12 @@ extern "C" ludvig_status ludvig_debug_mma_bf16(const void* a, const void* f, int
     LV_TRY(make_feature_map(&maps[2], f, 1, 16, 16, d));
     maps[3] = maps[2];
     AggArgs g{};
-    g.chunk_counter = &meta->counter;
     g.cap = 1;
-    g.chunk_item = &meta->item;
     g.chunk_rows = &meta->rows;
+    g.chunk_next = &meta->next;
+    g.item_first = &meta->first;
     g.chunk_gid = meta->gid;
+    g.nitems = 1;
     g.ntiles = 1;
     g.TX = 1;
     g.d = d;
