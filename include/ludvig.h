@@ -161,10 +161,9 @@ typedef enum {
     LUDVIG_STAGE_KNN = 6,
     LUDVIG_STAGE_GRAPH = 7,       /* union edges, weights, normalisation */
     LUDVIG_STAGE_DIFFUSE = 8,
-    LUDVIG_STAGE_SPLIT = 9,       /* inside COMPOSITE: float32 features -> two bfloat16 terms */
-    LUDVIG_STAGE_WEIGHTS = 10,    /* inside COMPOSITE: tensor-core path, compositing weights */
-    LUDVIG_STAGE_AGGREGATE = 11,  /* inside COMPOSITE: tensor-core path, W F products into num/den */
-    LUDVIG_STAGE_COUNT = 12
+    LUDVIG_STAGE_WEIGHTS = 9,     /* inside COMPOSITE: tensor-core path, compositing weights */
+    LUDVIG_STAGE_AGGREGATE = 10,  /* inside COMPOSITE: tensor-core path, W F products into num/den */
+    LUDVIG_STAGE_COUNT = 11
 } ludvig_stage;
 
 typedef struct {

@@ -4,8 +4,8 @@
 // bfloat16 features (NT = 1) and float32 features (NT = 2, float32-level
 // accuracy).
 //
-// NT = 2: the float32 features are split beforehand into two bfloat16 arrays
-// F = F1 + F2 (k_split_f32) and the weights into w = W1 + W2; the product keeps
+// NT = 2: the float32 features are split into two bfloat16 terms F = F1 + F2
+// in shared memory as they arrive, and the weights into w = W1 + W2; the product keeps
 // W1 F1 + W2 F1 + W1 F2 (16 significant bits per operand, the dropped W2 F2 and
 // the residuals are below 2^-16 relative).  den sums the same W terms, so each
 // f_i stays a convex combination of the features.
@@ -23,19 +23,24 @@
 //  and the tile's next chunk recorded per chunk, the first chunk per tile).
 //
 //  k_aggregate_tc (one persistent CTA per SM, warp-specialised, tiles taken
-//  round-robin with each tile's chunks back to back):
-//    warp 0     TMA producer: the chunk's W rows (4 x 16 KB per term, 128-byte
-//               swizzle, K-major) and the tile's feature blocks (256 pixels x
-//               64 channels, MN-major) into rings of stages;
-//    warp 1     MMA issuer: tcgen05.mma kind::f16, M = 128 rows, N = 64
-//               channels, K = 256 pixels, one 64-column TMEM slot (of 8) per
-//               channel block;
-//    warps 2-5  epilogue: den from the W rows in shared memory, then each slot
-//               read back (tcgen05.ld), turned through shared memory so that
-//               a warp's vector reductions cover two 256-byte row segments
-//               each, and added into num.
-//  mbarriers hand every stage between the roles, so loads, MMAs and the
-//  epilogue of neighbouring blocks and chunks overlap.
+//  round-robin with each tile's chunks back to back).  Per chunk the K loop is
+//  outermost: for each 64-pixel K atom, the atom of the W rows (16 KB per
+//  term) and then one feature unit (64 pixels x 64 channels) per channel
+//  block, all through rings of small stages so that many loads are in flight:
+//    warp 0     TMA producer (128-byte swizzle; W K-major, features MN-major);
+//    warps 10-17 (float32 features) turn each float32 unit into F1 | F2 in
+//               place;
+//    warp 1     MMA issuer: tcgen05.mma kind::f16, M = 128 rows, N = 128
+//               channels (64 for an odd last block), 16 pixels per step; unit u
+//               of the chunk accumulates over the 4 atoms in one 128-column
+//               TMEM slot (of 4);
+//    warps 2-9  epilogue, two warps per TMEM lane quarter (one per 64-column
+//               half): den from the W atoms in shared memory, then each
+//               finished slot read back (tcgen05.ld), one row per thread staged
+//               in shared memory and added into num by the bulk-copy engine
+//               (cp.reduce.async.bulk .add.f32, 256 B per row and block).
+//  mbarriers hand every stage between the roles, so loads, conversion, MMAs
+//  and the epilogue of neighbouring blocks and chunks overlap.
 //
 // Every mbarrier wait is bounded: on expiry the kernel records
 // LUDVIG_ERR_TIMEOUT, stops taking work, waits (bounded) for what it issued,
@@ -62,14 +67,13 @@ constexpr int kCRows = 128;                            // rows per chunk (MMA M)
 constexpr int kRowBytes = 256 * 2;                     // one row: 256 pixels, bfloat16
 constexpr uint32_t kChunkBytes = kCRows * kRowBytes;   // 64 KB per term
 constexpr uint32_t kAtomBytes = kCRows * 128;          // 64-pixel K atom of a chunk: 16 KB
-constexpr uint32_t kFBlockBytes = 256 * 64 * 2;        // 32 KB: 256 pixels x 64 channels
-constexpr int kSlots = 8;                              // TMEM: 8 slots of 64 float32 columns
-constexpr int kAggThreads = 192;                       // producer, MMA, 4 epilogue warps
+constexpr int kSlots = 4;                              // TMEM: 4 slots of 128 float32 columns
 
 // kind::f16 instruction descriptor: D float32, A and B bfloat16, A K-major,
-// B MN-major, M = 128, N = 64.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((64u >> 3) << 17) |
-                            ((128u >> 4) << 24);
+// B MN-major, M = 128, N = n.
+constexpr uint32_t idesc_n(uint32_t n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
 
 // ------------------------------------------------------------ weights
 
@@ -85,6 +89,7 @@ struct WeightsArgs {
     int* item_first;        // [nitems]: the tile's first chunk, or -1 (set to -1 before the launch)
     int* chunk_counter;
     int cap;
+    float* chunk_den;       // [cap][128][NT]: each row's sum of its weight term (rewritten on a re-run)
     int* status;
 };
 
@@ -233,10 +238,12 @@ __global__ void __launch_bounds__(256, 4) k_weights(WeightsArgs a) {
         const int nnew = __popc(rowmask);
         const int cur = S.cur_chunk, nxt = S.next_chunk, cstart = S.cur_start;
         // the staging row of the i-th new Gaussian goes to tile row nrows + i
-        // (chunk cur, or nxt past its 128 rows), 16 bytes per thread; the
-        // staging row is cleared behind it
+        // (chunk cur, or nxt past its 128 rows), 16 bytes per thread, one warp
+        // per row and term; the staging row is cleared behind it, and the
+        // row's sum of the term (the bfloat16 values the product uses) is
+        // kept for den
         const int per_term = nnew * 32;
-        for (int e = tid; e < NT * per_term; e += 256) {
+        for (int e = tid; e < NT * per_term; e += 256) {   // NT * per_term % 32 == 0: whole warps
             const int t = e / per_term, rem = e - t * per_term;
             const int i = rem >> 5, c16 = rem & 31;
             const int j = (int)__fns(rowmask, 0u, i + 1);
@@ -246,11 +253,19 @@ __global__ void __launch_bounds__(256, 4) k_weights(WeightsArgs a) {
                 ch = nxt;
             }
             uint4* src = reinterpret_cast<uint4*>(&S.stage[t][j * kRowBytes + c16 * 16]);
+            const uint4 v4 = *src;
             if (ch >= 0 && ch < a.cap) {
                 uint8_t* dst = (t == 0 ? a.wg1 : a.wg2) + (size_t)ch * kChunkBytes + local * kRowBytes + c16 * 16;
-                *reinterpret_cast<uint4*>(dst) = *src;
+                *reinterpret_cast<uint4*>(dst) = v4;
             }
             *src = make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t wv[4] = {v4.x, v4.y, v4.z, v4.w};
+            float sden = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sden += __uint_as_float(wv[k] << 16) + __uint_as_float(wv[k] & 0xffff0000u);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sden += __shfl_xor_sync(0xffffffffu, sden, o);
+            if (lane == 0 && ch >= 0 && ch < a.cap) a.chunk_den[((size_t)ch * kCRows + local) * NT + t] = sden;
         }
         if (tid < kTcBatch && ((rowmask >> tid) & 1u)) {
             int local = nrows + __popc(rowmask & lt_mask) - cstart, ch = cur;
@@ -287,6 +302,7 @@ struct AggArgs {
     const int* chunk_next;
     const int* item_first;
     const uint32_t* chunk_gid;
+    const float* chunk_den;   // [cap][128][NT]
     int nitems, ntiles, TX, d;
     float* num;
     float* den;
@@ -294,15 +310,23 @@ struct AggArgs {
     int store_mode;   // debug GEMM: num[gid * d + c] = accumulator (no den)
 };
 
+// Feature units: 64 pixels (one K atom) x 128 channels, as two 64-channel
+// 128-byte-swizzled atoms 8 KB apart (the MMA's N = 128).  NT = 1: two
+// bfloat16 TMA boxes (16 KB).  NT = 2: four float32 boxes of 32 channels
+// (32 KB), turned in place into F1 (first 16 KB) and F2 (second 16 KB) by the
+// converter warps.
 template <int NT>
 struct AggSmem {
-    static constexpr int kWS = NT == 1 ? 2 : 1;   // W stages (each NT x 64 KB)
-    static constexpr int kFS = 2;                  // feature-block stages
-    uint8_t W[kWS][NT][kChunkBytes];               // offset 0 (1024-aligned)
-    uint8_t F[kFS][kFBlockBytes];
-    float4 xpose[4][32 * 16];                      // epilogue: 32 rows x 64 columns per warp
-    uint64_t w_full[kWS], w_empty[kWS];
-    uint64_t f_full[kFS], f_empty[kFS];
+    static constexpr int kWA = NT == 1 ? 4 : 2;              // W atom stages (NT x 16 KB each)
+    static constexpr uint32_t kFStage = NT * 16384u;          // one feature unit
+    static constexpr int kFS = NT == 1 ? 5 : 3;               // 80 KB or 96 KB of stages
+    static constexpr int kEH = NT == 1 ? 2 : 1;               // epilogue warps per TMEM lane quarter
+    static constexpr int kPitch = 68;                         // staged row: 64 floats + 16 B pad
+    uint8_t W[kWA][NT][kAtomBytes];                           // offset 0 (1024-aligned)
+    uint8_t F[kFS][kFStage];
+    float rows[4 * kEH][32 * kPitch];                         // epilogue: 32 rows x 64 columns per warp
+    uint64_t w_full[kWA], w_empty[kWA];
+    uint64_t f_full[kFS], f_conv[kFS], f_empty[kFS];
     uint64_t t_full[kSlots], t_empty[kSlots];
     uint32_t tmem_base;
     int abort_flag;
@@ -311,6 +335,14 @@ struct AggSmem {
 template <int NT>
 constexpr size_t agg_smem_bytes() {
     return sizeof(AggSmem<NT>) + 1024;   // + alignment slack
+}
+static_assert(agg_smem_bytes<1>() <= 232448 && agg_smem_bytes<2>() <= 232448, "shared memory");
+
+// warp 0 producer, warp 1 MMA, then 4 kEH epilogue warps (8 for NT = 1, 4 for
+// NT = 2) and, for NT = 2, 8 converter warps (6 .. 13)
+template <int NT>
+constexpr int agg_threads() {
+    return NT == 1 ? 320 : 448;
 }
 
 // The chunks a CTA aggregates: those of tiles blockIdx.x, blockIdx.x + gridDim.x,
@@ -341,10 +373,26 @@ __device__ __forceinline__ bool agg_wait(volatile int* abort_flag, int* status, 
     return false;
 }
 
+// float32 -> bfloat16 f1 = rn(x) and f2 = rn(x - f1) for 8 values (x - f1 is
+// exact in float32), packed two per word in channel order.
+__device__ __forceinline__ void split8(const float* x, uint4& f1, uint4& f2) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const __nv_bfloat162 hb = __floats2bfloat162_rn(x[2 * k], x[2 * k + 1]);
+        const float2 hf = __bfloat1622float2(hb);
+        const __nv_bfloat162 lb = __floats2bfloat162_rn(x[2 * k] - hf.x, x[2 * k + 1] - hf.y);
+        h[k] = *reinterpret_cast<const uint32_t*>(&hb);
+        l[k] = *reinterpret_cast<const uint32_t*>(&lb);
+    }
+    f1 = make_uint4(h[0], h[1], h[2], h[3]);
+    f2 = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
 template <int DB, int NT>
-__global__ void __launch_bounds__(kAggThreads, 1)
+__global__ void __launch_bounds__(agg_threads<NT>(), 1)
     k_aggregate_tc(AggArgs a, const __grid_constant__ CUtensorMap wmap1, const __grid_constant__ CUtensorMap wmap2,
-                   const __grid_constant__ CUtensorMap fmap1, const __grid_constant__ CUtensorMap fmap2) {
+                   const __grid_constant__ CUtensorMap fmap) {
     using Sm = AggSmem<NT>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const uint32_t pad = (1024u - (saddr(smem_raw) & 1023u)) & 1023u;
@@ -353,17 +401,18 @@ __global__ void __launch_bounds__(kAggThreads, 1)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     if (tid == 0) {
-        for (int s = 0; s < Sm::kWS; ++s) {
+        for (int s = 0; s < Sm::kWA; ++s) {
             mbar_init(&S.w_full[s], 1);
-            mbar_init(&S.w_empty[s], 1 + 4);   // MMA commit + 4 epilogue warps (den read)
+            mbar_init(&S.w_empty[s], 1);       // MMA commit
         }
         for (int s = 0; s < Sm::kFS; ++s) {
             mbar_init(&S.f_full[s], 1);
+            mbar_init(&S.f_conv[s], 8);        // 8 converter warps (NT = 2)
             mbar_init(&S.f_empty[s], 1);
         }
         for (int s = 0; s < kSlots; ++s) {
             mbar_init(&S.t_full[s], 1);
-            mbar_init(&S.t_empty[s], 4);
+            mbar_init(&S.t_empty[s], 4 * Sm::kEH);
         }
         S.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -373,208 +422,246 @@ __global__ void __launch_bounds__(kAggThreads, 1)
     __syncthreads();
     tc_fence_after();
 
+    constexpr int U = (DB + 1) / 2;   // 128-channel units per chunk
     if (warp == 0) {
         if (lane == 0) {
-            // ---- TMA producer
+            // ---- TMA producer: per chunk, K atom ka: W atom, then the U feature units
             uint32_t wc = 0, fc = 0;
+            bool ok = true;
             ChunkWalk walk;
-            for (int c = walk.next(a); c >= 0 && !*abort_flag; c = walk.next(a)) {
+            for (int c = walk.next(a); c >= 0 && ok && !*abort_flag; c = walk.next(a)) {
                 const int item = walk.item;
                 const int v = item / a.ntiles, tile = item - v * a.ntiles;
                 const int tx = tile % a.TX, ty = tile / a.TX;
-                const uint32_t ws = wc % Sm::kWS;
-                if (wc >= (uint32_t)Sm::kWS &&
-                    !agg_wait(abort_flag, a.status, &S.w_empty[ws], ((wc / Sm::kWS) - 1) & 1u))
-                    break;
-                mbar_expect_tx(&S.w_full[ws], NT * kChunkBytes);
-                for (int t = 0; t < NT; ++t)
-                    for (int ka = 0; ka < 4; ++ka)
-                        tma_load_2d(S.W[ws][t] + ka * kAtomBytes, t == 0 ? &wmap1 : &wmap2, &S.w_full[ws], ka * 64,
-                                    c * kCRows);
-                ++wc;
-                bool ok = true;
-                for (int b = 0; b < DB && ok; ++b)
-                    for (int t = 0; t < NT; ++t) {
+                for (int ka = 0; ka < 4 && ok; ++ka) {
+                    const uint32_t ws = wc % Sm::kWA;
+                    if (wc >= (uint32_t)Sm::kWA &&
+                        !agg_wait(abort_flag, a.status, &S.w_empty[ws], ((wc / Sm::kWA) - 1) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&S.w_full[ws], NT * kAtomBytes);
+                    tma_load_2d(S.W[ws][0], &wmap1, &S.w_full[ws], ka * 64, c * kCRows);
+                    if (NT == 2) tma_load_2d(S.W[ws][NT - 1], &wmap2, &S.w_full[ws], ka * 64, c * kCRows);
+                    ++wc;
+                    for (int un = 0; un < U; ++un) {
                         const uint32_t s = fc % Sm::kFS;
                         if (fc >= (uint32_t)Sm::kFS &&
                             !agg_wait(abort_flag, a.status, &S.f_empty[s], ((fc / Sm::kFS) - 1) & 1u)) {
                             ok = false;
                             break;
                         }
-                        mbar_expect_tx(&S.f_full[s], kFBlockBytes);
-                        tma_load_4d(S.F[s], t == 0 ? &fmap1 : &fmap2, &S.f_full[s], 64 * b, tx * kTile, ty * kTile,
-                                    v);
+                        mbar_expect_tx(&S.f_full[s], Sm::kFStage);
+                        // boxes of 64 bfloat16 or 32 float32 channels, 8 KB each
+                        constexpr int kBoxes = 2 * NT, kBoxCh = 64 / NT;
+#pragma unroll
+                        for (int j = 0; j < kBoxes; ++j)
+                            tma_load_4d(S.F[s] + 8192 * j, &fmap, &S.f_full[s], 128 * un + kBoxCh * j, tx * kTile,
+                                        ty * kTile + 4 * ka, v);
                         ++fc;
                     }
-                if (!ok) break;
+                }
             }
             if (*abort_flag) {
                 // let the copies already issued land (bounded)
                 for (uint32_t u = (fc > (uint32_t)Sm::kFS ? fc - Sm::kFS : 0u); u < fc; ++u)
                     mbar_wait(&S.f_full[u % Sm::kFS], (u / Sm::kFS) & 1u);
-                for (uint32_t u = (wc > (uint32_t)Sm::kWS ? wc - Sm::kWS : 0u); u < wc; ++u)
-                    mbar_wait(&S.w_full[u % Sm::kWS], (u / Sm::kWS) & 1u);
+                for (uint32_t u = (wc > (uint32_t)Sm::kWA ? wc - Sm::kWA : 0u); u < wc; ++u)
+                    mbar_wait(&S.w_full[u % Sm::kWA], (u / Sm::kWA) & 1u);
+            }
+        }
+    } else if (NT == 2 && warp >= 6) {
+        // ---- converters: float32 unit (boxes j = 0..3 of 32 channels at 8 KB j)
+        // -> F1 atoms h = 0, 1 (64 channels at 8 KB h) and F2 atoms (16 KB + 8 KB h).
+        // Converter warp cw owns pixel rows 8 cw .. 8 cw + 7 of every region:
+        // the bytes it reads are the bytes it writes, so the in-place rewrite
+        // needs only a warp-level barrier.
+        const int cw = warp - 6;
+        uint32_t fc = 0;
+        ChunkWalk walk;
+        bool ok = true;
+        for (int c = walk.next(a); c >= 0 && ok && !*abort_flag; c = walk.next(a)) {
+            for (int un = 0; un < 4 * U; ++un) {
+                const uint32_t s = fc % Sm::kFS;
+                if (!agg_wait(abort_flag, a.status, &S.f_full[s], (fc / Sm::kFS) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t* base = S.F[s];
+                // item i: pixel row p, output chunk oc = channels 8 oc .. 8 oc + 7 of 128
+                const int oc = lane & 15, box = oc >> 2, j0 = 2 * (oc & 3);
+                float x[4][8];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int p = 8 * cw + 2 * i + (lane >> 4);
+                    const uint8_t* row = base + box * 8192 + p * 128;
+                    const float4 lo4 = *reinterpret_cast<const float4*>(row + ((j0 ^ (p & 7)) << 4));
+                    const float4 hi4 = *reinterpret_cast<const float4*>(row + (((j0 + 1) ^ (p & 7)) << 4));
+                    x[i][0] = lo4.x;
+                    x[i][1] = lo4.y;
+                    x[i][2] = lo4.z;
+                    x[i][3] = lo4.w;
+                    x[i][4] = hi4.x;
+                    x[i][5] = hi4.y;
+                    x[i][6] = hi4.z;
+                    x[i][7] = hi4.w;
+                }
+                __syncwarp();   // the warp's rows are read before any is overwritten
+                const int h = oc >> 3, cc = oc & 7;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int p = 8 * cw + 2 * i + (lane >> 4);
+                    uint4 f1, f2;
+                    split8(x[i], f1, f2);
+                    const int o = 8192 * h + p * 128 + ((cc ^ (p & 7)) << 4);
+                    *reinterpret_cast<uint4*>(base + o) = f1;
+                    *reinterpret_cast<uint4*>(base + 16384 + o) = f2;
+                }
+                fence_proxy_async();   // generic writes, read by the tensor core
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.f_conv[s]);
+                ++fc;
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---- MMA issuer
-            uint32_t wc = 0, fc = 0, uc = 0;
+            // ---- MMA issuer: unit un of a chunk (128 channels; 64 for the last one
+            // when DB is odd) accumulates over the 4 K atoms in TMEM slot
+            // (units so far + un) % 4.  Descriptors advance by plain adds: the
+            // start address is bits 0-13 (address / 16).
+            constexpr uint32_t kIdFull = idesc_n(128), kIdLast = idesc_n(DB % 2 ? 64 : 128);
+            const uint64_t w0 = sw128_desc(saddr(S.W[0][0]), 16, 1024);
+            const uint64_t f0 = sw128_desc(saddr(S.F[0]), 8192, 1024);
+            uint32_t wc = 0, fc = 0, ub = 0;
             bool ok = true;
             ChunkWalk walk;
             for (int c = walk.next(a); c >= 0 && ok && !*abort_flag; c = walk.next(a)) {
-                const uint32_t ws = wc % Sm::kWS;
-                if (!agg_wait(abort_flag, a.status, &S.w_full[ws], (wc / Sm::kWS) & 1u)) break;
-                tc_fence_after();
-                for (int b = 0; b < DB && ok; ++b) {
-                    const uint32_t slot = uc % kSlots;
-                    if (uc >= (uint32_t)kSlots &&
-                        !agg_wait(abort_flag, a.status, &S.t_empty[slot], ((uc / kSlots) - 1) & 1u)) {
+                for (int ka = 0; ka < 4 && ok; ++ka) {
+                    const uint32_t ws = wc % Sm::kWA;
+                    if (!agg_wait(abort_flag, a.status, &S.w_full[ws], (wc / Sm::kWA) & 1u)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t dt = S.tmem_base + 64u * slot;
-                    for (int t = 0; t < NT; ++t) {
+                    const uint64_t wd1 = w0 + ((ws * NT * kAtomBytes) >> 4);
+                    const uint64_t wd2 = wd1 + ((NT - 1) * kAtomBytes >> 4);
+                    for (int un = 0; un < U; ++un) {
+                        const uint32_t u = ub + un, slot = u % kSlots;
+                        if (ka == 0 && u >= (uint32_t)kSlots &&
+                            !agg_wait(abort_flag, a.status, &S.t_empty[slot], ((u / kSlots) - 1) & 1u)) {
+                            ok = false;
+                            break;
+                        }
                         const uint32_t s = fc % Sm::kFS;
-                        if (!agg_wait(abort_flag, a.status, &S.f_full[s], (fc / Sm::kFS) & 1u)) {
+                        if (!agg_wait(abort_flag, a.status, NT == 2 ? &S.f_conv[s] : &S.f_full[s],
+                                      (fc / Sm::kFS) & 1u)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t f_base = saddr(S.F[s]);
-                        // term 0 (F1): W1 F1 (+ W2 F1); term 1 (F2): W1 F2
+                        const uint32_t dt = S.tmem_base + 128u * slot;
+                        const uint64_t fd = f0 + ((s * Sm::kFStage) >> 4);
+                        const uint32_t id = un == U - 1 ? kIdLast : kIdFull;
+                        // W1 F1 (+ W2 F1 + W1 F2 for NT = 2), 16 pixels per step
 #pragma unroll
-                        for (int ks = 0; ks < 16; ++ks) {
-                            const uint64_t bd = sw128_desc(f_base + ks * 2048, 1024, 1024);
-                            const uint32_t koff = (ks >> 2) * kAtomBytes + (ks & 3) * 32;
-                            const uint32_t acc = (ks > 0 || t > 0) ? 1u : 0u;
-                            mma_bf16(dt, sw128_desc(saddr(S.W[ws][0]) + koff, 16, 1024), bd, kIdesc, acc);
-                            if (NT == 2 && t == 0)
-                                mma_bf16(dt, sw128_desc(saddr(S.W[ws][NT - 1]) + koff, 16, 1024), bd, kIdesc, 1u);
+                        for (int ks = 0; ks < 4; ++ks) {
+                            mma_bf16(dt, wd1 + 2 * ks, fd + 128 * ks, id, (ka > 0 || ks > 0) ? 1u : 0u);
+                            if (NT == 2) {
+                                mma_bf16(dt, wd2 + 2 * ks, fd + 128 * ks, id, 1u);
+                                mma_bf16(dt, wd1 + 2 * ks, fd + (16384 >> 4) + 128 * ks, id, 1u);
+                            }
                         }
                         mma_commit(&S.f_empty[s]);
                         ++fc;
+                        if (ka == 3) mma_commit(&S.t_full[slot]);
                     }
                     if (!ok) break;
-                    mma_commit(&S.t_full[slot]);
-                    ++uc;
+                    mma_commit(&S.w_empty[ws]);
+                    ++wc;
                 }
-                if (!ok) break;
-                mma_commit(&S.w_empty[ws]);
-                ++wc;
+                ub += U;
             }
-            if (*abort_flag && uc > 0)   // the MMAs issued complete in order (bounded)
-                mbar_wait(&S.t_full[(uc - 1) % kSlots], ((uc - 1) / kSlots) & 1u);
+            if (*abort_flag && fc > 0)   // the MMAs issued complete in order (bounded)
+                mbar_wait(&S.f_empty[(fc - 1) % Sm::kFS], ((fc - 1) / Sm::kFS) & 1u);
         }
-    } else {
-        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = chunk rows
-        const int q = warp & 3;
+    } else if (warp >= 2 && warp < 2 + 4 * Sm::kEH) {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = chunk rows;
+        // with two warps per lane quarter (NT = 1) warps 2-5 take the first 64
+        // columns of each unit and warps 6-9 the second 64
+        const int q = warp & 3, half = (warp - 2) >> 2;
         const int r = 32 * q + lane;
         const int d = a.d;
-        uint32_t wc = 0, uc = 0;
+        float* st = &S.rows[warp - 2][lane * Sm::kPitch];
+        uint32_t ub = 0;
+        bool ok = true;
         ChunkWalk walk;
-        for (int c = walk.next(a); c >= 0 && !*abort_flag; c = walk.next(a)) {
+        for (int c = walk.next(a); c >= 0 && ok && !*abort_flag; c = walk.next(a)) {
             const int rows = a.chunk_rows[c];
             const bool valid = r < rows;
             const uint32_t g = valid ? a.chunk_gid[(size_t)c * kCRows + r] : 0u;
-            const uint32_t ws = wc % Sm::kWS;
-            if (!agg_wait(abort_flag, a.status, &S.w_full[ws], (wc / Sm::kWS) & 1u)) break;
-            if (!a.store_mode && valid) {
-                // den: the row's W terms summed over the 256 pixels
+            if (half == 0 && valid && !a.store_mode) {
                 float sden = 0.f;
 #pragma unroll
-                for (int t = 0; t < NT; ++t) {
-                    const uint8_t* row = S.W[ws][t] + r * 128;
-#pragma unroll 2
-                    for (int ka = 0; ka < 4; ++ka) {
-#pragma unroll
-                        for (int c16 = 0; c16 < 8; ++c16) {
-                            const uint4 v4 = *reinterpret_cast<const uint4*>(row + ka * kAtomBytes + c16 * 16);
-                            const uint32_t wv[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                sden += __uint_as_float(wv[e] << 16);
-                                sden += __uint_as_float(wv[e] & 0xffff0000u);
-                            }
-                        }
-                    }
-                }
+                for (int t = 0; t < NT; ++t) sden += a.chunk_den[((size_t)c * kCRows + r) * NT + t];
                 atomicAdd(a.den + g, sden);
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&S.w_empty[ws]);
-            ++wc;
-            bool ok = true;
-            for (int b = 0; b < DB; ++b) {
-                const uint32_t slot = uc % kSlots;
-                if (!agg_wait(abort_flag, a.status, &S.t_full[slot], (uc / kSlots) & 1u)) {
+            for (int un = 0; un < U; ++un) {
+                const uint32_t u = ub + un, slot = u % kSlots;
+                if (!agg_wait(abort_flag, a.status, &S.t_full[slot], (u / kSlots) & 1u)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                float v0[32], v1[32];
-                const uint32_t taddr = S.tmem_base + ((uint32_t)(32 * q) << 16) + 64u * slot;
-                tmem_ld32(taddr, v0);
-                tmem_ld32(taddr + 32, v1);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&S.t_empty[slot]);
-                ++uc;
-                // this warp's 32 rows x 64 columns, row-major with the 16-byte
-                // chunks XOR-swizzled by row (conflict-free both ways)
-                float4* xp = S.xpose[q];
-#pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    const float* src = c < 8 ? &v0[4 * c] : &v1[4 * (c - 8)];
-                    xp[lane * 16 + (c ^ (lane & 7))] = make_float4(src[0], src[1], src[2], src[3]);
-                }
-                __syncwarp();
-                // lane l: row 2i + l / 16, columns 4 (l % 16) .. + 3
-                const int cc = lane & 15;
-                const int lim = d - 64 * b;   // channels of this block inside d
-#pragma unroll 4
-                for (int i = 0; i < 16; ++i) {
-                    const int rr = 2 * i + (lane >> 4);
-                    const uint32_t gr = __shfl_sync(0xffffffffu, g, rr);
-                    const float4 x = xp[rr * 16 + (cc ^ (rr & 7))];
-                    if (32 * q + rr < rows && 4 * cc < lim) {
-                        float* dst = a.num + (int64_t)gr * d + 64 * b + 4 * cc;
-                        if (a.store_mode) {
-                            dst[0] = x.x;
-                            if (4 * cc + 1 < lim) dst[1] = x.y;
-                            if (4 * cc + 2 < lim) dst[2] = x.z;
-                            if (4 * cc + 3 < lim) dst[3] = x.w;
-                        } else {
-                            red_add_v4(dst, x.x, x.y, x.z, x.w);
+                for (int hh = half; hh < 2; hh += Sm::kEH) {
+                    const int b = 2 * un + hh;   // this warp's 64-channel block
+                    const bool has = b < DB;
+                    float v0[32], v1[32];
+                    if (has) {
+                        const uint32_t taddr = S.tmem_base + ((uint32_t)(32 * q) << 16) + 128u * slot + 64u * hh;
+                        tmem_ld32(taddr, v0);
+                        tmem_ld32(taddr + 32, v1);
+                    }
+                    if (hh + Sm::kEH >= 2) {   // this warp's last read of the slot
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&S.t_empty[slot]);
+                    }
+                    if (!has) continue;
+                    const int lim = min(64, d - 64 * b);   // channels of this block inside d
+                    if (a.store_mode) {
+                        if (valid) {
+                            float* dst = a.num + (int64_t)g * d + 64 * b;
+    #pragma unroll
+                            for (int i = 0; i < 32; ++i) {
+                                if (i < lim) dst[i] = v0[i];
+                                if (32 + i < lim) dst[32 + i] = v1[i];
+                            }
+                        }
+                    } else {
+                        // the row goes to shared memory (pitch 272 B: conflict-free) and the
+                        // bulk-copy engine adds it into num[g, 64 b ..]
+                        bulk_wait_read_all();   // the previous block's row has been read
+    #pragma unroll
+                        for (int c4 = 0; c4 < 16; ++c4) {
+                            const float* src = c4 < 8 ? &v0[4 * c4] : &v1[4 * (c4 - 8)];
+                            *reinterpret_cast<float4*>(st + 4 * c4) = make_float4(src[0], src[1], src[2], src[3]);
+                        }
+                        fence_proxy_async();   // generic writes, read by the bulk copy
+                        if (valid && lim > 0) {
+                            bulk_reduce_add_f32(a.num + (int64_t)g * d + 64 * b, st, (uint32_t)lim * 4u);
+                            bulk_commit();
                         }
                     }
                 }
-                __syncwarp();
             }
-            if (!ok) break;
+            ub += U;
         }
     }
+    bulk_wait_all();   // this thread's reductions into num are complete
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0) tmem_dealloc(S.tmem_base, 512);
-}
-
-// float32 features -> two bfloat16 arrays with f = hi + lo to 16 significant bits.
-__global__ void k_split_f32(const float4* __restrict__ f, uint2* __restrict__ hi, uint2* __restrict__ lo,
-                            int64_t n4) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 x = f[i];
-        const __nv_bfloat16 a = __float2bfloat16_rn(x.x), b = __float2bfloat16_rn(x.y);
-        const __nv_bfloat16 c = __float2bfloat16_rn(x.z), e = __float2bfloat16_rn(x.w);
-        auto pk = [](__nv_bfloat16 l, __nv_bfloat16 h) {
-            return (uint32_t)__bfloat16_as_ushort(l) | ((uint32_t)__bfloat16_as_ushort(h) << 16);
-        };
-        hi[i] = make_uint2(pk(a, b), pk(c, e));
-        lo[i] = make_uint2(pk(__float2bfloat16_rn(x.x - __bfloat162float(a)), __float2bfloat16_rn(x.y - __bfloat162float(b))),
-                           pk(__float2bfloat16_rn(x.z - __bfloat162float(c)), __float2bfloat16_rn(x.w - __bfloat162float(e))));
-    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -592,16 +679,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// bfloat16 tensor map, 128-byte swizzle, zero fill out of bounds.
-ludvig_status encode_bf16(CUtensorMap* map, const void* base, cuuint32_t rank, const cuuint64_t* dims,
-                          const cuuint64_t* strides, const cuuint32_t* box) {
+// Tensor map with 128-byte swizzle and zero fill out of bounds.
+ludvig_status encode(CUtensorMap* map, CUtensorMapDataType type, const void* base, cuuint32_t rank,
+                     const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) {
         set_error("cuTensorMapEncodeTiled unavailable");
         return LUDVIG_ERR_CUDA;
     }
     cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(base), dims, strides, box, estr,
+    CUresult r = enc(map, type, rank, const_cast<void*>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -611,13 +698,17 @@ ludvig_status encode_bf16(CUtensorMap* map, const void* base, cuuint32_t rank, c
     return LUDVIG_OK;
 }
 
-// Tensor map over features [nv, H, W, d] bfloat16: box of 64 channels x 16 x 16
-// pixels of one view, zero fill outside the image and past d.
-ludvig_status make_feature_map(CUtensorMap* map, const void* feats, int nv, int width, int height, int d) {
+// Tensor map over features [nv, H, W, d]: one 64-pixel K atom (16 x 4 pixels)
+// of one view per box, 64 bfloat16 channels or 32 float32 channels (128-byte
+// rows either way), zero fill outside the image and past d.
+ludvig_status make_feature_map(CUtensorMap* map, const void* feats, int dtype, int nv, int width, int height,
+                               int d) {
+    const cuuint64_t es = dtype == LUDVIG_F32 ? 4 : 2;
     cuuint64_t dims[4] = {(cuuint64_t)d, (cuuint64_t)width, (cuuint64_t)height, (cuuint64_t)nv};
-    cuuint64_t strides[3] = {(cuuint64_t)d * 2, (cuuint64_t)width * d * 2, (cuuint64_t)height * width * d * 2};
-    cuuint32_t box[4] = {64, 16, 16, 1};
-    return encode_bf16(map, feats, 4, dims, strides, box);
+    cuuint64_t strides[3] = {(cuuint64_t)d * es, (cuuint64_t)width * d * es, (cuuint64_t)height * width * d * es};
+    cuuint32_t box[4] = {(cuuint32_t)(128 / es), 16, 4, 1};
+    return encode(map, dtype == LUDVIG_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                  feats, 4, dims, strides, box);
 }
 
 // Tensor map over chunk rows [cap * 128, 256] bfloat16: box of 64 pixels x 128
@@ -626,7 +717,7 @@ ludvig_status make_w_map(CUtensorMap* map, const void* w, int64_t cap) {
     cuuint64_t dims[2] = {256, (cuuint64_t)cap * kCRows};
     cuuint64_t strides[1] = {(cuuint64_t)kRowBytes};
     cuuint32_t box[2] = {64, (cuuint32_t)kCRows};
-    return encode_bf16(map, w, 2, dims, strides, box);
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w, 2, dims, strides, box);
 }
 
 template <int DB, int NT>
@@ -637,7 +728,7 @@ ludvig_status launch_agg(const AggArgs& args, const CUtensorMap* maps, int grid,
                                      (int)agg_smem_bytes<NT>()));
         configured = true;
     }
-    k_aggregate_tc<DB, NT><<<grid, kAggThreads, agg_smem_bytes<NT>(), st>>>(args, maps[0], maps[1], maps[2], maps[3]);
+    k_aggregate_tc<DB, NT><<<grid, agg_threads<NT>(), agg_smem_bytes<NT>(), st>>>(args, maps[0], maps[1], maps[2]);
     LV_LAUNCH();
     return LUDVIG_OK;
 }
@@ -684,22 +775,6 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
     const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
     const int nitems = nv * TX * TY;
     if (nitems == 0) return LUDVIG_OK;
-    const void* f1 = feats;
-    const void* f2 = feats;
-    if (dtype == LUDVIG_F32) {
-        // split the chunk's float32 features into two bfloat16 arrays
-        const int64_t count = (int64_t)nv * width * height * d;
-        void *hi, *lo;
-        LV_TRY(ws.get("tc.f_hi", (size_t)count * 2, &hi));
-        LV_TRY(ws.get("tc.f_lo", (size_t)count * 2, &lo));
-        StageScope split_scope(LUDVIG_STAGE_SPLIT, st);
-        k_split_f32<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, ceil_div(count / 4, 256))), 256,
-                      0, st>>>(static_cast<const float4*>(feats), static_cast<uint2*>(hi), static_cast<uint2*>(lo),
-                               count / 4);
-        LV_LAUNCH();
-        f1 = hi;
-        f2 = lo;
-    }
     int* counter;
     int* host;   // [0] chunks used, [1] status
     LV_TRY(ws.get("tc.counter", 1, &counter));
@@ -713,6 +788,7 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
     uint8_t *wg1 = nullptr, *wg2 = nullptr;
     uint32_t* cgid = nullptr;
     int *crows = nullptr, *cnext = nullptr, *ifirst = nullptr;
+    float* cden = nullptr;
     LV_TRY(ws.get("tc.item_first", (size_t)nitems, &ifirst));
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (cap > 0x7fffffff / kCRows) {
@@ -724,6 +800,7 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
         LV_TRY(ws.get("tc.chunk_gid", (size_t)cap * kCRows, &cgid));
         LV_TRY(ws.get("tc.chunk_rows", (size_t)cap, &crows));
         LV_TRY(ws.get("tc.chunk_next", (size_t)cap, &cnext));
+        LV_TRY(ws.get("tc.chunk_den", (size_t)cap * kCRows * NT, &cden));
         LV_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
         LV_CUDA(cudaMemsetAsync(ifirst, 0xff, sizeof(int) * (size_t)nitems, st));
         WeightsArgs w{};
@@ -741,6 +818,7 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
         w.item_first = ifirst;
         w.chunk_counter = counter;
         w.cap = (int)cap;
+        w.chunk_den = cden;
         w.status = status;
         const int tslot = trace_on() ? trace_begin(LUDVIG_STAGE_WEIGHTS, st) : -1;
         if (NT == 2)
@@ -767,17 +845,17 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
     }
     *chunk_cap = cap;
     if (count == 0) return LUDVIG_OK;
-    CUtensorMap maps[4];
+    CUtensorMap maps[3];
     LV_TRY(make_w_map(&maps[0], wg1, cap));
     LV_TRY(make_w_map(&maps[1], NT == 2 ? wg2 : wg1, cap));
-    LV_TRY(make_feature_map(&maps[2], f1, nv, width, height, d));
-    LV_TRY(make_feature_map(&maps[3], f2, nv, width, height, d));
+    LV_TRY(make_feature_map(&maps[2], feats, dtype, nv, width, height, d));
     AggArgs g{};
     g.cap = (int)cap;
     g.chunk_rows = crows;
     g.chunk_next = cnext;
     g.item_first = ifirst;
     g.chunk_gid = cgid;
+    g.chunk_den = cden;
     g.nitems = nitems;
     g.ntiles = TX * TY;
     g.TX = TX;
@@ -814,11 +892,10 @@ extern "C" ludvig_status ludvig_debug_mma_bf16(const void* a, const void* f, int
     h.status = 0;
     for (int r = 0; r < kCRows; ++r) h.gid[r] = (uint32_t)r;
     LV_CUDA(cudaMemcpyAsync(meta, &h, sizeof(Meta), cudaMemcpyHostToDevice, st));
-    CUtensorMap maps[4];
+    CUtensorMap maps[3];
     LV_TRY(make_w_map(&maps[0], a, 1));
     maps[1] = maps[0];
-    LV_TRY(make_feature_map(&maps[2], f, 1, 16, 16, d));
-    maps[3] = maps[2];
+    LV_TRY(make_feature_map(&maps[2], f, LUDVIG_BF16, 1, 16, 16, d));
     AggArgs g{};
     g.cap = 1;
     g.chunk_rows = &meta->rows;

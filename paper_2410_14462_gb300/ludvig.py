@@ -220,7 +220,7 @@ def get_option(option: int) -> int:
 
 
 STAGES = ["project", "depth_sort", "bin", "tile_sort", "composite", "normalise", "knn", "graph", "diffuse",
-          "split", "weights", "aggregate"]
+          "weights", "aggregate"]
 
 
 class TraceStruct(ctypes.Structure):
