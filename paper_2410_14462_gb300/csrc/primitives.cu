@@ -4,10 +4,11 @@
 // first.  Each pass: (1) every block histograms the digits of its 4096-key
 // tile, (2) one exclusive scan over the histograms laid out
 // [segment][digit][block] gives every (block, digit) its output base, (3)
-// every block re-reads its tile in order and scatters each key to
-// base + (number of equal digits before it in the tile), found with warp
-// match/popc and a per-digit prefix over the warps.  Segment-major histogram
-// order keeps equal-length segments apart, so one launch sorts many views.
+// every block re-reads its tile, ranks each key among the equal digits before
+// it in the tile (warp match/popc, then a prefix over the warps), sorts the
+// tile by digit in shared memory and writes each digit's run to its base.
+// Segment-major histogram order keeps equal-length segments apart, so one
+// launch sorts many views.
 #include "common.cuh"
 
 namespace ludvig {
@@ -152,46 +153,91 @@ k_radix_upsweep(const uint32_t* __restrict__ keys, int shift, uint32_t* __restri
     hist[(seg * 256 + threadIdx.x) * bps + b] = h[threadIdx.x];
 }
 
+// Warp w owns keys [512 w, 512 w + 512) of the block's tile (16 rounds of 32
+// consecutive keys), so per-digit counts accumulate warp-locally in tile order;
+// one block prefix over the warps then gives every key its place in the tile
+// sorted by digit (stable).  The tile is sorted in shared memory and written
+// out in digit runs, so the stores coalesce.
 __global__ void __launch_bounds__(kRadixThreads)
 k_radix_downsweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                   uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int shift,
                   const uint32_t* __restrict__ hist, int64_t bps) {
-    __shared__ uint32_t base_off[256];
-    __shared__ uint32_t run[256];
-    __shared__ uint32_t wcnt[kRadixThreads / 32][256];
+    constexpr int kWarps = kRadixThreads / 32;
+    __shared__ uint32_t s_key[kRadixTile];
+    __shared__ uint32_t s_val[kRadixTile];
+    __shared__ uint32_t wcnt[kWarps][256];   // per-warp digit counts, then their prefix
+    __shared__ uint32_t dstart[256];          // first tile position of each digit
+    __shared__ uint32_t obase[256];           // output position of each digit's first key
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t seg = blockIdx.x / bps, b = blockIdx.x % bps;
-    base_off[tid] = hist[(seg * 256 + tid) * bps + b];
-    run[tid] = 0;
     const int64_t base = (int64_t)blockIdx.x * kRadixTile;
     const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
+    __syncthreads();
+    uint32_t k[kRadixItems], v[kRadixItems], rk[kRadixItems];
+#pragma unroll
     for (int i = 0; i < kRadixItems; ++i) {
+        const int64_t idx = base + warp * (32 * kRadixItems) + i * 32 + lane;
+        k[i] = kin[idx];
+        v[i] = vin[idx];
+    }
 #pragma unroll
-        for (int w = 0; w < kRadixThreads / 32; ++w) wcnt[w][tid] = 0;
-        __syncthreads();
-        const int64_t idx = base + i * kRadixThreads + tid;
-        const uint32_t k = kin[idx];
-        const uint32_t v = vin[idx];
-        const uint32_t d = (k >> shift) & 0xffu;
+    for (int i = 0; i < kRadixItems; ++i) {
+        const uint32_t d = (k[i] >> shift) & 0xffu;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rank = __popc(peers & lt_mask);
-        if (rank == 0) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t s = run[tid];
+        const uint32_t before = wcnt[warp][d];   // equal digits in this warp's earlier rounds
+        rk[i] = before + __popc(peers & lt_mask);
+        __syncwarp();
+        if ((peers & lt_mask) == 0) wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // digit tid: exclusive prefix over the warps, tile total
+    uint32_t tot = 0;
 #pragma unroll
-            for (int w = 0; w < kRadixThreads / 32; ++w) {
-                const uint32_t c = wcnt[w][tid];
-                wcnt[w][tid] = s;
-                s += c;
-            }
-            run[tid] = s;
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = wcnt[w][tid];
+        wcnt[w][tid] = tot;
+        tot += c;
+    }
+    obase[tid] = hist[(seg * 256 + tid) * bps + b];
+    uint32_t ex;
+    {
+        // exclusive scan of tot over the 256 digits
+        __shared__ uint32_t wsum[kWarps];
+        uint32_t incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
         }
+        if (lane == 31) wsum[warp] = incl;
         __syncthreads();
-        const uint32_t pos = base_off[d] + wcnt[warp][d] + rank;
-        kout[pos] = k;
-        vout[pos] = v;
-        __syncthreads();
+        uint32_t before = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w)
+            if (w < warp) before += wsum[w];
+        ex = before + incl - tot;
+    }
+    dstart[tid] = ex;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kRadixItems; ++i) {
+        const uint32_t d = (k[i] >> shift) & 0xffu;
+        const uint32_t pos = dstart[d] + wcnt[warp][d] + rk[i];
+        s_key[pos] = k[i];
+        s_val[pos] = v[i];
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int i = 0; i < kRadixItems; ++i) {
+        const int p = i * kRadixThreads + tid;
+        const uint32_t kk = s_key[p];
+        const uint32_t d = (kk >> shift) & 0xffu;
+        const uint32_t o = obase[d] + (uint32_t)p - dstart[d];
+        kout[o] = kk;
+        vout[o] = s_val[p];
     }
 }
 
