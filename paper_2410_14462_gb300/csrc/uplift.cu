@@ -469,6 +469,29 @@ __global__ void k_normalise(const float* num, const float* __restrict__ den, flo
     if (beta && idx % d == 0) beta[i] = b;
 }
 
+// Same, one warp per Gaussian (d >= 32), float4 accesses when vec4 (d % 4 == 0
+// and 16-byte aligned rows).
+__global__ void k_normalise_rows(const float* num, const float* __restrict__ den, float* out, float* beta,
+                                 int64_t n, int d, int vec4) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps) {
+        const float b = den[i];
+        const float* src = num + i * d;
+        float* dst = out + i * d;
+        if (vec4) {
+            for (int c = 4 * lane; c < d; c += 128) {
+                const float4 x = *reinterpret_cast<const float4*>(src + c);
+                *reinterpret_cast<float4*>(dst + c) =
+                    b > 0.f ? make_float4(x.x / b, x.y / b, x.z / b, x.w / b) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        } else {
+            for (int c = lane; c < d; c += 32) dst[c] = b > 0.f ? src[c] / b : 0.f;
+        }
+        if (beta && lane == 0) beta[i] = b;
+    }
+}
+
 unsigned grid_for(int64_t work, int threads) { return (unsigned)ceil_div(work, threads); }
 
 struct ChunkDebug {
@@ -764,7 +787,15 @@ extern "C" ludvig_status ludvig_uplift_finalize(int64_t n, int32_t d, const floa
     if (n == 0) return LUDVIG_OK;
     LV_ARG(num != nullptr && den != nullptr && out != nullptr, "NULL buffer");
     StageScope scope(LUDVIG_STAGE_NORMALISE, static_cast<cudaStream_t>(stream));
-    k_normalise<<<grid_for(n * d, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(num, den, out, beta, n, d);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (d >= 32) {
+        const int vec4 = (d % 4 == 0) && (reinterpret_cast<uintptr_t>(num) % 16 == 0) &&
+                         (reinterpret_cast<uintptr_t>(out) % 16 == 0);
+        k_normalise_rows<<<(unsigned)std::min<int64_t>(ceil_div(n, 8), 152 * 64), 256, 0, st>>>(num, den, out, beta,
+                                                                                               n, d, vec4);
+    } else {
+        k_normalise<<<grid_for(n * d, 256), 256, 0, st>>>(num, den, out, beta, n, d);
+    }
     LV_LAUNCH();
     return LUDVIG_OK;
 }
