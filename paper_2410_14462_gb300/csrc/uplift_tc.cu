@@ -328,6 +328,10 @@ struct AggSmem {
     uint64_t w_full[kWA], w_empty[kWA];
     uint64_t f_full[kFS], f_conv[kFS], f_empty[kFS];
     uint64_t t_full[kSlots], t_empty[kSlots];
+    static constexpr int kQ = 16;                             // chunk queue (producer -> other roles)
+    static constexpr int kConsumers = 1 + 4 * kEH + (NT == 2 ? 8 : 0);   // MMA thread + warps
+    int4 q[kQ];                                               // chunk, tile, rows (chunk -1: end)
+    uint64_t q_full[kQ], q_empty[kQ];
     uint32_t tmem_base;
     int abort_flag;
 };
@@ -347,10 +351,11 @@ constexpr int agg_threads() {
 
 // The chunks a CTA aggregates: those of tiles blockIdx.x, blockIdx.x + gridDim.x,
 // ... in order, each tile's chunks back to back (so its feature blocks are
-// still in L2 for the second chunk).  Every role walks the same sequence.
+// still in L2 for the second chunk).  The producer walks the sequence and
+// hands it to the other roles through a queue in shared memory.
 struct ChunkWalk {
-    int item, c;
-    __device__ ChunkWalk() : item((int)blockIdx.x - (int)gridDim.x), c(-1) {}
+    int item, c, rows;
+    __device__ ChunkWalk() : item((int)blockIdx.x - (int)gridDim.x), c(-1), rows(0) {}
     // next non-empty chunk (its tile in item), or -1 at the end
     __device__ int next(const AggArgs& a) {
         for (;;) {
@@ -361,10 +366,28 @@ struct ChunkWalk {
                 c = a.item_first[item];
             }
             if (c >= a.cap) return -1;   // never with a complete weights pass
-            if (a.chunk_rows[c] > 0) return c;
+            rows = a.chunk_rows[c];
+            if (rows > 0) return c;
         }
     }
 };
+
+__device__ __forceinline__ bool agg_wait(volatile int* abort_flag, int* status, uint64_t* bar, uint32_t parity);
+
+// Next entry of the chunk queue for a consumer role (whole warp, or the MMA
+// thread alone); false on a timed-out wait.  The entry's slot is released
+// right away (one arrival per consumer warp).
+template <class Sm>
+__device__ __forceinline__ bool queue_next(Sm& S, volatile int* abort_flag, int* status, uint32_t& qc, int4& e,
+                                           bool single) {
+    const uint32_t slot = qc % Sm::kQ;
+    if (!agg_wait(abort_flag, status, &S.q_full[slot], (qc / Sm::kQ) & 1u)) return false;
+    e = S.q[slot];
+    if (!single) __syncwarp();
+    if (single || (threadIdx.x & 31) == 0) mbar_arrive(&S.q_empty[slot]);
+    ++qc;
+    return true;
+}
 
 __device__ __forceinline__ bool agg_wait(volatile int* abort_flag, int* status, uint64_t* bar, uint32_t parity) {
     if (mbar_wait(bar, parity)) return true;
@@ -414,6 +437,10 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
             mbar_init(&S.t_full[s], 1);
             mbar_init(&S.t_empty[s], 4 * Sm::kEH);
         }
+        for (int s = 0; s < Sm::kQ; ++s) {
+            mbar_init(&S.q_full[s], 1);
+            mbar_init(&S.q_empty[s], Sm::kConsumers);
+        }
         S.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -426,10 +453,20 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
     if (warp == 0) {
         if (lane == 0) {
             // ---- TMA producer: per chunk, K atom ka: W atom, then the U feature units
-            uint32_t wc = 0, fc = 0;
+            uint32_t wc = 0, fc = 0, qc = 0;
             bool ok = true;
             ChunkWalk walk;
-            for (int c = walk.next(a); c >= 0 && ok && !*abort_flag; c = walk.next(a)) {
+            for (;;) {
+                const int c = (ok && !*abort_flag) ? walk.next(a) : -1;
+                // publish the chunk (or the end) to the other roles
+                const uint32_t qs = qc % Sm::kQ;
+                if (qc >= (uint32_t)Sm::kQ &&
+                    !agg_wait(abort_flag, a.status, &S.q_empty[qs], ((qc / Sm::kQ) - 1) & 1u))
+                    break;
+                S.q[qs] = make_int4(c, c >= 0 ? walk.item : -1, c >= 0 ? walk.rows : 0, 0);
+                mbar_arrive(&S.q_full[qs]);
+                ++qc;
+                if (c < 0) break;
                 const int item = walk.item;
                 const int v = item / a.ntiles, tile = item - v * a.ntiles;
                 const int tx = tile % a.TX, ty = tile / a.TX;
@@ -477,10 +514,11 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
         // the bytes it reads are the bytes it writes, so the in-place rewrite
         // needs only a warp-level barrier.
         const int cw = warp - 6;
-        uint32_t fc = 0;
-        ChunkWalk walk;
+        uint32_t fc = 0, qc = 0;
         bool ok = true;
-        for (int c = walk.next(a); c >= 0 && ok && !*abort_flag; c = walk.next(a)) {
+        for (;;) {
+            int4 e;
+            if (!ok || *abort_flag || !queue_next(S, abort_flag, a.status, qc, e, false) || e.x < 0) break;
             for (int un = 0; un < 4 * U; ++un) {
                 const uint32_t s = fc % Sm::kFS;
                 if (!agg_wait(abort_flag, a.status, &S.f_full[s], (fc / Sm::kFS) & 1u)) {
@@ -532,10 +570,11 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
             constexpr uint32_t kIdFull = idesc_n(128), kIdLast = idesc_n(DB % 2 ? 64 : 128);
             const uint64_t w0 = sw128_desc(saddr(S.W[0][0]), 16, 1024);
             const uint64_t f0 = sw128_desc(saddr(S.F[0]), 8192, 1024);
-            uint32_t wc = 0, fc = 0, ub = 0;
+            uint32_t wc = 0, fc = 0, ub = 0, qc = 0;
             bool ok = true;
-            ChunkWalk walk;
-            for (int c = walk.next(a); c >= 0 && ok && !*abort_flag; c = walk.next(a)) {
+            for (;;) {
+                int4 e;
+                if (!ok || *abort_flag || !queue_next(S, abort_flag, a.status, qc, e, true) || e.x < 0) break;
                 for (int ka = 0; ka < 4 && ok; ++ka) {
                     const uint32_t ws = wc % Sm::kWA;
                     if (!agg_wait(abort_flag, a.status, &S.w_full[ws], (wc / Sm::kWA) & 1u)) {
@@ -592,11 +631,12 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
         const int r = 32 * q + lane;
         const int d = a.d;
         float* st = &S.rows[warp - 2][lane * Sm::kPitch];
-        uint32_t ub = 0;
+        uint32_t ub = 0, qc = 0;
         bool ok = true;
-        ChunkWalk walk;
-        for (int c = walk.next(a); c >= 0 && ok && !*abort_flag; c = walk.next(a)) {
-            const int rows = a.chunk_rows[c];
+        for (;;) {
+            int4 e;
+            if (!ok || *abort_flag || !queue_next(S, abort_flag, a.status, qc, e, false) || e.x < 0) break;
+            const int c = e.x, rows = e.z;
             const bool valid = r < rows;
             const uint32_t g = valid ? a.chunk_gid[(size_t)c * kCRows + r] : 0u;
             if (half == 0 && valid && !a.store_mode) {
