@@ -310,16 +310,19 @@ struct AggArgs {
     int store_mode;   // debug GEMM: num[gid * d + c] = accumulator (no den)
 };
 
-// Feature units: 64 pixels (one K atom) x 128 channels, as two 64-channel
-// 128-byte-swizzled atoms 8 KB apart (the MMA's N = 128).  NT = 1: two
-// bfloat16 TMA boxes (16 KB).  NT = 2: four float32 boxes of 32 channels
-// (32 KB), turned in place into F1 (first 16 KB) and F2 (second 16 KB) by the
-// converter warps.
+// Feature units (16 KB): 128 channels of 64 pixels (NT = 1: one K atom, two
+// 64-channel bfloat16 boxes of 8 KB) or of 32 pixels (NT = 2: half an atom,
+// four 32-channel float32 boxes of 4 KB, turned in place into F1 (first 8 KB)
+// and F2 (second 8 KB) by the converter warps).  The two 64-channel atoms of a
+// term sit kBoxBytes apart (the MMA's N = 128).
 template <int NT>
 struct AggSmem {
     static constexpr int kWA = NT == 1 ? 4 : 2;              // W atom stages (NT x 16 KB each)
-    static constexpr uint32_t kFStage = NT * 16384u;          // one feature unit
-    static constexpr int kFS = NT == 1 ? 5 : 3;               // 80 KB or 96 KB of stages
+    static constexpr int kHalves = NT == 2 ? 2 : 1;           // feature units per K atom and channel group
+    static constexpr int kUnitPx = 64 / kHalves;              // pixels per unit
+    static constexpr uint32_t kBoxBytes = kUnitPx * 128u;     // one 128-byte-wide box (and one F1 atom)
+    static constexpr uint32_t kFStage = 16384u;               // one feature unit
+    static constexpr int kFS = NT == 1 ? 5 : 6;               // 80 KB or 96 KB of stages
     static constexpr int kEH = NT == 1 ? 2 : 1;               // epilogue warps per TMEM lane quarter
     static constexpr int kPitch = 68;                         // staged row: 64 floats + 16 B pad
     uint8_t W[kWA][NT][kAtomBytes];                           // offset 0 (1024-aligned)
@@ -477,11 +480,19 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(&S.w_full[ws], NT * kAtomBytes);
-                    tma_load_2d(S.W[ws][0], &wmap1, &S.w_full[ws], ka * 64, c * kCRows);
-                    if (NT == 2) tma_load_2d(S.W[ws][NT - 1], &wmap2, &S.w_full[ws], ka * 64, c * kCRows);
+                    // only the chunk's rows, in boxes of 32 (the rest of the atom is not read
+                    // into any kept result)
+                    const int nrb = (walk.rows + 31) >> 5;
+                    mbar_expect_tx(&S.w_full[ws], (uint32_t)(NT * nrb) * 4096u);
+                    for (int rb = 0; rb < nrb; ++rb) {
+                        tma_load_2d(S.W[ws][0] + 4096 * rb, &wmap1, &S.w_full[ws], ka * 64, c * kCRows + 32 * rb);
+                        if (NT == 2)
+                            tma_load_2d(S.W[ws][NT - 1] + 4096 * rb, &wmap2, &S.w_full[ws], ka * 64,
+                                        c * kCRows + 32 * rb);
+                    }
                     ++wc;
-                    for (int un = 0; un < U; ++un) {
+                    for (int un = 0; un < U && ok; ++un)
+                    for (int hf = 0; hf < Sm::kHalves; ++hf) {
                         const uint32_t s = fc % Sm::kFS;
                         if (fc >= (uint32_t)Sm::kFS &&
                             !agg_wait(abort_flag, a.status, &S.f_empty[s], ((fc / Sm::kFS) - 1) & 1u)) {
@@ -489,12 +500,13 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
                             break;
                         }
                         mbar_expect_tx(&S.f_full[s], Sm::kFStage);
-                        // boxes of 64 bfloat16 or 32 float32 channels, 8 KB each
+                        // kUnitPx pixels (kUnitPx / 16 rows of the tile) x 128 channels:
+                        // boxes of 64 bfloat16 or 32 float32 channels
                         constexpr int kBoxes = 2 * NT, kBoxCh = 64 / NT;
 #pragma unroll
                         for (int j = 0; j < kBoxes; ++j)
-                            tma_load_4d(S.F[s] + 8192 * j, &fmap, &S.f_full[s], 128 * un + kBoxCh * j, tx * kTile,
-                                        ty * kTile + 4 * ka, v);
+                            tma_load_4d(S.F[s] + Sm::kBoxBytes * j, &fmap, &S.f_full[s], 128 * un + kBoxCh * j,
+                                        tx * kTile, ty * kTile + 4 * ka + (Sm::kUnitPx / 16) * hf, v);
                         ++fc;
                     }
                 }
@@ -519,7 +531,7 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
         for (;;) {
             int4 e;
             if (!ok || *abort_flag || !queue_next(S, abort_flag, a.status, qc, e, false) || e.x < 0) break;
-            for (int un = 0; un < 4 * U; ++un) {
+            for (int un = 0; un < 4 * Sm::kHalves * U; ++un) {
                 const uint32_t s = fc % Sm::kFS;
                 if (!agg_wait(abort_flag, a.status, &S.f_full[s], (fc / Sm::kFS) & 1u)) {
                     ok = false;
@@ -528,11 +540,11 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
                 uint8_t* base = S.F[s];
                 // item i: pixel row p, output chunk oc = channels 8 oc .. 8 oc + 7 of 128
                 const int oc = lane & 15, box = oc >> 2, j0 = 2 * (oc & 3);
-                float x[4][8];
+                float x[2][8];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int p = 8 * cw + 2 * i + (lane >> 4);
-                    const uint8_t* row = base + box * 8192 + p * 128;
+                for (int i = 0; i < 2; ++i) {
+                    const int p = 4 * cw + 2 * i + (lane >> 4);
+                    const uint8_t* row = base + box * 4096 + p * 128;
                     const float4 lo4 = *reinterpret_cast<const float4*>(row + ((j0 ^ (p & 7)) << 4));
                     const float4 hi4 = *reinterpret_cast<const float4*>(row + (((j0 + 1) ^ (p & 7)) << 4));
                     x[i][0] = lo4.x;
@@ -547,13 +559,13 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
                 __syncwarp();   // the warp's rows are read before any is overwritten
                 const int h = oc >> 3, cc = oc & 7;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int p = 8 * cw + 2 * i + (lane >> 4);
+                for (int i = 0; i < 2; ++i) {
+                    const int p = 4 * cw + 2 * i + (lane >> 4);
                     uint4 f1, f2;
                     split8(x[i], f1, f2);
-                    const int o = 8192 * h + p * 128 + ((cc ^ (p & 7)) << 4);
+                    const int o = 4096 * h + p * 128 + ((cc ^ (p & 7)) << 4);
                     *reinterpret_cast<uint4*>(base + o) = f1;
-                    *reinterpret_cast<uint4*>(base + 16384 + o) = f2;
+                    *reinterpret_cast<uint4*>(base + 8192 + o) = f2;
                 }
                 fence_proxy_async();   // generic writes, read by the tensor core
                 __syncwarp();
@@ -569,7 +581,7 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
             // start address is bits 0-13 (address / 16).
             constexpr uint32_t kIdFull = idesc_n(128), kIdLast = idesc_n(DB % 2 ? 64 : 128);
             const uint64_t w0 = sw128_desc(saddr(S.W[0][0]), 16, 1024);
-            const uint64_t f0 = sw128_desc(saddr(S.F[0]), 8192, 1024);
+            const uint64_t f0 = sw128_desc(saddr(S.F[0]), Sm::kBoxBytes, 1024);
             uint32_t wc = 0, fc = 0, ub = 0, qc = 0;
             bool ok = true;
             for (;;) {
@@ -584,9 +596,10 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
                     tc_fence_after();
                     const uint64_t wd1 = w0 + ((ws * NT * kAtomBytes) >> 4);
                     const uint64_t wd2 = wd1 + ((NT - 1) * kAtomBytes >> 4);
-                    for (int un = 0; un < U; ++un) {
+                    for (int un = 0; un < U && ok; ++un)
+                    for (int hf = 0; hf < Sm::kHalves; ++hf) {
                         const uint32_t u = ub + un, slot = u % kSlots;
-                        if (ka == 0 && u >= (uint32_t)kSlots &&
+                        if (ka == 0 && hf == 0 && u >= (uint32_t)kSlots &&
                             !agg_wait(abort_flag, a.status, &S.t_empty[slot], ((u / kSlots) - 1) & 1u)) {
                             ok = false;
                             break;
@@ -601,18 +614,21 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
                         const uint32_t dt = S.tmem_base + 128u * slot;
                         const uint64_t fd = f0 + ((s * Sm::kFStage) >> 4);
                         const uint32_t id = un == U - 1 ? kIdLast : kIdFull;
-                        // W1 F1 (+ W2 F1 + W1 F2 for NT = 2), 16 pixels per step
+                        // W1 F1 (+ W2 F1 + W1 F2 for NT = 2), 16 pixels per step; the unit
+                        // holds pixels kUnitPx hf .. of the atom
+                        constexpr int kKS = Sm::kUnitPx / 16;
 #pragma unroll
-                        for (int ks = 0; ks < 4; ++ks) {
-                            mma_bf16(dt, wd1 + 2 * ks, fd + 128 * ks, id, (ka > 0 || ks > 0) ? 1u : 0u);
+                        for (int ks = 0; ks < kKS; ++ks) {
+                            const uint32_t ka16 = kKS * hf + ks;   // 16-pixel step within the W atom
+                            mma_bf16(dt, wd1 + 2 * ka16, fd + 128 * ks, id, (ka > 0 || hf > 0 || ks > 0) ? 1u : 0u);
                             if (NT == 2) {
-                                mma_bf16(dt, wd2 + 2 * ks, fd + 128 * ks, id, 1u);
-                                mma_bf16(dt, wd1 + 2 * ks, fd + (16384 >> 4) + 128 * ks, id, 1u);
+                                mma_bf16(dt, wd2 + 2 * ka16, fd + 128 * ks, id, 1u);
+                                mma_bf16(dt, wd1 + 2 * ka16, fd + (8192 >> 4) + 128 * ks, id, 1u);
                             }
                         }
                         mma_commit(&S.f_empty[s]);
                         ++fc;
-                        if (ka == 3) mma_commit(&S.t_full[slot]);
+                        if (ka == 3 && hf == Sm::kHalves - 1) mma_commit(&S.t_full[slot]);
                     }
                     if (!ok) break;
                     mma_commit(&S.w_empty[ws]);
@@ -738,25 +754,25 @@ ludvig_status encode(CUtensorMap* map, CUtensorMapDataType type, const void* bas
     return LUDVIG_OK;
 }
 
-// Tensor map over features [nv, H, W, d]: one 64-pixel K atom (16 x 4 pixels)
-// of one view per box, 64 bfloat16 channels or 32 float32 channels (128-byte
+// Tensor map over features [nv, H, W, d]: 64 (bfloat16) or 32 (float32)
+// pixels of one view per box, 64 bfloat16 channels or 32 float32 channels (128-byte
 // rows either way), zero fill outside the image and past d.
 ludvig_status make_feature_map(CUtensorMap* map, const void* feats, int dtype, int nv, int width, int height,
                                int d) {
     const cuuint64_t es = dtype == LUDVIG_F32 ? 4 : 2;
     cuuint64_t dims[4] = {(cuuint64_t)d, (cuuint64_t)width, (cuuint64_t)height, (cuuint64_t)nv};
     cuuint64_t strides[3] = {(cuuint64_t)d * es, (cuuint64_t)width * d * es, (cuuint64_t)height * width * d * es};
-    cuuint32_t box[4] = {(cuuint32_t)(128 / es), 16, 4, 1};
+    cuuint32_t box[4] = {(cuuint32_t)(128 / es), 16, dtype == LUDVIG_F32 ? 2u : 4u, 1};
     return encode(map, dtype == LUDVIG_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                   feats, 4, dims, strides, box);
 }
 
-// Tensor map over chunk rows [cap * 128, 256] bfloat16: box of 64 pixels x 128
-// rows (one K atom of a chunk).
+// Tensor map over chunk rows [cap * 128, 256] bfloat16: box of 64 pixels x 32
+// rows (a quarter of one K atom of a chunk).
 ludvig_status make_w_map(CUtensorMap* map, const void* w, int64_t cap) {
     cuuint64_t dims[2] = {256, (cuuint64_t)cap * kCRows};
     cuuint64_t strides[1] = {(cuuint64_t)kRowBytes};
-    cuuint32_t box[2] = {64, (cuuint32_t)kCRows};
+    cuuint32_t box[2] = {64, 32};
     return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w, 2, dims, strides, box);
 }
 
