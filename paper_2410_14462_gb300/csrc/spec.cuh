@@ -266,13 +266,42 @@ __device__ __forceinline__ bool reaches_rect(float mx, float my, float ca, float
 __device__ __forceinline__ float block_x0(int tx, int w) { return (float)(tx * kTile + (w & 1) * 8) + 0.5f; }
 __device__ __forceinline__ float block_y0(int ty, int w) { return (float)(ty * kTile + (w >> 1) * 4) + 0.5f; }
 
-__device__ __forceinline__ uint32_t block_mask(const Reach& R, float mx, float my, float ca, float cb, float cc,
+// Per pixel-row band of the tile (4 rows of pixel centres), the x-range of the
+// ellipse {Q <= thr} (Q = a dx^2 + 2 b dx dy + c dy^2, d = mean - pixel
+// centre) over the band, in closed form: for a fixed dy the dx-range is
+// (-b dy -+ sqrt(thr a - det dy^2)) / a (det = a c - b^2); over an interval of
+// dy its largest dx is the ellipse's global one, sqrt(thr c / det) at
+// dy = -b dx / c, if that lies inside, else an end point (the upper boundary
+// is concave in dy), and likewise for the smallest.  Both ranges are widened
+// for rounding, so the mask keeps every block that the float32 per-pixel test
+// can reach (it only steers work, it decides no weight).
+__device__ __forceinline__ uint32_t block_mask(const Reach& R, float mx, float my, float a, float b, float c,
                                                int tx, int ty) {
+    if (!R.possible) return 0u;
+    const float thr = R.thr;
+    const float det = a * c - b * b;
+    if (!(det > 0.0f) || !(thr > 0.0f)) return 0xffu;
+    const float inv_a = 1.0f / a;
+    const float umax = sqrtf(thr * c / det);                   // largest |dx| on the ellipse
+    const float wmax = sqrtf(thr * a / det) * 1.0001f + 0.02f; // largest |dy|, widened
+    const float ws = -b * umax / c;                            // dy where dx = +umax (-ws for -umax)
+    const float thra = thr * a;
+    const float epsx = 1e-3f * (umax + 1.0f) + 0.02f;
+    const float xt = (float)(tx * kTile) + 0.5f, yt = (float)(ty * kTile) + 0.5f;
     uint32_t m = 0u;
-#pragma unroll 1
-    for (int w = 0; w < 8; ++w) {
-        const float xa = block_x0(tx, w), ya = block_y0(ty, w);
-        if (reaches_rect(R, mx, my, ca, cb, cc, xa, xa + 7.0f, ya, ya + 3.0f)) m |= 1u << w;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float ylo = yt + (float)(4 * k), yhi = ylo + 3.0f;
+        const float w0 = fmaxf(my - yhi, -wmax), w1 = fminf(my - ylo, wmax);
+        if (w0 > w1) continue;
+        const float s0 = sqrtf(fmaxf(thra - det * w0 * w0, 0.0f));
+        const float s1 = sqrtf(fmaxf(thra - det * w1 * w1, 0.0f));
+        const float hi = (ws >= w0 && ws <= w1) ? umax : fmaxf((-b * w0 + s0) * inv_a, (-b * w1 + s1) * inv_a);
+        const float lo = (-ws >= w0 && -ws <= w1) ? -umax : fminf((-b * w0 - s0) * inv_a, (-b * w1 - s1) * inv_a);
+        // pixel-centre x = mx - dx
+        const float xl = mx - hi - epsx, xr = mx - lo + epsx;
+        if (xr >= xt && xl <= xt + 7.0f) m |= 1u << (2 * k);
+        if (xr >= xt + 8.0f && xl <= xt + 15.0f) m |= 1u << (2 * k + 1);
     }
     return m;
 }
