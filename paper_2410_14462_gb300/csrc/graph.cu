@@ -301,18 +301,22 @@ __global__ void k_norms(const float* __restrict__ f, int64_t n, int df, float* _
 }
 
 // One warp per row: compact the distinct columns, weight every edge, then
-// threshold / normalise the row.
-__global__ void __launch_bounds__(256) k_weights(const uint32_t* __restrict__ tcol,
+// threshold / normalise the row (any df).  Row r of the launch is Gaussian
+// order[r] (grid-cell order, so that neighbours' feature rows stay in L2), or
+// r when order is null.
+__global__ void __launch_bounds__(256) k_edge_weights_any(const uint32_t* __restrict__ tcol,
                                                 const uint32_t* __restrict__ tptr,
                                                 const uint32_t* __restrict__ tcnt,
                                                 const int64_t* __restrict__ row_ptr,
                                                 const float* __restrict__ x, const float* __restrict__ f,
                                                 const float* __restrict__ nrm, int64_t n, int df,
                                                 float inv_h, float binarize, int row_normalize,
+                                                const uint32_t* __restrict__ order,
                                                 int32_t* __restrict__ col, float* __restrict__ val) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * 8 + warp;
-    if (i >= n) return;
+    const int64_t r = (int64_t)blockIdx.x * 8 + warp;
+    if (r >= n) return;
+    const int64_t i = order ? (int64_t)order[r] : r;
     const uint32_t* row = tcol + tptr[i];
     const uint32_t c = tcnt[i];
     const int64_t o0 = row_ptr[i];
@@ -348,9 +352,95 @@ __global__ void __launch_bounds__(256) k_weights(const uint32_t* __restrict__ tc
     }
 }
 
-__global__ void k_ucnt_to_u64(const uint32_t* __restrict__ u, int64_t n, int64_t* __restrict__ out) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = u[i];
+// Same for df <= 32 kR: one warp per row with f_i in registers; the row's
+// distinct columns are found 32 at a time (a sorted row repeats a column for
+// mutual neighbours) and dotted two at a time; the row sum normalises in
+// parallel.
+template <int kR>
+__global__ void __launch_bounds__(256) k_edge_weights(const uint32_t* __restrict__ tcol,
+                                                     const uint32_t* __restrict__ tptr,
+                                                     const uint32_t* __restrict__ tcnt,
+                                                     const int64_t* __restrict__ row_ptr,
+                                                     const float* __restrict__ x, const float* __restrict__ f,
+                                                     const float* __restrict__ nrm, int64_t n, int df,
+                                                     float inv_h, float binarize, int row_normalize,
+                                                     const uint32_t* __restrict__ order,
+                                                     int32_t* __restrict__ col, float* __restrict__ val) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * 8 + warp;
+    if (r >= n) return;   // whole warp
+    const int64_t i = order ? (int64_t)order[r] : r;
+    const uint32_t* row = tcol + tptr[i];
+    const uint32_t c = tcnt[i];
+    const int64_t o0 = row_ptr[i];
+    const float xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
+    const float ni = nrm[i];
+    float fr[kR];
+#pragma unroll
+    for (int k = 0; k < kR; ++k) {
+        const int ch = lane + 32 * k;
+        fr[k] = ch < df ? f[i * df + ch] : 0.f;
+    }
+    auto weight = [&](uint32_t j, float dot) {
+        const float ex = x[3 * j] - xi, ey = x[3 * j + 1] - yi, ez = x[3 * j + 2] - zi;
+        const float d2 = ex * ex + ey * ey + ez * ez;
+        const float den = ni * nrm[j];
+        const float cs = den > 0.f ? dot / den : 0.f;
+        float w = expf(-d2 * inv_h) * fmaxf(0.f, cs);
+        if (binarize > 0.f) w = w > binarize ? 1.f : 0.f;
+        return w;
+    };
+    int64_t o = o0;
+    float rsum = 0.f;   // lane 0
+    for (uint32_t t0 = 0; t0 < c; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        const uint32_t j = t < c ? row[t] : 0u;
+        const bool keep = t < c && !(t > 0 && row[t - 1] == j);
+        uint32_t m = __ballot_sync(0xffffffffu, keep);
+        while (m) {
+            const int l0 = __ffs(m) - 1;
+            m &= m - 1u;
+            const bool two = m != 0u;
+            const int l1 = two ? __ffs(m) - 1 : l0;
+            if (two) m &= m - 1u;
+            const uint32_t j0 = __shfl_sync(0xffffffffu, j, l0), j1 = __shfl_sync(0xffffffffu, j, l1);
+            const float* f0 = f + (int64_t)j0 * df;
+            const float* f1 = f + (int64_t)j1 * df;
+            float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+            for (int k = 0; k < kR; ++k) {
+                const int ch = lane + 32 * k;
+                if (ch < df) {
+                    d0 = fmaf(fr[k], f0[ch], d0);
+                    d1 = fmaf(fr[k], f1[ch], d1);
+                }
+            }
+#pragma unroll
+            for (int sft = 16; sft > 0; sft >>= 1) {
+                d0 += __shfl_xor_sync(0xffffffffu, d0, sft);
+                d1 += __shfl_xor_sync(0xffffffffu, d1, sft);
+            }
+            if (lane == 0) {
+                const float w0 = weight(j0, d0);
+                col[o] = (int32_t)j0;
+                val[o] = w0;
+                rsum += w0;
+                if (two) {
+                    const float w1 = weight(j1, d1);
+                    col[o + 1] = (int32_t)j1;
+                    val[o + 1] = w1;
+                    rsum += w1;
+                }
+            }
+            o += two ? 2 : 1;
+        }
+    }
+    if (row_normalize) {
+        rsum = __shfl_sync(0xffffffffu, rsum, 0);
+        const float inv = rsum > 0.f ? 1.0f / rsum : 0.f;
+        __syncwarp();
+        for (int64_t e = o0 + lane; e < o; e += 32) val[e] *= inv;
+    }
 }
 
 // exclusive scan into int64 row pointers (u32 scan + widening is enough while nnz < 2^32)
@@ -448,8 +538,11 @@ __global__ void __launch_bounds__(256) k_spmv_scaled(const int64_t* __restrict__
     }
 }
 
-ludvig_status knn_impl(ludvig_scene* s, int k, int32_t* nbr, cudaStream_t st) {
+// *order (if given) receives the points' indices sorted by grid cell (valid
+// until the scene's workspace is reused), or null.
+ludvig_status knn_impl(ludvig_scene* s, int k, int32_t* nbr, cudaStream_t st, const uint32_t** order = nullptr) {
     Arena& ws = s->ws;
+    if (order) *order = nullptr;
     const int64_t n = s->n;
     float* bb;
     LV_TRY(ws.get("knn.bbox", 8, &bb));
@@ -515,6 +608,7 @@ ludvig_status knn_impl(ludvig_scene* s, int k, int32_t* nbr, cudaStream_t st) {
         LV_TRY(ws.get("knn.pts", (size_t)n, &pts));
         k_gather_sorted<<<grid_for(n, 256), 256, 0, st>>>(s->means, sv, n, pts);
         LV_LAUNCH();
+        if (order) *order = sv;
         const unsigned g = grid_for(n, 128);
         if (k <= 8) k_knn<8><<<g, 128, 0, st>>>(pts, n, gr, cells, k, nbr);
         else if (k <= 16) k_knn<16><<<g, 128, 0, st>>>(pts, n, gr, cells, k, nbr);
@@ -589,9 +683,10 @@ extern "C" ludvig_status ludvig_graph_build(ludvig_scene_t scene, int32_t k, con
     GB_TRY(ws.get("g.tot", 2, &tot_d));
     utot_d = tot_d + 1;
     GB_TRY(ws.get("g.nrm", (size_t)n, &nrm));
+    const uint32_t* sorder = nullptr;   // rows in grid-cell order: neighbours' feature rows stay in L2
     {
         StageScope scope(LUDVIG_STAGE_KNN, st);
-        GB_TRY(knn_impl(scene, k, nbr, st));
+        GB_TRY(knn_impl(scene, k, nbr, st, &sorder));
     }
     StageScope gscope(LUDVIG_STAGE_GRAPH, st);
     if (cudaMemsetAsync(indeg, 0, sizeof(uint32_t) * n, st) != cudaSuccess ||
@@ -634,8 +729,21 @@ extern "C" ludvig_status ludvig_graph_build(ludvig_scene_t scene, int32_t k, con
         set_error("graph allocation failed");
         return fail(LUDVIG_ERR_OOM);
     }
-    k_weights<<<grid_for(n, 8), 256, 0, st>>>(tcol, tptr, cnt, g->row_ptr, scene->means, feats, nrm, n,
-                                              df, 1.0f / spatial_h, binarize, row_normalize, g->col, g->val);
+    {
+        const unsigned gb = grid_for(n, 8);
+        const float ih = 1.0f / spatial_h;
+#define LV_EW(R) k_edge_weights<R><<<gb, 256, 0, st>>>(tcol, tptr, cnt, g->row_ptr, scene->means, feats, nrm, n, \
+                                                        df, ih, binarize, row_normalize, sorder, g->col, g->val)
+        if (df <= 32) LV_EW(1);
+        else if (df <= 128) LV_EW(4);
+        else if (df <= 256) LV_EW(8);
+        else if (df <= 384) LV_EW(12);
+        else if (df <= 512) LV_EW(16);
+        else
+            k_edge_weights_any<<<gb, 256, 0, st>>>(tcol, tptr, cnt, g->row_ptr, scene->means, feats, nrm, n, df, ih,
+                                                   binarize, row_normalize, sorder, g->col, g->val);
+#undef LV_EW
+    }
     count_launch();
     if (cudaGetLastError() != cudaSuccess) {
         set_error("graph kernels failed to launch");
