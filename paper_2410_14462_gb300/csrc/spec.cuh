@@ -266,53 +266,99 @@ __device__ __forceinline__ bool reaches_rect(float mx, float my, float ca, float
 __device__ __forceinline__ float block_x0(int tx, int w) { return (float)(tx * kTile + (w & 1) * 8) + 0.5f; }
 __device__ __forceinline__ float block_y0(int ty, int w) { return (float)(ty * kTile + (w >> 1) * 4) + 0.5f; }
 
-// Per pixel-row band of the tile (4 rows of pixel centres), the x-range of the
-// ellipse {Q <= thr} (Q = a dx^2 + 2 b dx dy + c dy^2, d = mean - pixel
-// centre) over the band, in closed form: for a fixed dy the dx-range is
-// (-b dy -+ sqrt(thr a - det dy^2)) / a (det = a c - b^2); over an interval of
-// dy its largest dx is the ellipse's global one, sqrt(thr c / det) at
-// dy = -b dx / c, if that lies inside, else an end point (the upper boundary
-// is concave in dy), and likewise for the smallest.  Both ranges are widened
-// for rounding, so the mask keeps every block that the float32 per-pixel test
-// can reach (it only steers work, it decides no weight).
+// The pixel-centre x-range of the ellipse {Q <= thr} (Q = a dx^2 + 2 b dx dy
+// + c dy^2, d = mean - pixel centre) over a band of pixel-centre rows, in
+// closed form: for a fixed dy the dx-range is (-b dy -+ sqrt(thr a - det dy^2))
+// / a (det = a c - b^2); over an interval of dy its largest dx is the
+// ellipse's global one, sqrt(thr c / det) at dy = -b dx / c, if that lies
+// inside, else an end point (the upper boundary is concave in dy), and likewise
+// for the smallest.  Both ranges are widened for rounding (thr itself carries
+// the slack of reach_prep), so a pixel that the float32 per-pixel test of
+// Eq. 1 can give alpha >= 1/255 lies inside.  Every rounding is explicit:
+// k_project and k_emit_pairs must take the same tile decisions.
+struct EllipseX {
+    float b, det, thra, umax, wmax, ws, inv_a, epsx;
+    int state;   // 0: reaches nothing, 1: ranges valid, 2: degenerate (take everything)
+};
+
+__device__ __forceinline__ EllipseX ellipse_prep(const Reach& R, float a, float b, float c) {
+    EllipseX E{};
+    if (!R.possible) return E;
+    const float thr = R.thr;
+    E.b = b;
+    E.det = __fsub_rn(__fmul_rn(a, c), __fmul_rn(b, b));
+    if (!(E.det > 0.0f) || !(thr > 0.0f) || !(a > 0.0f) || !(c > 0.0f)) {
+        E.state = 2;
+        return E;
+    }
+    E.state = 1;
+    E.inv_a = __frcp_rn(a);
+    E.umax = __fsqrt_rn(__fdiv_rn(__fmul_rn(thr, c), E.det));
+    E.wmax = __fadd_rn(__fmul_rn(__fsqrt_rn(__fdiv_rn(__fmul_rn(thr, a), E.det)), 1.0001f), 0.02f);
+    E.ws = __fdiv_rn(__fmul_rn(-b, E.umax), c);
+    E.thra = __fmul_rn(thr, a);
+    E.epsx = __fadd_rn(__fmul_rn(1e-3f, __fadd_rn(E.umax, 1.0f)), 0.02f);
+    return E;
+}
+
+// False when the rows [ylo, yhi] miss the ellipse (state 1 only).
+__device__ __forceinline__ bool ellipse_x_range(const EllipseX& E, float mx, float my, float ylo, float yhi,
+                                                float& xl, float& xr) {
+    const float w0 = fmaxf(__fsub_rn(my, yhi), -E.wmax), w1 = fminf(__fsub_rn(my, ylo), E.wmax);
+    if (w0 > w1) return false;
+    const float s0 = __fsqrt_rn(fmaxf(__fsub_rn(E.thra, __fmul_rn(E.det, __fmul_rn(w0, w0))), 0.0f));
+    const float s1 = __fsqrt_rn(fmaxf(__fsub_rn(E.thra, __fmul_rn(E.det, __fmul_rn(w1, w1))), 0.0f));
+    const float bw0 = __fmul_rn(-E.b, w0), bw1 = __fmul_rn(-E.b, w1);
+    const float hi = (E.ws >= w0 && E.ws <= w1)
+                         ? E.umax
+                         : fmaxf(__fmul_rn(__fadd_rn(bw0, s0), E.inv_a), __fmul_rn(__fadd_rn(bw1, s1), E.inv_a));
+    const float lo = (-E.ws >= w0 && -E.ws <= w1)
+                         ? -E.umax
+                         : fminf(__fmul_rn(__fsub_rn(bw0, s0), E.inv_a), __fmul_rn(__fsub_rn(bw1, s1), E.inv_a));
+    xl = __fsub_rn(__fsub_rn(mx, hi), E.epsx);   // pixel-centre x = mx - dx
+    xr = __fadd_rn(__fsub_rn(mx, lo), E.epsx);
+    return true;
+}
+
+// Bit w of block_mask: the Gaussian can reach alpha >= 1/255 in the 8x4 block
+// w of tile (tx, ty) (per 4-row band, its x-range against the two halves).
 __device__ __forceinline__ uint32_t block_mask(const Reach& R, float mx, float my, float a, float b, float c,
                                                int tx, int ty) {
-    if (!R.possible) return 0u;
-    const float thr = R.thr;
-    const float det = a * c - b * b;
-    if (!(det > 0.0f) || !(thr > 0.0f)) return 0xffu;
-    const float inv_a = 1.0f / a;
-    const float umax = sqrtf(thr * c / det);                   // largest |dx| on the ellipse
-    const float wmax = sqrtf(thr * a / det) * 1.0001f + 0.02f; // largest |dy|, widened
-    const float ws = -b * umax / c;                            // dy where dx = +umax (-ws for -umax)
-    const float thra = thr * a;
-    const float epsx = 1e-3f * (umax + 1.0f) + 0.02f;
+    const EllipseX E = ellipse_prep(R, a, b, c);
+    if (E.state != 1) return E.state == 2 ? 0xffu : 0u;
     const float xt = (float)(tx * kTile) + 0.5f, yt = (float)(ty * kTile) + 0.5f;
     uint32_t m = 0u;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const float ylo = yt + (float)(4 * k), yhi = ylo + 3.0f;
-        const float w0 = fmaxf(my - yhi, -wmax), w1 = fminf(my - ylo, wmax);
-        if (w0 > w1) continue;
-        const float s0 = sqrtf(fmaxf(thra - det * w0 * w0, 0.0f));
-        const float s1 = sqrtf(fmaxf(thra - det * w1 * w1, 0.0f));
-        const float hi = (ws >= w0 && ws <= w1) ? umax : fmaxf((-b * w0 + s0) * inv_a, (-b * w1 + s1) * inv_a);
-        const float lo = (-ws >= w0 && -ws <= w1) ? -umax : fminf((-b * w0 - s0) * inv_a, (-b * w1 - s1) * inv_a);
-        // pixel-centre x = mx - dx
-        const float xl = mx - hi - epsx, xr = mx - lo + epsx;
+        const float ylo = yt + (float)(4 * k);
+        float xl, xr;
+        if (!ellipse_x_range(E, mx, my, ylo, ylo + 3.0f, xl, xr)) continue;
         if (xr >= xt && xl <= xt + 7.0f) m |= 1u << (2 * k);
         if (xr >= xt + 8.0f && xl <= xt + 15.0f) m |= 1u << (2 * k + 1);
     }
     return m;
 }
 
-// A (Gaussian, tile) pair is kept when the Gaussian can reach alpha >= 1/255
-// at some pixel centre of the tile; a Gaussian that cannot is skipped at every
-// pixel of the tile, so leaving it out of the tile's list changes no weight.
-__device__ __forceinline__ bool tile_used(const Reach& R, float mx, float my, float ca, float cb, float cc, int tx,
-                                          int ty) {
-    const float xa = (float)(tx * kTile) + 0.5f, ya = (float)(ty * kTile) + 0.5f;
-    return reaches_rect(R, mx, my, ca, cb, cc, xa, xa + 15.0f, ya, ya + 15.0f);
+// Tiles of row ty that the Gaussian reaches (a (Gaussian, tile) pair is kept
+// when it can give alpha >= 1/255 at some pixel centre of the tile; leaving
+// the others out of the tile lists changes no weight): columns [c0, c1) within
+// the tile rectangle's [x0, x1).
+__device__ __forceinline__ void tile_row_range(const EllipseX& E, float mx, float my, int ty, int x0, int x1,
+                                               int& c0, int& c1) {
+    c0 = x0;
+    c1 = x1;
+    if (E.state == 2) return;
+    float xl = 0.f, xr = -1.f;
+    const float ylo = (float)(ty * kTile) + 0.5f;
+    if (E.state == 0 || !ellipse_x_range(E, mx, my, ylo, ylo + 15.0f, xl, xr)) {
+        c1 = c0;
+        return;
+    }
+    // tile tx holds pixel centres x in [16 tx + 0.5, 16 tx + 15.5]
+    const float f0 = fmaxf(ceilf(__fmul_rn(__fsub_rn(xl, 15.5f), 0.0625f)), (float)x0);
+    const float f1 = fminf(__fadd_rn(floorf(__fmul_rn(__fsub_rn(xr, 0.5f), 0.0625f)), 1.0f), (float)x1);
+    c0 = (int)f0;
+    c1 = f1 > f0 ? (int)f1 : c0;
 }
 
 // One entry of a tile's depth-ordered list as the compositing kernels read it:

@@ -73,69 +73,6 @@ __global__ void k_scene_init(const float* __restrict__ means, const float* __res
 
 // ------------------------------------------------------------ 1. project
 
-// Shared-memory view of a warp's 32 Gaussians for the cooperative tile walk
-// of k_project and k_emit_pairs: the warp flattens the lanes' tile
-// rectangles and tests 32 tiles per round, so one large rectangle does not
-// leave the other lanes idle.
-struct WarpTiles {
-    float4 g[32];       // mx, my, conic a, conic b
-    float4 h[32];       // conic c, reach threshold, 1/a, 1/c
-    int4 r[32];         // x0, y0, width in tiles, reach possible
-    uint32_t ex[32];    // exclusive prefix of the rectangles' tile counts
-    uint32_t cnt[32];   // tiles used so far
-    uint32_t off[32];   // k_emit_pairs: first pair slot, Gaussian index, key base
-    uint32_t val[32];
-    uint32_t kbase[32];
-};
-
-__device__ __forceinline__ void warp_tiles_put(WarpTiles& W, int lane, float mx, float my, float ca, float cb,
-                                               float cc, const Reach& R, int x0, int y0, int w) {
-    W.g[lane] = make_float4(mx, my, ca, cb);
-    W.h[lane] = make_float4(cc, R.thr, R.inv_ca, R.inv_cc);
-    W.r[lane] = make_int4(x0, y0, w, R.possible ? 1 : 0);
-    W.cnt[lane] = 0u;
-}
-
-// Exclusive prefix of area over the warp into W.ex; returns the warp total.
-__device__ __forceinline__ uint32_t warp_tiles_scan(WarpTiles& W, int lane, uint32_t area) {
-    uint32_t incl = area;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    W.ex[lane] = incl - area;
-    __syncwarp();
-    return __shfl_sync(0xffffffffu, incl, 31);
-}
-
-// Tile t (< total) of the flattened rectangles: its owner lane and tile.
-__device__ __forceinline__ void warp_tile_locate(const WarpTiles& W, uint32_t t, int& own, int& tx, int& ty) {
-    int lo = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1)
-        if (W.ex[lo + step] <= t) lo += step;   // last lane whose range starts at or before t
-    own = lo;
-    const int4 r = W.r[own];
-    const uint32_t local = t - W.ex[own];
-    tx = r.x + (int)(local % (uint32_t)r.z);
-    ty = r.y + (int)(local / (uint32_t)r.z);
-}
-
-// ... and whether the owner's Gaussian can reach it (tile_used).
-__device__ __forceinline__ bool warp_tile_test(const WarpTiles& W, uint32_t t, int& own, int& tx, int& ty) {
-    warp_tile_locate(W, t, own, tx, ty);
-    const int4 r = W.r[own];
-    const float4 g = W.g[own], h = W.h[own];
-    Reach R;
-    R.thr = h.y;
-    R.inv_ca = h.z;
-    R.inv_cc = h.w;
-    R.cb2 = __fmul_rn(2.0f, g.w);
-    R.possible = r.w != 0;
-    return tile_used(R, g.x, g.y, g.z, g.w, h.x, tx, ty);
-}
-
 __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ geo, const float4* __restrict__ cov_a,
                           const float2* __restrict__ cov_b, int64_t n, int64_t npad, int nv,
                           CamBatch cb, int width, int height, float4* __restrict__ rec_a,
@@ -143,9 +80,7 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ geo,
                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                           uint32_t* __restrict__ ntile, float* __restrict__ dbg_rec,
                           int32_t* __restrict__ dbg_rect, int prune) {
-    __shared__ WarpTiles WT[8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // every warp is full: nv * npad is a multiple of the block size
+    // every block is full: nv * npad is a multiple of the block size
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int v = (int)(idx / npad);
     const int64_t i = idx - (int64_t)v * npad;
@@ -170,24 +105,15 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ geo,
     const bool vis = real && P.visible;
     const uint32_t area = vis ? (uint32_t)((P.x1 - P.x0) * (P.y1 - P.y0)) : 0u;
     uint32_t count = area;
-    if (prune) {
-        // only tiles that the alpha >= 1/255 ellipse can reach
-        WarpTiles& W = WT[warp];
-        const Reach R = reach_prep(vis ? P.ca : 1.f, vis ? P.cb : 0.f, vis ? P.cc : 1.f, vis ? op : 0.f);
-        warp_tiles_put(W, lane, P.mx, P.my, P.ca, P.cb, P.cc, R, P.x0, P.y0, vis ? P.x1 - P.x0 : 1);
-        const uint32_t total = warp_tiles_scan(W, lane, area);
-        for (uint32_t t0 = 0; t0 < total; t0 += 32) {
-            const uint32_t t = t0 + lane;
-            int own = 0, tx = 0, ty = 0;
-            const bool used = t < total && warp_tile_test(W, t, own, tx, ty);
-            // one shared-memory add per owner and round
-            const uint32_t peers = __match_any_sync(0xffffffffu, t < total ? own : -1);
-            const uint32_t u = __ballot_sync(0xffffffffu, used) & peers;
-            if (used && (u & ((1u << lane) - 1u)) == 0) W.cnt[own] += __popc(u);
-            __syncwarp();
+    if (prune && vis) {
+        // only tiles that the alpha >= 1/255 ellipse can reach, row by row
+        const EllipseX E = ellipse_prep(reach_prep(P.ca, P.cb, P.cc, op), P.ca, P.cb, P.cc);
+        count = 0;
+        for (int ty = P.y0; ty < P.y1; ++ty) {
+            int c0, c1;
+            tile_row_range(E, P.mx, P.my, ty, P.x0, P.x1, c0, c1);
+            count += (uint32_t)(c1 - c0);
         }
-        count = W.cnt[lane];
-        __syncwarp();
     }
     keys[idx] = count ? __float_as_uint(P.z) : 0xffffffffu;
     vals[idx] = (uint32_t)i;
@@ -220,69 +146,38 @@ __global__ void k_gather_counts(const uint32_t* __restrict__ skeys, const uint32
     cnt[idx] = skeys[idx] == 0xffffffffu ? 0u : ntile[v * npad + svals[idx]];
 }
 
-__global__ void __launch_bounds__(256) k_emit_pairs(const uint32_t* __restrict__ svals, const uint32_t* __restrict__ cnt,
+__global__ void k_emit_pairs(const uint32_t* __restrict__ svals, const uint32_t* __restrict__ cnt,
                              const uint32_t* __restrict__ off, const uint2* __restrict__ rect,
                              const float4* __restrict__ rec_a, const float2* __restrict__ rec_b,
                              int64_t n, int64_t npad, int64_t total, int TX, int ntiles, int prune,
                              uint32_t sentinel, uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval) {
-    __shared__ WarpTiles WT[8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    // every warp is full: total is a multiple of the block size
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
     const uint32_t c = cnt[idx];
-    WarpTiles& W = WT[warp];
-    uint32_t area = 0;
-    if (c > 0) {
-        const int64_t v = idx / npad;
-        const uint32_t i = svals[idx];
-        const uint2 r = rect[v * n + i];
-        const int x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff, y1 = r.y >> 16;
-        const float4 ra = rec_a[v * n + i];
-        const float2 rb = rec_b[v * n + i];
-        const Reach R = reach_prep(ra.z, ra.w, rb.x, rb.y);
-        warp_tiles_put(W, lane, ra.x, ra.y, ra.z, ra.w, rb.x, R, x0, y0, x1 - x0);
-        W.off[lane] = off[idx];
-        W.val[lane] = i;
-        W.kbase[lane] = (uint32_t)(v * ntiles);
-        area = (uint32_t)((x1 - x0) * (y1 - y0));
-    } else {
-        W.cnt[lane] = 0u;
-    }
-    const uint32_t tot = warp_tiles_scan(W, lane, area);
-    for (uint32_t t0 = 0; t0 < tot; t0 += 32) {
-        const uint32_t t = t0 + lane;
-        int own = 0, tx = 0, ty = 0;
-        bool used = false;
-        if (t < tot) {
-            if (prune) {
-                used = warp_tile_test(W, t, own, tx, ty);
-            } else {
-                warp_tile_locate(W, t, own, tx, ty);
-                used = true;
-            }
+    if (c == 0) return;
+    const int64_t v = idx / npad;
+    const uint32_t i = svals[idx];
+    const uint2 r = rect[v * n + i];
+    const int x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff, y1 = r.y >> 16;
+    const float4 ra = rec_a[v * n + i];
+    const float2 rb = rec_b[v * n + i];
+    EllipseX E{};
+    E.state = 2;   // unpruned: every tile of the rectangle
+    if (prune) E = ellipse_prep(reach_prep(ra.z, ra.w, rb.x, rb.y), ra.z, ra.w, rb.x);
+    uint32_t o = off[idx];
+    const uint32_t end = o + c;   // never write past the counted slots
+    const uint32_t base = (uint32_t)(v * ntiles);
+    for (int ty = y0; ty < y1 && o < end; ++ty) {
+        int c0, c1;
+        tile_row_range(E, ra.x, ra.y, ty, x0, x1, c0, c1);
+        for (int tx = c0; tx < c1 && o < end; ++tx, ++o) {
+            pkey[o] = base + (uint32_t)(ty * TX + tx);
+            pval[o] = i;
         }
-        // slots in tile order within each owner: rank among this round's used tiles
-        const uint32_t peers = __match_any_sync(0xffffffffu, t < tot ? own : -1);
-        const uint32_t u = __ballot_sync(0xffffffffu, used) & peers;
-        const uint32_t before = W.cnt[own];
-        if (used) {
-            const uint32_t slot = before + __popc(u & lt_mask);
-            // never write past the counted slots of the owner
-            if (slot < cnt[blockIdx.x * (int64_t)blockDim.x + warp * 32 + own]) {
-                const uint32_t o = W.off[own] + slot;
-                pkey[o] = W.kbase[own] + (uint32_t)(ty * TX + tx);
-                pval[o] = W.val[own];
-            }
-        }
-        __syncwarp();
-        if (used && (u & lt_mask) == 0) W.cnt[own] = before + __popc(u);
-        __syncwarp();
     }
-    // unreachable when both kernels agree; keeps the keys defined
-    for (uint32_t p = W.cnt[lane]; p < c; ++p) {
-        pkey[W.off[lane] + p] = sentinel;
-        pval[W.off[lane] + p] = 0u;
+    for (; o < end; ++o) {   // unreachable when both kernels agree; keeps the keys defined
+        pkey[o] = sentinel;
+        pval[o] = 0u;
     }
 }
 
