@@ -237,43 +237,75 @@ __global__ void __launch_bounds__(256, 4) k_weights(WeightsArgs a) {
         const uint32_t rowmask = S.rowmask[buf];
         const int nnew = __popc(rowmask);
         const int cur = S.cur_chunk, nxt = S.next_chunk, cstart = S.cur_start;
-        // the staging row of the i-th new Gaussian goes to tile row nrows + i
-        // (chunk cur, or nxt past its 128 rows), 16 bytes per thread, one warp
-        // per row and term; the staging row is cleared behind it, and the
-        // row's sum of the term (the bfloat16 values the product uses) is
-        // kept for den
-        const int per_term = nnew * 32;
-        for (int e = tid; e < NT * per_term; e += 256) {   // NT * per_term % 32 == 0: whole warps
-            const int t = e / per_term, rem = e - t * per_term;
-            const int i = rem >> 5, c16 = rem & 31;
-            const int j = (int)__fns(rowmask, 0u, i + 1);
-            int local = nrows + i - cstart, ch = cur;
-            if (local >= kCRows) {
-                local -= kCRows;
-                ch = nxt;
-            }
-            uint4* src = reinterpret_cast<uint4*>(&S.stage[t][j * kRowBytes + c16 * 16]);
-            const uint4 v4 = *src;
-            if (ch >= 0 && ch < a.cap) {
-                uint8_t* dst = (t == 0 ? a.wg1 : a.wg2) + (size_t)ch * kChunkBytes + local * kRowBytes + c16 * 16;
-                *reinterpret_cast<uint4*>(dst) = v4;
-            }
-            *src = make_uint4(0u, 0u, 0u, 0u);
-            const uint32_t wv[4] = {v4.x, v4.y, v4.z, v4.w};
-            float sden = 0.f;
+        // the staging row of the i-th new Gaussian (the i-th set bit j of the
+        // row mask) goes to tile row nrows + i (chunk cur, or nxt past its 128
+        // rows), 16 bytes per lane, one warp per row and term; the staging row
+        // is cleared behind, the row's sum of each term (the bfloat16 values the
+        // product uses) is kept for den, and the Gaussian id is recorded
+        if constexpr (NT == 2) {
+            // warp i % 8 takes row i, both terms
+            uint32_t m = rowmask;
+            for (int i = 0; m != 0u; ++i, m &= m - 1u) {
+                if ((i & 7) != warp) continue;
+                const int j = __ffs(m) - 1;
+                int local = nrows + i - cstart, ch = cur;
+                if (local >= kCRows) {
+                    local -= kCRows;
+                    ch = nxt;
+                }
+                const bool keep = ch >= 0 && ch < a.cap;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) sden += __uint_as_float(wv[k] << 16) + __uint_as_float(wv[k] & 0xffff0000u);
+                for (int t = 0; t < NT; ++t) {
+                    uint4* src = reinterpret_cast<uint4*>(&S.stage[t][j * kRowBytes + lane * 16]);
+                    const uint4 v4 = *src;
+                    if (keep) {
+                        uint8_t* dst = (t == 0 ? a.wg1 : a.wg2) + (size_t)ch * kChunkBytes + local * kRowBytes + lane * 16;
+                        *reinterpret_cast<uint4*>(dst) = v4;
+                    }
+                    *src = make_uint4(0u, 0u, 0u, 0u);
+                    const uint32_t wv[4] = {v4.x, v4.y, v4.z, v4.w};
+                    float sden = 0.f;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sden += __shfl_xor_sync(0xffffffffu, sden, o);
-            if (lane == 0 && ch >= 0 && ch < a.cap) a.chunk_den[((size_t)ch * kCRows + local) * NT + t] = sden;
-        }
-        if (tid < kTcBatch && ((rowmask >> tid) & 1u)) {
-            int local = nrows + __popc(rowmask & lt_mask) - cstart, ch = cur;
-            if (local >= kCRows) {
-                local -= kCRows;
-                ch = nxt;
+                    for (int k = 0; k < 4; ++k)
+                        sden += __uint_as_float(wv[k] << 16) + __uint_as_float(wv[k] & 0xffff0000u);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) sden += __shfl_xor_sync(0xffffffffu, sden, o);
+                    if (lane == 0 && keep) a.chunk_den[((size_t)ch * kCRows + local) * NT + t] = sden;
+                }
+                if (lane == 0 && keep) a.chunk_gid[(size_t)ch * kCRows + local] = rec[j].gid;
             }
-            if (ch >= 0 && ch < a.cap) a.chunk_gid[(size_t)ch * kCRows + local] = rec[tid].gid;
+        } else {
+            // warp w takes row w (row i of the 32 at most: warp i % 8 on pass i / 8)
+            for (int e = tid; e < nnew * 32; e += 256) {
+                const int i = e >> 5;
+                const int j = (int)__fns(rowmask, 0u, i + 1);
+                int local = nrows + i - cstart, ch = cur;
+                if (local >= kCRows) {
+                    local -= kCRows;
+                    ch = nxt;
+                }
+                uint4* src = reinterpret_cast<uint4*>(&S.stage[0][j * kRowBytes + lane * 16]);
+                const uint4 v4 = *src;
+                if (ch >= 0 && ch < a.cap)
+                    *reinterpret_cast<uint4*>(a.wg1 + (size_t)ch * kChunkBytes + local * kRowBytes + lane * 16) = v4;
+                *src = make_uint4(0u, 0u, 0u, 0u);
+                const uint32_t wv[4] = {v4.x, v4.y, v4.z, v4.w};
+                float sden = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    sden += __uint_as_float(wv[k] << 16) + __uint_as_float(wv[k] & 0xffff0000u);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sden += __shfl_xor_sync(0xffffffffu, sden, o);
+                if (lane == 0 && ch >= 0 && ch < a.cap) a.chunk_den[(size_t)ch * kCRows + local] = sden;
+            }
+            if (tid < kTcBatch && ((rowmask >> tid) & 1u)) {
+                int local = nrows + __popc(rowmask & lt_mask) - cstart, ch = cur;
+                if (local >= kCRows) {
+                    local -= kCRows;
+                    ch = nxt;
+                }
+                if (ch >= 0 && ch < a.cap) a.chunk_gid[(size_t)ch * kCRows + local] = rec[tid].gid;
+            }
         }
         nrows += nnew;
         // no barrier here: the next batch's counting barrier orders these stores
