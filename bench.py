@@ -174,7 +174,14 @@ def cpu_baseline(wl):
             "sample": f"uplift of view 0 of {wl.cams.v} (D={wl.d}, N={wl.scene.n}), {dt:.1f} s"}
 
 
-def roofline(tr, steps, alg_bytes_step):
+# DRAM bytes (read + write) of one k_aggregate_tc launch, from the ncu capture in
+# profiles/aggregate_paper_f32_traffic.md: (workload, dtype, d) -> (bytes, views in
+# the captured launch).  Scaled to a launch by its views; re-measure whenever the
+# kernel changes.
+TRAFFIC = {("paper", "f32", 384): (33.54e9, 16)}
+
+
+def roofline(tr, steps, alg_bytes_step, traffic_key=None, views_per_launch=None):
     """HBM roofline of the kernel that reads the features: the tensor-core
     aggregation (k_aggregate_tc) when it ran, else the CUDA-core composite.
     Algorithmic bytes per step: the features once, 44 B per Gaussian, and
@@ -188,8 +195,12 @@ def roofline(tr, steps, alg_bytes_step):
     alg_per_launch = alg_bytes_step / max(1.0, launches)
     peak, peak_kind = peaks()
     achieved = alg_per_launch / (launch_ms / 1e3) / 1e9
+    traffic = None
+    if stage == "aggregate" and traffic_key in TRAFFIC and views_per_launch:
+        b, v = TRAFFIC[traffic_key]
+        traffic = b * views_per_launch / v
     return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
             "alg_bytes_per_launch": alg_per_launch, "launch_ms": launch_ms}
 
 
@@ -306,7 +317,9 @@ def run_ours(args):
         ms = float(t.item())
     value = world * V * D / (ms / 1e3)
 
-    roof = roofline(tr, args.steps, V * H * W * D * esize + sc.n * 44 + sc.n * (D + 1) * 4)
+    launches = max(1.0, tr["calls"].get("aggregate", 0) / args.steps)
+    roof = roofline(tr, args.steps, V * H * W * D * esize + sc.n * 44 + sc.n * (D + 1) * 4,
+                    (args.workload, args.dtype, D), V / launches)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
