@@ -7,7 +7,8 @@ the CUDA library: the two meet only through the seeded input generators.
 
 * ``ludvig_oracle.c`` (plain C, float64 values, float32 decision track):
   projection, tile lists, per-pixel compositing (Eq. 1), uplift sums
-  (Eq. 3 / Eq. 5), exact kNN on Gaussian centres (Sec. 3.3).
+  (Eq. 3 / Eq. 5), rendering of per-Gaussian features (Eq. 4), exact kNN on
+  Gaussian centres (Sec. 3.3).
 * this module (numpy / scipy): the similarity graph (Eq. 7 and the edge
   weight of the diffusion workload), row normalisation, and the power
   iteration g_{t+1} = A g_t / ||g_t||_2 (Eq. 8).
@@ -67,6 +68,8 @@ def lib() -> ctypes.CDLL:
             L.orc_view_uplift.argtypes = [i64, p, p, p, p, p, i32, i32, p, i32, i32, p, p, p, p,
                                           i64, p, p, p, p, i32]
             L.orc_view_uplift.restype = i64
+            L.orc_view_render.argtypes = [i64, p, p, p, p, p, i32, i32, p, i32, i32, p, i32]
+            L.orc_view_render.restype = i64
             L.orc_normalise.argtypes = [i64, i32, p, p, p]
             L.orc_normalise.restype = None
             L.orc_knn.argtypes = [i64, p, i32, i64, p, p, p, i32]
@@ -196,6 +199,33 @@ def view_uplift(scene, cam_params, width, height, feats=None, num=None, den=None
     if t_final:
         res["t_final"] = tf
     return res
+
+
+def view_render(scene, cam_params, width, height, f, mode=MODE_HYBRID, nthreads=None):
+    """Renders per-Gaussian features into one view (Eq. 4, F_hat = W f).
+
+    ``f``: [N,D] features (any float type, taken as float64).  Returns
+    (F_hat [H,W,D] float64, number of contributions)."""
+    m, s, q, o = _scene_arrays(scene)
+    n = m.shape[0]
+    f = np.asarray(f)
+    f = _c(f.reshape(n, 1) if f.ndim == 1 else f, np.float64)
+    if f.ndim != 2 or f.shape[0] != n:
+        raise ValueError(f"features must be [{n}, d], got {f.shape}")
+    d = f.shape[1]
+    out = np.zeros((height, width, d), np.float64)
+    rc = lib().orc_view_render(n, _ptr(m), _ptr(s), _ptr(q), _ptr(o), _ptr(_c(cam_params, np.float32)),
+                               width, height, _ptr(f), d, mode, _ptr(out), nthreads or default_threads())
+    if rc < 0:
+        raise RuntimeError(f"orc_view_render failed: {rc}")
+    return out, int(rc)
+
+
+def render(scene, cams, f, views=None, mode=MODE_HYBRID, nthreads=None):
+    """F_hat = W f over ``views`` (default all): [V,H,W,D] float64 (Eq. 4)."""
+    views = list(range(cams.v)) if views is None else list(views)
+    return np.stack([view_render(scene, cams.params[v], cams.width, cams.height, f, mode=mode,
+                                 nthreads=nthreads)[0] for v in views])
 
 
 def normalise(num: np.ndarray, den: np.ndarray) -> np.ndarray:

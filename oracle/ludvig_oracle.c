@@ -574,6 +574,57 @@ int64_t orc_view_uplift(int64_t n, const float* means, const float* scales, cons
     return total;
 }
 
+/* Rendering of per-Gaussian features into one view (Sec. 3.2, Eq. 4):
+ *   out[p, :] = sum over the contributors i of pixel p of w_i(p) f_i
+ * with the weights of Eq. 1 (the same walk as the uplift), no normalisation
+ * and no background term.
+ *   f:   [n*d] float64 features of the Gaussians
+ *   out: [H*W*d] float64, OVERWRITTEN (zero where a pixel has no contributor)
+ * Returns the number of (pixel, Gaussian) contributions in the view. */
+int64_t orc_view_render(int64_t n, const float* means, const float* scales, const float* quats,
+                        const float* opac, const float* cam, int32_t width, int32_t height,
+                        const double* f, int32_t d, int32_t mode, double* out, int32_t nthreads)
+{
+    if (n < 0 || width <= 0 || height <= 0 || d < 0 || (d > 0 && (!f || !out))) return -1;
+    if (nthreads <= 0) nthreads = 1;
+    const int TX = (width + ORC_TILE - 1) / ORC_TILE, TY = (height + ORC_TILE - 1) / ORC_TILE;
+    const int64_t ntiles = (int64_t)TX * TY;
+    orc_proj* P = (orc_proj*)malloc(sizeof(orc_proj) * (size_t)(n > 0 ? n : 1));
+    if (!P) return -2;
+    project_all(n, means, scales, quats, opac, cam, width, height, P, nthreads);
+    uint8_t* tile_on = (uint8_t*)malloc((size_t)ntiles);
+    memset(tile_on, 1, (size_t)ntiles);
+    int64_t* off;
+    int32_t* lst;
+    if (build_lists(n, P, mode, TX, TY, tile_on, &off, &lst)) { free(P); free(tile_on); return -2; }
+    int64_t total = 0;
+    int failed = 0;
+    /* every pixel belongs to one tile, so tiles write disjoint parts of out */
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(+ : total)
+    for (int64_t t = 0; t < ntiles; ++t) {
+        const int tx = (int)(t % TX), ty = (int)(t / TX);
+        const int64_t len = off[t + 1] - off[t];
+        orc_contrib* pix = (orc_contrib*)malloc(sizeof(orc_contrib) * (size_t)(len > 0 ? len : 1));
+        if (!pix) { failed = 1; continue; }
+        for (int v = ty * ORC_TILE; v < ty * ORC_TILE + ORC_TILE && v < height; ++v)
+            for (int u = tx * ORC_TILE; u < tx * ORC_TILE + ORC_TILE && u < width; ++u) {
+                double tf;
+                const int64_t c = composite_pixel(P, lst + off[t], len, u, v, mode, pix, &tf);
+                double* o = out + ((int64_t)v * width + u) * d;
+                for (int32_t ch = 0; ch < d; ++ch) o[ch] = 0.0;
+                for (int64_t k = 0; k < c; ++k) {
+                    const double w = pix[k].w64;
+                    const double* fi = f + (int64_t)pix[k].g * d;
+                    for (int32_t ch = 0; ch < d; ++ch) o[ch] += w * fi[ch];
+                }
+                total += c;
+            }
+        free(pix);
+    }
+    free(tile_on); free(off); free(lst); free(P);
+    return failed ? -2 : total;
+}
+
 /* Normalisation (Eq. 3 / Eq. 5): f_i = num_i / beta_i, zero where beta_i = 0. */
 void orc_normalise(int64_t n, int32_t d, const double* num, const double* den, double* out)
 {

@@ -226,6 +226,16 @@ def feature_field(seed: int, view: int, d: int, height: int, width: int, device=
 # named workloads
 # --------------------------------------------------------------------------
 
+def gaussian_features(n: int, d: int, seed: int, normalise: bool = True) -> np.ndarray:
+    """Per-Gaussian features [n,d] float32 to render back (Eq. 4): N(0,1) rows,
+    L2-normalised like the uplifted DINOv2 features (zero rows stay zero)."""
+    f = _rng(seed, 7).standard_normal((n, d))
+    if normalise and d > 0:
+        nrm = np.linalg.norm(f, axis=1, keepdims=True)
+        f = np.divide(f, nrm, out=np.zeros_like(f), where=nrm > 0)
+    return f.astype(np.float32)
+
+
 @dataclasses.dataclass
 class Workload:
     name: str
