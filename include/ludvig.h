@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define LUDVIG_ABI_VERSION 1
+#define LUDVIG_ABI_VERSION 2
 
 typedef enum {
     LUDVIG_OK = 0,
@@ -148,6 +148,24 @@ ludvig_status ludvig_uplift_host(ludvig_scene_t scene, const ludvig_camera* cams
                                  int32_t width, int32_t height, const void* feats, int32_t dtype,
                                  int32_t d, float* out, float* beta, void* stream);
 
+/* Rendering of per-Gaussian features into views (Sec. 3.2, Eq. 4, F_hat = W f,
+ * the operator whose transpose the uplift applies):
+ *   out[v, y, x, :] = sum_i w_i(v, p) f[i, :]      p = pixel (x, y) of view v
+ * with the weights of Eq. 1 (the same walk, rules and float32 decisions as the
+ * uplift), no normalisation and no background term.
+ *   f:   device [n, d] float32 (e.g. uplifted features), 16-byte aligned when
+ *        d % 8 == 0 and 32 <= d <= 512 (the tensor-core path);
+ *   out: device [n_views, height, width, d] float32, OVERWRITTEN: pixels
+ *        without a contributor get 0.
+ * d in [1, 65536].  With LUDVIG_OPT_F32_TENSOR_CORES = 1 (default) and
+ * d % 8 == 0, 32 <= d <= 512, the products run on the tensor cores with
+ * split-bfloat16 operands (float32-level accuracy); otherwise on CUDA cores in
+ * float32.  Summation order is fixed (results are deterministic).
+ * LUDVIG_ERR_TIMEOUT if a bounded wait of the tensor-core kernel expired. */
+ludvig_status ludvig_render(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
+                            int32_t width, int32_t height, const float* f, int32_t d, float* out,
+                            void* stream);
+
 /* ---- tracing ------------------------------------------------------------ */
 
 /* Stages of the path, as reported by ludvig_trace_read. */
@@ -163,7 +181,9 @@ typedef enum {
     LUDVIG_STAGE_DIFFUSE = 8,
     LUDVIG_STAGE_WEIGHTS = 9,     /* inside COMPOSITE: tensor-core path, compositing weights */
     LUDVIG_STAGE_AGGREGATE = 10,  /* inside COMPOSITE: tensor-core path, W F products into num/den */
-    LUDVIG_STAGE_COUNT = 11
+    LUDVIG_STAGE_RENDER = 11,     /* ludvig_render, stage 6: weights + W f products */
+    LUDVIG_STAGE_RENDER_PRODUCT = 12, /* inside RENDER: the W f products alone */
+    LUDVIG_STAGE_COUNT = 13
 } ludvig_stage;
 
 typedef struct {

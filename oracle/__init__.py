@@ -68,7 +68,7 @@ def lib() -> ctypes.CDLL:
             L.orc_view_uplift.argtypes = [i64, p, p, p, p, p, i32, i32, p, i32, i32, p, p, p, p,
                                           i64, p, p, p, p, i32]
             L.orc_view_uplift.restype = i64
-            L.orc_view_render.argtypes = [i64, p, p, p, p, p, i32, i32, p, i32, i32, p, i32]
+            L.orc_view_render.argtypes = [i64, p, p, p, p, p, i32, i32, p, i32, i32, p, p, i32]
             L.orc_view_render.restype = i64
             L.orc_normalise.argtypes = [i64, i32, p, p, p]
             L.orc_normalise.restype = None
@@ -201,11 +201,12 @@ def view_uplift(scene, cam_params, width, height, feats=None, num=None, den=None
     return res
 
 
-def view_render(scene, cam_params, width, height, f, mode=MODE_HYBRID, nthreads=None):
+def view_render(scene, cam_params, width, height, f, mode=MODE_HYBRID, tiles=None, nthreads=None):
     """Renders per-Gaussian features into one view (Eq. 4, F_hat = W f).
 
-    ``f``: [N,D] features (any float type, taken as float64).  Returns
-    (F_hat [H,W,D] float64, number of contributions)."""
+    ``f``: [N,D] features (any float type, taken as float64); ``tiles``:
+    optional [ntiles] bool mask of the 16x16 tiles to render (the others stay
+    zero).  Returns (F_hat [H,W,D] float64, number of contributions)."""
     m, s, q, o = _scene_arrays(scene)
     n = m.shape[0]
     f = np.asarray(f)
@@ -214,8 +215,11 @@ def view_render(scene, cam_params, width, height, f, mode=MODE_HYBRID, nthreads=
         raise ValueError(f"features must be [{n}, d], got {f.shape}")
     d = f.shape[1]
     out = np.zeros((height, width, d), np.float64)
+    ntiles = ((width + 15) // 16) * ((height + 15) // 16)
+    tm = None if tiles is None else _c(np.asarray(tiles).reshape(ntiles).astype(np.uint8), np.uint8)
     rc = lib().orc_view_render(n, _ptr(m), _ptr(s), _ptr(q), _ptr(o), _ptr(_c(cam_params, np.float32)),
-                               width, height, _ptr(f), d, mode, _ptr(out), nthreads or default_threads())
+                               width, height, _ptr(f), d, mode, _ptr(tm), _ptr(out),
+                               nthreads or default_threads())
     if rc < 0:
         raise RuntimeError(f"orc_view_render failed: {rc}")
     return out, int(rc)

@@ -578,12 +578,15 @@ int64_t orc_view_uplift(int64_t n, const float* means, const float* scales, cons
  *   out[p, :] = sum over the contributors i of pixel p of w_i(p) f_i
  * with the weights of Eq. 1 (the same walk as the uplift), no normalisation
  * and no background term.
- *   f:   [n*d] float64 features of the Gaussians
- *   out: [H*W*d] float64, OVERWRITTEN (zero where a pixel has no contributor)
- * Returns the number of (pixel, Gaussian) contributions in the view. */
+ *   f:    [n*d] float64 features of the Gaussians
+ *   tiles: [ntiles] 0/1 mask of the 16x16 tiles to render, or NULL for all
+ *   out:  [H*W*d] float64; the selected tiles' pixels are OVERWRITTEN (zero
+ *         where a pixel has no contributor), the others are left as they are
+ * Returns the number of (pixel, Gaussian) contributions in the selected tiles. */
 int64_t orc_view_render(int64_t n, const float* means, const float* scales, const float* quats,
                         const float* opac, const float* cam, int32_t width, int32_t height,
-                        const double* f, int32_t d, int32_t mode, double* out, int32_t nthreads)
+                        const double* f, int32_t d, int32_t mode, const uint8_t* tiles, double* out,
+                        int32_t nthreads)
 {
     if (n < 0 || width <= 0 || height <= 0 || d < 0 || (d > 0 && (!f || !out))) return -1;
     if (nthreads <= 0) nthreads = 1;
@@ -593,7 +596,8 @@ int64_t orc_view_render(int64_t n, const float* means, const float* scales, cons
     if (!P) return -2;
     project_all(n, means, scales, quats, opac, cam, width, height, P, nthreads);
     uint8_t* tile_on = (uint8_t*)malloc((size_t)ntiles);
-    memset(tile_on, 1, (size_t)ntiles);
+    if (tiles) memcpy(tile_on, tiles, (size_t)ntiles);
+    else memset(tile_on, 1, (size_t)ntiles);
     int64_t* off;
     int32_t* lst;
     if (build_lists(n, P, mode, TX, TY, tile_on, &off, &lst)) { free(P); free(tile_on); return -2; }
@@ -602,6 +606,7 @@ int64_t orc_view_render(int64_t n, const float* means, const float* scales, cons
     /* every pixel belongs to one tile, so tiles write disjoint parts of out */
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(+ : total)
     for (int64_t t = 0; t < ntiles; ++t) {
+        if (!tile_on[t]) continue;
         const int tx = (int)(t % TX), ty = (int)(t / TX);
         const int64_t len = off[t + 1] - off[t];
         orc_contrib* pix = (orc_contrib*)malloc(sizeof(orc_contrib) * (size_t)(len > 0 ? len : 1));

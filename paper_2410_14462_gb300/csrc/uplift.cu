@@ -23,6 +23,10 @@
 //                  every Gaussian's partial sum into num / den with vector
 //                  reductions.
 //   7. normalise   f = num / den (den > 0), beta = den.
+//
+// Rendering (Eq. 4, F_hat = W f) runs stages 1-5 unchanged and replaces
+// stage 6 by the transposed product: every pixel's sum of w_i(p) f_i over its
+// contributors, written to the view's feature map.
 #include <algorithm>
 #include <cuda_bf16.h>
 
@@ -38,6 +42,14 @@ bool option_f32_tensor_cores();
 ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, int width, int height,
                            const void* feats, int dtype, int d, float* num, float* den, Arena& ws, int* status,
                            int64_t* chunk_cap, cudaStream_t st);
+ludvig_status render_tc(const PairRec* pairs, const uint2* ranges, int nv, int width, int height, const float* f,
+                        int d, float* out, Arena& ws, int* status, int64_t* chunk_cap, cudaStream_t st);
+
+// Per-Gaussian features rendered into the views of a chunk (Eq. 4).
+struct RenderJob {
+    const float* f;   // device [n, d]
+    float* out;       // device [views of the chunk, H, W, d]
+};
 
 struct CamBatch {
     Cam cam[kMaxViews];
@@ -464,6 +476,103 @@ __global__ void __launch_bounds__(256, 2) k_composite(CompositeArgs a) {
     }
 }
 
+// ------------------------------------------------------------ 6'. render (Eq. 4)
+struct RenderArgs {
+    const PairRec* pairs;   // list records in list order
+    const uint2* ranges;
+    int ntiles, TX, width, height;
+    const float* f;         // [n, d]
+    int d;
+    float* out;             // chunk's first view, [H, W, d]
+};
+
+// CUDA-core rendering: one CTA per (view, tile) and DC channels (blockIdx.y),
+// one thread per pixel.  Walks the tile's list in batches of 32 Gaussians with
+// the compositing rules of k_composite and adds w f_i (the batch's DC-channel
+// feature slices staged in shared memory) into per-pixel registers in list
+// order; every pixel of the image is written (zero without contributors).
+template <int DC>
+__global__ void __launch_bounds__(256) k_render_cc(RenderArgs a) {
+    __shared__ float4 ra[kBatch];
+    __shared__ float2 rb[kBatch];
+    __shared__ uint32_t bmask[kBatch];
+    __shared__ uint32_t gid[kBatch];
+    __shared__ float fs[kBatch][DC];
+    const int item = blockIdx.x, c0 = blockIdx.y * DC;
+    const int v = item / a.ntiles, tile = item - v * a.ntiles;
+    const int tx = tile % a.TX, ty = tile / a.TX;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // warp w covers the 8x4 pixel block ((w & 1) * 8, (w >> 1) * 4) of the tile
+    const int lx = (warp & 1) * 8 + (lane & 7), ly = (warp >> 1) * 4 + (lane >> 3);
+    const int px = tx * kTile + lx, py = ty * kTile + ly;
+    const bool inside = px < a.width && py < a.height;
+    const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
+    const uint2 range = a.ranges[item];
+    const int d = a.d;
+    float acc[DC];
+#pragma unroll
+    for (int c = 0; c < DC; ++c) acc[c] = 0.f;
+    float T = 1.0f;
+    bool done = !inside;
+    for (uint32_t b0 = range.x; b0 < range.y; b0 += kBatch) {
+        // every thread is done with the previous batch's shared memory
+        if (__syncthreads_count(!done) == 0) break;
+        const int cnt = (int)min((uint32_t)kBatch, range.y - b0);
+        if (tid < cnt) {
+            const PairRec r = a.pairs[b0 + tid];
+            ra[tid] = make_float4(r.mx, r.my, r.ca, r.cb);
+            rb[tid] = make_float2(r.cc, r.op);
+            bmask[tid] = r.mask;
+            gid[tid] = r.gid;
+        }
+        __syncthreads();
+        for (int e = tid; e < cnt * DC; e += 256) {
+            const int j = e / DC, c = e - j * DC;
+            fs[j][c] = c0 + c < d ? a.f[(int64_t)gid[j] * d + c0 + c] : 0.f;
+        }
+        __syncthreads();
+        uint32_t rel = __ballot_sync(0xffffffffu, lane < cnt && ((bmask[lane] >> warp) & 1u));
+        if (!__any_sync(0xffffffffu, !done)) rel = 0u;
+        float w[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            w[j] = 0.f;
+            if ((rel >> j) & 1u) {
+                const float4 g = ra[j];
+                const float2 h = rb[j];
+                w[j] = alpha_at(g.x, g.y, g.z, g.w, h.x, h.y, pxf, pyf);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const float al = w[j];
+            w[j] = 0.f;
+            if (al > 0.f && !done) {
+                const float Tn = __fmul_rn(T, __fsub_rn(1.0f, al));
+                if (Tn < kTransMin) {
+                    done = true;
+                } else {
+                    w[j] = __fmul_rn(al, T);
+                    T = Tn;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            if (w[j] != 0.f) {
+#pragma unroll
+                for (int c = 0; c < DC; ++c) acc[c] = fmaf(w[j], fs[j][c], acc[c]);
+            }
+        }
+    }
+    if (inside) {
+        float* o = a.out + (((int64_t)v * a.height + py) * a.width + px) * d + c0;
+#pragma unroll
+        for (int c = 0; c < DC; ++c)
+            if (c0 + c < d) o[c] = acc[c];
+    }
+}
+
 // ------------------------------------------------------------ 7. normalise
 __global__ void k_normalise(const float* num, const float* __restrict__ den, float* out, float* beta,
                             int64_t n, int d) {
@@ -549,10 +658,19 @@ ludvig_status launch_composite(const CompositeArgs& args, int64_t nitems, cudaSt
     return LUDVIG_OK;
 }
 
-// One chunk of views: stages 1-6.
+template <int DC>
+ludvig_status launch_render_cc(const RenderArgs& args, int64_t nitems, cudaStream_t st) {
+    const dim3 grid((unsigned)nitems, (unsigned)ceil_div(args.d, DC));
+    StageScope scope(LUDVIG_STAGE_RENDER_PRODUCT, st);
+    k_render_cc<DC><<<grid, 256, 0, st>>>(args);
+    LV_LAUNCH();
+    return LUDVIG_OK;
+}
+
+// One chunk of views: stages 1-6 (stage 6 renders instead when `rj` is set).
 ludvig_status run_chunk(ludvig_scene* s, const ludvig_camera* cams, int nv, int width, int height,
                         const void* feats, int dtype, int d, float* num, float* den, cudaStream_t st,
-                        const ChunkDebug* dbg, bool* too_many_pairs) {
+                        const ChunkDebug* dbg, bool* too_many_pairs, const RenderJob* rj = nullptr) {
     Arena& ws = s->ws;
     const int64_t n = s->n;
     const int64_t npad = round_up(n, kRadixTile);
@@ -669,6 +787,30 @@ ludvig_status run_chunk(ludvig_scene* s, const ludvig_camera* cams, int nv, int 
     }
     trace_end(tslot, st);
 
+    const int64_t nitems = (int64_t)nv * ntiles;
+    if (rj) {
+        StageScope scope(LUDVIG_STAGE_RENDER, st);
+        if (use_tensor_cores(LUDVIG_F32, d)) {
+            int* status;
+            LV_TRY(ws.get("tc.status", 1, &status));
+            return render_tc(pairs, ranges, nv, width, height, rj->f, d, rj->out, ws, status, &s->tc_chunk_cap,
+                             st);
+        }
+        RenderArgs r;
+        r.pairs = pairs;
+        r.ranges = ranges;
+        r.ntiles = ntiles;
+        r.TX = TX;
+        r.width = width;
+        r.height = height;
+        r.f = rj->f;
+        r.d = d;
+        r.out = rj->out;
+        if (d <= 4) return launch_render_cc<4>(r, nitems, st);
+        if (d <= 8) return launch_render_cc<8>(r, nitems, st);
+        if (d <= 16) return launch_render_cc<16>(r, nitems, st);
+        return launch_render_cc<32>(r, nitems, st);
+    }
     CompositeArgs args;
     args.pairs = pairs;
     args.ranges = ranges;
@@ -682,7 +824,6 @@ ludvig_status run_chunk(ludvig_scene* s, const ludvig_camera* cams, int nv, int 
     args.den = den;
     args.dbg_t = dbg ? dbg->t_final : nullptr;
     args.dbg_cnt = dbg ? dbg->n_contrib : nullptr;
-    const int64_t nitems = (int64_t)nv * ntiles;
     const bool vec = (d % 4 == 0);
     StageScope scope(LUDVIG_STAGE_COMPOSITE, st);
     if (use_tensor_cores(dtype, d)) {
@@ -712,7 +853,7 @@ ludvig_status check_views(const ludvig_camera* cams, int32_t n_views, int32_t wi
 
 ludvig_status accumulate(ludvig_scene* s, const ludvig_camera* cams, int32_t n_views, int32_t width,
                          int32_t height, const void* feats, int32_t dtype, int32_t d, float* num,
-                         float* den, cudaStream_t st, const ChunkDebug* dbg) {
+                         float* den, cudaStream_t st, const ChunkDebug* dbg, const RenderJob* rj = nullptr) {
     const size_t esize = dtype == LUDVIG_F32 ? 4 : 2;
     const int64_t view_elems = (int64_t)width * height * d;
     int* status = nullptr;
@@ -728,8 +869,11 @@ ludvig_status accumulate(ludvig_scene* s, const ludvig_camera* cams, int32_t n_v
     while (v0 < n_views) {
         const int nv = std::min(vc, n_views - v0);
         bool too_many = false;
-        const char* fp = static_cast<const char*>(feats) + (size_t)v0 * view_elems * esize;
-        LV_TRY(run_chunk(s, cams + v0, nv, width, height, fp, dtype, d, num, den, st, dbg, &too_many));
+        const char* fp = feats ? static_cast<const char*>(feats) + (size_t)v0 * view_elems * esize : nullptr;
+        RenderJob part{};
+        if (rj) part = RenderJob{rj->f, rj->out + (size_t)v0 * view_elems};
+        LV_TRY(run_chunk(s, cams + v0, nv, width, height, fp, dtype, d, num, den, st, dbg, &too_many,
+                         rj ? &part : nullptr));
         if (too_many) {
             if (nv == 1) {
                 set_error("view %d produces more than 2^31 tile/Gaussian pairs", v0);
@@ -748,7 +892,7 @@ ludvig_status accumulate(ludvig_scene* s, const ludvig_camera* cams, int32_t n_v
         LV_CUDA(cudaStreamSynchronize(st));
         const int code = *static_cast<int*>(h);
         if (code != 0) {
-            set_error("tensor-core aggregation reported status %d (a bounded wait expired)", code);
+            set_error("tensor-core kernel reported status %d (a bounded wait expired)", code);
             return (ludvig_status)code;
         }
     }
@@ -822,6 +966,28 @@ extern "C" ludvig_status ludvig_uplift(ludvig_scene_t scene, const ludvig_camera
     LV_CUDA(cudaMemsetAsync(den, 0, sizeof(float) * (size_t)n, st));
     LV_TRY(ludvig_uplift_accumulate(scene, cams, n_views, width, height, feats, dtype, d, out, den, stream));
     return ludvig_uplift_finalize(n, d, out, den, out, nullptr, stream);
+}
+
+extern "C" ludvig_status ludvig_render(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
+                                       int32_t width, int32_t height, const float* f, int32_t d, float* out,
+                                       void* stream) {
+    LV_ARG(scene != nullptr, "scene is NULL");
+    LV_TRY(check_views(cams, n_views, width, height));
+    LV_ARG(d >= 1 && d <= 65536, "d must be in [1, 65536]");
+    LV_ARG(n_views == 0 || out != nullptr, "out is NULL");
+    LV_ARG(scene->n == 0 || n_views == 0 || f != nullptr, "f is NULL");
+    if (n_views == 0) return LUDVIG_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (scene->n == 0) {
+        LV_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)n_views * height * width * d, st));
+        return LUDVIG_OK;
+    }
+    if (use_tensor_cores(LUDVIG_F32, d)) {
+        LV_ARG(((uintptr_t)f & 15) == 0, "f must be 16-byte aligned");
+    }
+    const RenderJob rj{f, out};
+    return accumulate(scene, cams, n_views, width, height, nullptr, LUDVIG_F32, d, nullptr, nullptr, st, nullptr,
+                      &rj);
 }
 
 extern "C" ludvig_status ludvig_uplift_host(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,

@@ -752,6 +752,267 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
     if (warp == 0) tmem_dealloc(S.tmem_base, 512);
 }
 
+// ------------------------------------------------------------ rendering (Eq. 4)
+//
+// F_hat[p, :] = sum_i w_i(p) f_i per 16x16 tile as the product
+// F_hat_tile^T (128 channels x 256 pixels) = f_K^T (128 channels x K rows) W_K
+// (K rows x 256 pixels) over the tile's weight rows K (its chunks): M = 128
+// channels, N = 256 pixels, 16 rows per MMA, both operands MN-major in the
+// 128-byte-swizzled layout (a W row segment of 64 pixels and an f row segment
+// of 64 channels are each one 128-byte line).  float32 accuracy as in the
+// aggregation: W = W1 + W2 and f = F1 + F2, products W1 F1 + W2 F1 + W1 F2.
+//
+// One CTA per (view, tile, 128-channel block), two per SM (256 TMEM columns
+// each); the CTAs of one tile are adjacent in the grid, so its weight rows
+// come from L2 for the second and third block.  Stages of 32 rows:
+//   warp 0     TMA producer: the stage's rows of W1 and W2, 4 boxes of 64
+//              pixels each;
+//   warps 2-5  gather f_gid rows (128 channels, float32 from global memory),
+//              split them into F1 | F2 in shared memory (rows past the chunk
+//              and channels past d are zero, and so are the W rows past the
+//              chunk once they have landed), then the epilogue: TMEM lanes =
+//              channels, columns = pixels, so one tcgen05.ld column is 32
+//              consecutive channels of a pixel: a 128-byte coalesced store;
+//   warp 1     TMEM allocation and the MMA issuer.
+// Tiles without rows write zeros.  Bounded waits as in the aggregation.
+struct RenderTcArgs {
+    int cap;
+    const int* chunk_rows;
+    const int* chunk_next;
+    const int* item_first;
+    const uint32_t* chunk_gid;
+    int ntiles, TX, width, height, d, nblk;   // nblk: 128-channel blocks
+    const float* f;                           // [n, d]
+    float* out;                               // chunk's first view, [nv, H, W, d]
+    int* status;
+};
+
+constexpr int kRS = 2;                         // stages of 32 weight rows
+constexpr int kRenderThreads = 192;
+constexpr uint32_t kRBox = 32 * 128;           // one box: 32 rows x 128 bytes
+
+struct RenderSmem {
+    uint8_t W[kRS][2][4 * kRBox];              // [stage][term][box of 64 pixels], offset 0 (1024-aligned)
+    uint8_t F[kRS][2][2 * kRBox];              // [stage][term][box of 64 channels]
+    uint64_t w_full[kRS], f_ready[kRS], s_empty[kRS], t_full;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+constexpr size_t render_smem_bytes() { return sizeof(RenderSmem) + 1024; }
+static_assert(2 * render_smem_bytes() <= 232448, "two render CTAs per SM");
+
+// kind::f16 instruction descriptor: D float32, A and B bfloat16, both MN-major,
+// M = 128, N = 256.
+constexpr uint32_t kIdRender =
+    (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+
+// The stages of one tile: chunk c, its rows, stage kb of ceil(rows / 32).
+struct TileStages {
+    int c, rows, kb, nkb;
+    __device__ void load(const RenderTcArgs& a) {
+        while (c >= 0 && c < a.cap) {
+            rows = a.chunk_rows[c];
+            nkb = (rows + 31) >> 5;
+            if (nkb > 0) return;
+            c = a.chunk_next[c];
+        }
+        c = -1;
+        rows = nkb = 0;
+    }
+    __device__ TileStages(const RenderTcArgs& a, int item) : c(a.item_first[item]), rows(0), kb(0), nkb(0) {
+        load(a);
+    }
+    __device__ bool valid() const { return c >= 0; }
+    __device__ void advance(const RenderTcArgs& a) {
+        if (++kb == nkb) {
+            kb = 0;
+            c = a.chunk_next[c];
+            load(a);
+        }
+    }
+};
+
+// Bounded wait taken by every lane of a warp, with a warp-uniform outcome.
+__device__ __forceinline__ bool warp_wait(volatile int* abort_flag, int* status, uint64_t* bar, uint32_t parity) {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, parity));
+    if (!ok && (threadIdx.x & 31) == 0) {
+        *abort_flag = 1;
+        atomicExch(status, (int)LUDVIG_ERR_TIMEOUT);
+    }
+    return ok;
+}
+
+__global__ void __launch_bounds__(kRenderThreads, 2)
+    k_render_tc(RenderTcArgs a, const __grid_constant__ CUtensorMap wmap1, const __grid_constant__ CUtensorMap wmap2) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint32_t pad = (1024u - (saddr(smem_raw) & 1023u)) & 1023u;
+    RenderSmem& S = *reinterpret_cast<RenderSmem*>(smem_raw + pad);
+    volatile int* abort_flag = &S.abort_flag;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int item = blockIdx.x / a.nblk, cb = blockIdx.x - item * a.nblk;
+    const int v = item / a.ntiles, tile = item - v * a.ntiles;
+    const int tx = tile % a.TX, ty = tile / a.TX;
+
+    if (tid == 0) {
+        for (int s = 0; s < kRS; ++s) {
+            mbar_init(&S.w_full[s], 1);
+            mbar_init(&S.f_ready[s], 4);   // the 4 gather warps
+            mbar_init(&S.s_empty[s], 1);   // MMA commit
+        }
+        mbar_init(&S.t_full, 1);
+        S.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(&S.tmem_base, 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer
+            uint32_t it = 0;
+            for (TileStages t(a, item); t.valid() && !*abort_flag; t.advance(a), ++it) {
+                const uint32_t s = it % kRS;
+                if (it >= (uint32_t)kRS && !agg_wait(abort_flag, a.status, &S.s_empty[s], ((it / kRS) - 1) & 1u))
+                    break;
+                mbar_expect_tx(&S.w_full[s], 2u * 4u * kRBox);
+                const int row = t.c * kCRows + 32 * t.kb;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    tma_load_2d(S.W[s][0] + kRBox * j, &wmap1, &S.w_full[s], 64 * j, row);
+                    tma_load_2d(S.W[s][1] + kRBox * j, &wmap2, &S.w_full[s], 64 * j, row);
+                }
+            }
+            if (*abort_flag)   // let the copies already issued land (bounded)
+                for (uint32_t u = (it > (uint32_t)kRS ? it - kRS : 0u); u < it; ++u)
+                    mbar_wait(&S.w_full[u % kRS], (u / kRS) & 1u);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer: descriptors advance by plain adds (start address / 16
+            // in bits 0-13); a 16-row step is 2048 bytes
+            const uint64_t wd0 = sw128_desc(saddr(S.W[0][0]), kRBox, 1024);
+            const uint64_t fd0 = sw128_desc(saddr(S.F[0][0]), kRBox, 1024);
+            uint32_t it = 0;
+            bool ok = true;
+            for (TileStages t(a, item); t.valid(); t.advance(a), ++it) {
+                const uint32_t s = it % kRS, ph = (it / kRS) & 1u;
+                if (*abort_flag || !agg_wait(abort_flag, a.status, &S.w_full[s], ph) ||
+                    !agg_wait(abort_flag, a.status, &S.f_ready[s], ph)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint64_t w1 = wd0 + ((s * sizeof(S.W[0])) >> 4), w2 = w1 + ((4 * kRBox) >> 4);
+                const uint64_t f1 = fd0 + ((s * sizeof(S.F[0])) >> 4), f2 = f1 + ((2 * kRBox) >> 4);
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint32_t o = 128u * ks;
+                    mma_bf16(S.tmem_base, f1 + o, w1 + o, kIdRender, (it > 0 || ks > 0) ? 1u : 0u);
+                    mma_bf16(S.tmem_base, f1 + o, w2 + o, kIdRender, 1u);
+                    mma_bf16(S.tmem_base, f2 + o, w1 + o, kIdRender, 1u);
+                }
+                mma_commit(&S.s_empty[s]);
+            }
+            if (ok && it > 0) mma_commit(&S.t_full);
+            if (!ok && it > 0)   // the MMAs issued complete in order (bounded)
+                mbar_wait(&S.s_empty[(it - 1) % kRS], ((it - 1) / kRS) & 1u);
+        }
+    } else {
+        // ---- gather (warps 2-5): thread g takes row r = g / 4 of the stage and
+        // channels 32 q .. 32 q + 31 of the block (q = g % 4)
+        const int g = tid - 64, r = g >> 2, q = g & 3;
+        const int ch0 = cb * 128 + 32 * q;
+        const int d = a.d;
+        uint32_t it = 0;
+        bool ok = true;
+        for (TileStages t(a, item); t.valid(); t.advance(a), ++it) {
+            const uint32_t s = it % kRS, ph = (it / kRS) & 1u;
+            if (__shfl_sync(0xffffffffu, *abort_flag, 0) ||
+                (it >= (uint32_t)kRS && !warp_wait(abort_flag, a.status, &S.s_empty[s], ((it / kRS) - 1) & 1u))) {
+                ok = false;
+                break;
+            }
+            const int valid = min(32, t.rows - 32 * t.kb);
+            float x[32];
+            if (r < valid) {
+                const uint32_t gid = a.chunk_gid[(size_t)t.c * kCRows + 32 * t.kb + r];
+                const float4* src = reinterpret_cast<const float4*>(a.f + (size_t)gid * d + ch0);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float4 x4 = ch0 + 4 * k < d ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    x[4 * k] = x4.x;
+                    x[4 * k + 1] = x4.y;
+                    x[4 * k + 2] = x4.z;
+                    x[4 * k + 3] = x4.w;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) x[k] = 0.f;
+            }
+            // channels 64 h .. 64 h + 63 are box h; 8 channels per 16-byte chunk,
+            // chunk index XOR (row & 7) under the 128-byte swizzle
+            uint8_t* fb = S.F[s][0] + kRBox * (q >> 1) + r * 128;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint4 h1, h2;
+                split8(x + 8 * k, h1, h2);
+                const int pc = ((q & 1) * 4 + k) ^ (r & 7);
+                *reinterpret_cast<uint4*>(fb + pc * 16) = h1;
+                *reinterpret_cast<uint4*>(fb + 2 * kRBox + pc * 16) = h2;
+            }
+            if (valid < 32) {
+                // rows past the chunk: zero the W lines that the copy brought in
+                if (!warp_wait(abort_flag, a.status, &S.w_full[s], ph)) {
+                    ok = false;
+                    break;
+                }
+                const int nz = (32 - valid) * 64;   // 16-byte pieces: rows x 2 terms x 4 boxes x 8
+                for (int e = g; e < nz; e += 128) {
+                    const int row = valid + (e >> 6), rem = e & 63;
+                    *reinterpret_cast<uint4*>(S.W[s][rem >> 5] + kRBox * ((rem >> 3) & 3) + row * 128 +
+                                              (rem & 7) * 16) = make_uint4(0u, 0u, 0u, 0u);
+                }
+            }
+            fence_proxy_async();   // generic writes, read by the tensor core
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.f_ready[s]);
+        }
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = channels
+        const int qq = warp & 3;
+        const int ch = cb * 128 + 32 * qq + lane;
+        bool have = ok && it > 0;
+        if (have) {
+            have = warp_wait(abort_flag, a.status, &S.t_full, 0u);
+            tc_fence_after();
+        }
+        if (ok && __shfl_sync(0xffffffffu, *abort_flag, 0) == 0) {
+            float* ob = a.out + (((size_t)v * a.height + ty * kTile) * a.width + tx * kTile) * d;
+            for (int gq = 0; gq < 8; ++gq) {   // pixels 32 gq .. 32 gq + 31: tile rows 2 gq, 2 gq + 1
+                float val[32];
+                if (have) {
+                    tmem_ld32(S.tmem_base + ((uint32_t)(32 * qq) << 16) + 32u * gq, val);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) val[i] = 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int lx = i & 15, ly = 2 * gq + (i >> 4);
+                    if (ch < d && tx * kTile + lx < a.width && ty * kTile + ly < a.height)
+                        ob[((size_t)ly * a.width + lx) * d + ch] = val[i];
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(S.tmem_base, 256);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -843,6 +1104,92 @@ ludvig_status sm_count(int* sms) {
     return LUDVIG_OK;
 }
 
+// The weight rows of every (view, tile) of a chunk of views, in chunks of 128
+// (k_weights), with the chunk capacity grown and the pass re-run when it
+// overflows.  Synchronises `st` (reads back the chunk count and status).
+struct TileWeights {
+    int64_t cap = 0;
+    int count = 0;
+    uint8_t *wg1 = nullptr, *wg2 = nullptr;
+    uint32_t* cgid = nullptr;
+    int *crows = nullptr, *cnext = nullptr, *ifirst = nullptr;
+    float* cden = nullptr;
+};
+
+ludvig_status tile_weights(const PairRec* pairs, const uint2* ranges, int nv, int width, int height, int NT,
+                           Arena& ws, int* status, int64_t* chunk_cap, cudaStream_t st, TileWeights* tw) {
+    const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
+    const int nitems = nv * TX * TY;
+    int* counter;
+    int* host;   // [0] chunks used, [1] status
+    LV_TRY(ws.get("tc.counter", 1, &counter));
+    {
+        void* p;
+        LV_TRY(ws.pinned("tc.host", 16, &p));
+        host = static_cast<int*>(p);
+    }
+    int64_t cap = std::max<int64_t>(*chunk_cap, 3 * (int64_t)nitems);
+    TileWeights t;
+    LV_TRY(ws.get("tc.item_first", (size_t)nitems, &t.ifirst));
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (cap > 0x7fffffff / kCRows) {
+            set_error("tile weights need %lld chunks of 128 rows", (long long)cap);
+            return LUDVIG_ERR_UNSUPPORTED;
+        }
+        LV_TRY(ws.get("tc.w1", (size_t)cap * kChunkBytes, &t.wg1));
+        if (NT == 2) LV_TRY(ws.get("tc.w2", (size_t)cap * kChunkBytes, &t.wg2));
+        LV_TRY(ws.get("tc.chunk_gid", (size_t)cap * kCRows, &t.cgid));
+        LV_TRY(ws.get("tc.chunk_rows", (size_t)cap, &t.crows));
+        LV_TRY(ws.get("tc.chunk_next", (size_t)cap, &t.cnext));
+        LV_TRY(ws.get("tc.chunk_den", (size_t)cap * kCRows * NT, &t.cden));
+        LV_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
+        LV_CUDA(cudaMemsetAsync(t.ifirst, 0xff, sizeof(int) * (size_t)nitems, st));
+        WeightsArgs w{};
+        w.pairs = pairs;
+        w.ranges = ranges;
+        w.ntiles = TX * TY;
+        w.TX = TX;
+        w.width = width;
+        w.height = height;
+        w.wg1 = t.wg1;
+        w.wg2 = NT == 2 ? t.wg2 : t.wg1;
+        w.chunk_gid = t.cgid;
+        w.chunk_rows = t.crows;
+        w.chunk_next = t.cnext;
+        w.item_first = t.ifirst;
+        w.chunk_counter = counter;
+        w.cap = (int)cap;
+        w.chunk_den = t.cden;
+        w.status = status;
+        const int tslot = trace_on() ? trace_begin(LUDVIG_STAGE_WEIGHTS, st) : -1;
+        if (NT == 2)
+            k_weights<2><<<nitems, 256, 0, st>>>(w);
+        else
+            k_weights<1><<<nitems, 256, 0, st>>>(w);
+        LV_LAUNCH();
+        trace_end(tslot, st);
+        LV_CUDA(cudaMemcpyAsync(host, counter, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LV_CUDA(cudaMemcpyAsync(host + 1, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LV_CUDA(cudaStreamSynchronize(st));
+        t.count = host[0];
+        if (host[1] != 0) {
+            set_error("tile weights: a bounded wait expired");
+            return (ludvig_status)host[1];
+        }
+        if (t.count <= cap) break;
+        // more chunks than kept: grow and run the weights again
+        cap = (int64_t)t.count + t.count / 8 + 1;
+    }
+    if (t.count > cap) {
+        set_error("tile weights exceed the chunk capacity");
+        return LUDVIG_ERR_INTERNAL;
+    }
+    t.cap = cap;
+    *chunk_cap = cap;
+    *tw = t;
+    return LUDVIG_OK;
+}
+
 }  // namespace
 
 // Tensor-core aggregation applies to d in [32, 512] with d % 8 == 0 (16-byte
@@ -863,87 +1210,20 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
     const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
     const int nitems = nv * TX * TY;
     if (nitems == 0) return LUDVIG_OK;
-    int* counter;
-    int* host;   // [0] chunks used, [1] status
-    LV_TRY(ws.get("tc.counter", 1, &counter));
-    {
-        void* p;
-        LV_TRY(ws.pinned("tc.host", 16, &p));
-        host = static_cast<int*>(p);
-    }
-    int64_t cap = std::max<int64_t>(*chunk_cap, 3 * (int64_t)nitems);
-    int count = 0;
-    uint8_t *wg1 = nullptr, *wg2 = nullptr;
-    uint32_t* cgid = nullptr;
-    int *crows = nullptr, *cnext = nullptr, *ifirst = nullptr;
-    float* cden = nullptr;
-    LV_TRY(ws.get("tc.item_first", (size_t)nitems, &ifirst));
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        if (cap > 0x7fffffff / kCRows) {
-            set_error("tile weights need %lld chunks of 128 rows", (long long)cap);
-            return LUDVIG_ERR_UNSUPPORTED;
-        }
-        LV_TRY(ws.get("tc.w1", (size_t)cap * kChunkBytes, &wg1));
-        if (NT == 2) LV_TRY(ws.get("tc.w2", (size_t)cap * kChunkBytes, &wg2));
-        LV_TRY(ws.get("tc.chunk_gid", (size_t)cap * kCRows, &cgid));
-        LV_TRY(ws.get("tc.chunk_rows", (size_t)cap, &crows));
-        LV_TRY(ws.get("tc.chunk_next", (size_t)cap, &cnext));
-        LV_TRY(ws.get("tc.chunk_den", (size_t)cap * kCRows * NT, &cden));
-        LV_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
-        LV_CUDA(cudaMemsetAsync(ifirst, 0xff, sizeof(int) * (size_t)nitems, st));
-        WeightsArgs w{};
-        w.pairs = pairs;
-        w.ranges = ranges;
-        w.ntiles = TX * TY;
-        w.TX = TX;
-        w.width = width;
-        w.height = height;
-        w.wg1 = wg1;
-        w.wg2 = NT == 2 ? wg2 : wg1;
-        w.chunk_gid = cgid;
-        w.chunk_rows = crows;
-        w.chunk_next = cnext;
-        w.item_first = ifirst;
-        w.chunk_counter = counter;
-        w.cap = (int)cap;
-        w.chunk_den = cden;
-        w.status = status;
-        const int tslot = trace_on() ? trace_begin(LUDVIG_STAGE_WEIGHTS, st) : -1;
-        if (NT == 2)
-            k_weights<2><<<nitems, 256, 0, st>>>(w);
-        else
-            k_weights<1><<<nitems, 256, 0, st>>>(w);
-        LV_LAUNCH();
-        trace_end(tslot, st);
-        LV_CUDA(cudaMemcpyAsync(host, counter, sizeof(int), cudaMemcpyDeviceToHost, st));
-        LV_CUDA(cudaMemcpyAsync(host + 1, status, sizeof(int), cudaMemcpyDeviceToHost, st));
-        LV_CUDA(cudaStreamSynchronize(st));
-        count = host[0];
-        if (host[1] != 0) {
-            set_error("tile weights: a bounded wait expired");
-            return (ludvig_status)host[1];
-        }
-        if (count <= cap) break;
-        // more chunks than kept: grow and run the weights again
-        cap = (int64_t)count + count / 8 + 1;
-    }
-    if (count > cap) {
-        set_error("tile weights exceed the chunk capacity");
-        return LUDVIG_ERR_INTERNAL;
-    }
-    *chunk_cap = cap;
-    if (count == 0) return LUDVIG_OK;
+    TileWeights t;
+    LV_TRY(tile_weights(pairs, ranges, nv, width, height, NT, ws, status, chunk_cap, st, &t));
+    if (t.count == 0) return LUDVIG_OK;
     CUtensorMap maps[3];
-    LV_TRY(make_w_map(&maps[0], wg1, cap));
-    LV_TRY(make_w_map(&maps[1], NT == 2 ? wg2 : wg1, cap));
+    LV_TRY(make_w_map(&maps[0], t.wg1, t.cap));
+    LV_TRY(make_w_map(&maps[1], NT == 2 ? t.wg2 : t.wg1, t.cap));
     LV_TRY(make_feature_map(&maps[2], feats, dtype, nv, width, height, d));
     AggArgs g{};
-    g.cap = (int)cap;
-    g.chunk_rows = crows;
-    g.chunk_next = cnext;
-    g.item_first = ifirst;
-    g.chunk_gid = cgid;
-    g.chunk_den = cden;
+    g.cap = (int)t.cap;
+    g.chunk_rows = t.crows;
+    g.chunk_next = t.cnext;
+    g.item_first = t.ifirst;
+    g.chunk_gid = t.cgid;
+    g.chunk_den = t.cden;
     g.nitems = nitems;
     g.ntiles = TX * TY;
     g.TX = TX;
@@ -956,6 +1236,48 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
     StageScope agg_scope(LUDVIG_STAGE_AGGREGATE, st);
     if (NT == 2) return dispatch_agg<2>(g, maps, grid, st);
     return dispatch_agg<1>(g, maps, grid, st);
+}
+
+// Rendering F_hat = W f of one chunk of views on the tensor cores (Eq. 4):
+// the weight rows of k_weights (float32 split in two bfloat16 terms), then
+// k_render_tc per (view, tile, 128-channel block).
+ludvig_status render_tc(const PairRec* pairs, const uint2* ranges, int nv, int width, int height, const float* f,
+                        int d, float* out, Arena& ws, int* status, int64_t* chunk_cap, cudaStream_t st) {
+    const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
+    const int nitems = nv * TX * TY;
+    if (nitems == 0) return LUDVIG_OK;
+    TileWeights t;
+    LV_TRY(tile_weights(pairs, ranges, nv, width, height, 2, ws, status, chunk_cap, st, &t));
+    CUtensorMap maps[2];
+    LV_TRY(make_w_map(&maps[0], t.wg1, t.cap));
+    LV_TRY(make_w_map(&maps[1], t.wg2, t.cap));
+    RenderTcArgs r{};
+    r.cap = (int)t.cap;
+    r.chunk_rows = t.crows;
+    r.chunk_next = t.cnext;
+    r.item_first = t.ifirst;
+    r.chunk_gid = t.cgid;
+    r.ntiles = TX * TY;
+    r.TX = TX;
+    r.width = width;
+    r.height = height;
+    r.d = d;
+    r.nblk = (d + 127) / 128;
+    r.f = f;
+    r.out = out;
+    r.status = status;
+    static bool configured = false;
+    if (!configured) {
+        LV_CUDA(cudaFuncSetAttribute(k_render_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)render_smem_bytes()));
+        configured = true;
+    }
+    const int tslot = trace_on() ? trace_begin(LUDVIG_STAGE_RENDER_PRODUCT, st) : -1;
+    k_render_tc<<<(unsigned)((int64_t)nitems * r.nblk), kRenderThreads, render_smem_bytes(), st>>>(r, maps[0],
+                                                                                                   maps[1]);
+    LV_LAUNCH();
+    trace_end(tslot, st);
+    return LUDVIG_OK;
 }
 
 }  // namespace ludvig

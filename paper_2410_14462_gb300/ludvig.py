@@ -38,6 +38,7 @@ SIGNATURES = {
     "ludvig_uplift_finalize": (_I32, [_I64, _I32, _P, _P, _P, _P, _P]),
     "ludvig_uplift": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
     "ludvig_uplift_host": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
+    "ludvig_render": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _P, _P]),
     "ludvig_set_option": (_I32, [_I32, _I64]),
     "ludvig_get_option": (_I64, [_I32]),
     "ludvig_trace_enable": (_I32, [_I32]),
@@ -208,6 +209,21 @@ def uplift_host(scene: Scene, cams_params, width, height, feats: torch.Tensor, s
     return out, beta
 
 
+def render(scene: Scene, cams_params, width, height, f: torch.Tensor, out=None, stream=None):
+    """F_hat = W f (Eq. 4) on the device.  f: [N,D] float32 CUDA tensor; returns
+    (or fills) out [V,H,W,D] float32."""
+    L = load()
+    cams, nv = cameras_struct(cams_params)
+    if f.dim() != 2 or f.shape[0] != scene.n:
+        raise LudvigError(f"f must be [{scene.n}, d], got {tuple(f.shape)}")
+    d = int(f.shape[1])
+    if out is None:
+        out = torch.empty((nv, height, width, d), dtype=torch.float32, device=f.device)
+    _check(L.ludvig_render(scene.handle, cams, nv, width, height, _dev(f, torch.float32, "f"), d,
+                           _dev(out, torch.float32, "out"), _stream(stream)), "ludvig_render")
+    return out
+
+
 OPT_F32_TENSOR_CORES = 0
 
 
@@ -220,7 +236,7 @@ def get_option(option: int) -> int:
 
 
 STAGES = ["project", "depth_sort", "bin", "tile_sort", "composite", "normalise", "knn", "graph", "diffuse",
-          "weights", "aggregate"]
+          "weights", "aggregate", "render", "render_product"]
 
 
 class TraceStruct(ctypes.Structure):

@@ -131,3 +131,17 @@ def test_empty_inputs():
     wl = inputs.tiny_mask_workload()
     Fh, count = oracle.view_render(wl.scene, wl.cams.params[0], 128, 128, np.zeros((wl.scene.n, 0)))
     assert Fh.shape == (128, 128, 0) and count > 10_000
+
+
+def test_tile_selection_matches_full_render():
+    """Rendering a subset of tiles gives those tiles' pixels of the full render
+    exactly and leaves the rest zero."""
+    wl = inputs.small_field_workload(n=3000, views=1, d=4, width=70, height=45)
+    f = inputs.gaussian_features(wl.scene.n, 4, seed=2).astype(np.float64)
+    full, cf = oracle.view_render(wl.scene, wl.cams.params[0], 70, 45, f)
+    tiles = np.zeros((3, 5), bool)
+    tiles[0, 1] = tiles[2, 4] = tiles[1, 2] = True
+    part, cp = oracle.view_render(wl.scene, wl.cams.params[0], 70, 45, f, tiles=tiles)
+    pix = np.kron(tiles, np.ones((16, 16), bool))[:45, :70]
+    assert np.array_equal(part[pix], full[pix]) and (part[~pix] == 0).all()
+    assert 0 < cp < cf
