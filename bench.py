@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="uplift only (not a full step)")
     ap.add_argument("--no-precision", action="store_true", help="skip the bf16 precision-form line")
-    ap.add_argument("--profile-case", choices=["tc2views"], default=None,
+    ap.add_argument("--no-render", action="store_true", help="skip the render-back (Eq. 4) line")
+    ap.add_argument("--profile-case", choices=["tc2views", "render2views"], default=None,
                     help="run a small fixed case for an ncu capture and exit (no JSON line)")
     return ap.parse_args()
 
@@ -250,6 +251,58 @@ def precision_form(sc, wl):
             "stages_ms_per_uplift": {k: v / reps for k, v in tr["ms"].items() if v > 0}}
 
 
+# DRAM bytes (read + write) of one k_render_tc launch, from the ncu capture in
+# profiles/render_paper_f32.md: d -> (bytes, views in the captured launch).
+RENDER_TRAFFIC = {}
+
+
+def render_back(sc, wl, f):
+    """Render-back F_hat = W f (Eq. 4) of the uplifted features f [N, D] into
+    every view of the workload, timed over whole ludvig_render calls.  The
+    roofline is that of the product kernel (k_render_tc): algorithmic bytes per
+    launch = the launch's output maps (views x H x W x D x 4) + f read once
+    (N x D x 4)."""
+    import torch
+    from paper_2410_14462_gb300 import ludvig
+    V, H, W = wl.cams.v, wl.cams.height, wl.cams.width
+    D = int(f.shape[1])
+    out = torch.empty((V, H, W, D), dtype=torch.float32, device="cuda")
+    ludvig.render(sc, wl.cams.params, W, H, f, out=out)
+    torch.cuda.synchronize()
+    ludvig.trace_read(reset=True)
+    ludvig.trace_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        ludvig.render(sc, wl.cams.params, W, H, f, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ludvig.trace_enable(False)
+    tr = ludvig.trace_read(reset=True)
+    ms = e0.elapsed_time(e1) / reps
+    launches = tr["calls"]["render_product"] / reps
+    launch_ms = tr["ms"]["render_product"] / max(1, tr["calls"]["render_product"])
+    views_per_launch = V / launches
+    alg = views_per_launch * H * W * D * 4 + sc.n * D * 4
+    peak, peak_kind = peaks()
+    achieved = alg / (launch_ms / 1e3) / 1e9
+    traffic = None
+    if D in RENDER_TRAFFIC:
+        b, v = RENDER_TRAFFIC[D]
+        traffic = b * views_per_launch / v
+    del out
+    torch.cuda.empty_cache()
+    return {"value": V * D / (ms / 1e3), "unit": UNIT, "ms_per_render": ms, "dtype": "f32",
+            "config": {"workload": wl.name, "d": D, "views": V,
+                       "f": "the step's uplifted features", "out": "[V,H,W,D] float32 in HBM"},
+            "roofline": {"bound": "hbm", "kernel": "k_render_tc", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                         "alg_bytes_per_launch": alg, "launch_ms": launch_ms},
+            "stages_ms_per_render": {k: v / reps for k, v in tr["ms"].items() if v > 0},
+            "gpu_launches_per_render": tr["kernel_launches"] / reps}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -350,9 +403,14 @@ def run_ours(args):
         del hf
     if rank == 0 and not args.no_precision and args.workload == "paper":
         del feats
+        feats = None
         torch.cuda.empty_cache()
         line["precision_form"] = precision_form(sc, wl)
         torch.cuda.empty_cache()
+    if rank == 0 and not args.no_render and args.dtype == "f32":
+        feats = None
+        torch.cuda.empty_cache()
+        line["render_back"] = render_back(sc, wl, out)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
@@ -363,8 +421,9 @@ def run_ours(args):
 
 
 def profile_case(name):
-    """Uplift of views 0-1 of the paper-scale workload, D=384, twice with float32
-    features and twice with the same field in bfloat16 (ncu captures)."""
+    """ncu captures on views 0-1 of the paper-scale workload, D=384.
+    tc2views: uplift twice with float32 features and twice with the same field
+    in bfloat16.  render2views: render of seeded unit-norm features, three times."""
     import torch
     from paper_2410_14462_gb300 import build, inputs, ludvig
     build.build()
@@ -372,6 +431,12 @@ def profile_case(name):
     wl = inputs.paper_scale_workload(views=2, d=384)
     sc = ludvig.Scene.from_inputs(wl.scene)
     W, H = wl.cams.width, wl.cams.height
+    if name == "render2views":
+        f = torch.from_numpy(inputs.gaussian_features(sc.n, 384, seed=21)).cuda()
+        for _ in range(3):
+            ludvig.render(sc, wl.cams.params, W, H, f)
+        torch.cuda.synchronize()
+        return 0
     F = torch.stack([wl.features(v, device="cuda") for v in range(2)]).contiguous()
     Fb = F.to(torch.bfloat16)
     for _ in range(2):
