@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="uplift only (not a full step)")
     ap.add_argument("--no-precision", action="store_true", help="skip the bf16 precision-form line")
     ap.add_argument("--no-render", action="store_true", help="skip the render-back (Eq. 4) line")
-    ap.add_argument("--profile-case", choices=["tc2views", "render2views"], default=None,
+    ap.add_argument("--profile-case", choices=["tc2views", "render2views", "render16views"], default=None,
                     help="run a small fixed case for an ncu capture and exit (no JSON line)")
     return ap.parse_args()
 
@@ -423,15 +423,17 @@ def run_ours(args):
 def profile_case(name):
     """ncu captures on views 0-1 of the paper-scale workload, D=384.
     tc2views: uplift twice with float32 features and twice with the same field
-    in bfloat16.  render2views: render of seeded unit-norm features, three times."""
+    in bfloat16.  render2views: render of seeded unit-norm features, three
+    times.  render16views: the same render of views 0-15 (one full launch of
+    the render kernels), three times."""
     import torch
     from paper_2410_14462_gb300 import build, inputs, ludvig
     build.build()
     ludvig.load()
-    wl = inputs.paper_scale_workload(views=2, d=384)
+    wl = inputs.paper_scale_workload(views=16 if name == "render16views" else 2, d=384)
     sc = ludvig.Scene.from_inputs(wl.scene)
     W, H = wl.cams.width, wl.cams.height
-    if name == "render2views":
+    if name in ("render2views", "render16views"):
         f = torch.from_numpy(inputs.gaussian_features(sc.n, 384, seed=21)).cuda()
         for _ in range(3):
             ludvig.render(sc, wl.cams.params, W, H, f)

@@ -70,6 +70,17 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
+// 16 bytes global -> shared through L2 (cp.async, not the bulk-copy engine).
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(dst)), "l"((uint64_t)src) : "memory");
+}
+
+// One arrival on the mbarrier once this thread's earlier cp.async copies have
+// landed (the arrival counts against the barrier's expected count).
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(saddr(bar)) : "memory");
+}
+
 // dst[0 .. bytes/4) += src[...] (float32) by the bulk-copy engine; both 16-byte
 // aligned, bytes % 16 == 0.  Completion is tracked per thread by bulk groups.
 __device__ __forceinline__ void bulk_reduce_add_f32(float* dst, const void* src, uint32_t bytes) {
@@ -77,6 +88,27 @@ __device__ __forceinline__ void bulk_reduce_add_f32(float* dst, const void* src,
                  "r"(saddr(src)), "r"(bytes)
                  : "memory");
 }
+// Tensor store shared -> global (4-d map), tracked by this thread's bulk groups;
+// elements outside the tensor are not written.
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0, int c1, int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"((uint64_t)map),
+        "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(saddr(src))
+        : "memory");
+}
+// at most one of this thread's bulk groups is still reading shared memory
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+
+// cp.async groups of this thread: close the current one; wait until at most N are pending
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// barrier over `count` threads (a multiple of 32) on hardware barrier `id` (1..15)
+__device__ __forceinline__ void named_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // this thread's bulk groups have finished reading their shared-memory sources
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }

@@ -762,76 +762,92 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
 // of 64 channels are each one 128-byte line).  float32 accuracy as in the
 // aggregation: W = W1 + W2 and f = F1 + F2, products W1 F1 + W2 F1 + W1 F2.
 //
-// One CTA per (view, tile, 128-channel block), two per SM (256 TMEM columns
-// each); the CTAs of one tile are adjacent in the grid, so its weight rows
-// come from L2 for the second and third block.  Stages of 32 rows:
-//   warp 0     TMA producer: the stage's rows of W1 and W2, 4 boxes of 64
-//              pixels each;
-//   warps 2-5  gather f_gid rows (128 channels, float32 from global memory),
-//              split them into F1 | F2 in shared memory (rows past the chunk
-//              and channels past d are zero, and so are the W rows past the
-//              chunk once they have landed), then the epilogue: TMEM lanes =
-//              channels, columns = pixels, so one tcgen05.ld column is 32
-//              consecutive channels of a pixel: a 128-byte coalesced store;
-//   warp 1     TMEM allocation and the MMA issuer.
-// Tiles without rows write zeros.  Bounded waits as in the aggregation.
+// A plan pass first flattens every tile's chunk chain into its stages of 32
+// weight rows ({first row, rows}, tile after tile), so that the kernel reads
+// its work from indexed arrays instead of following the chain.
+//
+// One persistent CTA per SM takes the work units (view, tile, 128-channel
+// block) blockIdx.x, blockIdx.x + gridDim.x, ...; the units of one tile are
+// adjacent, so neighbouring CTAs read its weight rows at the same time (once
+// from DRAM).  Stages flow through a ring of 4; each slot carries the stage's
+// unit, rows and first/last flags in shared memory, so only the producer
+// reads the plan:
+//   warp 0      producer: the stage's info and Gaussian ids into shared
+//               memory, then its rows of W1 and W2 by TMA (4 boxes of 64
+//               pixels each);
+//   warps 6-13  converters: each owns 4 rows of every stage, copies their f
+//               segments (128 channels of the unit's block) with 16-byte
+//               cp.async two stages ahead, 32 channels per 128-byte line, and
+//               turns the float32 lines into F1 | F2 in place (rows past the
+//               chunk and channels past d become zero); they also zero the W
+//               lines of rows past the chunk;
+//   warp 1      TMEM allocation and MMA issue, into one of two 256-column
+//               accumulators (unit by unit, alternating);
+//   warps 2-5   epilogue: TMEM lanes = channels, columns = pixels; 32 pixels
+//               at a time are staged [pixel][channel] in shared memory and
+//               written by one TMA store of 16 KB (many small stores from few
+//               warps would be limited by requests in flight, not bandwidth);
+//               the accumulator is released for the unit after next.
+// Units of tiles without rows write zeros.  Bounded waits as in the aggregation.
 struct RenderTcArgs {
-    int cap;
-    const int* chunk_rows;
-    const int* chunk_next;
-    const int* item_first;
+    const uint32_t* stage_start;              // [nitems + 1]: the item's stages in `stages`
+    const uint2* stages;                      // {first weight row, rows (1..32)}
     const uint32_t* chunk_gid;
     int ntiles, TX, width, height, d, nblk;   // nblk: 128-channel blocks
+    int nwork;                                // (view, tile) items x nblk
     const float* f;                           // [n, d]
     float* out;                               // chunk's first view, [nv, H, W, d]
     int* status;
 };
 
-constexpr int kRS = 2;                         // stages of 32 weight rows
-constexpr int kRenderThreads = 192;
+// Plan: stages per item (count pass), then the stages themselves (fill pass),
+// one thread per item walking its chain.
+__global__ void k_render_plan(const int* __restrict__ item_first, const int* __restrict__ chunk_rows,
+                              const int* __restrict__ chunk_next, int cap, int nitems,
+                              const uint32_t* __restrict__ start, uint32_t* __restrict__ count,
+                              uint2* __restrict__ stages) {
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= nitems) {
+        if (count && item == nitems) count[item] = 0u;
+        return;
+    }
+    uint32_t k = start ? start[item] : 0u;
+    for (int c = item_first[item]; c >= 0 && c < cap; c = chunk_next[c]) {
+        const int rows = chunk_rows[c];
+        for (int r = 0; r < rows; r += 32) {
+            if (stages) stages[k] = make_uint2((uint32_t)(c * kCRows + r), (uint32_t)min(32, rows - r));
+            ++k;
+        }
+    }
+    if (count) count[item] = k;
+}
+
+constexpr int kRS = 4;                         // ring of stages of 32 weight rows
+constexpr int kLook = 2;                       // stages of f rows in flight ahead of the one converted
+constexpr int kRenderThreads = 448;            // 14 warps
 constexpr uint32_t kRBox = 32 * 128;           // one box: 32 rows x 128 bytes
+constexpr int kFirst = 1, kLast = 2, kEnd = 4; // stage flags
 
 struct RenderSmem {
     uint8_t W[kRS][2][4 * kRBox];              // [stage][term][box of 64 pixels], offset 0 (1024-aligned)
-    uint8_t F[kRS][2][2 * kRBox];              // [stage][term][box of 64 channels]
-    uint64_t w_full[kRS], f_ready[kRS], s_empty[kRS], t_full;
+    uint8_t F[kRS][4 * kRBox];                 // float32 boxes of 32 channels, then F1 (2 boxes) | F2 (2 boxes)
+    float O[2][32 * 128];                      // output staging: 32 pixels x 128 channels, two buffers
+    int4 info[kRS];                            // unit, rows, channels of the block, flags
+    uint32_t gid[kRS][32];                     // the stage's Gaussian ids
+    uint64_t meta[kRS], full[kRS], ready[kRS], empty[kRS];
+    uint64_t t_full[2], t_empty[2];
     uint32_t tmem_base;
     int abort_flag;
+    int epi_go;
 };
 
 constexpr size_t render_smem_bytes() { return sizeof(RenderSmem) + 1024; }
-static_assert(2 * render_smem_bytes() <= 232448, "two render CTAs per SM");
+static_assert(render_smem_bytes() <= 232448, "shared memory");
 
 // kind::f16 instruction descriptor: D float32, A and B bfloat16, both MN-major,
 // M = 128, N = 256.
 constexpr uint32_t kIdRender =
     (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
-
-// The stages of one tile: chunk c, its rows, stage kb of ceil(rows / 32).
-struct TileStages {
-    int c, rows, kb, nkb;
-    __device__ void load(const RenderTcArgs& a) {
-        while (c >= 0 && c < a.cap) {
-            rows = a.chunk_rows[c];
-            nkb = (rows + 31) >> 5;
-            if (nkb > 0) return;
-            c = a.chunk_next[c];
-        }
-        c = -1;
-        rows = nkb = 0;
-    }
-    __device__ TileStages(const RenderTcArgs& a, int item) : c(a.item_first[item]), rows(0), kb(0), nkb(0) {
-        load(a);
-    }
-    __device__ bool valid() const { return c >= 0; }
-    __device__ void advance(const RenderTcArgs& a) {
-        if (++kb == nkb) {
-            kb = 0;
-            c = a.chunk_next[c];
-            load(a);
-        }
-    }
-};
 
 // Bounded wait taken by every lane of a warp, with a warp-uniform outcome.
 __device__ __forceinline__ bool warp_wait(volatile int* abort_flag, int* status, uint64_t* bar, uint32_t parity) {
@@ -843,174 +859,301 @@ __device__ __forceinline__ bool warp_wait(volatile int* abort_flag, int* status,
     return ok;
 }
 
-__global__ void __launch_bounds__(kRenderThreads, 2)
-    k_render_tc(RenderTcArgs a, const __grid_constant__ CUtensorMap wmap1, const __grid_constant__ CUtensorMap wmap2) {
+__device__ __forceinline__ bool warp_aborted(volatile int* abort_flag) {
+    return __shfl_sync(0xffffffffu, *abort_flag, 0) != 0;
+}
+
+__global__ void __launch_bounds__(kRenderThreads, 1)
+    k_render_tc(RenderTcArgs a, const __grid_constant__ CUtensorMap wmap1, const __grid_constant__ CUtensorMap wmap2,
+                const __grid_constant__ CUtensorMap omap) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const uint32_t pad = (1024u - (saddr(smem_raw) & 1023u)) & 1023u;
     RenderSmem& S = *reinterpret_cast<RenderSmem*>(smem_raw + pad);
     volatile int* abort_flag = &S.abort_flag;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int item = blockIdx.x / a.nblk, cb = blockIdx.x - item * a.nblk;
-    const int v = item / a.ntiles, tile = item - v * a.ntiles;
-    const int tx = tile % a.TX, ty = tile / a.TX;
 
     if (tid == 0) {
         for (int s = 0; s < kRS; ++s) {
-            mbar_init(&S.w_full[s], 1);
-            mbar_init(&S.f_ready[s], 4);   // the 4 gather warps
-            mbar_init(&S.s_empty[s], 1);   // MMA commit
+            mbar_init(&S.meta[s], 1);      // producer: info and ids written
+            mbar_init(&S.full[s], 1);      // producer's arrival with the W bytes
+            mbar_init(&S.ready[s], 8);     // the 8 converter warps
+            mbar_init(&S.empty[s], 1);     // MMA commit
         }
-        mbar_init(&S.t_full, 1);
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(&S.t_full[k], 1);    // MMA commit
+            mbar_init(&S.t_empty[k], 4);   // the 4 epilogue warps
+        }
         S.abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(&S.tmem_base, 256);
+    if (warp == 1) tmem_alloc(&S.tmem_base, 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
 
     if (warp == 0) {
-        if (lane == 0) {
-            // ---- TMA producer
-            uint32_t it = 0;
-            for (TileStages t(a, item); t.valid() && !*abort_flag; t.advance(a), ++it) {
-                const uint32_t s = it % kRS;
-                if (it >= (uint32_t)kRS && !agg_wait(abort_flag, a.status, &S.s_empty[s], ((it / kRS) - 1) & 1u))
-                    break;
-                mbar_expect_tx(&S.w_full[s], 2u * 4u * kRBox);
-                const int row = t.c * kCRows + 32 * t.kb;
+        // ---- producer (whole warp): per stage the info and the 32 Gaussian ids in
+        // shared memory (meta), then the W rows by TMA (full).  The plan is read 32
+        // stages per load, the next stage's ids one stage ahead.
+        uint32_t it = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; ok; u += gridDim.x) {
+            const bool end = u >= a.nwork;
+            const int item = end ? 0 : u / a.nblk, cb = end ? 0 : u - item * a.nblk;
+            const int dv = min(128, a.d - 128 * cb);   // channels of the block inside d (a multiple of 8)
+            const uint32_t k0 = end ? 0u : a.stage_start[item], k1 = end ? 1u : a.stage_start[item + 1];
+            for (uint32_t kb = k0; kb < k1 && ok; kb += 32) {
+                const uint2 rec = (!end && kb + lane < k1) ? a.stages[kb + lane] : make_uint2(0u, 0u);
+                const int m = (int)min(32u, k1 - kb);
+                // (shuffles outside any lane-dependent branch: every lane takes part)
+                const uint32_t row00 = __shfl_sync(0xffffffffu, rec.x, 0);
+                const int valid0 = (int)__shfl_sync(0xffffffffu, rec.y, 0);
+                uint32_t gid = lane < valid0 ? a.chunk_gid[row00 + lane] : 0u;
+                for (int j = 0; j < m; ++j, ++it) {
+                    const uint32_t row0 = __shfl_sync(0xffffffffu, rec.x, j);
+                    const int valid = (int)__shfl_sync(0xffffffffu, rec.y, j);
+                    const int jn = j + 1 < m ? j + 1 : j;
+                    const uint32_t row0n = __shfl_sync(0xffffffffu, rec.x, jn);
+                    const int validn = (int)__shfl_sync(0xffffffffu, rec.y, jn);
+                    const uint32_t gidn = (j + 1 < m && lane < validn) ? a.chunk_gid[row0n + lane] : 0u;
+                    const uint32_t s = it % kRS;
+                    if (warp_aborted(abort_flag) ||
+                        (it >= (uint32_t)kRS && !warp_wait(abort_flag, a.status, &S.empty[s], ((it / kRS) - 1) & 1u))) {
+                        ok = false;
+                        break;
+                    }
+                    S.gid[s][lane] = lane < valid ? gid : 0u;
+                    if (lane == 0) {
+                        const int flags = end ? kEnd : ((kb + j == k0 ? kFirst : 0) | (kb + j + 1 == k1 ? kLast : 0));
+                        S.info[s] = make_int4(u, valid, dv, flags);
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        __threadfence_block();
+                        mbar_arrive(&S.meta[s]);
+                        if (end) {
+                            mbar_arrive(&S.full[s]);
+                        } else {
+                            mbar_expect_tx(&S.full[s], 2u * 4u * kRBox);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    tma_load_2d(S.W[s][0] + kRBox * j, &wmap1, &S.w_full[s], 64 * j, row);
-                    tma_load_2d(S.W[s][1] + kRBox * j, &wmap2, &S.w_full[s], 64 * j, row);
+                            for (int q = 0; q < 4; ++q) {
+                                tma_load_2d(S.W[s][0] + kRBox * q, &wmap1, &S.full[s], 64 * q, (int)row0);
+                                tma_load_2d(S.W[s][1] + kRBox * q, &wmap2, &S.full[s], 64 * q, (int)row0);
+                            }
+                        }
+                    }
+                    gid = gidn;
                 }
             }
-            if (*abort_flag)   // let the copies already issued land (bounded)
-                for (uint32_t u = (it > (uint32_t)kRS ? it - kRS : 0u); u < it; ++u)
-                    mbar_wait(&S.w_full[u % kRS], (u / kRS) & 1u);
+            if (end) break;
         }
+        if (lane == 0 && *abort_flag)   // let the copies already issued land (bounded)
+            for (uint32_t k = (it > (uint32_t)kRS ? it - kRS : 0u); k < it; ++k)
+                mbar_wait(&S.full[k % kRS], (k / kRS) & 1u);
+    } else if (warp >= 6) {
+        // ---- converters: warp cw owns rows 4 cw .. 4 cw + 3 of every stage; lane:
+        // row p = 4 cw + lane / 8, o = lane % 8.  The warp copies its rows' f
+        // segments itself (cp.async, kLook stages ahead: lane o copies channels
+        // 4 (o + 8 m) .. + 3, m = 0..3, into float32 box m), then turns its
+        // rows' float32 lines into F1 | F2 in place: chunks of 8 channels o and
+        // 8 + o.  Every line a warp reads or writes belongs to its own rows, so
+        // warp barriers order the copies, reads and writes.
+        const int cw = warp - 6, p = 4 * cw + (lane >> 3), oc = lane & 7;
+        uint32_t end_it = 0xffffffffu;   // stage index of the end record, once seen
+        bool ok = true;
+        // copies of stage k (after its info and ids are published); one cp.async group per stage
+        auto issue = [&](uint32_t k) {
+            if (k <= end_it && ok) {
+                const uint32_t sk = k % kRS;
+                if (warp_aborted(abort_flag) || !warp_wait(abort_flag, a.status, &S.meta[sk], (k / kRS) & 1u)) {
+                    ok = false;
+                } else {
+                    const int4 inf = S.info[sk];
+                    if (inf.w & kEnd) {
+                        end_it = k;
+                    } else if (p < inf.y) {
+                        const int cbk = inf.x - (inf.x / a.nblk) * a.nblk;
+                        const float* src = a.f + (size_t)S.gid[sk][p] * a.d + 128 * cbk + 4 * oc;
+                        uint8_t* dst = S.F[sk] + p * 128 + oc * 16;
+#pragma unroll
+                        for (int mq = 0; mq < 4; ++mq)
+                            if (4 * (oc + 8 * mq) < inf.z) cp_async_16(dst + kRBox * mq, src + 32 * mq);
+                    }
+                }
+            }
+            cp_async_commit();
+        };
+        for (uint32_t k = 0; k < (uint32_t)kLook; ++k) issue(k);
+        for (uint32_t it = 0; ok; ++it) {
+            issue(it + kLook);
+            if (!ok) break;
+            cp_async_wait<kLook>();   // this thread's copies of stage it have landed
+            __syncwarp();             // and the warp's (its rows only)
+            const uint32_t s = it % kRS;
+            const int4 inf = S.info[s];
+            if (!(inf.w & kEnd)) {
+                const int valid = inf.y, dv = inf.z;
+                uint8_t* base = S.F[s];
+                float x[2][8];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = 64 * h + 8 * oc;   // first channel of the chunk
+                    const uint8_t* line = base + kRBox * (c >> 5) + p * 128 + (c & 31) * 4;
+                    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+                    if (p < valid && c < dv) {
+                        lo = *reinterpret_cast<const float4*>(line);
+                        hi = *reinterpret_cast<const float4*>(line + 16);
+                    }
+                    x[h][0] = lo.x;
+                    x[h][1] = lo.y;
+                    x[h][2] = lo.z;
+                    x[h][3] = lo.w;
+                    x[h][4] = hi.x;
+                    x[h][5] = hi.y;
+                    x[h][6] = hi.z;
+                    x[h][7] = hi.w;
+                }
+                __syncwarp();   // the warp's lines are read before any is overwritten
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint4 f1, f2;
+                    split8(x[h], f1, f2);
+                    const int o = kRBox * h + p * 128 + ((oc ^ (p & 7)) << 4);
+                    *reinterpret_cast<uint4*>(base + o) = f1;
+                    *reinterpret_cast<uint4*>(base + 2 * kRBox + o) = f2;
+                }
+                if (valid < 32) {
+                    // rows past the chunk: zero the W lines that the copy brought in
+                    if (!warp_wait(abort_flag, a.status, &S.full[s], (it / kRS) & 1u)) break;
+                    const int nz = (32 - valid) * 64;   // 16-byte pieces: rows x 2 terms x 4 boxes x 8
+                    for (int e = 32 * cw + lane; e < nz; e += 256) {
+                        const int row = valid + (e >> 6), rem = e & 63;
+                        *reinterpret_cast<uint4*>(S.W[s][rem >> 5] + kRBox * ((rem >> 3) & 3) + row * 128 +
+                                                  (rem & 7) * 16) = make_uint4(0u, 0u, 0u, 0u);
+                    }
+                }
+                fence_proxy_async();   // generic writes, read by the tensor core
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.ready[s]);
+            if (inf.w & kEnd) break;
+        }
+        cp_async_wait<0>();   // no copy of this thread is left in flight
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer: descriptors advance by plain adds (start address / 16
             // in bits 0-13); a 16-row step is 2048 bytes
             const uint64_t wd0 = sw128_desc(saddr(S.W[0][0]), kRBox, 1024);
-            const uint64_t fd0 = sw128_desc(saddr(S.F[0][0]), kRBox, 1024);
-            uint32_t it = 0;
+            const uint64_t fd0 = sw128_desc(saddr(S.F[0]), kRBox, 1024);
+            uint32_t it = 0, ks = 0;   // stages, units with stages
             bool ok = true;
-            for (TileStages t(a, item); t.valid(); t.advance(a), ++it) {
-                const uint32_t s = it % kRS, ph = (it / kRS) & 1u;
-                if (*abort_flag || !agg_wait(abort_flag, a.status, &S.w_full[s], ph) ||
-                    !agg_wait(abort_flag, a.status, &S.f_ready[s], ph)) {
+            for (;; ++it) {
+                const uint32_t s = it % kRS;
+                if (*abort_flag || !agg_wait(abort_flag, a.status, &S.ready[s], (it / kRS) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                const int4 inf = S.info[s];
+                if (inf.w & kEnd) break;
+                if (!agg_wait(abort_flag, a.status, &S.full[s], (it / kRS) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t slot = ks & 1u;
+                if ((inf.w & kFirst) && ks >= 2u &&
+                    !agg_wait(abort_flag, a.status, &S.t_empty[slot], ((ks >> 1) - 1) & 1u)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
+                const uint32_t dt = S.tmem_base + 256u * slot;
                 const uint64_t w1 = wd0 + ((s * sizeof(S.W[0])) >> 4), w2 = w1 + ((4 * kRBox) >> 4);
                 const uint64_t f1 = fd0 + ((s * sizeof(S.F[0])) >> 4), f2 = f1 + ((2 * kRBox) >> 4);
 #pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
-                    const uint32_t o = 128u * ks;
-                    mma_bf16(S.tmem_base, f1 + o, w1 + o, kIdRender, (it > 0 || ks > 0) ? 1u : 0u);
-                    mma_bf16(S.tmem_base, f1 + o, w2 + o, kIdRender, 1u);
-                    mma_bf16(S.tmem_base, f2 + o, w1 + o, kIdRender, 1u);
+                for (int kk = 0; kk < 2; ++kk) {
+                    const uint32_t o = 128u * kk;
+                    mma_bf16(dt, f1 + o, w1 + o, kIdRender, ((inf.w & kFirst) && kk == 0) ? 0u : 1u);
+                    mma_bf16(dt, f1 + o, w2 + o, kIdRender, 1u);
+                    mma_bf16(dt, f2 + o, w1 + o, kIdRender, 1u);
                 }
-                mma_commit(&S.s_empty[s]);
+                mma_commit(&S.empty[s]);
+                if (inf.w & kLast) {
+                    mma_commit(&S.t_full[slot]);
+                    ++ks;
+                }
             }
-            if (ok && it > 0) mma_commit(&S.t_full);
             if (!ok && it > 0)   // the MMAs issued complete in order (bounded)
-                mbar_wait(&S.s_empty[(it - 1) % kRS], ((it - 1) / kRS) & 1u);
+                mbar_wait(&S.empty[(it - 1) % kRS], ((it - 1) / kRS) & 1u);
         }
     } else {
-        // ---- gather (warps 2-5): thread g takes row r = g / 4 of the stage and
-        // channels 32 q .. 32 q + 31 of the block (q = g % 4)
-        const int g = tid - 64, r = g >> 2, q = g & 3;
-        const int ch0 = cb * 128 + 32 * q;
-        const int d = a.d;
-        uint32_t it = 0;
-        bool ok = true;
-        for (TileStages t(a, item); t.valid(); t.advance(a), ++it) {
-            const uint32_t s = it % kRS, ph = (it / kRS) & 1u;
-            if (__shfl_sync(0xffffffffu, *abort_flag, 0) ||
-                (it >= (uint32_t)kRS && !warp_wait(abort_flag, a.status, &S.s_empty[s], ((it / kRS) - 1) & 1u))) {
-                ok = false;
-                break;
-            }
-            const int valid = min(32, t.rows - 32 * t.kb);
-            float x[32];
-            if (r < valid) {
-                const uint32_t gid = a.chunk_gid[(size_t)t.c * kCRows + 32 * t.kb + r];
-                const float4* src = reinterpret_cast<const float4*>(a.f + (size_t)gid * d + ch0);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const float4 x4 = ch0 + 4 * k < d ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    x[4 * k] = x4.x;
-                    x[4 * k + 1] = x4.y;
-                    x[4 * k + 2] = x4.z;
-                    x[4 * k + 3] = x4.w;
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < 32; ++k) x[k] = 0.f;
-            }
-            // channels 64 h .. 64 h + 63 are box h; 8 channels per 16-byte chunk,
-            // chunk index XOR (row & 7) under the 128-byte swizzle
-            uint8_t* fb = S.F[s][0] + kRBox * (q >> 1) + r * 128;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                uint4 h1, h2;
-                split8(x + 8 * k, h1, h2);
-                const int pc = ((q & 1) * 4 + k) ^ (r & 7);
-                *reinterpret_cast<uint4*>(fb + pc * 16) = h1;
-                *reinterpret_cast<uint4*>(fb + 2 * kRBox + pc * 16) = h2;
-            }
-            if (valid < 32) {
-                // rows past the chunk: zero the W lines that the copy brought in
-                if (!warp_wait(abort_flag, a.status, &S.w_full[s], ph)) {
-                    ok = false;
-                    break;
-                }
-                const int nz = (32 - valid) * 64;   // 16-byte pieces: rows x 2 terms x 4 boxes x 8
-                for (int e = g; e < nz; e += 128) {
-                    const int row = valid + (e >> 6), rem = e & 63;
-                    *reinterpret_cast<uint4*>(S.W[s][rem >> 5] + kRBox * ((rem >> 3) & 3) + row * 128 +
-                                              (rem & 7) * 16) = make_uint4(0u, 0u, 0u, 0u);
-                }
-            }
-            fence_proxy_async();   // generic writes, read by the tensor core
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&S.f_ready[s]);
-        }
-        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = channels
+        // ---- epilogue (warps 2-5): warp w reads TMEM lanes 32 (w % 4) .. + 31 =
+        // channels; 32 pixels at a time go to a staging buffer [pixel][128
+        // channels] and out by one TMA store (2 tile rows x 16 pixels x 128
+        // channels; the store leaves out what lies outside the image or past d).
+        // Warp 2 lane 0 leads: it waits for the accumulator, issues the stores and
+        // tracks their reads of the two staging buffers.
         const int qq = warp & 3;
-        const int ch = cb * 128 + 32 * qq + lane;
-        bool have = ok && it > 0;
-        if (have) {
-            have = warp_wait(abort_flag, a.status, &S.t_full, 0u);
-            tc_fence_after();
+        const bool lead = warp == 2 && lane == 0;
+        uint32_t ks = 0;
+        int u = blockIdx.x;
+        bool has = false;
+        if (u < a.nwork) {
+            const int item = u / a.nblk;
+            has = a.stage_start[item + 1] > a.stage_start[item];
         }
-        if (ok && __shfl_sync(0xffffffffu, *abort_flag, 0) == 0) {
-            float* ob = a.out + (((size_t)v * a.height + ty * kTile) * a.width + tx * kTile) * d;
+        for (; u < a.nwork; u += gridDim.x) {
+            const int item = u / a.nblk, cb = u - item * a.nblk;
+            bool has_next = false;   // the next unit's stage count, loaded ahead
+            if (u + (int)gridDim.x < a.nwork) {
+                const int itn = (u + (int)gridDim.x) / a.nblk;
+                has_next = a.stage_start[itn + 1] > a.stage_start[itn];
+            }
+            const int v = item / a.ntiles, tile = item - v * a.ntiles;
+            const int tx = tile % a.TX, ty = tile / a.TX;
+            const uint32_t slot = ks & 1u;
+            if (warp == 2) {
+                bool go = true;
+                if (has) go = warp_wait(abort_flag, a.status, &S.t_full[slot], (ks >> 1) & 1u);
+                if (lane == 0) S.epi_go = go && !*abort_flag;
+            }
+            named_sync(1, 128);
+            if (!S.epi_go) break;
+            tc_fence_after();
             for (int gq = 0; gq < 8; ++gq) {   // pixels 32 gq .. 32 gq + 31: tile rows 2 gq, 2 gq + 1
+                const int b = gq & 1;
                 float val[32];
-                if (have) {
-                    tmem_ld32(S.tmem_base + ((uint32_t)(32 * qq) << 16) + 32u * gq, val);
+                if (has) {
+                    tmem_ld32(S.tmem_base + ((uint32_t)(32 * qq) << 16) + 256u * slot + 32u * gq, val);
+                    if (gq == 7) {   // the accumulator is free for the unit after next
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&S.t_empty[slot]);
+                    }
                 } else {
 #pragma unroll
                     for (int i = 0; i < 32; ++i) val[i] = 0.f;
                 }
+                if (lead) bulk_wait_read_1();   // the store of buffer b two rounds ago has read it
+                named_sync(1, 128);
+                float* ob = S.O[b] + 32 * qq + lane;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int lx = i & 15, ly = 2 * gq + (i >> 4);
-                    if (ch < d && tx * kTile + lx < a.width && ty * kTile + ly < a.height)
-                        ob[((size_t)ly * a.width + lx) * d + ch] = val[i];
+                for (int i = 0; i < 32; ++i) ob[128 * i] = val[i];
+                fence_proxy_async();   // generic writes, read by the TMA store
+                named_sync(1, 128);
+                if (lead && ty * kTile + 2 * gq < a.height) {   // (no store for a box wholly below the image)
+                    tma_store_4d(&omap, S.O[b], 128 * cb, tx * kTile, ty * kTile + 2 * gq, v);
+                    bulk_commit();
                 }
             }
+            if (has) ++ks;
+            has = has_next;
         }
+        if (lead) bulk_wait_all();   // the stores are complete
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 1) tmem_dealloc(S.tmem_base, 256);
+    if (warp == 1) tmem_dealloc(S.tmem_base, 512);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -1030,7 +1173,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // Tensor map with 128-byte swizzle and zero fill out of bounds.
 ludvig_status encode(CUtensorMap* map, CUtensorMapDataType type, const void* base, cuuint32_t rank,
-                     const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box) {
+                     const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box,
+                     CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_128B) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) {
         set_error("cuTensorMapEncodeTiled unavailable");
@@ -1038,7 +1182,7 @@ ludvig_status encode(CUtensorMap* map, CUtensorMapDataType type, const void* bas
     }
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(map, type, rank, const_cast<void*>(base), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -1058,6 +1202,15 @@ ludvig_status make_feature_map(CUtensorMap* map, const void* feats, int dtype, i
     cuuint32_t box[4] = {(cuuint32_t)(128 / es), 16, dtype == LUDVIG_F32 ? 2u : 4u, 1};
     return encode(map, dtype == LUDVIG_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                   feats, 4, dims, strides, box);
+}
+
+// Tensor map over rendered maps [nv, H, W, d] float32 for TMA stores: box of
+// 128 channels x 16 pixels x 2 rows of one view, no swizzle.
+ludvig_status make_out_map(CUtensorMap* map, float* out, int nv, int width, int height, int d) {
+    cuuint64_t dims[4] = {(cuuint64_t)d, (cuuint64_t)width, (cuuint64_t)height, (cuuint64_t)nv};
+    cuuint64_t strides[3] = {(cuuint64_t)d * 4, (cuuint64_t)width * d * 4, (cuuint64_t)height * width * d * 4};
+    cuuint32_t box[4] = {128, 16, 2, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, out, 4, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE);
 }
 
 // Tensor map over chunk rows [cap * 128, 256] bfloat16: box of 64 pixels x 32
@@ -1239,8 +1392,8 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
 }
 
 // Rendering F_hat = W f of one chunk of views on the tensor cores (Eq. 4):
-// the weight rows of k_weights (float32 split in two bfloat16 terms), then
-// k_render_tc per (view, tile, 128-channel block).
+// the weight rows of k_weights (float32 split in two bfloat16 terms), then the
+// persistent k_render_tc over the (view, tile, 128-channel block) units.
 ludvig_status render_tc(const PairRec* pairs, const uint2* ranges, int nv, int width, int height, const float* f,
                         int d, float* out, Arena& ws, int* status, int64_t* chunk_cap, cudaStream_t st) {
     const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
@@ -1248,14 +1401,24 @@ ludvig_status render_tc(const PairRec* pairs, const uint2* ranges, int nv, int w
     if (nitems == 0) return LUDVIG_OK;
     TileWeights t;
     LV_TRY(tile_weights(pairs, ranges, nv, width, height, 2, ws, status, chunk_cap, st, &t));
-    CUtensorMap maps[2];
+    // plan: stages of every item (a chunk has at most 4 stages of 32 rows)
+    uint32_t* start;
+    uint2* stages;
+    LV_TRY(ws.get("render.stage_start", (size_t)nitems + 1, &start));
+    LV_TRY(ws.get("render.stages", (size_t)std::max(1, 4 * t.count), &stages));
+    const int pb = 256, pg = (nitems + 1 + pb - 1) / pb;
+    k_render_plan<<<pg, pb, 0, st>>>(t.ifirst, t.crows, t.cnext, (int)t.cap, nitems, nullptr, start, nullptr);
+    LV_LAUNCH();
+    LV_TRY(scan_exclusive_u32(start, start, (int64_t)nitems + 1, nullptr, ws, st));
+    k_render_plan<<<pg, pb, 0, st>>>(t.ifirst, t.crows, t.cnext, (int)t.cap, nitems, start, nullptr, stages);
+    LV_LAUNCH();
+    CUtensorMap maps[3];
     LV_TRY(make_w_map(&maps[0], t.wg1, t.cap));
     LV_TRY(make_w_map(&maps[1], t.wg2, t.cap));
+    LV_TRY(make_out_map(&maps[2], out, nv, width, height, d));
     RenderTcArgs r{};
-    r.cap = (int)t.cap;
-    r.chunk_rows = t.crows;
-    r.chunk_next = t.cnext;
-    r.item_first = t.ifirst;
+    r.stage_start = start;
+    r.stages = stages;
     r.chunk_gid = t.cgid;
     r.ntiles = TX * TY;
     r.TX = TX;
@@ -1263,6 +1426,7 @@ ludvig_status render_tc(const PairRec* pairs, const uint2* ranges, int nv, int w
     r.height = height;
     r.d = d;
     r.nblk = (d + 127) / 128;
+    r.nwork = nitems * r.nblk;
     r.f = f;
     r.out = out;
     r.status = status;
@@ -1272,9 +1436,10 @@ ludvig_status render_tc(const PairRec* pairs, const uint2* ranges, int nv, int w
                                      (int)render_smem_bytes()));
         configured = true;
     }
+    int sms = 0;
+    LV_TRY(sm_count(&sms));
     const int tslot = trace_on() ? trace_begin(LUDVIG_STAGE_RENDER_PRODUCT, st) : -1;
-    k_render_tc<<<(unsigned)((int64_t)nitems * r.nblk), kRenderThreads, render_smem_bytes(), st>>>(r, maps[0],
-                                                                                                   maps[1]);
+    k_render_tc<<<std::min(sms, r.nwork), kRenderThreads, render_smem_bytes(), st>>>(r, maps[0], maps[1], maps[2]);
     LV_LAUNCH();
     trace_end(tslot, st);
     return LUDVIG_OK;
