@@ -253,7 +253,7 @@ def precision_form(sc, wl):
 
 # DRAM bytes (read + write) of one k_render_tc launch, from the ncu capture in
 # profiles/render_paper_f32.md: d -> (bytes, views in the captured launch).
-RENDER_TRAFFIC = {}
+RENDER_TRAFFIC = {384: (21.758e9, 16)}
 
 
 def render_back(sc, wl, f):
