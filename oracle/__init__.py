@@ -11,7 +11,8 @@ the CUDA library: the two meet only through the seeded input generators.
   Gaussian centres (Sec. 3.3).
 * this module (numpy / scipy): the similarity graph (Eq. 7 and the edge
   weight of the diffusion workload), row normalisation, and the power
-  iteration g_{t+1} = A g_t / ||g_t||_2 (Eq. 8).
+  iteration g_{t+1} = A g_t / ||g_t||_2 (Eq. 8), and the selection of the
+  most important Gaussians by beta (Sec. 3.2, Gaussian filtering).
 
 Parity pins live in ``tests/test_oracle_*.py``.  "Parity unpinned": absolute
 agreement with the paper's own rasteriser (no code or printed values exist)
@@ -230,6 +231,17 @@ def render(scene, cams, f, views=None, mode=MODE_HYBRID, nthreads=None):
     views = list(range(cams.v)) if views is None else list(views)
     return np.stack([view_render(scene, cams.params[v], cams.width, cams.height, f, mode=mode,
                                  nthreads=nthreads)[0] for v in views])
+
+
+def beta_select(beta, keep: int) -> np.ndarray:
+    """Gaussian filtering by importance (Sec. 3.2, "Gaussian filtering"): the
+    indices of the ``keep`` Gaussians with the largest beta_i, ties to the lower
+    index, returned in ascending index order.  beta values <= 0 (and NaN) rank
+    as 0."""
+    b = np.asarray(beta, dtype=np.float64).ravel()
+    b = np.where(b > 0, b, 0.0)
+    order = np.lexsort((np.arange(b.size), -b))   # by -beta, then index
+    return np.sort(order[:keep]).astype(np.int32)
 
 
 def normalise(num: np.ndarray, den: np.ndarray) -> np.ndarray:
