@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="uplift only (not a full step)")
     ap.add_argument("--no-precision", action="store_true", help="skip the bf16 precision-form line")
     ap.add_argument("--no-render", action="store_true", help="skip the render-back (Eq. 4) line")
+    ap.add_argument("--no-filter", action="store_true", help="skip the Gaussian-filtering line")
     ap.add_argument("--profile-case", choices=["tc2views", "render2views", "render16views"], default=None,
                     help="run a small fixed case for an ncu capture and exit (no JSON line)")
     return ap.parse_args()
@@ -303,6 +304,54 @@ def render_back(sc, wl, f):
             "gpu_launches_per_render": tr["kernel_launches"] / reps}
 
 
+def beta_filter(sc, wl, beta, feats):
+    """Gaussian filtering (Sec. 3.2): keep the half of the Gaussians with the
+    largest beta of the step's uplift (ludvig_beta_select, CUDA events), build
+    the filtered scene (ludvig_scene_subset, host clock: it synchronises), and
+    uplift the same views on it (the saving that later uplifts see).  Roofline
+    of the selection: algorithmic bytes = beta read once (4 N) + the kept
+    indices written once (4 keep)."""
+    import torch
+    from paper_2410_14462_gb300 import ludvig
+    V, H, W, D = wl.cams.v, wl.cams.height, wl.cams.width, int(feats.shape[-1])
+    n = sc.n
+    keep = n - n // 2
+    kept = ludvig.beta_select(sc, beta, keep)
+    ludvig.beta_select(sc, beta, keep)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record()
+    for _ in range(reps):
+        kept = ludvig.beta_select(sc, beta, keep)
+    e1.record()
+    torch.cuda.synchronize()
+    sel_ms = e0.elapsed_time(e1) / reps
+    t0 = time.perf_counter()
+    sub = sc.subset(kept)
+    sub_ms = (time.perf_counter() - t0) * 1e3
+    out = torch.empty((sub.n, D), dtype=torch.float32, device="cuda")
+    b2 = torch.empty((sub.n,), dtype=torch.float32, device="cuda")
+    ludvig.uplift(sub, wl.cams.params, W, H, feats, out, b2)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(2):
+        ludvig.uplift(sub, wl.cams.params, W, H, feats, out, b2)
+    e1.record()
+    torch.cuda.synchronize()
+    up_ms = e0.elapsed_time(e1) / 2
+    sub.close()
+    peak, peak_kind = peaks()
+    alg = 4.0 * n + 4.0 * keep
+    achieved = alg / (sel_ms / 1e3) / 1e9
+    return {"kept": keep, "of": n, "select_ms": sel_ms, "subset_ms": sub_ms,
+            "uplift_filtered_ms": up_ms, "uplift_filtered_value": V * D / (up_ms / 1e3), "unit": UNIT,
+            "roofline": {"bound": "hbm", "kernel": "ludvig_beta_select (sort + mark + compact)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "traffic": None, "alg_bytes_per_launch": alg,
+                         "launch_ms": sel_ms}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -401,6 +450,8 @@ def run_ours(args):
                        "d2h_bytes_per_step": int(sc.n * (D + 1) * 4),
                        "sample": f"views 0-{nv - 1} of {V} through ludvig_uplift_host (uplift only)"}
         del hf
+    if rank == 0 and not args.no_filter and args.workload == "paper" and args.dtype == "f32":
+        line["beta_filter"] = beta_filter(sc, wl, beta, feats)
     if rank == 0 and not args.no_precision and args.workload == "paper":
         del feats
         feats = None

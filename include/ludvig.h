@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define LUDVIG_ABI_VERSION 2
+#define LUDVIG_ABI_VERSION 3
 
 typedef enum {
     LUDVIG_OK = 0,
@@ -166,6 +166,29 @@ ludvig_status ludvig_render(ludvig_scene_t scene, const ludvig_camera* cams, int
                             int32_t width, int32_t height, const float* f, int32_t d, float* out,
                             void* stream);
 
+/* Gaussian filtering by importance (Sec. 3.2, "Gaussian filtering"; Sec. 4
+ * keeps half of the Gaussians): beta_i, the sum of Gaussian i's rendering
+ * weights over the training views (the beta output of the uplift), ranks the
+ * Gaussians.  Writes the indices of the `keep` Gaussians with the largest
+ * beta_i, ties to the lower index, in ascending order.
+ *   beta: device [n] float32 (n = the scene's size); values <= 0 and NaN rank
+ *         as 0;
+ *   kept: device [keep] int32, written.
+ * 0 <= keep <= n (keep = n - n/2 keeps the half the paper keeps).  The result
+ * is exact given beta (an integer decision on the float32 values). */
+ludvig_status ludvig_beta_select(ludvig_scene_t scene, const float* beta, int64_t keep, int32_t* kept,
+                                 void* stream);
+
+/* A new scene holding Gaussians idx[0..m) of `scene` (device int32 indices in
+ * [0, n); repeats allowed), in that order: the filtered scene that later
+ * uplifts and renders run on.  The precomputed covariances are copied, so each
+ * Gaussian projects exactly as in the source scene.  Synchronises `stream`
+ * (reads back an index check); LUDVIG_ERR_ARG if an index is out of range.
+ * *out receives the handle (ludvig_scene_destroy frees it); the source scene
+ * is unchanged. */
+ludvig_status ludvig_scene_subset(ludvig_scene_t scene, const int32_t* idx, int64_t m, void* stream,
+                                  ludvig_scene_t* out);
+
 /* ---- tracing ------------------------------------------------------------ */
 
 /* Stages of the path, as reported by ludvig_trace_read. */
@@ -183,7 +206,8 @@ typedef enum {
     LUDVIG_STAGE_AGGREGATE = 10,  /* inside COMPOSITE: tensor-core path, W F products into num/den */
     LUDVIG_STAGE_RENDER = 11,     /* ludvig_render, stage 6: weights + W f products */
     LUDVIG_STAGE_RENDER_PRODUCT = 12, /* inside RENDER: the W f products alone */
-    LUDVIG_STAGE_COUNT = 13
+    LUDVIG_STAGE_FILTER = 13,     /* ludvig_beta_select */
+    LUDVIG_STAGE_COUNT = 14
 } ludvig_stage;
 
 typedef struct {

@@ -39,6 +39,8 @@ SIGNATURES = {
     "ludvig_uplift": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
     "ludvig_uplift_host": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
     "ludvig_render": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _P, _P]),
+    "ludvig_beta_select": (_I32, [_P, _P, _I64, _P, _P]),
+    "ludvig_scene_subset": (_I32, [_P, _P, _I64, _P, ctypes.POINTER(_P)]),
     "ludvig_set_option": (_I32, [_I32, _I64]),
     "ludvig_get_option": (_I64, [_I32]),
     "ludvig_trace_enable": (_I32, [_I32]),
@@ -143,6 +145,20 @@ class Scene:
     def from_inputs(cls, scene, stream=None):
         return cls(scene.means, scene.scales, scene.quats, scene.opacity, stream)
 
+    @classmethod
+    def _wrap(cls, handle, n):
+        obj = cls.__new__(cls)
+        obj._h = handle
+        obj.n = int(n)
+        return obj
+
+    def subset(self, idx: torch.Tensor, stream=None) -> "Scene":
+        """A new scene of Gaussians idx (int32 CUDA tensor), ludvig_scene_subset."""
+        h = ctypes.c_void_p()
+        _check(load().ludvig_scene_subset(self._h, _dev(idx, torch.int32, "idx"), int(idx.numel()),
+                                          _stream(stream), ctypes.byref(h)), "ludvig_scene_subset")
+        return Scene._wrap(h, idx.numel())
+
     @property
     def handle(self):
         return self._h
@@ -224,6 +240,15 @@ def render(scene: Scene, cams_params, width, height, f: torch.Tensor, out=None, 
     return out
 
 
+def beta_select(scene: Scene, beta: torch.Tensor, keep: int, stream=None) -> torch.Tensor:
+    """Indices (ascending, int32) of the `keep` Gaussians with the largest beta
+    (ties to the lower index): Gaussian filtering, Sec. 3.2."""
+    kept = torch.empty((int(keep),), dtype=torch.int32, device=beta.device)
+    _check(load().ludvig_beta_select(scene.handle, _dev(beta, torch.float32, "beta"), int(keep),
+                                     _dev(kept, torch.int32, "kept"), _stream(stream)), "ludvig_beta_select")
+    return kept
+
+
 OPT_F32_TENSOR_CORES = 0
 
 
@@ -236,7 +261,7 @@ def get_option(option: int) -> int:
 
 
 STAGES = ["project", "depth_sort", "bin", "tile_sort", "composite", "normalise", "knn", "graph", "diffuse",
-          "weights", "aggregate", "render", "render_product"]
+          "weights", "aggregate", "render", "render_product", "filter"]
 
 
 class TraceStruct(ctypes.Structure):

@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version(lib):
-    assert lib.ludvig_abi_version() == 2
+    assert lib.ludvig_abi_version() == 3
 
 
 def test_argument_errors_are_synchronous(lib):
@@ -45,6 +45,9 @@ def test_argument_errors_are_synchronous(lib):
     assert lib.ludvig_uplift(None, None, 1, 64, 64, None, 0, 4, None, None, None) == 1
     assert lib.ludvig_knn(None, 4, None, None) == 1
     assert lib.ludvig_render(None, None, 1, 64, 64, None, 4, None, None) == 1
+    assert lib.ludvig_beta_select(None, None, 1, None, None) == 1
+    h2 = ctypes.c_void_p()
+    assert lib.ludvig_scene_subset(None, None, 1, None, ctypes.byref(h2)) == 1
     assert lib.ludvig_diffuse(None, None, 1, 1, None, None) == 1
     assert lib.ludvig_uplift_finalize(-1, 4, None, None, None, None, None) == 1
     assert lib.ludvig_scene_size(None) == -1

@@ -118,3 +118,23 @@ def test_fullsize_render_sampled_tiles(paper):
         assert (got[zero] == 0).all()
     del out
     torch.cuda.empty_cache()
+
+
+def test_fullsize_beta_select(paper):
+    """Gaussian filtering at full size: beta of the 1M-Gaussian scene over all
+    150 views (the uplift's normaliser), the top half selected on the GPU, equal
+    to the oracle's selection on the same beta values."""
+    wl = paper
+    W, H, V = wl.cams.width, wl.cams.height, wl.cams.v
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    feats = torch.empty((V, H, W, 4), dtype=torch.float32, device="cuda")
+    for v in range(V):
+        feats[v] = wl.features_d(v, 4, device="cuda")
+    _, beta = ludvig.uplift(sc, wl.cams.params, W, H, feats)
+    keep = sc.n - sc.n // 2
+    kept = ludvig.beta_select(sc, beta, keep).cpu().numpy()
+    ref = oracle.beta_select(beta.cpu().numpy(), keep)
+    print(f"full size filtering: {(beta > 0).sum().item()} Gaussians with beta > 0, kept {keep}")
+    assert np.array_equal(kept, ref)
+    del feats
+    torch.cuda.empty_cache()
