@@ -332,6 +332,69 @@ def edge_weights_rbf_unary(feats, rows, cols, bandwidth, s_f, unary=None):
     return w
 
 
+def _unit_rows(f):
+    f = np.asarray(f, np.float64)
+    nf = np.linalg.norm(f, axis=1, keepdims=True)
+    return np.where(nf > 0, f / np.where(nf > 0, nf, 1.0), 0.0)
+
+
+def feature_scale(feats, rows, cols):
+    """s_f of the RBF similarity (appendix, diffusion): the median of the l2
+    distances between l2-normalised features, taken over the graph's edges
+    (all n^2 pairs are out of reach at scale); numpy's median (the mean of
+    the two middle values for an even count)."""
+    fh = _unit_rows(feats)
+    d = np.sqrt(np.sum((fh[rows] - fh[cols]) ** 2, axis=1))
+    return float(np.median(d)) if d.size else 0.0
+
+
+def unary_anchor(feats, g0, bandwidth, s_f):
+    """Unary term of Eq. 7 when scribbles are given (appendix, diffusion):
+    P_i = S_f(f_i, f_bar) = exp(-||f^_i - f_bar||^2 / (b s_f^2)), with f_bar the
+    l2-normalised mean of the normalised features of the anchor nodes
+    {i : g0_i > 0} (zero when there are none)."""
+    fh = _unit_rows(feats)
+    anchors = np.asarray(g0, np.float64).reshape(len(fh), -1)[:, 0] > 0
+    fbar = fh[anchors].sum(axis=0) if anchors.any() else np.zeros(fh.shape[1])
+    fbar = _unit_rows(fbar[None, :])[0]
+    d2 = np.sum((fh - fbar[None, :]) ** 2, axis=1)
+    return np.exp(-d2 / (bandwidth * s_f * s_f))
+
+
+def topfrac_positive(u, percent: int):
+    """g_0 of the segmentation task (appendix, diffusion): the uplifted mask u
+    keeps its values on the top `percent` % of the Gaussians with u_i > 0
+    (ceil(npos * percent / 100) of them, larger u first, ties to the lower
+    index) and is zero elsewhere."""
+    u = np.asarray(u, np.float64).ravel()
+    pos = u > 0
+    keep = (int(pos.sum()) * int(percent) + 99) // 100
+    key = np.where(pos, u, 0.0)
+    order = np.lexsort((np.arange(u.size), -key))[:keep]
+    g0 = np.zeros_like(u)
+    g0[order] = u[order]
+    return g0
+
+
+def reach_weight(A, g0, T, unary=None):
+    """Segmentation weight after T diffusion steps (Sec. 4.1 and appendix):
+    S = {i : g_T,i > 0} for the non-negative A and g_0 >= 0, which in exact
+    arithmetic is the set reached from supp(g_0) by walks of exactly T edges
+    of A (taken here as that boolean walk, immune to underflow); h_i = P_i on
+    S (1 without a unary term) and 0 elsewhere.  Columns of g0 are separate
+    queries."""
+    g = np.asarray(g0, np.float64)
+    squeeze = g.ndim == 1
+    s = (g[:, None] if squeeze else g) > 0
+    pat = A.copy().tocsr()
+    pat.data = (pat.data > 0).astype(np.float64)
+    for _ in range(T):
+        s = (pat @ s.astype(np.float64)) > 0
+    p = np.ones(s.shape[0]) if unary is None else np.asarray(unary, np.float64)
+    h = np.where(s, p[:, None], 0.0)
+    return h[:, 0] if squeeze else h
+
+
 def csr(n, rows, cols, vals, row_normalize=True, binarize=0.0):
     """scipy CSR matrix of the graph.  With ``binarize`` > 0 every weight above
     the threshold becomes 1 and the rest 0 (the segmentation variant of Sec. 4.1

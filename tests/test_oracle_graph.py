@@ -142,3 +142,102 @@ def test_diffusion_matches_dense_matvec_multi_query():
         ref = Ad @ (ref / np.where(nrm > 0, nrm, 1.0))
     np.testing.assert_allclose(g, ref, rtol=1e-13, atol=1e-15)
     assert (g[:, 2] == 0).all()
+
+
+# ---- paper-form diffusion (Eq. 7 with the appendix's S_f and P, Sec. 4.1) ----
+
+def _tri():
+    f = np.array([[1, 0], [0, 1], [1, 1]], np.float32)
+    rows = np.array([0, 1, 0, 2, 1, 2])
+    cols = np.array([1, 0, 2, 0, 2, 1])
+    return f, rows, cols
+
+
+def test_feature_scale_closed_form_and_scale_invariance():
+    """f^ = (1,0), (0,1), (1,1)/sqrt2: the six directed edge distances are
+    sqrt2 twice and sqrt(2 - sqrt2) four times, so the median is sqrt(2 - sqrt2);
+    scaling feature rows by positive factors changes nothing."""
+    f, r, c = _tri()
+    assert abs(oracle.feature_scale(f, r, c) - np.sqrt(2 - np.sqrt(2))) < 1e-15
+    f2 = f * np.array([[3.0], [0.25], [7.0]], np.float32)
+    assert abs(oracle.feature_scale(f2, r, c) - oracle.feature_scale(f, r, c)) < 1e-15
+    # an even count takes the mean of the two middle values
+    assert abs(oracle.feature_scale(f, r[:4], c[:4]) - (np.sqrt(2) + np.sqrt(2 - np.sqrt(2))) / 2) < 1e-15
+
+
+def test_rbf_unary_edge_weights_closed_form():
+    """A_ij = exp(-||f^_i - f^_j||^2 / (b s^2)) sqrt(P_i P_j) by hand."""
+    f, r, c = _tri()
+    b, s = 0.5, 0.8
+    P = np.array([0.25, 1.0, 0.64])
+    w = oracle.edge_weights_rbf_unary(f, r, c, b, s, unary=P)
+    d01, d02 = 2.0, 2 - np.sqrt(2)
+    e = lambda d2, pi, pj: np.exp(-d2 / (b * s * s)) * np.sqrt(pi * pj)
+    ref = [e(d01, .25, 1), e(d01, 1, .25), e(d02, .25, .64), e(d02, .64, .25), e(d02, 1, .64), e(d02, .64, 1)]
+    np.testing.assert_allclose(w, ref, rtol=1e-12)
+    np.testing.assert_allclose(oracle.edge_weights_rbf_unary(f, r, c, b, s), [e(x, 1, 1) for x in
+                               (d01, d01, d02, d02, d02, d02)], rtol=1e-12)
+
+
+def test_unary_anchor_closed_form():
+    """Anchors along e1: f_bar = e1, so P = 1 on rows along e1, exp(-2/(b s^2))
+    on rows along e2, exp(-(2 - sqrt2)/(b s^2)) on the diagonal; no anchors:
+    f_bar = 0 and P = exp(-1/(b s^2)) on every non-zero row."""
+    f = np.array([[2, 0], [0, 1], [1, 1], [0.5, 0], [0, 0]], np.float32)
+    g0 = np.array([1.0, 0, 0, 0.3, 0])
+    b, s = 0.5, 0.7
+    P = oracle.unary_anchor(f, g0, b, s)
+    k = b * s * s
+    np.testing.assert_allclose(P, [1, np.exp(-2 / k), np.exp(-(2 - np.sqrt(2)) / k), 1, np.exp(-1 / k)],
+                               rtol=1e-12)
+    # anchors e1 and e2: the mean (1/2, 1/2) normalises to the diagonal
+    P2 = oracle.unary_anchor(f, np.array([0, 1.0, 0, 1.0, 0]), b, s)
+    np.testing.assert_allclose(P2[2], 1.0, rtol=1e-12)
+    np.testing.assert_allclose(P2[:2], [np.exp(-(2 - np.sqrt(2)) / k)] * 2, rtol=1e-12)
+    P0 = oracle.unary_anchor(f, np.zeros(5), b, s)
+    np.testing.assert_allclose(P0, [np.exp(-1 / k)] * 4 + [1.0], rtol=1e-12)
+
+
+def _brute_top(u, percent):
+    u = [float(x) for x in u]
+    pos = [i for i in range(len(u)) if u[i] > 0]
+    keep = (len(pos) * percent + 99) // 100
+    out = np.zeros(len(u))
+    for i in pos:
+        above = sum(1 for j in pos if u[j] > u[i] or (u[j] == u[i] and j < i))
+        if above < keep:
+            out[i] = u[i]
+    return out
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_topfrac_positive_rank_count(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 120))
+    u = rng.choice(np.array([0.0, -0.5, 0.2, 0.2, 0.7, 1.0], np.float32), size=n)
+    for pct in (10, 50, 100, 1):
+        assert np.array_equal(oracle.topfrac_positive(u, pct), _brute_top(u, pct)), (n, pct)
+    assert (oracle.topfrac_positive(np.zeros(7), 10) == 0).all()
+
+
+def test_reach_weight_is_support_of_diffusion():
+    """h = P on supp(g_T) (Eq. 8 on the binarised A, compared with the float64
+    power iteration where it cannot underflow) and on the BFS walk set."""
+    rng = np.random.default_rng(11)
+    n = 50
+    rows = rng.integers(0, n, 120)
+    cols = rng.integers(0, n, 120)
+    ok = rows != cols
+    R = np.concatenate([rows[ok], cols[ok]])
+    C = np.concatenate([cols[ok], rows[ok]])
+    V = rng.choice([1e-7, 0.3], size=R.size)
+    A = oracle.csr(n, R, C, V, row_normalize=False, binarize=1e-5)
+    g0 = np.zeros((n, 2))
+    g0[[3, 4], 0] = [0.5, 1.0]
+    g0[7, 1] = 2.0
+    P = rng.uniform(0.1, 1.0, n)
+    for T in (1, 2, 5):
+        h = oracle.reach_weight(A, g0, T, P)
+        g = oracle.diffuse(A, g0, T)
+        assert np.array_equal(h > 0, g > 0)
+        np.testing.assert_array_equal(h, np.where(g > 0, P[:, None], 0.0))
