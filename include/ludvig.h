@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define LUDVIG_ABI_VERSION 3
+#define LUDVIG_ABI_VERSION 4
 
 typedef enum {
     LUDVIG_OK = 0,
@@ -295,6 +295,63 @@ ludvig_status ludvig_graph_export(ludvig_graph_t graph, int64_t* row_ptr, int32_
  * 1 <= dx <= 32. */
 ludvig_status ludvig_diffuse(ludvig_graph_t graph, const float* x0, int32_t dx, int32_t iters,
                              float* out, void* stream);
+
+/* ---- paper-form diffusion (Eq. 7 with the appendix's S_f and P; Sec. 4.1) --
+ *
+ * The RBF similarity S_f(f_i, f_j) = exp(-||f^_i - f^_j||^2 / (b s_f^2)) of
+ * l2-normalised features, with s_f the median of the pairwise distances,
+ * read as the median over the graph's edges (all n^2 pairs are out of reach;
+ * the mean of the two middle values for an even edge count); the unary term
+ * P(f_i) = S_f(f_i, f_bar) (scribble form: f_bar the normalised mean of the
+ * anchors' normalised features, its own bandwidth); A_ij = S_f P_i^1/2
+ * P_j^1/2, thresholded at 1e-5 for segmentation; g_0 the top 10 % of the
+ * uplifted reference mask's positive values; h_i = P_i on the nodes g_T
+ * reaches after T steps, 0 elsewhere.  The scene part (kNN, edge distances,
+ * s_f) is built once; the prompt part (P, A, h) per query. */
+
+/* The union kNN graph of ludvig_graph_build (same edges) for the RBF
+ * similarity: keeps ||f^_i - f^_j||^2 per edge (float32, from the cosine of
+ * the two rows: 2 - 2 cos, 1 with one zero row, 0 with two) and s_f, the
+ * median edge distance; values are S_f with b = 1 and no unary term until
+ * ludvig_graph_reweight (0 when s_f = 0, e.g. identical features: the RBF
+ * similarity is then undefined).  feats: device [n, df] float32.
+ * Synchronises. */
+ludvig_status ludvig_graph_build_rbf(ludvig_scene_t scene, int32_t k, const float* feats, int32_t df,
+                                     void* stream, ludvig_graph_t* out);
+
+/* s_f of an RBF graph (host float). */
+ludvig_status ludvig_graph_feature_scale(ludvig_graph_t graph, float* s_f);
+
+/* Values of an RBF graph for a prompt: A_ij = exp(-d2_ij / (b s_f^2))
+ * sqrt(P_i P_j) (unary: device [n] or NULL for P = 1), then, if binarize > 0,
+ * 1 where A_ij > binarize and 0 elsewhere, then, if row_normalize, each row
+ * divided by its sum (zero rows stay zero).  LUDVIG_ERR_ARG when s_f = 0. */
+ludvig_status ludvig_graph_reweight(ludvig_graph_t graph, float bandwidth, const float* unary, float binarize,
+                                    int32_t row_normalize, void* stream);
+
+/* Unary term of the scribble form: P_i = exp(-||f^_i - f_bar||^2 / (b s_f^2))
+ * with the graph's s_f and f_bar the l2-normalised sum of f^_i over the anchor
+ * nodes {i : g0_i > 0} (zero without anchors).  feats: device [n, df]
+ * float32 (the graph's features); g0: device [n]; unary: device [n], written. */
+ludvig_status ludvig_unary_anchor(ludvig_graph_t graph, const float* feats, int32_t df, const float* g0,
+                                  float bandwidth, float* unary, void* stream);
+
+/* g_0 of the segmentation task: g0_i = u_i on the ceil(npos * percent / 100)
+ * Gaussians with the largest positive u_i (ties to the lower index; npos =
+ * the number of u_i > 0), 0 elsewhere.  u, g0: device [n] float32 (n = the
+ * scene's size); 0 <= percent <= 100. */
+ludvig_status ludvig_topfrac_positive(ludvig_scene_t scene, const float* u, int32_t percent, float* g0,
+                                      void* stream);
+
+/* Segmentation weight after `steps` diffusion steps: S = {i : g_T,i > 0}, which
+ * for A >= 0 and g_0 >= 0 is the set reached from {i : g0_i > 0} by walks of
+ * exactly `steps` edges with A_ij > 0 (computed as that walk on bit sets, so
+ * no float underflow can lose a node), then h_i = P_i on S (1 when unary is
+ * NULL) and 0 elsewhere.  g0, h: device [n, dx] (column q = query q), 1 <= dx
+ * <= 32; unary: device [n] or NULL.  Negative g0 entries count as not
+ * reached. */
+ludvig_status ludvig_reach_weight(ludvig_graph_t graph, const float* g0, int32_t dx, int32_t steps,
+                                  const float* unary, float* h, void* stream);
 
 /* Graph diffusion that allocates no memory (the paper has no counterpart: this
  * is a service entry point).  It computes exactly what ludvig_diffuse

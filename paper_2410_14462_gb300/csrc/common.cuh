@@ -118,6 +118,8 @@ struct ludvig_graph {
     int64_t* row_ptr = nullptr;   // [n+1]
     int32_t* col = nullptr;       // [nnz]
     float* val = nullptr;         // [nnz]
+    float* d2 = nullptr;          // [nnz] ||f^_i - f^_j||^2 (RBF graphs only)
+    float s_f = 0.f;              // median edge feature distance (RBF graphs only)
     ludvig::Arena ws;
 };
 

@@ -300,6 +300,17 @@ __global__ void k_norms(const float* __restrict__ f, int64_t n, int df, float* _
     if (lane == 0) nrm[i] = sqrtf(s);
 }
 
+// Edge value modes: the diffusion workload's spatial x cosine weight, or the
+// squared distance ||f^_i - f^_j||^2 of the l2-normalised features (for the
+// RBF similarity of the appendix; a zero feature vector normalises to zero):
+// 2 - 2 cos for two non-zero rows, 1 with one zero row, 0 with two.
+constexpr int kEdgeSpatialCos = 0, kEdgeFeatureDist2 = 1;
+
+__device__ __forceinline__ float feature_dist2(float ni, float nj, float cs) {
+    const float zi = ni > 0.f ? 1.f : 0.f, zj = nj > 0.f ? 1.f : 0.f;
+    return fmaxf(0.f, zi + zj - 2.f * cs);
+}
+
 // One warp per row: compact the distinct columns, weight every edge, then
 // threshold / normalise the row (any df).  Row r of the launch is Gaussian
 // order[r] (grid-cell order, so that neighbours' feature rows stay in L2), or
@@ -311,7 +322,7 @@ __global__ void __launch_bounds__(256) k_edge_weights_any(const uint32_t* __rest
                                                 const float* __restrict__ x, const float* __restrict__ f,
                                                 const float* __restrict__ nrm, int64_t n, int df,
                                                 float inv_h, float binarize, int row_normalize,
-                                                const uint32_t* __restrict__ order,
+                                                const uint32_t* __restrict__ order, int mode,
                                                 int32_t* __restrict__ col, float* __restrict__ val) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * 8 + warp;
@@ -338,7 +349,7 @@ __global__ void __launch_bounds__(256) k_edge_weights_any(const uint32_t* __rest
             const float d2 = ex * ex + ey * ey + ez * ez;
             const float den = ni * nrm[j];
             const float cs = den > 0.f ? dot / den : 0.f;
-            float w = expf(-d2 * inv_h) * fmaxf(0.f, cs);
+            float w = mode == kEdgeFeatureDist2 ? feature_dist2(ni, nrm[j], cs) : expf(-d2 * inv_h) * fmaxf(0.f, cs);
             if (binarize > 0.f) w = w > binarize ? 1.f : 0.f;
             col[o] = (int32_t)j;
             val[o] = w;
@@ -364,7 +375,7 @@ __global__ void __launch_bounds__(256) k_edge_weights(const uint32_t* __restrict
                                                      const float* __restrict__ x, const float* __restrict__ f,
                                                      const float* __restrict__ nrm, int64_t n, int df,
                                                      float inv_h, float binarize, int row_normalize,
-                                                     const uint32_t* __restrict__ order,
+                                                     const uint32_t* __restrict__ order, int mode,
                                                      int32_t* __restrict__ col, float* __restrict__ val) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * 8 + warp;
@@ -386,7 +397,7 @@ __global__ void __launch_bounds__(256) k_edge_weights(const uint32_t* __restrict
         const float d2 = ex * ex + ey * ey + ez * ez;
         const float den = ni * nrm[j];
         const float cs = den > 0.f ? dot / den : 0.f;
-        float w = expf(-d2 * inv_h) * fmaxf(0.f, cs);
+        float w = mode == kEdgeFeatureDist2 ? feature_dist2(ni, nrm[j], cs) : expf(-d2 * inv_h) * fmaxf(0.f, cs);
         if (binarize > 0.f) w = w > binarize ? 1.f : 0.f;
         return w;
     };
@@ -633,16 +644,13 @@ extern "C" ludvig_status ludvig_knn(ludvig_scene_t scene, int32_t k, int32_t* nb
     return knn_impl(scene, k, nbr, static_cast<cudaStream_t>(stream));
 }
 
-extern "C" ludvig_status ludvig_graph_build(ludvig_scene_t scene, int32_t k, const float* feats, int32_t df,
-                                            float spatial_h, float binarize, int32_t row_normalize,
-                                            void* stream, ludvig_graph_t* out) {
-    LV_ARG(out != nullptr, "out is NULL");
-    *out = nullptr;
-    LV_ARG(scene != nullptr, "scene is NULL");
-    LV_ARG(k >= 1 && k <= 64, "k must be in [1, 64]");
-    LV_ARG(df >= 1 && feats != nullptr, "features required (df >= 1)");
-    LV_ARG(spatial_h > 0.f, "spatial_h must be positive");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+namespace ludvig {
+namespace {
+
+// The union kNN graph with per-edge values of `mode` (see kEdgeSpatialCos).
+ludvig_status graph_build_impl(ludvig_scene_t scene, int32_t k, const float* feats, int32_t df, float spatial_h,
+                               float binarize, int32_t row_normalize, int mode, cudaStream_t st,
+                               ludvig_graph_t* out) {
     ludvig_graph* g = new ludvig_graph();
     g->n = scene->n;
     LV_CUDA(cudaGetDevice(&g->device));
@@ -733,7 +741,7 @@ extern "C" ludvig_status ludvig_graph_build(ludvig_scene_t scene, int32_t k, con
         const unsigned gb = grid_for(n, 8);
         const float ih = 1.0f / spatial_h;
 #define LV_EW(R) k_edge_weights<R><<<gb, 256, 0, st>>>(tcol, tptr, cnt, g->row_ptr, scene->means, feats, nrm, n, \
-                                                        df, ih, binarize, row_normalize, sorder, g->col, g->val)
+                                                        df, ih, binarize, row_normalize, sorder, mode, g->col, g->val)
         if (df <= 32) LV_EW(1);
         else if (df <= 128) LV_EW(4);
         else if (df <= 256) LV_EW(8);
@@ -741,7 +749,7 @@ extern "C" ludvig_status ludvig_graph_build(ludvig_scene_t scene, int32_t k, con
         else if (df <= 512) LV_EW(16);
         else
             k_edge_weights_any<<<gb, 256, 0, st>>>(tcol, tptr, cnt, g->row_ptr, scene->means, feats, nrm, n, df, ih,
-                                                   binarize, row_normalize, sorder, g->col, g->val);
+                                                   binarize, row_normalize, sorder, mode, g->col, g->val);
 #undef LV_EW
     }
     count_launch();
@@ -754,12 +762,29 @@ extern "C" ludvig_status ludvig_graph_build(ludvig_scene_t scene, int32_t k, con
     return LUDVIG_OK;
 }
 
+}  // namespace
+}  // namespace ludvig
+
+extern "C" ludvig_status ludvig_graph_build(ludvig_scene_t scene, int32_t k, const float* feats, int32_t df,
+                                            float spatial_h, float binarize, int32_t row_normalize,
+                                            void* stream, ludvig_graph_t* out) {
+    LV_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    LV_ARG(scene != nullptr, "scene is NULL");
+    LV_ARG(k >= 1 && k <= 64, "k must be in [1, 64]");
+    LV_ARG(df >= 1 && feats != nullptr, "features required (df >= 1)");
+    LV_ARG(spatial_h > 0.f, "spatial_h must be positive");
+    return graph_build_impl(scene, k, feats, df, spatial_h, binarize, row_normalize, kEdgeSpatialCos,
+                            static_cast<cudaStream_t>(stream), out);
+}
+
 extern "C" ludvig_status ludvig_graph_destroy(ludvig_graph_t g) {
     if (!g) return LUDVIG_OK;
     cudaDeviceSynchronize();
     cudaFree(g->row_ptr);
     cudaFree(g->col);
     cudaFree(g->val);
+    cudaFree(g->d2);
     g->ws.release();
     delete g;
     return LUDVIG_OK;
@@ -905,5 +930,348 @@ extern "C" ludvig_status ludvig_diffuse_noalloc(ludvig_graph_t g, const float* x
         LV_LAUNCH();
         xin = y;
     }
+    return LUDVIG_OK;
+}
+
+// ---------------------------------------------------------------- paper-form diffusion
+// Eq. 7 with the appendix's similarity and unary term, and the segmentation
+// variant of Sec. 4.1:
+//   S_f(f_i, f_j) = exp(-||f^_i - f^_j||^2 / (b s_f^2))   (f^ l2-normalised,
+//                   s_f the median edge distance),
+//   P(f_i) = S_f(f_i, f_bar) with bandwidth b_P (f_bar the normalised mean of
+//            the anchors' normalised features),
+//   A_ij = S_f(f_i, f_j) P_i^1/2 P_j^1/2, thresholded at 1e-5 for segmentation,
+//   g_0 = the top 10 % of the uplifted reference mask's positive values,
+//   h_i = P_i on the nodes that g_T reaches, 0 elsewhere.
+// The graph keeps each edge's ||f^_i - f^_j||^2 (the scene part, computed
+// once); ludvig_graph_reweight forms A for a prompt's P.
+
+namespace ludvig {
+namespace {
+
+__global__ void k_float_keys(const float* __restrict__ v, int64_t m, int64_t mpad, uint32_t* __restrict__ keys,
+                             uint32_t* __restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= mpad) return;
+    keys[i] = i < m ? __float_as_uint(v[i]) : 0xffffffffu;   // non-negative floats order like their bits
+    vals[i] = (uint32_t)i;
+}
+
+// s_f = median of sqrt(d2) over the edges: the mean of the two middle values
+// of the sorted squared distances' roots (one value for an odd count).
+__global__ void k_median_sf(const uint32_t* __restrict__ sorted, int64_t m, float* __restrict__ sf) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (m == 0) {
+        *sf = 0.f;
+        return;
+    }
+    const float a = sqrtf(__uint_as_float(sorted[(m - 1) / 2])), b = sqrtf(__uint_as_float(sorted[m / 2]));
+    *sf = (m & 1) ? a : 0.5f * (a + b);
+}
+
+// One warp per row: A_ij = exp(-d2 inv) sqrt(P_i P_j), thresholded and
+// row-normalised on request.
+__global__ void __launch_bounds__(256) k_rbf_reweight(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                      const float* __restrict__ d2, const float* __restrict__ P,
+                                                      int64_t n, float inv, float binarize, int row_normalize,
+                                                      float* __restrict__ val) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+    if (i >= n) return;
+    const int64_t e0 = rp[i], e1 = rp[i + 1];
+    const float pi = P ? P[i] : 1.f;
+    float rsum = 0.f;
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+        float w = expf(-d2[e] * inv);
+        if (P) w *= sqrtf(pi * P[col[e]]);
+        if (binarize > 0.f) w = w > binarize ? 1.f : 0.f;
+        val[e] = w;
+        rsum += w;
+    }
+    if (!row_normalize) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
+    const float s = rsum > 0.f ? 1.0f / rsum : 0.f;
+    for (int64_t e = e0 + lane; e < e1; e += 32) val[e] *= s;
+}
+
+// Sum of the normalised features of the anchor nodes (g0_i > 0), per channel,
+// in float64: block b takes rows [b R, (b + 1) R), thread t channels t, t + 256, ...
+constexpr int kAnchorRows = 1024;
+__global__ void __launch_bounds__(256) k_anchor_sum(const float* __restrict__ f, const float* __restrict__ nrm,
+                                                    const float* __restrict__ g0, int64_t n, int df,
+                                                    double* __restrict__ acc) {
+    const int64_t r0 = (int64_t)blockIdx.x * kAnchorRows, r1 = n < r0 + kAnchorRows ? n : r0 + kAnchorRows;
+    for (int c = threadIdx.x; c < df; c += blockDim.x) {
+        float s = 0.f;
+        for (int64_t i = r0; i < r1; ++i)
+            if (g0[i] > 0.f && nrm[i] > 0.f) s += f[i * df + c] / nrm[i];
+        if (s != 0.f) atomicAdd(acc + c, (double)s);
+    }
+}
+
+// f_bar = acc / ||acc|| (zero when acc is zero), one block.
+__global__ void k_anchor_finish(const double* __restrict__ acc, int df, float* __restrict__ fbar) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int c = threadIdx.x; c < df; c += blockDim.x) s += acc[c] * acc[c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double nr = sqrt(red[0]);
+    for (int c = threadIdx.x; c < df; c += blockDim.x) fbar[c] = nr > 0.0 ? (float)(acc[c] / nr) : 0.f;
+}
+
+// P_i = exp(-||f^_i - f_bar||^2 inv), one warp per row.
+__global__ void __launch_bounds__(256) k_unary(const float* __restrict__ f, const float* __restrict__ nrm,
+                                               const float* __restrict__ fbar, int64_t n, int df, float inv,
+                                               float* __restrict__ P) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+    if (i >= n) return;
+    const float ni = nrm[i];
+    const float sc = ni > 0.f ? 1.0f / ni : 0.f;
+    float d2 = 0.f;
+    for (int c = lane; c < df; c += 32) {
+        const float t = f[i * df + c] * sc - fbar[c];
+        d2 = fmaf(t, t, d2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    if (lane == 0) P[i] = expf(-d2 * inv);
+}
+
+// Top-percent selection of the positive values: keys as in the beta
+// selection (descending value, ties in index order), positives counted.
+__global__ void k_topfrac_keys(const float* __restrict__ u, int64_t n, int64_t npad, uint32_t* __restrict__ keys,
+                               uint32_t* __restrict__ vals, unsigned long long* __restrict__ npos) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool pos = false;
+    if (i < npad) {
+        uint32_t k = 0xffffffffu;
+        if (i < n && u[i] > 0.f) {
+            k = ~__float_as_uint(u[i]);
+            pos = true;
+        }
+        keys[i] = k;
+        vals[i] = (uint32_t)i;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, pos);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(npos, (unsigned long long)__popc(m));
+}
+
+__global__ void k_topfrac_mark(const uint32_t* __restrict__ vals, const float* __restrict__ u, int64_t n,
+                               const unsigned long long* __restrict__ npos, int percent, float* __restrict__ g0) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t keep = (int64_t)((*npos * (unsigned long long)percent + 99ull) / 100ull);
+    if (k < keep && k < n) g0[vals[k]] = u[vals[k]];
+}
+
+// Reachability as bit sets (bit q = query column q): s_{t+1,i} = OR over the
+// row's edges with A_ij > 0 of s_t,j, one warp per row.
+__global__ void k_reach_init(const float* __restrict__ g0, int64_t n, int dx, uint32_t* __restrict__ s) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t b = 0u;
+    for (int q = 0; q < dx; ++q)
+        if (g0[i * dx + q] > 0.f) b |= 1u << q;
+    s[i] = b;
+}
+
+__global__ void __launch_bounds__(256) k_reach_step(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                    const float* __restrict__ val, const uint32_t* __restrict__ s,
+                                                    int64_t n, uint32_t* __restrict__ s2) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+    if (i >= n) return;
+    uint32_t b = 0u;
+    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += 32)
+        if (val[e] > 0.f) b |= s[col[e]];
+    b = __reduce_or_sync(0xffffffffu, b);
+    if (lane == 0) s2[i] = b;
+}
+
+__global__ void k_reach_out(const uint32_t* __restrict__ s, const float* __restrict__ P, int64_t n, int dx,
+                            float* __restrict__ h) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * dx) return;
+    const int64_t i = t / dx;
+    const int q = (int)(t - i * dx);
+    h[t] = ((s[i] >> q) & 1u) ? (P ? P[i] : 1.f) : 0.f;
+}
+
+}  // namespace
+}  // namespace ludvig
+
+extern "C" ludvig_status ludvig_graph_build_rbf(ludvig_scene_t scene, int32_t k, const float* feats, int32_t df,
+                                                void* stream, ludvig_graph_t* out) {
+    LV_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    LV_ARG(scene != nullptr, "scene is NULL");
+    LV_ARG(k >= 1 && k <= 64, "k must be in [1, 64]");
+    LV_ARG(df >= 1 && (feats != nullptr || scene->n == 0), "features required (df >= 1)");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ludvig_graph_t g = nullptr;
+    LV_TRY(graph_build_impl(scene, k, feats, df, 1.0f, 0.f, 0, kEdgeFeatureDist2, st, &g));
+    // the squared distances move to d2; val gets S_f with b = 1 and no unary term
+    g->d2 = g->val;
+    g->val = nullptr;
+    const int64_t m = g->nnz;
+    auto fail = [&](ludvig_status r) {
+        ludvig_graph_destroy(g);
+        return r;
+    };
+    if (cudaMalloc(&g->val, sizeof(float) * (size_t)std::max<int64_t>(m, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("graph allocation failed");
+        return fail(LUDVIG_ERR_OOM);
+    }
+    if (g->n == 0) {
+        *out = g;
+        return LUDVIG_OK;
+    }
+    const int64_t mpad = round_up(std::max<int64_t>(m, 1), kRadixTile);
+    uint32_t *keys, *vals, *keys2, *vals2;
+    float* sf_d;
+    void* hb;
+    Arena& ws = g->ws;
+    ludvig_status r = LUDVIG_OK;
+    if ((r = ws.get("rbf.keys", (size_t)mpad, &keys)) != LUDVIG_OK || (r = ws.get("rbf.vals", (size_t)mpad, &vals)) ||
+        (r = ws.get("rbf.keys2", (size_t)mpad, &keys2)) || (r = ws.get("rbf.vals2", (size_t)mpad, &vals2)) ||
+        (r = ws.get("rbf.sf", 1, &sf_d)) || (r = ws.pinned("rbf.sf_h", 16, &hb)))
+        return fail(r);
+    {
+        StageScope scope(LUDVIG_STAGE_GRAPH, st);
+        k_float_keys<<<grid_for(mpad, 256), 256, 0, st>>>(g->d2, m, mpad, keys, vals);
+        count_launch();
+        uint32_t *sk = keys, *sv = vals;
+        if ((r = radix_sort_pairs(&sk, &sv, keys2, vals2, 1, mpad, 32, ws, st)) != LUDVIG_OK) return fail(r);
+        k_median_sf<<<1, 32, 0, st>>>(sk, m, sf_d);
+        count_launch();
+        if (cudaMemcpyAsync(hb, sf_d, sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            set_error("graph: CUDA failure");
+            return fail(LUDVIG_ERR_CUDA);
+        }
+    }
+    g->s_f = *static_cast<float*>(hb);
+    if (g->s_f > 0.f) {
+        if ((r = ludvig_graph_reweight(g, 1.0f, nullptr, 0.f, 0, stream)) != LUDVIG_OK) return fail(r);
+    } else if (m > 0 && cudaMemsetAsync(g->val, 0, sizeof(float) * (size_t)m, st) != cudaSuccess) {
+        set_error("graph: CUDA failure");
+        return fail(LUDVIG_ERR_CUDA);
+    }
+    *out = g;
+    return LUDVIG_OK;
+}
+
+extern "C" ludvig_status ludvig_graph_feature_scale(ludvig_graph_t graph, float* s_f) {
+    LV_ARG(graph != nullptr && s_f != nullptr, "NULL argument");
+    LV_ARG(graph->d2 != nullptr || graph->n == 0, "not an RBF graph (ludvig_graph_build_rbf)");
+    *s_f = graph->s_f;
+    return LUDVIG_OK;
+}
+
+extern "C" ludvig_status ludvig_graph_reweight(ludvig_graph_t graph, float bandwidth, const float* unary,
+                                               float binarize, int32_t row_normalize, void* stream) {
+    LV_ARG(graph != nullptr, "graph is NULL");
+    LV_ARG(graph->d2 != nullptr || graph->n == 0, "not an RBF graph (ludvig_graph_build_rbf)");
+    LV_ARG(bandwidth > 0.f, "bandwidth must be positive");
+    if (graph->n == 0 || graph->nnz == 0) return LUDVIG_OK;
+    LV_ARG(graph->s_f > 0.f, "the median edge distance is 0: the RBF similarity is undefined");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    StageScope scope(LUDVIG_STAGE_GRAPH, st);
+    const float inv = 1.0f / (bandwidth * graph->s_f * graph->s_f);
+    k_rbf_reweight<<<grid_for(graph->n, 8), 256, 0, st>>>(graph->row_ptr, graph->col, graph->d2, unary, graph->n,
+                                                          inv, binarize, row_normalize, graph->val);
+    LV_LAUNCH();
+    return LUDVIG_OK;
+}
+
+extern "C" ludvig_status ludvig_unary_anchor(ludvig_graph_t graph, const float* feats, int32_t df, const float* g0,
+                                             float bandwidth, float* unary, void* stream) {
+    LV_ARG(graph != nullptr, "graph is NULL");
+    LV_ARG(graph->d2 != nullptr || graph->n == 0, "not an RBF graph (ludvig_graph_build_rbf)");
+    LV_ARG(df >= 1 && df <= 4096, "df must be in [1, 4096]");
+    LV_ARG(bandwidth > 0.f, "bandwidth must be positive");
+    const int64_t n = graph->n;
+    if (n == 0) return LUDVIG_OK;
+    LV_ARG(feats != nullptr && g0 != nullptr && unary != nullptr, "NULL buffer");
+    LV_ARG(graph->s_f > 0.f, "the median edge distance is 0: the RBF similarity is undefined");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Arena& ws = graph->ws;
+    float *nrm, *fbar;
+    double* acc;
+    LV_TRY(ws.get("un.nrm", (size_t)n, &nrm));
+    LV_TRY(ws.get("un.fbar", (size_t)df, &fbar));
+    LV_TRY(ws.get("un.acc", (size_t)df, &acc));
+    StageScope scope(LUDVIG_STAGE_GRAPH, st);
+    LV_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)df, st));
+    k_norms<<<grid_for(n, 8), 256, 0, st>>>(feats, n, df, nrm);
+    LV_LAUNCH();
+    k_anchor_sum<<<(unsigned)ceil_div(n, kAnchorRows), 256, 0, st>>>(feats, nrm, g0, n, df, acc);
+    LV_LAUNCH();
+    k_anchor_finish<<<1, 256, 0, st>>>(acc, df, fbar);
+    LV_LAUNCH();
+    const float inv = 1.0f / (bandwidth * graph->s_f * graph->s_f);
+    k_unary<<<grid_for(n, 8), 256, 0, st>>>(feats, nrm, fbar, n, df, inv, unary);
+    LV_LAUNCH();
+    return LUDVIG_OK;
+}
+
+extern "C" ludvig_status ludvig_topfrac_positive(ludvig_scene_t scene, const float* u, int32_t percent, float* g0,
+                                                 void* stream) {
+    LV_ARG(scene != nullptr, "scene is NULL");
+    LV_ARG(percent >= 0 && percent <= 100, "percent must be in [0, 100]");
+    const int64_t n = scene->n;
+    if (n == 0) return LUDVIG_OK;
+    LV_ARG(u != nullptr && g0 != nullptr, "NULL buffer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Arena& ws = scene->ws;
+    const int64_t npad = round_up(n, kRadixTile);
+    uint32_t *keys, *vals, *keys2, *vals2;
+    unsigned long long* npos;
+    LV_TRY(ws.get("tf.keys", (size_t)npad, &keys));
+    LV_TRY(ws.get("tf.vals", (size_t)npad, &vals));
+    LV_TRY(ws.get("tf.keys2", (size_t)npad, &keys2));
+    LV_TRY(ws.get("tf.vals2", (size_t)npad, &vals2));
+    LV_TRY(ws.get("tf.npos", 1, &npos));
+    StageScope scope(LUDVIG_STAGE_FILTER, st);
+    LV_CUDA(cudaMemsetAsync(npos, 0, sizeof(unsigned long long), st));
+    LV_CUDA(cudaMemsetAsync(g0, 0, sizeof(float) * (size_t)n, st));
+    k_topfrac_keys<<<grid_for(npad, 256), 256, 0, st>>>(u, n, npad, keys, vals, npos);
+    LV_LAUNCH();
+    uint32_t *sk = keys, *sv = vals;
+    LV_TRY(radix_sort_pairs(&sk, &sv, keys2, vals2, 1, npad, 32, ws, st));
+    k_topfrac_mark<<<grid_for(n, 256), 256, 0, st>>>(sv, u, n, npos, percent, g0);
+    LV_LAUNCH();
+    return LUDVIG_OK;
+}
+
+extern "C" ludvig_status ludvig_reach_weight(ludvig_graph_t graph, const float* g0, int32_t dx, int32_t steps,
+                                             const float* unary, float* h, void* stream) {
+    LV_ARG(graph != nullptr, "graph is NULL");
+    LV_ARG(dx >= 1 && dx <= 32, "dx must be in [1, 32]");
+    LV_ARG(steps >= 0, "steps must be >= 0");
+    const int64_t n = graph->n;
+    if (n == 0) return LUDVIG_OK;
+    LV_ARG(g0 != nullptr && h != nullptr, "NULL buffer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t *s0, *s1;
+    LV_TRY(graph->ws.get("reach.s0", (size_t)n, &s0));
+    LV_TRY(graph->ws.get("reach.s1", (size_t)n, &s1));
+    StageScope scope(LUDVIG_STAGE_DIFFUSE, st);
+    k_reach_init<<<grid_for(n, 256), 256, 0, st>>>(g0, n, dx, s0);
+    LV_LAUNCH();
+    for (int t = 0; t < steps; ++t) {
+        k_reach_step<<<grid_for(n, 8), 256, 0, st>>>(graph->row_ptr, graph->col, graph->val, s0, n, s1);
+        LV_LAUNCH();
+        std::swap(s0, s1);
+    }
+    k_reach_out<<<grid_for(n * dx, 256), 256, 0, st>>>(s0, unary, n, dx, h);
+    LV_LAUNCH();
     return LUDVIG_OK;
 }

@@ -40,6 +40,12 @@ SIGNATURES = {
     "ludvig_uplift_host": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
     "ludvig_render": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _P, _P]),
     "ludvig_beta_select": (_I32, [_P, _P, _I64, _P, _P]),
+    "ludvig_graph_build_rbf": (_I32, [_P, _I32, _P, _I32, _P, ctypes.POINTER(_P)]),
+    "ludvig_graph_feature_scale": (_I32, [_P, ctypes.POINTER(_F)]),
+    "ludvig_graph_reweight": (_I32, [_P, _F, _P, _F, _I32, _P]),
+    "ludvig_unary_anchor": (_I32, [_P, _P, _I32, _P, _F, _P, _P]),
+    "ludvig_topfrac_positive": (_I32, [_P, _P, _I32, _P, _P]),
+    "ludvig_reach_weight": (_I32, [_P, _P, _I32, _I32, _P, _P, _P]),
     "ludvig_scene_subset": (_I32, [_P, _P, _I64, _P, ctypes.POINTER(_P)]),
     "ludvig_set_option": (_I32, [_I32, _I64]),
     "ludvig_get_option": (_I64, [_I32]),
@@ -249,6 +255,14 @@ def beta_select(scene: Scene, beta: torch.Tensor, keep: int, stream=None) -> tor
     return kept
 
 
+def topfrac_positive(scene: Scene, u: torch.Tensor, percent: int = 10, stream=None) -> torch.Tensor:
+    """g_0 = u on the top `percent` % of the positive entries (ludvig_topfrac_positive)."""
+    g0 = torch.empty_like(u)
+    _check(load().ludvig_topfrac_positive(scene.handle, _dev(u, torch.float32, "u"), int(percent),
+                                          _dev(g0, torch.float32, "g0"), _stream(stream)), "ludvig_topfrac_positive")
+    return g0
+
+
 OPT_F32_TENSOR_CORES = 0
 
 
@@ -345,6 +359,50 @@ class Graph:
                "ludvig_graph_build")
         self._h = h
         self.n = scene.n
+
+    @classmethod
+    def rbf(cls, scene: Scene, k: int, feats: torch.Tensor, stream=None) -> "Graph":
+        """ludvig_graph_build_rbf: the union kNN graph with each edge's squared
+        normalised-feature distance and the median edge distance s_f."""
+        L = load()
+        h = ctypes.c_void_p()
+        _check(L.ludvig_graph_build_rbf(scene.handle, k, _dev(feats, torch.float32, "feats"), int(feats.shape[1]),
+                                        _stream(stream), ctypes.byref(h)), "ludvig_graph_build_rbf")
+        obj = cls.__new__(cls)
+        obj._h = h
+        obj.n = scene.n
+        return obj
+
+    @property
+    def feature_scale(self) -> float:
+        v = ctypes.c_float()
+        _check(load().ludvig_graph_feature_scale(self._h, ctypes.byref(v)), "ludvig_graph_feature_scale")
+        return float(v.value)
+
+    def reweight(self, bandwidth: float, unary=None, binarize: float = 0.0, row_normalize: bool = False,
+                 stream=None):
+        _check(load().ludvig_graph_reweight(self._h, float(bandwidth),
+                                            None if unary is None else _dev(unary, torch.float32, "unary"),
+                                            float(binarize), int(row_normalize), _stream(stream)),
+               "ludvig_graph_reweight")
+
+    def unary_anchor(self, feats: torch.Tensor, g0: torch.Tensor, bandwidth: float, out=None, stream=None):
+        if out is None:
+            out = torch.empty((self.n,), dtype=torch.float32, device=feats.device)
+        _check(load().ludvig_unary_anchor(self._h, _dev(feats, torch.float32, "feats"), int(feats.shape[1]),
+                                          _dev(g0, torch.float32, "g0"), float(bandwidth),
+                                          _dev(out, torch.float32, "unary"), _stream(stream)), "ludvig_unary_anchor")
+        return out
+
+    def reach_weight(self, g0: torch.Tensor, steps: int, unary=None, out=None, stream=None):
+        g0 = g0.contiguous()
+        dx = 1 if g0.dim() == 1 else int(g0.shape[1])
+        if out is None:
+            out = torch.empty_like(g0)
+        _check(load().ludvig_reach_weight(self._h, _dev(g0, torch.float32, "g0"), dx, int(steps),
+                                          None if unary is None else _dev(unary, torch.float32, "unary"),
+                                          _dev(out, torch.float32, "h"), _stream(stream)), "ludvig_reach_weight")
+        return out
 
     @property
     def nnz(self) -> int:

@@ -1,0 +1,137 @@
+"""GPU parity of the paper-form diffusion (Eq. 7 with the appendix's RBF
+similarity S_f and unary term P, and the segmentation variant of Sec. 4.1)
+through the C ABI, on the features the GPU uplift produces:
+
+* the RBF graph has the union kNN pattern exactly, s_f within 1e-5 relative of
+  the oracle's median, and values within 1e-5 relative L2;
+* g_0 (top 10 % of the uplifted mask's positives) is bit-exact against the
+  oracle on the same uplifted values; P and the reweighted A within 1e-5;
+* the binarised pattern agrees except within 1e-3 relative of the threshold;
+* the reachability weight h is bit-exact against the oracle's walk on the
+  GPU's own graph (so float decisions cannot differ), for 1 and 2 queries;
+* multi-query diffusion on the RBF graph within 1e-5."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import torch
+
+import oracle
+from paper_2410_14462_gb300 import inputs, ludvig
+from tests.gpu_util import device_features, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2410_14462_gb300 import build
+    build.build()
+    ludvig.load()
+
+
+@pytest.fixture(scope="module")
+def setup():
+    wl = inputs.small_field_workload(n=20_000, views=3, d=48, width=100, height=75)
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    F = device_features(wl, range(3))
+    f, _ = ludvig.uplift(sc, wl.cams.params, wl.cams.width, wl.cams.height, F)
+    mask = torch.from_numpy(inputs.sphere_masks(wl.cams.subset([0]), radius=0.4)).cuda().contiguous()
+    u, _ = ludvig.uplift(sc, wl.cams.params[:1], wl.cams.width, wl.cams.height, mask)
+    torch.cuda.synchronize()
+    G = ludvig.Graph.rbf(sc, 16, f)
+    rp, col, _ = G.export()
+    rows = np.repeat(np.arange(sc.n), np.diff(rp.cpu().numpy()))
+    return dict(wl=wl, sc=sc, f=f, fn=f.cpu().numpy(), u=u[:, 0].contiguous(), G=G, rows=rows,
+                cols=col.cpu().numpy().astype(np.int64), rp=rp.cpu().numpy())
+
+
+def _csr(s, val):
+    n = s["sc"].n
+    return sp.csr_matrix((val.astype(np.float64), s["cols"], s["rp"]), shape=(n, n))
+
+
+def test_rbf_graph_pattern_scale_and_values(setup):
+    s = setup
+    nbr, _ = oracle.knn(s["wl"].scene.means, 16)
+    r_ref, c_ref = oracle.union_edges(nbr)
+    assert np.array_equal(s["rows"], r_ref) and np.array_equal(s["cols"], c_ref)
+    sf = s["G"].feature_scale
+    sf_ref = oracle.feature_scale(s["fn"], r_ref, c_ref)
+    print(f"s_f gpu {sf:.7f} oracle {sf_ref:.7f}")
+    assert abs(sf - sf_ref) <= 1e-5 * sf_ref
+    _, _, val = s["G"].export()
+    ref = oracle.edge_weights_rbf_unary(s["fn"], r_ref, c_ref, 1.0, sf)
+    assert rel_l2(val.cpu().numpy(), ref) <= 1e-5
+
+
+def test_g0_unary_and_reweight(setup):
+    s = setup
+    G, sc = s["G"], s["sc"]
+    g0 = ludvig.topfrac_positive(sc, s["u"], 10)
+    un = s["u"].cpu().numpy()
+    g0_ref = oracle.topfrac_positive(un, 10)
+    assert np.array_equal(g0.cpu().numpy(), g0_ref.astype(np.float32))
+    assert (g0_ref > 0).sum() == ((un > 0).sum() * 10 + 99) // 100 > 10
+    sf = G.feature_scale
+    P = G.unary_anchor(s["f"], g0, 0.5)
+    P_ref = oracle.unary_anchor(s["fn"], g0.cpu().numpy(), 0.5, sf)
+    Pn = P.cpu().numpy()
+    print(f"unary: rel L2 {rel_l2(Pn, P_ref):.2e}, range {Pn.min():.3g}..{Pn.max():.3g}")
+    assert rel_l2(Pn, P_ref) <= 1e-5
+    G.reweight(0.5, P, binarize=0.0, row_normalize=True)
+    _, _, val = G.export()
+    w_ref = oracle.edge_weights_rbf_unary(s["fn"], s["rows"], s["cols"], 0.5, sf, unary=Pn)
+    A_ref = oracle.csr(sc.n, s["rows"], s["cols"], w_ref, row_normalize=True)
+    assert rel_l2(val.cpu().numpy(), A_ref.data) <= 1e-5
+    G.reweight(0.5, P, binarize=1e-5, row_normalize=False)
+    _, _, vb = G.export()
+    vb = vb.cpu().numpy()
+    assert set(np.unique(vb).tolist()) <= {0.0, 1.0}
+    clear = np.abs(w_ref - 1e-5) > 1e-3 * 1e-5
+    assert np.array_equal(vb[clear], (w_ref[clear] > 1e-5).astype(np.float32))
+    print(f"binarised: {int(vb.sum())} of {vb.size} edges kept, {int((~clear).sum())} near the threshold")
+
+
+@pytest.mark.parametrize("steps", [1, 5, 30])
+def test_reach_weight_bitexact_on_gpu_graph(setup, steps):
+    s = setup
+    G, sc = s["G"], s["sc"]
+    g0 = ludvig.topfrac_positive(sc, s["u"], 10)
+    P = G.unary_anchor(s["f"], g0, 0.5)
+    G.reweight(0.5, P, binarize=1e-5, row_normalize=False)
+    _, _, vb = G.export()
+    A = _csr(s, vb.cpu().numpy())
+    g2 = torch.stack([g0, (torch.arange(sc.n, device="cuda") == 17).float()], 1).contiguous()
+    h = G.reach_weight(g2, steps, P).cpu().numpy()
+    h_ref = oracle.reach_weight(A, g2.cpu().numpy(), steps, P.cpu().numpy())
+    print(f"reach T={steps}: {(h[:, 0] > 0).sum()} and {(h[:, 1] > 0).sum()} nodes")
+    assert np.array_equal(h, h_ref.astype(np.float32))
+    h1 = G.reach_weight(g0, steps).cpu().numpy()
+    assert np.array_equal(h1, (h_ref[:, 0] > 0).astype(np.float32))
+
+
+def test_multi_query_diffusion_on_rbf_graph(setup):
+    s = setup
+    G, sc = s["G"], s["sc"]
+    G.reweight(0.5, None, binarize=0.0, row_normalize=True)
+    _, _, val = G.export()
+    A = _csr(s, val.cpu().numpy())
+    x0 = torch.rand((sc.n, 21), device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    y = G.diffuse(x0, 10).cpu().numpy()
+    ref = oracle.diffuse(A, x0.cpu().numpy(), 10)
+    assert rel_l2(y, ref) <= 1e-5
+
+
+def test_degenerate_scale_and_empty():
+    sc = ludvig.Scene.from_inputs(inputs.scene_uniform(2000, seed=3))
+    same = torch.ones((2000, 8), device="cuda")
+    G = ludvig.Graph.rbf(sc, 8, same)
+    assert G.feature_scale == 0.0
+    with pytest.raises(ludvig.LudvigError, match="ERR_ARG"):
+        G.reweight(0.5)
+    empty = inputs.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32),
+                         np.zeros((0, 4), np.float32), np.zeros((0,), np.float32))
+    G0 = ludvig.Graph.rbf(ludvig.Scene.from_inputs(empty), 8, torch.zeros((0, 8), device="cuda"))
+    assert G0.nnz == 0
