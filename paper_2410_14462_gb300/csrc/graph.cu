@@ -357,10 +357,8 @@ __global__ void __launch_bounds__(256) k_edge_weights_any(const uint32_t* __rest
         }
         ++o;
     }
-    if (row_normalize && lane == 0) {
-        const float inv = rsum > 0.f ? 1.0f / rsum : 0.f;
-        for (int64_t e = o0; e < o; ++e) val[e] *= inv;
-    }
+    if (row_normalize && lane == 0 && rsum > 0.f)   // divide: a denormal sum has an infinite reciprocal
+        for (int64_t e = o0; e < o; ++e) val[e] = val[e] / rsum;
 }
 
 // Same for df <= 32 kR: one warp per row with f_i in registers; the row's
@@ -448,9 +446,9 @@ __global__ void __launch_bounds__(256) k_edge_weights(const uint32_t* __restrict
     }
     if (row_normalize) {
         rsum = __shfl_sync(0xffffffffu, rsum, 0);
-        const float inv = rsum > 0.f ? 1.0f / rsum : 0.f;
         __syncwarp();
-        for (int64_t e = o0 + lane; e < o; e += 32) val[e] *= inv;
+        if (rsum > 0.f)   // divide: a denormal sum has an infinite reciprocal
+            for (int64_t e = o0 + lane; e < o; e += 32) val[e] = val[e] / rsum;
     }
 }
 
@@ -979,11 +977,11 @@ __global__ void __launch_bounds__(256) k_rbf_reweight(const int64_t* __restrict_
     const int64_t i = (int64_t)blockIdx.x * 8 + warp;
     if (i >= n) return;
     const int64_t e0 = rp[i], e1 = rp[i + 1];
-    const float pi = P ? P[i] : 1.f;
+    const float spi = P ? sqrtf(P[i]) : 1.f;   // sqrt(P_i) sqrt(P_j): the product P_i P_j may underflow
     float rsum = 0.f;
     for (int64_t e = e0 + lane; e < e1; e += 32) {
         float w = expf(-d2[e] * inv);
-        if (P) w *= sqrtf(pi * P[col[e]]);
+        if (P) w *= spi * sqrtf(P[col[e]]);
         if (binarize > 0.f) w = w > binarize ? 1.f : 0.f;
         val[e] = w;
         rsum += w;
@@ -991,8 +989,9 @@ __global__ void __launch_bounds__(256) k_rbf_reweight(const int64_t* __restrict_
     if (!row_normalize) return;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
-    const float s = rsum > 0.f ? 1.0f / rsum : 0.f;
-    for (int64_t e = e0 + lane; e < e1; e += 32) val[e] *= s;
+    // divide (not multiply by 1/sum): a denormal sum has an infinite reciprocal
+    if (rsum > 0.f)
+        for (int64_t e = e0 + lane; e < e1; e += 32) val[e] = val[e] / rsum;
 }
 
 // Sum of the normalised features of the anchor nodes (g0_i > 0), per channel,

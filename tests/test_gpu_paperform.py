@@ -75,16 +75,19 @@ def test_g0_unary_and_reweight(setup):
     assert np.array_equal(g0.cpu().numpy(), g0_ref.astype(np.float32))
     assert (g0_ref > 0).sum() == ((un > 0).sum() * 10 + 99) // 100 > 10
     sf = G.feature_scale
-    P = G.unary_anchor(s["f"], g0, 0.5)
-    P_ref = oracle.unary_anchor(s["fn"], g0.cpu().numpy(), 0.5, sf)
+    P = G.unary_anchor(s["f"], g0, 5.0)
+    P_ref = oracle.unary_anchor(s["fn"], g0.cpu().numpy(), 5.0, sf)
     Pn = P.cpu().numpy()
     print(f"unary: rel L2 {rel_l2(Pn, P_ref):.2e}, range {Pn.min():.3g}..{Pn.max():.3g}")
     assert rel_l2(Pn, P_ref) <= 1e-5
     G.reweight(0.5, P, binarize=0.0, row_normalize=True)
     _, _, val = G.export()
     w_ref = oracle.edge_weights_rbf_unary(s["fn"], s["rows"], s["cols"], 0.5, sf, unary=Pn)
-    A_ref = oracle.csr(sc.n, s["rows"], s["cols"], w_ref, row_normalize=True)
-    assert rel_l2(val.cpu().numpy(), A_ref.data) <= 1e-5
+    rs = np.bincount(s["rows"], weights=w_ref, minlength=sc.n)
+    a_ref = np.where(rs[s["rows"]] > 0, w_ref / np.where(rs[s["rows"]] > 0, rs[s["rows"]], 1.0), 0.0)
+    vn = val.cpu().numpy()
+    assert np.isfinite(vn).all()
+    assert rel_l2(vn, a_ref) <= 1e-5
     G.reweight(0.5, P, binarize=1e-5, row_normalize=False)
     _, _, vb = G.export()
     vb = vb.cpu().numpy()
@@ -99,7 +102,7 @@ def test_reach_weight_bitexact_on_gpu_graph(setup, steps):
     s = setup
     G, sc = s["G"], s["sc"]
     g0 = ludvig.topfrac_positive(sc, s["u"], 10)
-    P = G.unary_anchor(s["f"], g0, 0.5)
+    P = G.unary_anchor(s["f"], g0, 5.0)
     G.reweight(0.5, P, binarize=1e-5, row_normalize=False)
     _, _, vb = G.export()
     A = _csr(s, vb.cpu().numpy())
