@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-precision", action="store_true", help="skip the bf16 precision-form line")
     ap.add_argument("--no-render", action="store_true", help="skip the render-back (Eq. 4) line")
     ap.add_argument("--no-filter", action="store_true", help="skip the Gaussian-filtering line")
+    ap.add_argument("--no-paper-diffusion", action="store_true", help="skip the paper-form diffusion line")
     ap.add_argument("--profile-case", choices=["tc2views", "render2views", "render16views"], default=None,
                     help="run a small fixed case for an ncu capture and exit (no JSON line)")
     return ap.parse_args()
@@ -352,6 +353,71 @@ def beta_filter(sc, wl, beta, feats):
                          "launch_ms": sel_ms}}
 
 
+def paper_diffusion(sc, wl, f):
+    """Paper-form diffusion on the step's uplifted features f (Eq. 7 with the
+    appendix's S_f and P, Sec. 4.1): the scene part (kNN graph, edge feature
+    distances, s_f), the segmentation prompt (g_0 from the uplifted view-0
+    mask of a sphere around the first cluster centre, P with b_P = 5, A with
+    b = 0.5 binarised at 1e-5, reachability weight h after 100 steps) and the
+    21-query diffusion of 100 steps on the row-normalised RBF graph (the
+    paper's multi-query case).  Roofline of the reachability step kernel:
+    algorithmic bytes per step = the CSR streamed once (8 nnz + 8 n) + the bit
+    sets read and written once (8 n)."""
+    import torch
+    from paper_2410_14462_gb300 import inputs, ludvig
+    W, H = wl.cams.width, wl.cams.height
+    centre = inputs.cluster_centres(wl.seed)[0]
+    mask = torch.from_numpy(inputs.sphere_masks(wl.cams.subset([0]), radius=0.3, center=centre)).cuda()
+    u, _ = ludvig.uplift(sc, wl.cams.params[:1], W, H, mask.contiguous())
+    u = u[:, 0].contiguous()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=1):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3 / reps, r
+
+    scene_ms, G = timed(lambda: ludvig.Graph.rbf(sc, 16, f))
+    s_f = G.feature_scale
+
+    def prompt():
+        g0 = ludvig.topfrac_positive(sc, u, 10)
+        P = G.unary_anchor(f, g0, 5.0)
+        G.reweight(0.5, P, binarize=1e-5, row_normalize=False)
+        return G.reach_weight(g0, 100, P)
+
+    prompt()
+    torch.cuda.synchronize()
+    ludvig.trace_read(reset=True)
+    ludvig.trace_enable(True)
+    prompt_ms, h = timed(prompt, reps=3)
+    ludvig.trace_enable(False)
+    tr = ludvig.trace_read(reset=True)
+    reach_ms = tr["ms"]["diffuse"] / max(1, tr["calls"]["diffuse"]) / 100
+    reached = int((h > 0).sum().item())
+    anchors = int((ludvig.topfrac_positive(sc, u, 10) > 0).sum().item())
+    G.reweight(0.5, None, binarize=0.0, row_normalize=True)
+    x0 = torch.zeros((sc.n, 21), device="cuda")
+    x0[torch.arange(21, device="cuda") * 997, torch.arange(21, device="cuda")] = 1.0
+    q21_ms, _ = timed(lambda: G.diffuse(x0, 100), reps=2)
+    nnz = G.nnz
+    G.close()
+    peak, peak_kind = peaks()
+    alg = 8.0 * nnz + 16.0 * sc.n
+    achieved = alg / (reach_ms / 1e3) / 1e9
+    return {"scene_ms": scene_ms, "prompt_ms": prompt_ms, "q21_diffusion_100_steps_ms": q21_ms, "s_f": s_f,
+            "nnz": nnz, "anchors": anchors, "reached_after_100_steps": reached,
+            "config": {"k": 16, "b": 0.5, "b_P": 5.0, "binarize": 1e-5, "steps": 100, "g0": "top 10 % of the "
+                       "uplifted view-0 mask", "queries_multi": 21},
+            "roofline": {"bound": "hbm", "kernel": "k_reach_step", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                         "alg_bytes_per_launch": alg, "launch_ms": reach_ms}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -458,6 +524,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
         line["precision_form"] = precision_form(sc, wl)
         torch.cuda.empty_cache()
+    if rank == 0 and not args.no_paper_diffusion and args.workload == "paper" and args.dtype == "f32":
+        line["paper_diffusion"] = paper_diffusion(sc, wl, out)
     if rank == 0 and not args.no_render and args.dtype == "f32":
         feats = None
         torch.cuda.empty_cache()

@@ -178,14 +178,16 @@ def pixel_rays(cams: Cameras, v: int) -> tuple[np.ndarray, np.ndarray]:
     return cams.centers()[v], d
 
 
-def sphere_masks(cams: Cameras, radius: float = 0.4) -> np.ndarray:
+def sphere_masks(cams: Cameras, radius: float = 0.4, center=(0.0, 0.0, 0.0)) -> np.ndarray:
     """Binary masks [V,H,W,1] float32: 1 where the pixel ray passes within
-    ``radius`` of the world origin (a projected sphere, thresholded)."""
+    ``radius`` of ``center`` (a projected sphere, thresholded): the synthetic
+    stand-in for a reference frame's foreground mask."""
     out = np.zeros((cams.v, cams.height, cams.width, 1), dtype=np.float32)
+    c = np.asarray(center, dtype=np.float64)
     for v in range(cams.v):
         o, d = pixel_rays(cams, v)
-        # distance from the origin to the line o + s d (the sphere is in front)
-        cr = np.cross(np.broadcast_to(o, d.shape), d)
+        # distance from the centre to the line o + s d (the sphere is in front)
+        cr = np.cross(np.broadcast_to(o - c, d.shape), d)
         out[v, :, :, 0] = (np.linalg.norm(cr, axis=-1) < radius).astype(np.float32)
     return out
 
