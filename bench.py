@@ -353,9 +353,11 @@ def beta_filter(sc, wl, beta, feats):
                          "launch_ms": sel_ms}}
 
 
-def paper_diffusion(sc, wl, f):
-    """Paper-form diffusion on the step's uplifted features f (Eq. 7 with the
-    appendix's S_f and P, Sec. 4.1): the scene part (kNN graph, edge feature
+def paper_diffusion(sc, wl, f_all, beta):
+    """Paper-form diffusion in the paper's order: the half of the Gaussians
+    with the largest beta of the step's uplift is kept (Sec. 5), and their
+    uplifted features f are used (Eq. 7 with the appendix's S_f and P, Sec.
+    4.1): the scene part (kNN graph, edge feature
     distances, s_f), the segmentation prompt (g_0 from the uplifted view-0
     mask of a sphere around the first cluster centre, P with b_P = 5, A with
     b = 0.5 binarised at 1e-5, reachability weight h after 100 steps) and the
@@ -368,9 +370,11 @@ def paper_diffusion(sc, wl, f):
     W, H = wl.cams.width, wl.cams.height
     centre = inputs.cluster_centres(wl.seed)[0]
     mask = torch.from_numpy(inputs.sphere_masks(wl.cams.subset([0]), radius=0.3, center=centre)).cuda()
+    kept = ludvig.beta_select(sc, beta, sc.n - sc.n // 2)
+    full, sc = sc, sc.subset(kept)
+    f = f_all[kept.long()].contiguous()
     u, _ = ludvig.uplift(sc, wl.cams.params[:1], W, H, mask.contiguous())
     u = u[:, 0].contiguous()
-    ev = lambda: torch.cuda.Event(enable_timing=True)
 
     def timed(fn, reps=1):
         fn()
@@ -406,10 +410,12 @@ def paper_diffusion(sc, wl, f):
     q21_ms, _ = timed(lambda: G.diffuse(x0, 100), reps=2)
     nnz = G.nnz
     G.close()
+    n_kept = sc.n
+    sc.close()
     peak, peak_kind = peaks()
-    alg = 8.0 * nnz + 16.0 * sc.n
+    alg = 8.0 * nnz + 16.0 * n_kept
     achieved = alg / (reach_ms / 1e3) / 1e9
-    return {"scene_ms": scene_ms, "prompt_ms": prompt_ms, "q21_diffusion_100_steps_ms": q21_ms, "s_f": s_f,
+    return {"gaussians": n_kept, "of": full.n, "scene_ms": scene_ms, "prompt_ms": prompt_ms, "q21_diffusion_100_steps_ms": q21_ms, "s_f": s_f,
             "nnz": nnz, "anchors": anchors, "reached_after_100_steps": reached,
             "config": {"k": 16, "b": 0.5, "b_P": 5.0, "binarize": 1e-5, "steps": 100, "g0": "top 10 % of the "
                        "uplifted view-0 mask", "queries_multi": 21},
@@ -525,7 +531,7 @@ def run_ours(args):
         line["precision_form"] = precision_form(sc, wl)
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_paper_diffusion and args.workload == "paper" and args.dtype == "f32":
-        line["paper_diffusion"] = paper_diffusion(sc, wl, out)
+        line["paper_diffusion"] = paper_diffusion(sc, wl, out, beta)
     if rank == 0 and not args.no_render and args.dtype == "f32":
         feats = None
         torch.cuda.empty_cache()

@@ -141,35 +141,43 @@ def test_fullsize_beta_select(paper):
 
 
 def test_fullsize_paper_diffusion_reach(paper):
-    """Paper-form diffusion at full size (1M Gaussians, D = 384 field uplifted
-    from views 0-15): s_f within 1e-5 of the oracle's median over the GPU's
-    edges, and the reachability weight after 100 steps bit-exact against the
-    oracle's walk on the GPU's binarised graph."""
+    """Paper-form diffusion at full size, in the paper's order: uplift all 150
+    views (a D = 32 field), keep the half of the 1M Gaussians with the largest
+    beta (Sec. 5), then on the filtered scene: s_f within 1e-5 of the oracle's
+    median over the GPU's edges, g_0 bit-exact, and the reachability weight
+    after 100 steps bit-exact against the oracle's walk on the GPU's binarised
+    graph."""
     import scipy.sparse as sp
     wl = paper
-    W, H = wl.cams.width, wl.cams.height
+    W, H, V = wl.cams.width, wl.cams.height, wl.cams.v
     sc = ludvig.Scene.from_inputs(wl.scene)
-    F = torch.stack([wl.features(v, device="cuda") for v in range(16)]).contiguous()
-    f, _ = ludvig.uplift(sc, wl.cams.params[:16], W, H, F)
+    F = torch.empty((V, H, W, 32), dtype=torch.float32, device="cuda")
+    for v in range(V):
+        F[v] = wl.features_d(v, 32, device="cuda")
+    f_all, beta = ludvig.uplift(sc, wl.cams.params, W, H, F)
     del F
+    torch.cuda.empty_cache()
+    kept = ludvig.beta_select(sc, beta, sc.n - sc.n // 2)
+    sub = sc.subset(kept)
+    f = f_all[kept.long()].contiguous()
     centre = inputs.cluster_centres(wl.seed)[0]
     mask = torch.from_numpy(inputs.sphere_masks(wl.cams.subset([0]), radius=0.3, center=centre)).cuda()
-    u, _ = ludvig.uplift(sc, wl.cams.params[:1], W, H, mask.contiguous())
+    u, _ = ludvig.uplift(sub, wl.cams.params[:1], W, H, mask.contiguous())
     u = u[:, 0].contiguous()
-    G = ludvig.Graph.rbf(sc, 16, f)
+    G = ludvig.Graph.rbf(sub, 16, f)
     rp, col, _ = G.export()
     rp_n, col_n = rp.cpu().numpy(), col.cpu().numpy().astype(np.int64)
-    rows = np.repeat(np.arange(sc.n), np.diff(rp_n))
+    rows = np.repeat(np.arange(sub.n), np.diff(rp_n))
     sf_ref = oracle.feature_scale(f.cpu().numpy(), rows, col_n)
-    assert abs(G.feature_scale - sf_ref) <= 1e-5 * sf_ref
-    g0 = ludvig.topfrac_positive(sc, u, 10)
+    assert sf_ref > 0 and abs(G.feature_scale - sf_ref) <= 1e-5 * sf_ref
+    g0 = ludvig.topfrac_positive(sub, u, 10)
     assert np.array_equal(g0.cpu().numpy(), oracle.topfrac_positive(u.cpu().numpy(), 10).astype(np.float32))
     P = G.unary_anchor(f, g0, 5.0)
     G.reweight(0.5, P, binarize=1e-5, row_normalize=False)
     _, _, vb = G.export()
-    A = sp.csr_matrix((vb.cpu().numpy().astype(np.float64), col_n, rp_n), shape=(sc.n, sc.n))
+    A = sp.csr_matrix((vb.cpu().numpy().astype(np.float64), col_n, rp_n), shape=(sub.n, sub.n))
     h = G.reach_weight(g0, 100, P).cpu().numpy()
     h_ref = oracle.reach_weight(A, g0.cpu().numpy(), 100, P.cpu().numpy())
-    print(f"full size paper diffusion: s_f {G.feature_scale:.5f}, {(g0 > 0).sum().item()} anchors, "
-          f"{(h > 0).sum()} nodes reached after 100 steps")
+    print(f"full size paper diffusion: {sub.n} Gaussians kept, s_f {G.feature_scale:.5f}, "
+          f"{(g0 > 0).sum().item()} anchors, {(h > 0).sum()} nodes reached after 100 steps")
     assert np.array_equal(h, h_ref.astype(np.float32))
