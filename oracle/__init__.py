@@ -395,6 +395,21 @@ def reach_weight(A, g0, T, unary=None):
     return h[:, 0] if squeeze else h
 
 
+def relevancy(feats, phi_queries, phi_canon, temperature=10.0):
+    """Relevancy of uplifted CLIP features to text queries (appendix, relevancy
+    scores): r_iq = min_k exp(T s_iq) / (exp(T s_iq) + exp(T s_ik)), with s the
+    dot products of the l2-normalised feature f^_i with the l2-normalised query
+    and canonical-phrase embeddings.  Returns [n, q] float64."""
+    fh = _unit_rows(feats)
+    pq = _unit_rows(phi_queries)
+    pc = _unit_rows(phi_canon)
+    sq = fh @ pq.T                                  # [n, q]
+    sc = fh @ pc.T                                  # [n, k]
+    eq = np.exp(temperature * sq)[:, :, None]
+    ec = np.exp(temperature * sc)[:, None, :]
+    return np.min(eq / (eq + ec), axis=2)
+
+
 def csr(n, rows, cols, vals, row_normalize=True, binarize=0.0):
     """scipy CSR matrix of the graph.  With ``binarize`` > 0 every weight above
     the threshold becomes 1 and the rest 0 (the segmentation variant of Sec. 4.1
