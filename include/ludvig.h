@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define LUDVIG_ABI_VERSION 4
+#define LUDVIG_ABI_VERSION 5
 
 typedef enum {
     LUDVIG_OK = 0,
@@ -68,8 +68,12 @@ typedef enum {
 
 /* Process-wide options (ludvig_set_option / ludvig_get_option). */
 typedef enum {
-    LUDVIG_OPT_F32_TENSOR_CORES = 0   /* 1 (default): float32 features use the split-bfloat16
+    LUDVIG_OPT_F32_TENSOR_CORES = 0,  /* 1 (default): float32 features use the split-bfloat16
                                          tensor-core kernel where it applies; 0: CUDA-core FFMA */
+    LUDVIG_OPT_COUNT_NORMALISE = 1    /* 0 (default): the uplift divides by sum_{v,p} w_i (Eq. 3).
+                                         1: GaussianEditor's normaliser (appendix, comparison
+                                         with GaussianEditor): the number of (view, pixel) pairs
+                                         with w_i > 0; beta/den then hold those counts */
 } ludvig_option;
 
 /* Sets an option; LUDVIG_ERR_ARG for an unknown option. */
@@ -189,6 +193,19 @@ ludvig_status ludvig_beta_select(ludvig_scene_t scene, const float* beta, int64_
 ludvig_status ludvig_scene_subset(ludvig_scene_t scene, const int32_t* idx, int64_t m, void* stream,
                                   ludvig_scene_t* out);
 
+/* Relevancy of uplifted CLIP features to text queries (appendix, "Relevancy
+ * scores", after LERF):
+ *   r[i, q] = min_k exp(T s_iq) / (exp(T s_iq) + exp(T s_ik))
+ * with s_iq = f^_i . phi^_q, s_ik = f^_i . phi^_{n_queries + k}, every vector
+ * l2-normalised inside (a zero feature scores 1/2).
+ *   feats: device [n, d] float32; phi: device [n_queries + n_canon, d]
+ *   float32, the queries first, then the canonical phrases ("object",
+ *   "things", "stuff", "texture" in the paper); r: device [n, n_queries].
+ * 1 <= n_queries, 1 <= n_canon, n_queries + n_canon <= 64 and
+ * (n_queries + n_canon) * d <= 49152; temperature > 0 (the paper's T = 10). */
+ludvig_status ludvig_relevancy(const float* feats, int64_t n, int32_t d, const float* phi, int32_t n_queries,
+                               int32_t n_canon, float temperature, float* r, void* stream);
+
 /* ---- tracing ------------------------------------------------------------ */
 
 /* Stages of the path, as reported by ludvig_trace_read. */
@@ -206,8 +223,9 @@ typedef enum {
     LUDVIG_STAGE_AGGREGATE = 10,  /* inside COMPOSITE: tensor-core path, W F products into num/den */
     LUDVIG_STAGE_RENDER = 11,     /* ludvig_render, stage 6: weights + W f products */
     LUDVIG_STAGE_RENDER_PRODUCT = 12, /* inside RENDER: the W f products alone */
-    LUDVIG_STAGE_FILTER = 13,     /* ludvig_beta_select */
-    LUDVIG_STAGE_COUNT = 14
+    LUDVIG_STAGE_FILTER = 13,     /* ludvig_beta_select, ludvig_topfrac_positive */
+    LUDVIG_STAGE_RELEVANCY = 14,  /* ludvig_relevancy */
+    LUDVIG_STAGE_COUNT = 15
 } ludvig_stage;
 
 typedef struct {

@@ -252,13 +252,18 @@ def normalise(num: np.ndarray, den: np.ndarray) -> np.ndarray:
     return out
 
 
-def uplift(scene, cams, features, views=None, mode=MODE_HYBRID, want=None, nthreads=None):
+def uplift(scene, cams, features, views=None, mode=MODE_HYBRID, want=None, nthreads=None,
+           count_normalise=False):
     """Uplift over ``views`` (default all): returns (f [N,D], beta [N]) in float64.
 
     ``features(v)`` returns the [H,W,D] float32 map of view v (numpy or torch).
+    With ``count_normalise`` the normaliser is GaussianEditor's (appendix,
+    comparison with GaussianEditor): the number of (view, pixel) pairs with
+    w_i > 0, returned in place of beta.
     """
     views = range(cams.v) if views is None else views
     num = den = None
+    cnt = np.zeros(scene.n, np.float64)
     for v in views:
         F = features(v)
         F = F.cpu().numpy() if hasattr(F, "cpu") else np.asarray(F)
@@ -266,8 +271,12 @@ def uplift(scene, cams, features, views=None, mode=MODE_HYBRID, want=None, nthre
         if num is None:
             num = np.zeros((scene.n, F.shape[-1]), np.float64)
             den = np.zeros(scene.n, np.float64)
-        view_uplift(scene, cams.params[v], cams.width, cams.height, F, num, den, mode=mode,
-                    want=want, nthreads=nthreads)
+        res = view_uplift(scene, cams.params[v], cams.width, cams.height, F, num, den, mode=mode,
+                          want=want, nthreads=nthreads, triplets=count_normalise)
+        if count_normalise:
+            cnt += np.bincount(res["gid"], minlength=scene.n)
+    if count_normalise:
+        return normalise(num, cnt), cnt
     return normalise(num, den), den
 
 

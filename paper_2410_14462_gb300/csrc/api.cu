@@ -195,14 +195,19 @@ extern "C" int64_t ludvig_scene_size(ludvig_scene_t s) { return s ? s->n : -1; }
 namespace ludvig {
 namespace {
 std::atomic<int64_t> g_opt_f32_tc{1};
+std::atomic<int64_t> g_opt_count{0};
 }
 bool option_f32_tensor_cores() { return g_opt_f32_tc.load() != 0; }
+bool option_count_normalise() { return g_opt_count.load() != 0; }
 }  // namespace ludvig
 
 extern "C" ludvig_status ludvig_set_option(int32_t option, int64_t value) {
     switch (option) {
         case LUDVIG_OPT_F32_TENSOR_CORES:
             g_opt_f32_tc.store(value != 0);
+            return LUDVIG_OK;
+        case LUDVIG_OPT_COUNT_NORMALISE:
+            g_opt_count.store(value != 0);
             return LUDVIG_OK;
         default:
             set_error("unknown option %d", option);
@@ -213,6 +218,7 @@ extern "C" ludvig_status ludvig_set_option(int32_t option, int64_t value) {
 extern "C" int64_t ludvig_get_option(int32_t option) {
     switch (option) {
         case LUDVIG_OPT_F32_TENSOR_CORES: return g_opt_f32_tc.load();
+        case LUDVIG_OPT_COUNT_NORMALISE: return g_opt_count.load();
         default: return -1;
     }
 }

@@ -39,6 +39,7 @@ constexpr int kMaxViews = 16;
 
 bool tc_supported(int dtype, int d);
 bool option_f32_tensor_cores();
+bool option_count_normalise();
 ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, int width, int height,
                            const void* feats, int dtype, int d, float* num, float* den, Arena& ws, int* status,
                            int64_t* chunk_cap, cudaStream_t st);
@@ -258,6 +259,7 @@ struct CompositeArgs {
     float* den;
     float* dbg_t;           // [H*W] view 0 only, or null
     int32_t* dbg_cnt;
+    int count_den;          // den += the number of non-zero weights instead of their sum
 };
 
 struct CompositeSmem {
@@ -288,7 +290,7 @@ __device__ void flush_store(CompositeSmem& sm, const CompositeArgs& a, const TIn
         for (int r = warp; r < R; r += 8) {
             const uint32_t st = sm.row_start[r], c = sm.row_cnt[r];
             float s = 0.f;
-            for (uint32_t k = lane; k < c; k += 32) s += sm.store_w[st + k];
+            for (uint32_t k = lane; k < c; k += 32) s += a.count_den ? 1.f : sm.store_w[st + k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (lane == 0) atomicAdd(a.den + sm.row_gid[r], s);
@@ -824,6 +826,7 @@ ludvig_status run_chunk(ludvig_scene* s, const ludvig_camera* cams, int nv, int 
     args.den = den;
     args.dbg_t = dbg ? dbg->t_final : nullptr;
     args.dbg_cnt = dbg ? dbg->n_contrib : nullptr;
+    args.count_den = option_count_normalise() ? 1 : 0;
     const bool vec = (d % 4 == 0);
     StageScope scope(LUDVIG_STAGE_COMPOSITE, st);
     if (use_tensor_cores(dtype, d)) {

@@ -57,6 +57,8 @@
 
 namespace ludvig {
 
+bool option_count_normalise();
+
 namespace {
 
 using namespace tc;
@@ -91,6 +93,7 @@ struct WeightsArgs {
     int cap;
     float* chunk_den;       // [cap][128][NT]: each row's sum of its weight term (rewritten on a re-run)
     int* status;
+    int count_den;          // chunk_den holds each row's count of non-zero weights (term 0; term 1: 0)
 };
 
 template <int NT>
@@ -102,6 +105,24 @@ struct WeightsSmem {
     int cur_chunk, cur_start, next_chunk;
     int abort_flag;
 };
+
+// A weight row's contribution to den, from its 256 bfloat16 values (8 per
+// lane, packed in wv), summed over the warp: the sum of the term's values, or
+// with count_den the number of non-zero weights (counted on term 0; a weight
+// w > 0 is at least 1/255 * 1e-4, far above the smallest bfloat16).
+__device__ __forceinline__ float row_den(const uint32_t* wv, int count_den, int term) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (count_den)
+            s += term == 0 ? (float)((wv[k] & 0xffffu) != 0u) + (float)((wv[k] >> 16) != 0u) : 0.f;
+        else
+            s += __uint_as_float(wv[k] << 16) + __uint_as_float(wv[k] & 0xffff0000u);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
 
 __device__ __forceinline__ void finish_chunk(const WeightsArgs& a, int c, int rows, int next) {
     if (c >= 0 && c < a.cap) {
@@ -264,12 +285,7 @@ __global__ void __launch_bounds__(256, 4) k_weights(WeightsArgs a) {
                     }
                     *src = make_uint4(0u, 0u, 0u, 0u);
                     const uint32_t wv[4] = {v4.x, v4.y, v4.z, v4.w};
-                    float sden = 0.f;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        sden += __uint_as_float(wv[k] << 16) + __uint_as_float(wv[k] & 0xffff0000u);
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) sden += __shfl_xor_sync(0xffffffffu, sden, o);
+                    const float sden = row_den(wv, a.count_den, t);
                     if (lane == 0 && keep) a.chunk_den[((size_t)ch * kCRows + local) * NT + t] = sden;
                 }
                 if (lane == 0 && keep) a.chunk_gid[(size_t)ch * kCRows + local] = rec[j].gid;
@@ -290,12 +306,7 @@ __global__ void __launch_bounds__(256, 4) k_weights(WeightsArgs a) {
                     *reinterpret_cast<uint4*>(a.wg1 + (size_t)ch * kChunkBytes + local * kRowBytes + lane * 16) = v4;
                 *src = make_uint4(0u, 0u, 0u, 0u);
                 const uint32_t wv[4] = {v4.x, v4.y, v4.z, v4.w};
-                float sden = 0.f;
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    sden += __uint_as_float(wv[k] << 16) + __uint_as_float(wv[k] & 0xffff0000u);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) sden += __shfl_xor_sync(0xffffffffu, sden, o);
+                const float sden = row_den(wv, a.count_den, 0);
                 if (lane == 0 && ch >= 0 && ch < a.cap) a.chunk_den[(size_t)ch * kCRows + local] = sden;
             }
             if (tid < kTcBatch && ((rowmask >> tid) & 1u)) {
@@ -1314,6 +1325,7 @@ ludvig_status tile_weights(const PairRec* pairs, const uint2* ranges, int nv, in
         w.cap = (int)cap;
         w.chunk_den = t.cden;
         w.status = status;
+        w.count_den = option_count_normalise() ? 1 : 0;
         const int tslot = trace_on() ? trace_begin(LUDVIG_STAGE_WEIGHTS, st) : -1;
         if (NT == 2)
             k_weights<2><<<nitems, 256, 0, st>>>(w);

@@ -40,6 +40,7 @@ SIGNATURES = {
     "ludvig_uplift_host": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
     "ludvig_render": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _P, _P]),
     "ludvig_beta_select": (_I32, [_P, _P, _I64, _P, _P]),
+    "ludvig_relevancy": (_I32, [_P, _I64, _I32, _P, _I32, _I32, _F, _P, _P]),
     "ludvig_graph_build_rbf": (_I32, [_P, _I32, _P, _I32, _P, ctypes.POINTER(_P)]),
     "ludvig_graph_feature_scale": (_I32, [_P, ctypes.POINTER(_F)]),
     "ludvig_graph_reweight": (_I32, [_P, _F, _P, _F, _I32, _P]),
@@ -263,7 +264,23 @@ def topfrac_positive(scene: Scene, u: torch.Tensor, percent: int = 10, stream=No
     return g0
 
 
+def relevancy(feats: torch.Tensor, phi_queries: torch.Tensor, phi_canon: torch.Tensor, temperature: float = 10.0,
+              out=None, stream=None) -> torch.Tensor:
+    """LERF relevancy r [n, q] of features [n, d] to query embeddings [q, d]
+    against canonical-phrase embeddings [k, d] (ludvig_relevancy)."""
+    n, d = feats.shape
+    phi = torch.cat([phi_queries, phi_canon]).to(torch.float32).contiguous()
+    nq = int(phi_queries.shape[0])
+    if out is None:
+        out = torch.empty((n, nq), dtype=torch.float32, device=feats.device)
+    _check(load().ludvig_relevancy(_dev(feats, torch.float32, "feats"), int(n), int(d), _dev(phi), nq,
+                                   int(phi_canon.shape[0]), float(temperature), _dev(out, torch.float32, "r"),
+                                   _stream(stream)), "ludvig_relevancy")
+    return out
+
+
 OPT_F32_TENSOR_CORES = 0
+OPT_COUNT_NORMALISE = 1
 
 
 def set_option(option: int, value: int):
@@ -275,7 +292,7 @@ def get_option(option: int) -> int:
 
 
 STAGES = ["project", "depth_sort", "bin", "tile_sort", "composite", "normalise", "knn", "graph", "diffuse",
-          "weights", "aggregate", "render", "render_product", "filter"]
+          "weights", "aggregate", "render", "render_product", "filter", "relevancy"]
 
 
 class TraceStruct(ctypes.Structure):

@@ -211,3 +211,36 @@ def test_exp32_accuracy():
     assert (np.abs(e - ref) / ulp).max() <= 1.0
     assert oracle.exp32(np.array([0.0], np.float32))[0] == 1.0
     assert oracle.exp32(np.array([-100.0], np.float32))[0] == 0.0
+
+
+def test_count_normalised_uplift():
+    """GaussianEditor's normaliser (appendix): f_i = sum w F / |S_i|.  One
+    Gaussian: |S| is the number of pixels with w >= 1/255 (the closed form of
+    the single-Gaussian pin); in general f_count * count = f * beta = num."""
+    fx, fy, z = 120.0, 90.0, 4.0
+    cam = np.zeros(16, np.float32)
+    cam[[0, 4, 8]] = 1
+    cam[12:16] = (fx, fy, 40.5, 30.5)
+    sc = inputs.Scene(np.array([[0, 0, z]], np.float32), np.array([[0.05, 0.09, 0.02]], np.float32),
+                      np.array([[1, 0, 0, 0]], np.float32), np.array([0.7], np.float32))
+    W, H = 81, 61
+    a = (fx * float(np.float32(0.05))) ** 2 / z ** 2 + 0.3
+    c = (fy * float(np.float32(0.09))) ** 2 / z ** 2 + 0.3
+    op = float(np.float32(0.7))
+    F = (np.arange(H * W, dtype=np.float32) / (H * W)).reshape(H, W, 1)
+    cams = inputs.Cameras(cam[None, :], W, H)
+    fc, cnt = oracle.uplift(sc, cams, lambda v: F, mode=oracle.MODE_FP64, count_normalise=True)
+    ws = {}
+    for v in range(H):
+        for u in range(W):
+            dx, dy = u + 0.5 - 40.5, v + 0.5 - 30.5
+            wv = min(0.99, op * math.exp(-0.5 * (dx * dx / a + dy * dy / c)))
+            if wv >= 1 / 255:
+                ws[v * W + u] = wv
+    assert cnt[0] == len(ws)
+    assert abs(fc[0, 0] - sum(w * float(F.reshape(-1)[k]) for k, w in ws.items()) / len(ws)) < 1e-12
+    wl = inputs.small_field_workload(n=3000, views=2, d=4)
+    f, beta = oracle.uplift(wl.scene, wl.cams, lambda v: wl.features(v))
+    fc, cnt = oracle.uplift(wl.scene, wl.cams, lambda v: wl.features(v), count_normalise=True)
+    assert np.array_equal(cnt > 0, beta > 0) and (cnt == np.round(cnt)).all()
+    np.testing.assert_allclose(fc * cnt[:, None], f * beta[:, None], rtol=1e-12, atol=1e-12)
