@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-render", action="store_true", help="skip the render-back (Eq. 4) line")
     ap.add_argument("--no-filter", action="store_true", help="skip the Gaussian-filtering line")
     ap.add_argument("--no-paper-diffusion", action="store_true", help="skip the paper-form diffusion line")
+    ap.add_argument("--no-relevancy", action="store_true", help="skip the relevancy / count-normaliser lines")
     ap.add_argument("--profile-case", choices=["tc2views", "render2views", "render16views"], default=None,
                     help="run a small fixed case for an ncu capture and exit (no JSON line)")
     return ap.parse_args()
@@ -424,6 +425,61 @@ def paper_diffusion(sc, wl, f_all, beta):
                          "alg_bytes_per_launch": alg, "launch_ms": reach_ms}}
 
 
+def relevancy_line(f):
+    """LERF relevancy (appendix) of the step's uplifted features f [N, D] to 21
+    seeded query embeddings against 4 canonical-phrase embeddings (T = 10),
+    timed with CUDA events.  Roofline: algorithmic bytes = f read once (4 N D)
+    + r written once (4 N q)."""
+    import torch
+    from paper_2410_14462_gb300 import ludvig
+    n, d = f.shape
+    g = torch.Generator(device="cuda").manual_seed(11)
+    pq = torch.randn((21, d), device="cuda", generator=g)
+    pc = torch.randn((4, d), device="cuda", generator=g)
+    r = ludvig.relevancy(f, pq, pc, 10.0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record()
+    for _ in range(reps):
+        ludvig.relevancy(f, pq, pc, 10.0, out=r)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    alg = 4.0 * n * d + 4.0 * n * 21
+    peak, peak_kind = peaks()
+    achieved = alg / (ms / 1e3) / 1e9
+    return {"ms": ms, "gaussians": n, "d": d, "queries": 21, "phrases": 4,
+            "roofline": {"bound": "hbm", "kernel": "k_relevancy", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                         "alg_bytes_per_launch": alg, "launch_ms": ms}}
+
+
+def count_normalised_line(sc, wl, feats):
+    """The uplift of the step's 150 views with GaussianEditor's normaliser
+    (LUDVIG_OPT_COUNT_NORMALISE = 1): same kernels, the weights kernel counts
+    instead of summing; CUDA events around one uplift after a warm-up."""
+    import torch
+    from paper_2410_14462_gb300 import ludvig
+    V, H, W, D = wl.cams.v, wl.cams.height, wl.cams.width, int(feats.shape[-1])
+    out = torch.empty((sc.n, D), dtype=torch.float32, device="cuda")
+    cnt = torch.empty((sc.n,), dtype=torch.float32, device="cuda")
+    ludvig.set_option(ludvig.OPT_COUNT_NORMALISE, 1)
+    try:
+        ludvig.uplift(sc, wl.cams.params, W, H, feats, out, cnt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ludvig.uplift(sc, wl.cams.params, W, H, feats, out, cnt)
+        e1.record()
+        torch.cuda.synchronize()
+    finally:
+        ludvig.set_option(ludvig.OPT_COUNT_NORMALISE, 0)
+    ms = e0.elapsed_time(e1)
+    return {"ms": ms, "value": V * D / (ms / 1e3), "unit": UNIT,
+            "max_count": float(cnt.max().item()), "gaussians_counted": int((cnt > 0).sum().item())}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -522,6 +578,9 @@ def run_ours(args):
                        "d2h_bytes_per_step": int(sc.n * (D + 1) * 4),
                        "sample": f"views 0-{nv - 1} of {V} through ludvig_uplift_host (uplift only)"}
         del hf
+    if rank == 0 and not args.no_relevancy and args.workload == "paper" and args.dtype == "f32":
+        line["count_normalised_uplift"] = count_normalised_line(sc, wl, feats)
+        line["relevancy"] = relevancy_line(out)
     if rank == 0 and not args.no_filter and args.workload == "paper" and args.dtype == "f32":
         line["beta_filter"] = beta_filter(sc, wl, beta, feats)
     if rank == 0 and not args.no_precision and args.workload == "paper":
