@@ -484,7 +484,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2410_14462_gb300 import build, inputs, ludvig
+    from paper_2410_14462_gb300 import build, inputs, ludvig, shard
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -541,10 +541,7 @@ def run_ours(args):
     ludvig.trace_enable(False)
     tr = ludvig.trace_read(reset=True)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = shard.max_over_ranks(ms, device="cuda")
     value = world * V * D / (ms / 1e3)
 
     launches = max(1.0, tr["calls"].get("aggregate", 0) / args.steps)

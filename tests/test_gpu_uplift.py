@@ -276,3 +276,17 @@ def test_f32_tensor_core_and_cuda_core_paths(d):
           f"cuda-core f {errs[0][0]:.2e} beta {errs[0][1]:.2e}")
     for e in errs.values():
         assert e[0] <= 1e-5 and e[1] <= 1e-5
+
+
+def test_sharded_uplift_single_process_equals_uplift():
+    """shard.sharded_uplift without a process group is the plain uplift."""
+    from paper_2410_14462_gb300 import shard
+    wl = inputs.small_field_workload(n=10_000, views=4, d=16)
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    F = device_features(wl, range(4))
+    W, H = wl.cams.width, wl.cams.height
+    whole, beta = ludvig.uplift(sc, wl.cams.params, W, H, F)
+    part, den = shard.sharded_uplift(sc, wl.cams.params, W, H, F)
+    torch.cuda.synchronize()
+    assert rel_l2(part.cpu().numpy(), whole.cpu().numpy()) < 1e-6
+    assert rel_l2(den.cpu().numpy(), beta.cpu().numpy()) < 1e-6
