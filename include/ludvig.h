@@ -310,7 +310,10 @@ ludvig_status ludvig_graph_export(ludvig_graph_t graph, int64_t* row_ptr, int32_
 /* Graph diffusion (Sec. 3.3, Eq. 8) on every column of x0 (device [n,dx]):
  *   g_0 = x0,  g_{t+1} = A (g_t / ||g_t||_2),  t < iters.
  * out: device [n,dx]; must not alias x0.  A column whose norm is 0 stays 0.
- * 1 <= dx <= 32. */
+ * 1 <= dx <= 32.  With dx = 1 the steps run on a sliced copy of the matrix
+ * (32-row slices, column-major) that the first call after the graph's values
+ * change builds in the graph's workspace; that call synchronises `stream`
+ * once. */
 ludvig_status ludvig_diffuse(ludvig_graph_t graph, const float* x0, int32_t dx, int32_t iters,
                              float* out, void* stream);
 
@@ -372,7 +375,7 @@ ludvig_status ludvig_reach_weight(ludvig_graph_t graph, const float* g0, int32_t
                                   const float* unary, float* h, void* stream);
 
 /* Graph diffusion that allocates no memory (the paper has no counterpart: this
- * is a service entry point).  It computes exactly what ludvig_diffuse
+ * is a service entry point).  It computes what ludvig_diffuse
  * computes, for callers that must not allocate device memory: a request loop
  * that runs under a strict no-allocation policy once it is warm, a process
  * whose device memory is already handed out to another allocator, or code
@@ -386,7 +389,9 @@ ludvig_status ludvig_reach_weight(ludvig_graph_t graph, const float* g0, int32_t
  * call before any stream capture.  All calls share the one scratch area, so
  * calls whose work overlaps on the GPU (different streams, or different host
  * threads without ordering) race; the call clears the norm slots it uses.
- * Arguments, layouts and results are those of ludvig_diffuse. */
+ * Arguments, layouts and results are those of ludvig_diffuse (to float32
+ * rounding: it keeps the CSR kernel, whose summation order within a row
+ * differs from the sliced one). */
 ludvig_status ludvig_diffuse_noalloc(ludvig_graph_t graph, const float* x0, int32_t dx, int32_t iters,
                                      float* out, void* stream);
 

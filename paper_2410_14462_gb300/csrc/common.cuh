@@ -120,6 +120,9 @@ struct ludvig_graph {
     float* val = nullptr;         // [nnz]
     float* d2 = nullptr;          // [nnz] ||f^_i - f^_j||^2 (RBF graphs only)
     float s_f = 0.f;              // median edge feature distance (RBF graphs only)
+    int val_version = 0;          // bumped whenever val changes
+    int sell_version = -1;        // val_version of the sliced copy in ws ("sell.*"), -1: none
+    int64_t sell_slices = 0;
     ludvig::Arena ws;
 };
 

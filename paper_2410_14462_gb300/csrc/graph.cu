@@ -547,6 +547,77 @@ __global__ void __launch_bounds__(256) k_spmv_scaled(const int64_t* __restrict__
     }
 }
 
+// Sliced copy of the matrix for single-column diffusion: slices of 32
+// consecutive rows, each padded to its longest row and stored column-major
+// (slot j of row r at off[slice] + 32 j + r % 32; padding: column = the row,
+// value 0).  One thread per row then reads its columns and values with
+// coalesced 128-byte warp loads and no row-pointer dependence.
+__global__ void k_sell_width(const int64_t* __restrict__ rp, int64_t n, int64_t nslices, uint32_t* __restrict__ slots) {
+    const int lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (s > nslices) return;
+    if (s == nslices) {   // the scan's total
+        if (lane == 0) slots[s] = 0u;
+        return;
+    }
+    const int64_t r = s * 32 + lane;
+    uint32_t len = r < n ? (uint32_t)(rp[r + 1] - rp[r]) : 0u;
+    len = __reduce_max_sync(0xffffffffu, len);
+    if (lane == 0) slots[s] = 32u * len;
+}
+
+__global__ void k_sell_fill(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            const float* __restrict__ val, int64_t n, int64_t nslices,
+                            const uint32_t* __restrict__ off, int32_t* __restrict__ scol, float* __restrict__ sval) {
+    const int lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (s >= nslices) return;
+    const int64_t r = s * 32 + lane;
+    const int64_t e0 = r < n ? rp[r] : 0;
+    const uint32_t len = r < n ? (uint32_t)(rp[r + 1] - e0) : 0u;
+    const uint32_t w = (off[s + 1] - off[s]) / 32u;
+    for (uint32_t j = 0; j < w; ++j) {
+        const uint32_t p = off[s] + 32u * j + (uint32_t)lane;
+        const bool real = j < len;
+        scol[p] = real ? col[e0 + j] : (int32_t)(r < n ? r : 0);
+        sval[p] = real ? val[e0 + j] : 0.f;
+    }
+}
+
+// y = A (x / ||x||) for one column on the sliced copy: a warp per slice, a
+// thread per row; ||y||^2 reduced per block, added once per block (float64).
+__global__ void __launch_bounds__(256) k_spmv_sell(const uint32_t* __restrict__ off, const int32_t* __restrict__ scol,
+                                                  const float* __restrict__ sval, const float* __restrict__ x,
+                                                  int64_t n, int64_t nslices, const double* __restrict__ n2_in,
+                                                  float* __restrict__ y, double* __restrict__ n2_out) {
+    __shared__ double part[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double nn = n2_in[0];
+    const float sc = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.f;
+    double mine = 0.0;
+    for (int64_t s = (int64_t)blockIdx.x * 8 + warp; s < nslices; s += (int64_t)gridDim.x * 8) {
+        const uint32_t o1 = off[s + 1];
+        float acc = 0.f;
+#pragma unroll 4
+        for (uint32_t p = off[s] + (uint32_t)lane; p < o1; p += 32u) acc = fmaf(sval[p], x[scol[p]], acc);
+        const int64_t r = s * 32 + lane;
+        if (r < n) {
+            acc *= sc;
+            y[r] = acc;
+            mine += (double)acc * acc;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if (lane == 0) part[warp] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += part[w];
+        atomicAdd(n2_out, t);
+    }
+}
+
 // *order (if given) receives the points' indices sorted by grid cell (valid
 // until the scene's workspace is reused), or null.
 ludvig_status knn_impl(ludvig_scene* s, int k, int32_t* nbr, cudaStream_t st, const uint32_t** order = nullptr) {
@@ -802,6 +873,49 @@ extern "C" ludvig_status ludvig_graph_export(ludvig_graph_t g, int64_t* row_ptr,
     return LUDVIG_OK;
 }
 
+namespace ludvig {
+namespace {
+
+// The sliced copy of g's current values (built on first use and again after
+// the values change; synchronises once to size it).  *ok = false when its
+// slot count does not fit 32 bits (the CSR kernel is used then).
+ludvig_status ensure_sell(ludvig_graph* g, cudaStream_t st, bool* ok, uint32_t** off, int32_t** scol,
+                          float** sval) {
+    *ok = false;
+    const int64_t n = g->n, nslices = ceil_div(n, 32);
+    uint32_t* slots;
+    uint64_t* total_d;
+    void* hb;
+    LV_TRY(g->ws.get("sell.slots", (size_t)nslices + 1, &slots));
+    LV_TRY(g->ws.get("sell.off", (size_t)nslices + 1, off));
+    LV_TRY(g->ws.get("sell.total", 1, &total_d));
+    LV_TRY(g->ws.pinned("sell.total_h", 16, &hb));
+    uint64_t* total_h = static_cast<uint64_t*>(hb);
+    if (g->sell_version == g->val_version) {
+        LV_TRY(g->ws.get("sell.col", (size_t)std::max<uint64_t>(*total_h, 1), scol));
+        LV_TRY(g->ws.get("sell.val", (size_t)std::max<uint64_t>(*total_h, 1), sval));
+        *ok = true;
+        return LUDVIG_OK;
+    }
+    k_sell_width<<<grid_for(nslices + 1, 8), 256, 0, st>>>(g->row_ptr, n, nslices, slots);
+    LV_LAUNCH();
+    LV_TRY(scan_exclusive_u32(slots, *off, nslices + 1, total_d, g->ws, st));
+    LV_CUDA(cudaMemcpyAsync(total_h, total_d, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    LV_CUDA(cudaStreamSynchronize(st));
+    if (*total_h >= ((uint64_t)1 << 32)) return LUDVIG_OK;
+    LV_TRY(g->ws.get("sell.col", (size_t)std::max<uint64_t>(*total_h, 1), scol));
+    LV_TRY(g->ws.get("sell.val", (size_t)std::max<uint64_t>(*total_h, 1), sval));
+    k_sell_fill<<<grid_for(nslices, 8), 256, 0, st>>>(g->row_ptr, g->col, g->val, n, nslices, *off, *scol, *sval);
+    LV_LAUNCH();
+    g->sell_version = g->val_version;
+    g->sell_slices = nslices;
+    *ok = true;
+    return LUDVIG_OK;
+}
+
+}  // namespace
+}  // namespace ludvig
+
 extern "C" ludvig_status ludvig_diffuse(ludvig_graph_t g, const float* x0, int32_t dx, int32_t iters,
                                         float* out, void* stream) {
     LV_ARG(g != nullptr, "graph is NULL");
@@ -832,10 +946,18 @@ extern "C" ludvig_status ludvig_diffuse(ludvig_graph_t g, const float* x0, int32
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, ceil_div(n, 32)));
+    bool sell = false;
+    uint32_t* soff = nullptr;
+    int32_t* scol = nullptr;
+    float* sval = nullptr;
+    if (dx == 1) LV_TRY(ensure_sell(g, st, &sell, &soff, &scol, &sval));
     const float* xin = x0;
     for (int t = 0; t < iters; ++t) {
         float* y = bufs[t & 1];
-        if (dx == 1)
+        if (sell)
+            k_spmv_sell<<<blocks, 256, 0, st>>>(soff, scol, sval, xin, n, g->sell_slices, n2 + 32 * t, y,
+                                                n2 + 32 * (t + 1));
+        else if (dx == 1)
             k_spmv_scaled<8><<<blocks, 256, 0, st>>>(g->row_ptr, g->col, g->val, xin, n, 1, n2 + 32 * t, y,
                                                      n2 + 32 * (t + 1));
         else
@@ -1183,6 +1305,7 @@ extern "C" ludvig_status ludvig_graph_reweight(ludvig_graph_t graph, float bandw
     LV_ARG(graph->s_f > 0.f, "the median edge distance is 0: the RBF similarity is undefined");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     StageScope scope(LUDVIG_STAGE_GRAPH, st);
+    ++graph->val_version;
     const float inv = 1.0f / (bandwidth * graph->s_f * graph->s_f);
     k_rbf_reweight<<<grid_for(graph->n, 8), 256, 0, st>>>(graph->row_ptr, graph->col, graph->d2, unary, graph->n,
                                                           inv, binarize, row_normalize, graph->val);

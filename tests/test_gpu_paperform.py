@@ -138,3 +138,18 @@ def test_degenerate_scale_and_empty():
                          np.zeros((0, 4), np.float32), np.zeros((0,), np.float32))
     G0 = ludvig.Graph.rbf(ludvig.Scene.from_inputs(empty), 8, torch.zeros((0, 8), device="cuda"))
     assert G0.nnz == 0
+
+
+def test_single_column_diffusion_follows_reweighting(setup):
+    """ludvig_diffuse with one column runs on a sliced copy of the matrix; a
+    reweighting must reach it (the copy is rebuilt when the values change)."""
+    s = setup
+    G, sc = s["G"], s["sc"]
+    x0 = torch.rand((sc.n,), device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    for b in (0.5, 2.0):
+        G.reweight(b, None, binarize=0.0, row_normalize=True)
+        _, _, val = G.export()
+        A = _csr(s, val.cpu().numpy())
+        y = G.diffuse(x0, 20).cpu().numpy()
+        ref = oracle.diffuse(A, x0.cpu().numpy(), 20)
+        assert rel_l2(y, ref) <= 1e-5, b
