@@ -130,3 +130,18 @@ def test_render_edge_cases():
         got = _render(small, fn, [0, 1])
         ref = oracle.render(wl.scene, cams, fn)
         assert rel_l2(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("d,tc", [(40, True), (5, False)])
+def test_render_spans_view_chunks(d, tc):
+    """20 views run as two launches (16 + 4 views); each view's map must land
+    at its own offset of the output."""
+    wl = inputs.small_field_workload(n=8000, views=20, d=d, width=45, height=37)
+    f = inputs.gaussian_features(wl.scene.n, d, seed=30 + d)
+    views = list(range(20))
+    got = _render(wl, f, views, tensor_cores=tc)
+    ref = oracle.render(wl.scene, wl.cams, f, views=views)
+    assert np.isfinite(got).all()
+    for v in (0, 15, 16, 19):
+        assert rel_l2(got[v], ref[v]) <= 1e-5, v
+    assert rel_l2(got, ref) <= 1e-5
