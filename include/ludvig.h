@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define LUDVIG_ABI_VERSION 5
+#define LUDVIG_ABI_VERSION 6
 
 typedef enum {
     LUDVIG_OK = 0,
@@ -276,6 +276,16 @@ ludvig_status ludvig_debug_transmittance(ludvig_scene_t scene, const ludvig_came
  * f: device [16,16,d] bfloat16 (a feature tile, pixel p = 16*y + x),
  * out: device [128,d] float32; d in {64, 128, ..., 512}.  Synchronises. */
 ludvig_status ludvig_debug_mma_bf16(const void* a, const void* f, int32_t d, float* out, void* stream);
+
+/* Failure-detection check of the bounded waits (the paper has no
+ * counterpart): one kernel waits on an mbarrier that nothing arrives on, with
+ * the same expiry logic the tensor-core kernels use but a budget of `cycles`
+ * SM clock cycles (0 .. 4e9; the kernels' own budget is 4e9, about 2 s).
+ * When it expires the kernel records LUDVIG_ERR_TIMEOUT in a status word and
+ * returns; nothing traps or faults, so the context stays usable.  Returns
+ * that status (LUDVIG_ERR_TIMEOUT) with *waited (may be NULL) = the cycles
+ * waited.  Synchronises `stream`. */
+ludvig_status ludvig_debug_wait_timeout(int64_t cycles, int64_t* waited, void* stream);
 
 /* ---- graph diffusion (Sec. 3.3) ----------------------------------------- */
 

@@ -1461,6 +1461,47 @@ ludvig_status render_tc(const PairRec* pairs, const uint2* ranges, int nv, int w
 
 using namespace ludvig;
 
+namespace ludvig {
+namespace {
+// Failure-detection check: a bounded wait on an mbarrier that nothing arrives
+// on expires, records LUDVIG_ERR_TIMEOUT and returns (the kernels' pattern).
+__global__ void k_wait_timeout(long long budget, int* status, long long* waited) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const long long t0 = clock64();
+    const bool ok = mbar_wait_for(&bar, 0u, budget);
+    *waited = clock64() - t0;
+    *status = ok ? (int)LUDVIG_OK : (int)LUDVIG_ERR_TIMEOUT;
+    mbar_arrive(&bar);   // complete the phase so that nothing is left pending
+}
+}  // namespace
+}  // namespace ludvig
+
+extern "C" ludvig_status ludvig_debug_wait_timeout(int64_t cycles, int64_t* waited, void* stream) {
+    LV_ARG(cycles >= 0 && cycles <= 4000000000ll, "cycles must be in [0, 4e9]");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    struct Out {
+        int status;
+        int pad;
+        long long waited;
+    };
+    Out* d = nullptr;
+    LV_CUDA(cudaMalloc(&d, sizeof(Out)));
+    k_wait_timeout<<<1, 32, 0, st>>>((long long)cycles, &d->status, &d->waited);
+    LV_LAUNCH();
+    Out h{};
+    const cudaError_t e1 = cudaMemcpyAsync(&h, d, sizeof(Out), cudaMemcpyDeviceToHost, st);
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaFree(d);
+    LV_CUDA(e1);
+    LV_CUDA(e2);
+    if (waited) *waited = h.waited;
+    if (h.status != LUDVIG_OK) set_error("bounded wait expired after %lld cycles", h.waited);
+    return (ludvig_status)h.status;
+}
+
 extern "C" ludvig_status ludvig_debug_mma_bf16(const void* a, const void* f, int32_t d, float* out, void* stream) {
     LV_ARG(a != nullptr && f != nullptr && out != nullptr, "NULL argument");
     LV_ARG(d % 64 == 0 && d >= 64 && d <= 512, "d must be 64..512 in steps of 64");

@@ -56,6 +56,7 @@ SIGNATURES = {
     "ludvig_debug_tile_lists": (_I32, [_P, _P, _I32, _I32, _I32, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "ludvig_debug_transmittance": (_I32, [_P, _P, _I32, _I32, _P, _P, _P]),
     "ludvig_debug_mma_bf16": (_I32, [_P, _P, _I32, _P, _P]),
+    "ludvig_debug_wait_timeout": (_I32, [_I64, ctypes.POINTER(_I64), _P]),
     "ludvig_knn": (_I32, [_P, _I32, _P, _P]),
     "ludvig_graph_build": (_I32, [_P, _I32, _P, _I32, _F, _F, _I32, _P, ctypes.POINTER(_P)]),
     "ludvig_graph_destroy": (_I32, [_P]),
