@@ -70,10 +70,17 @@ typedef enum {
 typedef enum {
     LUDVIG_OPT_F32_TENSOR_CORES = 0,  /* 1 (default): float32 features use the split-bfloat16
                                          tensor-core kernel where it applies; 0: CUDA-core FFMA */
-    LUDVIG_OPT_COUNT_NORMALISE = 1    /* 0 (default): the uplift divides by sum_{v,p} w_i (Eq. 3).
+    LUDVIG_OPT_COUNT_NORMALISE = 1,   /* 0 (default): the uplift divides by sum_{v,p} w_i (Eq. 3).
                                          1: GaussianEditor's normaliser (appendix, comparison
                                          with GaussianEditor): the number of (view, pixel) pairs
                                          with w_i > 0; beta/den then hold those counts */
+    LUDVIG_OPT_FAULT_ALLOC = 2,       /* host-side fault injection for tests: k > 0 makes the k-th
+                                         workspace allocation from now fail once with
+                                         LUDVIG_ERR_OOM (nothing is allocated); 0 disarms */
+    LUDVIG_OPT_FAULT_LAUNCH = 3       /* k > 0: the k-th checked kernel launch from now reports
+                                         LUDVIG_ERR_CUDA once (the kernel itself was queued and
+                                         runs normally); 0 disarms.  The failed call's outputs
+                                         are undefined; a later call starts afresh */
 } ludvig_option;
 
 /* Sets an option; LUDVIG_ERR_ARG for an unknown option. */

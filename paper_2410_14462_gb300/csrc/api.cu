@@ -50,6 +50,20 @@ cudaEvent_t take_event() {
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Host-side fault injection: an armed counter k > 0 makes the k-th event from
+// now fail once (then disarms).  Nothing reaches the GPU.
+namespace {
+std::atomic<int64_t> g_fault_alloc{0}, g_fault_launch{0};
+bool fault_tick(std::atomic<int64_t>& c) {
+    int64_t v = c.load();
+    while (v > 0) {
+        if (c.compare_exchange_weak(v, v - 1)) return v == 1;
+    }
+    return false;
+}
+}  // namespace
+bool fault_launch_now() { return g_fault_launch.load(std::memory_order_relaxed) > 0 && fault_tick(g_fault_launch); }
 bool trace_on() { return g_trace.load(std::memory_order_relaxed); }
 
 int trace_begin(int stage, cudaStream_t st) {
@@ -93,6 +107,10 @@ ludvig_status Arena::get(const char* name, size_t bytes, void** out) {
             b.bytes = 0;
         }
         const size_t want = bytes + bytes / 8;   // grow with some headroom
+        if (g_fault_alloc.load(std::memory_order_relaxed) > 0 && fault_tick(g_fault_alloc)) {
+            set_error("workspace '%s': injected allocation failure", name);
+            return LUDVIG_ERR_OOM;
+        }
         cudaError_t e = cudaMalloc(&b.ptr, want);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -209,6 +227,12 @@ extern "C" ludvig_status ludvig_set_option(int32_t option, int64_t value) {
         case LUDVIG_OPT_COUNT_NORMALISE:
             g_opt_count.store(value != 0);
             return LUDVIG_OK;
+        case LUDVIG_OPT_FAULT_ALLOC:
+            g_fault_alloc.store(value > 0 ? value : 0);
+            return LUDVIG_OK;
+        case LUDVIG_OPT_FAULT_LAUNCH:
+            g_fault_launch.store(value > 0 ? value : 0);
+            return LUDVIG_OK;
         default:
             set_error("unknown option %d", option);
             return LUDVIG_ERR_ARG;
@@ -219,6 +243,8 @@ extern "C" int64_t ludvig_get_option(int32_t option) {
     switch (option) {
         case LUDVIG_OPT_F32_TENSOR_CORES: return g_opt_f32_tc.load();
         case LUDVIG_OPT_COUNT_NORMALISE: return g_opt_count.load();
+        case LUDVIG_OPT_FAULT_ALLOC: return g_fault_alloc.load();
+        case LUDVIG_OPT_FAULT_LAUNCH: return g_fault_launch.load();
         default: return -1;
     }
 }

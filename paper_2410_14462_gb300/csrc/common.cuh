@@ -18,6 +18,7 @@ void set_error(const char* fmt, ...);
 
 // ---------------------------------------------------------------- tracing
 void count_launch();
+bool fault_launch_now();   // host-side fault injection (LUDVIG_OPT_FAULT_LAUNCH)
 bool trace_on();
 int trace_begin(int stage, cudaStream_t st);   // returns a slot or -1
 void trace_end(int slot, cudaStream_t st);
@@ -45,6 +46,10 @@ struct StageScope {
 #define LV_LAUNCH()                                                                        \
     do {                                                                                   \
         ::ludvig::count_launch();                                                          \
+        if (::ludvig::fault_launch_now()) {                                                \
+            ::ludvig::set_error("%s:%d kernel launch: injected failure", __FILE__, __LINE__); \
+            return LUDVIG_ERR_CUDA;                                                        \
+        }                                                                                  \
         cudaError_t _e = cudaGetLastError();                                               \
         if (_e != cudaSuccess) {                                                           \
             ::ludvig::set_error("%s:%d kernel launch: %s", __FILE__, __LINE__,              \

@@ -282,6 +282,8 @@ def relevancy(feats: torch.Tensor, phi_queries: torch.Tensor, phi_canon: torch.T
 
 OPT_F32_TENSOR_CORES = 0
 OPT_COUNT_NORMALISE = 1
+OPT_FAULT_ALLOC = 2
+OPT_FAULT_LAUNCH = 3
 
 
 def set_option(option: int, value: int):

@@ -43,3 +43,27 @@ def test_bounded_wait_expires_and_context_survives():
     # a zero budget on a pending phase expires at once; arguments are checked
     assert L.ludvig_debug_wait_timeout(0, None, None) == 4
     assert L.ludvig_debug_wait_timeout(-1, None, None) == 1
+
+
+@pytest.mark.parametrize("opt,k,code", [(ludvig.OPT_FAULT_LAUNCH, 7, "ERR_CUDA"), (ludvig.OPT_FAULT_ALLOC, 1, "ERR_OOM")])
+def test_injected_host_faults_are_reported_and_recovered(opt, k, code):
+    """A failure injected on the host (an allocation, a launch check) comes back
+    as an error status with a message; the next call, with nothing armed,
+    succeeds and matches the oracle."""
+    wl = inputs.small_field_workload(n=4000, views=2, d=8, width=50, height=40)
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    F = device_features(wl, range(2))
+    ludvig.set_option(opt, k)
+    try:
+        with pytest.raises(ludvig.LudvigError, match=code) as ei:
+            ludvig.uplift(sc, wl.cams.params, wl.cams.width, wl.cams.height, F)
+        assert "injected" in str(ei.value)
+        assert ludvig.get_option(opt) == 0   # fired once, disarmed
+    finally:
+        ludvig.set_option(opt, 0)
+    torch.cuda.synchronize()
+    out, beta = ludvig.uplift(sc, wl.cams.params, wl.cams.width, wl.cams.height, F)
+    torch.cuda.synchronize()
+    f_ref, b_ref = oracle.uplift(wl.scene, wl.cams, lambda v: wl.features(v))
+    pos = b_ref > 0
+    assert rel_l2(out.cpu().numpy(), f_ref, pos) <= 1e-5
