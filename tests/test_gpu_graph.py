@@ -98,3 +98,19 @@ def test_diffusion_matches_oracle():
     assert rel_l2(got, ref) <= 1e-5
     assert (got[:, 1] == 0).all()
     assert np.array_equal(g.diffuse(xt, 0).cpu().numpy(), x0)
+
+
+def test_diffusion_resumes_from_an_intermediate_state():
+    """Eq. 8 depends only on g_t, so 2 steps then 5 more equal 7 steps at once
+    (checkpoint / resume of the diffusion), for one and for several columns."""
+    wl = inputs.small_field_workload(n=20_000, views=1, d=16)
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    f = np.random.default_rng(1).normal(size=(sc.n, 16)).astype(np.float32)
+    g = ludvig.Graph(sc, 16, torch.from_numpy(f).cuda(), spatial_h=0.01)
+    for dx in (1, 3):
+        x0 = torch.rand((sc.n, dx) if dx > 1 else (sc.n,), device="cuda",
+                        generator=torch.Generator("cuda").manual_seed(dx))
+        whole = g.diffuse(x0, 7)
+        part = g.diffuse(g.diffuse(x0, 2), 5)
+        torch.cuda.synchronize()
+        assert rel_l2(part.cpu().numpy(), whole.cpu().numpy()) <= 1e-6
