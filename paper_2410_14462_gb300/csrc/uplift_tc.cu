@@ -365,7 +365,7 @@ struct AggSmem {
     static constexpr int kUnitPx = 64 / kHalves;              // pixels per unit
     static constexpr uint32_t kBoxBytes = kUnitPx * 128u;     // one 128-byte-wide box (and one F1 atom)
     static constexpr uint32_t kFStage = 16384u;               // one feature unit
-    static constexpr int kFS = NT == 1 ? 5 : 6;               // 80 KB or 96 KB of stages
+    static constexpr int kFS = NT == 1 ? 5 : 7;               // 80 KB or 112 KB of stages
     static constexpr int kEH = NT == 1 ? 2 : 1;               // epilogue warps per TMEM lane quarter
     static constexpr int kPitch = 68;                         // staged row: 64 floats + 16 B pad
     uint8_t W[kWA][NT][kAtomBytes];                           // offset 0 (1024-aligned)
