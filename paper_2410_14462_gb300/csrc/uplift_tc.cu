@@ -132,7 +132,7 @@ __device__ __forceinline__ void finish_chunk(const WeightsArgs& a, int c, int ro
 }
 
 template <int NT>
-__global__ void __launch_bounds__(256, 4) k_weights(WeightsArgs a) {
+__global__ void __launch_bounds__(256, 5) k_weights(WeightsArgs a) {
     __shared__ WeightsSmem<NT> S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
