@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-filter", action="store_true", help="skip the Gaussian-filtering line")
     ap.add_argument("--no-paper-diffusion", action="store_true", help="skip the paper-form diffusion line")
     ap.add_argument("--no-relevancy", action="store_true", help="skip the relevancy / count-normaliser lines")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-form line")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-form line")
     ap.add_argument("--profile-case", choices=["tc2views", "render2views", "render16views"], default=None,
                     help="run a small fixed case for an ncu capture and exit (no JSON line)")
     return ap.parse_args()
@@ -480,6 +482,144 @@ def count_normalised_line(sc, wl, feats):
             "max_count": float(cnt.max().item()), "gaussians_counted": int((cnt > 0).sum().item())}
 
 
+def batched_form(pools, cams, slots=6):
+    """32 uplift jobs of uneven size (N log-uniform in [50k, 1M] clustered
+    Gaussians, V uniform in [20, 200] views of 640x480, D uniform over
+    {1, 3, 64, 384, 512}) with bfloat16 features from shared device pools,
+    run concurrently on ``slots`` streams; beside it the same jobs one after
+    another on one stream (bfloat16) and in the plain float32 form (the same
+    values widened to float32, views in chunks of 48), each timed with CUDA
+    events.  The bfloat16 error is stated against the float32 path on true
+    float32 features (8 views of the first job with D >= 64)."""
+    import torch
+    from paper_2410_14462_gb300 import inputs, ludvig, serve
+    W, H = cams.width, cams.height
+    specs = inputs.batch_jobs()
+    scenes = [ludvig.Scene.from_inputs(inputs.scene_clusters(s.n, seed=s.seed)) for s in specs]
+    jobs = [serve.Job(j, scenes[j], s.d, s.v0, s.views) for j, s in enumerate(specs)]
+    # largest first: the long jobs start early and the short ones fill the tail
+    jobs.sort(key=lambda j: -(j.scene.n * j.views * max(j.d, 32)))
+    work = sum(j.views * j.d for j in jobs)
+    res = serve.run_batch(jobs, pools, cams.params, W, H, slots=slots)   # warm-up: workspaces grow
+    if res["errors"]:
+        raise RuntimeError(f"batched form: {res['errors']}")
+    ludvig.trace_read(reset=True)
+    reps = 2
+    batched = [serve.run_batch(jobs, pools, cams.params, W, H, slots=slots)["device_ms"] for _ in range(reps)]
+    launches = ludvig.trace_read(reset=True)["kernel_launches"] / reps
+    serial = serve.run_batch(jobs, pools, cams.params, W, H, slots=1)["device_ms"]
+    # plain float32 form, one job after another; each job's scene is made
+    # afresh (the resident scenes' workspaces are freed first) and its float32
+    # pass runs once untimed so that the workspace has grown before timing
+    je = next(j for j in jobs if j.d >= 64)
+    nv = 8
+    fe = torch.stack([inputs.feature_field(5, je.v0 + v, je.d, H, W, device="cuda") for v in range(nv)]).contiguous()
+    o32, b32 = ludvig.uplift(je.scene, cams.params[je.v0:je.v0 + nv], W, H, fe)
+    obf, _ = ludvig.uplift(je.scene, cams.params[je.v0:je.v0 + nv], W, H, pools[je.d][je.v0:je.v0 + nv])
+    torch.cuda.synchronize()
+    pos = b32 > 0
+    err = float((obf[pos] - o32[pos]).norm() / o32[pos].norm())
+    err_case = f"job with N={je.scene.n}, D={je.d}, {nv} views"
+    del fe, o32, b32, obf, pos
+    for sc in scenes:
+        sc.close()
+    torch.cuda.empty_cache()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plain_ms = 0.0
+    for j in jobs:
+        sc = ludvig.Scene.from_inputs(inputs.scene_clusters(specs[j.jid].n, seed=specs[j.jid].seed))
+        num = torch.zeros((sc.n, j.d), dtype=torch.float32, device="cuda")
+        den = torch.zeros((sc.n,), dtype=torch.float32, device="cuda")
+        for rep in range(2):
+            num.zero_()
+            den.zero_()
+            for c0 in range(0, j.views, 48):
+                c1 = min(j.views, c0 + 48)
+                f32 = pools[j.d][j.v0 + c0:j.v0 + c1].float()
+                torch.cuda.synchronize()
+                e0.record()
+                ludvig.uplift_accumulate(sc, cams.params[j.v0 + c0:j.v0 + c1], W, H, f32, num, den)
+                e1.record()
+                torch.cuda.synchronize()
+                plain_ms += e0.elapsed_time(e1) if rep == 1 else 0.0
+                del f32
+            e0.record()
+            ludvig.uplift_finalize(num, den)
+            e1.record()
+            torch.cuda.synchronize()
+            plain_ms += e0.elapsed_time(e1) if rep == 1 else 0.0
+        del num, den
+        sc.close()
+        torch.cuda.empty_cache()
+    ms = float(np.median(batched))
+    out = {"value": work / (ms / 1e3), "unit": UNIT, "dtype": "bf16", "ms_per_batch": ms,
+           "ms_per_batch_runs": batched, "serial_bf16_ms": serial, "plain_f32_serial_ms": plain_ms,
+           "speedup_vs_serial_bf16": serial / ms, "speedup_vs_plain_f32": plain_ms / ms,
+           "plain_f32_value": work / (plain_ms / 1e3), "gpu_launches_per_batch": launches,
+           "rel_l2_bf16_vs_f32": err, "err_case": err_case,
+           "config": {"workload": "32 jobs: N log-uniform [50k, 1M], V U[20, 200] of 640x480, "
+                                  "D U{1, 3, 64, 384, 512}, bf16 pools, seed 3",
+                      "jobs": len(jobs), "views_ch": work, "gaussians": sum(s.n for s in specs),
+                      "slots": slots, "form": "concurrent streams, largest job first"}}
+    return out
+
+
+def serving_form(pools, cams, slots=2, n_requests=300, rate=200.0):
+    """Requests against 4 resident scenes (N = 250k, 500k, 750k, 1M clustered
+    Gaussians, seeds 40-43): Poisson arrivals at ``rate`` req/s; each request
+    uplifts V U[10, 150] views of 640x480 bfloat16 features with D uniform
+    over {1, 64, 384, 512}, and half of them then run U[20, 100] diffusion
+    steps (k = 16 graph from an uplift of 20 views at D = 384) on the uplifted
+    first channel.  Outputs are admitted against a 150 GB budget.  The first
+    run offers more work than the GPU serves (the queue grows), so its
+    throughput is the service capacity; the second replays 100 requests at
+    70% of that capacity."""
+    import torch
+    from paper_2410_14462_gb300 import inputs, ludvig, serve
+    W, H = cams.width, cams.height
+    scenes = [ludvig.Scene.from_inputs(inputs.scene_clusters(n, seed=s)) for n, s in inputs.SERVING_SCENES]
+    graphs = []
+    for sc in scenes:
+        f, _ = ludvig.uplift(sc, cams.params[:20], W, H, pools[384][:20])
+        graphs.append(ludvig.Graph(sc, 16, f, spatial_h=0.01))
+        del f
+    pools = {d: pools[d] for d in (1, 64, 384, 512)}
+    server = serve.Server(scenes, graphs, pools, cams.params, W, H, 150e9, slots=slots)
+    # warm-up: every replica's workspace grows to the largest request
+    warm = [serve.Request(i, 0.0, i % len(scenes), 512, 0, 150, 100) for i in range(len(scenes) * slots)]
+    server.run(warm)
+
+    def served_work(reqs, res):
+        return sum(q.views * q.d for q, r in zip(reqs, res) if r.ok)
+
+    reqs = serve.poisson_requests(n_requests, rate, len(scenes), cams.v, (1, 64, 384, 512), seed=44)
+    ludvig.trace_read(reset=True)
+    res = server.run(reqs)
+    launches = ludvig.trace_read(reset=True)["kernel_launches"]
+    over = serve.latency_summary(res)
+    cap = over["throughput_req_s"] or 1.0
+    span = max(r.done for r in res) - min(r.arrival for r in res)
+    reqs2 = serve.poisson_requests(100, 0.7 * cap, len(scenes), cams.v, (1, 64, 384, 512), seed=45)
+    res2 = server.run(reqs2)
+    under = serve.latency_summary(res2)
+    span2 = max(r.done for r in res2) - min(r.arrival for r in res2)
+    server.close()
+    for g in graphs:
+        g.close()
+    for sc in scenes:
+        sc.close()
+    torch.cuda.synchronize()
+    over.update({"rate_req_s": rate, "views_ch_per_s": served_work(reqs, res) / span, "gpu_launches": launches})
+    under.update({"rate_req_s": 0.7 * cap, "views_ch_per_s": served_work(reqs2, res2) / span2})
+    return {"p50_ms": over["p50_ms"], "p99_ms": over["p99_ms"], "throughput_req_s": over["throughput_req_s"],
+            "unit": "ms (latency = completion - arrival, queueing included)",
+            "offered_200_req_s": over, "at_70pct_capacity": under,
+            "config": {"workload": "4 resident scenes N 250k/500k/750k/1M (seeds 40-43); Poisson arrivals; "
+                                   "V U[10, 150] of 640x480, D U{1, 64, 384, 512} bf16; 50% + U[20, 100] "
+                                   "diffusion steps", "slots_per_scene": slots, "budget_bytes": 150e9,
+                       "requests": [n_requests, 100], "seeds": [44, 45]}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -592,6 +732,18 @@ def run_ours(args):
         feats = None
         torch.cuda.empty_cache()
         line["render_back"] = render_back(sc, wl, out)
+    if rank == 0 and args.workload == "paper" and not (args.no_batched and args.no_serving):
+        feats = None
+        torch.cuda.empty_cache()
+        fcams = inputs.form_cameras(200)
+        dims = (1, 64, 384, 512) if args.no_batched else (1, 3, 64, 384, 512)
+        pools = {d: inputs.form_pool(d, fcams) for d in dims}
+        if not args.no_batched:
+            line["batched_form"] = batched_form(pools, fcams)
+        if not args.no_serving:
+            line["serving"] = serving_form(pools, fcams)
+        pools = None
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:

@@ -100,12 +100,10 @@ template <int M>
 ludvig_status launch_relevancy(const float* f, int64_t n, int d, const float* phi, int nq, int m, float T, float* r,
                                cudaStream_t st) {
     const size_t smem = relevancy_smem<M>(d);
-    static bool configured = false;
-    if (!configured) {
-        LV_CUDA(cudaFuncSetAttribute(k_relevancy<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)relevancy_smem<M>(kRelMaxSmemFloats / M)));
-        configured = true;
-    }
+    // set once per process; a function-local static is initialised by one thread
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(k_relevancy<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)relevancy_smem<M>(kRelMaxSmemFloats / M));
+    LV_CUDA(configured);
     int dev = 0, sms = 0;
     LV_CUDA(cudaGetDevice(&dev));
     LV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -649,12 +649,10 @@ size_t composite_smem() { return sizeof(CompositeSmem); }
 
 template <class TIn, bool kVec>
 ludvig_status launch_composite(const CompositeArgs& args, int64_t nitems, cudaStream_t st) {
-    static bool configured = false;
-    if (!configured) {
-        LV_CUDA(cudaFuncSetAttribute(k_composite<TIn, kVec>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)composite_smem()));
-        configured = true;
-    }
+    // set once per process; a function-local static is initialised by one thread
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(k_composite<TIn, kVec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)composite_smem());
+    LV_CUDA(configured);
     k_composite<TIn, kVec><<<(unsigned)nitems, 256, composite_smem(), st>>>(args);
     LV_LAUNCH();
     return LUDVIG_OK;

@@ -1168,17 +1168,17 @@ __global__ void __launch_bounds__(kRenderThreads, 1)
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    // looked up once per process (a function-local static is initialised by one thread)
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-        else
-            cudaGetLastError();
-    }
+            return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        cudaGetLastError();
+        return static_cast<PFN_cuTensorMapEncodeTiled_v12000>(nullptr);
+    }();
     return fn;
 }
 
@@ -1235,12 +1235,10 @@ ludvig_status make_w_map(CUtensorMap* map, const void* w, int64_t cap) {
 
 template <int DB, int NT>
 ludvig_status launch_agg(const AggArgs& args, const CUtensorMap* maps, int grid, cudaStream_t st) {
-    static bool configured = false;
-    if (!configured) {
-        LV_CUDA(cudaFuncSetAttribute(k_aggregate_tc<DB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)agg_smem_bytes<NT>()));
-        configured = true;
-    }
+    // set once per process; a function-local static is initialised by one thread
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(k_aggregate_tc<DB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)agg_smem_bytes<NT>());
+    LV_CUDA(configured);
     k_aggregate_tc<DB, NT><<<grid, agg_threads<NT>(), agg_smem_bytes<NT>(), st>>>(args, maps[0], maps[1], maps[2]);
     LV_LAUNCH();
     return LUDVIG_OK;
@@ -1442,12 +1440,10 @@ ludvig_status render_tc(const PairRec* pairs, const uint2* ranges, int nv, int w
     r.f = f;
     r.out = out;
     r.status = status;
-    static bool configured = false;
-    if (!configured) {
-        LV_CUDA(cudaFuncSetAttribute(k_render_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)render_smem_bytes()));
-        configured = true;
-    }
+    // set once per process; a function-local static is initialised by one thread
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(k_render_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)render_smem_bytes());
+    LV_CUDA(configured);
     int sms = 0;
     LV_TRY(sm_count(&sms));
     const int tslot = trace_on() ? trace_begin(LUDVIG_STAGE_RENDER_PRODUCT, st) : -1;

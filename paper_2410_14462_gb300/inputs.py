@@ -283,3 +283,60 @@ def small_field_workload(n: int = 20_000, views: int = 4, d: int = 48, width: in
     scene = scene_clusters(n, seed=seed, n_clusters=8, sigma=0.25, extent=1.0)
     cams = cameras_orbit(views, 3.0, width, height, 0.9 * width, hemisphere=True)
     return Workload(f"clusters-{n}-{views}v-{width}x{height}-d{d}", scene, cams, d, seed, "field")
+
+
+# --------------------------------------------------------------------------
+# batched and serving forms: many uplifts of uneven size on shared pools
+# --------------------------------------------------------------------------
+
+FORM_WIDTH, FORM_HEIGHT, FORM_FOCAL = 640, 480, 600.0
+
+
+def form_cameras(views: int = 200) -> Cameras:
+    """Camera set shared by the jobs and requests: a hemisphere of radius 4
+    looking at the origin, 640x480, fx = fy = 600 (about the field of view of
+    the paper-scale cameras)."""
+    return cameras_orbit(views, 4.0, FORM_WIDTH, FORM_HEIGHT, FORM_FOCAL, hemisphere=True)
+
+
+def form_pool(d: int, cams: Cameras, seed: int = 5, device="cuda", dtype=None):
+    """Feature pool [V,H,W,d] (bfloat16 by default) built view by view on the
+    device: d = 1 holds each view's sphere mask (radius 0.4 at the origin),
+    any other d the smooth unit-norm field of ``feature_field``."""
+    import torch
+    dtype = dtype or torch.bfloat16
+    out = torch.empty((cams.v, cams.height, cams.width, d), dtype=dtype, device=device)
+    for v in range(cams.v):
+        if d == 1:
+            out[v] = torch.from_numpy(sphere_masks(cams.subset([v]))[0]).to(device=device, dtype=dtype)
+        else:
+            out[v] = feature_field(seed, v, d, cams.height, cams.width, device=device, dtype=dtype)
+    return out
+
+
+@dataclasses.dataclass
+class JobSpec:
+    n: int          # Gaussians (scene_clusters with the paper-scale layout)
+    seed: int       # scene seed
+    views: int
+    v0: int         # first view of the pool
+    d: int
+
+
+def batch_jobs(count: int = 32, seed: int = 3, pool_views: int = 200, dims=(1, 3, 64, 384, 512),
+               n_range=(50_000, 1_000_000), views_range=(20, 200)) -> list[JobSpec]:
+    """Seeded uneven jobs: N log-uniform in ``n_range``, V uniform in
+    ``views_range`` (a contiguous range of the pool's views), D uniform over
+    ``dims``; job j's scene has seed 100 + j."""
+    rng = _rng(seed, 9)
+    jobs = []
+    for j in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        v = int(rng.integers(views_range[0], views_range[1] + 1))
+        v0 = int(rng.integers(0, pool_views - v + 1))
+        d = int(dims[int(rng.integers(0, len(dims)))])
+        jobs.append(JobSpec(n, 100 + j, v, v0, d))
+    return jobs
+
+
+SERVING_SCENES = ((250_000, 40), (500_000, 41), (750_000, 42), (1_000_000, 43))   # (N, seed)

@@ -1,0 +1,283 @@
+"""Serving and batching of uplift requests on one GPU (the systems forms
+layered on the method: many uplifts of uneven size sharing the device).
+
+A request uplifts a range of views of a shared device-resident feature pool
+onto a resident scene (Sec. 3.2, Eq. 3), optionally followed by graph
+diffusion steps (Sec. 3.3, Eq. 8) on that scene's graph, applied to the
+uplifted first channel (the mask when D = 1).
+
+Scheduling (continuous batching):
+* every resident scene has ``slots`` device replicas (``ludvig_scene_subset``
+  with the identity index: the same Gaussians and covariances, each with its
+  own workspace, since a workspace serves one stream at a time); every
+  replica has a worker thread and a CUDA stream, so requests on any scene
+  overlap on the GPU as slots free up;
+* a request is admitted when its outputs fit the device-memory budget
+  (outputs are per-request buffers; the resident scenes, graphs, pools and
+  workspaces are outside the budget); a request too large for the budget
+  alone is rejected rather than run;
+* a scene's graph has one workspace, so its diffusions run one at a time
+  (a lock held from the launch until the stream has finished them);
+* requests arrive at their own times (``run`` replays an arrival schedule);
+  latency = completion - arrival, including queueing.
+
+The library calls release the GIL (ctypes), so the workers' GPU work and
+host-side waits overlap; each worker synchronises only its own stream.
+"""
+from __future__ import annotations
+
+import dataclasses
+import heapq
+import threading
+import time
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds from the start of the run
+    scene: int              # index of the resident scene
+    d: int                  # feature pool (channel count)
+    v0: int                 # first view of the pool
+    views: int
+    diffuse_iters: int = 0  # 0: uplift only
+    keep_output: bool = False
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    arrival: float
+    start: float
+    done: float
+    ok: bool
+    error: str = ""
+    out: object = None      # [N, D] features (when kept)
+    g: object = None        # diffused vector (when kept)
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def request_bytes(n: int, d: int) -> int:
+    """Device bytes a request's outputs take (features, beta, diffusion vectors)."""
+    return 4 * n * (d + 1) + 3 * 4 * n
+
+
+class Server:
+    """Resident scenes (``ludvig.Scene``), one diffusion graph per scene (or
+    None), feature pools {d: tensor [V, H, W, d] on the device}, the pool's
+    cameras [V, 16] and image size, an output budget in bytes, and the number
+    of slots (concurrent requests) per scene."""
+
+    def __init__(self, scenes, graphs, pools, cams, width, height, budget_bytes, slots: int = 2):
+        import torch
+        self.graphs = graphs
+        self.pools = pools
+        self.cams = cams
+        self.width, self.height = width, height
+        self.budget = int(budget_bytes)
+        self.replicas = []
+        for sc in scenes:
+            reps = [sc]
+            if slots > 1:
+                ident = torch.arange(sc.n, dtype=torch.int32, device="cuda")
+                reps += [sc.subset(ident) for _ in range(slots - 1)]
+                torch.cuda.synchronize()
+            self.replicas.append(reps)
+        self.graph_locks = [threading.Lock() for _ in scenes]
+        self._lock = threading.Condition()
+        self._in_use = 0
+
+    def close(self):
+        """Free the replicas this server made (not the caller's scenes)."""
+        for reps in self.replicas:
+            for r in reps[1:]:
+                r.close()
+        self.replicas = []
+
+    # ---- admission
+    def _admit(self, nbytes: int, deadline: float) -> bool:
+        with self._lock:
+            while self._in_use + nbytes > self.budget:
+                left = deadline - time.perf_counter()
+                if left <= 0:
+                    return False
+                self._lock.wait(timeout=min(left, 0.05))
+            self._in_use += nbytes
+            return True
+
+    def _release(self, nbytes: int):
+        with self._lock:
+            self._in_use -= nbytes
+            self._lock.notify_all()
+
+    # ---- one request on a replica's stream
+    def _execute(self, req: Request, sc, st, t0: float) -> Result:
+        import torch
+        from . import ludvig
+        pool = self.pools[req.d]
+        nbytes = request_bytes(sc.n, req.d)
+        start = time.perf_counter() - t0
+        if nbytes > self.budget:
+            return Result(req.rid, req.arrival, start, start, False, "larger than the memory budget")
+        if not self._admit(nbytes, time.perf_counter() + 60.0):
+            return Result(req.rid, req.arrival, start, time.perf_counter() - t0, False, "admission timed out")
+        try:
+            with torch.cuda.stream(st):
+                out = torch.empty((sc.n, req.d), dtype=torch.float32, device="cuda")
+                beta = torch.empty((sc.n,), dtype=torch.float32, device="cuda")
+                ludvig.uplift(sc, self.cams[req.v0:req.v0 + req.views], self.width, self.height,
+                              pool[req.v0:req.v0 + req.views], out, beta, stream=st)
+                g = None
+                graph = self.graphs[req.scene]
+                if req.diffuse_iters > 0 and graph is not None:
+                    x0 = out.view(-1) if req.d == 1 else out[:, 0].contiguous()
+                    with self.graph_locks[req.scene]:
+                        g = graph.diffuse(x0, req.diffuse_iters, stream=st)
+                        st.synchronize()
+            st.synchronize()
+            done = time.perf_counter() - t0
+            return Result(req.rid, req.arrival, start, done, True,
+                          out=out if req.keep_output else None, g=g if req.keep_output else None)
+        except Exception as e:   # the request fails, the server goes on
+            st.synchronize()
+            return Result(req.rid, req.arrival, start, time.perf_counter() - t0, False, str(e))
+        finally:
+            self._release(nbytes)
+
+    # ---- replay an arrival schedule
+    def run(self, requests: list[Request]) -> list[Result]:
+        """Serve the requests, each released at its arrival time; returns the
+        results in request order."""
+        import torch
+        t0 = time.perf_counter()
+        queues = [[] for _ in self.replicas]
+        cond = threading.Condition()
+        results = {}
+        pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        closed = [False]
+
+        def worker(s, sc):
+            st = torch.cuda.Stream()
+            while True:
+                with cond:
+                    while not queues[s] and not closed[0]:
+                        cond.wait(timeout=0.05)
+                    if not queues[s] and closed[0]:
+                        return
+                    _, _, req = heapq.heappop(queues[s])
+                results[req.rid] = self._execute(req, sc, st, t0)
+
+        threads = [threading.Thread(target=worker, args=(s, sc), daemon=True)
+                   for s, reps in enumerate(self.replicas) for sc in reps]
+        for t in threads:
+            t.start()
+        for req in pending:   # release each request at its arrival time
+            wait = req.arrival - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            with cond:
+                heapq.heappush(queues[req.scene], (req.arrival, req.rid, req))
+                cond.notify_all()
+        with cond:
+            closed[0] = True
+            cond.notify_all()
+        for t in threads:
+            t.join()
+        return [results[r.rid] for r in requests]
+
+
+def poisson_requests(n: int, rate: float, n_scenes: int, pool_views: int, dims, seed: int,
+                     views_range=(10, 150), diffuse_fraction=0.5, iters_range=(20, 100)) -> list[Request]:
+    """Seeded request stream: exponential inter-arrival times of mean 1/rate,
+    scene, channel count, view range and diffusion drawn uniformly."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    reqs = []
+    for i in range(n):
+        v = int(rng.integers(views_range[0], views_range[1] + 1))
+        v0 = int(rng.integers(0, pool_views - v + 1))
+        it = int(rng.integers(iters_range[0], iters_range[1] + 1)) if rng.random() < diffuse_fraction else 0
+        reqs.append(Request(i, float(t[i]), int(rng.integers(0, n_scenes)), int(rng.choice(dims)), v0, v, it))
+    return reqs
+
+
+def latency_summary(results: list[Result]) -> dict:
+    ok = [r for r in results if r.ok]
+    lat = np.array([r.latency for r in ok]) * 1e3
+    span = max(r.done for r in results) - min(r.arrival for r in results) if results else 0.0
+    return {"requests": len(results), "served": len(ok), "rejected": len(results) - len(ok),
+            "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+            "mean_ms": float(lat.mean()) if lat.size else None,
+            "throughput_req_s": len(ok) / span if span > 0 else None}
+
+
+@dataclasses.dataclass
+class Job:
+    """One uplift job of the batched form: a device-resident scene of its own
+    and a view range of a feature pool."""
+    jid: int
+    scene: object           # ludvig.Scene
+    d: int
+    v0: int
+    views: int
+
+
+def run_batch(jobs: list[Job], pools, cams, width, height, slots: int = 6, keep_outputs: bool = False) -> dict:
+    """Run independent uplift jobs of uneven size concurrently: ``slots``
+    worker threads, each with its own CUDA stream, take the jobs in order
+    (largest first balances the tail best; the caller chooses the order).
+    Returns the device time of the whole batch (CUDA events: every worker
+    stream waits for a start event on the caller's stream, which waits for
+    every worker's end event), the wall time, per-job (start, end) wall
+    times, errors, and the outputs when asked."""
+    import torch
+    from . import ludvig
+    order = list(jobs)
+    lock = threading.Lock()
+    times, errors, outs = {}, {}, {}
+    caller = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ends = [torch.cuda.Event() for _ in range(max(1, slots))]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record(caller)
+
+    def worker(k):
+        st = torch.cuda.Stream()
+        st.wait_event(e0)
+        while True:
+            with lock:
+                if not order:
+                    ends[k].record(st)
+                    return
+                job = order.pop(0)
+            ts = time.perf_counter() - t0
+            try:
+                with torch.cuda.stream(st):
+                    out, beta = ludvig.uplift(job.scene, cams[job.v0:job.v0 + job.views], width, height,
+                                              pools[job.d][job.v0:job.v0 + job.views], stream=st)
+                st.synchronize()
+                if keep_outputs:
+                    outs[job.jid] = (out, beta)
+            except Exception as e:
+                errors[job.jid] = str(e)
+            times[job.jid] = (ts, time.perf_counter() - t0)
+
+    threads = [threading.Thread(target=worker, args=(k,), daemon=True) for k in range(max(1, slots))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for ev in ends:
+        caller.wait_event(ev)
+    e1.record(caller)
+    torch.cuda.synchronize()
+    total = time.perf_counter() - t0
+    return {"device_ms": e0.elapsed_time(e1), "seconds": total, "jobs": len(jobs), "errors": errors,
+            "times": times, "outputs": outs}

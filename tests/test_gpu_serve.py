@@ -1,0 +1,101 @@
+"""Serving and batched forms on one GPU, through the C ABI:
+
+* every request of a concurrent mix (requests on two resident scenes arriving
+  together, with and without diffusion, two feature widths, bfloat16 and
+  float32 pools) gives the same result as when it runs alone: uplift within
+  1e-5 relative L2 (only the order of the atomic sums differs), diffused vector
+  within 1e-5;
+* a request whose outputs exceed the memory budget is rejected and the others
+  are served;
+* the batched runner finishes jobs of uneven size and each matches its own
+  uplift run alone."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2410_14462_gb300 import inputs, ludvig, serve
+from tests.gpu_util import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2410_14462_gb300 import build
+    build.build()
+    ludvig.load()
+
+
+@pytest.fixture(scope="module")
+def world():
+    W, H, V = 100, 75, 20
+    cams = inputs.cameras_orbit(V, 3.0, W, H, 0.9 * W, hemisphere=True)
+    host = [inputs.scene_clusters(n, seed=s, n_clusters=8, sigma=0.25, extent=1.0)
+            for n, s in ((20_000, 40), (12_000, 41))]
+    scenes = [ludvig.Scene.from_inputs(h) for h in host]
+    pools = {}
+    for d, dt in ((8, torch.float32), (48, torch.bfloat16)):
+        pools[d] = torch.stack([inputs.feature_field(7, v, d, H, W, device="cuda") for v in range(V)]
+                               ).to(dt).contiguous()
+    graphs = []
+    for sc in scenes:
+        f, _ = ludvig.uplift(sc, cams.params[:4], W, H, pools[48][:4].contiguous())
+        graphs.append(ludvig.Graph(sc, 8, f, spatial_h=0.01))
+    torch.cuda.synchronize()
+    return dict(W=W, H=H, V=V, cams=cams, host=host, scenes=scenes, pools=pools, graphs=graphs)
+
+
+def _server(w, budget=1 << 34, slots=2):
+    return serve.Server(w["scenes"], w["graphs"], w["pools"], w["cams"].params, w["W"], w["H"], budget, slots)
+
+
+def test_results_same_alone_and_in_the_mix(world):
+    rng = np.random.default_rng(0)
+    reqs = []
+    for i in range(12):
+        views = int(rng.integers(2, 9))
+        reqs.append(serve.Request(i, 0.0, i % 2, [8, 48][(i // 2) % 2], int(rng.integers(0, world["V"] - views)),
+                                  views, diffuse_iters=[0, 15][i % 3 == 0], keep_output=True))
+    srv = _server(world, slots=3)
+    mixed = srv.run(reqs)
+    srv.close()
+    assert all(r.ok for r in mixed), [r.error for r in mixed if not r.ok]
+    single = _server(world, slots=1)
+    for req, rm in zip(reqs, mixed):
+        alone = single.run([serve.Request(req.rid, 0.0, req.scene, req.d, req.v0, req.views,
+                                          req.diffuse_iters, True)])[0]
+        assert alone.ok
+        e = rel_l2(rm.out.cpu().numpy(), alone.out.cpu().numpy())
+        assert e <= 1e-5, (req, e)
+        if req.diffuse_iters:
+            assert rel_l2(rm.g.cpu().numpy(), alone.g.cpu().numpy()) <= 1e-5
+    s = serve.latency_summary(mixed)
+    print(f"mix: {s}")
+    assert s["served"] == 12 and s["p99_ms"] >= s["p50_ms"] > 0
+
+
+def test_admission_rejects_requests_over_budget(world):
+    budget = serve.request_bytes(world["scenes"][1].n, 8) + 1   # fits a small request on scene 1 only
+    reqs = [serve.Request(0, 0.0, 0, 48, 0, 4), serve.Request(1, 0.0, 1, 8, 0, 4),
+            serve.Request(2, 0.01, 1, 8, 4, 4)]
+    res = _server(world, budget, slots=1).run(reqs)
+    assert not res[0].ok and "budget" in res[0].error
+    assert res[1].ok and res[2].ok
+
+
+def test_batched_jobs_match_their_own_runs(world):
+    scenes = [world["scenes"][j % 2] if j < 2 else ludvig.Scene.from_inputs(world["host"][j % 2]) for j in range(6)]
+    jobs = [serve.Job(j, scenes[j], [8, 48][j % 2], j, 3 + j) for j in range(6)]
+    res = serve.run_batch(jobs, world["pools"], world["cams"].params, world["W"], world["H"], slots=3,
+                          keep_outputs=True)
+    assert not res["errors"] and len(res["times"]) == 6 and len(res["outputs"]) == 6
+    for j in jobs:
+        a, b = ludvig.uplift(j.scene, world["cams"].params[j.v0:j.v0 + j.views], world["W"], world["H"],
+                             world["pools"][j.d][j.v0:j.v0 + j.views])
+        out, beta = res["outputs"][j.jid]
+        assert rel_l2(out.cpu().numpy(), a.cpu().numpy()) <= 1e-5
+        assert rel_l2(beta.cpu().numpy(), b.cpu().numpy()) <= 1e-5
+    for sc in scenes[2:]:
+        sc.close()

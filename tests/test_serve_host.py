@@ -1,0 +1,84 @@
+"""Host logic of the serving and batched forms (no GPU): the seeded arrival
+stream and job recipe have the stated distributions, admission never lets the
+admitted outputs exceed the budget while several workers contend for it, and
+the latency summary reads the percentiles of completion - arrival."""
+import math
+import threading
+import time
+
+import numpy as np
+
+from paper_2410_14462_gb300 import inputs, serve
+
+
+def test_poisson_requests_distribution():
+    reqs = serve.poisson_requests(20_000, 200.0, 4, 200, (1, 64, 384, 512), seed=44)
+    t = np.array([r.arrival for r in reqs])
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert (gaps > 0).all()
+    assert abs(gaps.mean() - 1 / 200) < 4 * (1 / 200) / math.sqrt(len(gaps))
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.05          # exponential: CV = 1
+    views = np.array([r.views for r in reqs])
+    assert views.min() == 10 and views.max() == 150
+    assert all(0 <= r.v0 and r.v0 + r.views <= 200 for r in reqs)
+    assert {r.d for r in reqs} == {1, 64, 384, 512} and {r.scene for r in reqs} == {0, 1, 2, 3}
+    it = np.array([r.diffuse_iters for r in reqs])
+    assert abs((it > 0).mean() - 0.5) < 0.02
+    assert it[it > 0].min() == 20 and it.max() == 100
+    again = serve.poisson_requests(20_000, 200.0, 4, 200, (1, 64, 384, 512), seed=44)
+    assert [(r.arrival, r.scene, r.d, r.v0, r.views, r.diffuse_iters) for r in reqs] == \
+           [(r.arrival, r.scene, r.d, r.v0, r.views, r.diffuse_iters) for r in again]
+
+
+def test_batch_jobs_recipe():
+    jobs = inputs.batch_jobs(count=4000, seed=7)
+    n = np.array([j.n for j in jobs], float)
+    assert n.min() >= 50_000 and n.max() <= 1_000_000
+    # log-uniform: log N is uniform on [log 50k, log 1M]
+    u = (np.log(n) - math.log(50_000)) / (math.log(1_000_000) - math.log(50_000))
+    assert abs(u.mean() - 0.5) < 0.02 and abs(u.var() - 1 / 12) < 0.01
+    assert all(20 <= j.views <= 200 and 0 <= j.v0 and j.v0 + j.views <= 200 for j in jobs)
+    assert {j.d for j in jobs} == {1, 3, 64, 384, 512}
+    assert len(inputs.batch_jobs()) == 32
+
+
+def test_admission_never_exceeds_budget():
+    srv = serve.Server.__new__(serve.Server)
+    srv.budget = 1000
+    srv._lock = threading.Condition()
+    srv._in_use = 0
+    peak = [0]
+    seen = threading.Lock()
+    rng = np.random.default_rng(0)
+    sizes = [int(s) for s in rng.integers(100, 700, size=60)]
+
+    def client(sz):
+        assert srv._admit(sz, time.perf_counter() + 30.0)
+        with seen:
+            peak[0] = max(peak[0], srv._in_use)
+            assert srv._in_use <= srv.budget
+        time.sleep(0.001)
+        srv._release(sz)
+
+    threads = [threading.Thread(target=client, args=(s,)) for s in sizes]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=60)
+    assert not any(t.is_alive() for t in threads)
+    assert srv._in_use == 0 and 700 <= peak[0] <= 1000
+    # a request that cannot fit before its deadline is refused
+    srv._in_use = 900
+    assert not srv._admit(200, time.perf_counter() + 0.1)
+    assert srv._in_use == 900
+
+
+def test_latency_summary():
+    res = [serve.Result(i, 0.01 * i, 0.01 * i, 0.01 * i + 0.001 * (i + 1), True) for i in range(100)]
+    res.append(serve.Result(100, 1.0, 1.0, 1.0, False, "larger than the memory budget"))
+    s = serve.latency_summary(res)
+    lat = np.arange(1, 101, dtype=float)
+    assert s["served"] == 100 and s["rejected"] == 1
+    assert abs(s["p50_ms"] - np.percentile(lat, 50)) < 1e-9
+    assert abs(s["p99_ms"] - np.percentile(lat, 99)) < 1e-9
+    assert serve.request_bytes(10, 3) == 4 * 10 * 4 + 12 * 10
