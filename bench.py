@@ -486,7 +486,7 @@ def batched_form(pools, cams, slots=6):
     """32 uplift jobs of uneven size (N log-uniform in [50k, 1M] clustered
     Gaussians, V uniform in [20, 200] views of 640x480, D uniform over
     {1, 3, 64, 384, 512}) with bfloat16 features from shared device pools,
-    run concurrently on ``slots`` streams; beside it the same jobs one after
+    run by one ludvig_uplift_batch call on ``slots`` streams; beside it the same jobs one after
     another on one stream (bfloat16) and in the plain float32 form (the same
     values widened to float32, views in chunks of 48), each timed with CUDA
     events.  The bfloat16 error is stated against the float32 path on true
@@ -497,8 +497,6 @@ def batched_form(pools, cams, slots=6):
     specs = inputs.batch_jobs()
     scenes = [ludvig.Scene.from_inputs(inputs.scene_clusters(s.n, seed=s.seed)) for s in specs]
     jobs = [serve.Job(j, scenes[j], s.d, s.v0, s.views) for j, s in enumerate(specs)]
-    # largest first: the long jobs start early and the short ones fill the tail
-    jobs.sort(key=lambda j: -(j.scene.n * j.views * max(j.d, 32)))
     work = sum(j.views * j.d for j in jobs)
     res = serve.run_batch(jobs, pools, cams.params, W, H, slots=slots)   # warm-up: workspaces grow
     if res["errors"]:
@@ -507,7 +505,10 @@ def batched_form(pools, cams, slots=6):
     reps = 2
     batched = [serve.run_batch(jobs, pools, cams.params, W, H, slots=slots)["device_ms"] for _ in range(reps)]
     launches = ludvig.trace_read(reset=True)["kernel_launches"] / reps
+    ludvig.trace_enable(True)    # stage split of the one-stream run (stages do not overlap there)
     serial = serve.run_batch(jobs, pools, cams.params, W, H, slots=1)["device_ms"]
+    ludvig.trace_enable(False)
+    stages = {k: v for k, v in ludvig.trace_read(reset=True)["ms"].items() if v > 0}
     # plain float32 form, one job after another; each job's scene is made
     # afresh (the resident scenes' workspaces are freed first) and its float32
     # pass runs once untimed so that the workspace has grown before timing
@@ -523,6 +524,7 @@ def batched_form(pools, cams, slots=6):
     del fe, o32, b32, obf, pos
     for sc in scenes:
         sc.close()
+    ludvig.batch_release_workspaces()
     torch.cuda.empty_cache()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     plain_ms = 0.0
@@ -556,11 +558,12 @@ def batched_form(pools, cams, slots=6):
            "ms_per_batch_runs": batched, "serial_bf16_ms": serial, "plain_f32_serial_ms": plain_ms,
            "speedup_vs_serial_bf16": serial / ms, "speedup_vs_plain_f32": plain_ms / ms,
            "plain_f32_value": work / (plain_ms / 1e3), "gpu_launches_per_batch": launches,
-           "rel_l2_bf16_vs_f32": err, "err_case": err_case,
+           "rel_l2_bf16_vs_f32": err, "err_case": err_case, "serial_stages_ms": stages,
            "config": {"workload": "32 jobs: N log-uniform [50k, 1M], V U[20, 200] of 640x480, "
                                   "D U{1, 3, 64, 384, 512}, bf16 pools, seed 3",
                       "jobs": len(jobs), "views_ch": work, "gaussians": sum(s.n for s in specs),
-                      "slots": slots, "form": "concurrent streams, largest job first"}}
+                      "slots": slots,
+                      "form": "ludvig_uplift_batch: concurrent streams, native host threads, longest job first"}}
     return out
 
 
@@ -592,7 +595,7 @@ def serving_form(pools, cams, slots=2, n_requests=300, rate=200.0):
     def served_work(reqs, res):
         return sum(q.views * q.d for q, r in zip(reqs, res) if r.ok)
 
-    reqs = serve.poisson_requests(n_requests, rate, len(scenes), cams.v, (1, 64, 384, 512), seed=44)
+    reqs = serve.poisson_requests(n_requests, rate, len(scenes), cams.v, (1, 64, 384, 512), seed=4)
     ludvig.trace_read(reset=True)
     res = server.run(reqs)
     launches = ludvig.trace_read(reset=True)["kernel_launches"]
@@ -617,7 +620,7 @@ def serving_form(pools, cams, slots=2, n_requests=300, rate=200.0):
             "config": {"workload": "4 resident scenes N 250k/500k/750k/1M (seeds 40-43); Poisson arrivals; "
                                    "V U[10, 150] of 640x480, D U{1, 64, 384, 512} bf16; 50% + U[20, 100] "
                                    "diffusion steps", "slots_per_scene": slots, "budget_bytes": 150e9,
-                       "requests": [n_requests, 100], "seeds": [44, 45]}}
+                       "requests": [n_requests, 100], "seeds": [4, 45]}}
 
 
 def run_ours(args):

@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define LUDVIG_ABI_VERSION 6
+#define LUDVIG_ABI_VERSION 7
 
 typedef enum {
     LUDVIG_OK = 0,
@@ -58,12 +58,13 @@ typedef enum {
 } ludvig_status;
 
 typedef enum {
-    LUDVIG_F32 = 0,              /* float32 features.  32 <= d <= 512, d % 8 == 0: tensor-core
-                                    aggregation with features and weights split into two
-                                    bfloat16 terms each (float32-level accuracy); otherwise, or
-                                    with LUDVIG_OPT_F32_TENSOR_CORES = 0, CUDA-core FFMA */
-    LUDVIG_BF16 = 1              /* bfloat16 features.  32 <= d <= 512, d % 8 == 0: tensor-core
-                                    aggregation with bfloat16 weights; otherwise CUDA cores */
+    LUDVIG_F32 = 0,              /* float32 features.  d < 32, or 32 <= d <= 512 with d % 8 == 0:
+                                    tensor-core aggregation with features and weights split into
+                                    two bfloat16 terms each (float32-level accuracy); otherwise,
+                                    or with LUDVIG_OPT_F32_TENSOR_CORES = 0, CUDA-core FFMA */
+    LUDVIG_BF16 = 1              /* bfloat16 features.  d < 32, or 32 <= d <= 512 with d % 8 == 0:
+                                    tensor-core aggregation with bfloat16 weights; otherwise CUDA
+                                    cores with float32 weights */
 } ludvig_dtype;
 
 /* Process-wide options (ludvig_set_option / ludvig_get_option). */
@@ -125,12 +126,18 @@ int64_t ludvig_scene_size(ludvig_scene_t scene);
  *   num[i,:] += sum_{v,p} w_i(v,p) F_v[p,:]      den[i] += sum_{v,p} w_i(v,p)
  * over the n_views cameras `cams` (host [n_views]) of one image size
  * width x height (each <= 65535*16), with features `feats`
- * (device [n_views, height, width, d], channels-last, dtype `dtype`;
- * d % 4 == 0 for LUDVIG_F32 unless d < 4, d % 8 == 0 for LUDVIG_BF16).
+ * (device [n_views, height, width, d], channels-last, dtype `dtype`,
+ * 1 <= d <= 65536; num 16-byte aligned when d % 4 == 0).
  * num (device [n,d] float32) and den (device [n] float32) are ADDED to, so
  * partial sums over disjoint view sets can be merged by addition (view
  * sharding, checkpoint/resume).  Summation order on the GPU is not fixed
- * (atomics), so results are reproducible only to rounding. */
+ * (atomics), so results are reproducible only to rounding.
+ * Where the products run: d < 32, or 32 <= d <= 512 with d % 8 == 0, on the
+ * tensor cores (d < 32 on features the library zero-pads to 32 channels in
+ * its workspace), float32 features as split-bfloat16 terms (float32-level
+ * accuracy; LUDVIG_OPT_F32_TENSOR_CORES = 0 moves them to CUDA cores),
+ * bfloat16 features with the weights rounded to bfloat16 for the product;
+ * any other d on CUDA cores with float32 weights. */
 ludvig_status ludvig_uplift_accumulate(ludvig_scene_t scene, const ludvig_camera* cams,
                                        int32_t n_views, int32_t width, int32_t height,
                                        const void* feats, int32_t dtype, int32_t d,
@@ -158,6 +165,45 @@ ludvig_status ludvig_uplift(ludvig_scene_t scene, const ludvig_camera* cams, int
 ludvig_status ludvig_uplift_host(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
                                  int32_t width, int32_t height, const void* feats, int32_t dtype,
                                  int32_t d, float* out, float* beta, void* stream);
+
+/* One job of ludvig_uplift_batch: the arguments of one ludvig_uplift call
+ * (same meaning, layout and rules). */
+typedef struct {
+    ludvig_scene_t scene;
+    const ludvig_camera* cams;   /* host [n_views] */
+    int32_t n_views, width, height;
+    const void* feats;           /* device [n_views, height, width, d] */
+    int32_t dtype, d;
+    float* out;                  /* device [n, d] float32 */
+    float* beta;                 /* device [n] float32 or NULL */
+} ludvig_uplift_job;
+
+#define LUDVIG_MAX_BATCH_SLOTS 32
+
+/* Batched uplift: n_jobs independent uplifts of uneven size (each exactly
+ * ludvig_uplift with the job's arguments, Eq. 5) run concurrently on `slots`
+ * internal streams (1 <= slots <= LUDVIG_MAX_BATCH_SLOTS), each driven by a
+ * host thread (the calling thread is one), longest estimated job first.
+ * Every job's work is ordered after the work already on `stream`, and
+ * `stream` waits for all of it: to the caller the batch is one call on
+ * `stream`.  A scene may appear in one job only (LUDVIG_ERR_ARG otherwise);
+ * jobs may share feature buffers (read-only) but not outputs.
+ * job_status: host [n_jobs] or NULL, receives each job's status.  Returns
+ * LUDVIG_OK when every job succeeded, else the status of the first failing
+ * job in job order (ludvig_last_error() names it); the other jobs still run.
+ * Results equal those of the jobs run one by one, to float32 rounding
+ * (summation order is not fixed).
+ * Workspace: each slot lends a workspace from a process-wide pool to the jobs
+ * it runs (the scenes' own workspaces are left as they were), so device
+ * scratch grows with `slots`, not with n_jobs; the pool keeps the slot
+ * workspaces for later batches.  The call returns after every job's work has
+ * finished. */
+ludvig_status ludvig_uplift_batch(const ludvig_uplift_job* jobs, int32_t n_jobs, int32_t slots,
+                                  int32_t* job_status, void* stream);
+
+/* Frees the idle pooled workspaces of ludvig_uplift_batch on the current
+ * device (those of batches still running stay). */
+ludvig_status ludvig_batch_release_workspaces(void);
 
 /* Rendering of per-Gaussian features into views (Sec. 3.2, Eq. 4, F_hat = W f,
  * the operator whose transpose the uplift applies):

@@ -77,7 +77,15 @@ struct StageScope {
 // next call that grows it; callers treat workspace as scratch.
 class Arena {
   public:
+    Arena() = default;
+    Arena(const Arena&) = delete;              // buffers have one owner
+    Arena& operator=(const Arena&) = delete;
     ~Arena();
+    // Exchanges the buffers of two workspaces (lending a pooled workspace).
+    void swap(Arena& o) noexcept {
+        dev_.swap(o.dev_);
+        host_.swap(o.host_);
+    }
     // Returns a device buffer of at least `bytes` bytes (256-byte aligned).
     ludvig_status get(const char* name, size_t bytes, void** out);
     template <class T>

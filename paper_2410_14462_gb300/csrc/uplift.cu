@@ -900,6 +900,64 @@ ludvig_status accumulate(ludvig_scene* s, const ludvig_camera* cams, int32_t n_v
     return LUDVIG_OK;
 }
 
+// Few channels (d < 32): the tensor-core path with the features zero-padded
+// to kPadD channels.  The CUDA-core composite spends its time walking each
+// tile's list once per pixel and reducing per Gaussian; the weight-row walk
+// of the tensor-core path does the same walk faster, and the padded
+// contraction costs little next to it.  The padded features of up to
+// kMaxViews views live in the workspace, the padded numerator [n, kPadD]
+// too; its first d columns are added to num at the end (the zero channels
+// contribute nothing, den is the same sum of weights).
+constexpr int kPadD = 32;
+
+template <class T>
+__global__ void k_pad_features(const T* __restrict__ src, int64_t npx, int d, T* __restrict__ dst) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= npx * kPadD) return;
+    const int64_t p = e / kPadD;
+    const int c = (int)(e - p * kPadD);
+    dst[e] = c < d ? src[p * d + c] : T(0.f);
+}
+
+__global__ void k_add_columns(const float* __restrict__ wide, int64_t n, int d, float* __restrict__ num) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * d) return;
+    const int64_t i = e / d;
+    num[e] += wide[i * kPadD + (e - i * d)];
+}
+
+bool use_padded(int dtype, int d) { return d < kPadD && use_tensor_cores(dtype, kPadD); }
+
+ludvig_status accumulate_padded(ludvig_scene* s, const ludvig_camera* cams, int32_t n_views, int32_t width,
+                                int32_t height, const void* feats, int32_t dtype, int32_t d, float* num,
+                                float* den, cudaStream_t st) {
+    const int64_t n = s->n;
+    const int64_t px_view = (int64_t)width * height;
+    const size_t esize = dtype == LUDVIG_F32 ? 4 : 2;
+    const int vc = std::min<int>(kMaxViews, n_views);
+    float* wide;
+    void* fpad;
+    LV_TRY(s->ws.get("pad.num", (size_t)n * kPadD, &wide));
+    LV_TRY(s->ws.get("pad.feats", (size_t)vc * px_view * kPadD * esize, &fpad));
+    LV_CUDA(cudaMemsetAsync(wide, 0, sizeof(float) * (size_t)n * kPadD, st));
+    for (int v0 = 0; v0 < n_views; v0 += vc) {
+        const int nv = std::min(vc, n_views - v0);
+        const int64_t npx = (int64_t)nv * px_view;
+        const char* src = static_cast<const char*>(feats) + (size_t)v0 * px_view * d * esize;
+        if (dtype == LUDVIG_F32)
+            k_pad_features<float><<<grid_for(npx * kPadD, 256), 256, 0, st>>>(
+                reinterpret_cast<const float*>(src), npx, d, static_cast<float*>(fpad));
+        else
+            k_pad_features<__nv_bfloat16><<<grid_for(npx * kPadD, 256), 256, 0, st>>>(
+                reinterpret_cast<const __nv_bfloat16*>(src), npx, d, static_cast<__nv_bfloat16*>(fpad));
+        LV_LAUNCH();
+        LV_TRY(accumulate(s, cams + v0, nv, width, height, fpad, dtype, kPadD, wide, den, st, nullptr));
+    }
+    k_add_columns<<<grid_for(n * d, 256), 256, 0, st>>>(wide, n, d, num);
+    LV_LAUNCH();
+    return LUDVIG_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- scene
@@ -928,6 +986,9 @@ extern "C" ludvig_status ludvig_uplift_accumulate(ludvig_scene_t scene, const lu
     LV_ARG(n_views == 0 || feats != nullptr, "feats is NULL");
     if (d % 4 == 0) LV_ARG(((uintptr_t)num & 15) == 0, "num must be 16-byte aligned when d %% 4 == 0");
     if (scene->n == 0 || n_views == 0) return LUDVIG_OK;
+    if (use_padded(dtype, d))
+        return accumulate_padded(scene, cams, n_views, width, height, feats, dtype, d, num, den,
+                                 static_cast<cudaStream_t>(stream));
     return accumulate(scene, cams, n_views, width, height, feats, dtype, d, num, den,
                       static_cast<cudaStream_t>(stream), nullptr);
 }
@@ -1039,7 +1100,10 @@ extern "C" ludvig_status ludvig_uplift_host(ludvig_scene_t scene, const ludvig_c
         const int b = c & 1, v0 = c * vc, nv = std::min(vc, n_views - v0);
         if (c + 1 < nchunks) LV_TRY(upload(c + 1));   // overlaps the compute of chunk c
         LV_CUDA(cudaStreamWaitEvent(st, scene->ev_ready[b], 0));
-        LV_TRY(accumulate(scene, cams + v0, nv, width, height, fbuf[b], dtype, d, num, den, st, nullptr));
+        if (use_padded(dtype, d))
+            LV_TRY(accumulate_padded(scene, cams + v0, nv, width, height, fbuf[b], dtype, d, num, den, st));
+        else
+            LV_TRY(accumulate(scene, cams + v0, nv, width, height, fbuf[b], dtype, d, num, den, st, nullptr));
         LV_CUDA(cudaEventRecord(scene->ev_free[b], st));
     }
     LV_TRY(ludvig_uplift_finalize(n, d, num, den, num, nullptr, stream));

@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libludvig.so")
 
 F32 = 0
 BF16 = 1
+ERR_ARG = 1
+MAX_BATCH_SLOTS = 32          # LUDVIG_MAX_BATCH_SLOTS
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT", 5: "ERR_INTERNAL",
           6: "ERR_UNSUPPORTED"}
@@ -37,6 +39,8 @@ SIGNATURES = {
     "ludvig_uplift_accumulate": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
     "ludvig_uplift_finalize": (_I32, [_I64, _I32, _P, _P, _P, _P, _P]),
     "ludvig_uplift": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
+    "ludvig_uplift_batch": (_I32, [_P, _I32, _I32, _P, _P]),
+    "ludvig_batch_release_workspaces": (_I32, []),
     "ludvig_uplift_host": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
     "ludvig_render": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _P, _P]),
     "ludvig_beta_select": (_I32, [_P, _P, _I64, _P, _P]),
@@ -197,6 +201,46 @@ def uplift(scene: Scene, cams_params, width, height, feats: torch.Tensor, out=No
                            _dtype_code(feats), d, _dev(out, torch.float32, "out"),
                            _dev(beta, torch.float32, "beta"), _stream(stream)), "ludvig_uplift")
     return out, beta
+
+
+class UpliftJob(ctypes.Structure):
+    """ludvig_uplift_job: the arguments of one ludvig_uplift call."""
+    _fields_ = [("scene", ctypes.c_void_p), ("cams", ctypes.c_void_p), ("n_views", ctypes.c_int32),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("feats", ctypes.c_void_p),
+                ("dtype", ctypes.c_int32), ("d", ctypes.c_int32), ("out", ctypes.c_void_p),
+                ("beta", ctypes.c_void_p)]
+
+
+def uplift_batch(jobs, slots: int = 6, stream=None, raise_on_error: bool = True):
+    """ludvig_uplift_batch over jobs given as (scene, cams_params, width, height,
+    feats[V,H,W,D], out or None, beta or None); outputs left as None are
+    allocated here.  Returns [(out, beta)] in job order and the per-job
+    status codes."""
+    L = load()
+    arr = (UpliftJob * max(1, len(jobs)))()
+    keep, results = [], []
+    for k, (scene, cams_params, width, height, feats, out, beta) in enumerate(jobs):
+        cams, nv = cameras_struct(cams_params)
+        d = int(feats.shape[-1])
+        if out is None:
+            out = torch.empty((scene.n, d), dtype=torch.float32, device=feats.device)
+        if beta is None:
+            beta = torch.empty((scene.n,), dtype=torch.float32, device=feats.device)
+        keep.append(cams)
+        results.append((out, beta))
+        arr[k] = UpliftJob(scene.handle.value, ctypes.addressof(cams), nv, width, height,
+                           _dev(feats, name="feats").value, _dtype_code(feats), d,
+                           _dev(out, torch.float32, "out").value, _dev(beta, torch.float32, "beta").value)
+    status = (ctypes.c_int32 * max(1, len(jobs)))()
+    rc = L.ludvig_uplift_batch(arr, len(jobs), int(slots), status, _stream(stream))
+    if raise_on_error:
+        _check(rc, "ludvig_uplift_batch")
+    return results, [int(status[k]) for k in range(len(jobs))]
+
+
+def batch_release_workspaces():
+    """ludvig_batch_release_workspaces: free the batch executor's idle pooled workspaces."""
+    _check(load().ludvig_batch_release_workspaces(), "ludvig_batch_release_workspaces")
 
 
 def uplift_accumulate(scene: Scene, cams_params, width, height, feats, num, den, stream=None):

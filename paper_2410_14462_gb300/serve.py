@@ -229,55 +229,25 @@ class Job:
 
 
 def run_batch(jobs: list[Job], pools, cams, width, height, slots: int = 6, keep_outputs: bool = False) -> dict:
-    """Run independent uplift jobs of uneven size concurrently: ``slots``
-    worker threads, each with its own CUDA stream, take the jobs in order
-    (largest first balances the tail best; the caller chooses the order).
-    Returns the device time of the whole batch (CUDA events: every worker
-    stream waits for a start event on the caller's stream, which waits for
-    every worker's end event), the wall time, per-job (start, end) wall
-    times, errors, and the outputs when asked."""
+    """Run independent uplift jobs of uneven size through one
+    ``ludvig_uplift_batch`` call (``slots`` concurrent streams, each driven by
+    a native host thread, longest job first).  Returns the device time of
+    the batch (CUDA events on the caller's stream, which the batch joins), the
+    wall time, per-job status codes, and the outputs when asked."""
     import torch
     from . import ludvig
-    order = list(jobs)
-    lock = threading.Lock()
-    times, errors, outs = {}, {}, {}
-    caller = torch.cuda.current_stream()
+    outs = [(torch.empty((j.scene.n, j.d), dtype=torch.float32, device="cuda"),
+             torch.empty((j.scene.n,), dtype=torch.float32, device="cuda")) for j in jobs]
+    args = [(j.scene, cams[j.v0:j.v0 + j.views], width, height, pools[j.d][j.v0:j.v0 + j.views], o, b)
+            for j, (o, b) in zip(jobs, outs)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ends = [torch.cuda.Event() for _ in range(max(1, slots))]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e0.record(caller)
-
-    def worker(k):
-        st = torch.cuda.Stream()
-        st.wait_event(e0)
-        while True:
-            with lock:
-                if not order:
-                    ends[k].record(st)
-                    return
-                job = order.pop(0)
-            ts = time.perf_counter() - t0
-            try:
-                with torch.cuda.stream(st):
-                    out, beta = ludvig.uplift(job.scene, cams[job.v0:job.v0 + job.views], width, height,
-                                              pools[job.d][job.v0:job.v0 + job.views], stream=st)
-                st.synchronize()
-                if keep_outputs:
-                    outs[job.jid] = (out, beta)
-            except Exception as e:
-                errors[job.jid] = str(e)
-            times[job.jid] = (ts, time.perf_counter() - t0)
-
-    threads = [threading.Thread(target=worker, args=(k,), daemon=True) for k in range(max(1, slots))]
-    for t in threads:
-        t.start()
-    for t in threads:
-        t.join()
-    for ev in ends:
-        caller.wait_event(ev)
-    e1.record(caller)
+    e0.record()
+    _, status = ludvig.uplift_batch(args, slots=slots, raise_on_error=False)
+    e1.record()
     torch.cuda.synchronize()
     total = time.perf_counter() - t0
+    errors = {j.jid: st for j, st in zip(jobs, status) if st != 0}
     return {"device_ms": e0.elapsed_time(e1), "seconds": total, "jobs": len(jobs), "errors": errors,
-            "times": times, "outputs": outs}
+            "outputs": {j.jid: o for j, o in zip(jobs, outs)} if keep_outputs else {}}

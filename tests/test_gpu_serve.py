@@ -90,7 +90,7 @@ def test_batched_jobs_match_their_own_runs(world):
     jobs = [serve.Job(j, scenes[j], [8, 48][j % 2], j, 3 + j) for j in range(6)]
     res = serve.run_batch(jobs, world["pools"], world["cams"].params, world["W"], world["H"], slots=3,
                           keep_outputs=True)
-    assert not res["errors"] and len(res["times"]) == 6 and len(res["outputs"]) == 6
+    assert not res["errors"] and len(res["outputs"]) == 6
     for j in jobs:
         a, b = ludvig.uplift(j.scene, world["cams"].params[j.v0:j.v0 + j.views], world["W"], world["H"],
                              world["pools"][j.d][j.v0:j.v0 + j.views])
@@ -99,3 +99,34 @@ def test_batched_jobs_match_their_own_runs(world):
         assert rel_l2(beta.cpu().numpy(), b.cpu().numpy()) <= 1e-5
     for sc in scenes[2:]:
         sc.close()
+    # the slots' pooled workspaces hold device memory until released
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    ludvig.batch_release_workspaces()
+    assert torch.cuda.mem_get_info()[0] > free0
+    ludvig.batch_release_workspaces()   # an empty pool is fine
+
+
+def test_uplift_batch_abi_errors_and_job_status(world):
+    """Argument errors come before any work (a scene in two jobs, slots out of
+    range); a job that fails its own checks reports its status while the
+    other jobs of the batch still run to the right result."""
+    W, H, cams, pools = world["W"], world["H"], world["cams"].params, world["pools"]
+    s0, s1 = world["scenes"]
+    job = lambda sc, d, views: (sc, cams[:views], W, H, pools[d][:views], None, None)
+    with pytest.raises(ludvig.LudvigError, match="share a scene"):
+        ludvig.uplift_batch([job(s0, 8, 2), job(s0, 48, 2)])
+    with pytest.raises(ludvig.LudvigError, match="slots"):
+        ludvig.uplift_batch([job(s0, 8, 2)], slots=0)
+    with pytest.raises(ludvig.LudvigError, match="slots"):
+        ludvig.uplift_batch([job(s0, 8, 2)], slots=ludvig.MAX_BATCH_SLOTS + 1)
+    bad = np.array(cams[:2], copy=True)
+    bad[:, 12] = 0.0                                    # fx = 0: the job's own argument check fails
+    bad_job = (s1, bad, W, H, pools[8][:2], None, None)
+    res, status = ludvig.uplift_batch([job(s0, 48, 3), bad_job], slots=2, raise_on_error=False)
+    assert status[0] == 0 and status[1] == ludvig.ERR_ARG
+    with pytest.raises(ludvig.LudvigError, match="job 1"):
+        ludvig.uplift_batch([job(s0, 48, 3), bad_job], slots=2)
+    a, b = ludvig.uplift(s0, cams[:3], W, H, pools[48][:3])
+    assert rel_l2(res[0][0].cpu().numpy(), a.cpu().numpy()) <= 1e-5
+    assert ludvig.uplift_batch([], slots=3) == ([], [])

@@ -138,14 +138,24 @@ def test_uplift_f32_matches_oracle(name):
 
 def test_uplift_scalar_channels_and_bf16():
     base = inputs.small_field_workload(n=8000, views=3, d=3, width=61, height=45)
-    out, beta, F = _gpu_uplift(base, [0, 1, 2])
     f_ref, b_ref = oracle.uplift(base.scene, base.cams, lambda v: base.features(v))
     pos = b_ref > 0
-    assert rel_l2(out, f_ref, pos) <= 1e-5
+    # float32, d = 3: the tensor-core path on features padded to 32 channels
+    # (default) and the CUDA-core kernel both meet the float32 bar
+    try:
+        for opt in (1, 0):
+            ludvig.set_option(ludvig.OPT_F32_TENSOR_CORES, opt)
+            out, beta, F = _gpu_uplift(base, [0, 1, 2])
+            assert np.array_equal(beta > 0, pos)
+            assert rel_l2(out, f_ref, pos) <= 1e-5
+            assert rel_l2(beta, b_ref) <= 1e-5
+    finally:
+        ludvig.set_option(ludvig.OPT_F32_TENSOR_CORES, 1)
     # bfloat16 features, compared with the oracle run on the same bf16 values:
-    # d < 32 takes the CUDA-core kernel (float32 weights, 1e-5), d >= 32 the
-    # tensor-core kernel (weights rounded to bf16 for the product, 1e-2)
-    for d, gate in ((8, 1e-5), (40, 1e-2)):
+    # a multiple of 8 up to 512 takes the tensor-core kernel (weights rounded
+    # to bf16 for the product, 1e-2; d < 32 on features padded to 32), any
+    # other d the CUDA-core kernel (float32 weights, 1e-5)
+    for d, gate in ((8, 1e-2), (36, 1e-5), (40, 1e-2)):
         wl = inputs.small_field_workload(n=8000, views=3, d=d, width=61, height=45)
         out, beta, F = _gpu_uplift(wl, [0, 1, 2], dtype=torch.bfloat16)
         Fh = F.float().cpu().numpy()
@@ -245,15 +255,20 @@ def test_many_small_rows_overflow_row_table():
     cam[0, 12:16] = [300.0, 300.0, 16.0, 16.0]
     Fs = torch.rand((1, 32, 32, 8), device="cuda")
     sc = ludvig.Scene.from_inputs(sc_in)
-    out, beta = ludvig.uplift(sc, cam, 32, 32, Fs)
     Fh = Fs.cpu().numpy()
     cams = inputs.Cameras(cam, 32, 32)
     f_ref, b_ref = oracle.uplift(sc_in, cams, lambda v: Fh[v])
-    torch.cuda.synchronize()
     pos = b_ref > 0
     assert pos.sum() > 2000
-    assert np.array_equal(beta.cpu().numpy() > 0, pos)
-    assert rel_l2(out.cpu().numpy(), f_ref, pos) <= 1e-5
+    try:   # the CUDA-core kernel (its row table) and the padded tensor-core path
+        for opt in (0, 1):
+            ludvig.set_option(ludvig.OPT_F32_TENSOR_CORES, opt)
+            out, beta = ludvig.uplift(sc, cam, 32, 32, Fs)
+            torch.cuda.synchronize()
+            assert np.array_equal(beta.cpu().numpy() > 0, pos)
+            assert rel_l2(out.cpu().numpy(), f_ref, pos) <= 1e-5
+    finally:
+        ludvig.set_option(ludvig.OPT_F32_TENSOR_CORES, 1)
 
 
 @pytest.mark.parametrize("d", [32, 96, 384])
