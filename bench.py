@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--no-relevancy", action="store_true", help="skip the relevancy / count-normaliser lines")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form line")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-form line")
-    ap.add_argument("--profile-case", choices=["tc2views", "render2views", "render16views"], default=None,
+    ap.add_argument("--profile-case", default=None,
+                    choices=["tc2views", "render2views", "render16views", "batch8"],
                     help="run a small fixed case for an ncu capture and exit (no JSON line)")
     return ap.parse_args()
 
@@ -761,11 +762,22 @@ def profile_case(name):
     tc2views: uplift twice with float32 features and twice with the same field
     in bfloat16.  render2views: render of seeded unit-norm features, three
     times.  render16views: the same render of views 0-15 (one full launch of
-    the render kernels), three times."""
+    the render kernels), three times.  batch8: the first 8 jobs of the
+    32-job batched mix through one ludvig_uplift_batch call (6 slots)."""
     import torch
     from paper_2410_14462_gb300 import build, inputs, ludvig
     build.build()
     ludvig.load()
+    if name == "batch8":
+        from paper_2410_14462_gb300 import serve
+        cams = inputs.form_cameras(200)
+        specs = inputs.batch_jobs()[:8]
+        pools = {d: inputs.form_pool(d, cams) for d in sorted({s.d for s in specs})}
+        scenes = [ludvig.Scene.from_inputs(inputs.scene_clusters(s.n, seed=s.seed)) for s in specs]
+        jobs = [serve.Job(j, scenes[j], s.d, s.v0, s.views) for j, s in enumerate(specs)]
+        res = serve.run_batch(jobs, pools, cams.params, cams.width, cams.height, slots=6)
+        torch.cuda.synchronize()
+        return 1 if res["errors"] else 0
     wl = inputs.paper_scale_workload(views=16 if name == "render16views" else 2, d=384)
     sc = ludvig.Scene.from_inputs(wl.scene)
     W, H = wl.cams.width, wl.cams.height

@@ -910,13 +910,22 @@ ludvig_status accumulate(ludvig_scene* s, const ludvig_camera* cams, int32_t n_v
 // contribute nothing, den is the same sum of weights).
 constexpr int kPadD = 32;
 
+// One thread per 16-byte group of a padded pixel (8 bfloat16 or 4 float
+// channels): one vector store each, loads only for the channels below d.
 template <class T>
 __global__ void k_pad_features(const T* __restrict__ src, int64_t npx, int d, T* __restrict__ dst) {
+    constexpr int kPer = 16 / (int)sizeof(T);
+    constexpr int kGroups = kPadD / kPer;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= npx * kPadD) return;
-    const int64_t p = e / kPadD;
-    const int c = (int)(e - p * kPadD);
-    dst[e] = c < d ? src[p * d + c] : T(0.f);
+    if (e >= npx * kGroups) return;
+    const int64_t p = e / kGroups;
+    const int c0 = (int)(e - p * kGroups) * kPer;
+    T vals[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) vals[k] = c0 + k < d ? src[p * d + c0 + k] : T(0.f);
+    uint4 v;
+    memcpy(&v, vals, sizeof(v));
+    reinterpret_cast<uint4*>(dst)[e] = v;
 }
 
 __global__ void k_add_columns(const float* __restrict__ wide, int64_t n, int d, float* __restrict__ num) {
@@ -944,11 +953,13 @@ ludvig_status accumulate_padded(ludvig_scene* s, const ludvig_camera* cams, int3
         const int nv = std::min(vc, n_views - v0);
         const int64_t npx = (int64_t)nv * px_view;
         const char* src = static_cast<const char*>(feats) + (size_t)v0 * px_view * d * esize;
+        // 16-byte groups per padded pixel: 8 (float) or 4 (bfloat16)
+        const int64_t groups = npx * (kPadD * (int64_t)esize / 16);
         if (dtype == LUDVIG_F32)
-            k_pad_features<float><<<grid_for(npx * kPadD, 256), 256, 0, st>>>(
+            k_pad_features<float><<<grid_for(groups, 256), 256, 0, st>>>(
                 reinterpret_cast<const float*>(src), npx, d, static_cast<float*>(fpad));
         else
-            k_pad_features<__nv_bfloat16><<<grid_for(npx * kPadD, 256), 256, 0, st>>>(
+            k_pad_features<__nv_bfloat16><<<grid_for(groups, 256), 256, 0, st>>>(
                 reinterpret_cast<const __nv_bfloat16*>(src), npx, d, static_cast<__nv_bfloat16*>(fpad));
         LV_LAUNCH();
         LV_TRY(accumulate(s, cams + v0, nv, width, height, fpad, dtype, kPadD, wide, den, st, nullptr));
