@@ -53,3 +53,25 @@ def test_argument_errors_are_synchronous(lib):
     assert lib.ludvig_scene_size(None) == -1
     assert lib.ludvig_graph_nnz(None) == -1
     assert lib.ludvig_scene_destroy(None) == 0
+
+
+def test_batch_argument_errors_are_synchronous(lib):
+    """ludvig_uplift_batch checks its arguments before touching a scene or the
+    GPU: negative counts, NULL jobs, slots out of range, a NULL scene and a
+    scene shared by two jobs (the handles below are never dereferenced)."""
+    Job = ludvig.UpliftJob
+    status = (ctypes.c_int32 * 2)()
+    assert lib.ludvig_uplift_batch(None, 0, 4, None, None) == 0        # nothing to do
+    assert lib.ludvig_uplift_batch(None, -1, 4, None, None) == 1
+    assert lib.ludvig_uplift_batch(None, 2, 4, status, None) == 1
+    jobs = (Job * 2)()
+    jobs[0].scene = jobs[1].scene = 0x1000                             # same (fake) handle
+    for slots in (0, ludvig.MAX_BATCH_SLOTS + 1):
+        assert lib.ludvig_uplift_batch(jobs, 2, slots, status, None) == 1
+        assert b"slots" in lib.ludvig_last_error()
+    assert lib.ludvig_uplift_batch(jobs, 2, 2, status, None) == 1
+    assert b"share a scene" in lib.ludvig_last_error()
+    jobs[1].scene = None
+    assert lib.ludvig_uplift_batch(jobs, 2, 2, status, None) == 1
+    assert b"job 1: scene is NULL" in lib.ludvig_last_error()
+    assert ctypes.sizeof(Job) == 64                                    # matches ludvig_uplift_job
