@@ -1,8 +1,8 @@
 """Serving and batched forms on one GPU, through the C ABI:
 
 * every request of a concurrent mix (requests on two resident scenes arriving
-  together, with and without diffusion, two feature widths, bfloat16 and
-  float32 pools) gives the same result as when it runs alone: uplift within
+  together, with and without diffusion, D = 1 masks and two feature widths,
+  bfloat16 and float32 pools) gives the same result as when it runs alone: uplift within
   1e-5 relative L2 (only the order of the atomic sums differs), diffused vector
   within 1e-5;
 * a request whose outputs exceed the memory budget is rejected and the others
@@ -35,7 +35,7 @@ def world():
     host = [inputs.scene_clusters(n, seed=s, n_clusters=8, sigma=0.25, extent=1.0)
             for n, s in ((20_000, 40), (12_000, 41))]
     scenes = [ludvig.Scene.from_inputs(h) for h in host]
-    pools = {}
+    pools = {1: inputs.form_pool(1, cams, device="cuda", dtype=torch.float32)}   # sphere masks
     for d, dt in ((8, torch.float32), (48, torch.bfloat16)):
         pools[d] = torch.stack([inputs.feature_field(7, v, d, H, W, device="cuda") for v in range(V)]
                                ).to(dt).contiguous()
@@ -56,8 +56,8 @@ def test_results_same_alone_and_in_the_mix(world):
     reqs = []
     for i in range(12):
         views = int(rng.integers(2, 9))
-        reqs.append(serve.Request(i, 0.0, i % 2, [8, 48][(i // 2) % 2], int(rng.integers(0, world["V"] - views)),
-                                  views, diffuse_iters=[0, 15][i % 3 == 0], keep_output=True))
+        reqs.append(serve.Request(i, 0.0, i % 2, [8, 48, 1][(i // 2) % 3], int(rng.integers(0, world["V"] - views)),
+                                  views, diffuse_iters=[0, 15][i % 3 == 0 or i % 4 == 0], keep_output=True))
     srv = _server(world, slots=3)
     mixed = srv.run(reqs)
     srv.close()
