@@ -450,3 +450,68 @@ def diffuse(A, x0, iters):
         scale = np.where(nrm > 0, 1.0 / np.where(nrm > 0, nrm, 1.0), 0.0)
         g = A @ (g * scale[None, :])
     return g[:, 0] if squeeze else g
+
+
+# --------------------------------------------------------------------------
+# FP8-E4M3 storage of features (the precision form's 8-bit variant; the
+# format is the OCP 8-bit floating point one, not the paper's): 1 sign bit,
+# 4 exponent bits with bias 7, 3 mantissa bits, no infinities, code 0x7F
+# (and 0xFF) NaN.  Normal codes hold 2^(E-7) (1 + M/8), E = 1..15; E = 0
+# holds the subnormals M 2^-9.  The largest finite value is 448 (0x7E).
+# --------------------------------------------------------------------------
+
+E4M3_MAX = 448.0
+
+
+def e4m3_encode(x) -> np.ndarray:
+    """Codes (uint8) of the values x rounded to E4M3: round to nearest, ties
+    to the even code, magnitudes above 448 saturated to 448, NaN to 0x7F.
+    Every step is exact in float64 (scaling by powers of two)."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    code = np.zeros(x.shape, dtype=np.int64)
+    fin = np.isfinite(a) & (a > 0)
+    # exponent of the leading bit: a = m 2^k with m in [0.5, 1) -> e = k - 1
+    _, k = np.frexp(np.where(fin, a, 1.0))
+    e = np.maximum(k - 1, -6)                  # below 2^-6 the quantum stays 2^-9
+    q = np.rint(np.where(fin, a, 0.0) / np.ldexp(1.0, e - 3))   # units of the quantum; rint ties to even
+    # normal range: code = (e + 7) * 8 + (q - 8); subnormal (e = -6, q < 8):
+    # code = q; both forms agree at q = 8 and carry q = 16 into the next exponent
+    c = np.where(q < 8, q, (e + 7) * 8 + (q - 8)).astype(np.int64)
+    code = np.where(fin, np.minimum(c, 0x7E), code)
+    code = np.where(np.isinf(a) | (fin & (a > E4M3_MAX)), 0x7E, code)
+    code = np.where(np.isnan(x), 0x7F, code)
+    code = code | np.where(np.signbit(x) & ~np.isnan(x), 0x80, 0)
+    return code.astype(np.uint8)
+
+
+def e4m3_decode(code) -> np.ndarray:
+    """float64 values of E4M3 codes (NaN for 0x7F / 0xFF)."""
+    c = np.asarray(code, dtype=np.int64)
+    E, M = (c >> 3) & 15, c & 7
+    mag = np.where(E == 0, M * 2.0 ** -9, np.ldexp(1.0 + M / 8.0, E - 7))
+    mag = np.where((c & 0x7F) == 0x7F, np.nan, mag)
+    return np.where(c & 0x80, -mag, mag)
+
+
+def fp8_quantize(views) -> tuple[np.ndarray, np.ndarray]:
+    """Per-view absmax scaling then E4M3 rounding, for float32 views [V, ...]:
+    s_v = max|x| / 448 in float32 (1 when the view is all zero), codes of
+    float32(x / s_v).  Returns (codes uint8 [V, ...], s float32 [V])."""
+    xs = np.asarray(views, dtype=np.float32)
+    V = xs.shape[0]
+    s = np.ones(V, dtype=np.float32)
+    q = np.zeros(xs.shape, dtype=np.uint8)
+    for v in range(V):
+        amax = np.float32(np.max(np.abs(xs[v]))) if xs[v].size else np.float32(0)
+        if amax > 0:
+            s[v] = amax / np.float32(E4M3_MAX)
+        q[v] = e4m3_encode(xs[v] / s[v])
+    return q, s
+
+
+def fp8_dequantize(q, s) -> np.ndarray:
+    """x = decode(q) s_v in float64 (the values an FP8 uplift averages)."""
+    q = np.asarray(q)
+    s = np.asarray(s, dtype=np.float64).reshape((-1,) + (1,) * (q.ndim - 1))
+    return e4m3_decode(q) * s
