@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define LUDVIG_ABI_VERSION 7
+#define LUDVIG_ABI_VERSION 8
 
 typedef enum {
     LUDVIG_OK = 0,
@@ -165,6 +165,30 @@ ludvig_status ludvig_uplift(ludvig_scene_t scene, const ludvig_camera* cams, int
 ludvig_status ludvig_uplift_host(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
                                  int32_t width, int32_t height, const void* feats, int32_t dtype,
                                  int32_t d, float* out, float* beta, void* stream);
+
+/* FP8-E4M3 storage of features (the precision form's 8-bit variant; the
+ * OCP 8-bit floating point format: bias 7, 3 mantissa bits, largest finite
+ * value 448, no infinities).  Per view v of n_views views of view_elems
+ * values each (feats device, float32 or bfloat16 by `dtype`):
+ *   s_v = max |x| / 448 over the view (float32; 1 for an all-zero view),
+ *   q   = E4M3 code of x / s_v (IEEE float32 division, round to nearest
+ *         even, saturating at 448).
+ * q: device uint8 [n_views * view_elems], 4-byte aligned; scales: device
+ * float32 [n_views] (also the scratch of the per-view maximum).
+ * n_views <= 65535. */
+ludvig_status ludvig_fp8_quantize(const void* feats, int32_t dtype, int32_t n_views, int64_t view_elems,
+                                  uint8_t* q, float* scales, void* stream);
+
+/* Uplift (Eq. 5) of FP8-E4M3 features: the features are decode(q) * s_v
+ * (q: device [n_views, height, width, d] codes, 4-byte aligned; scales:
+ * device [n_views] float32, as ludvig_fp8_quantize writes them).  Each
+ * group of up to 16 views is decoded to bfloat16 in the scene's workspace
+ * (the E4M3 value times s_v, rounded to bfloat16) and uplifted by the
+ * bfloat16 path, so results carry the bfloat16 bar on the decoded values.
+ * out, beta as for ludvig_uplift. */
+ludvig_status ludvig_uplift_fp8(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
+                                int32_t width, int32_t height, const uint8_t* q, const float* scales,
+                                int32_t d, float* out, float* beta, void* stream);
 
 /* One job of ludvig_uplift_batch: the arguments of one ludvig_uplift call
  * (same meaning, layout and rules). */

@@ -29,6 +29,7 @@
 // contributors, written to the view's feature map.
 #include <algorithm>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "common.cuh"
 #include "spec.cuh"
@@ -969,6 +970,34 @@ ludvig_status accumulate_padded(ludvig_scene* s, const ludvig_camera* cams, int3
     return LUDVIG_OK;
 }
 
+// FP8-E4M3 features (codes q, per-view scales s): x = decode(q) s_v rounded
+// to bfloat16 for the tensor-core path (the E4M3 value is exact in half
+// precision; the bfloat16 rounding adds at most 2^-9 relative to an FP8
+// quantisation error of up to 2^-4).  Thread t converts elements 4t .. 4t+3
+// of the group (one 4-byte load, one 8-byte store); the scalar tail covers a
+// total that is not a multiple of 4.
+__device__ __forceinline__ __nv_bfloat16 dequant_e4m3(uint32_t code, float s) {
+    const __half h(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)code, __NV_E4M3));
+    return __float2bfloat16_rn(__half2float(h) * s);
+}
+
+__global__ void k_dequant_e4m3(const uint8_t* __restrict__ q, const float* __restrict__ s, int64_t view_elems,
+                               int64_t total, __nv_bfloat16* __restrict__ out) {
+    const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (e0 >= total) return;
+    if (e0 + 4 <= total) {
+        const uint32_t w = *reinterpret_cast<const uint32_t*>(q + e0);
+        __nv_bfloat16 o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[k] = dequant_e4m3((w >> (8 * k)) & 0xffu, s[(e0 + k) / view_elems]);
+        uint2 v;
+        memcpy(&v, o, sizeof(v));
+        *reinterpret_cast<uint2*>(out + e0) = v;
+    } else {
+        for (int64_t e = e0; e < total; ++e) out[e] = dequant_e4m3(q[e], s[e / view_elems]);
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- scene
@@ -1038,6 +1067,42 @@ extern "C" ludvig_status ludvig_uplift(ludvig_scene_t scene, const ludvig_camera
     LV_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)n * d, st));
     LV_CUDA(cudaMemsetAsync(den, 0, sizeof(float) * (size_t)n, st));
     LV_TRY(ludvig_uplift_accumulate(scene, cams, n_views, width, height, feats, dtype, d, out, den, stream));
+    return ludvig_uplift_finalize(n, d, out, den, out, nullptr, stream);
+}
+
+extern "C" ludvig_status ludvig_uplift_fp8(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
+                                           int32_t width, int32_t height, const uint8_t* q, const float* scales,
+                                           int32_t d, float* out, float* beta, void* stream) {
+    LV_ARG(scene != nullptr, "scene is NULL");
+    LV_ARG(out != nullptr || scene->n == 0, "out is NULL");
+    LV_ARG(d >= 1 && d <= 65536, "d must be in [1, 65536]");
+    LV_TRY(check_views(cams, n_views, width, height));
+    LV_ARG(n_views == 0 || (q != nullptr && scales != nullptr), "q/scales is NULL");
+    LV_ARG(((uintptr_t)q & 3) == 0, "q must be 4-byte aligned");
+    if (d % 4 == 0) LV_ARG(((uintptr_t)out & 15) == 0, "out must be 16-byte aligned when d %% 4 == 0");
+    const int64_t n = scene->n;
+    if (n == 0) return LUDVIG_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float* den = beta;
+    if (!den) LV_TRY(scene->ws.get("uplift.den", (size_t)n, &den));
+    LV_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)n * d, st));
+    LV_CUDA(cudaMemsetAsync(den, 0, sizeof(float) * (size_t)n, st));
+    const int64_t view_elems = (int64_t)width * height * d;
+    const int vc = std::min<int>(kMaxViews, std::max(1, n_views));
+    __nv_bfloat16* fb;
+    LV_TRY(scene->ws.get("fp8.bf16", (size_t)vc * view_elems, &fb));
+    for (int v0 = 0; v0 < n_views; v0 += vc) {
+        const int nv = std::min(vc, n_views - v0);
+        const int64_t total = (int64_t)nv * view_elems;
+        // groups start a multiple of 16 views in: the codes stay 4-byte aligned
+        k_dequant_e4m3<<<grid_for(ceil_div(total, 4), 256), 256, 0, st>>>(q + (size_t)v0 * view_elems, scales + v0,
+                                                                         view_elems, total, fb);
+        LV_LAUNCH();
+        if (use_padded(LUDVIG_BF16, d))
+            LV_TRY(accumulate_padded(scene, cams + v0, nv, width, height, fb, LUDVIG_BF16, d, out, den, st));
+        else
+            LV_TRY(accumulate(scene, cams + v0, nv, width, height, fb, LUDVIG_BF16, d, out, den, st, nullptr));
+    }
     return ludvig_uplift_finalize(n, d, out, den, out, nullptr, stream);
 }
 

@@ -41,6 +41,8 @@ SIGNATURES = {
     "ludvig_uplift": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
     "ludvig_uplift_batch": (_I32, [_P, _I32, _I32, _P, _P]),
     "ludvig_batch_release_workspaces": (_I32, []),
+    "ludvig_fp8_quantize": (_I32, [_P, _I32, _I32, _I64, _P, _P, _P]),
+    "ludvig_uplift_fp8": (_I32, [_P, _P, _I32, _I32, _I32, _P, _P, _I32, _P, _P, _P]),
     "ludvig_uplift_host": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
     "ludvig_render": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _P, _P]),
     "ludvig_beta_select": (_I32, [_P, _P, _I64, _P, _P]),
@@ -236,6 +238,38 @@ def uplift_batch(jobs, slots: int = 6, stream=None, raise_on_error: bool = True)
     if raise_on_error:
         _check(rc, "ludvig_uplift_batch")
     return results, [int(status[k]) for k in range(len(jobs))]
+
+
+def fp8_quantize(feats: torch.Tensor, q=None, scales=None, stream=None):
+    """ludvig_fp8_quantize: per-view absmax scale and E4M3 codes of feats
+    [V, ...] (float32 or bfloat16 CUDA tensor).  Returns (q uint8 of the same
+    shape, scales [V] float32)."""
+    V = int(feats.shape[0])
+    ve = int(feats[0].numel()) if V else 0
+    if q is None:
+        q = torch.empty(feats.shape, dtype=torch.uint8, device=feats.device)
+    if scales is None:
+        scales = torch.empty((V,), dtype=torch.float32, device=feats.device)
+    _check(load().ludvig_fp8_quantize(_dev(feats, name="feats"), _dtype_code(feats), V, ve,
+                                      _dev(q, torch.uint8, "q"), _dev(scales, torch.float32, "scales"),
+                                      _stream(stream)), "ludvig_fp8_quantize")
+    return q, scales
+
+
+def uplift_fp8(scene: Scene, cams_params, width, height, q: torch.Tensor, scales: torch.Tensor, out=None,
+               beta=None, stream=None):
+    """ludvig_uplift_fp8: uplift of E4M3 features q [V,H,W,D] (uint8) with
+    per-view scales [V]."""
+    cams, nv = cameras_struct(cams_params)
+    d = int(q.shape[-1])
+    if out is None:
+        out = torch.empty((scene.n, d), dtype=torch.float32, device=q.device)
+    if beta is None:
+        beta = torch.empty((scene.n,), dtype=torch.float32, device=q.device)
+    _check(load().ludvig_uplift_fp8(scene.handle, cams, nv, width, height, _dev(q, torch.uint8, "q"),
+                                    _dev(scales, torch.float32, "scales"), d, _dev(out, torch.float32, "out"),
+                                    _dev(beta, torch.float32, "beta"), _stream(stream)), "ludvig_uplift_fp8")
+    return out, beta
 
 
 def batch_release_workspaces():
