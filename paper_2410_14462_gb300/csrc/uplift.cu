@@ -14,7 +14,11 @@
 //   5. ranges      [start, end) of every (view, tile) list, and the lists
 //                  rewritten as 32-byte records (projected Gaussian, index,
 //                  8x4 block mask) that the compositing kernels stream
-//   6. composite + aggregate, one CTA (256 threads = 16x16 pixels) per
+//   6. composite + aggregate: on the tensor cores (uplift_tc.cu: weight rows
+//                  of every tile, then W^T F by tcgen05) for d < 32 (features
+//                  zero-padded to 32 channels) and for 32 <= d <= 512 with
+//                  d % 8 == 0; otherwise here on CUDA cores, one CTA (256
+//                  threads = 16x16 pixels) per
 //                  (view, tile): walk the list in batches of 32 Gaussians,
 //                  form w = alpha T per pixel, keep the non-zero weights of
 //                  the tile in a shared-memory sparse store grouped by
