@@ -16,8 +16,12 @@
  *  - Outputs are written only when the call returns LUDVIG_OK.
  *  - A scene (and a graph) may be used by one stream at a time: calls on the
  *    same scene from different streams must be ordered by the caller.
+ *    Calls on different scenes and graphs may come from several host
+ *    threads at once (the last-error message is per thread).
  *  - The library keeps a per-scene device workspace that grows on demand
  *    (cudaMalloc) and is reused; the first call at a new size allocates.
+ *    ludvig_uplift_batch lends pooled per-slot workspaces to its jobs
+ *    instead, so resident scenes need not each hold one.
  *
  * Geometry conventions (the paper fixes none; these are the 3D Gaussian
  * Splatting rasteriser's, which the paper uses, Sec. 5):
