@@ -11,8 +11,11 @@ the CUDA library: the two meet only through the seeded input generators.
   Gaussian centres (Sec. 3.3).
 * this module (numpy / scipy): the similarity graph (Eq. 7 and the edge
   weight of the diffusion workload), row normalisation, and the power
-  iteration g_{t+1} = A g_t / ||g_t||_2 (Eq. 8), and the selection of the
-  most important Gaussians by beta (Sec. 3.2, Gaussian filtering).
+  iteration g_{t+1} = A g_t / ||g_t||_2 (Eq. 8), the selection of the
+  most important Gaussians by beta (Sec. 3.2, Gaussian filtering), the
+  paper-form diffusion pieces (appendix), relevancy scores, and the FP8-E4M3
+  storage of features (OCP 8-bit format: encode, decode, per-view absmax
+  quantiser).
 
 Parity pins live in ``tests/test_oracle_*.py``.  "Parity unpinned": absolute
 agreement with the paper's own rasteriser (no code or printed values exist)
