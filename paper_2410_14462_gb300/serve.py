@@ -91,6 +91,7 @@ class Server:
         self.graph_locks = [threading.Lock() for _ in scenes]
         self._lock = threading.Condition()
         self._in_use = 0
+        self._new_stream = torch.cuda.Stream   # one per worker thread
 
     def close(self):
         """Free the replicas this server made (not the caller's scenes)."""
@@ -153,7 +154,6 @@ class Server:
     def run(self, requests: list[Request]) -> list[Result]:
         """Serve the requests, each released at its arrival time; returns the
         results in request order."""
-        import torch
         t0 = time.perf_counter()
         queues = [[] for _ in self.replicas]
         cond = threading.Condition()
@@ -162,7 +162,7 @@ class Server:
         closed = [False]
 
         def worker(s, sc):
-            st = torch.cuda.Stream()
+            st = self._new_stream()
             while True:
                 with cond:
                     while not queues[s] and not closed[0]:
