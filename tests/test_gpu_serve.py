@@ -76,6 +76,28 @@ def test_results_same_alone_and_in_the_mix(world):
     assert s["served"] == 12 and s["p99_ms"] >= s["p50_ms"] > 0
 
 
+def test_poisoned_request_leaves_the_others_intact(world):
+    """A request whose features are all NaN (its own pool) shares the GPU with
+    two clean requests on the same scene: its output is not finite, theirs
+    equal their runs alone (outputs are per-request buffers, and no kernel's
+    control flow depends on feature values)."""
+    V, H, W = world["V"], world["H"], world["W"]
+    pools = dict(world["pools"])
+    pools[16] = torch.full((V, H, W, 16), float("nan"), dtype=torch.float32, device="cuda")
+    srv = serve.Server(world["scenes"], world["graphs"], pools, world["cams"].params, W, H, 1 << 34, 3)
+    reqs = [serve.Request(0, 0.0, 0, 8, 0, 5, keep_output=True), serve.Request(1, 0.0, 0, 16, 2, 5, keep_output=True),
+            serve.Request(2, 0.0, 0, 48, 4, 5, keep_output=True)]
+    res = srv.run(reqs)
+    srv.close()
+    assert res[0].ok and res[2].ok
+    assert (not res[1].ok) or not bool(torch.isfinite(res[1].out).all())
+    single = _server(world, slots=1)
+    for k in (0, 2):
+        q = reqs[k]
+        alone = single.run([serve.Request(q.rid, 0.0, q.scene, q.d, q.v0, q.views, 0, True)])[0]
+        assert rel_l2(res[k].out.cpu().numpy(), alone.out.cpu().numpy()) <= 1e-5
+
+
 def test_admission_rejects_requests_over_budget(world):
     budget = serve.request_bytes(world["scenes"][1].n, 8) + 1   # fits a small request on scene 1 only
     reqs = [serve.Request(0, 0.0, 0, 48, 0, 4), serve.Request(1, 0.0, 1, 8, 0, 4),
