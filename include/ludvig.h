@@ -13,13 +13,23 @@
  *    reported synchronously before anything is enqueued.  A call returns
  *    LUDVIG_ERR_CUDA if a CUDA runtime call fails; the message is then in
  *    ludvig_last_error().
+ *  - The uplift entry points (ludvig_uplift, ludvig_uplift_accumulate,
+ *    ludvig_uplift_fp8) do not wait on the host: workspace capacities are
+ *    checked on the device and kernel-side failures (an expired bounded
+ *    wait) go to the scene's device status word.  ludvig_sync(scene) waits
+ *    for the scene's last such call, completes it and returns that status;
+ *    the results are final once it returns LUDVIG_OK.  The next call on the
+ *    same scene does the same first (so calls on one scene never overlap),
+ *    but only ludvig_sync reports the status.  Inputs and outputs of a call
+ *    must stay allocated until then.
  *  - Outputs are written only when the call returns LUDVIG_OK.
  *  - A scene (and a graph) may be used by one stream at a time: calls on the
  *    same scene from different streams must be ordered by the caller.
  *    Calls on different scenes and graphs may come from several host
  *    threads at once (the last-error message is per thread).
  *  - The library keeps a per-scene device workspace that grows on demand
- *    (cudaMalloc) and is reused; the first call at a new size allocates.
+ *    (cudaMalloc) and is reused; the first call at a new size allocates (and
+ *    synchronises the device, so a growing call waits on the host).
  *    ludvig_uplift_batch lends pooled per-slot workspaces to its jobs
  *    instead, so resident scenes need not each hold one.
  *
@@ -29,8 +39,9 @@
  *    z forward) and to pixel coordinates (fx x/z + cx, fy y/z + cy); pixel
  *    (u,v) is sampled at its centre (u+0.5, v+0.5).
  *  - Gaussian i: mean mu_i, covariance Sigma_i = R(q_i) diag(s_i)^2 R(q_i)^T
- *    with q_i = (w,x,y,z) normalised inside the library, s_i the LINEAR
- *    per-axis standard deviations, opacity o_i in (0,1) (post-sigmoid).
+ *    with q_i = (w,x,y,z) normalised inside the library, s_i the per-axis
+ *    standard deviations (given as logarithms, as a trained scene stores
+ *    them, or linear: ludvig_scene_opts), opacity o_i in (0,1) (post-sigmoid).
  *  - 2D footprint: EWA covariance J R Sigma R^T J^T + 0.3 I (Jacobian taken at
  *    the mean with x/z, y/z clamped to 1.3 x the half field of view), near
  *    plane z > 0.2, radius ceil(3 sqrt(lambda_max)), 16x16 pixel tiles.
@@ -49,7 +60,7 @@
 extern "C" {
 #endif
 
-#define LUDVIG_ABI_VERSION 8
+#define LUDVIG_ABI_VERSION 9
 
 typedef enum {
     LUDVIG_OK = 0,
@@ -110,15 +121,33 @@ int32_t ludvig_abi_version(void);
 /* Thread-local message describing the last failed call on this thread. */
 const char* ludvig_last_error(void);
 
+/* Options of ludvig_scene_create (NULL: all zero). */
+typedef struct {
+    int32_t scales_are_linear;   /* 0: scales are log standard deviations (exponentiated with
+                                    float32 expf); 1: linear standard deviations (> 0), e.g.
+                                    exponentiated by the caller in float64 for bit-reproducible
+                                    projections */
+} ludvig_scene_opts;
+
 /* Creates a scene from n Gaussians (Sec. 3.1: mean, covariance from scale and
  * rotation, opacity).  All inputs are device arrays and are COPIED:
- *   means [n,3], scales [n,3] (linear standard deviations, > 0),
+ *   means [n,3], scales [n,3] (log or linear standard deviations, see opts),
  *   quats [n,4] (w,x,y,z; any non-zero norm), opacity [n] (in (0,1)).
- * n may be 0.  The per-Gaussian 3D covariance is precomputed on `stream`.
- * *out receives the handle; destroy it with ludvig_scene_destroy. */
+ * n may be 0; opts may be NULL.  The per-Gaussian 3D covariance is
+ * precomputed on `stream`.  *out receives the handle; destroy it with
+ * ludvig_scene_destroy. */
 ludvig_status ludvig_scene_create(const float* means, const float* scales, const float* quats,
-                                  const float* opacity, int64_t n, void* stream,
-                                  ludvig_scene_t* out);
+                                  const float* opacity, int64_t n, const ludvig_scene_opts* opts,
+                                  void* stream, ludvig_scene_t* out);
+
+/* Waits for the scene's last asynchronous uplift call (if any), completes it
+ * and returns its device status word (cleared afterwards): LUDVIG_OK, or
+ * LUDVIG_ERR_TIMEOUT if a bounded wait of a kernel expired.  Groups of views
+ * whose (tile, Gaussian) pairs or weight rows did not fit the scene's
+ * workspace added nothing on the device; they are redone here, synchronously,
+ * after the workspace has grown to fit them (later calls then fit).  Blocks
+ * the calling thread. */
+ludvig_status ludvig_sync(ludvig_scene_t scene);
 
 /* Frees the scene and its workspace (synchronises the device). */
 ludvig_status ludvig_scene_destroy(ludvig_scene_t scene);
@@ -141,7 +170,11 @@ int64_t ludvig_scene_size(ludvig_scene_t scene);
  * its workspace), float32 features as split-bfloat16 terms (float32-level
  * accuracy; LUDVIG_OPT_F32_TENSOR_CORES = 0 moves them to CUDA cores),
  * bfloat16 features with the weights rounded to bfloat16 for the product;
- * any other d on CUDA cores with float32 weights. */
+ * any other d on CUDA cores with float32 weights.
+ * Asynchronous: num/den are complete once ludvig_sync(scene) has returned
+ * LUDVIG_OK (the views run in groups of up to 16; a group's projection, sorts
+ * and weights overlap the previous group's products on two internal streams
+ * that are joined back into `stream`). */
 ludvig_status ludvig_uplift_accumulate(ludvig_scene_t scene, const ludvig_camera* cams,
                                        int32_t n_views, int32_t width, int32_t height,
                                        const void* feats, int32_t dtype, int32_t d,
@@ -156,7 +189,9 @@ ludvig_status ludvig_uplift_finalize(int64_t n, int32_t d, const float* num, con
 /* Full uplift f = D^-1 W^T F (Eq. 5): zeroes out (used as the numerator),
  * accumulates every view and normalises in place.  out: device [n,d] float32;
  * beta: device [n] float32 (beta_i = sum of weights, the importance score of
- * Sec. 3.2 "Gaussian filtering") or NULL. */
+ * Sec. 3.2 "Gaussian filtering") or NULL.  Asynchronous like
+ * ludvig_uplift_accumulate: out/beta are final once ludvig_sync(scene) has
+ * returned LUDVIG_OK. */
 ludvig_status ludvig_uplift(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
                             int32_t width, int32_t height, const void* feats, int32_t dtype,
                             int32_t d, float* out, float* beta, void* stream);
@@ -165,7 +200,8 @@ ludvig_status ludvig_uplift(ludvig_scene_t scene, const ludvig_camera* cams, int
  * (pinned memory gives full copy bandwidth), out host [n,d] and beta host [n]
  * or NULL.  Views are streamed to the device in chunks through a double
  * buffer that overlaps copies with compute; the call returns after the
- * results are back in host memory. */
+ * results are back in host memory (it synchronises `stream`, and reports a
+ * kernel-side status itself). */
 ludvig_status ludvig_uplift_host(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
                                  int32_t width, int32_t height, const void* feats, int32_t dtype,
                                  int32_t d, float* out, float* beta, void* stream);
@@ -368,6 +404,15 @@ ludvig_status ludvig_debug_mma_bf16(const void* a, const void* f, int32_t d, flo
  * waited.  Synchronises `stream`. */
 ludvig_status ludvig_debug_wait_timeout(int64_t cycles, int64_t* waited, void* stream);
 
+/* Failure-detection check of the asynchronous status path (the paper has no
+ * counterpart): enqueues on `stream` one kernel that waits on an mbarrier that
+ * nothing arrives on, with the expiry logic of the tensor-core kernels and a
+ * budget of `cycles` SM clock cycles (0 .. 4e9).  On expiry it records
+ * LUDVIG_ERR_TIMEOUT in the scene's device status word, as a kernel of an
+ * asynchronous uplift would, and returns; nothing traps.  The call itself
+ * returns without waiting; ludvig_sync(scene) then reports the status. */
+ludvig_status ludvig_debug_scene_timeout(ludvig_scene_t scene, int64_t cycles, void* stream);
+
 /* ---- graph diffusion (Sec. 3.3) ----------------------------------------- */
 
 /* Exact k nearest neighbours of every Gaussian centre (Euclidean; the point
@@ -468,9 +513,9 @@ ludvig_status ludvig_reach_weight(ludvig_graph_t graph, const float* g0, int32_t
 /* Graph diffusion that allocates no memory (the paper has no counterpart: this
  * is a service entry point).  It computes what ludvig_diffuse
  * computes, for callers that must not allocate device memory: a request loop
- * that runs under a strict no-allocation policy once it is warm, a process
- * whose device memory is already handed out to another allocator, or code
- * that records its work into a CUDA graph.  Its scratch (the ping-pong vector
+ * that runs under a strict no-allocation policy once it is warm, or a process
+ * whose device memory is already handed out to another allocator.  Its
+ * scratch (the ping-pong vector
  * and the per-step norms) lives in statically allocated device memory of the
  * library: at most 1,048,576 elements (n * dx) and at most 1024 steps; larger
  * requests fail with LUDVIG_ERR_ARG before anything is enqueued.  Every GPU

@@ -148,7 +148,8 @@ ludvig_status Arena::pinned(const char* name, size_t bytes, void** out) {
 }
 
 ludvig_status scene_init(ludvig_scene* s, const float* means, const float* scales, const float* quats,
-                         const float* opac, cudaStream_t st);
+                         const float* opac, int scales_are_linear, cudaStream_t st);
+void scene_release_async(ludvig_scene* s);
 
 }  // namespace ludvig
 
@@ -159,8 +160,8 @@ extern "C" int32_t ludvig_abi_version(void) { return LUDVIG_ABI_VERSION; }
 extern "C" const char* ludvig_last_error(void) { return g_last_error; }
 
 extern "C" ludvig_status ludvig_scene_create(const float* means, const float* scales, const float* quats,
-                                             const float* opacity, int64_t n, void* stream,
-                                             ludvig_scene_t* out) {
+                                             const float* opacity, int64_t n, const ludvig_scene_opts* opts,
+                                             void* stream, ludvig_scene_t* out) {
     LV_ARG(out != nullptr, "out is NULL");
     *out = nullptr;
     LV_ARG(n >= 0 && n < ((int64_t)1 << 31), "n must be in [0, 2^31)");
@@ -181,7 +182,8 @@ extern "C" ludvig_status ludvig_scene_create(const float* means, const float* sc
             set_error("scene allocation failed for n=%lld", (long long)n);
             return LUDVIG_ERR_OOM;
         }
-        ludvig_status r = scene_init(s, means, scales, quats, opacity, st);
+        const int linear = opts ? (opts->scales_are_linear != 0) : 0;
+        ludvig_status r = scene_init(s, means, scales, quats, opacity, linear, st);
         if (r != LUDVIG_OK) {
             ludvig_scene_destroy(s);
             return r;
@@ -203,6 +205,7 @@ extern "C" ludvig_status ludvig_scene_destroy(ludvig_scene_t s) {
         if (s->ev_free[b]) cudaEventDestroy(s->ev_free[b]);
     }
     if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+    scene_release_async(s);
     s->ws.release();
     delete s;
     return LUDVIG_OK;

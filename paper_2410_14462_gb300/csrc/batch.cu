@@ -144,6 +144,8 @@ extern "C" ludvig_status ludvig_uplift_batch(const ludvig_uplift_job* jobs, int3
                     J.scene->ws.swap(*ws);   // lend the slot's workspace to the job
                     r = ludvig_uplift(J.scene, J.cams, J.n_views, J.width, J.height, J.feats, J.dtype, J.d,
                                       J.out, J.beta, st);
+                    // complete it (a redo of what did not fit uses the lent workspace too)
+                    if (r == LUDVIG_OK) r = ludvig_sync(J.scene);
                     J.scene->ws.swap(*ws);
                 }
                 status[(size_t)j] = r;

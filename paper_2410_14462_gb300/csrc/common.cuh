@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "ludvig.h"
 
@@ -106,6 +107,33 @@ class Arena {
     std::unordered_map<std::string, Buf> dev_, host_;
 };
 
+// Device-side sizes of one group of views of an asynchronous uplift, copied
+// back to the host with the call's status: the (tile, Gaussian) pairs the
+// group needed and the weight chunks it filled.
+struct GroupDiag {
+    uint64_t pairs;
+    int32_t chunks;
+    int32_t pad;
+};
+
+// An asynchronous uplift call whose device-side capacity checks have not been
+// read yet (ludvig_sync, or the next call on the scene, reads them).  The
+// arguments are kept so that groups which did not fit the workspace can be
+// redone once it has grown.
+struct PendingCall {
+    bool active = false;
+    int kind = 0;                      // 0: accumulate into num/den, 1: uplift (+ normalise)
+    int src = 0;                       // 0: plain features, 1: zero-padded to 32 channels, 2: FP8 codes
+    std::vector<ludvig_camera> cams;
+    int n_views = 0, width = 0, height = 0, dtype = 0, d = 0;
+    const void* feats = nullptr;       // features or FP8 codes
+    const float* scales = nullptr;     // FP8 per-view scales
+    float* num = nullptr;
+    float* den = nullptr;
+    std::vector<int> v0, nv;                    // the groups' views
+    std::vector<int64_t> pair_cap, chunk_cap;   // the capacities each group ran with
+};
+
 }  // namespace ludvig
 
 // The opaque scene: a device copy of the Gaussians with the view-independent
@@ -121,6 +149,19 @@ struct ludvig_scene {
     cudaEvent_t ev_ready[2] = {nullptr, nullptr};
     cudaEvent_t ev_free[2] = {nullptr, nullptr};
     int64_t tc_chunk_cap = 0;             // tensor-core path: weight chunks kept in ws
+    int64_t pair_cap = 0;                 // (tile, Gaussian) pairs per group kept in ws
+    // asynchronous uplift: front-end and aggregation streams, their events,
+    // the device status words ([0] bounded-wait status, [1] capacity overflow)
+    // and their host mirror with the groups' sizes
+    cudaStream_t st_front = nullptr, st_agg = nullptr;
+    cudaEvent_t ev_call = nullptr, ev_front[2] = {nullptr, nullptr}, ev_agg[2] = {nullptr, nullptr};
+    cudaEvent_t ev_join[2] = {nullptr, nullptr}, ev_done = nullptr;
+    int* dstat = nullptr;                 // device [2]
+    int* hstat = nullptr;                 // pinned [2], written at the end of each call
+    ludvig::GroupDiag* ddiag = nullptr;   // device [diag_cap]
+    ludvig::GroupDiag* hdiag = nullptr;   // pinned [diag_cap]
+    int diag_cap = 0;
+    ludvig::PendingCall pending;
     ludvig::Arena ws;
 };
 
@@ -159,6 +200,15 @@ ludvig_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, u
 ludvig_status radix_sort_pairs(uint32_t** keys, uint32_t** vals, uint32_t* keys_alt,
                                uint32_t* vals_alt, int64_t nseg, int64_t seg_len, int nbits,
                                Arena& ws, cudaStream_t st);
+
+// The same for one segment whose valid length is read on the device: `len`
+// (device, may be null = all of seg_len) entries of the seg_len-entry buffers
+// are sorted; the output holds them first, then (up to the next multiple of
+// kRadixTile) largest-key fillers.  The caller guarantees that the rounded-up
+// length fits the buffers.
+ludvig_status radix_sort_pairs_len(uint32_t** keys, uint32_t** vals, uint32_t* keys_alt,
+                                   uint32_t* vals_alt, int64_t nseg, int64_t seg_len, const uint64_t* len,
+                                   int nbits, Arena& ws, cudaStream_t st);
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }

@@ -137,16 +137,30 @@ __global__ void k_scan_apply(const uint32_t* __restrict__ in, uint32_t* __restri
 
 // ------------------------------------------------------------------ radix
 
+// Keys of a sort whose length lives in device memory (`len`, one segment):
+// entries at or past the length read as the largest key (they sort last), and
+// blocks that start past it take no part (zero histogram, no output).
+__device__ __forceinline__ int64_t radix_valid(const uint64_t* len, int64_t seg_len) {
+    return len ? (int64_t)min((uint64_t)seg_len, *len) : seg_len;
+}
+
 __global__ void __launch_bounds__(kRadixThreads)
-k_radix_upsweep(const uint32_t* __restrict__ keys, int shift, uint32_t* __restrict__ hist, int64_t bps) {
+k_radix_upsweep(const uint32_t* __restrict__ keys, int shift, uint32_t* __restrict__ hist, int64_t bps,
+                const uint64_t* __restrict__ len) {
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    // positions within the block's segment are compared with the valid length
+    const int64_t seg_base = (int64_t)(blockIdx.x % bps) * kRadixTile;
+    const int64_t valid = radix_valid(len, bps * kRadixTile);
+    if (seg_base < valid) {
 #pragma unroll 4
-    for (int i = 0; i < kRadixItems; ++i) {
-        const uint32_t k = keys[base + i * kRadixThreads + threadIdx.x];
-        atomicAdd(&h[(k >> shift) & 0xffu], 1u);
+        for (int i = 0; i < kRadixItems; ++i) {
+            const int64_t off = i * kRadixThreads + threadIdx.x;
+            const uint32_t k = seg_base + off < valid ? keys[base + off] : 0xffffffffu;
+            atomicAdd(&h[(k >> shift) & 0xffu], 1u);
+        }
     }
     __syncthreads();
     const int64_t seg = blockIdx.x / bps, b = blockIdx.x % bps;
@@ -161,7 +175,7 @@ k_radix_upsweep(const uint32_t* __restrict__ keys, int shift, uint32_t* __restri
 __global__ void __launch_bounds__(kRadixThreads)
 k_radix_downsweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                   uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int shift,
-                  const uint32_t* __restrict__ hist, int64_t bps) {
+                  const uint32_t* __restrict__ hist, int64_t bps, const uint64_t* __restrict__ len) {
     constexpr int kWarps = kRadixThreads / 32;
     __shared__ uint32_t s_key[kRadixTile];
     __shared__ uint32_t s_val[kRadixTile];
@@ -171,6 +185,9 @@ k_radix_downsweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t seg = blockIdx.x / bps, b = blockIdx.x % bps;
     const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    const int64_t seg_base = b * kRadixTile;   // the block's position within its segment
+    const int64_t valid = radix_valid(len, bps * kRadixTile);
+    if (seg_base >= valid) return;   // (whole block uniform)
     const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
@@ -178,9 +195,9 @@ k_radix_downsweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__
     uint32_t k[kRadixItems], v[kRadixItems], rk[kRadixItems];
 #pragma unroll
     for (int i = 0; i < kRadixItems; ++i) {
-        const int64_t idx = base + warp * (32 * kRadixItems) + i * 32 + lane;
-        k[i] = kin[idx];
-        v[i] = vin[idx];
+        const int64_t off = warp * (32 * kRadixItems) + i * 32 + lane;
+        k[i] = seg_base + off < valid ? kin[base + off] : 0xffffffffu;
+        v[i] = seg_base + off < valid ? vin[base + off] : 0u;
     }
 #pragma unroll
     for (int i = 0; i < kRadixItems; ++i) {
@@ -264,6 +281,16 @@ ludvig_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, u
 ludvig_status radix_sort_pairs(uint32_t** keys, uint32_t** vals, uint32_t* keys_alt,
                                uint32_t* vals_alt, int64_t nseg, int64_t seg_len, int nbits,
                                Arena& ws, cudaStream_t st) {
+    return radix_sort_pairs_len(keys, vals, keys_alt, vals_alt, nseg, seg_len, nullptr, nbits, ws, st);
+}
+
+ludvig_status radix_sort_pairs_len(uint32_t** keys, uint32_t** vals, uint32_t* keys_alt,
+                                   uint32_t* vals_alt, int64_t nseg, int64_t seg_len, const uint64_t* len,
+                                   int nbits, Arena& ws, cudaStream_t st) {
+    if (len && nseg != 1) {
+        set_error("radix_sort_pairs_len: a device length needs one segment");
+        return LUDVIG_ERR_INTERNAL;
+    }
     if (nseg <= 0 || seg_len <= 0 || nbits <= 0) return LUDVIG_OK;
     if (seg_len % kRadixTile != 0) {
         set_error("radix_sort_pairs: segment length %lld not a multiple of %d", (long long)seg_len,
@@ -281,11 +308,11 @@ ludvig_status radix_sort_pairs(uint32_t** keys, uint32_t** vals, uint32_t* keys_
     LV_TRY(ws.get("radix.hist", (size_t)nh, &hist));
     uint32_t *kin = *keys, *vin = *vals, *kout = keys_alt, *vout = vals_alt;
     for (int shift = 0; shift < nbits; shift += 8) {
-        k_radix_upsweep<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(kin, shift, hist, bps);
+        k_radix_upsweep<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(kin, shift, hist, bps, len);
         LV_LAUNCH();
         LV_TRY(scan_exclusive_u32(hist, hist, nh, nullptr, ws, st));
         k_radix_downsweep<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(kin, vin, kout, vout, shift,
-                                                                       hist, bps);
+                                                                       hist, bps, len);
         LV_LAUNCH();
         uint32_t* t = kin;
         kin = kout;

@@ -2,24 +2,24 @@
 // (Sec. 3.2, Eq. 3 / Eq. 5): f_i = sum_{v,p} w_i(v,p) F_v[p] / sum_{v,p} w_i(v,p)
 // with w the alpha-blending weights of Sec. 3.1 (Eq. 1).
 //
-// Pipeline per chunk of up to kMaxViews views (all stages are batched over the
-// chunk's views):
+// Pipeline per group of up to kMaxViews views (all stages are batched over the
+// group's views):
 //   1. project     one thread per (view, Gaussian): EWA footprint, depth key,
-//                  tile rectangle, number of tiles touched
+//                  tile rectangle, number of tiles reached
 //   2. depth sort  stable radix sort of (depth bits, index) per view
-//   3. bin         exclusive scan of tiles-touched in depth order, then one
-//                  (view*tiles + tile, index) pair per touched tile
+//   3. bin         the projected records rewritten in depth order (32 bytes
+//                  each), exclusive scan of the tiles reached, then one
+//                  (view*tiles + tile, depth rank) pair per reached tile
 //   4. tile sort   stable radix sort of the pairs by (view, tile): every
 //                  tile's list stays in (depth, index) order
-//   5. ranges      [start, end) of every (view, tile) list, and the lists
-//                  rewritten as 32-byte records (projected Gaussian, index,
-//                  8x4 block mask) that the compositing kernels stream
+//   5. ranges      [start, end) of every (view, tile) list
 //   6. composite + aggregate: on the tensor cores (uplift_tc.cu: weight rows
-//                  of every tile, then W^T F by tcgen05) for d < 32 (features
-//                  zero-padded to 32 channels) and for 32 <= d <= 512 with
-//                  d % 8 == 0; otherwise here on CUDA cores, one CTA (256
-//                  threads = 16x16 pixels) per
-//                  (view, tile): walk the list in batches of 32 Gaussians,
+//                  of every tile, gathering the walked records by rank, then
+//                  W^T F by tcgen05) for d < 32 (features zero-padded to 32
+//                  channels) and for 32 <= d <= 512 with d % 8 == 0; otherwise
+//                  here on CUDA cores, one CTA (256 threads = 16x16 pixels) per
+//                  (view, tile) over list records with their 8x4 block masks:
+//                  walk the list in batches of 32 Gaussians,
 //                  form w = alpha T per pixel, keep the non-zero weights of
 //                  the tile in a shared-memory sparse store grouped by
 //                  Gaussian, then multiply the store with the tile's feature
@@ -27,6 +27,15 @@
 //                  every Gaussian's partial sum into num / den with vector
 //                  reductions.
 //   7. normalise   f = num / den (den > 0), beta = den.
+//
+// The uplift entry points do not wait on the host.  The pair count and the
+// weight-chunk count of a group are checked on the device against the
+// workspace's capacities (a group that does not fit adds nothing and is
+// redone by ludvig_sync once the workspace has grown; capacities come from
+// earlier calls, or from a first group that runs checked).  Stages 1-5 and the
+// weights of a group run on the scene's front stream, its aggregation on the
+// aggregation stream, with two buffer sets for the weight rows, so the front
+// end of group g + 1 overlaps the aggregation of group g.
 //
 // Rendering (Eq. 4, F_hat = W f) runs stages 1-5 unchanged and replaces
 // stage 6 by the transposed product: every pixel's sum of w_i(p) f_i over its
@@ -37,25 +46,14 @@
 
 #include "common.cuh"
 #include "spec.cuh"
+#include "uplift_int.cuh"
 
 namespace ludvig {
 
 constexpr int kMaxViews = 16;
 
-bool tc_supported(int dtype, int d);
 bool option_f32_tensor_cores();
 bool option_count_normalise();
-ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, int width, int height,
-                           const void* feats, int dtype, int d, float* num, float* den, Arena& ws, int* status,
-                           int64_t* chunk_cap, cudaStream_t st);
-ludvig_status render_tc(const PairRec* pairs, const uint2* ranges, int nv, int width, int height, const float* f,
-                        int d, float* out, Arena& ws, int* status, int64_t* chunk_cap, cudaStream_t st);
-
-// Per-Gaussian features rendered into the views of a chunk (Eq. 4).
-struct RenderJob {
-    const float* f;   // device [n, d]
-    float* out;       // device [views of the chunk, H, W, d]
-};
 
 struct CamBatch {
     Cam cam[kMaxViews];
@@ -70,14 +68,21 @@ bool use_tensor_cores(int dtype, int d) {
 namespace {
 
 // ------------------------------------------------------------ scene setup
+// scales: linear standard deviations, or (log_scales) their logarithms,
+// exponentiated here with CUDA's expf.
 __global__ void k_scene_init(const float* __restrict__ means, const float* __restrict__ scales,
                              const float* __restrict__ quats, const float* __restrict__ opac,
-                             int64_t n, float4* __restrict__ geo, float4* __restrict__ cov_a,
+                             int64_t n, int log_scales, float4* __restrict__ geo, float4* __restrict__ cov_a,
                              float2* __restrict__ cov_b, float* __restrict__ means_copy) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float m[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
-    const float s[3] = {scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]};
+    float s[3] = {scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]};
+    if (log_scales) {
+        s[0] = expf(s[0]);
+        s[1] = expf(s[1]);
+        s[2] = expf(s[2]);
+    }
     const float q[4] = {quats[4 * i], quats[4 * i + 1], quats[4 * i + 2], quats[4 * i + 3]};
     float S[6];
     covariance3d(s, q, S);
@@ -155,42 +160,81 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ geo,
 }
 
 // ------------------------------------------------------------ 3. bin
-__global__ void k_gather_counts(const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ svals,
-                                const uint32_t* __restrict__ ntile, int64_t npad, int64_t total,
-                                uint32_t* __restrict__ cnt) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= total) return;
-    const int64_t v = idx / npad;
-    cnt[idx] = skeys[idx] == 0xffffffffu ? 0u : ntile[v * npad + svals[idx]];
+// Largest pair count a group may have: positions are 32-bit and the sort pads
+// to whole blocks.
+constexpr int64_t kMaxPairs = 0x7fffffff - 2 * (int64_t)kRadixTile;
+
+// Whether `np` pairs fit buffers of `cap` entries (cap a multiple of the sort block).
+__device__ __forceinline__ bool pairs_fit(uint64_t np, uint64_t cap) {
+    return np <= (uint64_t)kMaxPairs && (np + kRadixTile - 1) / kRadixTile * kRadixTile <= cap;
 }
 
-__global__ void k_emit_pairs(const uint32_t* __restrict__ svals, const uint32_t* __restrict__ cnt,
-                             const uint32_t* __restrict__ off, const uint2* __restrict__ rect,
-                             const float4* __restrict__ rec_a, const float2* __restrict__ rec_b,
-                             int64_t n, int64_t npad, int64_t total, int TX, int ntiles, int prune,
-                             uint32_t sentinel, uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval) {
+// The projected records in depth order, one per (view, rank): mean, conic,
+// opacity and index in a 32-byte record (its mask word unused) plus the tile
+// rectangle, and the number of tiles each reaches (0 for the culled ones,
+// whose records are never read).
+__global__ void k_sorted_records(const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ svals,
+                                 const uint32_t* __restrict__ ntile, const float4* __restrict__ rec_a,
+                                 const float2* __restrict__ rec_b, const uint2* __restrict__ rect, int64_t n,
+                                 int64_t npad, int64_t total, uint32_t* __restrict__ cnt, PairRec* __restrict__ srec,
+                                 uint2* __restrict__ srect) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
+    if (skeys[idx] == 0xffffffffu) {
+        cnt[idx] = 0u;
+        return;
+    }
+    const int64_t v = idx / npad;
+    const uint32_t i = svals[idx];
+    const float4 ra = rec_a[v * n + i];
+    const float2 rb = rec_b[v * n + i];
+    cnt[idx] = ntile[v * npad + i];
+    PairRec r;
+    r.mx = ra.x;
+    r.my = ra.y;
+    r.ca = ra.z;
+    r.cb = ra.w;
+    r.cc = rb.x;
+    r.op = rb.y;
+    r.gid = i;
+    r.mask = 0u;
+    srec[idx] = r;
+    srect[idx] = rect[v * n + i];
+}
+
+// One (view * tiles + tile, rank) pair per tile a Gaussian reaches, written in
+// depth order at the Gaussian's scanned offset.  Nothing is written when the
+// group's pairs do not fit the buffers (the overflow word is set instead).
+__global__ void k_emit_pairs(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off,
+                             const PairRec* __restrict__ srec, const uint2* __restrict__ srect, int64_t npad,
+                             int64_t total, int TX, int ntiles, int prune, const uint64_t* __restrict__ np_dev,
+                             uint64_t cap, int* ovf, uint32_t sentinel, uint32_t* __restrict__ pkey,
+                             uint32_t* __restrict__ pval) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    if (!pairs_fit(*np_dev, cap)) {
+        if (idx == 0 && ovf) atomicOr(ovf, 1);
+        return;
+    }
     const uint32_t c = cnt[idx];
     if (c == 0) return;
     const int64_t v = idx / npad;
-    const uint32_t i = svals[idx];
-    const uint2 r = rect[v * n + i];
-    const int x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff, y1 = r.y >> 16;
-    const float4 ra = rec_a[v * n + i];
-    const float2 rb = rec_b[v * n + i];
+    const uint32_t rank = (uint32_t)(idx - v * npad);
+    const PairRec r = srec[idx];
+    const uint2 rt = srect[idx];
+    const int x0 = rt.x & 0xffff, y0 = rt.x >> 16, x1 = rt.y & 0xffff, y1 = rt.y >> 16;
     EllipseX E{};
     E.state = 2;   // unpruned: every tile of the rectangle
-    if (prune) E = ellipse_prep(reach_prep(ra.z, ra.w, rb.x, rb.y), ra.z, ra.w, rb.x);
+    if (prune) E = ellipse_prep(reach_prep(r.ca, r.cb, r.cc, r.op), r.ca, r.cb, r.cc);
     uint32_t o = off[idx];
     const uint32_t end = o + c;   // never write past the counted slots
     const uint32_t base = (uint32_t)(v * ntiles);
     for (int ty = y0; ty < y1 && o < end; ++ty) {
         int c0, c1;
-        tile_row_range(E, ra.x, ra.y, ty, x0, x1, c0, c1);
+        tile_row_range(E, r.mx, r.my, ty, x0, x1, c0, c1);
         for (int tx = c0; tx < c1 && o < end; ++tx, ++o) {
             pkey[o] = base + (uint32_t)(ty * TX + tx);
-            pval[o] = i;
+            pval[o] = rank;
         }
     }
     for (; o < end; ++o) {   // unreachable when both kernels agree; keeps the keys defined
@@ -199,44 +243,37 @@ __global__ void k_emit_pairs(const uint32_t* __restrict__ svals, const uint32_t*
     }
 }
 
-__global__ void k_fill(uint32_t* __restrict__ a, uint32_t value, int64_t from, int64_t to) {
-    const int64_t j = from + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < to) a[j] = value;
-}
-
 // ------------------------------------------------------------ 5. ranges
-__global__ void k_ranges(const uint32_t* __restrict__ pkey, int64_t P, uint32_t nkeys,
-                         uint2* __restrict__ ranges) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= P) return;
-    const uint32_t k = pkey[j];
-    if (k >= nkeys) return;
-    if (j == 0 || pkey[j - 1] != k) ranges[k].x = (uint32_t)j;
-    if (j == P - 1 || pkey[j + 1] != k) ranges[k].y = (uint32_t)(j + 1);
+__global__ void k_ranges(const uint32_t* __restrict__ pkey, const uint64_t* __restrict__ np_dev, uint64_t cap,
+                         uint32_t nkeys, uint2* __restrict__ ranges) {
+    const uint64_t np = *np_dev;
+    if (!pairs_fit(np, cap)) return;
+    const int64_t P = (int64_t)np;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = pkey[j];
+        if (k >= nkeys) continue;
+        if (j == 0 || pkey[j - 1] != k) ranges[k].x = (uint32_t)j;
+        if (j == P - 1 || pkey[j + 1] != k) ranges[k].y = (uint32_t)(j + 1);
+    }
 }
 
-// The sorted lists as the compositing kernels stream them: one 32-byte record
-// per entry, in list order, with the entry's 8x4 block mask.
-__global__ void k_pair_records(const uint32_t* __restrict__ pkey, const uint32_t* __restrict__ pval, int64_t P,
-                               int ntiles, int TX, int64_t n, const float4* __restrict__ rec_a,
-                               const float2* __restrict__ rec_b, PairRec* __restrict__ out) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= P) return;
-    const uint32_t key = pkey[j], g = pval[j];
-    const uint32_t v = key / (uint32_t)ntiles, tile = key - v * (uint32_t)ntiles;
-    const int tx = (int)(tile % (uint32_t)TX), ty = (int)(tile / (uint32_t)TX);
-    const float4 ra = rec_a[(int64_t)v * n + g];
-    const float2 rb = rec_b[(int64_t)v * n + g];
-    PairRec r;
-    r.mx = ra.x;
-    r.my = ra.y;
-    r.ca = ra.z;
-    r.cb = ra.w;
-    r.cc = rb.x;
-    r.op = rb.y;
-    r.gid = g;
-    r.mask = block_mask(reach_prep(ra.z, ra.w, rb.x, rb.y), ra.x, ra.y, ra.z, ra.w, rb.x, tx, ty);
-    out[j] = r;
+// The sorted lists as the CUDA-core compositing kernels stream them: one
+// 32-byte record per entry, in list order, with the entry's 8x4 block mask.
+// (The tensor-core weights kernel gathers the depth-ordered records itself.)
+__global__ void k_pair_records(const uint32_t* __restrict__ pkey, const uint32_t* __restrict__ pval,
+                               const uint64_t* __restrict__ np_dev, uint64_t cap, int ntiles, int TX, int64_t npad,
+                               const PairRec* __restrict__ srec, PairRec* __restrict__ out) {
+    const uint64_t np = *np_dev;
+    if (!pairs_fit(np, cap)) return;
+    const int64_t P = (int64_t)np;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = pkey[j];
+        const uint32_t v = key / (uint32_t)ntiles, tile = key - v * (uint32_t)ntiles;
+        const int tx = (int)(tile % (uint32_t)TX), ty = (int)(tile / (uint32_t)TX);
+        PairRec r = srec[(int64_t)v * npad + pval[j]];
+        r.mask = block_mask(reach_prep(r.ca, r.cb, r.cc, r.op), r.mx, r.my, r.ca, r.cb, r.cc, tx, ty);
+        out[j] = r;
+    }
 }
 
 // ------------------------------------------------------------ 6. composite + aggregate
@@ -581,10 +618,13 @@ __global__ void __launch_bounds__(256) k_render_cc(RenderArgs a) {
 }
 
 // ------------------------------------------------------------ 7. normalise
+// `skip` (device, may be null): when non-zero, nothing is written (an
+// asynchronous uplift whose sums are still incomplete).
 __global__ void k_normalise(const float* num, const float* __restrict__ den, float* out, float* beta,
-                            int64_t n, int d) {
+                            int64_t n, int d, const int* __restrict__ skip) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * d) return;
+    if (skip && *skip) return;
     const int64_t i = idx / d;
     const float b = den[i];
     out[idx] = b > 0.f ? num[idx] / b : 0.f;
@@ -594,7 +634,8 @@ __global__ void k_normalise(const float* num, const float* __restrict__ den, flo
 // Same, one warp per Gaussian (d >= 32), float4 accesses when vec4 (d % 4 == 0
 // and 16-byte aligned rows).
 __global__ void k_normalise_rows(const float* num, const float* __restrict__ den, float* out, float* beta,
-                                 int64_t n, int d, int vec4) {
+                                 int64_t n, int d, int vec4, const int* __restrict__ skip) {
+    if (skip && *skip) return;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps) {
@@ -615,6 +656,9 @@ __global__ void k_normalise_rows(const float* num, const float* __restrict__ den
 }
 
 unsigned grid_for(int64_t work, int threads) { return (unsigned)ceil_div(work, threads); }
+
+// Grid of the grid-stride kernels over a group's pairs (their count is on the device).
+constexpr unsigned kPairGrid = 152 * 16;
 
 struct ChunkDebug {
     float* rec = nullptr;
@@ -645,9 +689,13 @@ __global__ void k_debug_fill(float* __restrict__ t, int32_t* __restrict__ c, int
     }
 }
 
-__global__ void k_copy_u32_i32(const uint32_t* __restrict__ a, int32_t* __restrict__ b, int64_t n) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) b[t] = (int32_t)a[t];
+// The list entries as Gaussian indices (the lists hold depth ranks).
+__global__ void k_export_list(const uint32_t* __restrict__ pkey, const uint32_t* __restrict__ pval, int64_t P,
+                              int ntiles, int64_t npad, const PairRec* __restrict__ srec, int32_t* __restrict__ out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P) return;
+    const int64_t v = pkey[j] / (uint32_t)ntiles;
+    out[j] = (int32_t)srec[v * npad + pval[j]].gid;
 }
 
 size_t composite_smem() { return sizeof(CompositeSmem); }
@@ -669,239 +717,6 @@ ludvig_status launch_render_cc(const RenderArgs& args, int64_t nitems, cudaStrea
     StageScope scope(LUDVIG_STAGE_RENDER_PRODUCT, st);
     k_render_cc<DC><<<grid, 256, 0, st>>>(args);
     LV_LAUNCH();
-    return LUDVIG_OK;
-}
-
-// One chunk of views: stages 1-6 (stage 6 renders instead when `rj` is set).
-ludvig_status run_chunk(ludvig_scene* s, const ludvig_camera* cams, int nv, int width, int height,
-                        const void* feats, int dtype, int d, float* num, float* den, cudaStream_t st,
-                        const ChunkDebug* dbg, bool* too_many_pairs, const RenderJob* rj = nullptr) {
-    Arena& ws = s->ws;
-    const int64_t n = s->n;
-    const int64_t npad = round_up(n, kRadixTile);
-    const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
-    const int ntiles = TX * TY;
-    const int64_t nG = (int64_t)nv * npad;
-    const int prune = (dbg && dbg->unpruned) ? 0 : 1;
-    *too_many_pairs = false;
-
-    float4* rec_a;
-    float2* rec_b;
-    uint2* rect;
-    uint32_t *keys, *vals, *keys2, *vals2, *ntile, *cnt, *off;
-    uint64_t* total_d;
-    LV_TRY(ws.get("up.rec_a", (size_t)nv * n, &rec_a));
-    LV_TRY(ws.get("up.rec_b", (size_t)nv * n, &rec_b));
-    LV_TRY(ws.get("up.rect", (size_t)nv * n, &rect));
-    LV_TRY(ws.get("up.keys", (size_t)nG, &keys));
-    LV_TRY(ws.get("up.vals", (size_t)nG, &vals));
-    LV_TRY(ws.get("up.keys2", (size_t)nG, &keys2));
-    LV_TRY(ws.get("up.vals2", (size_t)nG, &vals2));
-    LV_TRY(ws.get("up.ntile", (size_t)nG, &ntile));
-    LV_TRY(ws.get("up.cnt", (size_t)nG, &cnt));
-    LV_TRY(ws.get("up.off", (size_t)nG, &off));
-    LV_TRY(ws.get("up.total", 1, &total_d));
-    uint64_t* total_h = nullptr;
-    {
-        void* p;
-        LV_TRY(ws.pinned("up.total_h", 16, &p));
-        total_h = static_cast<uint64_t*>(p);
-    }
-
-    CamBatch cb;
-    for (int v = 0; v < nv; ++v) {
-        const ludvig_camera& c = cams[v];
-        for (int k = 0; k < 9; ++k) cb.cam[v].R[k] = c.R[k];
-        for (int k = 0; k < 3; ++k) cb.cam[v].t[k] = c.t[k];
-        cb.cam[v].fx = c.fx;
-        cb.cam[v].fy = c.fy;
-        cb.cam[v].cx = c.cx;
-        cb.cam[v].cy = c.cy;
-    }
-    int tslot = trace_on() ? trace_begin(LUDVIG_STAGE_PROJECT, st) : -1;
-    k_project<<<grid_for(nG, 256), 256, 0, st>>>(s->geo, s->cov_a, s->cov_b, n, npad, nv, cb, width,
-                                                  height, rec_a, rec_b, rect, keys, vals, ntile,
-                                                  dbg ? dbg->rec : nullptr, dbg ? dbg->rect : nullptr,
-                                                  prune);
-    LV_LAUNCH();
-    trace_end(tslot, st);
-    if (dbg && dbg->stop_after_project) return LUDVIG_OK;
-
-    uint32_t *sk = keys, *sv = vals;
-    tslot = trace_on() ? trace_begin(LUDVIG_STAGE_DEPTH_SORT, st) : -1;
-    LV_TRY(radix_sort_pairs(&sk, &sv, keys2, vals2, nv, npad, 32, ws, st));
-    trace_end(tslot, st);
-    tslot = trace_on() ? trace_begin(LUDVIG_STAGE_BIN, st) : -1;
-    k_gather_counts<<<grid_for(nG, 256), 256, 0, st>>>(sk, sv, ntile, npad, nG, cnt);
-    LV_LAUNCH();
-    LV_TRY(scan_exclusive_u32(cnt, off, nG, total_d, ws, st));
-    LV_CUDA(cudaMemcpyAsync(total_h, total_d, 8, cudaMemcpyDeviceToHost, st));
-    LV_CUDA(cudaStreamSynchronize(st));
-    const int64_t P = (int64_t)*total_h;
-    if (P > (int64_t)0x7fffffff - 2 * kRadixTile) {
-        *too_many_pairs = true;
-        return LUDVIG_OK;
-    }
-    const int64_t Ppad = round_up(std::max<int64_t>(P, 1), kRadixTile);
-    const uint32_t sentinel = (uint32_t)nv * (uint32_t)ntiles;
-    uint32_t *pk, *pv, *pk2, *pv2;
-    LV_TRY(ws.get("up.pk", (size_t)Ppad, &pk));
-    LV_TRY(ws.get("up.pv", (size_t)Ppad, &pv));
-    LV_TRY(ws.get("up.pk2", (size_t)Ppad, &pk2));
-    LV_TRY(ws.get("up.pv2", (size_t)Ppad, &pv2));
-    k_emit_pairs<<<grid_for(nG, 256), 256, 0, st>>>(sv, cnt, off, rect, rec_a, rec_b, n, npad, nG, TX, ntiles,
-                                                     prune, sentinel, pk, pv);
-    LV_LAUNCH();
-    trace_end(tslot, st);
-    tslot = trace_on() ? trace_begin(LUDVIG_STAGE_TILE_SORT, st) : -1;
-    if (Ppad > P) {
-        k_fill<<<grid_for(Ppad - P, 256), 256, 0, st>>>(pk, sentinel, P, Ppad);
-        LV_LAUNCH();
-        k_fill<<<grid_for(Ppad - P, 256), 256, 0, st>>>(pv, 0u, P, Ppad);
-        LV_LAUNCH();
-    }
-    int nbits = 1;
-    while (((uint32_t)1 << nbits) <= sentinel) ++nbits;
-    uint32_t *spk = pk, *spv = pv;
-    LV_TRY(radix_sort_pairs(&spk, &spv, pk2, pv2, 1, Ppad, nbits, ws, st));
-    uint2* ranges;
-    LV_TRY(ws.get("up.ranges", (size_t)nv * ntiles, &ranges));
-    LV_CUDA(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)nv * ntiles, st));
-    if (P > 0) {
-        k_ranges<<<grid_for(P, 256), 256, 0, st>>>(spk, P, sentinel, ranges);
-        LV_LAUNCH();
-    }
-    trace_end(tslot, st);
-    if (dbg && dbg->ranges64) {
-        k_export_ranges<<<grid_for(ntiles, 256), 256, 0, st>>>(ranges, ntiles, dbg->ranges64);
-        LV_LAUNCH();
-        *dbg->list_total = P;
-        if (P <= dbg->list_cap && P > 0) {
-            k_copy_u32_i32<<<grid_for(P, 256), 256, 0, st>>>(spv, dbg->list, P);
-            LV_LAUNCH();
-        }
-    }
-    if (dbg && dbg->stop_after_sort) return LUDVIG_OK;
-
-    PairRec* pairs;
-    LV_TRY(ws.get("up.pairs", (size_t)std::max<int64_t>(P, 1), &pairs));
-    tslot = trace_on() ? trace_begin(LUDVIG_STAGE_TILE_SORT, st) : -1;
-    if (P > 0) {
-        k_pair_records<<<grid_for(P, 256), 256, 0, st>>>(spk, spv, P, ntiles, TX, n, rec_a, rec_b, pairs);
-        LV_LAUNCH();
-    }
-    trace_end(tslot, st);
-
-    const int64_t nitems = (int64_t)nv * ntiles;
-    if (rj) {
-        StageScope scope(LUDVIG_STAGE_RENDER, st);
-        if (use_tensor_cores(LUDVIG_F32, d)) {
-            int* status;
-            LV_TRY(ws.get("tc.status", 1, &status));
-            return render_tc(pairs, ranges, nv, width, height, rj->f, d, rj->out, ws, status, &s->tc_chunk_cap,
-                             st);
-        }
-        RenderArgs r;
-        r.pairs = pairs;
-        r.ranges = ranges;
-        r.ntiles = ntiles;
-        r.TX = TX;
-        r.width = width;
-        r.height = height;
-        r.f = rj->f;
-        r.d = d;
-        r.out = rj->out;
-        if (d <= 4) return launch_render_cc<4>(r, nitems, st);
-        if (d <= 8) return launch_render_cc<8>(r, nitems, st);
-        if (d <= 16) return launch_render_cc<16>(r, nitems, st);
-        return launch_render_cc<32>(r, nitems, st);
-    }
-    CompositeArgs args;
-    args.pairs = pairs;
-    args.ranges = ranges;
-    args.ntiles = ntiles;
-    args.TX = TX;
-    args.width = width;
-    args.height = height;
-    args.feats = feats;
-    args.d = d;
-    args.num = num;
-    args.den = den;
-    args.dbg_t = dbg ? dbg->t_final : nullptr;
-    args.dbg_cnt = dbg ? dbg->n_contrib : nullptr;
-    args.count_den = option_count_normalise() ? 1 : 0;
-    const bool vec = (d % 4 == 0);
-    StageScope scope(LUDVIG_STAGE_COMPOSITE, st);
-    if (use_tensor_cores(dtype, d)) {
-        int* status;
-        LV_TRY(ws.get("tc.status", 1, &status));
-        return composite_tc(pairs, ranges, nv, width, height, feats, dtype, d, num, den, ws, status,
-                            &s->tc_chunk_cap, st);
-    }
-    if (dtype == LUDVIG_F32) {
-        if (vec) return launch_composite<float, true>(args, nitems, st);
-        return launch_composite<float, false>(args, nitems, st);
-    }
-    if (vec) return launch_composite<__nv_bfloat16, true>(args, nitems, st);
-    return launch_composite<__nv_bfloat16, false>(args, nitems, st);
-}
-
-ludvig_status check_views(const ludvig_camera* cams, int32_t n_views, int32_t width, int32_t height) {
-    LV_ARG(n_views >= 0, "n_views must be >= 0");
-    LV_ARG(n_views == 0 || cams != nullptr, "cams is NULL");
-    LV_ARG(width > 0 && height > 0, "width and height must be positive");
-    LV_ARG(width <= 16 * 4095 && height <= 16 * 4095, "image too large");
-    for (int v = 0; v < n_views; ++v) {
-        LV_ARG(cams[v].fx > 0.f && cams[v].fy > 0.f, "camera %d: focal lengths must be positive", v);
-    }
-    return LUDVIG_OK;
-}
-
-ludvig_status accumulate(ludvig_scene* s, const ludvig_camera* cams, int32_t n_views, int32_t width,
-                         int32_t height, const void* feats, int32_t dtype, int32_t d, float* num,
-                         float* den, cudaStream_t st, const ChunkDebug* dbg, const RenderJob* rj = nullptr) {
-    const size_t esize = dtype == LUDVIG_F32 ? 4 : 2;
-    const int64_t view_elems = (int64_t)width * height * d;
-    int* status = nullptr;
-    if (use_tensor_cores(dtype, d)) {
-        LV_TRY(s->ws.get("tc.status", 1, &status));
-        LV_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
-    }
-    int v0 = 0;
-    int vc = std::min<int>(kMaxViews, std::max<int>(1, n_views));
-    // keep the per-chunk Gaussian scratch (about 80 bytes per Gaussian and view) near 2 GB
-    const int64_t per_view = std::max<int64_t>(1, s->n) * 80;
-    vc = (int)std::max<int64_t>(1, std::min<int64_t>(vc, ((int64_t)2 << 30) / per_view));
-    while (v0 < n_views) {
-        const int nv = std::min(vc, n_views - v0);
-        bool too_many = false;
-        const char* fp = feats ? static_cast<const char*>(feats) + (size_t)v0 * view_elems * esize : nullptr;
-        RenderJob part{};
-        if (rj) part = RenderJob{rj->f, rj->out + (size_t)v0 * view_elems};
-        LV_TRY(run_chunk(s, cams + v0, nv, width, height, fp, dtype, d, num, den, st, dbg, &too_many,
-                         rj ? &part : nullptr));
-        if (too_many) {
-            if (nv == 1) {
-                set_error("view %d produces more than 2^31 tile/Gaussian pairs", v0);
-                return LUDVIG_ERR_UNSUPPORTED;
-            }
-            vc = std::max(1, nv / 2);
-            continue;
-        }
-        v0 += nv;
-    }
-    if (status) {
-        // device-side status of the tensor-core kernel (bounded waits)
-        void* h;
-        LV_TRY(s->ws.pinned("tc.status_h", 16, &h));
-        LV_CUDA(cudaMemcpyAsync(h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
-        LV_CUDA(cudaStreamSynchronize(st));
-        const int code = *static_cast<int*>(h);
-        if (code != 0) {
-            set_error("tensor-core kernel reported status %d (a bounded wait expired)", code);
-            return (ludvig_status)code;
-        }
-    }
     return LUDVIG_OK;
 }
 
@@ -942,38 +757,6 @@ __global__ void k_add_columns(const float* __restrict__ wide, int64_t n, int d, 
 
 bool use_padded(int dtype, int d) { return d < kPadD && use_tensor_cores(dtype, kPadD); }
 
-ludvig_status accumulate_padded(ludvig_scene* s, const ludvig_camera* cams, int32_t n_views, int32_t width,
-                                int32_t height, const void* feats, int32_t dtype, int32_t d, float* num,
-                                float* den, cudaStream_t st) {
-    const int64_t n = s->n;
-    const int64_t px_view = (int64_t)width * height;
-    const size_t esize = dtype == LUDVIG_F32 ? 4 : 2;
-    const int vc = std::min<int>(kMaxViews, n_views);
-    float* wide;
-    void* fpad;
-    LV_TRY(s->ws.get("pad.num", (size_t)n * kPadD, &wide));
-    LV_TRY(s->ws.get("pad.feats", (size_t)vc * px_view * kPadD * esize, &fpad));
-    LV_CUDA(cudaMemsetAsync(wide, 0, sizeof(float) * (size_t)n * kPadD, st));
-    for (int v0 = 0; v0 < n_views; v0 += vc) {
-        const int nv = std::min(vc, n_views - v0);
-        const int64_t npx = (int64_t)nv * px_view;
-        const char* src = static_cast<const char*>(feats) + (size_t)v0 * px_view * d * esize;
-        // 16-byte groups per padded pixel: 8 (float) or 4 (bfloat16)
-        const int64_t groups = npx * (kPadD * (int64_t)esize / 16);
-        if (dtype == LUDVIG_F32)
-            k_pad_features<float><<<grid_for(groups, 256), 256, 0, st>>>(
-                reinterpret_cast<const float*>(src), npx, d, static_cast<float*>(fpad));
-        else
-            k_pad_features<__nv_bfloat16><<<grid_for(groups, 256), 256, 0, st>>>(
-                reinterpret_cast<const __nv_bfloat16*>(src), npx, d, static_cast<__nv_bfloat16*>(fpad));
-        LV_LAUNCH();
-        LV_TRY(accumulate(s, cams + v0, nv, width, height, fpad, dtype, kPadD, wide, den, st, nullptr));
-    }
-    k_add_columns<<<grid_for(n * d, 256), 256, 0, st>>>(wide, n, d, num);
-    LV_LAUNCH();
-    return LUDVIG_OK;
-}
-
 // FP8-E4M3 features (codes q, per-view scales s): x = decode(q) s_v rounded
 // to bfloat16 for the tensor-core path (the E4M3 value is exact in half
 // precision; the bfloat16 rounding adds at most 2^-9 relative to an FP8
@@ -1002,21 +785,601 @@ __global__ void k_dequant_e4m3(const uint8_t* __restrict__ q, const float* __res
     }
 }
 
-}  // namespace
+// ---------------------------------------------------------------- front end
 
-// ---------------------------------------------------------------- scene
-ludvig_status scene_init(ludvig_scene* s, const float* means, const float* scales, const float* quats,
-                         const float* opac, cudaStream_t st) {
-    if (s->n == 0) return LUDVIG_OK;
-    k_scene_init<<<grid_for(s->n, 256), 256, 0, st>>>(means, scales, quats, opac, s->n, s->geo, s->cov_a,
-                                                      s->cov_b, s->means);
+// The lists of a group of views after stages 1-5.
+struct FrontEnd {
+    GroupLists L{};
+    const uint32_t* spk = nullptr;   // sorted pair keys (view * tiles + tile)
+    const uint64_t* np = nullptr;    // device: the group's pair count
+    int64_t cap = 0;                 // capacity of the pair buffers
+    int64_t P = -1;                  // pair count, when read back (checked runs)
+    bool too_many = false;           // checked runs: more pairs than one group may hold
+};
+
+// Stages 1-5 of a group of nv views on `st`.  checked: the pair count is read
+// back (synchronises `st`) and the pair buffers grow to fit it.  Otherwise
+// nothing waits: the buffers keep the scene's pair capacity, and a group that
+// needs more sets *ovf, writes no pairs (all lists empty) and is redone later.
+ludvig_status front_end(ludvig_scene* s, const ludvig_camera* cams, int nv, int width, int height, bool checked,
+                        int* ovf, const ChunkDebug* dbg, cudaStream_t st, FrontEnd* fe) {
+    Arena& ws = s->ws;
+    const int64_t n = s->n;
+    const int64_t npad = round_up(n, kRadixTile);
+    const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
+    const int ntiles = TX * TY;
+    const int64_t nG = (int64_t)nv * npad;
+    const int prune = (dbg && dbg->unpruned) ? 0 : 1;
+
+    float4* rec_a;
+    float2* rec_b;
+    uint2 *rect, *srect;
+    uint32_t *keys, *vals, *keys2, *vals2, *ntile, *cnt, *off;
+    PairRec* srec;
+    uint64_t* total_d;
+    LV_TRY(ws.get("up.rec_a", (size_t)nv * n, &rec_a));
+    LV_TRY(ws.get("up.rec_b", (size_t)nv * n, &rec_b));
+    LV_TRY(ws.get("up.rect", (size_t)nv * n, &rect));
+    LV_TRY(ws.get("up.keys", (size_t)nG, &keys));
+    LV_TRY(ws.get("up.vals", (size_t)nG, &vals));
+    LV_TRY(ws.get("up.keys2", (size_t)nG, &keys2));
+    LV_TRY(ws.get("up.vals2", (size_t)nG, &vals2));
+    LV_TRY(ws.get("up.ntile", (size_t)nG, &ntile));
+    LV_TRY(ws.get("up.cnt", (size_t)nG, &cnt));
+    LV_TRY(ws.get("up.off", (size_t)nG, &off));
+    LV_TRY(ws.get("up.srec", (size_t)nG, &srec));
+    LV_TRY(ws.get("up.srect", (size_t)nG, &srect));
+    LV_TRY(ws.get("up.total", 1, &total_d));
+
+    CamBatch cb;
+    for (int v = 0; v < nv; ++v) {
+        const ludvig_camera& c = cams[v];
+        for (int k = 0; k < 9; ++k) cb.cam[v].R[k] = c.R[k];
+        for (int k = 0; k < 3; ++k) cb.cam[v].t[k] = c.t[k];
+        cb.cam[v].fx = c.fx;
+        cb.cam[v].fy = c.fy;
+        cb.cam[v].cx = c.cx;
+        cb.cam[v].cy = c.cy;
+    }
+    int tslot = trace_on() ? trace_begin(LUDVIG_STAGE_PROJECT, st) : -1;
+    k_project<<<grid_for(nG, 256), 256, 0, st>>>(s->geo, s->cov_a, s->cov_b, n, npad, nv, cb, width,
+                                                  height, rec_a, rec_b, rect, keys, vals, ntile,
+                                                  dbg ? dbg->rec : nullptr, dbg ? dbg->rect : nullptr,
+                                                  prune);
+    LV_LAUNCH();
+    trace_end(tslot, st);
+    if (dbg && dbg->stop_after_project) return LUDVIG_OK;
+
+    uint32_t *sk = keys, *sv = vals;
+    tslot = trace_on() ? trace_begin(LUDVIG_STAGE_DEPTH_SORT, st) : -1;
+    LV_TRY(radix_sort_pairs(&sk, &sv, keys2, vals2, nv, npad, 32, ws, st));
+    trace_end(tslot, st);
+    tslot = trace_on() ? trace_begin(LUDVIG_STAGE_BIN, st) : -1;
+    k_sorted_records<<<grid_for(nG, 256), 256, 0, st>>>(sk, sv, ntile, rec_a, rec_b, rect, n, npad, nG, cnt, srec,
+                                                        srect);
+    LV_LAUNCH();
+    LV_TRY(scan_exclusive_u32(cnt, off, nG, total_d, ws, st));
+    int64_t P = -1;
+    if (checked) {
+        void* h;
+        LV_TRY(ws.pinned("up.total_h", 16, &h));
+        LV_CUDA(cudaMemcpyAsync(h, total_d, 8, cudaMemcpyDeviceToHost, st));
+        LV_CUDA(cudaStreamSynchronize(st));
+        P = (int64_t)*static_cast<uint64_t*>(h);
+        if (P > kMaxPairs) {
+            trace_end(tslot, st);
+            fe->too_many = true;
+            return LUDVIG_OK;
+        }
+        const int64_t need = round_up(std::max<int64_t>(P, 1), kRadixTile);
+        if (s->pair_cap < need) s->pair_cap = round_up(need + need / 8, kRadixTile);
+    }
+    const int64_t cap = std::max<int64_t>(s->pair_cap, kRadixTile);
+    const uint32_t sentinel = (uint32_t)nv * (uint32_t)ntiles;
+    uint32_t *pk, *pv, *pk2, *pv2;
+    LV_TRY(ws.get("up.pk", (size_t)cap, &pk));
+    LV_TRY(ws.get("up.pv", (size_t)cap, &pv));
+    LV_TRY(ws.get("up.pk2", (size_t)cap, &pk2));
+    LV_TRY(ws.get("up.pv2", (size_t)cap, &pv2));
+    k_emit_pairs<<<grid_for(nG, 256), 256, 0, st>>>(cnt, off, srec, srect, npad, nG, TX, ntiles, prune, total_d,
+                                                     (uint64_t)cap, ovf, sentinel, pk, pv);
+    LV_LAUNCH();
+    trace_end(tslot, st);
+    tslot = trace_on() ? trace_begin(LUDVIG_STAGE_TILE_SORT, st) : -1;
+    int nbits = 1;
+    while (((uint32_t)1 << nbits) <= sentinel) ++nbits;
+    uint32_t *spk = pk, *spv = pv;
+    LV_TRY(radix_sort_pairs_len(&spk, &spv, pk2, pv2, 1, cap, total_d, nbits, ws, st));
+    uint2* ranges;
+    LV_TRY(ws.get("up.ranges", (size_t)nv * ntiles, &ranges));
+    LV_CUDA(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)nv * ntiles, st));
+    k_ranges<<<kPairGrid, 256, 0, st>>>(spk, total_d, (uint64_t)cap, sentinel, ranges);
+    LV_LAUNCH();
+    trace_end(tslot, st);
+    if (dbg && dbg->ranges64) {
+        k_export_ranges<<<grid_for(ntiles, 256), 256, 0, st>>>(ranges, ntiles, dbg->ranges64);
+        LV_LAUNCH();
+        *dbg->list_total = P;
+        if (P <= dbg->list_cap && P > 0) {
+            k_export_list<<<grid_for(P, 256), 256, 0, st>>>(spk, spv, P, ntiles, npad, srec, dbg->list);
+            LV_LAUNCH();
+        }
+    }
+    fe->L = GroupLists{ranges, spv, srec, npad};
+    fe->spk = spk;
+    fe->np = total_d;
+    fe->cap = cap;
+    fe->P = P;
+    return LUDVIG_OK;
+}
+
+// CUDA-core stage 6 of a group (k_composite): the list records with their
+// block masks, then the per-tile composite with its shared-memory weight store.
+ludvig_status composite_cc(ludvig_scene* s, const FrontEnd& fe, int nv, int width, int height, const void* feats,
+                           int dtype, int d, float* num, float* den, const ChunkDebug* dbg, cudaStream_t st) {
+    const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
+    const int ntiles = TX * TY;
+    PairRec* pairs;
+    LV_TRY(s->ws.get("up.pairs", (size_t)fe.cap, &pairs));
+    StageScope scope(LUDVIG_STAGE_COMPOSITE, st);
+    k_pair_records<<<kPairGrid, 256, 0, st>>>(fe.spk, fe.L.rank, fe.np, (uint64_t)fe.cap, ntiles, TX, fe.L.npad,
+                                              fe.L.srec, pairs);
+    LV_LAUNCH();
+    CompositeArgs args;
+    args.pairs = pairs;
+    args.ranges = fe.L.ranges;
+    args.ntiles = ntiles;
+    args.TX = TX;
+    args.width = width;
+    args.height = height;
+    args.feats = feats;
+    args.d = d;
+    args.num = num;
+    args.den = den;
+    args.dbg_t = dbg ? dbg->t_final : nullptr;
+    args.dbg_cnt = dbg ? dbg->n_contrib : nullptr;
+    args.count_den = option_count_normalise() ? 1 : 0;
+    const int64_t nitems = (int64_t)nv * ntiles;
+    const bool vec = (d % 4 == 0);
+    if (dtype == LUDVIG_F32) {
+        if (vec) return launch_composite<float, true>(args, nitems, st);
+        return launch_composite<float, false>(args, nitems, st);
+    }
+    if (vec) return launch_composite<__nv_bfloat16, true>(args, nitems, st);
+    return launch_composite<__nv_bfloat16, false>(args, nitems, st);
+}
+
+// ---------------------------------------------------------------- group pipeline
+
+// The features of a call as its groups read them.
+struct FeatSrc {
+    int kind = 0;                  // 0: as given, 1: zero-padded to kPadD channels, 2: FP8-E4M3 codes
+    const void* feats = nullptr;   // [n_views, H, W, d] features, or codes for kind 2
+    const float* scales = nullptr; // kind 2: per-view scales
+    int dtype = LUDVIG_F32;        // of the given features (kind 2: decoded to bfloat16)
+    int d = 1;
+};
+
+bool src_padded(const FeatSrc& f) { return f.kind == 1 || (f.kind == 2 && f.d < kPadD); }
+
+// How a group's work is ordered.
+struct Exec {
+    bool async = false;          // device-side capacity checks; front end on the scene's front stream and
+                                 // aggregation on its aggregation stream; the host never waits
+    cudaStream_t st = nullptr;   // checked runs: the stream everything runs on
+    int group = 0;               // index within the call (async: selects the buffer set)
+    GroupDiag* diag = nullptr;   // async: the group's device record
+    int* ovf = nullptr;          // async: the call's overflow word
+};
+
+// Stages 1-6 of one group (views v0 .. v0 + nv - 1): num/den (pad_num when
+// padded) += the group's W^T F and weight sums.
+ludvig_status uplift_group(ludvig_scene* s, const ludvig_camera* cams, int v0, int nv, int width, int height,
+                           const FeatSrc& src, float* num, float* den, float* pad_num, const Exec& ex,
+                           bool* too_many, int64_t* pair_cap = nullptr, int64_t* chunk_cap = nullptr) {
+    const bool padded = src_padded(src);
+    const int fdt = src.kind == 2 ? LUDVIG_BF16 : src.dtype;   // the dtype the kernels read
+    const int deff = padded ? kPadD : src.d;
+    const bool tc = padded || use_tensor_cores(fdt, deff);
+    cudaStream_t sf = ex.async ? s->st_front : ex.st;
+    cudaStream_t sa = ex.async ? s->st_agg : ex.st;
+    const int p = ex.group & 1;
+    *too_many = false;
+    FrontEnd fe;
+    LV_TRY(front_end(s, cams + v0, nv, width, height, !ex.async, ex.async ? ex.ovf : nullptr, nullptr, sf, &fe));
+    if (fe.too_many) {
+        *too_many = true;
+        return LUDVIG_OK;
+    }
+    if (ex.async) LV_CUDA(cudaMemcpyAsync(&ex.diag->pairs, fe.np, sizeof(uint64_t), cudaMemcpyDeviceToDevice, sf));
+    if (pair_cap) *pair_cap = fe.cap;
+    if (chunk_cap) *chunk_cap = 0x7fffffff;   // no weight rows on the CUDA-core path
+    const int64_t view_elems = (int64_t)width * height * src.d;
+    const size_t esize = src.kind == 2 ? 1 : (src.dtype == LUDVIG_F32 ? 4 : 2);
+    const void* f = static_cast<const char*>(src.feats) + (size_t)v0 * view_elems * esize;
+    if (!tc) return composite_cc(s, fe, nv, width, height, f, fdt, deff, num, den, nullptr, sf);
+
+    // tensor cores: the operand features and the weight rows go to the
+    // buffer set of parity p, free once the aggregation of group - 2 is done
+    if (ex.async && ex.group >= 2) LV_CUDA(cudaStreamWaitEvent(sf, s->ev_agg[p], 0));
+    static const char* const kFb[2] = {"fp8.bf16.0", "fp8.bf16.1"};
+    static const char* const kPad[2] = {"pad.feats.0", "pad.feats.1"};
+    if (src.kind == 2) {
+        __nv_bfloat16* fb;
+        const int64_t total = (int64_t)nv * view_elems;
+        LV_TRY(s->ws.get(kFb[p], (size_t)total, &fb));
+        // groups start a multiple of 16 views in: the codes stay 4-byte aligned
+        k_dequant_e4m3<<<grid_for(ceil_div(total, 4), 256), 256, 0, sf>>>(static_cast<const uint8_t*>(f),
+                                                                         src.scales + v0, view_elems, total, fb);
+        LV_LAUNCH();
+        f = fb;
+    }
+    if (padded) {
+        const int64_t npx = (int64_t)nv * width * height;
+        const size_t pes = fdt == LUDVIG_F32 ? 4 : 2;
+        void* fpad;
+        LV_TRY(s->ws.get(kPad[p], (size_t)npx * kPadD * pes, &fpad));
+        // 16-byte groups per padded pixel: 8 (float) or 4 (bfloat16)
+        const int64_t groups = npx * (kPadD * (int64_t)pes / 16);
+        if (fdt == LUDVIG_F32)
+            k_pad_features<float><<<grid_for(groups, 256), 256, 0, sf>>>(static_cast<const float*>(f), npx, src.d,
+                                                                         static_cast<float*>(fpad));
+        else
+            k_pad_features<__nv_bfloat16><<<grid_for(groups, 256), 256, 0, sf>>>(
+                static_cast<const __nv_bfloat16*>(f), npx, src.d, static_cast<__nv_bfloat16*>(fpad));
+        LV_LAUNCH();
+        f = fpad;
+    }
+    TileWeights t;
+    LV_TRY(tc_weights(fe.L, nv, width, height, fdt == LUDVIG_F32 ? 2 : 1, s->ws, p, s->dstat, &s->tc_chunk_cap,
+                      !ex.async, sf, &t));
+    if (chunk_cap) *chunk_cap = t.cap;
+    if (ex.async) {
+        LV_CUDA(cudaMemcpyAsync(&ex.diag->chunks, t.counter, sizeof(int), cudaMemcpyDeviceToDevice, sf));
+        LV_CUDA(cudaEventRecord(s->ev_front[p], sf));
+        LV_CUDA(cudaStreamWaitEvent(sa, s->ev_front[p], 0));
+    }
+    LV_TRY(tc_aggregate(t, nv, width, height, f, fdt, deff, padded ? pad_num : num, den, s->dstat,
+                        ex.async ? ex.ovf : nullptr, sa));
+    if (ex.async) LV_CUDA(cudaEventRecord(s->ev_agg[p], sa));
+    return LUDVIG_OK;
+}
+
+// Views per group: up to kMaxViews, with the per-group Gaussian scratch
+// (about 120 bytes per Gaussian and view) kept near 2 GB.
+int views_per_group(const ludvig_scene* s, int n_views) {
+    int vc = std::min<int>(kMaxViews, std::max<int>(1, n_views));
+    const int64_t per_view = std::max<int64_t>(1, s->n) * 120;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(vc, ((int64_t)2 << 30) / per_view));
+}
+
+// Groups of views [v0, v0 + nv) run checked on `st`; a group with more pairs
+// than one group may hold is split in halves.
+ludvig_status run_checked(ludvig_scene* s, const ludvig_camera* cams, int v0, int nv_total, int width, int height,
+                          const FeatSrc& src, float* num, float* den, float* pad_num, cudaStream_t st) {
+    int vc = views_per_group(s, nv_total);
+    const int end = v0 + nv_total;
+    Exec ex;
+    ex.st = st;
+    while (v0 < end) {
+        const int nv = std::min(vc, end - v0);
+        bool too_many = false;
+        LV_TRY(uplift_group(s, cams, v0, nv, width, height, src, num, den, pad_num, ex, &too_many));
+        if (too_many) {
+            if (nv == 1) {
+                set_error("view %d produces more than 2^31 tile/Gaussian pairs", v0);
+                return LUDVIG_ERR_UNSUPPORTED;
+            }
+            vc = std::max(1, nv / 2);
+            continue;
+        }
+        v0 += nv;
+    }
+    return LUDVIG_OK;
+}
+
+// Streams, events and status words of the asynchronous path (first use).
+ludvig_status ensure_async(ludvig_scene* s, int ngroups) {
+    if (!s->st_front) {
+        int lo = 0, hi = 0;
+        LV_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        LV_CUDA(cudaStreamCreateWithFlags(&s->st_front, cudaStreamNonBlocking));
+        // the aggregation streams the features: its blocks go first when SMs free up
+        LV_CUDA(cudaStreamCreateWithPriority(&s->st_agg, cudaStreamNonBlocking, hi));
+        LV_CUDA(cudaEventCreateWithFlags(&s->ev_call, cudaEventDisableTiming));
+        LV_CUDA(cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming));
+        for (int b = 0; b < 2; ++b) {
+            LV_CUDA(cudaEventCreateWithFlags(&s->ev_front[b], cudaEventDisableTiming));
+            LV_CUDA(cudaEventCreateWithFlags(&s->ev_agg[b], cudaEventDisableTiming));
+            LV_CUDA(cudaEventCreateWithFlags(&s->ev_join[b], cudaEventDisableTiming));
+        }
+    }
+    if (s->diag_cap < ngroups) {
+        LV_CUDA(cudaDeviceSynchronize());
+        if (s->ddiag) LV_CUDA(cudaFree(s->ddiag));
+        if (s->hdiag) LV_CUDA(cudaFreeHost(s->hdiag));
+        s->ddiag = nullptr;
+        s->hdiag = nullptr;
+        s->diag_cap = 0;
+        const int cap = std::max(ngroups, 16);
+        LV_CUDA(cudaMalloc(&s->ddiag, sizeof(GroupDiag) * (size_t)cap));
+        LV_CUDA(cudaMallocHost(&s->hdiag, sizeof(GroupDiag) * (size_t)cap));
+        s->diag_cap = cap;
+    }
+    return LUDVIG_OK;
+}
+
+// Reads the device status word after a checked call (synchronises `st`) and
+// clears it; returns its code.
+ludvig_status read_status(ludvig_scene* s, cudaStream_t st) {
+    LV_CUDA(cudaMemcpyAsync(s->hstat, s->dstat, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    LV_CUDA(cudaStreamSynchronize(st));
+    const int code = s->hstat[0];
+    if (code != 0) {
+        LV_CUDA(cudaMemsetAsync(s->dstat, 0, sizeof(int), st));
+        LV_CUDA(cudaStreamSynchronize(st));
+        set_error("tensor-core kernel reported status %d (a bounded wait expired)", code);
+        return (ludvig_status)code;
+    }
+    return LUDVIG_OK;
+}
+
+ludvig_status normalise(int64_t n, int d, const float* num, const float* den, float* out, float* beta,
+                        const int* skip, cudaStream_t st) {
+    StageScope scope(LUDVIG_STAGE_NORMALISE, st);
+    if (d >= 32) {
+        const int vec4 = (d % 4 == 0) && (reinterpret_cast<uintptr_t>(num) % 16 == 0) &&
+                         (reinterpret_cast<uintptr_t>(out) % 16 == 0);
+        k_normalise_rows<<<(unsigned)std::min<int64_t>(ceil_div(n, 8), 152 * 64), 256, 0, st>>>(num, den, out, beta,
+                                                                                               n, d, vec4, skip);
+    } else {
+        k_normalise<<<grid_for(n * d, 256), 256, 0, st>>>(num, den, out, beta, n, d, skip);
+    }
     LV_LAUNCH();
     return LUDVIG_OK;
 }
 
+// Waits for the scene's asynchronous call, if one is pending, and finishes it:
+// groups that did not fit the workspace are redone (checked, so the workspace
+// grows) and the normalisation they held back runs.  Returns the device status
+// word (bounded waits) of that call and clears it.
+ludvig_status resolve_pending(ludvig_scene* s) {
+    if (!s->pending.active) return LUDVIG_OK;
+    PendingCall pc = std::move(s->pending);
+    s->pending = PendingCall();
+    LV_CUDA(cudaEventSynchronize(s->ev_done));
+    const int code = s->hstat[0], ovf = s->hstat[1];
+    if (ovf) {
+        cudaStream_t st = s->st_front;
+        FeatSrc src;
+        src.kind = pc.src;
+        src.feats = pc.feats;
+        src.scales = pc.scales;
+        src.dtype = pc.dtype;
+        src.d = pc.d;
+        const bool padded = src_padded(src);
+        float* pad_num = nullptr;
+        if (padded) {
+            LV_TRY(s->ws.get("pad.num", (size_t)s->n * kPadD, &pad_num));
+            LV_CUDA(cudaMemsetAsync(pad_num, 0, sizeof(float) * (size_t)s->n * kPadD, st));
+        }
+        LV_CUDA(cudaMemsetAsync(s->dstat + 1, 0, sizeof(int), st));
+        for (size_t g = 0; g < pc.v0.size(); ++g) {
+            const GroupDiag& gd = s->hdiag[g];
+            const bool fits = gd.pairs <= (uint64_t)kMaxPairs &&
+                              round_up((int64_t)gd.pairs, kRadixTile) <= pc.pair_cap[g] &&
+                              gd.chunks <= pc.chunk_cap[g];
+            if (fits) continue;
+            LV_TRY(run_checked(s, pc.cams.data(), pc.v0[g], pc.nv[g], pc.width, pc.height, src, pc.num, pc.den,
+                               pad_num, st));
+        }
+        if (padded) {
+            k_add_columns<<<grid_for(s->n * pc.d, 256), 256, 0, st>>>(pad_num, s->n, pc.d, pc.num);
+            LV_LAUNCH();
+        }
+        if (pc.kind == 1) LV_TRY(normalise(s->n, pc.d, pc.num, pc.den, pc.num, nullptr, nullptr, st));
+        LV_TRY(read_status(s, st));
+    }
+    if (code != 0) {
+        LV_CUDA(cudaMemsetAsync(s->dstat, 0, sizeof(int), s->st_front));
+        LV_CUDA(cudaStreamSynchronize(s->st_front));
+        set_error("tensor-core kernel reported status %d (a bounded wait expired)", code);
+        return (ludvig_status)code;
+    }
+    return LUDVIG_OK;
+}
+
+// One uplift call: kind 0 adds into num/den, kind 1 zeroes them first and
+// normalises at the end (num becomes f, den stays beta).  Asynchronous unless
+// `checked`: see ludvig_sync.
+ludvig_status run_call(ludvig_scene* s, int kind, const FeatSrc& src, const ludvig_camera* cams, int n_views,
+                       int width, int height, float* num, float* den, cudaStream_t st, bool checked) {
+    LV_TRY(resolve_pending(s));
+    const int64_t n = s->n;
+    const int d = src.d;
+    const bool padded = src_padded(src);
+    float* pad_num = nullptr;
+    if (kind == 1) {
+        LV_CUDA(cudaMemsetAsync(num, 0, sizeof(float) * (size_t)n * d, st));
+        LV_CUDA(cudaMemsetAsync(den, 0, sizeof(float) * (size_t)n, st));
+    }
+    if (padded) {
+        LV_TRY(s->ws.get("pad.num", (size_t)n * kPadD, &pad_num));
+        LV_CUDA(cudaMemsetAsync(pad_num, 0, sizeof(float) * (size_t)n * kPadD, st));
+    }
+    const int vc = views_per_group(s, n_views);
+    const int ngroups = (int)ceil_div(std::max(n_views, 0), vc);
+    LV_TRY(ensure_async(s, ngroups));
+    const int fdt = src.kind == 2 ? LUDVIG_BF16 : src.dtype;
+    const bool tc = padded || use_tensor_cores(fdt, d);
+    int v0 = 0;
+    if (!checked && n_views > 0 && (s->pair_cap == 0 || (tc && s->tc_chunk_cap == 0))) {
+        // the workspace has not been sized yet: the first group runs checked and
+        // sizes it, with headroom for the other groups
+        const int nv = std::min(vc, n_views);
+        LV_TRY(run_checked(s, cams, 0, nv, width, height, src, num, den, pad_num, st));
+        s->pair_cap = round_up(s->pair_cap + s->pair_cap / 4, kRadixTile);
+        s->tc_chunk_cap += s->tc_chunk_cap / 4;
+        v0 = nv;
+    }
+    std::vector<int> gv0, gnv;
+    std::vector<int64_t> gpcap, gccap;
+    if (checked) {
+        LV_TRY(run_checked(s, cams, 0, n_views, width, height, src, num, den, pad_num, st));
+    } else if (v0 < n_views) {
+        cudaStream_t sf = s->st_front, sa = s->st_agg;
+        LV_CUDA(cudaMemsetAsync(s->dstat + 1, 0, sizeof(int), st));
+        LV_CUDA(cudaEventRecord(s->ev_call, st));
+        LV_CUDA(cudaStreamWaitEvent(sf, s->ev_call, 0));
+        LV_CUDA(cudaStreamWaitEvent(sa, s->ev_call, 0));
+        for (int g = 0; v0 < n_views; ++g) {
+            const int nv = std::min(vc, n_views - v0);
+            Exec ex;
+            ex.async = true;
+            ex.group = g;
+            ex.diag = s->ddiag + g;
+            ex.ovf = s->dstat + 1;
+            bool too_many = false;
+            int64_t pcap = 0, ccap = 0;
+            LV_TRY(uplift_group(s, cams, v0, nv, width, height, src, num, den, pad_num, ex, &too_many, &pcap,
+                                &ccap));
+            gv0.push_back(v0);
+            gnv.push_back(nv);
+            gpcap.push_back(pcap);
+            gccap.push_back(ccap);
+            v0 += nv;
+        }
+        LV_CUDA(cudaEventRecord(s->ev_join[0], sf));
+        LV_CUDA(cudaEventRecord(s->ev_join[1], sa));
+        LV_CUDA(cudaStreamWaitEvent(st, s->ev_join[0], 0));
+        LV_CUDA(cudaStreamWaitEvent(st, s->ev_join[1], 0));
+    }
+    const bool async = !gv0.empty();
+    if (padded) {
+        k_add_columns<<<grid_for(n * d, 256), 256, 0, st>>>(pad_num, n, d, num);
+        LV_LAUNCH();
+    }
+    if (kind == 1) LV_TRY(normalise(n, d, num, den, num, nullptr, async ? s->dstat + 1 : nullptr, st));
+    if (!async) return read_status(s, st);
+    LV_CUDA(cudaMemcpyAsync(s->hstat, s->dstat, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    LV_CUDA(cudaMemcpyAsync(s->hdiag, s->ddiag, sizeof(GroupDiag) * gv0.size(), cudaMemcpyDeviceToHost, st));
+    LV_CUDA(cudaEventRecord(s->ev_done, st));
+    PendingCall& pc = s->pending;
+    pc.kind = kind;
+    pc.src = src.kind;
+    pc.cams.assign(cams, cams + n_views);
+    pc.n_views = n_views;
+    pc.width = width;
+    pc.height = height;
+    pc.dtype = src.dtype;
+    pc.d = d;
+    pc.feats = src.feats;
+    pc.scales = src.scales;
+    pc.num = num;
+    pc.den = den;
+    pc.v0 = std::move(gv0);
+    pc.nv = std::move(gnv);
+    pc.pair_cap = std::move(gpcap);
+    pc.chunk_cap = std::move(gccap);
+    pc.active = true;
+    return LUDVIG_OK;
+}
+
+ludvig_status check_views(const ludvig_camera* cams, int32_t n_views, int32_t width, int32_t height) {
+    LV_ARG(n_views >= 0, "n_views must be >= 0");
+    LV_ARG(n_views == 0 || cams != nullptr, "cams is NULL");
+    LV_ARG(width > 0 && height > 0, "width and height must be positive");
+    LV_ARG(width <= 16 * 4095 && height <= 16 * 4095, "image too large");
+    for (int v = 0; v < n_views; ++v) {
+        LV_ARG(cams[v].fx > 0.f && cams[v].fy > 0.f, "camera %d: focal lengths must be positive", v);
+    }
+    return LUDVIG_OK;
+}
+
+// Rendering of one group (Eq. 4): stages 1-5, then W f per tile (checked).
+ludvig_status render_group(ludvig_scene* s, const ludvig_camera* cams, int nv, int width, int height,
+                           const float* f, int d, float* out, cudaStream_t st, bool* too_many) {
+    FrontEnd fe;
+    LV_TRY(front_end(s, cams, nv, width, height, true, nullptr, nullptr, st, &fe));
+    *too_many = fe.too_many;
+    if (fe.too_many) return LUDVIG_OK;
+    StageScope scope(LUDVIG_STAGE_RENDER, st);
+    if (use_tensor_cores(LUDVIG_F32, d)) {
+        TileWeights t;
+        LV_TRY(tc_weights(fe.L, nv, width, height, 2, s->ws, 0, s->dstat, &s->tc_chunk_cap, true, st, &t));
+        return tc_render(t, s->ws, nv, width, height, f, d, out, s->dstat, st);
+    }
+    const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
+    PairRec* pairs;
+    LV_TRY(s->ws.get("up.pairs", (size_t)fe.cap, &pairs));
+    k_pair_records<<<kPairGrid, 256, 0, st>>>(fe.spk, fe.L.rank, fe.np, (uint64_t)fe.cap, TX * TY, TX, fe.L.npad,
+                                              fe.L.srec, pairs);
+    LV_LAUNCH();
+    RenderArgs r;
+    r.pairs = pairs;
+    r.ranges = fe.L.ranges;
+    r.ntiles = TX * TY;
+    r.TX = TX;
+    r.width = width;
+    r.height = height;
+    r.f = f;
+    r.d = d;
+    r.out = out;
+    const int64_t nitems = (int64_t)nv * TX * TY;
+    if (d <= 4) return launch_render_cc<4>(r, nitems, st);
+    if (d <= 8) return launch_render_cc<8>(r, nitems, st);
+    if (d <= 16) return launch_render_cc<16>(r, nitems, st);
+    return launch_render_cc<32>(r, nitems, st);
+}
+
+// First use: the status words of a scene.
+ludvig_status ensure_status(ludvig_scene* s) {
+    if (s->dstat) return LUDVIG_OK;
+    LV_CUDA(cudaMalloc(&s->dstat, 2 * sizeof(int)));
+    LV_CUDA(cudaMemset(s->dstat, 0, 2 * sizeof(int)));
+    LV_CUDA(cudaMallocHost(&s->hstat, 2 * sizeof(int)));
+    s->hstat[0] = s->hstat[1] = 0;
+    return LUDVIG_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- scene
+ludvig_status scene_init(ludvig_scene* s, const float* means, const float* scales, const float* quats,
+                         const float* opac, int scales_are_linear, cudaStream_t st) {
+    if (s->n == 0) return LUDVIG_OK;
+    LV_TRY(ensure_status(s));
+    k_scene_init<<<grid_for(s->n, 256), 256, 0, st>>>(means, scales, quats, opac, s->n, scales_are_linear ? 0 : 1,
+                                                      s->geo, s->cov_a, s->cov_b, s->means);
+    LV_LAUNCH();
+    return LUDVIG_OK;
+}
+
+// Releases the asynchronous path's streams, events and status words.
+void scene_release_async(ludvig_scene* s) {
+    if (s->st_front) cudaStreamDestroy(s->st_front);
+    if (s->st_agg) cudaStreamDestroy(s->st_agg);
+    cudaEvent_t* evs[] = {&s->ev_call, &s->ev_done, &s->ev_front[0], &s->ev_front[1], &s->ev_agg[0], &s->ev_agg[1],
+                          &s->ev_join[0], &s->ev_join[1]};
+    for (cudaEvent_t* e : evs)
+        if (*e) cudaEventDestroy(*e);
+    if (s->dstat) cudaFree(s->dstat);
+    if (s->hstat) cudaFreeHost(s->hstat);
+    if (s->ddiag) cudaFree(s->ddiag);
+    if (s->hdiag) cudaFreeHost(s->hdiag);
+}
+
+// Finishes a scene's pending asynchronous call (ludvig_sync).
+ludvig_status scene_sync(ludvig_scene* s) { return resolve_pending(s); }
+
 }  // namespace ludvig
 
 using namespace ludvig;
+
+extern "C" ludvig_status ludvig_sync(ludvig_scene_t scene) {
+    LV_ARG(scene != nullptr, "scene is NULL");
+    return scene_sync(scene);
+}
 
 extern "C" ludvig_status ludvig_uplift_accumulate(ludvig_scene_t scene, const ludvig_camera* cams,
                                                   int32_t n_views, int32_t width, int32_t height,
@@ -1030,11 +1393,13 @@ extern "C" ludvig_status ludvig_uplift_accumulate(ludvig_scene_t scene, const lu
     LV_ARG(n_views == 0 || feats != nullptr, "feats is NULL");
     if (d % 4 == 0) LV_ARG(((uintptr_t)num & 15) == 0, "num must be 16-byte aligned when d %% 4 == 0");
     if (scene->n == 0 || n_views == 0) return LUDVIG_OK;
-    if (use_padded(dtype, d))
-        return accumulate_padded(scene, cams, n_views, width, height, feats, dtype, d, num, den,
-                                 static_cast<cudaStream_t>(stream));
-    return accumulate(scene, cams, n_views, width, height, feats, dtype, d, num, den,
-                      static_cast<cudaStream_t>(stream), nullptr);
+    LV_TRY(ensure_status(scene));
+    FeatSrc src;
+    src.kind = use_padded(dtype, d) ? 1 : 0;
+    src.feats = feats;
+    src.dtype = dtype;
+    src.d = d;
+    return run_call(scene, 0, src, cams, n_views, width, height, num, den, static_cast<cudaStream_t>(stream), false);
 }
 
 extern "C" ludvig_status ludvig_uplift_finalize(int64_t n, int32_t d, const float* num, const float* den,
@@ -1042,18 +1407,7 @@ extern "C" ludvig_status ludvig_uplift_finalize(int64_t n, int32_t d, const floa
     LV_ARG(n >= 0 && d >= 1, "bad sizes");
     if (n == 0) return LUDVIG_OK;
     LV_ARG(num != nullptr && den != nullptr && out != nullptr, "NULL buffer");
-    StageScope scope(LUDVIG_STAGE_NORMALISE, static_cast<cudaStream_t>(stream));
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (d >= 32) {
-        const int vec4 = (d % 4 == 0) && (reinterpret_cast<uintptr_t>(num) % 16 == 0) &&
-                         (reinterpret_cast<uintptr_t>(out) % 16 == 0);
-        k_normalise_rows<<<(unsigned)std::min<int64_t>(ceil_div(n, 8), 152 * 64), 256, 0, st>>>(num, den, out, beta,
-                                                                                               n, d, vec4);
-    } else {
-        k_normalise<<<grid_for(n * d, 256), 256, 0, st>>>(num, den, out, beta, n, d);
-    }
-    LV_LAUNCH();
-    return LUDVIG_OK;
+    return normalise(n, d, num, den, out, beta, nullptr, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" ludvig_status ludvig_uplift(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
@@ -1063,15 +1417,21 @@ extern "C" ludvig_status ludvig_uplift(ludvig_scene_t scene, const ludvig_camera
     LV_ARG(out != nullptr || scene->n == 0, "out is NULL");
     LV_ARG(d >= 1 && d <= 65536, "d must be in [1, 65536]");
     LV_TRY(check_views(cams, n_views, width, height));
+    LV_ARG(dtype == LUDVIG_F32 || dtype == LUDVIG_BF16, "unknown dtype %d", dtype);
+    LV_ARG(n_views == 0 || feats != nullptr, "feats is NULL");
+    if (d % 4 == 0) LV_ARG(((uintptr_t)out & 15) == 0, "out must be 16-byte aligned when d %% 4 == 0");
     const int64_t n = scene->n;
     if (n == 0) return LUDVIG_OK;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LV_TRY(ensure_status(scene));
+    LV_TRY(resolve_pending(scene));
     float* den = beta;
     if (!den) LV_TRY(scene->ws.get("uplift.den", (size_t)n, &den));
-    LV_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)n * d, st));
-    LV_CUDA(cudaMemsetAsync(den, 0, sizeof(float) * (size_t)n, st));
-    LV_TRY(ludvig_uplift_accumulate(scene, cams, n_views, width, height, feats, dtype, d, out, den, stream));
-    return ludvig_uplift_finalize(n, d, out, den, out, nullptr, stream);
+    FeatSrc src;
+    src.kind = use_padded(dtype, d) ? 1 : 0;
+    src.feats = feats;
+    src.dtype = dtype;
+    src.d = d;
+    return run_call(scene, 1, src, cams, n_views, width, height, out, den, static_cast<cudaStream_t>(stream), false);
 }
 
 extern "C" ludvig_status ludvig_uplift_fp8(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
@@ -1086,28 +1446,17 @@ extern "C" ludvig_status ludvig_uplift_fp8(ludvig_scene_t scene, const ludvig_ca
     if (d % 4 == 0) LV_ARG(((uintptr_t)out & 15) == 0, "out must be 16-byte aligned when d %% 4 == 0");
     const int64_t n = scene->n;
     if (n == 0) return LUDVIG_OK;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LV_TRY(ensure_status(scene));
+    LV_TRY(resolve_pending(scene));
     float* den = beta;
     if (!den) LV_TRY(scene->ws.get("uplift.den", (size_t)n, &den));
-    LV_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)n * d, st));
-    LV_CUDA(cudaMemsetAsync(den, 0, sizeof(float) * (size_t)n, st));
-    const int64_t view_elems = (int64_t)width * height * d;
-    const int vc = std::min<int>(kMaxViews, std::max(1, n_views));
-    __nv_bfloat16* fb;
-    LV_TRY(scene->ws.get("fp8.bf16", (size_t)vc * view_elems, &fb));
-    for (int v0 = 0; v0 < n_views; v0 += vc) {
-        const int nv = std::min(vc, n_views - v0);
-        const int64_t total = (int64_t)nv * view_elems;
-        // groups start a multiple of 16 views in: the codes stay 4-byte aligned
-        k_dequant_e4m3<<<grid_for(ceil_div(total, 4), 256), 256, 0, st>>>(q + (size_t)v0 * view_elems, scales + v0,
-                                                                         view_elems, total, fb);
-        LV_LAUNCH();
-        if (use_padded(LUDVIG_BF16, d))
-            LV_TRY(accumulate_padded(scene, cams + v0, nv, width, height, fb, LUDVIG_BF16, d, out, den, st));
-        else
-            LV_TRY(accumulate(scene, cams + v0, nv, width, height, fb, LUDVIG_BF16, d, out, den, st, nullptr));
-    }
-    return ludvig_uplift_finalize(n, d, out, den, out, nullptr, stream);
+    FeatSrc src;
+    src.kind = 2;
+    src.feats = q;
+    src.scales = scales;
+    src.dtype = LUDVIG_BF16;
+    src.d = d;
+    return run_call(scene, 1, src, cams, n_views, width, height, out, den, static_cast<cudaStream_t>(stream), false);
 }
 
 extern "C" ludvig_status ludvig_render(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
@@ -1127,9 +1476,26 @@ extern "C" ludvig_status ludvig_render(ludvig_scene_t scene, const ludvig_camera
     if (use_tensor_cores(LUDVIG_F32, d)) {
         LV_ARG(((uintptr_t)f & 15) == 0, "f must be 16-byte aligned");
     }
-    const RenderJob rj{f, out};
-    return accumulate(scene, cams, n_views, width, height, nullptr, LUDVIG_F32, d, nullptr, nullptr, st, nullptr,
-                      &rj);
+    LV_TRY(ensure_status(scene));
+    LV_TRY(resolve_pending(scene));
+    const int64_t view_elems = (int64_t)width * height * d;
+    int vc = views_per_group(scene, n_views);
+    int v0 = 0;
+    while (v0 < n_views) {
+        const int nv = std::min(vc, n_views - v0);
+        bool too_many = false;
+        LV_TRY(render_group(scene, cams + v0, nv, width, height, f, d, out + (size_t)v0 * view_elems, st, &too_many));
+        if (too_many) {
+            if (nv == 1) {
+                set_error("view %d produces more than 2^31 tile/Gaussian pairs", v0);
+                return LUDVIG_ERR_UNSUPPORTED;
+            }
+            vc = std::max(1, nv / 2);
+            continue;
+        }
+        v0 += nv;
+    }
+    return read_status(scene, st);
 }
 
 extern "C" ludvig_status ludvig_uplift_host(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
@@ -1143,6 +1509,8 @@ extern "C" ludvig_status ludvig_uplift_host(ludvig_scene_t scene, const ludvig_c
     LV_TRY(check_views(cams, n_views, width, height));
     const int64_t n = scene->n;
     if (n == 0) return LUDVIG_OK;
+    LV_TRY(ensure_status(scene));
+    LV_TRY(resolve_pending(scene));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (!scene->copy_stream) {
         LV_CUDA(cudaStreamCreateWithFlags(&scene->copy_stream, cudaStreamNonBlocking));
@@ -1164,6 +1532,15 @@ extern "C" ludvig_status ludvig_uplift_host(ludvig_scene_t scene, const ludvig_c
     LV_TRY(scene->ws.get("host.den", (size_t)n, &den));
     LV_CUDA(cudaMemsetAsync(num, 0, sizeof(float) * (size_t)n * d, st));
     LV_CUDA(cudaMemsetAsync(den, 0, sizeof(float) * (size_t)n, st));
+    FeatSrc src;
+    src.kind = use_padded(dtype, d) ? 1 : 0;
+    src.dtype = dtype;
+    src.d = d;
+    float* pad_num = nullptr;
+    if (src.kind == 1) {
+        LV_TRY(scene->ws.get("pad.num", (size_t)n * kPadD, &pad_num));
+        LV_CUDA(cudaMemsetAsync(pad_num, 0, sizeof(float) * (size_t)n * kPadD, st));
+    }
     // both buffers start free once the zeroing above is ordered
     for (int b = 0; b < 2; ++b) LV_CUDA(cudaEventRecord(scene->ev_free[b], st));
     const int nchunks = (int)ceil_div(n_views, vc);
@@ -1180,16 +1557,33 @@ extern "C" ludvig_status ludvig_uplift_host(ludvig_scene_t scene, const ludvig_c
         const int b = c & 1, v0 = c * vc, nv = std::min(vc, n_views - v0);
         if (c + 1 < nchunks) LV_TRY(upload(c + 1));   // overlaps the compute of chunk c
         LV_CUDA(cudaStreamWaitEvent(st, scene->ev_ready[b], 0));
-        if (use_padded(dtype, d))
-            LV_TRY(accumulate_padded(scene, cams + v0, nv, width, height, fbuf[b], dtype, d, num, den, st));
-        else
-            LV_TRY(accumulate(scene, cams + v0, nv, width, height, fbuf[b], dtype, d, num, den, st, nullptr));
+        src.feats = fbuf[b];
+        LV_TRY(run_checked(scene, cams + v0, 0, nv, width, height, src, num, den, pad_num, st));
         LV_CUDA(cudaEventRecord(scene->ev_free[b], st));
     }
-    LV_TRY(ludvig_uplift_finalize(n, d, num, den, num, nullptr, stream));
+    if (pad_num) {
+        k_add_columns<<<grid_for(n * d, 256), 256, 0, st>>>(pad_num, n, d, num);
+        LV_LAUNCH();
+    }
+    LV_TRY(normalise(n, d, num, den, num, nullptr, nullptr, st));
     LV_CUDA(cudaMemcpyAsync(out, num, sizeof(float) * (size_t)n * d, cudaMemcpyDeviceToHost, st));
     if (beta) LV_CUDA(cudaMemcpyAsync(beta, den, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, st));
-    LV_CUDA(cudaStreamSynchronize(st));
+    return read_status(scene, st);
+}
+
+extern "C" ludvig_status ludvig_debug_scene_timeout(ludvig_scene_t scene, int64_t cycles, void* stream) {
+    LV_ARG(scene != nullptr, "scene is NULL");
+    LV_ARG(cycles >= 0 && cycles <= 4000000000ll, "cycles must be in [0, 4e9]");
+    LV_TRY(ensure_status(scene));
+    LV_TRY(resolve_pending(scene));
+    LV_TRY(ensure_async(scene, 1));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    LV_TRY(tc_wait_into_status(cycles, scene->dstat, st));
+    LV_CUDA(cudaMemcpyAsync(scene->hstat, scene->dstat, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    LV_CUDA(cudaEventRecord(scene->ev_done, st));
+    scene->pending = PendingCall();
+    scene->pending.kind = 2;   // nothing to redo: the status alone
+    scene->pending.active = true;
     return LUDVIG_OK;
 }
 
@@ -1199,13 +1593,14 @@ extern "C" ludvig_status ludvig_debug_project(ludvig_scene_t scene, const ludvig
     LV_ARG(scene != nullptr && rec != nullptr && rect != nullptr, "NULL argument");
     LV_TRY(check_views(cam, 1, width, height));
     if (scene->n == 0) return LUDVIG_OK;
+    LV_TRY(ensure_status(scene));
+    LV_TRY(resolve_pending(scene));
     ChunkDebug dbg;
     dbg.rec = rec;
     dbg.rect = rect;
     dbg.stop_after_project = true;
-    bool tm;
-    return run_chunk(scene, cam, 1, width, height, nullptr, LUDVIG_F32, 1, nullptr, nullptr,
-                     static_cast<cudaStream_t>(stream), &dbg, &tm);
+    FrontEnd fe;
+    return front_end(scene, cam, 1, width, height, true, nullptr, &dbg, static_cast<cudaStream_t>(stream), &fe);
 }
 
 extern "C" ludvig_status ludvig_debug_tile_lists(ludvig_scene_t scene, const ludvig_camera* cam,
@@ -1221,6 +1616,8 @@ extern "C" ludvig_status ludvig_debug_tile_lists(ludvig_scene_t scene, const lud
         *total = 0;
         return LUDVIG_OK;
     }
+    LV_TRY(ensure_status(scene));
+    LV_TRY(resolve_pending(scene));
     ChunkDebug dbg;
     dbg.ranges64 = ranges;
     dbg.list = list;
@@ -1228,9 +1625,9 @@ extern "C" ludvig_status ludvig_debug_tile_lists(ludvig_scene_t scene, const lud
     dbg.list_total = total;
     dbg.stop_after_sort = true;
     dbg.unpruned = (pruned == 0);
-    bool tm;
-    LV_TRY(run_chunk(scene, cam, 1, width, height, nullptr, LUDVIG_F32, 1, nullptr, nullptr, st, &dbg, &tm));
-    if (tm) {
+    FrontEnd fe;
+    LV_TRY(front_end(scene, cam, 1, width, height, true, nullptr, &dbg, st, &fe));
+    if (fe.too_many) {
         set_error("too many pairs");
         return LUDVIG_ERR_UNSUPPORTED;
     }
@@ -1248,6 +1645,8 @@ extern "C" ludvig_status ludvig_debug_transmittance(ludvig_scene_t scene, const 
     k_debug_fill<<<grid_for(npx, 256), 256, 0, st>>>(t_final, n_contrib, npx);
     LV_LAUNCH();
     if (scene->n == 0) return LUDVIG_OK;
+    LV_TRY(ensure_status(scene));
+    LV_TRY(resolve_pending(scene));
     float* num;
     float* den;
     LV_TRY(scene->ws.get("dbg.num", (size_t)scene->n, &num));
@@ -1258,6 +1657,11 @@ extern "C" ludvig_status ludvig_debug_transmittance(ludvig_scene_t scene, const 
     ChunkDebug dbg;
     dbg.t_final = t_final;
     dbg.n_contrib = n_contrib;
-    bool tm;
-    return run_chunk(scene, cam, 1, width, height, fz, LUDVIG_F32, 1, num, den, st, &dbg, &tm);
+    FrontEnd fe;
+    LV_TRY(front_end(scene, cam, 1, width, height, true, nullptr, nullptr, st, &fe));
+    if (fe.too_many) {
+        set_error("too many pairs");
+        return LUDVIG_ERR_UNSUPPORTED;
+    }
+    return composite_cc(scene, fe, 1, width, height, fz, LUDVIG_F32, 1, num, den, &dbg, st);
 }

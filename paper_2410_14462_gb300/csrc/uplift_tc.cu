@@ -15,8 +15,10 @@
 //  k_weights (CUDA cores, one CTA of 8 warps per (view, tile), several CTAs
 //  per SM): walks the tile's depth-ordered list in batches of 32 Gaussians
 //  (float32 rules of Eq. 1: alpha, 1/255 skip, 1e-4 stop), one 8x4 pixel block
-//  per warp, the list records streaming in by bulk copies kRing - 1 batches
-//  ahead.  The batch's weights go to 32 staging rows in shared memory; the
+//  per warp.  Warp 0 gathers the batches' projected records (from the
+//  depth-ordered record array, by the ranks the list holds) with cp.async
+//  kRing - 1 batches ahead, and computes each entry's 8x4 block mask once its
+//  record has landed; only the batches the walk reaches are gathered.  The batch's weights go to 32 staging rows in shared memory; the
 //  Gaussians with a non-zero weight somewhere in the tile are then appended,
 //  as dense bfloat16 rows of 256 pixels, to the tile's "chunks" of 128 rows in
 //  global memory (chunk ids from an atomic counter; row count, Gaussian ids
@@ -54,6 +56,7 @@
 #include "common.cuh"
 #include "spec.cuh"
 #include "tc_ptx.cuh"
+#include "uplift_int.cuh"
 
 namespace ludvig {
 
@@ -80,7 +83,9 @@ constexpr uint32_t idesc_n(uint32_t n) {
 // ------------------------------------------------------------ weights
 
 struct WeightsArgs {
-    const PairRec* pairs;   // list records in list order
+    const uint32_t* rank;   // list entries: depth rank within the view
+    const PairRec* srec;    // [nv, npad] projected records in depth order
+    int64_t npad;
     const uint2* ranges;
     int ntiles, TX, width, height;
     uint8_t* wg1;           // [cap][128][256] bfloat16: W (NT = 1) or W1
@@ -92,18 +97,15 @@ struct WeightsArgs {
     int* chunk_counter;
     int cap;
     float* chunk_den;       // [cap][128][NT]: each row's sum of its weight term (rewritten on a re-run)
-    int* status;
     int count_den;          // chunk_den holds each row's count of non-zero weights (term 0; term 1: 0)
 };
 
 template <int NT>
 struct WeightsSmem {
-    uint64_t rec_full[kRing];
     alignas(16) PairRec rec[kRing][kTcBatch];
     alignas(16) uint8_t stage[NT][kTcBatch * kRowBytes];   // [term][j][256 pixels]
     uint32_t rowmask[2];
     int cur_chunk, cur_start, next_chunk;
-    int abort_flag;
 };
 
 // A weight row's contribution to den, from its 256 bfloat16 values (8 per
@@ -149,32 +151,42 @@ __global__ void __launch_bounds__(256, 5) k_weights(WeightsArgs a) {
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
 
     if (tid == 0) {
-        for (int s = 0; s < kRing; ++s) mbar_init(&S.rec_full[s], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         S.rowmask[0] = 0u;
         S.rowmask[1] = 0u;
         S.cur_chunk = -1;
         S.cur_start = 0;
         S.next_chunk = -1;
-        S.abort_flag = 0;
     }
     for (int e = tid; e < (int)(NT * kTcBatch * kRowBytes / 16); e += 256)
         reinterpret_cast<uint4*>(&S.stage[0][0])[e] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
 
-    // batch k of the list goes to ring slot k % kRing
-    uint32_t rissue = 0, rcons = 0;
-    auto issue_records = [&](uint32_t k) {
-        if (tid == 0) {
-            const uint32_t s = k % kRing;
-            const uint32_t b0 = range.x + k * kTcBatch;
-            const uint32_t bytes = min((uint32_t)kTcBatch, range.y - b0) * (uint32_t)sizeof(PairRec);
-            mbar_expect_tx(&S.rec_full[s], bytes);
-            bulk_load(S.rec[s], a.pairs + b0, bytes, &S.rec_full[s]);
-        }
-        ++rissue;
+    // batch k of the list goes to ring slot k % kRing.  Warp 0, lane j gathers
+    // entry j of a batch (two 16-byte cp.async of its 32-byte record) and
+    // commits one cp.async group per batch, empty past the list's end, so
+    // that "at most kRing - 2 groups pending" always means "batch k landed".
+    // The rank of the batch after next is loaded one iteration early, so the
+    // gather does not wait on it.
+    const PairRec* vrec = a.srec + (int64_t)v * a.npad;
+    auto rank_of = [&](uint32_t k) -> uint32_t {
+        const uint32_t e = range.x + k * kTcBatch + (uint32_t)lane;
+        return (k < nb && e < range.y) ? a.rank[e] : 0xffffffffu;
     };
-    for (uint32_t k = 0; k < nb && k + 1 < (uint32_t)kRing; ++k) issue_records(k);
+    auto issue_records = [&](uint32_t k, uint32_t rk) {
+        if (warp == 0) {
+            if (rk != 0xffffffffu) {
+                PairRec* dst = &S.rec[k % kRing][lane];
+                cp_async_16(dst, vrec + rk);
+                cp_async_16(reinterpret_cast<uint8_t*>(dst) + 16, reinterpret_cast<const uint8_t*>(vrec + rk) + 16);
+            }
+            cp_async_commit();
+        }
+    };
+    uint32_t next_rank = 0xffffffffu;   // warp 0: rank of batch k + kRing - 1 at iteration k
+    if (warp == 0) {
+        for (uint32_t k = 0; k + 1 < (uint32_t)kRing; ++k) issue_records(k, rank_of(k));
+        next_rank = rank_of(kRing - 1);
+    }
 
     float T = 1.0f;
     bool done = !(px < a.width && py < a.height);
@@ -182,14 +194,20 @@ __global__ void __launch_bounds__(256, 5) k_weights(WeightsArgs a) {
     int buf = 0;
     for (uint32_t k = 0; k < nb; ++k, buf ^= 1) {
         const uint32_t slot = k % kRing;
-        if (!mbar_wait(&S.rec_full[slot], (k / kRing) & 1u)) {
-            S.abort_flag = 1;
-            atomicExch(a.status, (int)LUDVIG_ERR_TIMEOUT);
+        if (warp == 0) {
+            // this lane's record of batch k has landed: its block mask
+            cp_async_wait<kRing - 2>();
+            if (range.x + k * kTcBatch + (uint32_t)lane < range.y) {
+                PairRec& r = S.rec[slot][lane];
+                r.mask = block_mask(reach_prep(r.ca, r.cb, r.cc, r.op), r.mx, r.my, r.ca, r.cb, r.cc, tx, ty);
+            }
         }
-        ++rcons;
-        if (__syncthreads_count(!done) == 0 || S.abort_flag) break;
+        if (__syncthreads_count(!done) == 0) break;
         // every thread is past batch k-1: its slot takes batch k + kRing - 1
-        if (k + kRing - 1 < nb) issue_records(k + kRing - 1);
+        if (warp == 0) {
+            issue_records(k + kRing - 1, next_rank);
+            next_rank = rank_of(k + kRing);
+        }
         if (tid == 0) {
             // rows [nrows, nrows + 32) must have chunks; a chunk filled to
             // exactly 128 rows may not have its successor yet
@@ -321,9 +339,8 @@ __global__ void __launch_bounds__(256, 5) k_weights(WeightsArgs a) {
         nrows += nnew;
         // no barrier here: the next batch's counting barrier orders these stores
     }
-    // batches issued past an early stop still land: wait for them (bounded)
-    for (uint32_t k = rcons; k < rissue; ++k)
-        if (!mbar_wait(&S.rec_full[k % kRing], (k / kRing) & 1u)) break;
+    // gathers issued past an early stop still land before the CTA exits
+    if (warp == 0) cp_async_wait<0>();
     __syncthreads();
     if (tid == 0) {
         const int cur = S.cur_chunk, cstart = S.cur_start, nxt = S.next_chunk;
@@ -350,7 +367,9 @@ struct AggArgs {
     float* num;
     float* den;
     int* status;
-    int store_mode;   // debug GEMM: num[gid * d + c] = accumulator (no den)
+    int store_mode;          // debug GEMM: num[gid * d + c] = accumulator (no den)
+    const int* chunk_count;  // chunks the weights pass used (may be null: known to fit)
+    int* ovf;                // set to 2 when they exceeded cap (the launch then adds nothing)
 };
 
 // Feature units (16 KB): 128 channels of 64 pixels (NT = 1: one K atom, two
@@ -463,6 +482,12 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
     k_aggregate_tc(AggArgs a, const __grid_constant__ CUtensorMap wmap1, const __grid_constant__ CUtensorMap wmap2,
                    const __grid_constant__ CUtensorMap fmap) {
     using Sm = AggSmem<NT>;
+    // a weights pass that ran out of chunks left incomplete rows: the group is
+    // redone once the workspace has grown, so nothing of it may be added now
+    if (a.chunk_count && *a.chunk_count > a.cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0 && a.ovf) atomicOr(a.ovf, 2);
+        return;
+    }
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const uint32_t pad = (1024u - (saddr(smem_raw) & 1023u)) & 1023u;
     Sm& S = *reinterpret_cast<Sm*>(smem_raw + pad);
@@ -502,6 +527,10 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
             uint32_t wc = 0, fc = 0, qc = 0;
             bool ok = true;
             ChunkWalk walk;
+            // weight rows are read once and a tile's features by its chunks only:
+            // first out of L2 after their last use, so that the num lines the
+            // epilogue adds into stay there between tiles
+            const uint64_t stream_policy = policy_evict_first(), keep_policy = policy_evict_normal();
             for (;;) {
                 const int c = (ok && !*abort_flag) ? walk.next(a) : -1;
                 // publish the chunk (or the end) to the other roles
@@ -516,6 +545,9 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
                 const int item = walk.item;
                 const int v = item / a.ntiles, tile = item - v * a.ntiles;
                 const int tx = tile % a.TX, ty = tile / a.TX;
+                const int nx = a.chunk_next[c];
+                const bool tile_last = nx < 0 || nx >= a.cap || a.chunk_rows[nx] == 0;
+                const uint64_t fpolicy = tile_last ? stream_policy : keep_policy;
                 for (int ka = 0; ka < 4 && ok; ++ka) {
                     const uint32_t ws = wc % Sm::kWA;
                     if (wc >= (uint32_t)Sm::kWA &&
@@ -528,10 +560,11 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
                     const int nrb = (walk.rows + 31) >> 5;
                     mbar_expect_tx(&S.w_full[ws], (uint32_t)(NT * nrb) * 4096u);
                     for (int rb = 0; rb < nrb; ++rb) {
-                        tma_load_2d(S.W[ws][0] + 4096 * rb, &wmap1, &S.w_full[ws], ka * 64, c * kCRows + 32 * rb);
+                        tma_load_2d_hint(S.W[ws][0] + 4096 * rb, &wmap1, &S.w_full[ws], ka * 64, c * kCRows + 32 * rb,
+                                         stream_policy);
                         if (NT == 2)
-                            tma_load_2d(S.W[ws][NT - 1] + 4096 * rb, &wmap2, &S.w_full[ws], ka * 64,
-                                        c * kCRows + 32 * rb);
+                            tma_load_2d_hint(S.W[ws][NT - 1] + 4096 * rb, &wmap2, &S.w_full[ws], ka * 64,
+                                             c * kCRows + 32 * rb, stream_policy);
                     }
                     ++wc;
                     for (int un = 0; un < U && ok; ++un)
@@ -548,8 +581,9 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
                         constexpr int kBoxes = 2 * NT, kBoxCh = 64 / NT;
 #pragma unroll
                         for (int j = 0; j < kBoxes; ++j)
-                            tma_load_4d(S.F[s] + Sm::kBoxBytes * j, &fmap, &S.f_full[s], 128 * un + kBoxCh * j,
-                                        tx * kTile, ty * kTile + 4 * ka + (Sm::kUnitPx / 16) * hf, v);
+                            tma_load_4d_hint(S.F[s] + Sm::kBoxBytes * j, &fmap, &S.f_full[s], 128 * un + kBoxCh * j,
+                                             tx * kTile, ty * kTile + 4 * ka + (Sm::kUnitPx / 16) * hf, v,
+                                             fpolicy);
                         ++fc;
                     }
                 }
@@ -690,6 +724,7 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
         const int r = 32 * q + lane;
         const int d = a.d;
         float* st = &S.rows[warp - 2][lane * Sm::kPitch];
+        const uint64_t num_policy = policy_evict_last();   // num lines recur in nearby tiles
         uint32_t ub = 0, qc = 0;
         bool ok = true;
         for (;;) {
@@ -747,7 +782,8 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
                         }
                         fence_proxy_async();   // generic writes, read by the bulk copy
                         if (valid && lim > 0) {
-                            bulk_reduce_add_f32(a.num + (int64_t)g * d + 64 * b, st, (uint32_t)lim * 4u);
+                            bulk_reduce_add_f32_hint(a.num + (int64_t)g * d + 64 * b, st, (uint32_t)lim * 4u,
+                                                     num_policy);
                             bulk_commit();
                         }
                     }
@@ -1266,49 +1302,56 @@ ludvig_status sm_count(int* sms) {
     return LUDVIG_OK;
 }
 
-// The weight rows of every (view, tile) of a chunk of views, in chunks of 128
-// (k_weights), with the chunk capacity grown and the pass re-run when it
-// overflows.  Synchronises `st` (reads back the chunk count and status).
-struct TileWeights {
-    int64_t cap = 0;
-    int count = 0;
-    uint8_t *wg1 = nullptr, *wg2 = nullptr;
-    uint32_t* cgid = nullptr;
-    int *crows = nullptr, *cnext = nullptr, *ifirst = nullptr;
-    float* cden = nullptr;
-};
+}  // namespace
 
-ludvig_status tile_weights(const PairRec* pairs, const uint2* ranges, int nv, int width, int height, int NT,
-                           Arena& ws, int* status, int64_t* chunk_cap, cudaStream_t st, TileWeights* tw) {
+// Tensor-core aggregation applies to d in [32, 512] with d % 8 == 0 (16-byte
+// rows for TMA); bfloat16 features always, float32 unless disabled.
+bool tc_supported(int dtype, int d) {
+    return (dtype == LUDVIG_BF16 || dtype == LUDVIG_F32) && d >= 32 && d <= 512 && d % 8 == 0;
+}
+
+ludvig_status tc_weights(const GroupLists& L, int nv, int width, int height, int NT, Arena& ws, int parity,
+                         int* status, int64_t* chunk_cap, bool checked, cudaStream_t st, TileWeights* tw) {
+    // workspace names of the two buffer sets
+    static const char* const kW1[2] = {"tc.w1.0", "tc.w1.1"};
+    static const char* const kW2[2] = {"tc.w2.0", "tc.w2.1"};
+    static const char* const kGid[2] = {"tc.chunk_gid.0", "tc.chunk_gid.1"};
+    static const char* const kRows[2] = {"tc.chunk_rows.0", "tc.chunk_rows.1"};
+    static const char* const kNext[2] = {"tc.chunk_next.0", "tc.chunk_next.1"};
+    static const char* const kDen[2] = {"tc.chunk_den.0", "tc.chunk_den.1"};
+    static const char* const kFirst[2] = {"tc.item_first.0", "tc.item_first.1"};
+    static const char* const kCounter[2] = {"tc.counter.0", "tc.counter.1"};
+    const int p = parity & 1;
     const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
     const int nitems = nv * TX * TY;
-    int* counter;
-    int* host;   // [0] chunks used, [1] status
-    LV_TRY(ws.get("tc.counter", 1, &counter));
-    {
-        void* p;
-        LV_TRY(ws.pinned("tc.host", 16, &p));
-        host = static_cast<int*>(p);
+    TileWeights t;
+    LV_TRY(ws.get(kCounter[p], 1, &t.counter));
+    LV_TRY(ws.get(kFirst[p], (size_t)nitems, &t.ifirst));
+    int* host = nullptr;   // [0] chunks used, [1] status
+    if (checked) {
+        void* hp;
+        LV_TRY(ws.pinned("tc.host", 16, &hp));
+        host = static_cast<int*>(hp);
     }
     int64_t cap = std::max<int64_t>(*chunk_cap, 3 * (int64_t)nitems);
-    TileWeights t;
-    LV_TRY(ws.get("tc.item_first", (size_t)nitems, &t.ifirst));
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (cap > 0x7fffffff / kCRows) {
             set_error("tile weights need %lld chunks of 128 rows", (long long)cap);
             return LUDVIG_ERR_UNSUPPORTED;
         }
-        LV_TRY(ws.get("tc.w1", (size_t)cap * kChunkBytes, &t.wg1));
-        if (NT == 2) LV_TRY(ws.get("tc.w2", (size_t)cap * kChunkBytes, &t.wg2));
-        LV_TRY(ws.get("tc.chunk_gid", (size_t)cap * kCRows, &t.cgid));
-        LV_TRY(ws.get("tc.chunk_rows", (size_t)cap, &t.crows));
-        LV_TRY(ws.get("tc.chunk_next", (size_t)cap, &t.cnext));
-        LV_TRY(ws.get("tc.chunk_den", (size_t)cap * kCRows * NT, &t.cden));
-        LV_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
+        LV_TRY(ws.get(kW1[p], (size_t)cap * kChunkBytes, &t.wg1));
+        if (NT == 2) LV_TRY(ws.get(kW2[p], (size_t)cap * kChunkBytes, &t.wg2));
+        LV_TRY(ws.get(kGid[p], (size_t)cap * kCRows, &t.cgid));
+        LV_TRY(ws.get(kRows[p], (size_t)cap, &t.crows));
+        LV_TRY(ws.get(kNext[p], (size_t)cap, &t.cnext));
+        LV_TRY(ws.get(kDen[p], (size_t)cap * kCRows * NT, &t.cden));
+        LV_CUDA(cudaMemsetAsync(t.counter, 0, sizeof(int), st));
         LV_CUDA(cudaMemsetAsync(t.ifirst, 0xff, sizeof(int) * (size_t)nitems, st));
         WeightsArgs w{};
-        w.pairs = pairs;
-        w.ranges = ranges;
+        w.rank = L.rank;
+        w.srec = L.srec;
+        w.npad = L.npad;
+        w.ranges = L.ranges;
         w.ntiles = TX * TY;
         w.TX = TX;
         w.width = width;
@@ -1319,10 +1362,9 @@ ludvig_status tile_weights(const PairRec* pairs, const uint2* ranges, int nv, in
         w.chunk_rows = t.crows;
         w.chunk_next = t.cnext;
         w.item_first = t.ifirst;
-        w.chunk_counter = counter;
+        w.chunk_counter = t.counter;
         w.cap = (int)cap;
         w.chunk_den = t.cden;
-        w.status = status;
         w.count_den = option_count_normalise() ? 1 : 0;
         const int tslot = trace_on() ? trace_begin(LUDVIG_STAGE_WEIGHTS, st) : -1;
         if (NT == 2)
@@ -1331,7 +1373,8 @@ ludvig_status tile_weights(const PairRec* pairs, const uint2* ranges, int nv, in
             k_weights<1><<<nitems, 256, 0, st>>>(w);
         LV_LAUNCH();
         trace_end(tslot, st);
-        LV_CUDA(cudaMemcpyAsync(host, counter, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (!checked) break;
+        LV_CUDA(cudaMemcpyAsync(host, t.counter, sizeof(int), cudaMemcpyDeviceToHost, st));
         LV_CUDA(cudaMemcpyAsync(host + 1, status, sizeof(int), cudaMemcpyDeviceToHost, st));
         LV_CUDA(cudaStreamSynchronize(st));
         t.count = host[0];
@@ -1343,7 +1386,7 @@ ludvig_status tile_weights(const PairRec* pairs, const uint2* ranges, int nv, in
         // more chunks than kept: grow and run the weights again
         cap = (int64_t)t.count + t.count / 8 + 1;
     }
-    if (t.count > cap) {
+    if (checked && t.count > cap) {
         set_error("tile weights exceed the chunk capacity");
         return LUDVIG_ERR_INTERNAL;
     }
@@ -1353,29 +1396,14 @@ ludvig_status tile_weights(const PairRec* pairs, const uint2* ranges, int nv, in
     return LUDVIG_OK;
 }
 
-}  // namespace
-
-// Tensor-core aggregation applies to d in [32, 512] with d % 8 == 0 (16-byte
-// rows for TMA); bfloat16 features always, float32 unless disabled.
-bool tc_supported(int dtype, int d) {
-    return (dtype == LUDVIG_BF16 || dtype == LUDVIG_F32) && d >= 32 && d <= 512 && d % 8 == 0;
-}
-
-// Composite + tensor-core aggregation of one chunk of views (stage 6 of the
-// uplift pipeline).  `status` receives LUDVIG_ERR_TIMEOUT if a wait expired;
-// `*chunk_cap` (chunks of 128 weight rows kept in workspace) grows as needed.
-ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, int width, int height,
-                           const void* feats, int dtype, int d, float* num, float* den, Arena& ws, int* status,
-                           int64_t* chunk_cap, cudaStream_t st) {
+ludvig_status tc_aggregate(const TileWeights& t, int nv, int width, int height, const void* feats, int dtype,
+                           int d, float* num, float* den, int* status, int* ovf, cudaStream_t st) {
     const int NT = dtype == LUDVIG_F32 ? 2 : 1;
-    int sms = 0;
-    LV_TRY(sm_count(&sms));
     const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
     const int nitems = nv * TX * TY;
-    if (nitems == 0) return LUDVIG_OK;
-    TileWeights t;
-    LV_TRY(tile_weights(pairs, ranges, nv, width, height, NT, ws, status, chunk_cap, st, &t));
-    if (t.count == 0) return LUDVIG_OK;
+    if (nitems == 0 || t.count == 0) return LUDVIG_OK;
+    int sms = 0;
+    LV_TRY(sm_count(&sms));
     CUtensorMap maps[3];
     LV_TRY(make_w_map(&maps[0], t.wg1, t.cap));
     LV_TRY(make_w_map(&maps[1], NT == 2 ? t.wg2 : t.wg1, t.cap));
@@ -1395,22 +1423,26 @@ ludvig_status composite_tc(const PairRec* pairs, const uint2* ranges, int nv, in
     g.den = den;
     g.status = status;
     g.store_mode = 0;
+    g.chunk_count = t.count >= 0 ? nullptr : t.counter;   // a checked run already fits
+    g.ovf = ovf;
     const int grid = std::min(sms, nitems);
     StageScope agg_scope(LUDVIG_STAGE_AGGREGATE, st);
     if (NT == 2) return dispatch_agg<2>(g, maps, grid, st);
     return dispatch_agg<1>(g, maps, grid, st);
 }
 
-// Rendering F_hat = W f of one chunk of views on the tensor cores (Eq. 4):
-// the weight rows of k_weights (float32 split in two bfloat16 terms), then the
+// Rendering F_hat = W f of a group on the tensor cores (Eq. 4): the weight
+// rows of k_weights (float32 split in two bfloat16 terms), then the
 // persistent k_render_tc over the (view, tile, 128-channel block) units.
-ludvig_status render_tc(const PairRec* pairs, const uint2* ranges, int nv, int width, int height, const float* f,
-                        int d, float* out, Arena& ws, int* status, int64_t* chunk_cap, cudaStream_t st) {
+ludvig_status tc_render(const TileWeights& t, Arena& ws, int nv, int width, int height, const float* f, int d,
+                        float* out, int* status, cudaStream_t st) {
     const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
     const int nitems = nv * TX * TY;
     if (nitems == 0) return LUDVIG_OK;
-    TileWeights t;
-    LV_TRY(tile_weights(pairs, ranges, nv, width, height, 2, ws, status, chunk_cap, st, &t));
+    if (t.count < 0) {
+        set_error("render needs a checked weights pass");
+        return LUDVIG_ERR_INTERNAL;
+    }
     // plan: stages of every item (a chunk has at most 4 stages of 32 rows)
     uint32_t* start;
     uint2* stages;
@@ -1472,7 +1504,24 @@ __global__ void k_wait_timeout(long long budget, int* status, long long* waited)
     *status = ok ? (int)LUDVIG_OK : (int)LUDVIG_ERR_TIMEOUT;
     mbar_arrive(&bar);   // complete the phase so that nothing is left pending
 }
+
+// The same wait reporting into a status word the way the tensor-core kernels
+// do (only an expiry writes it).
+__global__ void k_wait_timeout_status(long long budget, int* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait_for(&bar, 0u, budget)) atomicExch(status, (int)LUDVIG_ERR_TIMEOUT);
+    mbar_arrive(&bar);
+}
 }  // namespace
+
+ludvig_status tc_wait_into_status(int64_t cycles, int* status, cudaStream_t st) {
+    k_wait_timeout_status<<<1, 32, 0, st>>>((long long)cycles, status);
+    LV_LAUNCH();
+    return LUDVIG_OK;
+}
 }  // namespace ludvig
 
 extern "C" ludvig_status ludvig_debug_wait_timeout(int64_t cycles, int64_t* waited, void* stream) {
@@ -1534,6 +1583,8 @@ extern "C" ludvig_status ludvig_debug_mma_bf16(const void* a, const void* f, int
     g.den = nullptr;
     g.status = &meta->status;
     g.store_mode = 1;
+    g.chunk_count = nullptr;
+    g.ovf = nullptr;
     LV_TRY(dispatch_agg<1>(g, maps, 1, st));
     int hs = 0;
     LV_CUDA(cudaMemcpyAsync(&hs, &meta->status, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -33,7 +33,8 @@ _F = ctypes.c_float
 SIGNATURES = {
     "ludvig_abi_version": (_I32, []),
     "ludvig_last_error": (ctypes.c_char_p, []),
-    "ludvig_scene_create": (_I32, [_P, _P, _P, _P, _I64, _P, ctypes.POINTER(_P)]),
+    "ludvig_scene_create": (_I32, [_P, _P, _P, _P, _I64, _P, _P, ctypes.POINTER(_P)]),
+    "ludvig_sync": (_I32, [_P]),
     "ludvig_scene_destroy": (_I32, [_P]),
     "ludvig_scene_size": (_I64, [_P]),
     "ludvig_uplift_accumulate": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
@@ -63,6 +64,7 @@ SIGNATURES = {
     "ludvig_debug_transmittance": (_I32, [_P, _P, _I32, _I32, _P, _P, _P]),
     "ludvig_debug_mma_bf16": (_I32, [_P, _P, _I32, _P, _P]),
     "ludvig_debug_wait_timeout": (_I32, [_I64, ctypes.POINTER(_I64), _P]),
+    "ludvig_debug_scene_timeout": (_I32, [_P, _I64, _P]),
     "ludvig_knn": (_I32, [_P, _I32, _P, _P]),
     "ludvig_graph_build": (_I32, [_P, _I32, _P, _I32, _F, _F, _I32, _P, ctypes.POINTER(_P)]),
     "ludvig_graph_destroy": (_I32, [_P]),
@@ -140,18 +142,26 @@ def _dtype_code(t: torch.Tensor) -> int:
     raise LudvigError(f"features must be float32 or bfloat16, got {t.dtype}")
 
 
-class Scene:
-    """A device-resident Gaussian scene (ludvig_scene_create)."""
+class SceneOpts(ctypes.Structure):
+    """ludvig_scene_opts."""
+    _fields_ = [("scales_are_linear", ctypes.c_int32)]
 
-    def __init__(self, means, scales, quats, opacity, stream=None):
+
+class Scene:
+    """A device-resident Gaussian scene (ludvig_scene_create).  scales are
+    linear standard deviations unless log_scales is set."""
+
+    def __init__(self, means, scales, quats, opacity, stream=None, log_scales=False):
         L = load()
         dev = torch.device("cuda")
         t = [torch.as_tensor(a, dtype=torch.float32).to(dev).contiguous()
              for a in (means, scales, quats, opacity)]
         self.n = int(t[0].shape[0])
         h = ctypes.c_void_p()
+        opts = SceneOpts(0 if log_scales else 1)
         _check(L.ludvig_scene_create(_dev(t[0]), _dev(t[1]), _dev(t[2]), _dev(t[3]), self.n,
-                                     _stream(stream), ctypes.byref(h)), "ludvig_scene_create")
+                                     ctypes.byref(opts), _stream(stream), ctypes.byref(h)),
+               "ludvig_scene_create")
         torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
         self._h = h
 
@@ -177,6 +187,10 @@ class Scene:
     def handle(self):
         return self._h
 
+    def sync(self):
+        """ludvig_sync: wait for and complete the scene's last asynchronous uplift."""
+        _check(load().ludvig_sync(self._h), "ludvig_sync")
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             load().ludvig_scene_destroy(self._h)
@@ -190,8 +204,10 @@ class Scene:
 
 
 def uplift(scene: Scene, cams_params, width, height, feats: torch.Tensor, out=None, beta=None,
-           stream=None):
-    """f = D^-1 W^T F on the device.  feats: [V,H,W,D] float32/bfloat16 CUDA tensor."""
+           stream=None, sync=True):
+    """f = D^-1 W^T F on the device.  feats: [V,H,W,D] float32/bfloat16 CUDA tensor.
+    With sync (the default) the call ends with ludvig_sync, so out/beta are
+    final on return; otherwise call scene.sync() before using them."""
     L = load()
     cams, nv = cameras_struct(cams_params)
     d = int(feats.shape[-1])
@@ -202,6 +218,8 @@ def uplift(scene: Scene, cams_params, width, height, feats: torch.Tensor, out=No
     _check(L.ludvig_uplift(scene.handle, cams, nv, width, height, _dev(feats, name="feats"),
                            _dtype_code(feats), d, _dev(out, torch.float32, "out"),
                            _dev(beta, torch.float32, "beta"), _stream(stream)), "ludvig_uplift")
+    if sync:
+        scene.sync()
     return out, beta
 
 
@@ -257,7 +275,7 @@ def fp8_quantize(feats: torch.Tensor, q=None, scales=None, stream=None):
 
 
 def uplift_fp8(scene: Scene, cams_params, width, height, q: torch.Tensor, scales: torch.Tensor, out=None,
-               beta=None, stream=None):
+               beta=None, stream=None, sync=True):
     """ludvig_uplift_fp8: uplift of E4M3 features q [V,H,W,D] (uint8) with
     per-view scales [V]."""
     cams, nv = cameras_struct(cams_params)
@@ -269,6 +287,8 @@ def uplift_fp8(scene: Scene, cams_params, width, height, q: torch.Tensor, scales
     _check(load().ludvig_uplift_fp8(scene.handle, cams, nv, width, height, _dev(q, torch.uint8, "q"),
                                     _dev(scales, torch.float32, "scales"), d, _dev(out, torch.float32, "out"),
                                     _dev(beta, torch.float32, "beta"), _stream(stream)), "ludvig_uplift_fp8")
+    if sync:
+        scene.sync()
     return out, beta
 
 
@@ -277,13 +297,15 @@ def batch_release_workspaces():
     _check(load().ludvig_batch_release_workspaces(), "ludvig_batch_release_workspaces")
 
 
-def uplift_accumulate(scene: Scene, cams_params, width, height, feats, num, den, stream=None):
+def uplift_accumulate(scene: Scene, cams_params, width, height, feats, num, den, stream=None, sync=True):
     L = load()
     cams, nv = cameras_struct(cams_params)
     _check(L.ludvig_uplift_accumulate(scene.handle, cams, nv, width, height, _dev(feats, name="feats"),
                                       _dtype_code(feats), int(feats.shape[-1]),
                                       _dev(num, torch.float32, "num"), _dev(den, torch.float32, "den"),
                                       _stream(stream)), "ludvig_uplift_accumulate")
+    if sync:
+        scene.sync()
 
 
 def uplift_finalize(num, den, out=None, beta=None, stream=None):

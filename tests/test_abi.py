@@ -34,14 +34,16 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version(lib):
-    assert lib.ludvig_abi_version() == 8
+    assert lib.ludvig_abi_version() == 9
 
 
 def test_argument_errors_are_synchronous(lib):
     h = ctypes.c_void_p()
-    assert lib.ludvig_scene_create(None, None, None, None, 5, None, ctypes.byref(h)) == 1
+    assert lib.ludvig_scene_create(None, None, None, None, 5, None, None, ctypes.byref(h)) == 1
     assert b"NULL" in lib.ludvig_last_error()
-    assert lib.ludvig_scene_create(None, None, None, None, -1, None, ctypes.byref(h)) == 1
+    assert lib.ludvig_scene_create(None, None, None, None, -1, None, None, ctypes.byref(h)) == 1
+    assert lib.ludvig_sync(None) == 1
+    assert lib.ludvig_debug_scene_timeout(None, 10, None) == 1
     assert lib.ludvig_uplift(None, None, 1, 64, 64, None, 0, 4, None, None, None) == 1
     assert lib.ludvig_knn(None, 4, None, None) == 1
     assert lib.ludvig_render(None, None, 1, 64, 64, None, 4, None, None) == 1
