@@ -93,10 +93,14 @@ typedef enum {
     LUDVIG_OPT_FAULT_ALLOC = 2,       /* host-side fault injection for tests: k > 0 makes the k-th
                                          workspace allocation from now fail once with
                                          LUDVIG_ERR_OOM (nothing is allocated); 0 disarms */
-    LUDVIG_OPT_FAULT_LAUNCH = 3       /* k > 0: the k-th checked kernel launch from now reports
+    LUDVIG_OPT_FAULT_LAUNCH = 3,      /* k > 0: the k-th checked kernel launch from now reports
                                          LUDVIG_ERR_CUDA once (the kernel itself was queued and
                                          runs normally); 0 disarms.  The failed call's outputs
                                          are undefined; a later call starts afresh */
+    LUDVIG_OPT_AGG_CONFIG = 4         /* shared-memory layout of the float32 tensor-core
+                                         aggregation: 0 = seven feature stages, four epilogue
+                                         warps; 1 = five stages, eight epilogue warps.  Results
+                                         are the same to rounding; only the speed differs */
 } ludvig_option;
 
 /* Sets an option; LUDVIG_ERR_ARG for an unknown option. */

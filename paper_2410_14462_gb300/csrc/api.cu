@@ -217,9 +217,11 @@ namespace ludvig {
 namespace {
 std::atomic<int64_t> g_opt_f32_tc{1};
 std::atomic<int64_t> g_opt_count{0};
+std::atomic<int64_t> g_opt_agg_config{0};
 }
 bool option_f32_tensor_cores() { return g_opt_f32_tc.load() != 0; }
 bool option_count_normalise() { return g_opt_count.load() != 0; }
+int option_agg_config() { return (int)g_opt_agg_config.load(); }
 }  // namespace ludvig
 
 extern "C" ludvig_status ludvig_set_option(int32_t option, int64_t value) {
@@ -236,6 +238,13 @@ extern "C" ludvig_status ludvig_set_option(int32_t option, int64_t value) {
         case LUDVIG_OPT_FAULT_LAUNCH:
             g_fault_launch.store(value > 0 ? value : 0);
             return LUDVIG_OK;
+        case LUDVIG_OPT_AGG_CONFIG:
+            if (value < 0 || value > 1) {
+                set_error("LUDVIG_OPT_AGG_CONFIG must be 0 or 1");
+                return LUDVIG_ERR_ARG;
+            }
+            g_opt_agg_config.store(value);
+            return LUDVIG_OK;
         default:
             set_error("unknown option %d", option);
             return LUDVIG_ERR_ARG;
@@ -248,6 +257,7 @@ extern "C" int64_t ludvig_get_option(int32_t option) {
         case LUDVIG_OPT_COUNT_NORMALISE: return g_opt_count.load();
         case LUDVIG_OPT_FAULT_ALLOC: return g_fault_alloc.load();
         case LUDVIG_OPT_FAULT_LAUNCH: return g_fault_launch.load();
+        case LUDVIG_OPT_AGG_CONFIG: return g_opt_agg_config.load();
         default: return -1;
     }
 }

@@ -1078,6 +1078,38 @@ ludvig_status run_checked(ludvig_scene* s, const ludvig_camera* cams, int v0, in
     return LUDVIG_OK;
 }
 
+// Allocates what asynchronous groups of up to nv views use at the scene's
+// current capacities (both buffer sets), so that they find it in place: a
+// workspace that grows synchronises the device.
+ludvig_status reserve_async(ludvig_scene* s, int nv, int width, int height, const FeatSrc& src, bool tc) {
+    Arena& ws = s->ws;
+    void* q;
+    const int64_t cap = std::max<int64_t>(s->pair_cap, kRadixTile);
+    for (const char* name : {"up.pk", "up.pv", "up.pk2", "up.pv2"}) LV_TRY(ws.get(name, sizeof(uint32_t) * (size_t)cap, &q));
+    // the radix sorts' digit histograms (pairs, and the depth sort of nv views) and their scan sums
+    const int64_t npad = round_up(s->n, kRadixTile);
+    const int64_t hist = 256 * std::max<int64_t>(cap, (int64_t)nv * npad) / kRadixTile;
+    LV_TRY(ws.get("radix.hist", sizeof(uint32_t) * (size_t)hist, &q));
+    LV_TRY(ws.get("scan.sums", sizeof(unsigned long long) * (size_t)ceil_div(std::max(hist, (int64_t)nv * npad), 4096),
+                  &q));
+    if (!tc) {
+        LV_TRY(ws.get("up.pairs", sizeof(PairRec) * (size_t)cap, &q));
+        return LUDVIG_OK;
+    }
+    const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
+    const bool padded = src_padded(src);
+    const int fdt = src.kind == 2 ? LUDVIG_BF16 : src.dtype;
+    LV_TRY(tc_reserve(ws, fdt == LUDVIG_F32 ? 2 : 1, nv * TX * TY, s->tc_chunk_cap));
+    const int64_t npx = (int64_t)nv * width * height;
+    for (int p = 0; p < 2; ++p) {
+        static const char* const kFb[2] = {"fp8.bf16.0", "fp8.bf16.1"};
+        static const char* const kPad[2] = {"pad.feats.0", "pad.feats.1"};
+        if (src.kind == 2) LV_TRY(ws.get(kFb[p], 2 * (size_t)npx * src.d, &q));
+        if (padded) LV_TRY(ws.get(kPad[p], (size_t)npx * kPadD * (fdt == LUDVIG_F32 ? 4 : 2), &q));
+    }
+    return LUDVIG_OK;
+}
+
 // Streams, events and status words of the asynchronous path (first use).
 ludvig_status ensure_async(ludvig_scene* s, int ngroups) {
     if (!s->st_front) {
@@ -1220,6 +1252,7 @@ ludvig_status run_call(ludvig_scene* s, int kind, const FeatSrc& src, const ludv
         LV_TRY(run_checked(s, cams, 0, nv, width, height, src, num, den, pad_num, st));
         s->pair_cap = round_up(s->pair_cap + s->pair_cap / 4, kRadixTile);
         s->tc_chunk_cap += s->tc_chunk_cap / 4;
+        LV_TRY(reserve_async(s, nv, width, height, src, tc));
         v0 = nv;
     }
     std::vector<int> gv0, gnv;

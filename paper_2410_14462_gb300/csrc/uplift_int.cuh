@@ -24,6 +24,8 @@ struct TileWeights {
     uint32_t* cgid = nullptr;
     int *crows = nullptr, *cnext = nullptr, *ifirst = nullptr;
     float* cden = nullptr;
+    uint32_t* plan_off = nullptr;   // [nitems + 1]: each tile's entries in plan
+    int2* plan = nullptr;           // [cap]: {chunk, rows} of the non-empty chunks, tile after tile
 };
 
 bool tc_supported(int dtype, int d);
@@ -35,6 +37,11 @@ bool tc_supported(int dtype, int d);
 // with *chunk_cap chunks and the aggregation checks the count on the device.
 ludvig_status tc_weights(const GroupLists& L, int nv, int width, int height, int NT, Arena& ws, int parity,
                          int* status, int64_t* chunk_cap, bool checked, cudaStream_t st, TileWeights* tw);
+
+// Allocates both buffer sets of the weight rows for groups of up to nitems
+// (view, tile) items and cap chunks (allocation synchronises the device, so an
+// asynchronous call that finds them in place never waits).
+ludvig_status tc_reserve(Arena& ws, int NT, int nitems, int64_t cap);
 
 // num[i,:] += W^T F and den[i] += row sums for the group's weight rows
 // (k_aggregate_tc).  When the weights overflowed their chunks the kernel adds

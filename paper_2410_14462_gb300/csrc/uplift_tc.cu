@@ -61,6 +61,7 @@
 namespace ludvig {
 
 bool option_count_normalise();
+int option_agg_config();
 
 namespace {
 
@@ -370,6 +371,8 @@ struct AggArgs {
     int store_mode;          // debug GEMM: num[gid * d + c] = accumulator (no den)
     const int* chunk_count;  // chunks the weights pass used (may be null: known to fit)
     int* ovf;                // set to 2 when they exceeded cap (the launch then adds nothing)
+    const uint32_t* plan_off;   // [nitems + 1]: the item's chunks are plan[plan_off[item] ..)
+    const int2* plan;           // {chunk, rows} of every non-empty chunk, tile after tile
 };
 
 // Feature units (16 KB): 128 channels of 64 pixels (NT = 1: one K atom, two
@@ -377,15 +380,19 @@ struct AggArgs {
 // four 32-channel float32 boxes of 4 KB, turned in place into F1 (first 8 KB)
 // and F2 (second 8 KB) by the converter warps).  The two 64-channel atoms of a
 // term sit kBoxBytes apart (the MMA's N = 128).
-template <int NT>
+// CF selects the float32 layout: 0 = seven feature stages and four epilogue
+// warps, 1 = five stages and eight epilogue warps (more staged rows in flight).
+template <int NT, int CF>
 struct AggSmem {
     static constexpr int kWA = NT == 1 ? 4 : 2;              // W atom stages (NT x 16 KB each)
     static constexpr int kHalves = NT == 2 ? 2 : 1;           // feature units per K atom and channel group
     static constexpr int kUnitPx = 64 / kHalves;              // pixels per unit
     static constexpr uint32_t kBoxBytes = kUnitPx * 128u;     // one 128-byte-wide box (and one F1 atom)
     static constexpr uint32_t kFStage = 16384u;               // one feature unit
-    static constexpr int kFS = NT == 1 ? 5 : 7;               // 80 KB or 112 KB of stages
-    static constexpr int kEH = NT == 1 ? 2 : 1;               // epilogue warps per TMEM lane quarter
+    static constexpr int kFS = (NT == 1 || CF == 1) ? 5 : 7;  // 80 KB or 112 KB of stages
+    static constexpr int kEH = (NT == 1 || CF == 1) ? 2 : 1;  // epilogue warps per TMEM lane quarter
+    static constexpr int kConv0 = 2 + 4 * kEH;                // first converter warp (NT = 2)
+    static constexpr int kThreads = 32 * (kConv0 + (NT == 2 ? 8 : 0));
     static constexpr int kPitch = 68;                         // staged row: 64 floats + 16 B pad
     uint8_t W[kWA][NT][kAtomBytes];                           // offset 0 (1024-aligned)
     uint8_t F[kFS][kFStage];
@@ -401,41 +408,48 @@ struct AggSmem {
     int abort_flag;
 };
 
-template <int NT>
+template <int NT, int CF>
 constexpr size_t agg_smem_bytes() {
-    return sizeof(AggSmem<NT>) + 1024;   // + alignment slack
+    return sizeof(AggSmem<NT, CF>) + 1024;   // + alignment slack
 }
-static_assert(agg_smem_bytes<1>() <= 232448 && agg_smem_bytes<2>() <= 232448, "shared memory");
+static_assert(agg_smem_bytes<1, 0>() <= 232448 && agg_smem_bytes<2, 0>() <= 232448 &&
+                  agg_smem_bytes<2, 1>() <= 232448,
+              "shared memory");
 
-// warp 0 producer, warp 1 MMA, then 4 kEH epilogue warps (8 for NT = 1, 4 for
-// NT = 2) and, for NT = 2, 8 converter warps (6 .. 13)
-template <int NT>
+// warp 0 producer, warp 1 MMA, then 4 kEH epilogue warps (8, or 4 for NT = 2
+// with CF = 0) and, for NT = 2, 8 converter warps from kConv0
+template <int NT, int CF>
 constexpr int agg_threads() {
-    return NT == 1 ? 320 : 448;
+    return AggSmem<NT, CF>::kThreads;
 }
 
 // The chunks a CTA aggregates: those of tiles blockIdx.x, blockIdx.x + gridDim.x,
 // ... in order, each tile's chunks back to back (so its feature blocks are
-// still in L2 for the second chunk).  The producer walks the sequence and
-// hands it to the other roles through a queue in shared memory.
-struct ChunkWalk {
-    int item, c, rows;
-    __device__ ChunkWalk() : item((int)blockIdx.x - (int)gridDim.x), c(-1), rows(0) {}
-    // next non-empty chunk (its tile in item), or -1 at the end
-    __device__ int next(const AggArgs& a) {
-        for (;;) {
-            if (c >= 0) c = a.chunk_next[c];
-            while (c < 0) {
-                item += gridDim.x;
-                if (item >= a.nitems) return -1;
-                c = a.item_first[item];
-            }
-            if (c >= a.cap) return -1;   // never with a complete weights pass
-            rows = a.chunk_rows[c];
-            if (rows > 0) return c;
-        }
+// still in L2 for the second chunk).  A plan pass flattens every tile's chunk
+// chain into consecutive {chunk, rows} entries first, so that the producer
+// reads its sequence with independent loads it can issue ahead (following the
+// chain would cost it a few dependent global loads per chunk), and hands it
+// to the other roles through a queue in shared memory.
+
+// Plan: non-empty chunks per item (count pass), then their entries (fill
+// pass), one thread per item walking its chain.
+__global__ void k_agg_plan(const int* __restrict__ item_first, const int* __restrict__ chunk_rows,
+                           const int* __restrict__ chunk_next, int cap, int nitems, const uint32_t* __restrict__ off,
+                           uint32_t* __restrict__ count, int2* __restrict__ plan) {
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= nitems) {
+        if (count && item == nitems) count[item] = 0u;
+        return;
     }
-};
+    uint32_t k = off ? off[item] : 0u;
+    for (int c = item_first[item]; c >= 0 && c < cap; c = chunk_next[c]) {
+        const int rows = chunk_rows[c];
+        if (rows <= 0) continue;
+        if (plan) plan[k] = make_int2(c, rows);
+        ++k;
+    }
+    if (count) count[item] = k;
+}
 
 __device__ __forceinline__ bool agg_wait(volatile int* abort_flag, int* status, uint64_t* bar, uint32_t parity);
 
@@ -477,11 +491,11 @@ __device__ __forceinline__ void split8(const float* x, uint4& f1, uint4& f2) {
     f2 = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-template <int DB, int NT>
-__global__ void __launch_bounds__(agg_threads<NT>(), 1)
+template <int DB, int NT, int CF>
+__global__ void __launch_bounds__(agg_threads<NT, CF>(), 1)
     k_aggregate_tc(AggArgs a, const __grid_constant__ CUtensorMap wmap1, const __grid_constant__ CUtensorMap wmap2,
                    const __grid_constant__ CUtensorMap fmap) {
-    using Sm = AggSmem<NT>;
+    using Sm = AggSmem<NT, CF>;
     // a weights pass that ran out of chunks left incomplete rows: the group is
     // redone once the workspace has grown, so nothing of it may be added now
     if (a.chunk_count && *a.chunk_count > a.cap) {
@@ -526,27 +540,52 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
             // ---- TMA producer: per chunk, K atom ka: W atom, then the U feature units
             uint32_t wc = 0, fc = 0, qc = 0;
             bool ok = true;
-            ChunkWalk walk;
             // weight rows are read once and a tile's features by its chunks only:
             // first out of L2 after their last use, so that the num lines the
             // epilogue adds into stay there between tiles
             const uint64_t stream_policy = policy_evict_first(), keep_policy = policy_evict_normal();
+            // plan entries: this item's [k, kend), the next item's range loaded one item ahead
+            int item = blockIdx.x;
+            uint32_t k = 0, kend = 0;
+            if (item < a.nitems) {
+                k = a.plan_off[item];
+                kend = a.plan_off[item + 1];
+            }
+            int nitem = item + (int)gridDim.x;
+            uint32_t nk = 0, nkend = 0;
+            if (nitem < a.nitems) {
+                nk = a.plan_off[nitem];
+                nkend = a.plan_off[nitem + 1];
+            }
+            int2 e = k < kend ? a.plan[k] : make_int2(-1, 0);
             for (;;) {
-                const int c = (ok && !*abort_flag) ? walk.next(a) : -1;
+                while (item < a.nitems && k >= kend) {   // next item with chunks
+                    item = nitem;
+                    k = nk;
+                    kend = nkend;
+                    nitem += (int)gridDim.x;
+                    if (nitem < a.nitems) {
+                        nk = a.plan_off[nitem];
+                        nkend = a.plan_off[nitem + 1];
+                    }
+                    if (k < kend) e = a.plan[k];
+                }
+                const int c = (ok && !*abort_flag && item < a.nitems) ? e.x : -1;
+                const int rows = e.y;
+                const bool tile_last = k + 1 >= kend;
+                if (c >= 0 && !tile_last) e = a.plan[k + 1];   // the next entry, ahead of its use
                 // publish the chunk (or the end) to the other roles
                 const uint32_t qs = qc % Sm::kQ;
                 if (qc >= (uint32_t)Sm::kQ &&
                     !agg_wait(abort_flag, a.status, &S.q_empty[qs], ((qc / Sm::kQ) - 1) & 1u))
                     break;
-                S.q[qs] = make_int4(c, c >= 0 ? walk.item : -1, c >= 0 ? walk.rows : 0, 0);
+                S.q[qs] = make_int4(c, c >= 0 ? item : -1, c >= 0 ? rows : 0, 0);
                 mbar_arrive(&S.q_full[qs]);
                 ++qc;
                 if (c < 0) break;
-                const int item = walk.item;
+                ++k;
                 const int v = item / a.ntiles, tile = item - v * a.ntiles;
                 const int tx = tile % a.TX, ty = tile / a.TX;
-                const int nx = a.chunk_next[c];
-                const bool tile_last = nx < 0 || nx >= a.cap || a.chunk_rows[nx] == 0;
                 const uint64_t fpolicy = tile_last ? stream_policy : keep_policy;
                 for (int ka = 0; ka < 4 && ok; ++ka) {
                     const uint32_t ws = wc % Sm::kWA;
@@ -557,7 +596,7 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
                     }
                     // only the chunk's rows, in boxes of 32 (the rest of the atom is not read
                     // into any kept result)
-                    const int nrb = (walk.rows + 31) >> 5;
+                    const int nrb = (rows + 31) >> 5;
                     mbar_expect_tx(&S.w_full[ws], (uint32_t)(NT * nrb) * 4096u);
                     for (int rb = 0; rb < nrb; ++rb) {
                         tma_load_2d_hint(S.W[ws][0] + 4096 * rb, &wmap1, &S.w_full[ws], ka * 64, c * kCRows + 32 * rb,
@@ -596,13 +635,13 @@ __global__ void __launch_bounds__(agg_threads<NT>(), 1)
                     mbar_wait(&S.w_full[u % Sm::kWA], (u / Sm::kWA) & 1u);
             }
         }
-    } else if (NT == 2 && warp >= 6) {
+    } else if (NT == 2 && warp >= Sm::kConv0) {
         // ---- converters: float32 unit (boxes j = 0..3 of 32 channels at 8 KB j)
         // -> F1 atoms h = 0, 1 (64 channels at 8 KB h) and F2 atoms (16 KB + 8 KB h).
         // Converter warp cw owns pixel rows 8 cw .. 8 cw + 7 of every region:
         // the bytes it reads are the bytes it writes, so the in-place rewrite
         // needs only a warp-level barrier.
-        const int cw = warp - 6;
+        const int cw = warp - Sm::kConv0;
         uint32_t fc = 0, qc = 0;
         bool ok = true;
         for (;;) {
@@ -1269,30 +1308,37 @@ ludvig_status make_w_map(CUtensorMap* map, const void* w, int64_t cap) {
     return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w, 2, dims, strides, box);
 }
 
-template <int DB, int NT>
+template <int DB, int NT, int CF>
 ludvig_status launch_agg(const AggArgs& args, const CUtensorMap* maps, int grid, cudaStream_t st) {
     // set once per process; a function-local static is initialised by one thread
-    static const cudaError_t configured =
-        cudaFuncSetAttribute(k_aggregate_tc<DB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)agg_smem_bytes<NT>());
+    static const cudaError_t configured = cudaFuncSetAttribute(
+        k_aggregate_tc<DB, NT, CF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)agg_smem_bytes<NT, CF>());
     LV_CUDA(configured);
-    k_aggregate_tc<DB, NT><<<grid, agg_threads<NT>(), agg_smem_bytes<NT>(), st>>>(args, maps[0], maps[1], maps[2]);
+    k_aggregate_tc<DB, NT, CF>
+        <<<grid, agg_threads<NT, CF>(), agg_smem_bytes<NT, CF>(), st>>>(args, maps[0], maps[1], maps[2]);
     LV_LAUNCH();
     return LUDVIG_OK;
 }
 
-template <int NT>
-ludvig_status dispatch_agg(const AggArgs& args, const CUtensorMap* maps, int grid, cudaStream_t st) {
+template <int NT, int CF>
+ludvig_status dispatch_agg_cf(const AggArgs& args, const CUtensorMap* maps, int grid, cudaStream_t st) {
     switch ((args.d + 63) / 64) {
-        case 1: return launch_agg<1, NT>(args, maps, grid, st);
-        case 2: return launch_agg<2, NT>(args, maps, grid, st);
-        case 3: return launch_agg<3, NT>(args, maps, grid, st);
-        case 4: return launch_agg<4, NT>(args, maps, grid, st);
-        case 5: return launch_agg<5, NT>(args, maps, grid, st);
-        case 6: return launch_agg<6, NT>(args, maps, grid, st);
-        case 7: return launch_agg<7, NT>(args, maps, grid, st);
-        case 8: return launch_agg<8, NT>(args, maps, grid, st);
+        case 1: return launch_agg<1, NT, CF>(args, maps, grid, st);
+        case 2: return launch_agg<2, NT, CF>(args, maps, grid, st);
+        case 3: return launch_agg<3, NT, CF>(args, maps, grid, st);
+        case 4: return launch_agg<4, NT, CF>(args, maps, grid, st);
+        case 5: return launch_agg<5, NT, CF>(args, maps, grid, st);
+        case 6: return launch_agg<6, NT, CF>(args, maps, grid, st);
+        case 7: return launch_agg<7, NT, CF>(args, maps, grid, st);
+        case 8: return launch_agg<8, NT, CF>(args, maps, grid, st);
         default: set_error("tensor-core path needs 32 <= d <= 512"); return LUDVIG_ERR_INTERNAL;
     }
+}
+
+template <int NT>
+ludvig_status dispatch_agg(const AggArgs& args, const CUtensorMap* maps, int grid, cudaStream_t st) {
+    if (NT == 2 && option_agg_config() == 1) return dispatch_agg_cf<2, 1>(args, maps, grid, st);
+    return dispatch_agg_cf<NT, 0>(args, maps, grid, st);
 }
 
 ludvig_status sm_count(int* sms) {
@@ -1310,23 +1356,44 @@ bool tc_supported(int dtype, int d) {
     return (dtype == LUDVIG_BF16 || dtype == LUDVIG_F32) && d >= 32 && d <= 512 && d % 8 == 0;
 }
 
+// workspace names of the two buffer sets of the weight rows
+const char* const kWsW1[2] = {"tc.w1.0", "tc.w1.1"};
+const char* const kWsW2[2] = {"tc.w2.0", "tc.w2.1"};
+const char* const kWsGid[2] = {"tc.chunk_gid.0", "tc.chunk_gid.1"};
+const char* const kWsRows[2] = {"tc.chunk_rows.0", "tc.chunk_rows.1"};
+const char* const kWsNext[2] = {"tc.chunk_next.0", "tc.chunk_next.1"};
+const char* const kWsDen[2] = {"tc.chunk_den.0", "tc.chunk_den.1"};
+const char* const kWsFirst[2] = {"tc.item_first.0", "tc.item_first.1"};
+const char* const kWsCounter[2] = {"tc.counter.0", "tc.counter.1"};
+const char* const kWsPlanOff[2] = {"tc.plan_off.0", "tc.plan_off.1"};
+const char* const kWsPlan[2] = {"tc.plan.0", "tc.plan.1"};
+
+ludvig_status tc_reserve(Arena& ws, int NT, int nitems, int64_t cap) {
+    cap = std::max<int64_t>(cap, 3 * (int64_t)nitems);
+    for (int p = 0; p < 2; ++p) {
+        void* q;
+        LV_TRY(ws.get(kWsCounter[p], sizeof(int), &q));
+        LV_TRY(ws.get(kWsFirst[p], sizeof(int) * (size_t)nitems, &q));
+        LV_TRY(ws.get(kWsW1[p], (size_t)cap * kChunkBytes, &q));
+        if (NT == 2) LV_TRY(ws.get(kWsW2[p], (size_t)cap * kChunkBytes, &q));
+        LV_TRY(ws.get(kWsGid[p], sizeof(uint32_t) * (size_t)cap * kCRows, &q));
+        LV_TRY(ws.get(kWsRows[p], sizeof(int) * (size_t)cap, &q));
+        LV_TRY(ws.get(kWsNext[p], sizeof(int) * (size_t)cap, &q));
+        LV_TRY(ws.get(kWsDen[p], sizeof(float) * (size_t)cap * kCRows * NT, &q));
+        LV_TRY(ws.get(kWsPlanOff[p], sizeof(uint32_t) * ((size_t)nitems + 1), &q));
+        LV_TRY(ws.get(kWsPlan[p], sizeof(int2) * (size_t)cap, &q));
+    }
+    return LUDVIG_OK;
+}
+
 ludvig_status tc_weights(const GroupLists& L, int nv, int width, int height, int NT, Arena& ws, int parity,
                          int* status, int64_t* chunk_cap, bool checked, cudaStream_t st, TileWeights* tw) {
-    // workspace names of the two buffer sets
-    static const char* const kW1[2] = {"tc.w1.0", "tc.w1.1"};
-    static const char* const kW2[2] = {"tc.w2.0", "tc.w2.1"};
-    static const char* const kGid[2] = {"tc.chunk_gid.0", "tc.chunk_gid.1"};
-    static const char* const kRows[2] = {"tc.chunk_rows.0", "tc.chunk_rows.1"};
-    static const char* const kNext[2] = {"tc.chunk_next.0", "tc.chunk_next.1"};
-    static const char* const kDen[2] = {"tc.chunk_den.0", "tc.chunk_den.1"};
-    static const char* const kFirst[2] = {"tc.item_first.0", "tc.item_first.1"};
-    static const char* const kCounter[2] = {"tc.counter.0", "tc.counter.1"};
     const int p = parity & 1;
     const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
     const int nitems = nv * TX * TY;
     TileWeights t;
-    LV_TRY(ws.get(kCounter[p], 1, &t.counter));
-    LV_TRY(ws.get(kFirst[p], (size_t)nitems, &t.ifirst));
+    LV_TRY(ws.get(kWsCounter[p], 1, &t.counter));
+    LV_TRY(ws.get(kWsFirst[p], (size_t)nitems, &t.ifirst));
     int* host = nullptr;   // [0] chunks used, [1] status
     if (checked) {
         void* hp;
@@ -1339,12 +1406,12 @@ ludvig_status tc_weights(const GroupLists& L, int nv, int width, int height, int
             set_error("tile weights need %lld chunks of 128 rows", (long long)cap);
             return LUDVIG_ERR_UNSUPPORTED;
         }
-        LV_TRY(ws.get(kW1[p], (size_t)cap * kChunkBytes, &t.wg1));
-        if (NT == 2) LV_TRY(ws.get(kW2[p], (size_t)cap * kChunkBytes, &t.wg2));
-        LV_TRY(ws.get(kGid[p], (size_t)cap * kCRows, &t.cgid));
-        LV_TRY(ws.get(kRows[p], (size_t)cap, &t.crows));
-        LV_TRY(ws.get(kNext[p], (size_t)cap, &t.cnext));
-        LV_TRY(ws.get(kDen[p], (size_t)cap * kCRows * NT, &t.cden));
+        LV_TRY(ws.get(kWsW1[p], (size_t)cap * kChunkBytes, &t.wg1));
+        if (NT == 2) LV_TRY(ws.get(kWsW2[p], (size_t)cap * kChunkBytes, &t.wg2));
+        LV_TRY(ws.get(kWsGid[p], (size_t)cap * kCRows, &t.cgid));
+        LV_TRY(ws.get(kWsRows[p], (size_t)cap, &t.crows));
+        LV_TRY(ws.get(kWsNext[p], (size_t)cap, &t.cnext));
+        LV_TRY(ws.get(kWsDen[p], (size_t)cap * kCRows * NT, &t.cden));
         LV_CUDA(cudaMemsetAsync(t.counter, 0, sizeof(int), st));
         LV_CUDA(cudaMemsetAsync(t.ifirst, 0xff, sizeof(int) * (size_t)nitems, st));
         WeightsArgs w{};
@@ -1390,6 +1457,17 @@ ludvig_status tc_weights(const GroupLists& L, int nv, int width, int height, int
         set_error("tile weights exceed the chunk capacity");
         return LUDVIG_ERR_INTERNAL;
     }
+    // the aggregation's plan: every tile's non-empty chunks, flattened
+    LV_TRY(ws.get(kWsPlanOff[p], (size_t)nitems + 1, &t.plan_off));
+    LV_TRY(ws.get(kWsPlan[p], (size_t)cap, &t.plan));
+    {
+        const int pb = 256, pg = (nitems + 1 + pb - 1) / pb;
+        k_agg_plan<<<pg, pb, 0, st>>>(t.ifirst, t.crows, t.cnext, (int)cap, nitems, nullptr, t.plan_off, nullptr);
+        LV_LAUNCH();
+        LV_TRY(scan_exclusive_u32(t.plan_off, t.plan_off, (int64_t)nitems + 1, nullptr, ws, st));
+        k_agg_plan<<<pg, pb, 0, st>>>(t.ifirst, t.crows, t.cnext, (int)cap, nitems, t.plan_off, nullptr, t.plan);
+        LV_LAUNCH();
+    }
     t.cap = cap;
     *chunk_cap = cap;
     *tw = t;
@@ -1425,6 +1503,8 @@ ludvig_status tc_aggregate(const TileWeights& t, int nv, int width, int height, 
     g.store_mode = 0;
     g.chunk_count = t.count >= 0 ? nullptr : t.counter;   // a checked run already fits
     g.ovf = ovf;
+    g.plan_off = t.plan_off;
+    g.plan = t.plan;
     const int grid = std::min(sms, nitems);
     StageScope agg_scope(LUDVIG_STAGE_AGGREGATE, st);
     if (NT == 2) return dispatch_agg<2>(g, maps, grid, st);
@@ -1555,6 +1635,8 @@ extern "C" ludvig_status ludvig_debug_mma_bf16(const void* a, const void* f, int
     struct Meta {
         int first, next, rows, status;
         uint32_t gid[kCRows];
+        uint32_t off[2];
+        int2 plan[1];
     };
     static Meta* meta = nullptr;
     if (!meta) LV_CUDA(cudaMalloc(&meta, sizeof(Meta)));
@@ -1564,6 +1646,9 @@ extern "C" ludvig_status ludvig_debug_mma_bf16(const void* a, const void* f, int
     h.rows = kCRows;
     h.status = 0;
     for (int r = 0; r < kCRows; ++r) h.gid[r] = (uint32_t)r;
+    h.off[0] = 0u;
+    h.off[1] = 1u;
+    h.plan[0] = make_int2(0, kCRows);
     LV_CUDA(cudaMemcpyAsync(meta, &h, sizeof(Meta), cudaMemcpyHostToDevice, st));
     CUtensorMap maps[3];
     LV_TRY(make_w_map(&maps[0], a, 1));
@@ -1585,6 +1670,8 @@ extern "C" ludvig_status ludvig_debug_mma_bf16(const void* a, const void* f, int
     g.store_mode = 1;
     g.chunk_count = nullptr;
     g.ovf = nullptr;
+    g.plan_off = meta->off;
+    g.plan = meta->plan;
     LV_TRY(dispatch_agg<1>(g, maps, 1, st));
     int hs = 0;
     LV_CUDA(cudaMemcpyAsync(&hs, &meta->status, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -384,6 +384,7 @@ OPT_F32_TENSOR_CORES = 0
 OPT_COUNT_NORMALISE = 1
 OPT_FAULT_ALLOC = 2
 OPT_FAULT_LAUNCH = 3
+OPT_AGG_CONFIG = 4
 
 
 def set_option(option: int, value: int):
