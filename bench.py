@@ -290,7 +290,7 @@ def fp8_variant(sc, wl, D, o32, b32, nv):
         err = float((o8[pos] - o32[pos]).norm() / o32[pos].norm())
         res = {"value": V * D / (ms / 1e3), "unit": UNIT, "ms_per_uplift": ms, "dtype": "fp8-e4m3",
                "storage_gb": q.numel() / 1e9, "rel_l2_vs_f32_path": err, "err_views": nv,
-               "form": "per-view absmax scale; codes decoded to bf16 per 16-view group, bf16 tensor-core path"}
+               "form": "per-view absmax scale; codes decoded to bf16 in the aggregation's shared memory (d % 16 == 0), bf16 tensor-core path"}
         del q, out, beta, o8
         return res
     except Exception as e:   # reported in the line; the other forms stand

@@ -225,11 +225,13 @@ ludvig_status ludvig_fp8_quantize(const void* feats, int32_t dtype, int32_t n_vi
 
 /* Uplift (Eq. 5) of FP8-E4M3 features: the features are decode(q) * s_v
  * (q: device [n_views, height, width, d] codes, 4-byte aligned; scales:
- * device [n_views] float32, as ludvig_fp8_quantize writes them).  Each
- * group of up to 16 views is decoded to bfloat16 in the scene's workspace
- * (the E4M3 value times s_v, rounded to bfloat16) and uplifted by the
+ * device [n_views] float32, as ludvig_fp8_quantize writes them), each
+ * rounded to bfloat16 (the E4M3 value times s_v) and uplifted by the
  * bfloat16 path, so results carry the bfloat16 bar on the decoded values.
- * out, beta as for ludvig_uplift. */
+ * With d % 16 == 0, 32 <= d <= 512 and q 16-byte aligned the aggregation
+ * reads the codes themselves and decodes them in shared memory (one byte
+ * per value crosses DRAM); otherwise each group of up to 16 views is decoded
+ * into the scene's workspace first.  out, beta as for ludvig_uplift. */
 ludvig_status ludvig_uplift_fp8(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
                                 int32_t width, int32_t height, const uint8_t* q, const float* scales,
                                 int32_t d, float* out, float* beta, void* stream);

@@ -1004,7 +1004,10 @@ ludvig_status uplift_group(ludvig_scene* s, const ludvig_camera* cams, int v0, i
     if (ex.async && ex.group >= 2) LV_CUDA(cudaStreamWaitEvent(sf, s->ev_agg[p], 0));
     static const char* const kFb[2] = {"fp8.bf16.0", "fp8.bf16.1"};
     static const char* const kPad[2] = {"pad.feats.0", "pad.feats.1"};
-    if (src.kind == 2) {
+    // FP8 codes the aggregation decodes itself (no bfloat16 copy in HBM)
+    const bool f8_in_kernel = src.kind == 2 && !padded && tc_e4m3_supported(src.d) &&
+                              (reinterpret_cast<uintptr_t>(src.feats) & 15) == 0;
+    if (src.kind == 2 && !f8_in_kernel) {
         __nv_bfloat16* fb;
         const int64_t total = (int64_t)nv * view_elems;
         LV_TRY(s->ws.get(kFb[p], (size_t)total, &fb));
@@ -1039,8 +1042,8 @@ ludvig_status uplift_group(ludvig_scene* s, const ludvig_camera* cams, int v0, i
         LV_CUDA(cudaEventRecord(s->ev_front[p], sf));
         LV_CUDA(cudaStreamWaitEvent(sa, s->ev_front[p], 0));
     }
-    LV_TRY(tc_aggregate(t, nv, width, height, f, fdt, deff, padded ? pad_num : num, den, s->dstat,
-                        ex.async ? ex.ovf : nullptr, sa));
+    LV_TRY(tc_aggregate(t, nv, width, height, f, f8_in_kernel ? kDtypeE4M3 : fdt, deff, padded ? pad_num : num, den,
+                        s->dstat, ex.async ? ex.ovf : nullptr, sa, f8_in_kernel ? src.scales + v0 : nullptr));
     if (ex.async) LV_CUDA(cudaEventRecord(s->ev_agg[p], sa));
     return LUDVIG_OK;
 }
@@ -1104,7 +1107,8 @@ ludvig_status reserve_async(ludvig_scene* s, int nv, int width, int height, cons
     for (int p = 0; p < 2; ++p) {
         static const char* const kFb[2] = {"fp8.bf16.0", "fp8.bf16.1"};
         static const char* const kPad[2] = {"pad.feats.0", "pad.feats.1"};
-        if (src.kind == 2) LV_TRY(ws.get(kFb[p], 2 * (size_t)npx * src.d, &q));
+        if (src.kind == 2 && (padded || !tc_e4m3_supported(src.d) || (reinterpret_cast<uintptr_t>(src.feats) & 15)))
+            LV_TRY(ws.get(kFb[p], 2 * (size_t)npx * src.d, &q));
         if (padded) LV_TRY(ws.get(kPad[p], (size_t)npx * kPadD * (fdt == LUDVIG_F32 ? 4 : 2), &q));
     }
     return LUDVIG_OK;

@@ -30,6 +30,11 @@ struct TileWeights {
 
 bool tc_supported(int dtype, int d);
 
+// Internal dtype code of FP8-E4M3 codes read by the aggregation (decoded in
+// the kernel: x = decode(q) s_v rounded to bfloat16); d % 16 == 0, 32..512.
+constexpr int kDtypeE4M3 = 2;
+inline bool tc_e4m3_supported(int d) { return d >= 32 && d <= 512 && d % 16 == 0; }
+
 // k_weights over every (view, tile) of a group into the buffers of `parity`
 // (0 or 1, so that a group's weights can be formed while the previous group's
 // are aggregated).  checked: the chunk count is read back (synchronises `st`)
@@ -47,7 +52,8 @@ ludvig_status tc_reserve(Arena& ws, int NT, int nitems, int64_t cap);
 // (k_aggregate_tc).  When the weights overflowed their chunks the kernel adds
 // nothing and sets bit 1 (value 2) of *ovf (ovf may be null for checked runs).
 ludvig_status tc_aggregate(const TileWeights& t, int nv, int width, int height, const void* feats, int dtype,
-                           int d, float* num, float* den, int* status, int* ovf, cudaStream_t st);
+                           int d, float* num, float* den, int* status, int* ovf, cudaStream_t st,
+                           const float* scales = nullptr);
 
 // F_hat = W f for the group (k_render_tc); t must come from a checked tc_weights.
 ludvig_status tc_render(const TileWeights& t, Arena& ws, int nv, int width, int height, const float* f, int d,

@@ -50,6 +50,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 
@@ -373,6 +375,7 @@ struct AggArgs {
     int* ovf;                // set to 2 when they exceeded cap (the launch then adds nothing)
     const uint32_t* plan_off;   // [nitems + 1]: the item's chunks are plan[plan_off[item] ..)
     const int2* plan;           // {chunk, rows} of every non-empty chunk, tile after tile
+    const float* scales;        // FP8 codes: the views' scales (x = decode(q) s_v)
 };
 
 // Feature units (16 KB): 128 channels of 64 pixels (NT = 1: one K atom, two
@@ -382,6 +385,11 @@ struct AggArgs {
 // term sit kBoxBytes apart (the MMA's N = 128).
 // CF selects the float32 layout: 0 = seven feature stages and four epilogue
 // warps, 1 = five stages and eight epilogue warps (more staged rows in flight).
+// With NT = 1, CF = 2 takes FP8-E4M3 codes: each stage's codes (64 pixels x
+// 128 channels, one 8 KB box in its second half) are decoded by 8 converter
+// warps into the bfloat16 unit layout the MMA reads (x its view's scale,
+// rounded to bfloat16), so the codes cross DRAM and the TMA unit at one byte
+// per value.
 template <int NT, int CF>
 struct AggSmem {
     static constexpr int kWA = NT == 1 ? 4 : 2;              // W atom stages (NT x 16 KB each)
@@ -391,8 +399,10 @@ struct AggSmem {
     static constexpr uint32_t kFStage = 16384u;               // one feature unit
     static constexpr int kFS = (NT == 1 || CF == 1) ? 5 : 7;  // 80 KB or 112 KB of stages
     static constexpr int kEH = (NT == 1 || CF == 1) ? 2 : 1;  // epilogue warps per TMEM lane quarter
-    static constexpr int kConv0 = 2 + 4 * kEH;                // first converter warp (NT = 2)
-    static constexpr int kThreads = 32 * (kConv0 + (NT == 2 ? 8 : 0));
+    static constexpr bool kF8 = NT == 1 && CF == 2;          // operands decoded from FP8 codes
+    static constexpr int kConvWarps = (NT == 2 || kF8) ? 8 : 0;
+    static constexpr int kConv0 = 2 + 4 * kEH;                // first converter warp
+    static constexpr int kThreads = 32 * (kConv0 + kConvWarps);
     static constexpr int kPitch = 68;                         // staged row: 64 floats + 16 B pad
     uint8_t W[kWA][NT][kAtomBytes];                           // offset 0 (1024-aligned)
     uint8_t F[kFS][kFStage];
@@ -401,7 +411,7 @@ struct AggSmem {
     uint64_t f_full[kFS], f_conv[kFS], f_empty[kFS];
     uint64_t t_full[kSlots], t_empty[kSlots];
     static constexpr int kQ = 16;                             // chunk queue (producer -> other roles)
-    static constexpr int kConsumers = 1 + 4 * kEH + (NT == 2 ? 8 : 0);   // MMA thread + warps
+    static constexpr int kConsumers = 1 + 4 * kEH + kConvWarps;   // MMA thread + warps
     int4 q[kQ];                                               // chunk, tile, rows (chunk -1: end)
     uint64_t q_full[kQ], q_empty[kQ];
     uint32_t tmem_base;
@@ -413,7 +423,7 @@ constexpr size_t agg_smem_bytes() {
     return sizeof(AggSmem<NT, CF>) + 1024;   // + alignment slack
 }
 static_assert(agg_smem_bytes<1, 0>() <= 232448 && agg_smem_bytes<2, 0>() <= 232448 &&
-                  agg_smem_bytes<2, 1>() <= 232448,
+                  agg_smem_bytes<2, 1>() <= 232448 && agg_smem_bytes<1, 2>() <= 232448,
               "shared memory");
 
 // warp 0 producer, warp 1 MMA, then 4 kEH epilogue warps (8, or 4 for NT = 2
@@ -614,15 +624,22 @@ __global__ void __launch_bounds__(agg_threads<NT, CF>(), 1)
                             ok = false;
                             break;
                         }
-                        mbar_expect_tx(&S.f_full[s], Sm::kFStage);
-                        // kUnitPx pixels (kUnitPx / 16 rows of the tile) x 128 channels:
-                        // boxes of 64 bfloat16 or 32 float32 channels
-                        constexpr int kBoxes = 2 * NT, kBoxCh = 64 / NT;
+                        if constexpr (Sm::kF8) {
+                            // 64 pixels x 128 codes, one box, into the stage's second half
+                            mbar_expect_tx(&S.f_full[s], 8192u);
+                            tma_load_4d_hint(S.F[s] + 8192, &fmap, &S.f_full[s], 128 * un, tx * kTile,
+                                             ty * kTile + 4 * ka, v, fpolicy);
+                        } else {
+                            mbar_expect_tx(&S.f_full[s], Sm::kFStage);
+                            // kUnitPx pixels (kUnitPx / 16 rows of the tile) x 128 channels:
+                            // boxes of 64 bfloat16 or 32 float32 channels
+                            constexpr int kBoxes = 2 * NT, kBoxCh = 64 / NT;
 #pragma unroll
-                        for (int j = 0; j < kBoxes; ++j)
-                            tma_load_4d_hint(S.F[s] + Sm::kBoxBytes * j, &fmap, &S.f_full[s], 128 * un + kBoxCh * j,
-                                             tx * kTile, ty * kTile + 4 * ka + (Sm::kUnitPx / 16) * hf, v,
-                                             fpolicy);
+                            for (int j = 0; j < kBoxes; ++j)
+                                tma_load_4d_hint(S.F[s] + Sm::kBoxBytes * j, &fmap, &S.f_full[s],
+                                                 128 * un + kBoxCh * j, tx * kTile,
+                                                 ty * kTile + 4 * ka + (Sm::kUnitPx / 16) * hf, v, fpolicy);
+                        }
                         ++fc;
                     }
                 }
@@ -633,6 +650,60 @@ __global__ void __launch_bounds__(agg_threads<NT, CF>(), 1)
                     mbar_wait(&S.f_full[u % Sm::kFS], (u / Sm::kFS) & 1u);
                 for (uint32_t u = (wc > (uint32_t)Sm::kWA ? wc - Sm::kWA : 0u); u < wc; ++u)
                     mbar_wait(&S.w_full[u % Sm::kWA], (u / Sm::kWA) & 1u);
+            }
+        }
+    } else if (Sm::kF8 && warp >= Sm::kConv0) {
+        // ---- FP8 decoders: the stage's codes (row p = pixel, 128 bytes = 128
+        // channels at 8 KB + 128 p, 16-byte chunks swizzled by p & 7) -> the
+        // bfloat16 unit: 64-channel box h at 8 KB h, row p, 16-byte chunk c'
+        // (8 channels) at ((c' ^ (p & 7)) << 4).  Warp cw owns rows 8 cw .. 8 cw
+        // + 7; lane: row 8 cw + lane / 8 + 4 i, code chunk c = lane % 8
+        // (channels 16 c ..); the codes of both rows are read before the warp
+        // overwrites them (box 1 shares their bytes).
+        const int cw = warp - Sm::kConv0, c = lane & 7;
+        uint32_t fc = 0, qc = 0;
+        bool ok = true;
+        for (;;) {
+            int4 e;
+            if (!ok || *abort_flag || !queue_next(S, abort_flag, a.status, qc, e, false) || e.x < 0) break;
+            const float sv = a.scales[e.y / a.ntiles];   // the chunk's view
+            for (int un = 0; un < 4 * U; ++un) {
+                const uint32_t s = fc % Sm::kFS;
+                if (!agg_wait(abort_flag, a.status, &S.f_full[s], (fc / Sm::kFS) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t* base = S.F[s];
+                uint4 code[2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int p = 8 * cw + (lane >> 3) + 4 * i;
+                    code[i] = *reinterpret_cast<const uint4*>(base + 8192 + p * 128 + ((c ^ (p & 7)) << 4));
+                }
+                __syncwarp();   // the warp's rows are read before any is overwritten
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int p = 8 * cw + (lane >> 3) + 4 * i;
+                    const uint32_t w[4] = {code[i].x, code[i].y, code[i].z, code[i].w};
+                    uint32_t o[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {   // codes 2k, 2k + 1 -> one word of two bfloat16
+                        const uint32_t pair = (w[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+                        const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)pair, __NV_E4M3);
+                        const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&hr));
+                        const __nv_bfloat162 b = __floats2bfloat162_rn(f.x * sv, f.y * sv);
+                        o[k] = *reinterpret_cast<const uint32_t*>(&b);
+                    }
+                    const int h = c >> 2, c0 = 2 * (c & 3);
+                    *reinterpret_cast<uint4*>(base + 8192 * h + p * 128 + ((c0 ^ (p & 7)) << 4)) =
+                        make_uint4(o[0], o[1], o[2], o[3]);
+                    *reinterpret_cast<uint4*>(base + 8192 * h + p * 128 + (((c0 + 1) ^ (p & 7)) << 4)) =
+                        make_uint4(o[4], o[5], o[6], o[7]);
+                }
+                fence_proxy_async();   // generic writes, read by the tensor core
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.f_conv[s]);
+                ++fc;
             }
         }
     } else if (NT == 2 && warp >= Sm::kConv0) {
@@ -721,7 +792,7 @@ __global__ void __launch_bounds__(agg_threads<NT, CF>(), 1)
                             break;
                         }
                         const uint32_t s = fc % Sm::kFS;
-                        if (!agg_wait(abort_flag, a.status, NT == 2 ? &S.f_conv[s] : &S.f_full[s],
+                        if (!agg_wait(abort_flag, a.status, (NT == 2 || Sm::kF8) ? &S.f_conv[s] : &S.f_full[s],
                                       (fc / Sm::kFS) & 1u)) {
                             ok = false;
                             break;
@@ -1282,12 +1353,14 @@ ludvig_status encode(CUtensorMap* map, CUtensorMapDataType type, const void* bas
 // rows either way), zero fill outside the image and past d.
 ludvig_status make_feature_map(CUtensorMap* map, const void* feats, int dtype, int nv, int width, int height,
                                int d) {
-    const cuuint64_t es = dtype == LUDVIG_F32 ? 4 : 2;
+    const cuuint64_t es = dtype == LUDVIG_F32 ? 4 : (dtype == kDtypeE4M3 ? 1 : 2);
     cuuint64_t dims[4] = {(cuuint64_t)d, (cuuint64_t)width, (cuuint64_t)height, (cuuint64_t)nv};
     cuuint64_t strides[3] = {(cuuint64_t)d * es, (cuuint64_t)width * d * es, (cuuint64_t)height * width * d * es};
     cuuint32_t box[4] = {(cuuint32_t)(128 / es), 16, dtype == LUDVIG_F32 ? 2u : 4u, 1};
-    return encode(map, dtype == LUDVIG_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-                  feats, 4, dims, strides, box);
+    const CUtensorMapDataType t = dtype == LUDVIG_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                  : dtype == kDtypeE4M3 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                                        : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    return encode(map, t, feats, 4, dims, strides, box);
 }
 
 // Tensor map over rendered maps [nv, H, W, d] float32 for TMA stores: box of
@@ -1475,7 +1548,8 @@ ludvig_status tc_weights(const GroupLists& L, int nv, int width, int height, int
 }
 
 ludvig_status tc_aggregate(const TileWeights& t, int nv, int width, int height, const void* feats, int dtype,
-                           int d, float* num, float* den, int* status, int* ovf, cudaStream_t st) {
+                           int d, float* num, float* den, int* status, int* ovf, cudaStream_t st,
+                           const float* scales) {
     const int NT = dtype == LUDVIG_F32 ? 2 : 1;
     const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
     const int nitems = nv * TX * TY;
@@ -1505,8 +1579,10 @@ ludvig_status tc_aggregate(const TileWeights& t, int nv, int width, int height, 
     g.ovf = ovf;
     g.plan_off = t.plan_off;
     g.plan = t.plan;
+    g.scales = scales;
     const int grid = std::min(sms, nitems);
     StageScope agg_scope(LUDVIG_STAGE_AGGREGATE, st);
+    if (dtype == kDtypeE4M3) return dispatch_agg_cf<1, 2>(g, maps, grid, st);
     if (NT == 2) return dispatch_agg<2>(g, maps, grid, st);
     return dispatch_agg<1>(g, maps, grid, st);
 }

@@ -3,7 +3,8 @@ scales and every code are bit-exact against the oracle's quantiser (float32
 and bfloat16 inputs, an all-zero view, totals that are not a multiple of 4);
 the uplift of the codes meets the bfloat16 bar (1e-2 relative L2) against
 the oracle's float64 uplift of the decoded values, on the tensor-core path
-(D = 48) and the padded one (D = 3)."""
+(D = 48) and the padded one (D = 3); and the codes decoded inside the
+aggregation give the bfloat16 uplift of the same decoded values."""
 import numpy as np
 import pytest
 import torch
@@ -72,3 +73,25 @@ def test_fp8_arguments():
     assert (out == 0).all()
     q0, s0 = ludvig.fp8_quantize(torch.zeros((0, 4), device="cuda"))
     assert q0.numel() == 0 and s0.numel() == 0
+
+
+@pytest.mark.parametrize("d,views", [(48, 3), (64, 20), (40, 3), (512, 2)])
+def test_uplift_fp8_equals_bf16_uplift_of_the_decoded_values(d, views):
+    """The aggregation decodes the codes itself when d % 16 == 0 (d = 48, 64,
+    512; 20 views: two groups, so the per-view scales are indexed across
+    groups); d = 40 takes the decode pass.  Either way the result is the
+    bfloat16 uplift of x = decode(q) s_v rounded to bfloat16, here decoded by
+    torch's float8_e4m3fn (float32 product, then bfloat16), to float32
+    rounding (only the order of the atomic sums differs)."""
+    wl = inputs.small_field_workload(n=8000, views=views, d=d, width=61, height=45)
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    F = torch.stack([wl.features(v, device="cuda") for v in range(views)]).contiguous()
+    q, s = ludvig.fp8_quantize(F)
+    out, beta = ludvig.uplift_fp8(sc, wl.cams.params, wl.cams.width, wl.cams.height, q, s)
+    X = (q.view(torch.float8_e4m3fn).float() * s.view(-1, 1, 1, 1)).to(torch.bfloat16).contiguous()
+    ob, bb = ludvig.uplift(sc, wl.cams.params, wl.cams.width, wl.cams.height, X)
+    torch.cuda.synchronize()
+    e = rel_l2(out.cpu().numpy(), ob.cpu().numpy())
+    print(f"fp8 d={d}, {views} views: rel L2 vs the bfloat16 uplift of the decoded values {e:.2e}")
+    assert e <= 1e-6
+    assert rel_l2(beta.cpu().numpy(), bb.cpu().numpy()) <= 1e-6
