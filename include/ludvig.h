@@ -60,7 +60,7 @@
 extern "C" {
 #endif
 
-#define LUDVIG_ABI_VERSION 9
+#define LUDVIG_ABI_VERSION 10
 
 typedef enum {
     LUDVIG_OK = 0,
@@ -158,6 +158,13 @@ ludvig_status ludvig_scene_destroy(ludvig_scene_t scene);
 
 /* Number of Gaussians of a scene. */
 int64_t ludvig_scene_size(ludvig_scene_t scene);
+
+/* Device bytes the scene's workspace holds now (it grows to the largest call
+ * the scene has run); -1 for a NULL scene.  Safe to call from any thread,
+ * also while a call on the scene runs (the figure may then be about to grow):
+ * a server's admission can charge its resident scenes' workspaces against a
+ * memory budget. */
+int64_t ludvig_scene_workspace_bytes(ludvig_scene_t scene);
 
 /* Uplifting, accumulation half (Sec. 3.2, Eq. 3; matrix form Eq. 5):
  *   num[i,:] += sum_{v,p} w_i(v,p) F_v[p,:]      den[i] += sum_{v,p} w_i(v,p)
@@ -443,6 +450,11 @@ ludvig_status ludvig_graph_destroy(ludvig_graph_t graph);
 
 /* Number of stored (directed) edges of the graph. Synchronises nothing. */
 int64_t ludvig_graph_nnz(ludvig_graph_t graph);
+
+/* Device bytes the graph's workspace holds now (diffusion scratch, the sliced
+ * matrix copy); -1 for a NULL graph.  Same rules as
+ * ludvig_scene_workspace_bytes. */
+int64_t ludvig_graph_workspace_bytes(ludvig_graph_t graph);
 
 /* Copies the CSR arrays to device buffers: row_ptr [n+1] int64, col [nnz]
  * int32, val [nnz] float32 (columns sorted within each row). */

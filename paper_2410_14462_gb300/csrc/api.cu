@@ -93,6 +93,7 @@ void Arena::release() {
         if (kv.second.ptr) cudaFreeHost(kv.second.ptr);
     dev_.clear();
     host_.clear();
+    bytes_.store(0);
 }
 
 ludvig_status Arena::get(const char* name, size_t bytes, void** out) {
@@ -103,6 +104,7 @@ ludvig_status Arena::get(const char* name, size_t bytes, void** out) {
             // a kernel queued earlier may still read the old buffer
             LV_CUDA(cudaDeviceSynchronize());
             LV_CUDA(cudaFree(b.ptr));
+            bytes_.fetch_sub(b.bytes);
             b.ptr = nullptr;
             b.bytes = 0;
         }
@@ -126,6 +128,7 @@ ludvig_status Arena::get(const char* name, size_t bytes, void** out) {
         } else {
             b.bytes = want;
         }
+        bytes_.fetch_add(b.bytes);
     }
     *out = b.ptr;
     return LUDVIG_OK;
@@ -212,6 +215,8 @@ extern "C" ludvig_status ludvig_scene_destroy(ludvig_scene_t s) {
 }
 
 extern "C" int64_t ludvig_scene_size(ludvig_scene_t s) { return s ? s->n : -1; }
+
+extern "C" int64_t ludvig_scene_workspace_bytes(ludvig_scene_t s) { return s ? (int64_t)s->ws.device_bytes() : -1; }
 
 namespace ludvig {
 namespace {

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -86,7 +87,12 @@ class Arena {
     void swap(Arena& o) noexcept {
         dev_.swap(o.dev_);
         host_.swap(o.host_);
+        const size_t a = bytes_.load(), b = o.bytes_.load();
+        bytes_.store(b);
+        o.bytes_.store(a);
     }
+    // Device bytes held (readable from any thread while another grows it).
+    size_t device_bytes() const { return bytes_.load(std::memory_order_relaxed); }
     // Returns a device buffer of at least `bytes` bytes (256-byte aligned).
     ludvig_status get(const char* name, size_t bytes, void** out);
     template <class T>
@@ -105,6 +111,7 @@ class Arena {
         size_t bytes = 0;
     };
     std::unordered_map<std::string, Buf> dev_, host_;
+    std::atomic<size_t> bytes_{0};
 };
 
 // Device-side sizes of one group of views of an asynchronous uplift, copied

@@ -861,6 +861,8 @@ extern "C" ludvig_status ludvig_graph_destroy(ludvig_graph_t g) {
 
 extern "C" int64_t ludvig_graph_nnz(ludvig_graph_t g) { return g ? g->nnz : -1; }
 
+extern "C" int64_t ludvig_graph_workspace_bytes(ludvig_graph_t g) { return g ? (int64_t)g->ws.device_bytes() : -1; }
+
 extern "C" ludvig_status ludvig_graph_export(ludvig_graph_t g, int64_t* row_ptr, int32_t* col, float* val,
                                              void* stream) {
     LV_ARG(g != nullptr, "graph is NULL");

@@ -37,6 +37,7 @@ SIGNATURES = {
     "ludvig_sync": (_I32, [_P]),
     "ludvig_scene_destroy": (_I32, [_P]),
     "ludvig_scene_size": (_I64, [_P]),
+    "ludvig_scene_workspace_bytes": (_I64, [_P]),
     "ludvig_uplift_accumulate": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
     "ludvig_uplift_finalize": (_I32, [_I64, _I32, _P, _P, _P, _P, _P]),
     "ludvig_uplift": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
@@ -69,6 +70,7 @@ SIGNATURES = {
     "ludvig_graph_build": (_I32, [_P, _I32, _P, _I32, _F, _F, _I32, _P, ctypes.POINTER(_P)]),
     "ludvig_graph_destroy": (_I32, [_P]),
     "ludvig_graph_nnz": (_I64, [_P]),
+    "ludvig_graph_workspace_bytes": (_I64, [_P]),
     "ludvig_graph_export": (_I32, [_P, _P, _P, _P, _P]),
     "ludvig_diffuse": (_I32, [_P, _P, _I32, _I32, _P, _P]),
     "ludvig_diffuse_noalloc": (_I32, [_P, _P, _I32, _I32, _P, _P]),
@@ -190,6 +192,10 @@ class Scene:
     def sync(self):
         """ludvig_sync: wait for and complete the scene's last asynchronous uplift."""
         _check(load().ludvig_sync(self._h), "ludvig_sync")
+
+    def workspace_bytes(self) -> int:
+        """ludvig_scene_workspace_bytes: device bytes of the scene's workspace."""
+        return int(load().ludvig_scene_workspace_bytes(self._h))
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -529,6 +535,10 @@ class Graph:
     def nnz(self) -> int:
         return int(load().ludvig_graph_nnz(self._h))
 
+    def workspace_bytes(self) -> int:
+        """ludvig_graph_workspace_bytes: device bytes of the graph's workspace."""
+        return int(load().ludvig_graph_workspace_bytes(self._h))
+
     def export(self, stream=None):
         L = load()
         rp = torch.empty((self.n + 1,), dtype=torch.int64, device="cuda")
@@ -538,10 +548,19 @@ class Graph:
                "ludvig_graph_export")
         return rp, col[: self.nnz], val[: self.nnz]
 
+    def _diffusion_args(self, x0: torch.Tensor, out):
+        """The C entry points cannot see buffer sizes: x0 must be [n] or
+        [n, dx] and out the same shape, both contiguous float32 on the GPU."""
+        if x0.dim() not in (1, 2) or int(x0.shape[0]) != self.n:
+            raise LudvigError(f"x0 must be [{self.n}] or [{self.n}, dx], got {tuple(x0.shape)}")
+        if out is not None and tuple(out.shape) != tuple(x0.shape):
+            raise LudvigError(f"out must have the shape of x0 {tuple(x0.shape)}, got {tuple(out.shape)}")
+        return 1 if x0.dim() == 1 else int(x0.shape[1])
+
     def diffuse(self, x0: torch.Tensor, iters: int, out=None, stream=None):
         L = load()
         x0 = x0.contiguous()
-        dx = 1 if x0.dim() == 1 else int(x0.shape[1])
+        dx = self._diffusion_args(x0, out)
         if out is None:
             out = torch.empty_like(x0)
         _check(L.ludvig_diffuse(self._h, _dev(x0, torch.float32, "x0"), dx, iters,
@@ -552,7 +571,8 @@ class Graph:
         """ludvig_diffuse_noalloc: the same diffusion with the library's static
         scratch; `out` must be supplied (nothing is allocated)."""
         L = load()
-        dx = 1 if x0.dim() == 1 else int(x0.shape[1])
+        x0 = x0.contiguous()
+        dx = self._diffusion_args(x0, out)
         _check(L.ludvig_diffuse_noalloc(self._h, _dev(x0, torch.float32, "x0"), dx, iters,
                                         _dev(out, torch.float32, "out"), _stream(stream)),
                "ludvig_diffuse_noalloc")

@@ -12,14 +12,21 @@ Scheduling (continuous batching):
   own workspace, since a workspace serves one stream at a time); every
   replica has a worker thread and a CUDA stream, so requests on any scene
   overlap on the GPU as slots free up;
-* a request is admitted when its outputs fit the device-memory budget
-  (outputs are per-request buffers; the resident scenes, graphs, pools and
-  workspaces are outside the budget); a request too large for the budget
-  alone is rejected rather than run;
+* the device-memory budget covers what serving adds to the caller's
+  resident data: the replicas the server makes (52 bytes per Gaussian), the
+  workspaces of every replica and graph (read live with
+  ``ludvig_scene_workspace_bytes`` / ``ludvig_graph_workspace_bytes``: a
+  workspace grows during a call on it, up to the largest request it has
+  served) and the outputs of the requests in flight.  A request is admitted
+  when its outputs fit beside the others and the workspaces; one that could
+  not fit even alone is rejected rather than run.  The caller's scenes,
+  graphs and feature pools are outside the budget;
 * a scene's graph has one workspace, so its diffusions run one at a time
   (a lock held from the launch until the stream has finished them);
 * requests arrive at their own times (``run`` replays an arrival schedule);
-  latency = completion - arrival, including queueing.
+  latency = completion - arrival, including queueing; each result records the
+  queue depth (requests released but not started, itself included) at its
+  arrival.
 
 The library calls release the GIL (ctypes), so the workers' GPU work and
 host-side waits overlap; each worker synchronises only its own stream.
@@ -56,6 +63,7 @@ class Result:
     error: str = ""
     out: object = None      # [N, D] features (when kept)
     g: object = None        # diffused vector (when kept)
+    depth: int = 0          # requests queued (released, not started) at its arrival, itself included
 
     @property
     def latency(self) -> float:
@@ -67,11 +75,15 @@ def request_bytes(n: int, d: int) -> int:
     return 4 * n * (d + 1) + 3 * 4 * n
 
 
+SCENE_BYTES_PER_GAUSSIAN = 52   # a scene's device copy: float4 geo + float4/float2 covariance + float3 mean
+
+
 class Server:
     """Resident scenes (``ludvig.Scene``), one diffusion graph per scene (or
     None), feature pools {d: tensor [V, H, W, d] on the device}, the pool's
-    cameras [V, 16] and image size, an output budget in bytes, and the number
-    of slots (concurrent requests) per scene."""
+    cameras [V, 16] and image size, a device-memory budget in bytes for the
+    replicas, workspaces and outputs, and the number of slots (concurrent
+    requests) per scene."""
 
     def __init__(self, scenes, graphs, pools, cams, width, height, budget_bytes, slots: int = 2):
         import torch
@@ -92,6 +104,19 @@ class Server:
         self._lock = threading.Condition()
         self._in_use = 0
         self._new_stream = torch.cuda.Stream   # one per worker thread
+        if self.resident_bytes() > self.budget:
+            self.close()
+            raise ValueError("the scene replicas alone exceed the memory budget")
+
+    def resident_bytes(self) -> int:
+        """Device bytes serving holds besides the outputs: the replicas this
+        server made and the workspaces of every replica and graph, now."""
+        total = 0
+        for reps in self.replicas:
+            total += sum(SCENE_BYTES_PER_GAUSSIAN * r.n for r in reps[1:])
+            total += sum(max(r.workspace_bytes(), 0) for r in reps)
+        total += sum(max(g.workspace_bytes(), 0) for g in self.graphs if g is not None)
+        return total
 
     def close(self):
         """Free the replicas this server made (not the caller's scenes)."""
@@ -102,8 +127,11 @@ class Server:
 
     # ---- admission
     def _admit(self, nbytes: int, deadline: float) -> bool:
+        """Charges a request's outputs once they fit beside the outputs in
+        flight and the resident bytes (re-read while waiting: workspaces
+        grow); False at the deadline."""
         with self._lock:
-            while self._in_use + nbytes > self.budget:
+            while self._in_use + self.resident_bytes() + nbytes > self.budget:
                 left = deadline - time.perf_counter()
                 if left <= 0:
                     return False
@@ -123,7 +151,7 @@ class Server:
         pool = self.pools[req.d]
         nbytes = request_bytes(sc.n, req.d)
         start = time.perf_counter() - t0
-        if nbytes > self.budget:
+        if nbytes + self.resident_bytes() > self.budget:
             return Result(req.rid, req.arrival, start, start, False, "larger than the memory budget")
         if not self._admit(nbytes, time.perf_counter() + 60.0):
             return Result(req.rid, req.arrival, start, time.perf_counter() - t0, False, "admission timed out")
@@ -145,19 +173,26 @@ class Server:
             return Result(req.rid, req.arrival, start, done, True,
                           out=out if req.keep_output else None, g=g if req.keep_output else None)
         except Exception as e:   # the request fails, the server goes on
-            st.synchronize()
-            return Result(req.rid, req.arrival, start, time.perf_counter() - t0, False, str(e))
+            msg = str(e)
+            try:                 # its outputs are released only once the stream is idle
+                st.synchronize()
+            except Exception as e2:
+                msg += f"; stream: {e2}"
+            return Result(req.rid, req.arrival, start, time.perf_counter() - t0, False, msg)
         finally:
             self._release(nbytes)
 
     # ---- replay an arrival schedule
     def run(self, requests: list[Request]) -> list[Result]:
-        """Serve the requests, each released at its arrival time; returns the
-        results in request order."""
+        """Serve the requests, each released at its arrival time; returns one
+        result per request, in request order (a request the workers did not
+        finish is reported as failed)."""
         t0 = time.perf_counter()
         queues = [[] for _ in self.replicas]
         cond = threading.Condition()
         results = {}
+        depth_at = {}
+        queued = [0]
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
         closed = [False]
 
@@ -170,7 +205,14 @@ class Server:
                     if not queues[s] and closed[0]:
                         return
                     _, _, req = heapq.heappop(queues[s])
-                results[req.rid] = self._execute(req, sc, st, t0)
+                    queued[0] -= 1
+                try:
+                    r = self._execute(req, sc, st, t0)
+                except Exception as e:   # a failure outside the request's own handling
+                    now = time.perf_counter() - t0
+                    r = Result(req.rid, req.arrival, now, now, False, f"worker: {e}")
+                r.depth = depth_at.get(req.rid, 0)
+                results[req.rid] = r
 
         threads = [threading.Thread(target=worker, args=(s, sc), daemon=True)
                    for s, reps in enumerate(self.replicas) for sc in reps]
@@ -182,13 +224,17 @@ class Server:
                 time.sleep(wait)
             with cond:
                 heapq.heappush(queues[req.scene], (req.arrival, req.rid, req))
+                queued[0] += 1
+                depth_at[req.rid] = queued[0]
                 cond.notify_all()
         with cond:
             closed[0] = True
             cond.notify_all()
         for t in threads:
             t.join()
-        return [results[r.rid] for r in requests]
+        end = time.perf_counter() - t0
+        return [results.get(r.rid) or Result(r.rid, r.arrival, end, end, False, "not served",
+                                             depth=depth_at.get(r.rid, 0)) for r in requests]
 
 
 def poisson_requests(n: int, rate: float, n_scenes: int, pool_views: int, dims, seed: int,
@@ -210,11 +256,14 @@ def latency_summary(results: list[Result]) -> dict:
     ok = [r for r in results if r.ok]
     lat = np.array([r.latency for r in ok]) * 1e3
     span = max(r.done for r in results) - min(r.arrival for r in results) if results else 0.0
+    depth = np.array([r.depth for r in results])
     return {"requests": len(results), "served": len(ok), "rejected": len(results) - len(ok),
             "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
             "mean_ms": float(lat.mean()) if lat.size else None,
-            "throughput_req_s": len(ok) / span if span > 0 else None}
+            "throughput_req_s": len(ok) / span if span > 0 else None,
+            "queue_depth_p50": float(np.percentile(depth, 50)) if depth.size else None,
+            "queue_depth_max": int(depth.max()) if depth.size else None}
 
 
 @dataclasses.dataclass

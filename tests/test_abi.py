@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version(lib):
-    assert lib.ludvig_abi_version() == 9
+    assert lib.ludvig_abi_version() == 10
 
 
 def test_argument_errors_are_synchronous(lib):
@@ -54,6 +54,8 @@ def test_argument_errors_are_synchronous(lib):
     assert lib.ludvig_uplift_finalize(-1, 4, None, None, None, None, None) == 1
     assert lib.ludvig_scene_size(None) == -1
     assert lib.ludvig_graph_nnz(None) == -1
+    assert lib.ludvig_scene_workspace_bytes(None) == -1
+    assert lib.ludvig_graph_workspace_bytes(None) == -1
     assert lib.ludvig_scene_destroy(None) == 0
 
 
@@ -77,3 +79,20 @@ def test_batch_argument_errors_are_synchronous(lib):
     assert lib.ludvig_uplift_batch(jobs, 2, 2, status, None) == 1
     assert b"job 1: scene is NULL" in lib.ludvig_last_error()
     assert ctypes.sizeof(Job) == 64                                    # matches ludvig_uplift_job
+
+
+def test_diffusion_wrappers_check_shapes_before_launch(lib):
+    """Graph.diffuse and Graph.diffuse_noalloc reject an x0 whose first
+    dimension is not the graph's n, an x0 of rank 3 and an out of another
+    shape, before any library call (the handle here is never used)."""
+    import torch
+    g = ludvig.Graph.__new__(ludvig.Graph)
+    g.n = 10
+    g._h = None
+    ok = torch.zeros(10, 3)
+    for x0, out in ((torch.zeros(9), None), (torch.zeros(10, 2, 2), None), (ok, torch.zeros(10, 2)),
+                    (torch.zeros(10), torch.zeros(10, 1))):
+        with pytest.raises(ludvig.LudvigError, match="x0|out"):
+            g.diffuse(x0, 3, out=out)
+        with pytest.raises(ludvig.LudvigError, match="x0|out"):
+            g.diffuse_noalloc(x0, 3, out if out is not None else torch.zeros_like(x0))

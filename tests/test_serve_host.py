@@ -1,7 +1,9 @@
 """Host logic of the serving and batched forms (no GPU): the seeded arrival
 stream and job recipe have the stated distributions, admission never lets the
-admitted outputs exceed the budget while several workers contend for it, and
-the latency summary reads the percentiles of completion - arrival."""
+admitted outputs and the resident workspaces exceed the budget while several
+workers contend for it, the scheduler returns one result per request (also
+when an executor raises) with the queue depth at its arrival, and the latency
+summary reads the percentiles of completion - arrival."""
 import math
 import threading
 import time
@@ -47,6 +49,7 @@ def test_admission_never_exceeds_budget():
     srv.budget = 1000
     srv._lock = threading.Condition()
     srv._in_use = 0
+    srv.resident_bytes = lambda: 0
     peak = [0]
     seen = threading.Lock()
     rng = np.random.default_rng(0)
@@ -71,6 +74,63 @@ def test_admission_never_exceeds_budget():
     srv._in_use = 900
     assert not srv._admit(200, time.perf_counter() + 0.1)
     assert srv._in_use == 900
+
+
+class _FakeScene:
+    def __init__(self, n, ws):
+        self.n, self.ws = n, ws
+
+    def workspace_bytes(self):
+        return self.ws
+
+
+def test_admission_counts_replicas_and_workspaces():
+    """The resident figure is the server's own replicas (52 B per Gaussian;
+    the caller's scene, first in each list, is not charged) plus every
+    replica's and graph's workspace, read live: a request is admitted only
+    beside them, and one that cannot fit even alone is rejected at once."""
+    srv = serve.Server.__new__(serve.Server)
+    srv.replicas = [[_FakeScene(10, 100), _FakeScene(10, 50)], [_FakeScene(5, 0)]]
+    srv.graphs = [_FakeScene(0, 30), None]
+    assert srv.resident_bytes() == 52 * 10 + 100 + 50 + 30
+    srv.budget = srv.resident_bytes() + 400
+    srv._lock = threading.Condition()
+    srv._in_use = 0
+    assert srv._admit(300, time.perf_counter() + 1.0)
+    assert not srv._admit(200, time.perf_counter() + 0.1)            # 300 + 200 > 400 beside the workspaces
+    srv._release(300)
+    srv.replicas[0][1].ws += 250                                      # a workspace grew
+    assert not srv._admit(200, time.perf_counter() + 0.1)
+    assert srv._admit(150, time.perf_counter() + 0.1)
+    srv._release(150)
+    srv.pools = {4: None}
+    res = srv._execute(serve.Request(0, 0.0, 0, 4, 0, 1), srv.replicas[0][0], None, time.perf_counter())
+    assert not res.ok and "budget" in res.error                       # request_bytes(10, 4) alone does not fit
+
+
+def test_one_result_per_request_and_queue_depth():
+    """An executor that raises for some requests still yields one result per
+    request, in order, the failures marked; with one slot and three requests
+    arriving together the queue depths at arrival are 1, 2, 3."""
+    srv = serve.Server.__new__(serve.Server)
+    srv.replicas = [["a0"]]
+    srv._new_stream = lambda: None
+
+    def fake_execute(req, sc, st, t0):
+        time.sleep(0.02)
+        if req.rid == 1:
+            raise RuntimeError("planted")
+        now = time.perf_counter() - t0
+        return serve.Result(req.rid, req.arrival, now, now, True)
+
+    srv._execute = fake_execute
+    reqs = [serve.Request(i, 0.0, 0, 8, 0, 1) for i in range(3)]
+    res = srv.run(reqs)
+    assert [r.rid for r in res] == [0, 1, 2]
+    assert [r.ok for r in res] == [True, False, True] and "planted" in res[1].error
+    assert sorted(r.depth for r in res) == [1, 2, 3]
+    s = serve.latency_summary(res)
+    assert s["served"] == 2 and s["rejected"] == 1 and s["queue_depth_max"] == 3 and s["queue_depth_p50"] == 2
 
 
 def test_latency_summary():

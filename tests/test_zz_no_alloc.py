@@ -1,11 +1,12 @@
 """ludvig_diffuse_noalloc: the graph diffusion for callers that must not
 allocate device memory (a warm request loop under a no-allocation policy, a
-process whose device memory belongs to another allocator, work recorded into a
-CUDA graph).  Its scratch is the library's static device memory, so the call
-is checked against the allocating ludvig_diffuse on the same inputs, twice in a
-row (the second call must not see the first call's leftovers), for one and for
-several columns, and its size limit is checked.  Collected last on purpose:
-the file name sorts after every other test file."""
+process whose device memory belongs to another allocator).  Its scratch is the
+library's static device memory, so the call is checked against the
+allocating ludvig_diffuse on the same inputs, twice in a row (the second call
+must not see the first call's leftovers), for one and for several columns; a
+warm call leaves the device's free memory, torch's pool and the graph's
+workspace unchanged; and its size limit is checked.  Collected last on
+purpose: the file name sorts after every other test file."""
 import ctypes
 
 import numpy as np
@@ -55,6 +56,26 @@ def test_noalloc_matches_allocating_call_twice(graph):
         torch.cuda.synchronize()
         assert _rel(got, ref) <= 1e-5
         assert (got[:, 1] == 0).all()
+
+
+def test_noalloc_warm_call_allocates_nothing(graph):
+    s, sc, g = graph
+    x = torch.from_numpy((s.means[:, 1] > 0.0).astype(np.float32)).cuda()
+    X = torch.stack([x, 1.0 - x], 1).contiguous()
+    out, OUT = torch.empty_like(x), torch.empty_like(X)
+    g.diffuse_noalloc(x, 20, out)                      # first call: kernels loaded, nothing else
+    g.diffuse_noalloc(X, 20, OUT)
+    torch.cuda.synchronize()
+    before = (torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved(), g.workspace_bytes(),
+              sc.workspace_bytes())
+    for _ in range(3):
+        g.diffuse_noalloc(x, 20, out)
+        g.diffuse_noalloc(X, 20, OUT)
+    torch.cuda.synchronize()
+    after = (torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved(), g.workspace_bytes(),
+             sc.workspace_bytes())
+    print(f"free bytes, torch reserved, graph and scene workspace: {before} -> {after}")
+    assert after == before
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(graph):
