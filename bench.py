@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form line")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-form line")
     ap.add_argument("--profile-case", default=None,
-                    choices=["tc2views", "render2views", "render16views", "batch8"],
+                    choices=["tc2views", "render2views", "render16views", "uplift16views", "batch8"],
                     help="run a small fixed case for an ncu capture and exit (no JSON line)")
     return ap.parse_args()
 
@@ -125,6 +125,105 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# ---------------------------------------------------------------- CPU oracle timing
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def oracle_view_seconds(wl, views, nthreads):
+    """Seconds the oracle takes to uplift each of `views` (every Gaussian, all
+    D channels); the view's features and the float64 accumulators are made
+    outside the timed call."""
+    import oracle
+    oracle.build()
+    out = []
+    for v in views:
+        F = wl.features(v).numpy()
+        num = np.zeros((wl.scene.n, wl.d))
+        den = np.zeros(wl.scene.n)
+        t0 = time.perf_counter()
+        oracle.view_uplift(wl.scene, wl.cams.params[v], wl.cams.width, wl.cams.height, F, num, den,
+                           nthreads=nthreads)
+        out.append(time.perf_counter() - t0)
+    return out
+
+
+def _cpulist(text):
+    cpus = set()
+    for part in text.strip().split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus
+
+
+def gpu_local_cpus(gpu_uuid):
+    """(NUMA node, CPU set) of the host memory next to the GPU, read from the
+    sysfs entry of its PCI device; (None, None) when unknown."""
+    try:
+        bus = subprocess.run(["nvidia-smi", "--query-gpu=pci.bus_id", "--format=csv,noheader", "-i", gpu_uuid],
+                             capture_output=True, text=True, timeout=30).stdout.strip()
+        dom, rest = bus.split(":", 1)
+        dev = f"/sys/bus/pci/devices/{dom[-4:].lower()}:{rest.lower()}"
+        node = int(open(dev + "/numa_node").read())
+        cpus = _cpulist(open(dev + "/local_cpulist").read())
+        return (node if node >= 0 else None), (cpus or None)
+    except (OSError, ValueError, subprocess.SubprocessError):
+        return None, None
+
+
+def pinned_near(shape, dtype, cpus):
+    """A page-locked host tensor whose pages are placed from `cpus` (the
+    calling thread runs there while the pages are allocated and pinned)."""
+    import torch
+    old = os.sched_getaffinity(0)
+    use = (cpus & old) or cpus if cpus else None
+    if use:
+        os.sched_setaffinity(0, use)
+    try:
+        t = torch.empty(shape, dtype=dtype, pin_memory=True)
+    finally:
+        if use:
+            os.sched_setaffinity(0, old)
+    return t
+
+
+def copy_rates(host, dev):
+    """Measured host->device and device->host GB/s of one copy between a
+    pinned host tensor and a device tensor of the same size (CUDA events)."""
+    import torch
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    dev.copy_(host, non_blocking=True)        # warm
+    torch.cuda.synchronize()
+    e[0].record()
+    dev.copy_(host, non_blocking=True)
+    e[1].record()
+    e[2].record()
+    host.copy_(dev, non_blocking=True)
+    e[3].record()
+    torch.cuda.synchronize()
+    nbytes = host.numel() * host.element_size()
+    return nbytes / (e[0].elapsed_time(e[1]) / 1e3) / 1e9, nbytes / (e[2].elapsed_time(e[3]) / 1e3) / 1e9
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -132,60 +231,46 @@ def run_reference(args):
         return 0
     import oracle
     wl = workload(args.workload)
-    oracle.build()
-    cams = wl.cams
     nthreads = oracle.default_threads()
-    # bounded sample per step: one view, every Gaussian, all D channels
-    times = []
-    feats = {}
-    for s in range(args.warmup + args.steps):
-        v = s % cams.v
-        if v not in feats:
-            feats[v] = wl.features(v).numpy()
-        num = np.zeros((wl.scene.n, wl.d))
-        den = np.zeros(wl.scene.n)
-        t0 = time.perf_counter()
-        oracle.view_uplift(wl.scene, cams.params[v], cams.width, cams.height, feats[v], num, den,
-                           nthreads=nthreads)
-        dt = time.perf_counter() - t0
-        if s >= args.warmup:
-            times.append(dt)
-    t = float(np.mean(times))
+    # bounded sample per step: one view, every Gaussian, all D channels; the
+    # warm-up steps are views too, untimed
+    secs = oracle_view_seconds(wl, [s % wl.cams.v for s in range(args.warmup + args.steps)], nthreads)
+    t = float(np.mean(secs[args.warmup:]))
     value = wl.d / t
+    sample = (f"views {args.warmup}-{args.warmup + args.steps - 1} of {wl.cams.v}, one per step, after "
+              f"{args.warmup} untimed (D={wl.d}, N={wl.scene.n})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": wl.name, "sample": "1 view per step (uplift only), all Gaussians"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-                             "sample": f"1 of {cams.v} views per step, D={wl.d}, N={wl.scene.n}"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "cpu_model": cpu_model(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
 # ---------------------------------------------------------------- our arm
-def cpu_baseline(wl):
+def cpu_baseline(wl, views=4):
+    """The oracle on the host cores, warm: view 0 untimed, then views 1 ..
+    views-1 (about 3 s each at paper scale on 16 cores), as the reference arm
+    times them."""
     import oracle
-    oracle.build()
     nthreads = oracle.default_threads()
-    v = 0
-    F = wl.features(v).numpy()
-    num = np.zeros((wl.scene.n, wl.d))
-    den = np.zeros(wl.scene.n)
-    t0 = time.perf_counter()
-    oracle.view_uplift(wl.scene, wl.cams.params[v], wl.cams.width, wl.cams.height, F, num, den,
-                       nthreads=nthreads)
-    dt = time.perf_counter() - t0
-    return {"value": wl.d / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-            "sample": f"uplift of view 0 of {wl.cams.v} (D={wl.d}, N={wl.scene.n}), {dt:.1f} s"}
+    secs = oracle_view_seconds(wl, list(range(views)), nthreads)
+    t = float(np.mean(secs[1:]))
+    return {"value": wl.d / t, "unit": UNIT, "cores": nthreads, "cpu_model": cpu_model(), "kind": "oracle",
+            "sample": (f"uplift of views 1-{views - 1} of {wl.cams.v} after an untimed view 0 "
+                       f"(D={wl.d}, N={wl.scene.n}), {t:.2f} s per view")}
 
 
 # DRAM bytes (read + write) of one k_aggregate_tc launch, from the ncu capture in
-# profiles/aggregate_paper_f32_traffic.md: (workload, dtype, d) -> (bytes, views in
-# the captured launch).  Scaled to a launch by its views; re-measure whenever the
-# kernel changes.
-TRAFFIC = {("paper", "f32", 384): (33.45e9, 16)}
+# profiles/aggregate_paper_f32_traffic.md (profile case uplift16views: one
+# 16-view launch): (workload, dtype, d) -> (bytes, views in the captured
+# launch).  Scaled to a launch by its views; re-measure whenever the kernel
+# changes.
+TRAFFIC = {("paper", "f32", 384): (28.01e9, 16)}
 
 
 def roofline(tr, steps, alg_bytes_step, traffic_key=None, views_per_launch=None):
@@ -750,7 +835,13 @@ def run_ours(args):
 
     if rank == 0 and not args.no_e2e:
         nv = min(args.e2e_views, V)
-        hf = feats[:nv].cpu().pin_memory()
+        node, cpus = gpu_local_cpus(gpu_id)
+        hf = pinned_near(tuple(feats[:nv].shape), fdt, cpus)   # pages next to the GPU
+        hf.copy_(feats[:nv])
+        scratch = torch.empty_like(feats[:nv])
+        h2d_gbs, d2h_gbs = copy_rates(hf, scratch)
+        del scratch
+        torch.cuda.empty_cache()
         ludvig.uplift_host(sc, wl.cams.params[:nv], W, H, hf)   # warm-up
         ts = []
         for _ in range(max(1, min(3, args.steps))):
@@ -759,9 +850,14 @@ def run_ours(args):
             ludvig.uplift_host(sc, wl.cams.params[:nv], W, H, hf)
             ts.append(time.perf_counter() - t0)
         te = float(np.median(ts))
-        line["e2e"] = {"value": nv * D / te, "unit": UNIT, "h2d_bytes_per_step": int(hf.numel() * esize),
-                       "d2h_bytes_per_step": int(sc.n * (D + 1) * 4),
-                       "sample": f"views 0-{nv - 1} of {V} through ludvig_uplift_host (uplift only)"}
+        bi, bo = int(hf.numel() * esize), int(sc.n * (D + 1) * 4)
+        line["e2e"] = {"value": nv * D / te, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+                       "seconds_per_step": te,
+                       "h2d_gbs_measured": h2d_gbs, "d2h_gbs_measured": d2h_gbs,
+                       "copy_floor_s": bi / (h2d_gbs * 1e9) + bo / (d2h_gbs * 1e9),
+                       "pinned_numa_node": node, "pinned_near_cpus": len(cpus) if cpus else None,
+                       "sample": (f"views 0-{nv - 1} of {V} through ludvig_uplift_host (uplift only); "
+                                  "the host->device rate is one plain copy of the same pinned buffer")}
         del hf
     if rank == 0 and not args.no_relevancy and args.workload == "paper" and args.dtype == "f32":
         line["count_normalised_uplift"] = count_normalised_line(sc, wl, feats)
@@ -793,6 +889,8 @@ def run_ours(args):
         pools = None
         torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        del feats
+        torch.cuda.empty_cache()
         line["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
         print(json.dumps(line))
@@ -806,7 +904,9 @@ def profile_case(name):
     tc2views: uplift twice with float32 features and twice with the same field
     in bfloat16.  render2views: render of seeded unit-norm features, three
     times.  render16views: the same render of views 0-15 (one full launch of
-    the render kernels), three times.  batch8: the first 8 jobs of the
+    the render kernels), three times.  uplift16views: float32 uplift of
+    views 0-15 (one full launch of the aggregation, 13 GB of features), three
+    times.  batch8: the first 8 jobs of the
     32-job batched mix through one ludvig_uplift_batch call (6 slots)."""
     import torch
     from paper_2410_14462_gb300 import build, inputs, ludvig
@@ -822,13 +922,21 @@ def profile_case(name):
         res = serve.run_batch(jobs, pools, cams.params, cams.width, cams.height, slots=6)
         torch.cuda.synchronize()
         return 1 if res["errors"] else 0
-    wl = inputs.paper_scale_workload(views=16 if name == "render16views" else 2, d=384)
+    wl = inputs.paper_scale_workload(views=16 if name in ("render16views", "uplift16views") else 2, d=384)
     sc = ludvig.Scene.from_inputs(wl.scene)
     W, H = wl.cams.width, wl.cams.height
     if name in ("render2views", "render16views"):
         f = torch.from_numpy(inputs.gaussian_features(sc.n, 384, seed=21)).cuda()
         for _ in range(3):
             ludvig.render(sc, wl.cams.params, W, H, f)
+        torch.cuda.synchronize()
+        return 0
+    if name == "uplift16views":
+        F = torch.empty((16, H, W, 384), dtype=torch.float32, device="cuda")
+        for v in range(16):
+            F[v] = wl.features(v, device="cuda")
+        for _ in range(3):
+            ludvig.uplift(sc, wl.cams.params, W, H, F)
         torch.cuda.synchronize()
         return 0
     F = torch.stack([wl.features(v, device="cuda") for v in range(2)]).contiguous()

@@ -99,10 +99,21 @@ def test_poisoned_request_leaves_the_others_intact(world):
 
 
 def test_admission_rejects_requests_over_budget(world):
-    budget = serve.request_bytes(world["scenes"][1].n, 8) + 1   # fits a small request on scene 1 only
+    """The budget covers the server's replicas and the live workspaces besides
+    the outputs: with room for the workspaces (already grown by the earlier
+    requests on these scenes), one small output and 2 MB, the large request
+    on scene 0 is rejected and the small ones on scene 1 are served."""
+    srv = _server(world, 1 << 40, slots=2)
+    res_bytes = srv.resident_bytes()
+    assert res_bytes >= serve.SCENE_BYTES_PER_GAUSSIAN * sum(sc.n for sc in world["scenes"])   # one replica each
+    assert res_bytes >= sum(sc.workspace_bytes() for sc in world["scenes"]) > 0
+    srv.close()
+    srv = _server(world, 1 << 40, slots=1)
+    srv.budget = srv.resident_bytes() + serve.request_bytes(world["scenes"][1].n, 8) + (2 << 20)
+    assert serve.request_bytes(world["scenes"][0].n, 48) > serve.request_bytes(world["scenes"][1].n, 8) + (2 << 20)
     reqs = [serve.Request(0, 0.0, 0, 48, 0, 4), serve.Request(1, 0.0, 1, 8, 0, 4),
             serve.Request(2, 0.01, 1, 8, 4, 4)]
-    res = _server(world, budget, slots=1).run(reqs)
+    res = srv.run(reqs)
     assert not res[0].ok and "budget" in res[0].error
     assert res[1].ok and res[2].ok
 
