@@ -612,29 +612,66 @@ def batched_form(pools, cams, slots=6):
     """32 uplift jobs of uneven size (N log-uniform in [50k, 1M] clustered
     Gaussians, V uniform in [20, 200] views of 640x480, D uniform over
     {1, 3, 64, 384, 512}) with bfloat16 features from shared device pools,
-    run by one ludvig_uplift_batch call on ``slots`` streams; beside it the same jobs one after
-    another on one stream (bfloat16) and in the plain float32 form (the same
-    values widened to float32, views in chunks of 48), each timed with CUDA
-    events.  The bfloat16 error is stated against the float32 path on true
-    float32 features (8 views of the first job with D >= 64)."""
+    run by one ludvig_uplift_batch call: the jobs' views packed into shared
+    groups per (dtype, D) class, group sizes picked by the library's tuner
+    during the untimed first batch.  Beside it the unpacked forms (every job
+    its own ludvig_uplift call) one after another on one stream and on
+    ``slots`` concurrent streams, and the plain float32 form (the same values
+    widened to float32, views in chunks of 48), each timed with CUDA events.
+    The bfloat16 error is stated against the float64 oracle on the same
+    bfloat16 values for the two cheapest jobs to check (all their views), and
+    against the float32 path on true float32 features (8 views of the first
+    job with D >= 64)."""
     import torch
+    import oracle
     from paper_2410_14462_gb300 import inputs, ludvig, serve
     W, H = cams.width, cams.height
     specs = inputs.batch_jobs()
     scenes = [ludvig.Scene.from_inputs(inputs.scene_clusters(s.n, seed=s.seed)) for s in specs]
     jobs = [serve.Job(j, scenes[j], s.d, s.v0, s.views) for j, s in enumerate(specs)]
     work = sum(j.views * j.d for j in jobs)
-    res = serve.run_batch(jobs, pools, cams.params, W, H, slots=slots)   # warm-up: workspaces grow
+    res = serve.run_batch(jobs, pools, cams.params, W, H, slots=slots)   # warm-up: tuning, workspaces grow
     if res["errors"]:
         raise RuntimeError(f"batched form: {res['errors']}")
+    plan = ludvig.batch_last_plan()
     ludvig.trace_read(reset=True)
     reps = 2
-    batched = [serve.run_batch(jobs, pools, cams.params, W, H, slots=slots)["device_ms"] for _ in range(reps)]
+    runs = [serve.run_batch(jobs, pools, cams.params, W, H, slots=slots, keep_outputs=(r == reps - 1))
+            for r in range(reps)]
+    batched = [r["device_ms"] for r in runs]
     launches = ludvig.trace_read(reset=True)["kernel_launches"] / reps
-    ludvig.trace_enable(True)    # stage split of the one-stream run (stages do not overlap there)
-    serial = serve.run_batch(jobs, pools, cams.params, W, H, slots=1)["device_ms"]
-    ludvig.trace_enable(False)
-    stages = {k: v for k, v in ludvig.trace_read(reset=True)["ms"].items() if v > 0}
+    kept = runs[-1]["outputs"]
+    ludvig.set_option(ludvig.OPT_BATCH_PACK, 0)
+    try:
+        serve.run_batch(jobs, pools, cams.params, W, H, slots=slots)     # the lent workspaces grow
+        ludvig.trace_read(reset=True)
+        ludvig.trace_enable(True)    # stage split of the one-stream run (stages do not overlap there)
+        serial = serve.run_batch(jobs, pools, cams.params, W, H, slots=1)["device_ms"]
+        ludvig.trace_enable(False)
+        tr = ludvig.trace_read(reset=True)
+        stages = {k: v for k, v in tr["ms"].items() if v > 0}
+        launches_unpacked = tr["kernel_launches"]
+        concurrent = serve.run_batch(jobs, pools, cams.params, W, H, slots=slots)["device_ms"]
+    finally:
+        ludvig.set_option(ludvig.OPT_BATCH_PACK, 1)
+    # bfloat16 vs float64 on sampled jobs: the two cheapest for the oracle
+    checks = []
+    for j in sorted(jobs, key=lambda j: j.scene.n * j.views * (j.d + 32))[:2]:
+        s = specs[j.jid]
+        host = inputs.scene_clusters(s.n, seed=s.seed)
+        sub = inputs.Cameras(cams.params[j.v0:j.v0 + j.views], W, H)
+        X = pools[j.d][j.v0:j.v0 + j.views].float().cpu().numpy()
+        t0 = time.perf_counter()
+        f_ref, b_ref = oracle.uplift(host, sub, lambda v: X[v])
+        out, beta = kept[j.jid]
+        pos = b_ref > 0
+        got = out.cpu().numpy().astype(np.float64)
+        e = float(np.linalg.norm(got[pos] - f_ref[pos]) / max(np.linalg.norm(f_ref[pos]), 1e-300))
+        checks.append({"job": j.jid, "n": s.n, "views": j.views, "d": j.d, "rel_l2_vs_fp64": e,
+                       "beta_support_equal": bool(np.array_equal(beta.cpu().numpy() > 0, pos)),
+                       "oracle_s": time.perf_counter() - t0})
+        del X, f_ref, b_ref
+    del kept, runs
     # plain float32 form, one job after another; each job's scene is made
     # afresh (the resident scenes' workspaces are freed first) and its float32
     # pass runs once untimed so that the workspace has grown before timing
@@ -681,15 +718,20 @@ def batched_form(pools, cams, slots=6):
         torch.cuda.empty_cache()
     ms = float(np.median(batched))
     out = {"value": work / (ms / 1e3), "unit": UNIT, "dtype": "bf16", "ms_per_batch": ms,
-           "ms_per_batch_runs": batched, "serial_bf16_ms": serial, "plain_f32_serial_ms": plain_ms,
-           "speedup_vs_serial_bf16": serial / ms, "speedup_vs_plain_f32": plain_ms / ms,
+           "ms_per_batch_runs": batched, "serial_bf16_ms": serial, "unpacked_concurrent_bf16_ms": concurrent,
+           "plain_f32_serial_ms": plain_ms,
+           "speedup_vs_serial_bf16": serial / ms, "speedup_vs_unpacked_concurrent": concurrent / ms,
+           "speedup_vs_plain_f32": plain_ms / ms,
            "plain_f32_value": work / (plain_ms / 1e3), "gpu_launches_per_batch": launches,
+           "gpu_launches_unpacked": launches_unpacked, "plan": plan,
+           "bf16_vs_fp64_sampled_jobs": checks,
            "rel_l2_bf16_vs_f32": err, "err_case": err_case, "serial_stages_ms": stages,
            "config": {"workload": "32 jobs: N log-uniform [50k, 1M], V U[20, 200] of 640x480, "
                                   "D U{1, 3, 64, 384, 512}, bf16 pools, seed 3",
                       "jobs": len(jobs), "views_ch": work, "gaussians": sum(s.n for s in specs),
                       "slots": slots,
-                      "form": "ludvig_uplift_batch: concurrent streams, native host threads, longest job first"}}
+                      "form": "ludvig_uplift_batch: views packed into shared groups per (dtype, D) class, "
+                              "group size tuned per class, classes on concurrent contexts"}}
     return out
 
 

@@ -60,7 +60,7 @@
 extern "C" {
 #endif
 
-#define LUDVIG_ABI_VERSION 10
+#define LUDVIG_ABI_VERSION 11
 
 typedef enum {
     LUDVIG_OK = 0,
@@ -97,10 +97,23 @@ typedef enum {
                                          LUDVIG_ERR_CUDA once (the kernel itself was queued and
                                          runs normally); 0 disarms.  The failed call's outputs
                                          are undefined; a later call starts afresh */
-    LUDVIG_OPT_AGG_CONFIG = 4         /* shared-memory layout of the float32 tensor-core
+    LUDVIG_OPT_AGG_CONFIG = 4,        /* shared-memory layout of the float32 tensor-core
                                          aggregation: 0 = seven feature stages, four epilogue
                                          warps; 1 = five stages, eight epilogue warps.  Results
                                          are the same to rounding; only the speed differs */
+    LUDVIG_OPT_GROUP_MB = 5,          /* views per group of the pipeline: up to 128, with their
+                                         per-view Gaussian scratch (about 120 bytes per view
+                                         and Gaussian) within this many MiB (default 2048,
+                                         range 1..65536; a group holds at least one view).  Larger groups take fewer launches
+                                         and more workspace; results are the same to rounding */
+    LUDVIG_OPT_BATCH_TUNE = 6,        /* 1 (default): ludvig_uplift_batch picks the group size
+                                         of each class of jobs by timing candidates on the
+                                         class's own jobs the first time it meets the class
+                                         (see ludvig_uplift_batch); 0: LUDVIG_OPT_GROUP_MB */
+    LUDVIG_OPT_BATCH_PACK = 7         /* 1 (default): ludvig_uplift_batch packs the views of
+                                         tensor-core jobs into shared groups; 0: every job
+                                         runs as its own ludvig_uplift call (the unpacked
+                                         form, kept for comparison) */
 } ludvig_option;
 
 /* Sets an option; LUDVIG_ERR_ARG for an unknown option. */
@@ -258,28 +271,61 @@ typedef struct {
 #define LUDVIG_MAX_BATCH_SLOTS 32
 
 /* Batched uplift: n_jobs independent uplifts of uneven size (each exactly
- * ludvig_uplift with the job's arguments, Eq. 5) run concurrently on `slots`
- * internal streams (1 <= slots <= LUDVIG_MAX_BATCH_SLOTS), each driven by a
- * host thread (the calling thread is one), longest estimated job first.
+ * ludvig_uplift with the job's arguments, Eq. 5) sharing the GPU.
+ * Jobs on the tensor-core path (packed_supported: bfloat16 features, float32
+ * with LUDVIG_OPT_F32_TENSOR_CORES, any d < 32) with the same dtype, d and
+ * image size whose feature buffers lie a whole number of views apart (as
+ * slices of one feature array do) form a class: the class's views are
+ * packed, largest scene first, into common groups of up to 128 views of
+ * several jobs, so every stage launch serves many jobs.  The group size (the
+ * per-view Gaussian scratch bound of a group) is picked per class: with
+ * LUDVIG_OPT_BATCH_TUNE = 1 (default) by timing candidate sizes (256 MiB ..
+ * 2 GiB) on up to 4 of the class's jobs and 256 of their views, into scratch
+ * outputs, the first time the process meets the class (dtype, d, image size,
+ * log2 of the mean scene size), and kept for later batches; else
+ * LUDVIG_OPT_GROUP_MB.  A class that runs out of device memory is redone
+ * with half the bound (down to 64 MiB).  Classes run on up to `slots` pooled contexts (each
+ * with its own workspace and streams, driven by a host thread), largest
+ * class first; other jobs run as ludvig_uplift calls on `slots` host threads
+ * with pooled workspaces lent to their scenes.  1 <= slots <=
+ * LUDVIG_MAX_BATCH_SLOTS.
  * Every job's work is ordered after the work already on `stream`, and
  * `stream` waits for all of it: to the caller the batch is one call on
  * `stream`.  A scene may appear in one job only (LUDVIG_ERR_ARG otherwise);
- * jobs may share feature buffers (read-only) but not outputs.
- * job_status: host [n_jobs] or NULL, receives each job's status.  Returns
- * LUDVIG_OK when every job succeeded, else the status of the first failing
- * job in job order (ludvig_last_error() names it); the other jobs still run.
+ * jobs may share feature buffers (read-only) but not outputs.  A job whose
+ * arguments ludvig_uplift would reject fails alone.
+ * job_status: host [n_jobs] or NULL, receives each job's status (a failure
+ * inside a class fails the class's jobs).  Returns LUDVIG_OK when every job
+ * succeeded, else the status of the first failing job in job order
+ * (ludvig_last_error() names it); the other jobs still run.
  * Results equal those of the jobs run one by one, to float32 rounding
  * (summation order is not fixed).
- * Workspace: each slot lends a workspace from a process-wide pool to the jobs
- * it runs (the scenes' own workspaces are left as they were), so device
- * scratch grows with `slots`, not with n_jobs; the pool keeps the slot
- * workspaces for later batches.  The call returns after every job's work has
- * finished. */
+ * Workspace: the contexts and slot workspaces come from a process-wide pool
+ * (the scenes' own workspaces are left as they were), so device scratch
+ * grows with `slots`, not with n_jobs; the pool keeps them for later
+ * batches.  The call returns after every job's work has finished. */
 ludvig_status ludvig_uplift_batch(const ludvig_uplift_job* jobs, int32_t n_jobs, int32_t slots,
                                   int32_t* job_status, void* stream);
 
-/* Frees the idle pooled workspaces of ludvig_uplift_batch on the current
- * device (those of batches still running stay). */
+/* One class of the last ludvig_uplift_batch call on any thread. */
+typedef struct {
+    int32_t dtype, d, width, height;
+    int32_t jobs, views;
+    int32_t groups;     /* groups formed: launches of each pipeline stage (-1: the single calls) */
+    int32_t group_mb;   /* the groups' per-view Gaussian scratch bound, MiB */
+    int32_t tuned;      /* 1: group_mb was picked by the tuner */
+} ludvig_batch_class;
+
+/* Copies up to cap classes of the last batch into out (host, may be NULL) and
+ * returns how many it had: the packed classes, then one entry (groups = -1)
+ * for the jobs run as single calls. */
+int32_t ludvig_batch_last_plan(ludvig_batch_class* out, int32_t cap);
+
+/* Forgets the tuner's choices (the next batch times its classes again). */
+ludvig_status ludvig_batch_forget_tuning(void);
+
+/* Frees the idle pooled workspaces and contexts of ludvig_uplift_batch on the
+ * current device (those of batches still running stay). */
 ludvig_status ludvig_batch_release_workspaces(void);
 
 /* Rendering of per-Gaussian features into views (Sec. 3.2, Eq. 4, F_hat = W f,

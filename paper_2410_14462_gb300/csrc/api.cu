@@ -223,10 +223,16 @@ namespace {
 std::atomic<int64_t> g_opt_f32_tc{1};
 std::atomic<int64_t> g_opt_count{0};
 std::atomic<int64_t> g_opt_agg_config{0};
+std::atomic<int64_t> g_opt_group_mb{2048};
+std::atomic<int64_t> g_opt_batch_tune{1};
+std::atomic<int64_t> g_opt_batch_pack{1};
 }
 bool option_f32_tensor_cores() { return g_opt_f32_tc.load() != 0; }
 bool option_count_normalise() { return g_opt_count.load() != 0; }
 int option_agg_config() { return (int)g_opt_agg_config.load(); }
+int64_t option_group_bytes() { return g_opt_group_mb.load() << 20; }
+bool option_batch_tune() { return g_opt_batch_tune.load() != 0; }
+bool option_batch_pack() { return g_opt_batch_pack.load() != 0; }
 }  // namespace ludvig
 
 extern "C" ludvig_status ludvig_set_option(int32_t option, int64_t value) {
@@ -250,6 +256,19 @@ extern "C" ludvig_status ludvig_set_option(int32_t option, int64_t value) {
             }
             g_opt_agg_config.store(value);
             return LUDVIG_OK;
+        case LUDVIG_OPT_GROUP_MB:
+            if (value < 1 || value > (64 << 10)) {
+                set_error("LUDVIG_OPT_GROUP_MB must be in [1, 65536]");
+                return LUDVIG_ERR_ARG;
+            }
+            g_opt_group_mb.store(value);
+            return LUDVIG_OK;
+        case LUDVIG_OPT_BATCH_TUNE:
+            g_opt_batch_tune.store(value != 0);
+            return LUDVIG_OK;
+        case LUDVIG_OPT_BATCH_PACK:
+            g_opt_batch_pack.store(value != 0);
+            return LUDVIG_OK;
         default:
             set_error("unknown option %d", option);
             return LUDVIG_ERR_ARG;
@@ -263,6 +282,9 @@ extern "C" int64_t ludvig_get_option(int32_t option) {
         case LUDVIG_OPT_FAULT_ALLOC: return g_fault_alloc.load();
         case LUDVIG_OPT_FAULT_LAUNCH: return g_fault_launch.load();
         case LUDVIG_OPT_AGG_CONFIG: return g_opt_agg_config.load();
+        case LUDVIG_OPT_GROUP_MB: return g_opt_group_mb.load();
+        case LUDVIG_OPT_BATCH_TUNE: return g_opt_batch_tune.load();
+        case LUDVIG_OPT_BATCH_PACK: return g_opt_batch_pack.load();
         default: return -1;
     }
 }

@@ -50,13 +50,25 @@
 
 namespace ludvig {
 
-constexpr int kMaxViews = 16;
+constexpr int kMaxViews = kMaxGroupViews;
 
 bool option_f32_tensor_cores();
 bool option_count_normalise();
+int64_t option_group_bytes();
 
+// Per-view cameras and scenes of a group (kernel parameters, read in place).
 struct CamBatch {
     Cam cam[kMaxViews];
+};
+struct SceneBatch {
+    const float4* geo[kMaxViews];
+    const float4* cov_a[kMaxViews];
+    const float2* cov_b[kMaxViews];
+    int64_t n[kMaxViews];
+};
+// Per-view coordinates in a feature array (kernel parameter).
+struct FViews {
+    int f[kMaxViews];
 };
 
 // Whether a request's aggregation runs on the tensor cores (else CUDA cores).
@@ -96,10 +108,11 @@ __global__ void k_scene_init(const float* __restrict__ means, const float* __res
 
 // ------------------------------------------------------------ 1. project
 
-__global__ void __launch_bounds__(256) k_project(const float4* __restrict__ geo, const float4* __restrict__ cov_a,
-                          const float2* __restrict__ cov_b, int64_t n, int64_t npad, int nv,
-                          CamBatch cb, int width, int height, float4* __restrict__ rec_a,
-                          float2* __restrict__ rec_b, uint2* __restrict__ rect,
+// View v projects the sb.n[v] Gaussians of its own scene; the records of the
+// group have a stride of n (the largest scene) per view.
+__global__ void __launch_bounds__(256) k_project(const __grid_constant__ SceneBatch sb, int64_t n, int64_t npad,
+                          int nv, const __grid_constant__ CamBatch cb, int width, int height,
+                          float4* __restrict__ rec_a, float2* __restrict__ rec_b, uint2* __restrict__ rect,
                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                           uint32_t* __restrict__ ntile, float* __restrict__ dbg_rec,
                           int32_t* __restrict__ dbg_rect, int prune) {
@@ -107,13 +120,13 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ geo,
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int v = (int)(idx / npad);
     const int64_t i = idx - (int64_t)v * npad;
-    const bool real = i < n;
+    const bool real = i < sb.n[v];
     Projected P{};
     float op = 0.f;
     if (real) {
-        const float4 g = geo[i];
-        const float4 ca = cov_a[i];
-        const float2 cbv = cov_b[i];
+        const float4 g = sb.geo[v][i];
+        const float4 ca = sb.cov_a[v][i];
+        const float2 cbv = sb.cov_b[v][i];
         const float m[3] = {g.x, g.y, g.z};
         const float S6[6] = {ca.x, ca.y, ca.z, ca.w, cbv.x, cbv.y};
         P = project_gaussian(m, S6, cb.cam[v], width, height);
@@ -732,20 +745,24 @@ constexpr int kPadD = 32;
 
 // One thread per 16-byte group of a padded pixel (8 bfloat16 or 4 float
 // channels): one vector store each, loads only for the channels below d.
+// Padded view v (group order) comes from view coordinate fv.f[v] of src.
 template <class T>
-__global__ void k_pad_features(const T* __restrict__ src, int64_t npx, int d, T* __restrict__ dst) {
+__global__ void k_pad_features(const T* __restrict__ src, const __grid_constant__ FViews fv, int64_t view_px,
+                               int64_t npx, int d, T* __restrict__ dst) {
     constexpr int kPer = 16 / (int)sizeof(T);
     constexpr int kGroups = kPadD / kPer;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= npx * kGroups) return;
     const int64_t p = e / kGroups;
+    const int64_t v = p / view_px;
+    const T* sp = src + ((int64_t)fv.f[v] * view_px + (p - v * view_px)) * d;
     const int c0 = (int)(e - p * kGroups) * kPer;
     T vals[kPer];
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) vals[k] = c0 + k < d ? src[p * d + c0 + k] : T(0.f);
-    uint4 v;
-    memcpy(&v, vals, sizeof(v));
-    reinterpret_cast<uint4*>(dst)[e] = v;
+    for (int k = 0; k < kPer; ++k) vals[k] = c0 + k < d ? sp[c0 + k] : T(0.f);
+    uint4 packed;
+    memcpy(&packed, vals, sizeof(packed));
+    reinterpret_cast<uint4*>(dst)[e] = packed;
 }
 
 __global__ void k_add_columns(const float* __restrict__ wide, int64_t n, int d, float* __restrict__ num) {
@@ -761,8 +778,9 @@ bool use_padded(int dtype, int d) { return d < kPadD && use_tensor_cores(dtype, 
 // to bfloat16 for the tensor-core path (the E4M3 value is exact in half
 // precision; the bfloat16 rounding adds at most 2^-9 relative to an FP8
 // quantisation error of up to 2^-4).  Thread t converts elements 4t .. 4t+3
-// of the group (one 4-byte load, one 8-byte store); the scalar tail covers a
-// total that is not a multiple of 4.
+// of the group (one 4-byte load, one 8-byte store, when the codes and the
+// output are aligned for them; else element by element); the scalar tail
+// covers a total that is not a multiple of 4.
 __device__ __forceinline__ __nv_bfloat16 dequant_e4m3(uint32_t code, float s) {
     const __half h(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)code, __NV_E4M3));
     return __float2bfloat16_rn(__half2float(h) * s);
@@ -772,7 +790,8 @@ __global__ void k_dequant_e4m3(const uint8_t* __restrict__ q, const float* __res
                                int64_t total, __nv_bfloat16* __restrict__ out) {
     const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (e0 >= total) return;
-    if (e0 + 4 <= total) {
+    const bool aligned = ((reinterpret_cast<uintptr_t>(q) & 3) | (reinterpret_cast<uintptr_t>(out) & 7)) == 0;
+    if (aligned && e0 + 4 <= total) {
         const uint32_t w = *reinterpret_cast<const uint32_t*>(q + e0);
         __nv_bfloat16 o[4];
 #pragma unroll
@@ -781,7 +800,7 @@ __global__ void k_dequant_e4m3(const uint8_t* __restrict__ q, const float* __res
         memcpy(&v, o, sizeof(v));
         *reinterpret_cast<uint2*>(out + e0) = v;
     } else {
-        for (int64_t e = e0; e < total; ++e) out[e] = dequant_e4m3(q[e], s[e / view_elems]);
+        for (int64_t e = e0; e < total && e < e0 + 4; ++e) out[e] = dequant_e4m3(q[e], s[e / view_elems]);
     }
 }
 
@@ -797,54 +816,105 @@ struct FrontEnd {
     bool too_many = false;           // checked runs: more pairs than one group may hold
 };
 
-// Stages 1-5 of a group of nv views on `st`.  checked: the pair count is read
-// back (synchronises `st`) and the pair buffers grow to fit it.  Otherwise
-// nothing waits: the buffers keep the scene's pair capacity, and a group that
-// needs more sets *ovf, writes no pairs (all lists empty) and is redone later.
-ludvig_status front_end(ludvig_scene* s, const ludvig_camera* cams, int nv, int width, int height, bool checked,
-                        int* ovf, const ChunkDebug* dbg, cudaStream_t st, FrontEnd* fe) {
-    Arena& ws = s->ws;
-    const int64_t n = s->n;
-    const int64_t npad = round_up(n, kRadixTile);
-    const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
-    const int ntiles = TX * TY;
-    const int64_t nG = (int64_t)nv * npad;
-    const int prune = (dbg && dbg->unpruned) ? 0 : 1;
+// The views v0 .. v0 + nv - 1 of one scene as a group: feature coordinates
+// v0 .. v0 + nv - 1, sums into num / den.
+GroupViews scene_group(const ludvig_scene* s, const ludvig_camera* cams, int v0, int nv, float* num, float* den) {
+    GroupViews g;
+    g.nmax = s->n;
+    g.v.resize((size_t)nv);
+    for (int k = 0; k < nv; ++k) g.v[(size_t)k] = ViewRef{s, cams[v0 + k], v0 + k, num, den};
+    return g;
+}
 
+// Whether the group's views read consecutive feature coordinates and add into
+// the same num / den (a group of one scene's call).
+bool single_call(const GroupViews& g) {
+    for (size_t k = 1; k < g.v.size(); ++k)
+        if (g.v[k].fview != g.v[0].fview + (int)k || g.v[k].num != g.v[0].num || g.v[k].den != g.v[0].den ||
+            g.v[k].scene != g.v[0].scene)
+            return false;
+    return true;
+}
+
+// The per-view Gaussian scratch of a group of nv views of up to n Gaussians
+// (about 120 bytes per view and Gaussian).
+struct FrontBufs {
     float4* rec_a;
     float2* rec_b;
     uint2 *rect, *srect;
     uint32_t *keys, *vals, *keys2, *vals2, *ntile, *cnt, *off;
     PairRec* srec;
-    uint64_t* total_d;
-    LV_TRY(ws.get("up.rec_a", (size_t)nv * n, &rec_a));
-    LV_TRY(ws.get("up.rec_b", (size_t)nv * n, &rec_b));
-    LV_TRY(ws.get("up.rect", (size_t)nv * n, &rect));
-    LV_TRY(ws.get("up.keys", (size_t)nG, &keys));
-    LV_TRY(ws.get("up.vals", (size_t)nG, &vals));
-    LV_TRY(ws.get("up.keys2", (size_t)nG, &keys2));
-    LV_TRY(ws.get("up.vals2", (size_t)nG, &vals2));
-    LV_TRY(ws.get("up.ntile", (size_t)nG, &ntile));
-    LV_TRY(ws.get("up.cnt", (size_t)nG, &cnt));
-    LV_TRY(ws.get("up.off", (size_t)nG, &off));
-    LV_TRY(ws.get("up.srec", (size_t)nG, &srec));
-    LV_TRY(ws.get("up.srect", (size_t)nG, &srect));
-    LV_TRY(ws.get("up.total", 1, &total_d));
+    uint64_t* total;
+};
 
+ludvig_status front_buffers(Arena& ws, int nv, int64_t n, FrontBufs* b) {
+    const int64_t nG = (int64_t)nv * round_up(std::max<int64_t>(n, 1), kRadixTile);
+    LV_TRY(ws.get("up.rec_a", (size_t)nv * n, &b->rec_a));
+    LV_TRY(ws.get("up.rec_b", (size_t)nv * n, &b->rec_b));
+    LV_TRY(ws.get("up.rect", (size_t)nv * n, &b->rect));
+    LV_TRY(ws.get("up.keys", (size_t)nG, &b->keys));
+    LV_TRY(ws.get("up.vals", (size_t)nG, &b->vals));
+    LV_TRY(ws.get("up.keys2", (size_t)nG, &b->keys2));
+    LV_TRY(ws.get("up.vals2", (size_t)nG, &b->vals2));
+    LV_TRY(ws.get("up.ntile", (size_t)nG, &b->ntile));
+    LV_TRY(ws.get("up.cnt", (size_t)nG, &b->cnt));
+    LV_TRY(ws.get("up.off", (size_t)nG, &b->off));
+    LV_TRY(ws.get("up.srec", (size_t)nG, &b->srec));
+    LV_TRY(ws.get("up.srect", (size_t)nG, &b->srect));
+    LV_TRY(ws.get("up.total", 1, &b->total));
+    return LUDVIG_OK;
+}
+
+// Stages 1-5 of a group on `st`, in the workspace of `ctx` (the scene of a
+// one-scene call, or a batch's context).  checked: the pair count is read
+// back (synchronises `st`) and the pair buffers grow to fit it.  Otherwise
+// nothing waits: the buffers keep ctx's pair capacity, and a group that
+// needs more sets *ovf, writes no pairs (all lists empty) and is redone later.
+ludvig_status front_end(ludvig_scene* ctx, const GroupViews& g, int width, int height, bool checked,
+                        int* ovf, const ChunkDebug* dbg, cudaStream_t st, FrontEnd* fe) {
+    ludvig_scene* s = ctx;
+    Arena& ws = s->ws;
+    const int nv = (int)g.v.size();
+    const int64_t n = g.nmax;
+    const int64_t npad = round_up(std::max<int64_t>(n, 1), kRadixTile);
+    const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
+    const int ntiles = TX * TY;
+    const int64_t nG = (int64_t)nv * npad;
+    const int prune = (dbg && dbg->unpruned) ? 0 : 1;
+
+    FrontBufs b;
+    LV_TRY(front_buffers(ws, nv, n, &b));
+    float4* rec_a = b.rec_a;
+    float2* rec_b = b.rec_b;
+    uint2 *rect = b.rect, *srect = b.srect;
+    uint32_t *keys = b.keys, *vals = b.vals, *keys2 = b.keys2, *vals2 = b.vals2, *ntile = b.ntile, *cnt = b.cnt,
+             *off = b.off;
+    PairRec* srec = b.srec;
+    uint64_t* total_d = b.total;
+
+    if (nv < 1 || nv > kMaxViews) {
+        set_error("a group holds 1 to %d views, not %d", kMaxViews, nv);
+        return LUDVIG_ERR_INTERNAL;
+    }
     CamBatch cb;
+    SceneBatch sb;
     for (int v = 0; v < nv; ++v) {
-        const ludvig_camera& c = cams[v];
+        const ludvig_camera& c = g.v[(size_t)v].cam;
         for (int k = 0; k < 9; ++k) cb.cam[v].R[k] = c.R[k];
         for (int k = 0; k < 3; ++k) cb.cam[v].t[k] = c.t[k];
         cb.cam[v].fx = c.fx;
         cb.cam[v].fy = c.fy;
         cb.cam[v].cx = c.cx;
         cb.cam[v].cy = c.cy;
+        const ludvig_scene* vs = g.v[(size_t)v].scene;
+        sb.geo[v] = vs->geo;
+        sb.cov_a[v] = vs->cov_a;
+        sb.cov_b[v] = vs->cov_b;
+        sb.n[v] = vs->n;
     }
     int tslot = trace_on() ? trace_begin(LUDVIG_STAGE_PROJECT, st) : -1;
-    k_project<<<grid_for(nG, 256), 256, 0, st>>>(s->geo, s->cov_a, s->cov_b, n, npad, nv, cb, width,
-                                                  height, rec_a, rec_b, rect, keys, vals, ntile,
-                                                  dbg ? dbg->rec : nullptr, dbg ? dbg->rect : nullptr,
+    k_project<<<grid_for(nG, 256), 256, 0, st>>>(sb, n, npad, nv, cb, width, height, rec_a, rec_b, rect, keys,
+                                                  vals, ntile, dbg ? dbg->rec : nullptr, dbg ? dbg->rect : nullptr,
                                                   prune);
     LV_LAUNCH();
     trace_end(tslot, st);
@@ -951,15 +1021,6 @@ ludvig_status composite_cc(ludvig_scene* s, const FrontEnd& fe, int nv, int widt
 
 // ---------------------------------------------------------------- group pipeline
 
-// The features of a call as its groups read them.
-struct FeatSrc {
-    int kind = 0;                  // 0: as given, 1: zero-padded to kPadD channels, 2: FP8-E4M3 codes
-    const void* feats = nullptr;   // [n_views, H, W, d] features, or codes for kind 2
-    const float* scales = nullptr; // kind 2: per-view scales
-    int dtype = LUDVIG_F32;        // of the given features (kind 2: decoded to bfloat16)
-    int d = 1;
-};
-
 bool src_padded(const FeatSrc& f) { return f.kind == 1 || (f.kind == 2 && f.d < kPadD); }
 
 // How a group's work is ordered.
@@ -972,21 +1033,28 @@ struct Exec {
     int* ovf = nullptr;          // async: the call's overflow word
 };
 
-// Stages 1-6 of one group (views v0 .. v0 + nv - 1): num/den (pad_num when
-// padded) += the group's W^T F and weight sums.
-ludvig_status uplift_group(ludvig_scene* s, const ludvig_camera* cams, int v0, int nv, int width, int height,
-                           const FeatSrc& src, float* num, float* den, float* pad_num, const Exec& ex,
-                           bool* too_many, int64_t* pair_cap = nullptr, int64_t* chunk_cap = nullptr) {
+// Stages 1-6 of one group: each view's num/den (its padded numerator when
+// padded) += the view's W^T F and weight sums.
+ludvig_status uplift_group(ludvig_scene* ctx, const GroupViews& g, int width, int height, const FeatSrc& src,
+                           const Exec& ex, bool* too_many, int64_t* pair_cap = nullptr,
+                           int64_t* chunk_cap = nullptr) {
+    ludvig_scene* s = ctx;
+    const int nv = (int)g.v.size();
     const bool padded = src_padded(src);
     const int fdt = src.kind == 2 ? LUDVIG_BF16 : src.dtype;   // the dtype the kernels read
     const int deff = padded ? kPadD : src.d;
     const bool tc = padded || use_tensor_cores(fdt, deff);
+    const bool one_call = single_call(g);
     cudaStream_t sf = ex.async ? s->st_front : ex.st;
     cudaStream_t sa = ex.async ? s->st_agg : ex.st;
     const int p = ex.group & 1;
     *too_many = false;
+    if (!tc && !one_call) {
+        set_error("views of several calls share a group only on the tensor-core path");
+        return LUDVIG_ERR_INTERNAL;
+    }
     FrontEnd fe;
-    LV_TRY(front_end(s, cams + v0, nv, width, height, !ex.async, ex.async ? ex.ovf : nullptr, nullptr, sf, &fe));
+    LV_TRY(front_end(s, g, width, height, !ex.async, ex.async ? ex.ovf : nullptr, nullptr, sf, &fe));
     if (fe.too_many) {
         *too_many = true;
         return LUDVIG_OK;
@@ -996,42 +1064,64 @@ ludvig_status uplift_group(ludvig_scene* s, const ludvig_camera* cams, int v0, i
     if (chunk_cap) *chunk_cap = 0x7fffffff;   // no weight rows on the CUDA-core path
     const int64_t view_elems = (int64_t)width * height * src.d;
     const size_t esize = src.kind == 2 ? 1 : (src.dtype == LUDVIG_F32 ? 4 : 2);
-    const void* f = static_cast<const char*>(src.feats) + (size_t)v0 * view_elems * esize;
-    if (!tc) return composite_cc(s, fe, nv, width, height, f, fdt, deff, num, den, nullptr, sf);
+    const int fv0 = g.v[0].fview;
+    int fmax = 0;
+    for (const ViewRef& r : g.v) fmax = std::max(fmax, r.fview);
+    // a one-scene group's features start at its first coordinate
+    const void* f0 = static_cast<const char*>(src.feats) + (size_t)fv0 * view_elems * esize;
+    if (!tc) return composite_cc(s, fe, nv, width, height, f0, fdt, deff, g.v[0].num, g.v[0].den, nullptr, sf);
 
     // tensor cores: the operand features and the weight rows go to the
     // buffer set of parity p, free once the aggregation of group - 2 is done
     if (ex.async && ex.group >= 2) LV_CUDA(cudaStreamWaitEvent(sf, s->ev_agg[p], 0));
     static const char* const kFb[2] = {"fp8.bf16.0", "fp8.bf16.1"};
     static const char* const kPad[2] = {"pad.feats.0", "pad.feats.1"};
+    AggViews av;
+    for (int k = 0; k < nv; ++k) {
+        av.fview[k] = g.v[(size_t)k].fview;
+        av.num[k] = g.v[(size_t)k].num;
+        av.den[k] = g.v[(size_t)k].den;
+    }
+    const void* f = src.feats;   // the array the aggregation reads, at coordinates av.fview
+    int fextent = fmax + 1;
     // FP8 codes the aggregation decodes itself (no bfloat16 copy in HBM)
     const bool f8_in_kernel = src.kind == 2 && !padded && tc_e4m3_supported(src.d) &&
                               (reinterpret_cast<uintptr_t>(src.feats) & 15) == 0;
     if (src.kind == 2 && !f8_in_kernel) {
+        if (!one_call) {
+            set_error("FP8 codes decoded before the aggregation need a one-scene group");
+            return LUDVIG_ERR_INTERNAL;
+        }
         __nv_bfloat16* fb;
         const int64_t total = (int64_t)nv * view_elems;
         LV_TRY(s->ws.get(kFb[p], (size_t)total, &fb));
-        // groups start a multiple of 16 views in: the codes stay 4-byte aligned
-        k_dequant_e4m3<<<grid_for(ceil_div(total, 4), 256), 256, 0, sf>>>(static_cast<const uint8_t*>(f),
-                                                                         src.scales + v0, view_elems, total, fb);
+        k_dequant_e4m3<<<grid_for(ceil_div(total, 4), 256), 256, 0, sf>>>(static_cast<const uint8_t*>(f0),
+                                                                         src.scales + fv0, view_elems, total, fb);
         LV_LAUNCH();
         f = fb;
+        fextent = nv;
+        for (int k = 0; k < nv; ++k) av.fview[k] = k;
     }
     if (padded) {
         const int64_t npx = (int64_t)nv * width * height;
         const size_t pes = fdt == LUDVIG_F32 ? 4 : 2;
         void* fpad;
         LV_TRY(s->ws.get(kPad[p], (size_t)npx * kPadD * pes, &fpad));
+        FViews fvs;
+        for (int k = 0; k < nv; ++k) fvs.f[k] = av.fview[k];
         // 16-byte groups per padded pixel: 8 (float) or 4 (bfloat16)
         const int64_t groups = npx * (kPadD * (int64_t)pes / 16);
+        const int64_t view_px = (int64_t)width * height;
         if (fdt == LUDVIG_F32)
-            k_pad_features<float><<<grid_for(groups, 256), 256, 0, sf>>>(static_cast<const float*>(f), npx, src.d,
-                                                                         static_cast<float*>(fpad));
+            k_pad_features<float><<<grid_for(groups, 256), 256, 0, sf>>>(static_cast<const float*>(f), fvs, view_px,
+                                                                         npx, src.d, static_cast<float*>(fpad));
         else
             k_pad_features<__nv_bfloat16><<<grid_for(groups, 256), 256, 0, sf>>>(
-                static_cast<const __nv_bfloat16*>(f), npx, src.d, static_cast<__nv_bfloat16*>(fpad));
+                static_cast<const __nv_bfloat16*>(f), fvs, view_px, npx, src.d, static_cast<__nv_bfloat16*>(fpad));
         LV_LAUNCH();
         f = fpad;
+        fextent = nv;
+        for (int k = 0; k < nv; ++k) av.fview[k] = k;
     }
     TileWeights t;
     LV_TRY(tc_weights(fe.L, nv, width, height, fdt == LUDVIG_F32 ? 2 : 1, s->ws, p, s->dstat, &s->tc_chunk_cap,
@@ -1042,40 +1132,51 @@ ludvig_status uplift_group(ludvig_scene* s, const ludvig_camera* cams, int v0, i
         LV_CUDA(cudaEventRecord(s->ev_front[p], sf));
         LV_CUDA(cudaStreamWaitEvent(sa, s->ev_front[p], 0));
     }
-    LV_TRY(tc_aggregate(t, nv, width, height, f, f8_in_kernel ? kDtypeE4M3 : fdt, deff, padded ? pad_num : num, den,
-                        s->dstat, ex.async ? ex.ovf : nullptr, sa, f8_in_kernel ? src.scales + v0 : nullptr));
+    LV_TRY(tc_aggregate(t, nv, width, height, f, fextent, f8_in_kernel ? kDtypeE4M3 : fdt, deff, av, s->dstat,
+                        ex.async ? ex.ovf : nullptr, sa, f8_in_kernel ? src.scales : nullptr));
     if (ex.async) LV_CUDA(cudaEventRecord(s->ev_agg[p], sa));
     return LUDVIG_OK;
 }
 
 // Views per group: up to kMaxViews, with the per-group Gaussian scratch
-// (about 120 bytes per Gaussian and view) kept near 2 GB.
-int views_per_group(const ludvig_scene* s, int n_views) {
+// (about 120 bytes per Gaussian and view) kept within the group budget
+// (LUDVIG_OPT_GROUP_MB, 2 GB by default).
+int views_per_group(int64_t n, int n_views, int64_t budget) {
     int vc = std::min<int>(kMaxViews, std::max<int>(1, n_views));
-    const int64_t per_view = std::max<int64_t>(1, s->n) * 120;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(vc, ((int64_t)2 << 30) / per_view));
+    const int64_t per_view = std::max<int64_t>(1, n) * 120;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(vc, budget / per_view));
 }
 
-// Groups of views [v0, v0 + nv) run checked on `st`; a group with more pairs
-// than one group may hold is split in halves.
-ludvig_status run_checked(ludvig_scene* s, const ludvig_camera* cams, int v0, int nv_total, int width, int height,
-                          const FeatSrc& src, float* num, float* den, float* pad_num, cudaStream_t st) {
-    int vc = views_per_group(s, nv_total);
-    const int end = v0 + nv_total;
+// A group run checked on `st`; a group with more pairs than one group may
+// hold is split in halves (each run the same way).
+ludvig_status run_checked(ludvig_scene* ctx, const GroupViews& g, int width, int height, const FeatSrc& src,
+                          cudaStream_t st) {
     Exec ex;
     ex.st = st;
-    while (v0 < end) {
+    bool too_many = false;
+    LV_TRY(uplift_group(ctx, g, width, height, src, ex, &too_many));
+    if (!too_many) return LUDVIG_OK;
+    if (g.v.size() == 1) {
+        set_error("view %d produces more than 2^31 tile/Gaussian pairs", g.v[0].fview);
+        return LUDVIG_ERR_UNSUPPORTED;
+    }
+    const size_t h = g.v.size() / 2;
+    for (int half = 0; half < 2; ++half) {
+        GroupViews part;
+        part.v.assign(g.v.begin() + (half ? h : 0), half ? g.v.end() : g.v.begin() + h);
+        for (const ViewRef& r : part.v) part.nmax = std::max(part.nmax, r.scene->n);
+        LV_TRY(run_checked(ctx, part, width, height, src, st));
+    }
+    return LUDVIG_OK;
+}
+
+// Views [v0, v0 + nv_total) of one scene's call, group by group, checked.
+ludvig_status run_checked_range(ludvig_scene* s, const ludvig_camera* cams, int v0, int nv_total, int width,
+                                int height, const FeatSrc& src, float* num, float* den, cudaStream_t st) {
+    const int vc = views_per_group(s->n, nv_total, option_group_bytes());
+    for (int end = v0 + nv_total; v0 < end;) {
         const int nv = std::min(vc, end - v0);
-        bool too_many = false;
-        LV_TRY(uplift_group(s, cams, v0, nv, width, height, src, num, den, pad_num, ex, &too_many));
-        if (too_many) {
-            if (nv == 1) {
-                set_error("view %d produces more than 2^31 tile/Gaussian pairs", v0);
-                return LUDVIG_ERR_UNSUPPORTED;
-            }
-            vc = std::max(1, nv / 2);
-            continue;
-        }
+        LV_TRY(run_checked(s, scene_group(s, cams, v0, nv, num, den), width, height, src, st));
         v0 += nv;
     }
     return LUDVIG_OK;
@@ -1084,16 +1185,22 @@ ludvig_status run_checked(ludvig_scene* s, const ludvig_camera* cams, int v0, in
 // Allocates what asynchronous groups of up to nv views use at the scene's
 // current capacities (both buffer sets), so that they find it in place: a
 // workspace that grows synchronises the device.
-ludvig_status reserve_async(ludvig_scene* s, int nv, int width, int height, const FeatSrc& src, bool tc) {
+// Groups of up to nv views whose largest per-view Gaussian scratch is that of
+// ng views of n Gaussians.
+ludvig_status reserve_async(ludvig_scene* s, int nv, int ng, int64_t n, int width, int height, const FeatSrc& src,
+                            bool tc) {
     Arena& ws = s->ws;
     void* q;
+    FrontBufs fb;
+    LV_TRY(front_buffers(ws, ng, n, &fb));
     const int64_t cap = std::max<int64_t>(s->pair_cap, kRadixTile);
     for (const char* name : {"up.pk", "up.pv", "up.pk2", "up.pv2"}) LV_TRY(ws.get(name, sizeof(uint32_t) * (size_t)cap, &q));
-    // the radix sorts' digit histograms (pairs, and the depth sort of nv views) and their scan sums
-    const int64_t npad = round_up(s->n, kRadixTile);
-    const int64_t hist = 256 * std::max<int64_t>(cap, (int64_t)nv * npad) / kRadixTile;
+    // the radix sorts' digit histograms (pairs, and the depth sort of nv views of
+    // up to n Gaussians) and their scan sums
+    const int64_t npad = round_up(std::max<int64_t>(n, 1), kRadixTile);
+    const int64_t hist = 256 * std::max<int64_t>(cap, (int64_t)ng * npad) / kRadixTile;
     LV_TRY(ws.get("radix.hist", sizeof(uint32_t) * (size_t)hist, &q));
-    LV_TRY(ws.get("scan.sums", sizeof(unsigned long long) * (size_t)ceil_div(std::max(hist, (int64_t)nv * npad), 4096),
+    LV_TRY(ws.get("scan.sums", sizeof(unsigned long long) * (size_t)ceil_div(std::max(hist, (int64_t)ng * npad), 4096),
                   &q));
     if (!tc) {
         LV_TRY(ws.get("up.pairs", sizeof(PairRec) * (size_t)cap, &q));
@@ -1175,6 +1282,12 @@ ludvig_status normalise(int64_t n, int d, const float* num, const float* den, fl
     return LUDVIG_OK;
 }
 
+// Whether a group that ran asynchronously with the capacities (pcap, ccap)
+// completed: its pairs and weight chunks fitted.
+bool group_fits(const GroupDiag& gd, int64_t pcap, int64_t ccap) {
+    return gd.pairs <= (uint64_t)kMaxPairs && round_up((int64_t)gd.pairs, kRadixTile) <= pcap && gd.chunks <= ccap;
+}
+
 // Waits for the scene's asynchronous call, if one is pending, and finishes it:
 // groups that did not fit the workspace are redone (checked, so the workspace
 // grows) and the normalisation they held back runs.  Returns the device status
@@ -1201,13 +1314,9 @@ ludvig_status resolve_pending(ludvig_scene* s) {
         }
         LV_CUDA(cudaMemsetAsync(s->dstat + 1, 0, sizeof(int), st));
         for (size_t g = 0; g < pc.v0.size(); ++g) {
-            const GroupDiag& gd = s->hdiag[g];
-            const bool fits = gd.pairs <= (uint64_t)kMaxPairs &&
-                              round_up((int64_t)gd.pairs, kRadixTile) <= pc.pair_cap[g] &&
-                              gd.chunks <= pc.chunk_cap[g];
-            if (fits) continue;
-            LV_TRY(run_checked(s, pc.cams.data(), pc.v0[g], pc.nv[g], pc.width, pc.height, src, pc.num, pc.den,
-                               pad_num, st));
+            if (group_fits(s->hdiag[g], pc.pair_cap[g], pc.chunk_cap[g])) continue;
+            LV_TRY(run_checked(s, scene_group(s, pc.cams.data(), pc.v0[g], pc.nv[g], padded ? pad_num : pc.num, pc.den),
+                               pc.width, pc.height, src, st));
         }
         if (padded) {
             k_add_columns<<<grid_for(s->n * pc.d, 256), 256, 0, st>>>(pad_num, s->n, pc.d, pc.num);
@@ -1228,6 +1337,69 @@ ludvig_status resolve_pending(ludvig_scene* s) {
 // One uplift call: kind 0 adds into num/den, kind 1 zeroes them first and
 // normalises at the end (num becomes f, den stays beta).  Asynchronous unless
 // `checked`: see ludvig_sync.
+// Enqueues groups[first ..] on ctx's front-end and aggregation streams after
+// the work on `st` (device-side capacity checks, group k - first's sizes into
+// ctx->ddiag), and makes `st` wait for them; pcap/ccap receive the
+// capacities each group ran with.
+ludvig_status enqueue_async(ludvig_scene* s, const std::vector<GroupViews>& groups, size_t first, int width,
+                            int height, const FeatSrc& src, cudaStream_t st, std::vector<int64_t>* pcap,
+                            std::vector<int64_t>* ccap) {
+    cudaStream_t sf = s->st_front, sa = s->st_agg;
+    LV_CUDA(cudaMemsetAsync(s->dstat + 1, 0, sizeof(int), st));
+    LV_CUDA(cudaEventRecord(s->ev_call, st));
+    LV_CUDA(cudaStreamWaitEvent(sf, s->ev_call, 0));
+    LV_CUDA(cudaStreamWaitEvent(sa, s->ev_call, 0));
+    for (size_t k = first; k < groups.size(); ++k) {
+        const int g = (int)(k - first);
+        Exec ex;
+        ex.async = true;
+        ex.group = g;
+        ex.diag = s->ddiag + g;
+        ex.ovf = s->dstat + 1;
+        bool too_many = false;
+        int64_t pc = 0, cc = 0;
+        LV_TRY(uplift_group(s, groups[k], width, height, src, ex, &too_many, &pc, &cc));
+        pcap->push_back(pc);
+        ccap->push_back(cc);
+    }
+    LV_CUDA(cudaEventRecord(s->ev_join[0], sf));
+    LV_CUDA(cudaEventRecord(s->ev_join[1], sa));
+    LV_CUDA(cudaStreamWaitEvent(st, s->ev_join[0], 0));
+    LV_CUDA(cudaStreamWaitEvent(st, s->ev_join[1], 0));
+    return LUDVIG_OK;
+}
+
+// Sizes ctx's workspace for asynchronous groups: when it has not been sized
+// (or `always`), groups[0] runs checked first (*first = 1: the groups after
+// it run asynchronously) and capacities it had to grow get headroom; then
+// everything the groups allocate is reserved.
+ludvig_status size_for_async(ludvig_scene* s, const std::vector<GroupViews>& groups, int width, int height,
+                             const FeatSrc& src, bool tc, bool always, cudaStream_t st, size_t* first) {
+    *first = 0;
+    if (groups.empty()) return LUDVIG_OK;
+    if (always || s->pair_cap == 0 || (tc && s->tc_chunk_cap == 0)) {
+        const int64_t pc0 = s->pair_cap, cc0 = s->tc_chunk_cap;
+        LV_TRY(run_checked(s, groups[0], width, height, src, st));
+        if (s->pair_cap > pc0) s->pair_cap = round_up(s->pair_cap + s->pair_cap / 4, kRadixTile);
+        if (s->tc_chunk_cap > cc0) s->tc_chunk_cap += s->tc_chunk_cap / 4;
+        *first = 1;
+    }
+    int nv = 1, ng = 1;
+    int64_t n = 1;
+    for (const GroupViews& g : groups) {
+        nv = std::max(nv, (int)g.v.size());
+        const int64_t npad = round_up(std::max<int64_t>(g.nmax, 1), kRadixTile);
+        if ((int64_t)g.v.size() * npad > (int64_t)ng * round_up(n, kRadixTile)) {
+            ng = (int)g.v.size();
+            n = std::max<int64_t>(g.nmax, 1);
+        }
+    }
+    return reserve_async(s, nv, ng, n, width, height, src, tc);
+}
+
+// One uplift call: kind 0 adds into num/den, kind 1 zeroes them first and
+// normalises at the end (num becomes f, den stays beta).  Asynchronous unless
+// `checked`: see ludvig_sync.
 ludvig_status run_call(ludvig_scene* s, int kind, const FeatSrc& src, const ludvig_camera* cams, int n_views,
                        int width, int height, float* num, float* den, cudaStream_t st, bool checked) {
     LV_TRY(resolve_pending(s));
@@ -1243,55 +1415,22 @@ ludvig_status run_call(ludvig_scene* s, int kind, const FeatSrc& src, const ludv
         LV_TRY(s->ws.get("pad.num", (size_t)n * kPadD, &pad_num));
         LV_CUDA(cudaMemsetAsync(pad_num, 0, sizeof(float) * (size_t)n * kPadD, st));
     }
-    const int vc = views_per_group(s, n_views);
-    const int ngroups = (int)ceil_div(std::max(n_views, 0), vc);
-    LV_TRY(ensure_async(s, ngroups));
+    const int vc = views_per_group(n, n_views, option_group_bytes());
+    std::vector<GroupViews> groups;
+    for (int v0 = 0; v0 < n_views; v0 += vc)
+        groups.push_back(scene_group(s, cams, v0, std::min(vc, n_views - v0), padded ? pad_num : num, den));
+    LV_TRY(ensure_async(s, (int)groups.size()));
     const int fdt = src.kind == 2 ? LUDVIG_BF16 : src.dtype;
     const bool tc = padded || use_tensor_cores(fdt, d);
-    int v0 = 0;
-    if (!checked && n_views > 0 && (s->pair_cap == 0 || (tc && s->tc_chunk_cap == 0))) {
-        // the workspace has not been sized yet: the first group runs checked and
-        // sizes it, with headroom for the other groups
-        const int nv = std::min(vc, n_views);
-        LV_TRY(run_checked(s, cams, 0, nv, width, height, src, num, den, pad_num, st));
-        s->pair_cap = round_up(s->pair_cap + s->pair_cap / 4, kRadixTile);
-        s->tc_chunk_cap += s->tc_chunk_cap / 4;
-        LV_TRY(reserve_async(s, nv, width, height, src, tc));
-        v0 = nv;
-    }
-    std::vector<int> gv0, gnv;
+    size_t first = groups.size();
     std::vector<int64_t> gpcap, gccap;
     if (checked) {
-        LV_TRY(run_checked(s, cams, 0, n_views, width, height, src, num, den, pad_num, st));
-    } else if (v0 < n_views) {
-        cudaStream_t sf = s->st_front, sa = s->st_agg;
-        LV_CUDA(cudaMemsetAsync(s->dstat + 1, 0, sizeof(int), st));
-        LV_CUDA(cudaEventRecord(s->ev_call, st));
-        LV_CUDA(cudaStreamWaitEvent(sf, s->ev_call, 0));
-        LV_CUDA(cudaStreamWaitEvent(sa, s->ev_call, 0));
-        for (int g = 0; v0 < n_views; ++g) {
-            const int nv = std::min(vc, n_views - v0);
-            Exec ex;
-            ex.async = true;
-            ex.group = g;
-            ex.diag = s->ddiag + g;
-            ex.ovf = s->dstat + 1;
-            bool too_many = false;
-            int64_t pcap = 0, ccap = 0;
-            LV_TRY(uplift_group(s, cams, v0, nv, width, height, src, num, den, pad_num, ex, &too_many, &pcap,
-                                &ccap));
-            gv0.push_back(v0);
-            gnv.push_back(nv);
-            gpcap.push_back(pcap);
-            gccap.push_back(ccap);
-            v0 += nv;
-        }
-        LV_CUDA(cudaEventRecord(s->ev_join[0], sf));
-        LV_CUDA(cudaEventRecord(s->ev_join[1], sa));
-        LV_CUDA(cudaStreamWaitEvent(st, s->ev_join[0], 0));
-        LV_CUDA(cudaStreamWaitEvent(st, s->ev_join[1], 0));
+        for (const GroupViews& g : groups) LV_TRY(run_checked(s, g, width, height, src, st));
+    } else {
+        LV_TRY(size_for_async(s, groups, width, height, src, tc, false, st, &first));
+        if (first < groups.size()) LV_TRY(enqueue_async(s, groups, first, width, height, src, st, &gpcap, &gccap));
     }
-    const bool async = !gv0.empty();
+    const bool async = first < groups.size();
     if (padded) {
         k_add_columns<<<grid_for(n * d, 256), 256, 0, st>>>(pad_num, n, d, num);
         LV_LAUNCH();
@@ -1299,7 +1438,8 @@ ludvig_status run_call(ludvig_scene* s, int kind, const FeatSrc& src, const ludv
     if (kind == 1) LV_TRY(normalise(n, d, num, den, num, nullptr, async ? s->dstat + 1 : nullptr, st));
     if (!async) return read_status(s, st);
     LV_CUDA(cudaMemcpyAsync(s->hstat, s->dstat, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    LV_CUDA(cudaMemcpyAsync(s->hdiag, s->ddiag, sizeof(GroupDiag) * gv0.size(), cudaMemcpyDeviceToHost, st));
+    LV_CUDA(cudaMemcpyAsync(s->hdiag, s->ddiag, sizeof(GroupDiag) * (groups.size() - first),
+                            cudaMemcpyDeviceToHost, st));
     LV_CUDA(cudaEventRecord(s->ev_done, st));
     PendingCall& pc = s->pending;
     pc.kind = kind;
@@ -1314,8 +1454,12 @@ ludvig_status run_call(ludvig_scene* s, int kind, const FeatSrc& src, const ludv
     pc.scales = src.scales;
     pc.num = num;
     pc.den = den;
-    pc.v0 = std::move(gv0);
-    pc.nv = std::move(gnv);
+    pc.v0.clear();
+    pc.nv.clear();
+    for (size_t k = first; k < groups.size(); ++k) {
+        pc.v0.push_back(groups[k].v[0].fview);
+        pc.nv.push_back((int)groups[k].v.size());
+    }
     pc.pair_cap = std::move(gpcap);
     pc.chunk_cap = std::move(gccap);
     pc.active = true;
@@ -1337,7 +1481,8 @@ ludvig_status check_views(const ludvig_camera* cams, int32_t n_views, int32_t wi
 ludvig_status render_group(ludvig_scene* s, const ludvig_camera* cams, int nv, int width, int height,
                            const float* f, int d, float* out, cudaStream_t st, bool* too_many) {
     FrontEnd fe;
-    LV_TRY(front_end(s, cams, nv, width, height, true, nullptr, nullptr, st, &fe));
+    LV_TRY(front_end(s, scene_group(s, cams, 0, nv, nullptr, nullptr), width, height, true, nullptr, nullptr, st,
+                     &fe));
     *too_many = fe.too_many;
     if (fe.too_many) return LUDVIG_OK;
     StageScope scope(LUDVIG_STAGE_RENDER, st);
@@ -1380,6 +1525,98 @@ ludvig_status ensure_status(ludvig_scene* s) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------- packed batches
+bool packed_supported(int dtype, int d) { return use_padded(dtype, d) || use_tensor_cores(dtype, d); }
+
+ludvig_status uplift_packed(ludvig_scene* ctx, const PackedJob* jobs, int njobs, const void* feats, int dtype, int d,
+                            int width, int height, int64_t group_bytes, cudaStream_t st, int* groups_formed) {
+    if (groups_formed) *groups_formed = 0;
+    if (njobs <= 0) return LUDVIG_OK;
+    if (!packed_supported(dtype, d)) {
+        set_error("packed uplift needs the tensor-core path (dtype %d, d %d)", dtype, d);
+        return LUDVIG_ERR_UNSUPPORTED;
+    }
+    FeatSrc src;
+    src.kind = use_padded(dtype, d) ? 1 : 0;
+    src.feats = feats;
+    src.dtype = dtype;
+    src.d = d;
+    const bool padded = src.kind == 1;
+    LV_TRY(ensure_status(ctx));
+    // per job: den (beta, else the context's), the padded numerator
+    int64_t nden = 0, npadn = 0;
+    for (int j = 0; j < njobs; ++j) {
+        if (!jobs[j].beta) nden += jobs[j].scene->n;
+        if (padded) npadn += jobs[j].scene->n * kPadD;
+    }
+    float *den_ws = nullptr, *pad_ws = nullptr;
+    if (nden) LV_TRY(ctx->ws.get("pk.den", (size_t)nden, &den_ws));
+    if (npadn) LV_TRY(ctx->ws.get("pk.pad", (size_t)npadn, &pad_ws));
+    std::vector<float*> den(njobs), acc(njobs);
+    for (int j = 0; j < njobs; ++j) {
+        const int64_t n = jobs[j].scene->n;
+        den[j] = jobs[j].beta ? jobs[j].beta : den_ws;
+        if (!jobs[j].beta) den_ws += n;
+        acc[j] = padded ? pad_ws : jobs[j].out;
+        if (padded) pad_ws += n * kPadD;
+        LV_CUDA(cudaMemsetAsync(jobs[j].out, 0, sizeof(float) * (size_t)n * d, st));
+        LV_CUDA(cudaMemsetAsync(den[j], 0, sizeof(float) * (size_t)n, st));
+        if (padded) LV_CUDA(cudaMemsetAsync(acc[j], 0, sizeof(float) * (size_t)n * kPadD, st));
+    }
+    // the groups: every job's views in job order; a group closes at kMaxViews
+    // views or when one more view would take its Gaussian scratch past the budget
+    std::vector<GroupViews> groups;
+    GroupViews cur;
+    for (int j = 0; j < njobs; ++j) {
+        const ludvig_scene* sc = jobs[j].scene;
+        if (sc->n == 0) continue;
+        for (int v = 0; v < jobs[j].n_views; ++v) {
+            int64_t nmax = std::max(cur.nmax, sc->n);
+            const int64_t need = (int64_t)(cur.v.size() + 1) * round_up(nmax, kRadixTile) * 120;
+            if (!cur.v.empty() && ((int)cur.v.size() == kMaxViews || need > group_bytes)) {
+                groups.push_back(std::move(cur));
+                cur = GroupViews();
+                nmax = sc->n;
+            }
+            cur.v.push_back(ViewRef{sc, jobs[j].cams[v], jobs[j].fview0 + v, acc[j], den[j]});
+            cur.nmax = nmax;
+        }
+    }
+    if (!cur.v.empty()) groups.push_back(std::move(cur));
+    if (groups_formed) *groups_formed = (int)groups.size();
+    if (!groups.empty()) {
+        LV_TRY(ensure_async(ctx, (int)groups.size()));
+        size_t first = 0;
+        // the context served other classes of jobs: size it on this class's first group
+        LV_TRY(size_for_async(ctx, groups, width, height, src, true, true, st, &first));
+        std::vector<int64_t> gpcap, gccap;
+        if (first < groups.size()) {
+            LV_TRY(enqueue_async(ctx, groups, first, width, height, src, st, &gpcap, &gccap));
+            LV_CUDA(cudaMemcpyAsync(ctx->hstat, ctx->dstat, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            LV_CUDA(cudaMemcpyAsync(ctx->hdiag, ctx->ddiag, sizeof(GroupDiag) * (groups.size() - first),
+                                    cudaMemcpyDeviceToHost, st));
+            LV_CUDA(cudaEventRecord(ctx->ev_done, st));
+            LV_CUDA(cudaEventSynchronize(ctx->ev_done));
+            if (ctx->hstat[1]) {   // groups that did not fit: redone checked (the workspace grows)
+                for (size_t k = first; k < groups.size(); ++k)
+                    if (!group_fits(ctx->hdiag[k - first], gpcap[k - first], gccap[k - first]))
+                        LV_TRY(run_checked(ctx, groups[k], width, height, src, st));
+                LV_CUDA(cudaMemsetAsync(ctx->dstat + 1, 0, sizeof(int), st));
+            }
+        }
+    }
+    for (int j = 0; j < njobs; ++j) {
+        const int64_t n = jobs[j].scene->n;
+        if (n == 0) continue;
+        if (padded) {
+            k_add_columns<<<grid_for(n * d, 256), 256, 0, st>>>(acc[j], n, d, jobs[j].out);
+            LV_LAUNCH();
+        }
+        LV_TRY(normalise(n, d, jobs[j].out, den[j], jobs[j].out, nullptr, nullptr, st));
+    }
+    return read_status(ctx, st);
+}
 
 // ---------------------------------------------------------------- scene
 ludvig_status scene_init(ludvig_scene* s, const float* means, const float* scales, const float* quats,
@@ -1447,9 +1684,9 @@ extern "C" ludvig_status ludvig_uplift_finalize(int64_t n, int32_t d, const floa
     return normalise(n, d, num, den, out, beta, nullptr, static_cast<cudaStream_t>(stream));
 }
 
-extern "C" ludvig_status ludvig_uplift(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
-                                       int32_t width, int32_t height, const void* feats, int32_t dtype,
-                                       int32_t d, float* out, float* beta, void* stream) {
+namespace ludvig {
+ludvig_status check_uplift_args(const ludvig_scene* scene, const ludvig_camera* cams, int32_t n_views, int32_t width,
+                                int32_t height, const void* feats, int32_t dtype, int32_t d, const float* out) {
     LV_ARG(scene != nullptr, "scene is NULL");
     LV_ARG(out != nullptr || scene->n == 0, "out is NULL");
     LV_ARG(d >= 1 && d <= 65536, "d must be in [1, 65536]");
@@ -1457,6 +1694,14 @@ extern "C" ludvig_status ludvig_uplift(ludvig_scene_t scene, const ludvig_camera
     LV_ARG(dtype == LUDVIG_F32 || dtype == LUDVIG_BF16, "unknown dtype %d", dtype);
     LV_ARG(n_views == 0 || feats != nullptr, "feats is NULL");
     if (d % 4 == 0) LV_ARG(((uintptr_t)out & 15) == 0, "out must be 16-byte aligned when d %% 4 == 0");
+    return LUDVIG_OK;
+}
+}  // namespace ludvig
+
+extern "C" ludvig_status ludvig_uplift(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
+                                       int32_t width, int32_t height, const void* feats, int32_t dtype,
+                                       int32_t d, float* out, float* beta, void* stream) {
+    LV_TRY(check_uplift_args(scene, cams, n_views, width, height, feats, dtype, d, out));
     const int64_t n = scene->n;
     if (n == 0) return LUDVIG_OK;
     LV_TRY(ensure_status(scene));
@@ -1516,7 +1761,7 @@ extern "C" ludvig_status ludvig_render(ludvig_scene_t scene, const ludvig_camera
     LV_TRY(ensure_status(scene));
     LV_TRY(resolve_pending(scene));
     const int64_t view_elems = (int64_t)width * height * d;
-    int vc = views_per_group(scene, n_views);
+    int vc = views_per_group(scene->n, n_views, option_group_bytes());
     int v0 = 0;
     while (v0 < n_views) {
         const int nv = std::min(vc, n_views - v0);
@@ -1595,7 +1840,7 @@ extern "C" ludvig_status ludvig_uplift_host(ludvig_scene_t scene, const ludvig_c
         if (c + 1 < nchunks) LV_TRY(upload(c + 1));   // overlaps the compute of chunk c
         LV_CUDA(cudaStreamWaitEvent(st, scene->ev_ready[b], 0));
         src.feats = fbuf[b];
-        LV_TRY(run_checked(scene, cams + v0, 0, nv, width, height, src, num, den, pad_num, st));
+        LV_TRY(run_checked_range(scene, cams + v0, 0, nv, width, height, src, pad_num ? pad_num : num, den, st));
         LV_CUDA(cudaEventRecord(scene->ev_free[b], st));
     }
     if (pad_num) {
@@ -1637,7 +1882,8 @@ extern "C" ludvig_status ludvig_debug_project(ludvig_scene_t scene, const ludvig
     dbg.rect = rect;
     dbg.stop_after_project = true;
     FrontEnd fe;
-    return front_end(scene, cam, 1, width, height, true, nullptr, &dbg, static_cast<cudaStream_t>(stream), &fe);
+    return front_end(scene, scene_group(scene, cam, 0, 1, nullptr, nullptr), width, height, true, nullptr, &dbg,
+                     static_cast<cudaStream_t>(stream), &fe);
 }
 
 extern "C" ludvig_status ludvig_debug_tile_lists(ludvig_scene_t scene, const ludvig_camera* cam,
@@ -1663,7 +1909,8 @@ extern "C" ludvig_status ludvig_debug_tile_lists(ludvig_scene_t scene, const lud
     dbg.stop_after_sort = true;
     dbg.unpruned = (pruned == 0);
     FrontEnd fe;
-    LV_TRY(front_end(scene, cam, 1, width, height, true, nullptr, &dbg, st, &fe));
+    LV_TRY(front_end(scene, scene_group(scene, cam, 0, 1, nullptr, nullptr), width, height, true, nullptr, &dbg, st,
+                     &fe));
     if (fe.too_many) {
         set_error("too many pairs");
         return LUDVIG_ERR_UNSUPPORTED;
@@ -1695,7 +1942,8 @@ extern "C" ludvig_status ludvig_debug_transmittance(ludvig_scene_t scene, const 
     dbg.t_final = t_final;
     dbg.n_contrib = n_contrib;
     FrontEnd fe;
-    LV_TRY(front_end(scene, cam, 1, width, height, true, nullptr, nullptr, st, &fe));
+    LV_TRY(front_end(scene, scene_group(scene, cam, 0, 1, nullptr, nullptr), width, height, true, nullptr, nullptr,
+                     st, &fe));
     if (fe.too_many) {
         set_error("too many pairs");
         return LUDVIG_ERR_UNSUPPORTED;

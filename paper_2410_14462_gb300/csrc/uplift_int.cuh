@@ -2,10 +2,87 @@
 // group pipeline, entry points) and uplift_tc.cu (tensor-core kernels).
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 #include "spec.cuh"
 
 namespace ludvig {
+
+// Most views one group of the pipeline holds.  Each view carries its own
+// camera, scene, feature coordinate and accumulation targets in the kernels'
+// parameters (so a group may mix views of several scenes).
+constexpr int kMaxGroupViews = 128;
+
+// Per-view operands of the aggregation: the view's coordinate in the feature
+// array the tensor map covers, and the num [n, d] / den [n] it adds into.
+struct AggViews {
+    int fview[kMaxGroupViews];
+    float* num[kMaxGroupViews];
+    float* den[kMaxGroupViews];
+};
+
+// One view of a group: the scene it projects, its camera, its coordinate in
+// the features the group reads, and the num [n, d] / den [n] it adds into (on
+// the zero-padded path, num is the padded numerator [n, 32]).
+struct ViewRef {
+    const ludvig_scene* scene;
+    ludvig_camera cam;
+    int fview;
+    float* num;
+    float* den;
+};
+
+// The views of one group (at most kMaxGroupViews) and the largest of their
+// scenes (the stride of the group's per-view Gaussian scratch).
+struct GroupViews {
+    std::vector<ViewRef> v;
+    int64_t nmax = 0;
+};
+
+// The features of a call as its groups read them: views [*, H, W, d] at the
+// coordinates the group's views name.
+struct FeatSrc {
+    int kind = 0;                  // 0: as given, 1: zero-padded to 32 channels, 2: FP8-E4M3 codes
+    const void* feats = nullptr;   // features, or codes for kind 2
+    const float* scales = nullptr; // kind 2: scales by view coordinate
+    int dtype = LUDVIG_F32;        // of the given features (kind 2: decoded to bfloat16)
+    int d = 1;
+};
+
+// One job of a packed batch: the arguments of one ludvig_uplift call, with its
+// features at view coordinates fview0 .. fview0 + n_views - 1 of the batch's
+// feature array.
+struct PackedJob {
+    ludvig_scene* scene;
+    const ludvig_camera* cams;
+    int n_views;
+    int fview0;
+    float* out;
+    float* beta;   // may be null
+};
+
+// Uplift of jobs that share the feature array `feats` ([*, height, width, d],
+// dtype), each exactly ludvig_uplift on its own scene: their views are packed
+// in job order into common groups (views of several jobs in one group, up to
+// kMaxGroupViews views and group_bytes of per-view Gaussian scratch), run on
+// ctx's streams and workspace with device-side capacity checks; what did not
+// fit is redone before the call returns (it waits for the work).  Every job's
+// work is ordered after the work on `st`, and `st` waits for all of it.
+// *groups_formed (may be null) receives the number of groups.
+ludvig_status uplift_packed(ludvig_scene* ctx, const PackedJob* jobs, int njobs, const void* feats, int dtype, int d,
+                            int width, int height, int64_t group_bytes, cudaStream_t st, int* groups_formed);
+
+// Whether ludvig_uplift with these features runs on the tensor cores (the
+// precondition of uplift_packed).
+bool packed_supported(int dtype, int d);
+
+// The argument checks of ludvig_uplift (LUDVIG_ERR_ARG with the message set).
+ludvig_status check_uplift_args(const ludvig_scene* scene, const ludvig_camera* cams, int32_t n_views, int32_t width,
+                                int32_t height, const void* feats, int32_t dtype, int32_t d, const float* out);
+
+// Finishes a scene's pending asynchronous call (ludvig_sync).
+ludvig_status scene_sync(ludvig_scene* s);
 
 // The per-tile lists of a group of views as the compositing kernels read them.
 struct GroupLists {
@@ -48,11 +125,14 @@ ludvig_status tc_weights(const GroupLists& L, int nv, int width, int height, int
 // asynchronous call that finds them in place never waits).
 ludvig_status tc_reserve(Arena& ws, int NT, int nitems, int64_t cap);
 
-// num[i,:] += W^T F and den[i] += row sums for the group's weight rows
-// (k_aggregate_tc).  When the weights overflowed their chunks the kernel adds
-// nothing and sets bit 1 (value 2) of *ovf (ovf may be null for checked runs).
-ludvig_status tc_aggregate(const TileWeights& t, int nv, int width, int height, const void* feats, int dtype,
-                           int d, float* num, float* den, int* status, int* ovf, cudaStream_t st,
+// num_v[i,:] += W^T F and den_v[i] += row sums for the group's weight rows
+// (k_aggregate_tc), view v's features at coordinate av.fview[v] of `feats`
+// ([fextent, height, width, d]) and its sums into av.num[v] / av.den[v].
+// FP8 codes take the scale scales[av.fview[v]].  When the weights overflowed
+// their chunks the kernel adds nothing and sets bit 1 (value 2) of *ovf (ovf
+// may be null for checked runs).
+ludvig_status tc_aggregate(const TileWeights& t, int nv, int width, int height, const void* feats, int fextent,
+                           int dtype, int d, const AggViews& av, int* status, int* ovf, cudaStream_t st,
                            const float* scales = nullptr);
 
 // F_hat = W f for the group (k_render_tc); t must come from a checked tc_weights.

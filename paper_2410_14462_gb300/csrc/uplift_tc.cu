@@ -367,15 +367,14 @@ struct AggArgs {
     const uint32_t* chunk_gid;
     const float* chunk_den;   // [cap][128][NT]
     int nitems, ntiles, TX, d;
-    float* num;
-    float* den;
     int* status;
-    int store_mode;          // debug GEMM: num[gid * d + c] = accumulator (no den)
+    int store_mode;          // debug GEMM: views.num[0][gid * d + c] = accumulator (no den)
     const int* chunk_count;  // chunks the weights pass used (may be null: known to fit)
     int* ovf;                // set to 2 when they exceeded cap (the launch then adds nothing)
     const uint32_t* plan_off;   // [nitems + 1]: the item's chunks are plan[plan_off[item] ..)
     const int2* plan;           // {chunk, rows} of every non-empty chunk, tile after tile
-    const float* scales;        // FP8 codes: the views' scales (x = decode(q) s_v)
+    const float* scales;        // FP8 codes: the scales by feature coordinate (x = decode(q) s_v)
+    AggViews views;             // per view: feature coordinate and the num / den it adds into
 };
 
 // Feature units (16 KB): 128 channels of 64 pixels (NT = 1: one K atom, two
@@ -503,7 +502,8 @@ __device__ __forceinline__ void split8(const float* x, uint4& f1, uint4& f2) {
 
 template <int DB, int NT, int CF>
 __global__ void __launch_bounds__(agg_threads<NT, CF>(), 1)
-    k_aggregate_tc(AggArgs a, const __grid_constant__ CUtensorMap wmap1, const __grid_constant__ CUtensorMap wmap2,
+    k_aggregate_tc(const __grid_constant__ AggArgs a, const __grid_constant__ CUtensorMap wmap1,
+                   const __grid_constant__ CUtensorMap wmap2,
                    const __grid_constant__ CUtensorMap fmap) {
     using Sm = AggSmem<NT, CF>;
     // a weights pass that ran out of chunks left incomplete rows: the group is
@@ -596,6 +596,7 @@ __global__ void __launch_bounds__(agg_threads<NT, CF>(), 1)
                 ++k;
                 const int v = item / a.ntiles, tile = item - v * a.ntiles;
                 const int tx = tile % a.TX, ty = tile / a.TX;
+                const int fv = a.views.fview[v];   // the view's coordinate in the feature array
                 const uint64_t fpolicy = tile_last ? stream_policy : keep_policy;
                 for (int ka = 0; ka < 4 && ok; ++ka) {
                     const uint32_t ws = wc % Sm::kWA;
@@ -628,7 +629,7 @@ __global__ void __launch_bounds__(agg_threads<NT, CF>(), 1)
                             // 64 pixels x 128 codes, one box, into the stage's second half
                             mbar_expect_tx(&S.f_full[s], 8192u);
                             tma_load_4d_hint(S.F[s] + 8192, &fmap, &S.f_full[s], 128 * un, tx * kTile,
-                                             ty * kTile + 4 * ka, v, fpolicy);
+                                             ty * kTile + 4 * ka, fv, fpolicy);
                         } else {
                             mbar_expect_tx(&S.f_full[s], Sm::kFStage);
                             // kUnitPx pixels (kUnitPx / 16 rows of the tile) x 128 channels:
@@ -638,7 +639,7 @@ __global__ void __launch_bounds__(agg_threads<NT, CF>(), 1)
                             for (int j = 0; j < kBoxes; ++j)
                                 tma_load_4d_hint(S.F[s] + Sm::kBoxBytes * j, &fmap, &S.f_full[s],
                                                  128 * un + kBoxCh * j, tx * kTile,
-                                                 ty * kTile + 4 * ka + (Sm::kUnitPx / 16) * hf, v, fpolicy);
+                                                 ty * kTile + 4 * ka + (Sm::kUnitPx / 16) * hf, fv, fpolicy);
                         }
                         ++fc;
                     }
@@ -666,7 +667,7 @@ __global__ void __launch_bounds__(agg_threads<NT, CF>(), 1)
         for (;;) {
             int4 e;
             if (!ok || *abort_flag || !queue_next(S, abort_flag, a.status, qc, e, false) || e.x < 0) break;
-            const float sv = a.scales[e.y / a.ntiles];   // the chunk's view
+            const float sv = a.scales[a.views.fview[e.y / a.ntiles]];   // the chunk's view
             for (int un = 0; un < 4 * U; ++un) {
                 const uint32_t s = fc % Sm::kFS;
                 if (!agg_wait(abort_flag, a.status, &S.f_full[s], (fc / Sm::kFS) & 1u)) {
@@ -843,11 +844,13 @@ __global__ void __launch_bounds__(agg_threads<NT, CF>(), 1)
             const int c = e.x, rows = e.z;
             const bool valid = r < rows;
             const uint32_t g = valid ? a.chunk_gid[(size_t)c * kCRows + r] : 0u;
+            const int cv = e.y / a.ntiles;   // the chunk's view: its num and den
+            float* const num = a.views.num[cv];
             if (half == 0 && valid && !a.store_mode) {
                 float sden = 0.f;
 #pragma unroll
                 for (int t = 0; t < NT; ++t) sden += a.chunk_den[((size_t)c * kCRows + r) * NT + t];
-                atomicAdd(a.den + g, sden);
+                atomicAdd(a.views.den[cv] + g, sden);
             }
             for (int un = 0; un < U; ++un) {
                 const uint32_t u = ub + un, slot = u % kSlots;
@@ -874,7 +877,7 @@ __global__ void __launch_bounds__(agg_threads<NT, CF>(), 1)
                     const int lim = min(64, d - 64 * b);   // channels of this block inside d
                     if (a.store_mode) {
                         if (valid) {
-                            float* dst = a.num + (int64_t)g * d + 64 * b;
+                            float* dst = num + (int64_t)g * d + 64 * b;
     #pragma unroll
                             for (int i = 0; i < 32; ++i) {
                                 if (i < lim) dst[i] = v0[i];
@@ -892,7 +895,7 @@ __global__ void __launch_bounds__(agg_threads<NT, CF>(), 1)
                         }
                         fence_proxy_async();   // generic writes, read by the bulk copy
                         if (valid && lim > 0) {
-                            bulk_reduce_add_f32_hint(a.num + (int64_t)g * d + 64 * b, st, (uint32_t)lim * 4u,
+                            bulk_reduce_add_f32_hint(num + (int64_t)g * d + 64 * b, st, (uint32_t)lim * 4u,
                                                      num_policy);
                             bulk_commit();
                         }
@@ -1547,8 +1550,8 @@ ludvig_status tc_weights(const GroupLists& L, int nv, int width, int height, int
     return LUDVIG_OK;
 }
 
-ludvig_status tc_aggregate(const TileWeights& t, int nv, int width, int height, const void* feats, int dtype,
-                           int d, float* num, float* den, int* status, int* ovf, cudaStream_t st,
+ludvig_status tc_aggregate(const TileWeights& t, int nv, int width, int height, const void* feats, int fextent,
+                           int dtype, int d, const AggViews& av, int* status, int* ovf, cudaStream_t st,
                            const float* scales) {
     const int NT = dtype == LUDVIG_F32 ? 2 : 1;
     const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
@@ -1559,7 +1562,7 @@ ludvig_status tc_aggregate(const TileWeights& t, int nv, int width, int height, 
     CUtensorMap maps[3];
     LV_TRY(make_w_map(&maps[0], t.wg1, t.cap));
     LV_TRY(make_w_map(&maps[1], NT == 2 ? t.wg2 : t.wg1, t.cap));
-    LV_TRY(make_feature_map(&maps[2], feats, dtype, nv, width, height, d));
+    LV_TRY(make_feature_map(&maps[2], feats, dtype, fextent, width, height, d));
     AggArgs g{};
     g.cap = (int)t.cap;
     g.chunk_rows = t.crows;
@@ -1571,8 +1574,6 @@ ludvig_status tc_aggregate(const TileWeights& t, int nv, int width, int height, 
     g.ntiles = TX * TY;
     g.TX = TX;
     g.d = d;
-    g.num = num;
-    g.den = den;
     g.status = status;
     g.store_mode = 0;
     g.chunk_count = t.count >= 0 ? nullptr : t.counter;   // a checked run already fits
@@ -1580,6 +1581,7 @@ ludvig_status tc_aggregate(const TileWeights& t, int nv, int width, int height, 
     g.plan_off = t.plan_off;
     g.plan = t.plan;
     g.scales = scales;
+    g.views = av;
     const int grid = std::min(sms, nitems);
     StageScope agg_scope(LUDVIG_STAGE_AGGREGATE, st);
     if (dtype == kDtypeE4M3) return dispatch_agg_cf<1, 2>(g, maps, grid, st);
@@ -1740,8 +1742,9 @@ extern "C" ludvig_status ludvig_debug_mma_bf16(const void* a, const void* f, int
     g.ntiles = 1;
     g.TX = 1;
     g.d = d;
-    g.num = out;
-    g.den = nullptr;
+    g.views.fview[0] = 0;
+    g.views.num[0] = out;
+    g.views.den[0] = nullptr;
     g.status = &meta->status;
     g.store_mode = 1;
     g.chunk_count = nullptr;

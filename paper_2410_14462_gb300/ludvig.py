@@ -43,6 +43,8 @@ SIGNATURES = {
     "ludvig_uplift": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
     "ludvig_uplift_batch": (_I32, [_P, _I32, _I32, _P, _P]),
     "ludvig_batch_release_workspaces": (_I32, []),
+    "ludvig_batch_last_plan": (_I32, [_P, _I32]),
+    "ludvig_batch_forget_tuning": (_I32, []),
     "ludvig_fp8_quantize": (_I32, [_P, _I32, _I32, _I64, _P, _P, _P]),
     "ludvig_uplift_fp8": (_I32, [_P, _P, _I32, _I32, _I32, _P, _P, _I32, _P, _P, _P]),
     "ludvig_uplift_host": (_I32, [_P, _P, _I32, _I32, _I32, _P, _I32, _I32, _P, _P, _P]),
@@ -299,8 +301,30 @@ def uplift_fp8(scene: Scene, cams_params, width, height, q: torch.Tensor, scales
 
 
 def batch_release_workspaces():
-    """ludvig_batch_release_workspaces: free the batch executor's idle pooled workspaces."""
+    """ludvig_batch_release_workspaces: free the batch executor's idle pooled
+    workspaces and contexts."""
     _check(load().ludvig_batch_release_workspaces(), "ludvig_batch_release_workspaces")
+
+
+class BatchClass(ctypes.Structure):
+    """ludvig_batch_class: one class of the last batch."""
+    _fields_ = [(name, ctypes.c_int32) for name in
+                ("dtype", "d", "width", "height", "jobs", "views", "groups", "group_mb", "tuned")]
+
+
+def batch_last_plan() -> list[dict]:
+    """ludvig_batch_last_plan: the classes of the last ludvig_uplift_batch
+    call (the last entry, groups = -1, counts the jobs run as single calls)."""
+    L = load()
+    n = int(L.ludvig_batch_last_plan(None, 0))
+    arr = (BatchClass * max(1, n))()
+    n = int(L.ludvig_batch_last_plan(arr, n))
+    return [{f: int(getattr(arr[k], f)) for f, _ in BatchClass._fields_} for k in range(n)]
+
+
+def batch_forget_tuning():
+    """ludvig_batch_forget_tuning: the next batch times its classes again."""
+    _check(load().ludvig_batch_forget_tuning(), "ludvig_batch_forget_tuning")
 
 
 def uplift_accumulate(scene: Scene, cams_params, width, height, feats, num, den, stream=None, sync=True):
@@ -391,6 +415,9 @@ OPT_COUNT_NORMALISE = 1
 OPT_FAULT_ALLOC = 2
 OPT_FAULT_LAUNCH = 3
 OPT_AGG_CONFIG = 4
+OPT_GROUP_MB = 5
+OPT_BATCH_TUNE = 6
+OPT_BATCH_PACK = 7
 
 
 def set_option(option: int, value: int):

@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version(lib):
-    assert lib.ludvig_abi_version() == 10
+    assert lib.ludvig_abi_version() == 11
 
 
 def test_argument_errors_are_synchronous(lib):

@@ -113,7 +113,7 @@ def test_groups_that_outgrow_the_workspace_are_redone(d):
     pairs_near = int((ranges[:, 1] - ranges[:, 0]).sum())
     pairs_far = int((r_far[:, 1] - r_far[:, 0]).sum())
     print(f"pairs per view: far {pairs_far}, near {pairs_near}")
-    # a group of 16 near views needs several times what the 2 far views did
+    # the near views need several times what the 2 far views did
     assert 16 * pairs_near > 8 * 2 * max(pairs_far, 1)
     out = torch.empty((sc.n, d), device="cuda")
     beta = torch.empty((sc.n,), device="cuda")
@@ -126,3 +126,23 @@ def test_groups_that_outgrow_the_workspace_are_redone(d):
     out2, _ = ludvig.uplift(sc, near.params, near.width, near.height, F)
     torch.cuda.synchronize()
     assert rel_l2(out2.cpu().numpy(), f_ref, b_ref > 0) <= 1e-5
+
+
+@pytest.mark.parametrize("d,dtype", [(48, torch.bfloat16), (3, torch.float32), (40, torch.float32)])
+def test_many_groups_equal_one_group(d, dtype):
+    """With a 1 MiB group bound each of the 12 views is a group of its own
+    (12 asynchronous groups on alternating buffer sets); the result equals
+    the one-group call's to float32 rounding."""
+    wl = inputs.small_field_workload(n=8000, views=12, d=d, width=61, height=45)
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    F = device_features(wl, range(12), dtype)
+    one, b1 = ludvig.uplift(sc, wl.cams.params, wl.cams.width, wl.cams.height, F)
+    saved = ludvig.get_option(ludvig.OPT_GROUP_MB)
+    ludvig.set_option(ludvig.OPT_GROUP_MB, 1)
+    try:
+        many, bm = ludvig.uplift(sc, wl.cams.params, wl.cams.width, wl.cams.height, F)
+    finally:
+        ludvig.set_option(ludvig.OPT_GROUP_MB, saved)
+    torch.cuda.synchronize()
+    assert rel_l2(many.cpu().numpy(), one.cpu().numpy()) <= 1e-5
+    assert rel_l2(bm.cpu().numpy(), b1.cpu().numpy()) <= 1e-5

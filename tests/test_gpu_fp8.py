@@ -75,11 +75,13 @@ def test_fp8_arguments():
     assert q0.numel() == 0 and s0.numel() == 0
 
 
-@pytest.mark.parametrize("d,views", [(48, 3), (64, 20), (40, 3), (512, 2)])
-def test_uplift_fp8_equals_bf16_uplift_of_the_decoded_values(d, views):
+@pytest.mark.parametrize("d,views,group_mb", [(48, 3, 2048), (64, 20, 1), (40, 3, 2048), (3, 7, 1), (512, 2, 2048)])
+def test_uplift_fp8_equals_bf16_uplift_of_the_decoded_values(d, views, group_mb):
     """The aggregation decodes the codes itself when d % 16 == 0 (d = 48, 64,
-    512; 20 views: two groups, so the per-view scales are indexed across
-    groups); d = 40 takes the decode pass.  Either way the result is the
+    512; with a 1 MiB group bound every view is a group of its own, so the
+    scales are indexed by the views' coordinates across groups); d = 40 and
+    d = 3 take the decode pass (d = 3 with one-view groups: a view holds an
+    odd number of codes, so most groups' codes are not 4-byte aligned).  Either way the result is the
     bfloat16 uplift of x = decode(q) s_v rounded to bfloat16, here decoded by
     torch's float8_e4m3fn (float32 product, then bfloat16), to float32
     rounding (only the order of the atomic sums differs)."""
@@ -87,7 +89,12 @@ def test_uplift_fp8_equals_bf16_uplift_of_the_decoded_values(d, views):
     sc = ludvig.Scene.from_inputs(wl.scene)
     F = torch.stack([wl.features(v, device="cuda") for v in range(views)]).contiguous()
     q, s = ludvig.fp8_quantize(F)
-    out, beta = ludvig.uplift_fp8(sc, wl.cams.params, wl.cams.width, wl.cams.height, q, s)
+    saved = ludvig.get_option(ludvig.OPT_GROUP_MB)
+    ludvig.set_option(ludvig.OPT_GROUP_MB, group_mb)
+    try:
+        out, beta = ludvig.uplift_fp8(sc, wl.cams.params, wl.cams.width, wl.cams.height, q, s)
+    finally:
+        ludvig.set_option(ludvig.OPT_GROUP_MB, saved)
     X = (q.view(torch.float8_e4m3fn).float() * s.view(-1, 1, 1, 1)).to(torch.bfloat16).contiguous()
     ob, bb = ludvig.uplift(sc, wl.cams.params, wl.cams.width, wl.cams.height, X)
     torch.cuda.synchronize()
