@@ -641,19 +641,30 @@ def batched_form(pools, cams, slots=6):
     batched = [r["device_ms"] for r in runs]
     launches = ludvig.trace_read(reset=True)["kernel_launches"] / reps
     kept = runs[-1]["outputs"]
+    ludvig.batch_release_workspaces()     # the packed contexts; the unpacked form lends slot workspaces
     ludvig.set_option(ludvig.OPT_BATCH_PACK, 0)
+    unpacked_slots = 3   # each slot lends a workspace grown to its largest job: bounded beside the pools
+
+    def unpacked(n_slots):
+        r = serve.run_batch(jobs, pools, cams.params, W, H, slots=n_slots)
+        if r["errors"]:
+            raise RuntimeError(f"unpacked batched form: {r['errors']}")
+        return r["device_ms"]
+
     try:
-        serve.run_batch(jobs, pools, cams.params, W, H, slots=slots)     # the lent workspaces grow
+        unpacked(unpacked_slots)     # the lent workspaces grow
         ludvig.trace_read(reset=True)
         ludvig.trace_enable(True)    # stage split of the one-stream run (stages do not overlap there)
-        serial = serve.run_batch(jobs, pools, cams.params, W, H, slots=1)["device_ms"]
+        serial = unpacked(1)
         ludvig.trace_enable(False)
         tr = ludvig.trace_read(reset=True)
         stages = {k: v for k, v in tr["ms"].items() if v > 0}
         launches_unpacked = tr["kernel_launches"]
-        concurrent = serve.run_batch(jobs, pools, cams.params, W, H, slots=slots)["device_ms"]
+        concurrent = unpacked(unpacked_slots)
     finally:
         ludvig.set_option(ludvig.OPT_BATCH_PACK, 1)
+        ludvig.batch_release_workspaces()
+        torch.cuda.empty_cache()
     # bfloat16 vs float64 on sampled jobs: the two cheapest for the oracle
     checks = []
     for j in sorted(jobs, key=lambda j: j.scene.n * j.views * (j.d + 32))[:2]:
@@ -720,6 +731,7 @@ def batched_form(pools, cams, slots=6):
     out = {"value": work / (ms / 1e3), "unit": UNIT, "dtype": "bf16", "ms_per_batch": ms,
            "ms_per_batch_runs": batched, "serial_bf16_ms": serial, "unpacked_concurrent_bf16_ms": concurrent,
            "plain_f32_serial_ms": plain_ms,
+           "unpacked_concurrent_slots": unpacked_slots,
            "speedup_vs_serial_bf16": serial / ms, "speedup_vs_unpacked_concurrent": concurrent / ms,
            "speedup_vs_plain_f32": plain_ms / ms,
            "plain_f32_value": work / (plain_ms / 1e3), "gpu_launches_per_batch": launches,

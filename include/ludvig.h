@@ -110,10 +110,14 @@ typedef enum {
                                          of each class of jobs by timing candidates on the
                                          class's own jobs the first time it meets the class
                                          (see ludvig_uplift_batch); 0: LUDVIG_OPT_GROUP_MB */
-    LUDVIG_OPT_BATCH_PACK = 7         /* 1 (default): ludvig_uplift_batch packs the views of
+    LUDVIG_OPT_BATCH_PACK = 7,        /* 1 (default): ludvig_uplift_batch packs the views of
                                          tensor-core jobs into shared groups; 0: every job
                                          runs as its own ludvig_uplift call (the unpacked
                                          form, kept for comparison) */
+    LUDVIG_OPT_AGG_SMS = 8            /* 0 (default): the tensor-core aggregation runs one
+                                         persistent CTA on every SM; k > 0: on at most k SMs,
+                                         leaving the others to the next group's front end on
+                                         its own stream.  Results are the same to rounding */
 } ludvig_option;
 
 /* Sets an option; LUDVIG_ERR_ARG for an unknown option. */
@@ -280,14 +284,17 @@ typedef struct {
  * several jobs, so every stage launch serves many jobs.  The group size (the
  * per-view Gaussian scratch bound of a group) is picked per class: with
  * LUDVIG_OPT_BATCH_TUNE = 1 (default) by timing candidate sizes (256 MiB ..
- * 2 GiB) on up to 4 of the class's jobs and 256 of their views, into scratch
- * outputs, the first time the process meets the class (dtype, d, image size,
+ * 2 GiB) on up to 4 of the class's jobs (spread over its scene sizes) and 64
+ * of their views each, into scratch outputs, the first time the process meets the class (dtype, d, image size,
  * log2 of the mean scene size), and kept for later batches; else
- * LUDVIG_OPT_GROUP_MB.  A class that runs out of device memory is redone
- * with half the bound (down to 64 MiB).  Classes run on up to `slots` pooled contexts (each
- * with its own workspace and streams, driven by a host thread), largest
- * class first; other jobs run as ludvig_uplift calls on `slots` host threads
- * with pooled workspaces lent to their scenes.  1 <= slots <=
+ * LUDVIG_OPT_GROUP_MB.  A packed group also holds at most bound / 32 pixels
+ * (bound / 64 for float32: its weight rows grow with its pixels).  A class
+ * that runs out of device memory is redone with half the bound (down to
+ * 64 MiB).  The classes run one after another, largest first, on one
+ * pooled context (its own workspace and two streams) driven by the calling
+ * thread; the other jobs run as ludvig_uplift calls on `slots` host threads
+ * (the calling thread joins them after the classes) with pooled workspaces
+ * lent to their scenes.  1 <= slots <=
  * LUDVIG_MAX_BATCH_SLOTS.
  * Every job's work is ordered after the work already on `stream`, and
  * `stream` waits for all of it: to the caller the batch is one call on
@@ -311,9 +318,12 @@ ludvig_status ludvig_uplift_batch(const ludvig_uplift_job* jobs, int32_t n_jobs,
 typedef struct {
     int32_t dtype, d, width, height;
     int32_t jobs, views;
-    int32_t groups;     /* groups formed: launches of each pipeline stage (-1: the single calls) */
-    int32_t group_mb;   /* the groups' per-view Gaussian scratch bound, MiB */
-    int32_t tuned;      /* 1: group_mb was picked by the tuner */
+    int32_t groups;        /* groups formed: launches of each pipeline stage (-1: the single calls) */
+    int32_t group_mb;      /* the groups' scratch bound, MiB */
+    int32_t tuned;         /* 1: group_mb was picked by the tuner */
+    int32_t redone;        /* groups that outgrew the workspace and were run again */
+    int32_t workspace_mb;  /* device workspace of the class's context afterwards, MiB */
+    float ms;              /* host time of the class (tuning included), ms */
 } ludvig_batch_class;
 
 /* Copies up to cap classes of the last batch into out (host, may be NULL) and

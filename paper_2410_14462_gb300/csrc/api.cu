@@ -226,6 +226,7 @@ std::atomic<int64_t> g_opt_agg_config{0};
 std::atomic<int64_t> g_opt_group_mb{2048};
 std::atomic<int64_t> g_opt_batch_tune{1};
 std::atomic<int64_t> g_opt_batch_pack{1};
+std::atomic<int64_t> g_opt_agg_sms{0};
 }
 bool option_f32_tensor_cores() { return g_opt_f32_tc.load() != 0; }
 bool option_count_normalise() { return g_opt_count.load() != 0; }
@@ -233,6 +234,7 @@ int option_agg_config() { return (int)g_opt_agg_config.load(); }
 int64_t option_group_bytes() { return g_opt_group_mb.load() << 20; }
 bool option_batch_tune() { return g_opt_batch_tune.load() != 0; }
 bool option_batch_pack() { return g_opt_batch_pack.load() != 0; }
+int option_agg_sms() { return (int)g_opt_agg_sms.load(); }
 }  // namespace ludvig
 
 extern "C" ludvig_status ludvig_set_option(int32_t option, int64_t value) {
@@ -269,6 +271,13 @@ extern "C" ludvig_status ludvig_set_option(int32_t option, int64_t value) {
         case LUDVIG_OPT_BATCH_PACK:
             g_opt_batch_pack.store(value != 0);
             return LUDVIG_OK;
+        case LUDVIG_OPT_AGG_SMS:
+            if (value < 0 || value > 4096) {
+                set_error("LUDVIG_OPT_AGG_SMS must be in [0, 4096]");
+                return LUDVIG_ERR_ARG;
+            }
+            g_opt_agg_sms.store(value);
+            return LUDVIG_OK;
         default:
             set_error("unknown option %d", option);
             return LUDVIG_ERR_ARG;
@@ -285,6 +294,7 @@ extern "C" int64_t ludvig_get_option(int32_t option) {
         case LUDVIG_OPT_GROUP_MB: return g_opt_group_mb.load();
         case LUDVIG_OPT_BATCH_TUNE: return g_opt_batch_tune.load();
         case LUDVIG_OPT_BATCH_PACK: return g_opt_batch_pack.load();
+        case LUDVIG_OPT_AGG_SMS: return g_opt_agg_sms.load();
         default: return -1;
     }
 }

@@ -11,16 +11,18 @@
 // own scene, camera, feature coordinate and output in the kernels'
 // parameters), so that a launch of each pipeline stage serves up to 128
 // views of many jobs.  The group size (views per group under a bound on the
-// per-view Gaussian scratch) is picked per class by a tuner that times
-// candidate sizes on the class's own jobs the first time it meets the class
-// (LUDVIG_OPT_BATCH_TUNE), and kept for later batches.  Classes run on up to
-// `slots` pooled contexts (a workspace, two streams and their events each),
-// each driven by a host thread, largest class first.
+// per-view Gaussian scratch and the pixels) is picked per class by a tuner
+// that times candidate sizes on the class's own jobs the first time it meets
+// the class (LUDVIG_OPT_BATCH_TUNE), and kept for later batches.  The classes
+// run one after another, largest first, on one pooled context (a workspace,
+// two streams and their events) driven by the calling thread: each class
+// fills the GPU with its groups, and one context bounds the weight-row
+// memory.
 //
 // Other jobs (the CUDA-core float32 path) run as ludvig_uplift calls on
-// `slots` host threads, each with its own stream and a pooled workspace lent
-// to the job's scene for the call (swapped in and back out), longest job
-// first.
+// `slots` host threads (the calling thread joins them after the classes),
+// each with its own stream and a pooled workspace lent to the job's scene for
+// the call (swapped in and back out), longest job first.
 //
 // Every slot stream waits for an event recorded on the caller's stream before
 // its first job, and the caller's stream waits for every slot's final event,
@@ -176,8 +178,9 @@ std::tuple<int, int, int, int, int> tune_key(const ludvig_uplift_job* jobs, cons
     return std::make_tuple(c.key.dtype, c.key.d, c.key.width, c.key.height, (int)std::floor(std::log2(mean)));
 }
 
-// Times each candidate on up to 4 jobs of the class and up to 256 of their
-// views, outputs in the context's scratch (the jobs' outputs are untouched);
+// Times each candidate on up to 4 jobs of the class (spread over its scene
+// sizes) and up to 64 views of each, outputs in the context's scratch (the
+// jobs' outputs are untouched);
 // one run at the largest candidate first grows the workspace.  A candidate
 // that runs out of device memory is dropped with every larger one.
 ludvig_status tune_class(ludvig_scene* ctx, const ludvig_uplift_job* jobs, const JobClass& c, cudaStream_t st,
@@ -186,10 +189,17 @@ ludvig_status tune_class(ludvig_scene* ctx, const ludvig_uplift_job* jobs, const
     std::vector<PackedJob> sample;
     int64_t out_elems = 0, beta_elems = 0;
     int views = 0;
-    for (int32_t j : c.jobs) {
-        if ((int)sample.size() == 4 || views >= 256) break;
+    // up to 4 jobs spread over the class's sizes (largest first), 64 views each
+    std::vector<int32_t> pick;
+    const size_t nj = c.jobs.size();
+    for (size_t q = 0; q < 4 && q < nj; ++q) {
+        const int32_t j = c.jobs[nj <= 4 ? q : q * (nj - 1) / 3];
+        if (pick.empty() || pick.back() != j) pick.push_back(j);
+    }
+    for (int32_t j : pick) {
+        if (views >= 256) break;
         const ludvig_uplift_job& J = jobs[j];
-        const int nv = std::min(J.n_views, 256 - views);
+        const int nv = std::min(std::min(J.n_views, 64), 256 - views);
         if (nv <= 0 || J.scene->n == 0) continue;
         // scratch outputs of at most about 2 GiB (the first job always)
         if (!sample.empty() && out_elems + J.scene->n * (int64_t)c.key.d > ((int64_t)1 << 29)) break;
@@ -201,15 +211,21 @@ ludvig_status tune_class(ludvig_scene* ctx, const ludvig_uplift_job* jobs, const
     }
     *best = option_group_bytes();
     if (sample.empty()) return LUDVIG_OK;
-    float *out, *beta;
-    LV_TRY(ctx->ws.get("tune.out", (size_t)out_elems, &out));
-    LV_TRY(ctx->ws.get("tune.beta", (size_t)beta_elems, &beta));
-    for (PackedJob& p : sample) {
-        p.out = out;
-        p.beta = beta;
-        out += round_up(p.scene->n * c.key.d, 64);
-        beta += round_up(p.scene->n, 64);
-    }
+    // the scratch outputs live in the context's workspace: bound again after
+    // every reset of the context
+    auto bind_scratch = [&]() -> ludvig_status {
+        float *out, *beta;
+        LV_TRY(ctx->ws.get("tune.out", (size_t)out_elems, &out));
+        LV_TRY(ctx->ws.get("tune.beta", (size_t)beta_elems, &beta));
+        for (PackedJob& p : sample) {
+            p.out = out;
+            p.beta = beta;
+            out += round_up(p.scene->n * c.key.d, 64);
+            beta += round_up(p.scene->n, 64);
+        }
+        return LUDVIG_OK;
+    };
+    LV_TRY(bind_scratch());
     cudaEvent_t e0, e1;
     LV_CUDA(cudaEventCreate(&e0));
     LV_CUDA(cudaEventCreate(&e1));
@@ -229,6 +245,7 @@ ludvig_status tune_class(ludvig_scene* ctx, const ludvig_uplift_job* jobs, const
         if (r == LUDVIG_OK) break;
         if (r != LUDVIG_ERR_OOM || top == 0) return r;
         reset_context(ctx);
+        LV_TRY(bind_scratch());
     }
     float best_ms = 0.f;
     for (int k = 0; k <= top; ++k) {
@@ -361,12 +378,14 @@ extern "C" ludvig_status ludvig_uplift_batch(const ludvig_uplift_job* jobs, int3
     std::stable_sort(plain.begin(), plain.end(),
                      [&](int32_t a, int32_t b) { return job_cost(jobs[a]) > job_cost(jobs[b]); });
 
-    // work items: the classes, then the single jobs, each largest first
-    const int nitems = (int)(classes.size() + plain.size());
+    // the classes run in the calling thread on one context, largest first
+    // (each fills the GPU with groups of many views; one context bounds the
+    // weight-row memory); the single jobs run on every slot thread, the
+    // calling thread joining them after the classes
     int dev = 0;
     LV_CUDA(cudaGetDevice(&dev));
     cudaStream_t caller = static_cast<cudaStream_t>(stream);
-    const int nslots = std::max(1, std::min<int>(slots, nitems));
+    const int nslots = std::max(1, std::min<int>(slots, (int)plain.size() + (classes.empty() ? 0 : 1)));
     SlotResources res;
     res.streams.assign((size_t)nslots, nullptr);
     res.done.assign((size_t)nslots, nullptr);
@@ -380,81 +399,98 @@ extern "C" ludvig_status ludvig_uplift_batch(const ludvig_uplift_job* jobs, int3
 
     std::atomic<int> next{0};
     std::vector<cudaError_t> slot_err((size_t)nslots, cudaSuccess);
+    std::vector<PackedStats> cstats(classes.size());
+    std::vector<float> cms(classes.size(), 0.f);
+    std::vector<int64_t> cws(classes.size(), 0);
     auto fail = [&](int32_t j, ludvig_status r) {
         status[(size_t)j] = r;
         message[(size_t)j] = ludvig_last_error();
     };
+    auto run_classes = [&](cudaStream_t st) {
+        if (classes.empty()) return;
+        ludvig_scene* ctx = nullptr;
+        try {
+            ctx = take_context(dev);
+        } catch (...) {
+        }
+        for (size_t i = 0; i < classes.size(); ++i) {
+            JobClass& c = classes[i];
+            ludvig_status r = LUDVIG_ERR_OOM;
+            if (!ctx) set_error("no context for the packed jobs");
+            try {
+                const auto t0 = std::chrono::steady_clock::now();
+                if (ctx) r = class_group_bytes(ctx, jobs, c, st);
+                if (ctx && r == LUDVIG_OK) {
+                    const size_t vb = (size_t)c.key.width * c.key.height * c.key.d * elem_size(c.key.dtype);
+                    std::vector<PackedJob> pj;
+                    for (int32_t j : c.jobs) {
+                        const ludvig_uplift_job& J = jobs[j];
+                        pj.push_back(PackedJob{J.scene, J.cams, J.n_views,
+                                               (int)((static_cast<const char*>(J.feats) - c.base) / vb), J.out,
+                                               J.beta});
+                    }
+                    r = uplift_packed(ctx, pj.data(), (int)pj.size(), c.base, c.key.dtype, c.key.d, c.key.width,
+                                      c.key.height, c.group_bytes, st, &cstats[i]);
+                    // out of device memory: smaller groups (the outputs are zeroed again)
+                    while (r == LUDVIG_ERR_OOM && c.group_bytes > 64 * kMiB) {
+                        reset_context(ctx);
+                        c.group_bytes /= 2;
+                        r = uplift_packed(ctx, pj.data(), (int)pj.size(), c.base, c.key.dtype, c.key.d, c.key.width,
+                                          c.key.height, c.group_bytes, st, &cstats[i]);
+                    }
+                    c.groups = cstats[i].groups;
+                }
+                cms[i] = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+                if (ctx) cws[i] = (int64_t)ctx->ws.device_bytes();
+            } catch (...) {
+                set_error("internal error in a packed class");
+                r = LUDVIG_ERR_INTERNAL;
+            }
+            if (r != LUDVIG_OK)
+                for (int32_t j : c.jobs) fail(j, r);
+        }
+        if (ctx) {
+            cudaStreamSynchronize(st);   // the context returns to the pool once idle
+            try {
+                return_context(dev, ctx);
+            } catch (...) {
+            }
+        }
+    };
     auto worker = [&](int k) {
         cudaError_t e = cudaSetDevice(dev);
         cudaStream_t st = res.streams[(size_t)k];
+        if (k == 0 && e == cudaSuccess) run_classes(st);
         std::unique_ptr<Arena> ws;
-        ludvig_scene* ctx = nullptr;
         for (;;) {
             const int i = next.fetch_add(1);
-            if (i >= nitems) break;
+            if (i >= (int)plain.size()) break;
+            const int32_t j = plain[(size_t)i];
             try {   // nothing may escape a std::thread
-                if (i < (int)classes.size()) {
-                    JobClass& c = classes[(size_t)i];
-                    ludvig_status r = LUDVIG_ERR_CUDA;
-                    if (e == cudaSuccess && !ctx) ctx = take_context(dev);
-                    if (e == cudaSuccess && ctx) {
-                        r = class_group_bytes(ctx, jobs, c, st);
-                        if (r == LUDVIG_OK) {
-                            const size_t vb = (size_t)c.key.width * c.key.height * c.key.d * elem_size(c.key.dtype);
-                            std::vector<PackedJob> pj;
-                            for (int32_t j : c.jobs) {
-                                const ludvig_uplift_job& J = jobs[j];
-                                pj.push_back(PackedJob{J.scene, J.cams, J.n_views,
-                                                       (int)((static_cast<const char*>(J.feats) - c.base) / vb),
-                                                       J.out, J.beta});
-                            }
-                            r = uplift_packed(ctx, pj.data(), (int)pj.size(), c.base, c.key.dtype, c.key.d,
-                                              c.key.width, c.key.height, c.group_bytes, st, &c.groups);
-                            // out of device memory: smaller groups (the outputs are zeroed again)
-                            while (r == LUDVIG_ERR_OOM && c.group_bytes > 64 * kMiB) {
-                                reset_context(ctx);
-                                c.group_bytes /= 2;
-                                r = uplift_packed(ctx, pj.data(), (int)pj.size(), c.base, c.key.dtype, c.key.d,
-                                                  c.key.width, c.key.height, c.group_bytes, st, &c.groups);
-                            }
-                        }
-                    } else {
-                        set_error("slot setup failed");
-                    }
-                    if (r != LUDVIG_OK)
-                        for (int32_t j : c.jobs) fail(j, r);
+                const ludvig_uplift_job& J = jobs[j];
+                if (!ws) ws = take_workspace(dev);
+                ludvig_status r = LUDVIG_ERR_CUDA;
+                if (e == cudaSuccess) {
+                    J.scene->ws.swap(*ws);   // lend the slot's workspace to the job
+                    r = ludvig_uplift(J.scene, J.cams, J.n_views, J.width, J.height, J.feats, J.dtype, J.d,
+                                      J.out, J.beta, st);
+                    // complete it (a redo of what did not fit uses the lent workspace too)
+                    if (r == LUDVIG_OK) r = ludvig_sync(J.scene);
+                    J.scene->ws.swap(*ws);
                 } else {
-                    const int32_t j = plain[(size_t)(i - (int)classes.size())];
-                    const ludvig_uplift_job& J = jobs[j];
-                    if (!ws) ws = take_workspace(dev);
-                    ludvig_status r = LUDVIG_ERR_CUDA;
-                    if (e == cudaSuccess) {
-                        J.scene->ws.swap(*ws);   // lend the slot's workspace to the job
-                        r = ludvig_uplift(J.scene, J.cams, J.n_views, J.width, J.height, J.feats, J.dtype, J.d,
-                                          J.out, J.beta, st);
-                        // complete it (a redo of what did not fit uses the lent workspace too)
-                        if (r == LUDVIG_OK) r = ludvig_sync(J.scene);
-                        J.scene->ws.swap(*ws);
-                    } else {
-                        set_error("slot setup failed");
-                    }
-                    if (r != LUDVIG_OK) fail(j, r);
+                    set_error("slot setup failed");
                 }
+                if (r != LUDVIG_OK) fail(j, r);
             } catch (...) {
-                if (i < (int)classes.size()) {
-                    for (int32_t j : classes[(size_t)i].jobs) status[(size_t)j] = LUDVIG_ERR_INTERNAL;
-                } else {
-                    status[(size_t)plain[(size_t)(i - (int)classes.size())]] = LUDVIG_ERR_INTERNAL;
-                }
+                status[(size_t)j] = LUDVIG_ERR_INTERNAL;
             }
         }
         slot_err[(size_t)k] = cudaEventRecord(res.done[(size_t)k], st);
-        // workspaces and contexts return to the pools once their streams are idle
+        // the workspace returns to the pool once its stream is idle
         const cudaError_t se = cudaStreamSynchronize(st);
         if (slot_err[(size_t)k] == cudaSuccess) slot_err[(size_t)k] = se;
         try {
             if (ws) return_workspace(dev, std::move(ws));
-            if (ctx) return_context(dev, ctx);
         } catch (...) {
         }
     };
@@ -474,8 +510,12 @@ extern "C" ludvig_status ludvig_uplift_batch(const ludvig_uplift_job* jobs, int3
         std::lock_guard<std::mutex> lk(g_plan_mu);
         std::vector<ludvig_batch_class>& plan = last_plan();
         plan.clear();
-        for (const JobClass& c : classes) {
+        for (size_t i = 0; i < classes.size(); ++i) {
+            const JobClass& c = classes[i];
             ludvig_batch_class b{};
+            b.redone = cstats[i].redone;
+            b.workspace_mb = (int32_t)(cws[i] >> 20);
+            b.ms = cms[i];
             b.dtype = c.key.dtype;
             b.d = c.key.d;
             b.width = c.key.width;

@@ -116,20 +116,34 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ SceneBa
                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                           uint32_t* __restrict__ ntile, float* __restrict__ dbg_rec,
                           int32_t* __restrict__ dbg_rect, int prune) {
-    // every block is full: nv * npad is a multiple of the block size
+    // every block is full and lies in one view: npad is a multiple of the
+    // block size.  The view's camera and scene go to shared memory once.
+    __shared__ Cam cam;
+    __shared__ const float4* s_geo;
+    __shared__ const float4* s_cov_a;
+    __shared__ const float2* s_cov_b;
+    __shared__ int64_t s_n;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int v = (int)(idx / npad);
+    const int v = (int)((int64_t)blockIdx.x * blockDim.x / npad);
+    if (threadIdx.x < 16) reinterpret_cast<float*>(&cam)[threadIdx.x] = reinterpret_cast<const float*>(&cb.cam[v])[threadIdx.x];
+    if (threadIdx.x == 0) {
+        s_geo = sb.geo[v];
+        s_cov_a = sb.cov_a[v];
+        s_cov_b = sb.cov_b[v];
+        s_n = sb.n[v];
+    }
+    __syncthreads();
     const int64_t i = idx - (int64_t)v * npad;
-    const bool real = i < sb.n[v];
+    const bool real = i < s_n;
     Projected P{};
     float op = 0.f;
     if (real) {
-        const float4 g = sb.geo[v][i];
-        const float4 ca = sb.cov_a[v][i];
-        const float2 cbv = sb.cov_b[v][i];
+        const float4 g = s_geo[i];
+        const float4 ca = s_cov_a[i];
+        const float2 cbv = s_cov_b[i];
         const float m[3] = {g.x, g.y, g.z};
         const float S6[6] = {ca.x, ca.y, ca.z, ca.w, cbv.x, cbv.y};
-        P = project_gaussian(m, S6, cb.cam[v], width, height);
+        P = project_gaussian(m, S6, cam, width, height);
         op = g.w;
         const int64_t o = (int64_t)v * n + i;
         rec_a[o] = make_float4(P.mx, P.my, P.ca, P.cb);
@@ -1138,11 +1152,18 @@ ludvig_status uplift_group(ludvig_scene* ctx, const GroupViews& g, int width, in
     return LUDVIG_OK;
 }
 
+// Pixels a group of the given scratch budget may hold: its weight rows and
+// lists grow with its pixels (a few hundred bytes per pixel at paper scale),
+// so a group holds at most budget / 256 pixels.
+int64_t group_pixels(int64_t budget) { return std::max<int64_t>(1, budget / 256); }
+
 // Views per group: up to kMaxViews, with the per-group Gaussian scratch
 // (about 120 bytes per Gaussian and view) kept within the group budget
-// (LUDVIG_OPT_GROUP_MB, 2 GB by default).
-int views_per_group(int64_t n, int n_views, int64_t budget) {
-    int vc = std::min<int>(kMaxViews, std::max<int>(1, n_views));
+// (LUDVIG_OPT_GROUP_MB, 2 GB by default) and the pixels within
+// group_pixels(budget).
+int views_per_group(int64_t n, int n_views, int64_t view_px, int64_t budget) {
+    int64_t vc = std::min<int>(kMaxViews, std::max<int>(1, n_views));
+    vc = std::min<int64_t>(vc, group_pixels(budget) / std::max<int64_t>(1, view_px));
     const int64_t per_view = std::max<int64_t>(1, n) * 120;
     return (int)std::max<int64_t>(1, std::min<int64_t>(vc, budget / per_view));
 }
@@ -1173,7 +1194,7 @@ ludvig_status run_checked(ludvig_scene* ctx, const GroupViews& g, int width, int
 // Views [v0, v0 + nv_total) of one scene's call, group by group, checked.
 ludvig_status run_checked_range(ludvig_scene* s, const ludvig_camera* cams, int v0, int nv_total, int width,
                                 int height, const FeatSrc& src, float* num, float* den, cudaStream_t st) {
-    const int vc = views_per_group(s->n, nv_total, option_group_bytes());
+    const int vc = views_per_group(s->n, nv_total, (int64_t)width * height, option_group_bytes());
     for (int end = v0 + nv_total; v0 < end;) {
         const int nv = std::min(vc, end - v0);
         LV_TRY(run_checked(s, scene_group(s, cams, v0, nv, num, den), width, height, src, st));
@@ -1415,7 +1436,7 @@ ludvig_status run_call(ludvig_scene* s, int kind, const FeatSrc& src, const ludv
         LV_TRY(s->ws.get("pad.num", (size_t)n * kPadD, &pad_num));
         LV_CUDA(cudaMemsetAsync(pad_num, 0, sizeof(float) * (size_t)n * kPadD, st));
     }
-    const int vc = views_per_group(n, n_views, option_group_bytes());
+    const int vc = views_per_group(n, n_views, (int64_t)width * height, option_group_bytes());
     std::vector<GroupViews> groups;
     for (int v0 = 0; v0 < n_views; v0 += vc)
         groups.push_back(scene_group(s, cams, v0, std::min(vc, n_views - v0), padded ? pad_num : num, den));
@@ -1529,9 +1550,18 @@ ludvig_status ensure_status(ludvig_scene* s) {
 // ---------------------------------------------------------------- packed batches
 bool packed_supported(int dtype, int d) { return use_padded(dtype, d) || use_tensor_cores(dtype, d); }
 
+// Packed groups may take more pixels than one call's groups (a batch runs
+// one context at a time): about 32 bytes of the budget per pixel and weight
+// term.
+int64_t packed_pixels(int64_t group_bytes, int dtype) {
+    return std::max<int64_t>(1, group_bytes / (dtype == LUDVIG_F32 ? 64 : 32));
+}
+
 ludvig_status uplift_packed(ludvig_scene* ctx, const PackedJob* jobs, int njobs, const void* feats, int dtype, int d,
-                            int width, int height, int64_t group_bytes, cudaStream_t st, int* groups_formed) {
-    if (groups_formed) *groups_formed = 0;
+                            int width, int height, int64_t group_bytes, cudaStream_t st, PackedStats* stats) {
+    PackedStats dummy;
+    if (!stats) stats = &dummy;
+    *stats = PackedStats();
     if (njobs <= 0) return LUDVIG_OK;
     if (!packed_supported(dtype, d)) {
         set_error("packed uplift needs the tensor-core path (dtype %d, d %d)", dtype, d);
@@ -1565,7 +1595,9 @@ ludvig_status uplift_packed(ludvig_scene* ctx, const PackedJob* jobs, int njobs,
         if (padded) LV_CUDA(cudaMemsetAsync(acc[j], 0, sizeof(float) * (size_t)n * kPadD, st));
     }
     // the groups: every job's views in job order; a group closes at kMaxViews
-    // views or when one more view would take its Gaussian scratch past the budget
+    // views, at group_pixels(group_bytes) pixels, or when one more view would
+    // take its Gaussian scratch past the budget
+    const int64_t max_views = std::max<int64_t>(1, packed_pixels(group_bytes, dtype) / ((int64_t)width * height));
     std::vector<GroupViews> groups;
     GroupViews cur;
     for (int j = 0; j < njobs; ++j) {
@@ -1574,7 +1606,8 @@ ludvig_status uplift_packed(ludvig_scene* ctx, const PackedJob* jobs, int njobs,
         for (int v = 0; v < jobs[j].n_views; ++v) {
             int64_t nmax = std::max(cur.nmax, sc->n);
             const int64_t need = (int64_t)(cur.v.size() + 1) * round_up(nmax, kRadixTile) * 120;
-            if (!cur.v.empty() && ((int)cur.v.size() == kMaxViews || need > group_bytes)) {
+            if (!cur.v.empty() &&
+                ((int)cur.v.size() == kMaxViews || (int64_t)cur.v.size() == max_views || need > group_bytes)) {
                 groups.push_back(std::move(cur));
                 cur = GroupViews();
                 nmax = sc->n;
@@ -1584,7 +1617,19 @@ ludvig_status uplift_packed(ludvig_scene* ctx, const PackedJob* jobs, int njobs,
         }
     }
     if (!cur.v.empty()) groups.push_back(std::move(cur));
-    if (groups_formed) *groups_formed = (int)groups.size();
+    stats->groups = (int)groups.size();
+    // on a failure, nothing of the call may still run when it returns
+    struct Drain {
+        ludvig_scene* c;
+        cudaStream_t st;
+        bool armed = true;
+        ~Drain() {
+            if (!armed) return;
+            if (c->st_front) cudaStreamSynchronize(c->st_front);
+            if (c->st_agg) cudaStreamSynchronize(c->st_agg);
+            cudaStreamSynchronize(st);
+        }
+    } drain{ctx, st};
     if (!groups.empty()) {
         LV_TRY(ensure_async(ctx, (int)groups.size()));
         size_t first = 0;
@@ -1600,8 +1645,10 @@ ludvig_status uplift_packed(ludvig_scene* ctx, const PackedJob* jobs, int njobs,
             LV_CUDA(cudaEventSynchronize(ctx->ev_done));
             if (ctx->hstat[1]) {   // groups that did not fit: redone checked (the workspace grows)
                 for (size_t k = first; k < groups.size(); ++k)
-                    if (!group_fits(ctx->hdiag[k - first], gpcap[k - first], gccap[k - first]))
+                    if (!group_fits(ctx->hdiag[k - first], gpcap[k - first], gccap[k - first])) {
                         LV_TRY(run_checked(ctx, groups[k], width, height, src, st));
+                        ++stats->redone;
+                    }
                 LV_CUDA(cudaMemsetAsync(ctx->dstat + 1, 0, sizeof(int), st));
             }
         }
@@ -1615,6 +1662,7 @@ ludvig_status uplift_packed(ludvig_scene* ctx, const PackedJob* jobs, int njobs,
         }
         LV_TRY(normalise(n, d, jobs[j].out, den[j], jobs[j].out, nullptr, nullptr, st));
     }
+    drain.armed = false;
     return read_status(ctx, st);
 }
 
@@ -1761,7 +1809,7 @@ extern "C" ludvig_status ludvig_render(ludvig_scene_t scene, const ludvig_camera
     LV_TRY(ensure_status(scene));
     LV_TRY(resolve_pending(scene));
     const int64_t view_elems = (int64_t)width * height * d;
-    int vc = views_per_group(scene->n, n_views, option_group_bytes());
+    int vc = views_per_group(scene->n, n_views, (int64_t)width * height, option_group_bytes());
     int v0 = 0;
     while (v0 < n_views) {
         const int nv = std::min(vc, n_views - v0);

@@ -69,9 +69,16 @@ struct PackedJob {
 // ctx's streams and workspace with device-side capacity checks; what did not
 // fit is redone before the call returns (it waits for the work).  Every job's
 // work is ordered after the work on `st`, and `st` waits for all of it.
-// *groups_formed (may be null) receives the number of groups.
+// A group also holds at most packed_pixels(group_bytes, dtype) pixels (its
+// weight rows grow with them).  *stats (may be null) receives the groups
+// formed and those redone.
+struct PackedStats {
+    int groups = 0;
+    int redone = 0;
+};
+int64_t packed_pixels(int64_t group_bytes, int dtype);
 ludvig_status uplift_packed(ludvig_scene* ctx, const PackedJob* jobs, int njobs, const void* feats, int dtype, int d,
-                            int width, int height, int64_t group_bytes, cudaStream_t st, int* groups_formed);
+                            int width, int height, int64_t group_bytes, cudaStream_t st, PackedStats* stats);
 
 // Whether ludvig_uplift with these features runs on the tensor cores (the
 // precondition of uplift_packed).

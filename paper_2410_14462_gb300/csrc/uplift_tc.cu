@@ -64,6 +64,7 @@ namespace ludvig {
 
 bool option_count_normalise();
 int option_agg_config();
+int option_agg_sms();
 
 namespace {
 
@@ -1582,7 +1583,8 @@ ludvig_status tc_aggregate(const TileWeights& t, int nv, int width, int height, 
     g.plan = t.plan;
     g.scales = scales;
     g.views = av;
-    const int grid = std::min(sms, nitems);
+    const int cap_sms = option_agg_sms();
+    const int grid = std::min(cap_sms > 0 ? std::min(cap_sms, sms) : sms, nitems);
     StageScope agg_scope(LUDVIG_STAGE_AGGREGATE, st);
     if (dtype == kDtypeE4M3) return dispatch_agg_cf<1, 2>(g, maps, grid, st);
     if (NT == 2) return dispatch_agg<2>(g, maps, grid, st);

@@ -309,7 +309,8 @@ def batch_release_workspaces():
 class BatchClass(ctypes.Structure):
     """ludvig_batch_class: one class of the last batch."""
     _fields_ = [(name, ctypes.c_int32) for name in
-                ("dtype", "d", "width", "height", "jobs", "views", "groups", "group_mb", "tuned")]
+                ("dtype", "d", "width", "height", "jobs", "views", "groups", "group_mb", "tuned", "redone",
+                 "workspace_mb")] + [("ms", ctypes.c_float)]
 
 
 def batch_last_plan() -> list[dict]:
@@ -319,7 +320,8 @@ def batch_last_plan() -> list[dict]:
     n = int(L.ludvig_batch_last_plan(None, 0))
     arr = (BatchClass * max(1, n))()
     n = int(L.ludvig_batch_last_plan(arr, n))
-    return [{f: int(getattr(arr[k], f)) for f, _ in BatchClass._fields_} for k in range(n)]
+    return [{f: (float if f == "ms" else int)(getattr(arr[k], f)) for f, _ in BatchClass._fields_}
+            for k in range(n)]
 
 
 def batch_forget_tuning():
@@ -418,6 +420,7 @@ OPT_AGG_CONFIG = 4
 OPT_GROUP_MB = 5
 OPT_BATCH_TUNE = 6
 OPT_BATCH_PACK = 7
+OPT_AGG_SMS = 8
 
 
 def set_option(option: int, value: int):
