@@ -270,7 +270,7 @@ def cpu_baseline(wl, views=4):
 # 16-view launch): (workload, dtype, d) -> (bytes, views in the captured
 # launch).  Scaled to a launch by its views; re-measure whenever the kernel
 # changes.
-TRAFFIC = {("paper", "f32", 384): (28.01e9, 16)}
+TRAFFIC = {("paper", "f32", 384): (26.17e9, 15)}
 
 
 def roofline(tr, steps, alg_bytes_step, traffic_key=None, views_per_launch=None):
@@ -754,7 +754,9 @@ def serving_form(pools, cams, slots=2, n_requests=900, rate=200.0):
     over {1, 64, 384, 512}, and half of them then run U[20, 100] diffusion
     steps (k = 16 graph from an uplift of 20 views at D = 384) on the uplifted
     first channel.  A 150 GB budget covers the replicas, every replica's and
-    graph's workspace and the outputs in flight.  The first run offers more
+    graph's workspace and the outputs in flight; the replicas' groups are
+    bounded at 512 MiB of scratch (LUDVIG_OPT_GROUP_MB) so that eight
+    workspaces leave room for the outputs.  The first run offers more
     work than the GPU serves for 4.5 s (the queue grows), so its throughput
     is the service capacity; the second replays 100 requests at 70% of that
     capacity.  Both report latency percentiles and the queue depth at
@@ -769,6 +771,8 @@ def serving_form(pools, cams, slots=2, n_requests=900, rate=200.0):
         graphs.append(ludvig.Graph(sc, 16, f, spatial_h=0.01))
         del f
     pools = {d: pools[d] for d in (1, 64, 384, 512)}
+    group_mb = ludvig.get_option(ludvig.OPT_GROUP_MB)
+    ludvig.set_option(ludvig.OPT_GROUP_MB, 512)
     server = serve.Server(scenes, graphs, pools, cams.params, W, H, 150e9, slots=slots)
     # warm-up: every replica's workspace grows to the largest request
     warm = [serve.Request(i, 0.0, i % len(scenes), 512, 0, 150, 100) for i in range(len(scenes) * slots)]
@@ -790,6 +794,7 @@ def serving_form(pools, cams, slots=2, n_requests=900, rate=200.0):
     under = serve.latency_summary(res2)
     span2 = max(r.done for r in res2) - min(r.arrival for r in res2)
     server.close()
+    ludvig.set_option(ludvig.OPT_GROUP_MB, group_mb)
     for g in graphs:
         g.close()
     for sc in scenes:
@@ -803,6 +808,7 @@ def serving_form(pools, cams, slots=2, n_requests=900, rate=200.0):
             "config": {"workload": "4 resident scenes N 250k/500k/750k/1M (seeds 40-43); Poisson arrivals; "
                                    "V U[10, 150] of 640x480, D U{1, 64, 384, 512} bf16; 50% + U[20, 100] "
                                    "diffusion steps", "slots_per_scene": slots, "budget_bytes": 150e9,
+                       "group_mb": 512,
                        "resident_bytes_after_warmup": resident,
                        "requests": [n_requests, 100], "seeds": [4, 45]}}
 

@@ -257,7 +257,13 @@ def latency_summary(results: list[Result]) -> dict:
     lat = np.array([r.latency for r in ok]) * 1e3
     span = max(r.done for r in results) - min(r.arrival for r in results) if results else 0.0
     depth = np.array([r.depth for r in results])
+    reasons = {}
+    for r in results:
+        if not r.ok:
+            key = r.error.split(":")[0][:60]
+            reasons[key] = reasons.get(key, 0) + 1
     return {"requests": len(results), "served": len(ok), "rejected": len(results) - len(ok),
+            "rejected_reasons": reasons,
             "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
             "mean_ms": float(lat.mean()) if lat.size else None,
