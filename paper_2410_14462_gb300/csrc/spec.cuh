@@ -339,6 +339,45 @@ __device__ __forceinline__ uint32_t block_mask(const Reach& R, float mx, float m
     return m;
 }
 
+// A superset of block_mask's bits at a fraction of its cost, for the
+// compositing kernels' per-batch skip test (it decides no weight: a block it
+// keeps in vain costs only the per-pixel alpha test that then finds nothing).
+// The same closed form with the hardware's approximate reciprocal and
+// reciprocal square root in place of the correctly rounded division and
+// square root; their relative error (a few ulp) is covered by widening the
+// x-ranges by 2e-3 (|dx| + 1) + 0.05 px and the dy-range by 2e-4 relative +
+// 0.05 px, well above what the exact form's own slack needs.
+__device__ __forceinline__ float sqrt_approx(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+
+__device__ __forceinline__ uint32_t block_mask_fast(float mx, float my, float a, float b, float c, float op, int tx,
+                                                    int ty) {
+    if (op < kAlphaMin) return 0u;
+    const float thr = 2.0f * __logf(255.0f * op) * 1.001f + 1e-3f;
+    const float det = a * c - b * b;
+    if (!(det > 0.0f) || !(thr > 0.0f) || !(a > 0.0f) || !(c > 0.0f)) return 0xffu;
+    const float inv_a = __fdividef(1.0f, a), inv_det = __fdividef(1.0f, det);
+    const float umax = sqrt_approx(thr * c * inv_det);
+    const float wmax = sqrt_approx(thr * a * inv_det) * 1.0002f + 0.05f;
+    const float ws = -b * umax * __fdividef(1.0f, c);
+    const float thra = thr * a;
+    const float epsx = 2e-3f * (umax + 1.0f) + 0.05f;
+    const float xt = (float)(tx * kTile) + 0.5f, yt = (float)(ty * kTile) + 0.5f;
+    uint32_t m = 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float ylo = yt + (float)(4 * k);
+        const float w0 = fmaxf(my - (ylo + 3.0f), -wmax), w1 = fminf(my - ylo, wmax);
+        if (w0 > w1) continue;
+        const float s0 = sqrt_approx(thra - det * w0 * w0), s1 = sqrt_approx(thra - det * w1 * w1);
+        const float hi = (ws >= w0 && ws <= w1) ? umax : fmaxf((-b * w0 + s0) * inv_a, (-b * w1 + s1) * inv_a);
+        const float lo = (-ws >= w0 && -ws <= w1) ? -umax : fminf((-b * w0 - s0) * inv_a, (-b * w1 - s1) * inv_a);
+        const float xl = mx - hi - epsx, xr = mx - lo + epsx;
+        if (xr >= xt && xl <= xt + 7.0f) m |= 1u << (2 * k);
+        if (xr >= xt + 8.0f && xl <= xt + 15.0f) m |= 1u << (2 * k + 1);
+    }
+    return m;
+}
+
 // Tiles of row ty that the Gaussian reaches (a (Gaussian, tile) pair is kept
 // when it can give alpha >= 1/255 at some pixel centre of the tile; leaving
 // the others out of the tile lists changes no weight): columns [c0, c1) within

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256, 5) k_weights(WeightsArgs a) {
             cp_async_wait<kRing - 2>();
             if (range.x + k * kTcBatch + (uint32_t)lane < range.y) {
                 PairRec& r = S.rec[slot][lane];
-                r.mask = block_mask(reach_prep(r.ca, r.cb, r.cc, r.op), r.mx, r.my, r.ca, r.cb, r.cc, tx, ty);
+                r.mask = block_mask_fast(r.mx, r.my, r.ca, r.cb, r.cc, r.op, tx, ty);
             }
         }
         if (__syncthreads_count(!done) == 0) break;
