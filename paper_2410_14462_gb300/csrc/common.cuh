@@ -184,6 +184,8 @@ struct ludvig_graph {
     int val_version = 0;          // bumped whenever val changes
     int sell_version = -1;        // val_version of the sliced copy in ws ("sell.*"), -1: none
     int64_t sell_slices = 0;
+    int32_t* perm = nullptr;      // [n] node at position r of the kNN grid's cell order (null: identity)
+    int32_t* inv = nullptr;       // [n] position of each node in that order
     ludvig::Arena ws;
 };
 

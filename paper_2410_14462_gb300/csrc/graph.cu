@@ -552,7 +552,12 @@ __global__ void __launch_bounds__(256) k_spmv_scaled(const int64_t* __restrict__
 // (slot j of row r at off[slice] + 32 j + r % 32; padding: column = the row,
 // value 0).  One thread per row then reads its columns and values with
 // coalesced 128-byte warp loads and no row-pointer dependence.
-__global__ void k_sell_width(const int64_t* __restrict__ rp, int64_t n, int64_t nslices, uint32_t* __restrict__ slots) {
+// With perm (the kNN grid's cell order) the sliced copy is renumbered: its
+// row r is node perm[r] and its columns are positions (inv), so that the rows
+// of a slice and the x entries they gather are spatial neighbours; the
+// diffusion then runs on the permuted vector.
+__global__ void k_sell_width(const int64_t* __restrict__ rp, int64_t n, int64_t nslices,
+                             const int32_t* __restrict__ perm, uint32_t* __restrict__ slots) {
     const int lane = threadIdx.x & 31;
     const int64_t s = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (s > nslices) return;
@@ -561,27 +566,48 @@ __global__ void k_sell_width(const int64_t* __restrict__ rp, int64_t n, int64_t 
         return;
     }
     const int64_t r = s * 32 + lane;
-    uint32_t len = r < n ? (uint32_t)(rp[r + 1] - rp[r]) : 0u;
+    const int64_t i = r < n ? (perm ? (int64_t)perm[r] : r) : 0;
+    uint32_t len = r < n ? (uint32_t)(rp[i + 1] - rp[i]) : 0u;
     len = __reduce_max_sync(0xffffffffu, len);
     if (lane == 0) slots[s] = 32u * len;
 }
 
 __global__ void k_sell_fill(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                             const float* __restrict__ val, int64_t n, int64_t nslices,
+                            const int32_t* __restrict__ perm, const int32_t* __restrict__ inv,
                             const uint32_t* __restrict__ off, int32_t* __restrict__ scol, float* __restrict__ sval) {
     const int lane = threadIdx.x & 31;
     const int64_t s = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (s >= nslices) return;
     const int64_t r = s * 32 + lane;
-    const int64_t e0 = r < n ? rp[r] : 0;
-    const uint32_t len = r < n ? (uint32_t)(rp[r + 1] - e0) : 0u;
+    const int64_t i = r < n ? (perm ? (int64_t)perm[r] : r) : 0;
+    const int64_t e0 = r < n ? rp[i] : 0;
+    const uint32_t len = r < n ? (uint32_t)(rp[i + 1] - e0) : 0u;
     const uint32_t w = (off[s + 1] - off[s]) / 32u;
     for (uint32_t j = 0; j < w; ++j) {
         const uint32_t p = off[s] + 32u * j + (uint32_t)lane;
         const bool real = j < len;
-        scol[p] = real ? col[e0 + j] : (int32_t)(r < n ? r : 0);
+        const int32_t c = real ? col[e0 + j] : 0;
+        scol[p] = real ? (inv ? inv[c] : c) : (int32_t)(r < n ? r : 0);
         sval[p] = real ? val[e0 + j] : 0.f;
     }
+}
+
+__global__ void k_invert_perm(const int32_t* __restrict__ perm, int64_t n, int32_t* __restrict__ inv) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) inv[perm[r]] = (int32_t)r;
+}
+
+__global__ void k_gather_perm(const float* __restrict__ x, const int32_t* __restrict__ perm, int64_t n,
+                              float* __restrict__ y) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) y[r] = x[perm[r]];
+}
+
+__global__ void k_scatter_perm(const float* __restrict__ y, const int32_t* __restrict__ perm, int64_t n,
+                               float* __restrict__ x) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) x[perm[r]] = y[r];
 }
 
 // y = A (x / ||x||) for one column on the sliced copy: a warp per slice, a
@@ -765,6 +791,19 @@ ludvig_status graph_build_impl(ludvig_scene_t scene, int32_t k, const float* fea
         StageScope scope(LUDVIG_STAGE_KNN, st);
         GB_TRY(knn_impl(scene, k, nbr, st, &sorder));
     }
+    if (sorder) {   // the graph keeps the cell order for its diffusion (sliced copy renumbered)
+        if (cudaMalloc(&g->perm, sizeof(int32_t) * (size_t)n) != cudaSuccess ||
+            cudaMalloc(&g->inv, sizeof(int32_t) * (size_t)n) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("graph allocation failed");
+            return fail(LUDVIG_ERR_OOM);
+        }
+        if (cudaMemcpyAsync(g->perm, sorder, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess)
+            return fail(LUDVIG_ERR_CUDA);
+        k_invert_perm<<<grid_for(n, 256), 256, 0, st>>>(g->perm, n, g->inv);
+        count_launch();
+    }
     StageScope gscope(LUDVIG_STAGE_GRAPH, st);
     if (cudaMemsetAsync(indeg, 0, sizeof(uint32_t) * n, st) != cudaSuccess ||
         cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * n, st) != cudaSuccess)
@@ -854,6 +893,8 @@ extern "C" ludvig_status ludvig_graph_destroy(ludvig_graph_t g) {
     cudaFree(g->col);
     cudaFree(g->val);
     cudaFree(g->d2);
+    cudaFree(g->perm);
+    cudaFree(g->inv);
     g->ws.release();
     delete g;
     return LUDVIG_OK;
@@ -899,7 +940,7 @@ ludvig_status ensure_sell(ludvig_graph* g, cudaStream_t st, bool* ok, uint32_t**
         *ok = true;
         return LUDVIG_OK;
     }
-    k_sell_width<<<grid_for(nslices + 1, 8), 256, 0, st>>>(g->row_ptr, n, nslices, slots);
+    k_sell_width<<<grid_for(nslices + 1, 8), 256, 0, st>>>(g->row_ptr, n, nslices, g->perm, slots);
     LV_LAUNCH();
     LV_TRY(scan_exclusive_u32(slots, *off, nslices + 1, total_d, g->ws, st));
     LV_CUDA(cudaMemcpyAsync(total_h, total_d, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
@@ -907,7 +948,8 @@ ludvig_status ensure_sell(ludvig_graph* g, cudaStream_t st, bool* ok, uint32_t**
     if (*total_h >= ((uint64_t)1 << 32)) return LUDVIG_OK;
     LV_TRY(g->ws.get("sell.col", (size_t)std::max<uint64_t>(*total_h, 1), scol));
     LV_TRY(g->ws.get("sell.val", (size_t)std::max<uint64_t>(*total_h, 1), sval));
-    k_sell_fill<<<grid_for(nslices, 8), 256, 0, st>>>(g->row_ptr, g->col, g->val, n, nslices, *off, *scol, *sval);
+    k_sell_fill<<<grid_for(nslices, 8), 256, 0, st>>>(g->row_ptr, g->col, g->val, n, nslices, g->perm, g->inv,
+                                                      *off, *scol, *sval);
     LV_LAUNCH();
     g->sell_version = g->val_version;
     g->sell_slices = nslices;
@@ -953,9 +995,19 @@ extern "C" ludvig_status ludvig_diffuse(ludvig_graph_t g, const float* x0, int32
     int32_t* scol = nullptr;
     float* sval = nullptr;
     if (dx == 1) LV_TRY(ensure_sell(g, st, &sell, &soff, &scol, &sval));
-    const float* xin = x0;
+    // the renumbered sliced copy works on the permuted vector: x0 gathered in,
+    // the last step's vector scattered back to out
+    const bool permuted = sell && g->perm;
+    float *pa = nullptr, *pb = nullptr;
+    if (permuted) {
+        LV_TRY(g->ws.get("d.pa", (size_t)n, &pa));
+        LV_TRY(g->ws.get("d.pb", (size_t)n, &pb));
+        k_gather_perm<<<grid_for(n, 256), 256, 0, st>>>(x0, g->perm, n, pa);
+        LV_LAUNCH();
+    }
+    const float* xin = permuted ? pa : x0;
     for (int t = 0; t < iters; ++t) {
-        float* y = bufs[t & 1];
+        float* y = permuted ? ((t & 1) ? pa : pb) : bufs[t & 1];
         if (sell)
             k_spmv_sell<<<blocks, 256, 0, st>>>(soff, scol, sval, xin, n, g->sell_slices, n2 + 32 * t, y,
                                                 n2 + 32 * (t + 1));
@@ -967,6 +1019,10 @@ extern "C" ludvig_status ludvig_diffuse(ludvig_graph_t g, const float* x0, int32
                                                      n2 + 32 * (t + 1));
         LV_LAUNCH();
         xin = y;
+    }
+    if (permuted) {
+        k_scatter_perm<<<grid_for(n, 256), 256, 0, st>>>(xin, g->perm, n, out);
+        LV_LAUNCH();
     }
     return LUDVIG_OK;
 }

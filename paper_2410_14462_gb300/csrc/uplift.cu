@@ -232,104 +232,41 @@ __global__ void k_sorted_records(const uint32_t* __restrict__ skeys, const uint3
 // One (view * tiles + tile, rank) pair per tile a Gaussian reaches, written in
 // depth order at the Gaussian's scanned offset.  Nothing is written when the
 // group's pairs do not fit the buffers (the overflow word is set instead).
-// A Gaussian reaching more than kEmitWide tiles is emitted by its whole warp
-// (row ranges one row per lane, then each row's tiles by consecutive lanes),
-// so that a few large Gaussians neither serialise their warp nor scatter its
-// stores; the others write their own pairs.
-constexpr uint32_t kEmitWide = 24;
-
 __global__ void k_emit_pairs(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off,
                              const PairRec* __restrict__ srec, const uint2* __restrict__ srect, int64_t npad,
                              int64_t total, int TX, int ntiles, int prune, const uint64_t* __restrict__ np_dev,
                              uint64_t cap, int* ovf, uint32_t sentinel, uint32_t* __restrict__ pkey,
                              uint32_t* __restrict__ pval) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    if (!pairs_fit(*np_dev, cap)) {   // the same for every thread
+    if (idx >= total) return;
+    if (!pairs_fit(*np_dev, cap)) {
         if (idx == 0 && ovf) atomicOr(ovf, 1);
         return;
     }
-    // every lane of a warp stays to the end (the wide Gaussians take the warp)
-    const bool valid = idx < total;
-    const uint32_t c = valid ? cnt[idx] : 0u;
-    const int64_t v = valid ? idx / npad : 0;
+    const uint32_t c = cnt[idx];
+    if (c == 0) return;
+    const int64_t v = idx / npad;
     const uint32_t rank = (uint32_t)(idx - v * npad);
-    PairRec r{};
-    uint2 rt = make_uint2(0u, 0u);
+    const PairRec r = srec[idx];
+    const uint2 rt = srect[idx];
+    const int x0 = rt.x & 0xffff, y0 = rt.x >> 16, x1 = rt.y & 0xffff, y1 = rt.y >> 16;
     EllipseX E{};
     E.state = 2;   // unpruned: every tile of the rectangle
-    if (c) {
-        r = srec[idx];
-        rt = srect[idx];
-        if (prune) E = ellipse_prep(reach_prep(r.ca, r.cb, r.cc, r.op), r.ca, r.cb, r.cc);
-    }
-    const int x0 = rt.x & 0xffff, y0 = rt.x >> 16, x1 = rt.y & 0xffff, y1 = rt.y >> 16;
-    const uint32_t o0 = c ? off[idx] : 0u;
+    if (prune) E = ellipse_prep(reach_prep(r.ca, r.cb, r.cc, r.op), r.ca, r.cb, r.cc);
+    uint32_t o = off[idx];
+    const uint32_t end = o + c;   // never write past the counted slots
     const uint32_t base = (uint32_t)(v * ntiles);
-    if (c && c <= kEmitWide) {
-        uint32_t o = o0;
-        const uint32_t end = o + c;   // never write past the counted slots
-        for (int ty = y0; ty < y1 && o < end; ++ty) {
-            int c0, c1;
-            tile_row_range(E, r.mx, r.my, ty, x0, x1, c0, c1);
-            for (int tx = c0; tx < c1 && o < end; ++tx, ++o) {
-                pkey[o] = base + (uint32_t)(ty * TX + tx);
-                pval[o] = rank;
-            }
-        }
-        for (; o < end; ++o) {   // unreachable when both kernels agree; keeps the keys defined
-            pkey[o] = sentinel;
-            pval[o] = 0u;
+    for (int ty = y0; ty < y1 && o < end; ++ty) {
+        int c0, c1;
+        tile_row_range(E, r.mx, r.my, ty, x0, x1, c0, c1);
+        for (int tx = c0; tx < c1 && o < end; ++tx, ++o) {
+            pkey[o] = base + (uint32_t)(ty * TX + tx);
+            pval[o] = rank;
         }
     }
-    uint32_t wide = __ballot_sync(0xffffffffu, c > kEmitWide);
-    while (wide) {
-        const int src = __ffs(wide) - 1;
-        wide &= wide - 1u;
-        EllipseX Ew;
-        Ew.b = __shfl_sync(0xffffffffu, E.b, src);
-        Ew.det = __shfl_sync(0xffffffffu, E.det, src);
-        Ew.thra = __shfl_sync(0xffffffffu, E.thra, src);
-        Ew.umax = __shfl_sync(0xffffffffu, E.umax, src);
-        Ew.wmax = __shfl_sync(0xffffffffu, E.wmax, src);
-        Ew.ws = __shfl_sync(0xffffffffu, E.ws, src);
-        Ew.inv_a = __shfl_sync(0xffffffffu, E.inv_a, src);
-        Ew.epsx = __shfl_sync(0xffffffffu, E.epsx, src);
-        Ew.state = __shfl_sync(0xffffffffu, E.state, src);
-        const float mx = __shfl_sync(0xffffffffu, r.mx, src), my = __shfl_sync(0xffffffffu, r.my, src);
-        const int wx0 = __shfl_sync(0xffffffffu, x0, src), wx1 = __shfl_sync(0xffffffffu, x1, src);
-        const int wy0 = __shfl_sync(0xffffffffu, y0, src), wy1 = __shfl_sync(0xffffffffu, y1, src);
-        const uint32_t wrank = __shfl_sync(0xffffffffu, rank, src), wbase = __shfl_sync(0xffffffffu, base, src);
-        uint32_t o = __shfl_sync(0xffffffffu, o0, src);
-        const uint32_t end = o + __shfl_sync(0xffffffffu, c, src);
-        for (int ty0 = wy0; ty0 < wy1; ty0 += 32) {
-            // lane k: the tile range of row ty0 + k, and where its pairs start
-            int c0 = 0, c1 = 0;
-            if (ty0 + lane < wy1) tile_row_range(Ew, mx, my, ty0 + lane, wx0, wx1, c0, c1);
-            const int n = c1 - c0;
-            int incl = n;
-#pragma unroll
-            for (int dd = 1; dd < 32; dd <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, incl, dd);
-                if (lane >= dd) incl += t;
-            }
-            const int rows = min(32, wy1 - ty0);
-            for (int k = 0; k < rows; ++k) {
-                const int ck = __shfl_sync(0xffffffffu, c0, k), nk = __shfl_sync(0xffffffffu, n, k);
-                const uint32_t ok = o + (uint32_t)(__shfl_sync(0xffffffffu, incl, k) - nk);
-                const uint32_t key = wbase + (uint32_t)((ty0 + k) * TX + ck);
-                for (int t = lane; t < nk; t += 32)
-                    if (ok + (uint32_t)t < end) {
-                        pkey[ok + t] = key + (uint32_t)t;
-                        pval[ok + t] = wrank;
-                    }
-            }
-            o += (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
-        }
-        for (uint32_t q = o + lane; q < end; q += 32) {   // unreachable when both kernels agree
-            pkey[q] = sentinel;
-            pval[q] = 0u;
-        }
+    for (; o < end; ++o) {   // unreachable when both kernels agree; keeps the keys defined
+        pkey[o] = sentinel;
+        pval[o] = 0u;
     }
 }
 
