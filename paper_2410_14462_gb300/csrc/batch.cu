@@ -99,7 +99,10 @@ ludvig_scene* take_context(int dev) {
         return c;
     }
     ludvig_scene* c = new (std::nothrow) ludvig_scene();
-    if (c) c->device = dev;
+    if (c) {
+        c->device = dev;
+        c->onesweep = true;   // many groups: one kernel per radix pass
+    }
     return c;
 }
 

@@ -157,6 +157,7 @@ struct ludvig_scene {
     cudaEvent_t ev_free[2] = {nullptr, nullptr};
     int64_t tc_chunk_cap = 0;             // tensor-core path: weight chunks kept in ws
     int64_t pair_cap = 0;                 // (tile, Gaussian) pairs per group kept in ws
+    bool onesweep = false;                // sorts with the one-sweep radix sort (packed batch contexts)
     // asynchronous uplift: front-end and aggregation streams, their events,
     // the device status words ([0] bounded-wait status, [1] capacity overflow)
     // and their host mirror with the groups' sizes
@@ -218,6 +219,14 @@ ludvig_status radix_sort_pairs(uint32_t** keys, uint32_t** vals, uint32_t* keys_
 ludvig_status radix_sort_pairs_len(uint32_t** keys, uint32_t** vals, uint32_t* keys_alt,
                                    uint32_t* vals_alt, int64_t nseg, int64_t seg_len, const uint64_t* len,
                                    int nbits, Arena& ws, cudaStream_t st);
+
+// The same sort (and the same device-length rule) with one kernel per pass
+// after an up-front histogram of every pass; the passes chain their prefix
+// through the blocks.  A wait that runs past its bound records
+// LUDVIG_ERR_TIMEOUT in *err (device, may be null).
+ludvig_status radix_sort_onesweep(uint32_t** keys, uint32_t** vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                                  int64_t nseg, int64_t seg_len, const uint64_t* len, int nbits, int* err,
+                                  Arena& ws, cudaStream_t st);
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }

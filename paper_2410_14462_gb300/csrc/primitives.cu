@@ -258,6 +258,195 @@ k_radix_downsweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__
     }
 }
 
+// ------------------------------------------------------------------ one-sweep radix
+// The same stable LSD sort with the per-pass histogram scan chained through
+// the blocks of each pass instead of a device-wide scan between kernels (the
+// one-sweep scheme of Adinets and Merrill, 2022, "Onesweep: a faster least
+// significant digit radix sort for GPUs"): one kernel histograms the digits of
+// every pass per segment up front; each pass is then one kernel in which a
+// block takes the next tile in order (a counter, so every earlier tile belongs
+// to a block that has started), ranks its keys as k_radix_downsweep does,
+// publishes its per-digit counts, and adds up the counts of the earlier tiles
+// of its segment (the last inclusive prefix published, plus the counts after
+// it) to find where each digit's run goes.  Waits are bounded: past the limit
+// the block records LUDVIG_ERR_TIMEOUT in *err and goes on with what it has.
+
+constexpr uint64_t kOsAgg = 1ull << 62, kOsIncl = 2ull << 62, kOsValMask = (1ull << 62) - 1ull;
+constexpr int kOsSpinLimit = 1 << 22;
+
+__global__ void __launch_bounds__(kRadixThreads)
+k_os_hist(const uint32_t* __restrict__ keys, int64_t bps, const uint64_t* __restrict__ len, int npass,
+          uint32_t* __restrict__ ghist) {
+    __shared__ uint32_t h[4][256];
+    for (int p = 0; p < 4; ++p) h[p][threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    const int64_t seg = blockIdx.x / bps, seg_base = (int64_t)(blockIdx.x % bps) * kRadixTile;
+    const int64_t valid = radix_valid(len, bps * kRadixTile);
+    if (seg_base >= valid) return;   // (whole block uniform)
+#pragma unroll 4
+    for (int i = 0; i < kRadixItems; ++i) {
+        const int64_t off = i * kRadixThreads + threadIdx.x;
+        const uint32_t k = seg_base + off < valid ? keys[base + off] : 0xffffffffu;
+        for (int p = 0; p < npass; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xffu], 1u);
+    }
+    __syncthreads();
+    for (int p = 0; p < npass; ++p)
+        if (h[p][threadIdx.x]) atomicAdd(&ghist[(seg * npass + p) * 256 + threadIdx.x], h[p][threadIdx.x]);
+}
+
+// A status word as the L2 holds it (a relaxed device-scope load; the word
+// itself carries everything the reader uses).
+__device__ __forceinline__ uint64_t os_read(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(kRadixThreads)
+k_os_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+          uint32_t* __restrict__ vout, int pass, int npass, const uint32_t* __restrict__ ghist, int64_t bps,
+          const uint64_t* __restrict__ len, uint64_t* __restrict__ status, uint32_t* __restrict__ counter,
+          int* __restrict__ err) {
+    constexpr int kWarps = kRadixThreads / 32;
+    __shared__ uint32_t s_key[kRadixTile];
+    __shared__ uint32_t s_val[kRadixTile];
+    __shared__ uint32_t wcnt[kWarps][256];
+    __shared__ uint32_t dstart[256];
+    __shared__ uint64_t obase[256];
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t wsum[kWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int shift = 8 * pass;
+    if (tid == 0) s_tile = atomicAdd(counter, 1u);
+    __syncthreads();
+    const int64_t t = s_tile;
+    const int64_t seg = t / bps, b = t - seg * bps;
+    const int64_t base = t * kRadixTile;
+    const int64_t seg_base = b * kRadixTile;
+    const int64_t valid = radix_valid(len, bps * kRadixTile);
+    // tiles past the valid length take no part; no tile before them waits on them
+    if (seg_base >= valid) return;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
+    __syncthreads();
+    uint32_t k[kRadixItems], v[kRadixItems], rk[kRadixItems];
+#pragma unroll
+    for (int i = 0; i < kRadixItems; ++i) {
+        const int64_t off = warp * (32 * kRadixItems) + i * 32 + lane;
+        k[i] = seg_base + off < valid ? kin[base + off] : 0xffffffffu;
+        v[i] = seg_base + off < valid ? vin[base + off] : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < kRadixItems; ++i) {
+        const uint32_t d = (k[i] >> shift) & 0xffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = wcnt[warp][d];
+        rk[i] = before + __popc(peers & lt_mask);
+        __syncwarp();
+        if ((peers & lt_mask) == 0) wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // digit tid: exclusive prefix over the warps, the tile's count
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = wcnt[w][tid];
+        wcnt[w][tid] = tot;
+        tot += c;
+    }
+    // publish the tile's count of digit tid, then add up the earlier tiles' counts
+    uint64_t* my = status + t * 256 + tid;
+    if (b == 0) {
+        atomicExch(reinterpret_cast<unsigned long long*>(my), (unsigned long long)(kOsIncl | tot));
+    } else {
+        atomicExch(reinterpret_cast<unsigned long long*>(my), (unsigned long long)(kOsAgg | tot));
+    }
+    uint64_t excl = 0;
+    if (b > 0) {
+        // windows of up to kOsWin earlier tiles, read together: the nearest
+        // inclusive prefix ends the walk (the segment's first tile has one)
+        constexpr int kOsWin = 8;
+        const int64_t first = t - b;
+        bool gave_up = false, found = false;
+        for (int64_t top = t - 1; !found && !gave_up; top -= kOsWin) {
+            uint64_t w[kOsWin];
+#pragma unroll
+            for (int j = 0; j < kOsWin; ++j) w[j] = top - j >= first ? os_read(status + (top - j) * 256 + tid) : kOsIncl;
+#pragma unroll
+            for (int j = 0; j < kOsWin; ++j) {
+                for (int it = 0; !gave_up && (w[j] >> 62) == 0; ++it) {
+                    if (it >= kOsSpinLimit) {
+                        gave_up = true;
+                        break;
+                    }
+                    if (it >= 32) __nanosleep(32);
+                    w[j] = os_read(status + (top - j) * 256 + tid);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kOsWin; ++j) {
+                if (found) continue;
+                excl += w[j] & kOsValMask;   // (the tiles before the segment read as an empty inclusive prefix)
+                if (w[j] & kOsIncl) found = true;
+            }
+        }
+        if (gave_up && err) atomicExch(err, (int)LUDVIG_ERR_TIMEOUT);
+        atomicExch(reinterpret_cast<unsigned long long*>(my), (unsigned long long)(kOsIncl | (excl + tot)));
+    }
+    // where digit tid's run of this tile starts: the segment's start, the keys
+    // of smaller digits in the segment, the earlier tiles' keys of this digit
+    const uint32_t g = ghist[(seg * npass + pass) * 256 + tid];
+    uint32_t incl = g;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint64_t gbefore = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w)
+        if (w < warp) gbefore += wsum[w];
+    obase[tid] = (uint64_t)seg * (uint64_t)(bps * kRadixTile) + gbefore + (incl - g) + excl;
+    // the tile sorted by digit in shared memory (as k_radix_downsweep)
+    uint32_t tincl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, tincl, o);
+        if (lane >= o) tincl += x;
+    }
+    __syncthreads();   // wsum is reused
+    if (lane == 31) wsum[warp] = tincl;
+    __syncthreads();
+    uint32_t tbefore = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w)
+        if (w < warp) tbefore += wsum[w];
+    dstart[tid] = tbefore + tincl - tot;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kRadixItems; ++i) {
+        const uint32_t d = (k[i] >> shift) & 0xffu;
+        const uint32_t pos = dstart[d] + wcnt[warp][d] + rk[i];
+        s_key[pos] = k[i];
+        s_val[pos] = v[i];
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int i = 0; i < kRadixItems; ++i) {
+        const int p = i * kRadixThreads + tid;
+        const uint32_t kk = s_key[p];
+        const uint32_t d = (kk >> shift) & 0xffu;
+        const uint64_t o = obase[d] + (uint64_t)(p - (int)dstart[d]);
+        kout[o] = kk;
+        vout[o] = s_val[p];
+    }
+}
+
 }  // namespace
 
 ludvig_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* total_dev,
@@ -313,6 +502,57 @@ ludvig_status radix_sort_pairs_len(uint32_t** keys, uint32_t** vals, uint32_t* k
         LV_TRY(scan_exclusive_u32(hist, hist, nh, nullptr, ws, st));
         k_radix_downsweep<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(kin, vin, kout, vout, shift,
                                                                        hist, bps, len);
+        LV_LAUNCH();
+        uint32_t* t = kin;
+        kin = kout;
+        kout = t;
+        t = vin;
+        vin = vout;
+        vout = t;
+    }
+    *keys = kin;
+    *vals = vin;
+    return LUDVIG_OK;
+}
+
+}  // namespace ludvig
+
+namespace ludvig {
+
+ludvig_status radix_sort_onesweep(uint32_t** keys, uint32_t** vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                                  int64_t nseg, int64_t seg_len, const uint64_t* len, int nbits, int* err,
+                                  Arena& ws, cudaStream_t st) {
+    if (len && nseg != 1) {
+        set_error("radix_sort_onesweep: a device length needs one segment");
+        return LUDVIG_ERR_INTERNAL;
+    }
+    if (nseg <= 0 || seg_len <= 0 || nbits <= 0) return LUDVIG_OK;
+    if (seg_len % kRadixTile != 0 || nbits > 32) {
+        set_error("radix_sort_onesweep: segment length %lld not a multiple of %d", (long long)seg_len, kRadixTile);
+        return LUDVIG_ERR_INTERNAL;
+    }
+    const int64_t bps = seg_len / kRadixTile;
+    const int64_t nblocks = bps * nseg;
+    if (nblocks > 0x7fffffff || seg_len * nseg >= ((int64_t)1 << 40)) {
+        set_error("radix_sort_onesweep: too many blocks");
+        return LUDVIG_ERR_ARG;
+    }
+    const int npass = (nbits + 7) / 8;
+    uint32_t* ghist = nullptr;
+    uint64_t* status = nullptr;
+    uint32_t* counters = nullptr;
+    LV_TRY(ws.get("os.hist", (size_t)nseg * npass * 256, &ghist));
+    LV_TRY(ws.get("os.status", (size_t)nblocks * 256, &status));
+    LV_TRY(ws.get("os.counters", 4, &counters));
+    LV_CUDA(cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * (size_t)nseg * npass * 256, st));
+    LV_CUDA(cudaMemsetAsync(counters, 0, sizeof(uint32_t) * 4, st));
+    k_os_hist<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(*keys, bps, len, npass, ghist);
+    LV_LAUNCH();
+    uint32_t *kin = *keys, *vin = *vals, *kout = keys_alt, *vout = vals_alt;
+    for (int pass = 0; pass < npass; ++pass) {
+        LV_CUDA(cudaMemsetAsync(status, 0, sizeof(uint64_t) * (size_t)nblocks * 256, st));
+        k_os_pass<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(kin, vin, kout, vout, pass, npass, ghist, bps, len,
+                                                              status, counters + pass, err);
         LV_LAUNCH();
         uint32_t* t = kin;
         kin = kout;

@@ -936,7 +936,12 @@ ludvig_status front_end(ludvig_scene* ctx, const GroupViews& g, int width, int h
 
     uint32_t *sk = keys, *sv = vals;
     tslot = trace_on() ? trace_begin(LUDVIG_STAGE_DEPTH_SORT, st) : -1;
-    LV_TRY(radix_sort_pairs(&sk, &sv, keys2, vals2, nv, npad, 32, ws, st));
+    // (a packed batch's context sorts in one kernel per pass: fewer launches for
+    // many groups; a single call takes the faster reduce-then-scan passes)
+    if (s->onesweep)
+        LV_TRY(radix_sort_onesweep(&sk, &sv, keys2, vals2, nv, npad, nullptr, 32, s->dstat, ws, st));
+    else
+        LV_TRY(radix_sort_pairs(&sk, &sv, keys2, vals2, nv, npad, 32, ws, st));
     trace_end(tslot, st);
     tslot = trace_on() ? trace_begin(LUDVIG_STAGE_BIN, st) : -1;
     k_sorted_records<<<grid_for(nG, 256), 256, 0, st>>>(sk, sv, ntile, rec_a, rec_b, rect, n, npad, nG, cnt, srec,
@@ -973,7 +978,10 @@ ludvig_status front_end(ludvig_scene* ctx, const GroupViews& g, int width, int h
     int nbits = 1;
     while (((uint32_t)1 << nbits) <= sentinel) ++nbits;
     uint32_t *spk = pk, *spv = pv;
-    LV_TRY(radix_sort_pairs_len(&spk, &spv, pk2, pv2, 1, cap, total_d, nbits, ws, st));
+    if (s->onesweep)
+        LV_TRY(radix_sort_onesweep(&spk, &spv, pk2, pv2, 1, cap, total_d, nbits, s->dstat, ws, st));
+    else
+        LV_TRY(radix_sort_pairs_len(&spk, &spv, pk2, pv2, 1, cap, total_d, nbits, ws, st));
     uint2* ranges;
     LV_TRY(ws.get("up.ranges", (size_t)nv * ntiles, &ranges));
     LV_CUDA(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)nv * ntiles, st));
@@ -1220,7 +1228,13 @@ ludvig_status reserve_async(ludvig_scene* s, int nv, int ng, int64_t n, int widt
     // up to n Gaussians) and their scan sums
     const int64_t npad = round_up(std::max<int64_t>(n, 1), kRadixTile);
     const int64_t hist = 256 * std::max<int64_t>(cap, (int64_t)ng * npad) / kRadixTile;
-    LV_TRY(ws.get("radix.hist", sizeof(uint32_t) * (size_t)hist, &q));
+    if (s->onesweep) {
+        LV_TRY(ws.get("os.status", sizeof(uint64_t) * (size_t)hist, &q));
+        LV_TRY(ws.get("os.hist", sizeof(uint32_t) * 4 * 256 * (size_t)std::max(ng, 1), &q));
+        LV_TRY(ws.get("os.counters", sizeof(uint32_t) * 4, &q));
+    } else {
+        LV_TRY(ws.get("radix.hist", sizeof(uint32_t) * (size_t)hist, &q));
+    }
     LV_TRY(ws.get("scan.sums", sizeof(unsigned long long) * (size_t)ceil_div(std::max(hist, (int64_t)ng * npad), 4096),
                   &q));
     if (!tc) {
