@@ -1,7 +1,7 @@
 """Packed batches (ludvig_uplift_batch) on one GPU, through the C ABI:
 
-* jobs of three classes (bfloat16 D = 48, bfloat16 D = 3 on the zero-padded
-  path, float32 D = 40 on the split-bfloat16 path), their features slices of
+* jobs of four classes (bfloat16 D = 48, bfloat16 D = 3 and float32 D = 1 masks
+  on the zero-padded path, float32 D = 40 on the split-bfloat16 path), their features slices of
   shared pools at different view offsets, scenes of uneven size, one job
   without beta: every job equals its own ludvig_uplift run to 1e-5 relative
   L2 (only the order of the atomic sums differs), with groups of one or two
@@ -47,7 +47,8 @@ def world():
              3: torch.stack([inputs.feature_field(8, v, 3, H, W, device="cuda") for v in range(V)]
                             ).to(torch.bfloat16).contiguous(),
              40: torch.stack([inputs.feature_field(7, v, 40, H, W, device="cuda") for v in range(V)]
-                             ).contiguous()}
+                             ).contiguous(),
+             1: inputs.form_pool(1, cams, device="cuda", dtype=torch.float32)}   # float32 sphere masks
     torch.cuda.synchronize()
     return dict(cams=cams, host=host, pools=pools)
 
@@ -64,7 +65,8 @@ def options():
 
 # (scene index, d, first view, views, with beta)
 SPECS = [(0, 48, 0, 12, True), (1, 48, 7, 25, True), (2, 48, 30, 10, False), (3, 3, 2, 9, True),
-         (4, 3, 11, 17, True), (5, 40, 5, 14, True), (1, 40, 20, 6, True), (3, 48, 1, 3, True)]
+         (4, 3, 11, 17, True), (5, 40, 5, 14, True), (1, 40, 20, 6, True), (3, 48, 1, 3, True),
+         (2, 1, 4, 11, True), (5, 1, 25, 7, False)]
 
 
 def _jobs(world, specs=SPECS):
@@ -115,9 +117,10 @@ def test_packed_jobs_equal_their_own_runs(world, options, group_mb):
     plan = ludvig.batch_last_plan()
     print(f"group bound {group_mb} MiB: {plan}")
     packed = {(c["dtype"], c["d"]): c for c in plan if c["groups"] >= 0}
-    assert set(packed) == {(ludvig.BF16, 48), (ludvig.BF16, 3), (ludvig.F32, 40)}
+    assert set(packed) == {(ludvig.BF16, 48), (ludvig.BF16, 3), (ludvig.F32, 40), (ludvig.F32, 1)}
     assert plan[-1]["groups"] == -1 and plan[-1]["jobs"] == 0
-    views = {(ludvig.BF16, 48): 12 + 25 + 10 + 3, (ludvig.BF16, 3): 9 + 17, (ludvig.F32, 40): 14 + 6}
+    views = {(ludvig.BF16, 48): 12 + 25 + 10 + 3, (ludvig.BF16, 3): 9 + 17, (ludvig.F32, 40): 14 + 6,
+             (ludvig.F32, 1): 11 + 7}
     for key, c in packed.items():
         assert c["views"] == views[key] and c["group_mb"] == group_mb and not c["tuned"]
         if group_mb == 1:
@@ -135,7 +138,7 @@ def test_float32_jobs_run_as_single_calls_without_tensor_cores(world, options):
     rc, status = _run_batch(args, slots=3)
     assert rc == 0 and status == [0] * len(args)
     plan = ludvig.batch_last_plan()
-    assert plan[-1]["jobs"] == 2 and plan[-1]["views"] == 14 + 6
+    assert plan[-1]["jobs"] == 4 and plan[-1]["views"] == 14 + 6 + 11 + 7
     assert {(c["dtype"], c["d"]) for c in plan if c["groups"] >= 0} == {(ludvig.BF16, 48), (ludvig.BF16, 3)}
     _check_alone(args)
 
