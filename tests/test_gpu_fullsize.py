@@ -66,8 +66,16 @@ def test_fullsize_f32(paper):
     pos = b_ref > 0
     e = rel_l2(out[idx][pos], f_ref[pos])
     eb = rel_l2(beta[idx], b_ref)
-    print(f"full size float32: {pos.sum()} sampled Gaussians, rel L2 f {e:.2e}, beta {eb:.2e}")
+    # worst single Gaussian: its feature vector's relative error, and beta's
+    g = out[idx][pos].astype(np.float64)
+    worst = float(np.max(np.linalg.norm(g - f_ref[pos], axis=1) / np.linalg.norm(f_ref[pos], axis=1)))
+    worst_b = float(np.max(np.abs(beta[idx][pos] - b_ref[pos]) / b_ref[pos]))
+    print(f"full size float32: {pos.sum()} sampled Gaussians, rel L2 f {e:.2e}, beta {eb:.2e}; "
+          f"worst Gaussian f {worst:.2e}, beta {worst_b:.2e}")
     assert e <= 1e-5 and eb <= 1e-5
+    # per Gaussian: beta is a float32 sum of positive weights (no cancellation); f's
+    # channels are signed sums whose vector can be short when views disagree
+    assert worst <= 1e-3 and worst_b <= 1e-4
     del feats
     torch.cuda.empty_cache()
 
@@ -88,8 +96,11 @@ def test_fullsize_bf16_precision_form(paper):
     assert np.array_equal(beta[idx] > 0, b_ref > 0)
     pos = b_ref > 0
     e = rel_l2(out[idx][pos], f_ref[pos])
-    print(f"full size bf16 (50 views, D=512): {pos.sum()} sampled Gaussians, rel L2 vs float64 oracle {e:.2e}")
-    assert e <= 1e-2
+    g = out[idx][pos].astype(np.float64)
+    worst = float(np.max(np.linalg.norm(g - f_ref[pos], axis=1) / np.linalg.norm(f_ref[pos], axis=1)))
+    print(f"full size bf16 (50 views, D=512): {pos.sum()} sampled Gaussians, rel L2 vs float64 oracle {e:.2e}, "
+          f"worst Gaussian {worst:.2e}")
+    assert e <= 1e-2 and worst <= 1e-1
 
 
 def test_fullsize_render_sampled_tiles(paper):
