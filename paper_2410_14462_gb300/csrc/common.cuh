@@ -220,6 +220,11 @@ ludvig_status radix_sort_pairs_len(uint32_t** keys, uint32_t** vals, uint32_t* k
                                    uint32_t* vals_alt, int64_t nseg, int64_t seg_len, const uint64_t* len,
                                    int nbits, Arena& ws, cudaStream_t st);
 
+// radix_sort_pairs_len with 16-bit keys (nbits <= 16): less traffic per pass.
+ludvig_status radix_sort_pairs_len16(uint16_t** keys, uint32_t** vals, uint16_t* keys_alt, uint32_t* vals_alt,
+                                     int64_t nseg, int64_t seg_len, const uint64_t* len, int nbits, Arena& ws,
+                                     cudaStream_t st);
+
 // The same sort (and the same device-length rule) with one kernel per pass
 // after an up-front histogram of every pass; the passes chain their prefix
 // through the blocks.  A wait that runs past its bound records

@@ -144,9 +144,13 @@ __device__ __forceinline__ int64_t radix_valid(const uint64_t* len, int64_t seg_
     return len ? (int64_t)min((uint64_t)seg_len, *len) : seg_len;
 }
 
+// Keys are 32-bit or 16-bit (KeyT); entries past the valid length read as the
+// type's largest key.
+template <class KeyT>
 __global__ void __launch_bounds__(kRadixThreads)
-k_radix_upsweep(const uint32_t* __restrict__ keys, int shift, uint32_t* __restrict__ hist, int64_t bps,
+k_radix_upsweep(const KeyT* __restrict__ keys, int shift, uint32_t* __restrict__ hist, int64_t bps,
                 const uint64_t* __restrict__ len) {
+    constexpr uint32_t kFill = (uint32_t)(KeyT)~(KeyT)0;
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -158,7 +162,7 @@ k_radix_upsweep(const uint32_t* __restrict__ keys, int shift, uint32_t* __restri
 #pragma unroll 4
         for (int i = 0; i < kRadixItems; ++i) {
             const int64_t off = i * kRadixThreads + threadIdx.x;
-            const uint32_t k = seg_base + off < valid ? keys[base + off] : 0xffffffffu;
+            const uint32_t k = seg_base + off < valid ? (uint32_t)keys[base + off] : kFill;
             atomicAdd(&h[(k >> shift) & 0xffu], 1u);
         }
     }
@@ -172,11 +176,13 @@ k_radix_upsweep(const uint32_t* __restrict__ keys, int shift, uint32_t* __restri
 // one block prefix over the warps then gives every key its place in the tile
 // sorted by digit (stable).  The tile is sorted in shared memory and written
 // out in digit runs, so the stores coalesce.
+template <class KeyT>
 __global__ void __launch_bounds__(kRadixThreads)
-k_radix_downsweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                  uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int shift,
+k_radix_downsweep(const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin,
+                  KeyT* __restrict__ kout, uint32_t* __restrict__ vout, int shift,
                   const uint32_t* __restrict__ hist, int64_t bps, const uint64_t* __restrict__ len) {
     constexpr int kWarps = kRadixThreads / 32;
+    constexpr uint32_t kFill = (uint32_t)(KeyT)~(KeyT)0;
     __shared__ uint32_t s_key[kRadixTile];
     __shared__ uint32_t s_val[kRadixTile];
     __shared__ uint32_t wcnt[kWarps][256];   // per-warp digit counts, then their prefix
@@ -196,7 +202,7 @@ k_radix_downsweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__
 #pragma unroll
     for (int i = 0; i < kRadixItems; ++i) {
         const int64_t off = warp * (32 * kRadixItems) + i * 32 + lane;
-        k[i] = seg_base + off < valid ? kin[base + off] : 0xffffffffu;
+        k[i] = seg_base + off < valid ? (uint32_t)kin[base + off] : kFill;
         v[i] = seg_base + off < valid ? vin[base + off] : 0u;
     }
 #pragma unroll
@@ -253,7 +259,7 @@ k_radix_downsweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__
         const uint32_t kk = s_key[p];
         const uint32_t d = (kk >> shift) & 0xffu;
         const uint32_t o = obase[d] + (uint32_t)p - dstart[d];
-        kout[o] = kk;
+        kout[o] = (KeyT)kk;
         vout[o] = s_val[p];
     }
 }
@@ -473,9 +479,10 @@ ludvig_status radix_sort_pairs(uint32_t** keys, uint32_t** vals, uint32_t* keys_
     return radix_sort_pairs_len(keys, vals, keys_alt, vals_alt, nseg, seg_len, nullptr, nbits, ws, st);
 }
 
-ludvig_status radix_sort_pairs_len(uint32_t** keys, uint32_t** vals, uint32_t* keys_alt,
-                                   uint32_t* vals_alt, int64_t nseg, int64_t seg_len, const uint64_t* len,
-                                   int nbits, Arena& ws, cudaStream_t st) {
+namespace {
+template <class KeyT>
+ludvig_status radix_sort_impl(KeyT** keys, uint32_t** vals, KeyT* keys_alt, uint32_t* vals_alt, int64_t nseg,
+                              int64_t seg_len, const uint64_t* len, int nbits, Arena& ws, cudaStream_t st) {
     if (len && nseg != 1) {
         set_error("radix_sort_pairs_len: a device length needs one segment");
         return LUDVIG_ERR_INTERNAL;
@@ -495,24 +502,42 @@ ludvig_status radix_sort_pairs_len(uint32_t** keys, uint32_t** vals, uint32_t* k
     const int64_t nh = nseg * 256 * bps;
     uint32_t* hist = nullptr;
     LV_TRY(ws.get("radix.hist", (size_t)nh, &hist));
-    uint32_t *kin = *keys, *vin = *vals, *kout = keys_alt, *vout = vals_alt;
+    KeyT *kin = *keys, *kout = keys_alt;
+    uint32_t *vin = *vals, *vout = vals_alt;
     for (int shift = 0; shift < nbits; shift += 8) {
-        k_radix_upsweep<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(kin, shift, hist, bps, len);
+        k_radix_upsweep<KeyT><<<(unsigned)nblocks, kRadixThreads, 0, st>>>(kin, shift, hist, bps, len);
         LV_LAUNCH();
         LV_TRY(scan_exclusive_u32(hist, hist, nh, nullptr, ws, st));
-        k_radix_downsweep<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(kin, vin, kout, vout, shift,
-                                                                       hist, bps, len);
+        k_radix_downsweep<KeyT><<<(unsigned)nblocks, kRadixThreads, 0, st>>>(kin, vin, kout, vout, shift,
+                                                                             hist, bps, len);
         LV_LAUNCH();
-        uint32_t* t = kin;
+        KeyT* tk = kin;
         kin = kout;
-        kout = t;
-        t = vin;
+        kout = tk;
+        uint32_t* tv = vin;
         vin = vout;
-        vout = t;
+        vout = tv;
     }
     *keys = kin;
     *vals = vin;
     return LUDVIG_OK;
+}
+}  // namespace
+
+ludvig_status radix_sort_pairs_len(uint32_t** keys, uint32_t** vals, uint32_t* keys_alt,
+                                   uint32_t* vals_alt, int64_t nseg, int64_t seg_len, const uint64_t* len,
+                                   int nbits, Arena& ws, cudaStream_t st) {
+    return radix_sort_impl<uint32_t>(keys, vals, keys_alt, vals_alt, nseg, seg_len, len, nbits, ws, st);
+}
+
+ludvig_status radix_sort_pairs_len16(uint16_t** keys, uint32_t** vals, uint16_t* keys_alt, uint32_t* vals_alt,
+                                     int64_t nseg, int64_t seg_len, const uint64_t* len, int nbits, Arena& ws,
+                                     cudaStream_t st) {
+    if (nbits > 16) {
+        set_error("radix_sort_pairs_len16: %d key bits", nbits);
+        return LUDVIG_ERR_INTERNAL;
+    }
+    return radix_sort_impl<uint16_t>(keys, vals, keys_alt, vals_alt, nseg, seg_len, len, nbits, ws, st);
 }
 
 }  // namespace ludvig

@@ -232,10 +232,12 @@ __global__ void k_sorted_records(const uint32_t* __restrict__ skeys, const uint3
 // One (view * tiles + tile, rank) pair per tile a Gaussian reaches, written in
 // depth order at the Gaussian's scanned offset.  Nothing is written when the
 // group's pairs do not fit the buffers (the overflow word is set instead).
+// Keys are 32-bit, or 16-bit when every (view, tile) key and the sentinel fit.
+template <class KeyT>
 __global__ void k_emit_pairs(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off,
                              const PairRec* __restrict__ srec, const uint2* __restrict__ srect, int64_t npad,
                              int64_t total, int TX, int ntiles, int prune, const uint64_t* __restrict__ np_dev,
-                             uint64_t cap, int* ovf, uint32_t sentinel, uint32_t* __restrict__ pkey,
+                             uint64_t cap, int* ovf, uint32_t sentinel, KeyT* __restrict__ pkey,
                              uint32_t* __restrict__ pval) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
@@ -260,18 +262,19 @@ __global__ void k_emit_pairs(const uint32_t* __restrict__ cnt, const uint32_t* _
         int c0, c1;
         tile_row_range(E, r.mx, r.my, ty, x0, x1, c0, c1);
         for (int tx = c0; tx < c1 && o < end; ++tx, ++o) {
-            pkey[o] = base + (uint32_t)(ty * TX + tx);
+            pkey[o] = (KeyT)(base + (uint32_t)(ty * TX + tx));
             pval[o] = rank;
         }
     }
     for (; o < end; ++o) {   // unreachable when both kernels agree; keeps the keys defined
-        pkey[o] = sentinel;
+        pkey[o] = (KeyT)sentinel;
         pval[o] = 0u;
     }
 }
 
 // ------------------------------------------------------------ 5. ranges
-__global__ void k_ranges(const uint32_t* __restrict__ pkey, const uint64_t* __restrict__ np_dev, uint64_t cap,
+template <class KeyT>
+__global__ void k_ranges(const KeyT* __restrict__ pkey, const uint64_t* __restrict__ np_dev, uint64_t cap,
                          uint32_t nkeys, uint2* __restrict__ ranges) {
     const uint64_t np = *np_dev;
     if (!pairs_fit(np, cap)) return;
@@ -279,8 +282,8 @@ __global__ void k_ranges(const uint32_t* __restrict__ pkey, const uint64_t* __re
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P; j += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t k = pkey[j];
         if (k >= nkeys) continue;
-        if (j == 0 || pkey[j - 1] != k) ranges[k].x = (uint32_t)j;
-        if (j == P - 1 || pkey[j + 1] != k) ranges[k].y = (uint32_t)(j + 1);
+        if (j == 0 || (uint32_t)pkey[j - 1] != k) ranges[k].x = (uint32_t)j;
+        if (j == P - 1 || (uint32_t)pkey[j + 1] != k) ranges[k].y = (uint32_t)(j + 1);
     }
 }
 
@@ -885,7 +888,7 @@ ludvig_status front_buffers(Arena& ws, int nv, int64_t n, FrontBufs* b) {
 // nothing waits: the buffers keep ctx's pair capacity, and a group that
 // needs more sets *ovf, writes no pairs (all lists empty) and is redone later.
 ludvig_status front_end(ludvig_scene* ctx, const GroupViews& g, int width, int height, bool checked,
-                        int* ovf, const ChunkDebug* dbg, cudaStream_t st, FrontEnd* fe) {
+                        int* ovf, const ChunkDebug* dbg, cudaStream_t st, FrontEnd* fe, bool keys16_ok = false) {
     ludvig_scene* s = ctx;
     Arena& ws = s->ws;
     const int nv = (int)g.v.size();
@@ -970,22 +973,37 @@ ludvig_status front_end(ludvig_scene* ctx, const GroupViews& g, int width, int h
     LV_TRY(ws.get("up.pv", (size_t)cap, &pv));
     LV_TRY(ws.get("up.pk2", (size_t)cap, &pk2));
     LV_TRY(ws.get("up.pv2", (size_t)cap, &pv2));
-    k_emit_pairs<<<grid_for(nG, 256), 256, 0, st>>>(cnt, off, srec, srect, npad, nG, TX, ntiles, prune, total_d,
-                                                     (uint64_t)cap, ovf, sentinel, pk, pv);
+    // 16-bit keys when the caller reads only the ranks and lists afterwards
+    // (the tensor-core path) and every key and the sentinel fit
+    const bool k16 = keys16_ok && !s->onesweep && sentinel < 0xffffu && !dbg;
+    if (k16)
+        k_emit_pairs<uint16_t><<<grid_for(nG, 256), 256, 0, st>>>(cnt, off, srec, srect, npad, nG, TX, ntiles, prune,
+                                                                  total_d, (uint64_t)cap, ovf, sentinel,
+                                                                  reinterpret_cast<uint16_t*>(pk), pv);
+    else
+        k_emit_pairs<uint32_t><<<grid_for(nG, 256), 256, 0, st>>>(cnt, off, srec, srect, npad, nG, TX, ntiles, prune,
+                                                                  total_d, (uint64_t)cap, ovf, sentinel, pk, pv);
     LV_LAUNCH();
     trace_end(tslot, st);
     tslot = trace_on() ? trace_begin(LUDVIG_STAGE_TILE_SORT, st) : -1;
     int nbits = 1;
     while (((uint32_t)1 << nbits) <= sentinel) ++nbits;
     uint32_t *spk = pk, *spv = pv;
-    if (s->onesweep)
+    uint16_t* spk16 = reinterpret_cast<uint16_t*>(pk);
+    if (k16)
+        LV_TRY(radix_sort_pairs_len16(&spk16, &spv, reinterpret_cast<uint16_t*>(pk2), pv2, 1, cap, total_d, nbits, ws,
+                                      st));
+    else if (s->onesweep)
         LV_TRY(radix_sort_onesweep(&spk, &spv, pk2, pv2, 1, cap, total_d, nbits, s->dstat, ws, st));
     else
         LV_TRY(radix_sort_pairs_len(&spk, &spv, pk2, pv2, 1, cap, total_d, nbits, ws, st));
     uint2* ranges;
     LV_TRY(ws.get("up.ranges", (size_t)nv * ntiles, &ranges));
     LV_CUDA(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)nv * ntiles, st));
-    k_ranges<<<kPairGrid, 256, 0, st>>>(spk, total_d, (uint64_t)cap, sentinel, ranges);
+    if (k16)
+        k_ranges<uint16_t><<<kPairGrid, 256, 0, st>>>(spk16, total_d, (uint64_t)cap, sentinel, ranges);
+    else
+        k_ranges<uint32_t><<<kPairGrid, 256, 0, st>>>(spk, total_d, (uint64_t)cap, sentinel, ranges);
     LV_LAUNCH();
     trace_end(tslot, st);
     if (dbg && dbg->ranges64) {
@@ -998,7 +1016,7 @@ ludvig_status front_end(ludvig_scene* ctx, const GroupViews& g, int width, int h
         }
     }
     fe->L = GroupLists{ranges, spv, srec, npad};
-    fe->spk = spk;
+    fe->spk = k16 ? nullptr : spk;   // (16-bit keys: only the ranks and lists are read afterwards)
     fe->np = total_d;
     fe->cap = cap;
     fe->P = P;
@@ -1076,7 +1094,7 @@ ludvig_status uplift_group(ludvig_scene* ctx, const GroupViews& g, int width, in
         return LUDVIG_ERR_INTERNAL;
     }
     FrontEnd fe;
-    LV_TRY(front_end(s, g, width, height, !ex.async, ex.async ? ex.ovf : nullptr, nullptr, sf, &fe));
+    LV_TRY(front_end(s, g, width, height, !ex.async, ex.async ? ex.ovf : nullptr, nullptr, sf, &fe, tc));
     if (fe.too_many) {
         *too_many = true;
         return LUDVIG_OK;
