@@ -255,10 +255,11 @@ def run_reference(args):
 def cpu_baseline(args):
     """The oracle on the host cores, timed exactly as the reference arm times
     it: a child process running `bench.py --impl reference` on the same
-    workload (one view per step, 3 timed after 1 untimed), so that the two
-    agree; this process's GPU work and its threads stay out of the timing."""
+    workload and views (one view per step, views 3-5 after 3 untimed, as the
+    reference arm's default warm-up gives), so that the two agree; this
+    process's GPU work and its threads stay out of the timing."""
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", args.workload,
-           "--steps", "3", "--warmup", "1"]
+           "--steps", "3", "--warmup", "3"]
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
     line = next((json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")), None)
