@@ -233,57 +233,138 @@ __global__ void k_sorted_records(const uint32_t* __restrict__ skeys, const uint3
 // depth order at the Gaussian's scanned offset.  Nothing is written when the
 // group's pairs do not fit the buffers (the overflow word is set instead).
 // Keys are 32-bit, or 16-bit when every (view, tile) key and the sentinel fit.
+//
+// The pairs of a warp's 32 consecutive Gaussians occupy one contiguous range
+// (the offsets are an exclusive scan of the counts).  The warp fills that
+// range window by window: each lane puts its pairs that fall in the window
+// into shared memory (re-walking its tile rows from the first for a later
+// window), then the warp copies the window out with consecutive lanes on
+// consecutive entries, so the stores coalesce instead of scattering one
+// 2- or 4-byte store per pair over the Gaussians' separate runs.
+constexpr int kEmitThreads = 128;
+constexpr int kEmitWin = 1024;   // pairs per warp and window
+
 template <class KeyT>
-__global__ void k_emit_pairs(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off,
-                             const PairRec* __restrict__ srec, const uint2* __restrict__ srect, int64_t npad,
-                             int64_t total, int TX, int ntiles, int prune, const uint64_t* __restrict__ np_dev,
-                             uint64_t cap, int* ovf, uint32_t sentinel, KeyT* __restrict__ pkey,
-                             uint32_t* __restrict__ pval) {
+__global__ void __launch_bounds__(kEmitThreads)
+k_emit_pairs(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off, const PairRec* __restrict__ srec,
+             const uint2* __restrict__ srect, int64_t npad, int64_t total, int TX, int ntiles, int prune,
+             const uint64_t* __restrict__ np_dev, uint64_t cap, int* ovf, uint32_t sentinel,
+             KeyT* __restrict__ pkey, uint32_t* __restrict__ pval) {
+    __shared__ KeyT s_key[kEmitThreads / 32][kEmitWin];
+    __shared__ uint32_t s_val[kEmitThreads / 32][kEmitWin];
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= total) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (idx - lane >= total) return;   // (whole warp)
     if (!pairs_fit(*np_dev, cap)) {
         if (idx == 0 && ovf) atomicOr(ovf, 1);
         return;
     }
-    const uint32_t c = cnt[idx];
-    if (c == 0) return;
-    const int64_t v = idx / npad;
-    const uint32_t rank = (uint32_t)(idx - v * npad);
-    const PairRec r = srec[idx];
-    const uint2 rt = srect[idx];
-    const int x0 = rt.x & 0xffff, y0 = rt.x >> 16, x1 = rt.y & 0xffff, y1 = rt.y >> 16;
+    const bool in = idx < total;
+    const uint32_t c = in ? cnt[idx] : 0u;
+    const uint32_t o = in ? off[idx] : 0u;
+    const uint32_t wbase = __shfl_sync(0xffffffffu, o, 0);           // lane 0 is in range
+    const uint32_t wend = __reduce_max_sync(0xffffffffu, in ? o + c : 0u);
+    if (wend <= wbase) return;
+    int64_t v = 0;
+    uint32_t rank = 0;
+    PairRec r{};
+    int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
     EllipseX E{};
     E.state = 2;   // unpruned: every tile of the rectangle
-    if (prune) E = ellipse_prep(reach_prep(r.ca, r.cb, r.cc, r.op), r.ca, r.cb, r.cc);
-    uint32_t o = off[idx];
-    const uint32_t end = o + c;   // never write past the counted slots
-    const uint32_t base = (uint32_t)(v * ntiles);
-    for (int ty = y0; ty < y1 && o < end; ++ty) {
-        int c0, c1;
-        tile_row_range(E, r.mx, r.my, ty, x0, x1, c0, c1);
-        for (int tx = c0; tx < c1 && o < end; ++tx, ++o) {
-            pkey[o] = (KeyT)(base + (uint32_t)(ty * TX + tx));
-            pval[o] = rank;
-        }
+    if (c > 0) {
+        v = idx / npad;
+        rank = (uint32_t)(idx - v * npad);
+        r = srec[idx];
+        const uint2 rt = srect[idx];
+        x0 = rt.x & 0xffff;
+        y0 = rt.x >> 16;
+        x1 = rt.y & 0xffff;
+        y1 = rt.y >> 16;
+        if (prune) E = ellipse_prep(reach_prep(r.ca, r.cb, r.cc, r.op), r.ca, r.cb, r.cc);
     }
-    for (; o < end; ++o) {   // unreachable when both kernels agree; keeps the keys defined
-        pkey[o] = (KeyT)sentinel;
-        pval[o] = 0u;
+    const uint32_t base = (uint32_t)(v * ntiles);
+    const uint32_t end = o + c;   // never write past the counted slots
+    KeyT* sk = s_key[warp];
+    uint32_t* sv = s_val[warp];
+    for (uint32_t win = wbase; win < wend; win += kEmitWin) {
+        const uint32_t wlim = min(win + (uint32_t)kEmitWin, wend);
+        if (c > 0 && o < wlim && end > win) {
+            uint32_t p = o;
+            for (int ty = y0; ty < y1 && p < end && p < wlim; ++ty) {
+                int c0, c1;
+                tile_row_range(E, r.mx, r.my, ty, x0, x1, c0, c1);
+                if (p + (uint32_t)(c1 - c0) <= win) {   // the whole row lies before the window
+                    p += (uint32_t)(c1 - c0);
+                    continue;
+                }
+                for (int tx = c0; tx < c1 && p < end && p < wlim; ++tx, ++p)
+                    if (p >= win) {
+                        sk[p - win] = (KeyT)(base + (uint32_t)(ty * TX + tx));
+                        sv[p - win] = rank;
+                    }
+            }
+            // unreachable when the count and this walk agree; keeps the keys defined
+            for (p = max(p, win); p < end && p < wlim; ++p) {
+                sk[p - win] = (KeyT)sentinel;
+                sv[p - win] = 0u;
+            }
+        }
+        __syncwarp();
+        for (uint32_t j = lane; j < wlim - win; j += 32) {
+            pkey[win + j] = sk[j];
+            pval[win + j] = sv[j];
+        }
+        __syncwarp();
     }
 }
 
 // ------------------------------------------------------------ 5. ranges
+// Each thread takes 8 consecutive sorted keys (one or two 16-byte loads) and
+// marks where a key's run starts and ends; the neighbours across its group
+// come from two scalar loads.  The key buffer starts on a 16-byte boundary.
 template <class KeyT>
 __global__ void k_ranges(const KeyT* __restrict__ pkey, const uint64_t* __restrict__ np_dev, uint64_t cap,
                          uint32_t nkeys, uint2* __restrict__ ranges) {
+    constexpr int kV = 8;
     const uint64_t np = *np_dev;
     if (!pairs_fit(np, cap)) return;
     const int64_t P = (int64_t)np;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P; j += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t k = pkey[j];
-        if (k >= nkeys) continue;
-        if (j == 0 || (uint32_t)pkey[j - 1] != k) ranges[k].x = (uint32_t)j;
-        if (j == P - 1 || (uint32_t)pkey[j + 1] != k) ranges[k].y = (uint32_t)(j + 1);
+    const int64_t ngroups = (P + kV - 1) / kV;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j0 = g * kV;
+        uint32_t k[kV];
+        if (j0 + kV <= P) {
+            if constexpr (sizeof(KeyT) == 2) {
+                const uint4 q = *reinterpret_cast<const uint4*>(pkey + j0);
+                const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    k[2 * i] = w[i] & 0xffffu;
+                    k[2 * i + 1] = w[i] >> 16;
+                }
+            } else {
+                const uint4 a = *reinterpret_cast<const uint4*>(pkey + j0);
+                const uint4 b = *reinterpret_cast<const uint4*>(pkey + j0 + 4);
+                k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w;
+                k[4] = b.x; k[5] = b.y; k[6] = b.z; k[7] = b.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kV; ++i) k[i] = j0 + i < P ? (uint32_t)pkey[j0 + i] : 0xffffffffu;
+        }
+        const uint32_t prev = j0 > 0 ? (uint32_t)pkey[j0 - 1] : 0xffffffffu;
+        const uint32_t next = j0 + kV < P ? (uint32_t)pkey[j0 + kV] : 0xffffffffu;
+#pragma unroll
+        for (int i = 0; i < kV; ++i) {
+            const int64_t j = j0 + i;
+            const uint32_t kk = k[i];
+            if (j >= P || kk >= nkeys) continue;
+            const uint32_t before = i > 0 ? k[i - 1] : prev;
+            const uint32_t after = i + 1 < kV ? k[i + 1] : next;
+            if (j == 0 || before != kk) ranges[kk].x = (uint32_t)j;
+            if (j == P - 1 || after != kk) ranges[kk].y = (uint32_t)(j + 1);
+        }
     }
 }
 
@@ -977,11 +1058,11 @@ ludvig_status front_end(ludvig_scene* ctx, const GroupViews& g, int width, int h
     // (the tensor-core path) and every key and the sentinel fit
     const bool k16 = keys16_ok && !s->onesweep && sentinel < 0xffffu && !dbg;
     if (k16)
-        k_emit_pairs<uint16_t><<<grid_for(nG, 256), 256, 0, st>>>(cnt, off, srec, srect, npad, nG, TX, ntiles, prune,
+        k_emit_pairs<uint16_t><<<grid_for(nG, kEmitThreads), kEmitThreads, 0, st>>>(cnt, off, srec, srect, npad, nG, TX, ntiles, prune,
                                                                   total_d, (uint64_t)cap, ovf, sentinel,
                                                                   reinterpret_cast<uint16_t*>(pk), pv);
     else
-        k_emit_pairs<uint32_t><<<grid_for(nG, 256), 256, 0, st>>>(cnt, off, srec, srect, npad, nG, TX, ntiles, prune,
+        k_emit_pairs<uint32_t><<<grid_for(nG, kEmitThreads), kEmitThreads, 0, st>>>(cnt, off, srec, srect, npad, nG, TX, ntiles, prune,
                                                                   total_d, (uint64_t)cap, ovf, sentinel, pk, pv);
     LV_LAUNCH();
     trace_end(tslot, st);
