@@ -187,9 +187,20 @@ __global__ void __launch_bounds__(256, 5) k_weights(WeightsArgs a) {
         }
     };
     uint32_t next_rank = 0xffffffffu;   // warp 0: rank of batch k + kRing - 1 at iteration k
+    // warp 0, lane j: entry j of batch k has landed; its block mask.  Batch 0's
+    // is computed here, batch k + 1's after warp 0 has composited batch k (off
+    // the path of the other warps, which are still compositing batch k)
+    auto mask_batch = [&](uint32_t k) {
+        cp_async_wait<kRing - 2>();
+        if (k < nb && range.x + k * kTcBatch + (uint32_t)lane < range.y) {
+            PairRec& r = S.rec[k % kRing][lane];
+            r.mask = block_mask_fast(r.mx, r.my, r.ca, r.cb, r.cc, r.op, tx, ty);
+        }
+    };
     if (warp == 0) {
         for (uint32_t k = 0; k + 1 < (uint32_t)kRing; ++k) issue_records(k, rank_of(k));
         next_rank = rank_of(kRing - 1);
+        mask_batch(0);
     }
 
     float T = 1.0f;
@@ -198,14 +209,6 @@ __global__ void __launch_bounds__(256, 5) k_weights(WeightsArgs a) {
     int buf = 0;
     for (uint32_t k = 0; k < nb; ++k, buf ^= 1) {
         const uint32_t slot = k % kRing;
-        if (warp == 0) {
-            // this lane's record of batch k has landed: its block mask
-            cp_async_wait<kRing - 2>();
-            if (range.x + k * kTcBatch + (uint32_t)lane < range.y) {
-                PairRec& r = S.rec[slot][lane];
-                r.mask = block_mask_fast(r.mx, r.my, r.ca, r.cb, r.cc, r.op, tx, ty);
-            }
-        }
         if (__syncthreads_count(!done) == 0) break;
         // every thread is past batch k-1: its slot takes batch k + kRing - 1
         if (warp == 0) {
@@ -275,6 +278,7 @@ __global__ void __launch_bounds__(256, 5) k_weights(WeightsArgs a) {
             const uint32_t mine = __reduce_or_sync(0xffffffffu, lm);
             if (lane == 0 && mine) atomicOr(&S.rowmask[buf], mine);
         }
+        if (warp == 0) mask_batch(k + 1);   // (pending: batches k+1 .. k+kRing-1)
         if (tid == 0) S.rowmask[buf ^ 1] = 0u;
         __syncthreads();
         const uint32_t rowmask = S.rowmask[buf];
