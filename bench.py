@@ -36,7 +36,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["paper", "small"], default="paper")
+    ap.add_argument("--workload", choices=["paper", "small", "tiny"], default="paper")
     ap.add_argument("--dtype", choices=["f32", "bf16"], default="f32")
     ap.add_argument("--e2e-views", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -59,6 +59,8 @@ def workload(name):
     from paper_2410_14462_gb300 import inputs
     if name == "paper":
         return inputs.paper_scale_workload()
+    if name == "tiny":
+        return inputs.tiny_mask_workload()
     return inputs.paper_scale_workload(n=100_000, views=12, d=64, width=490, height=273)
 
 
@@ -252,14 +254,11 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm
-def cpu_baseline(args):
-    """The oracle on the host cores, timed exactly as the reference arm times
-    it: a child process running `bench.py --impl reference` on the same
-    workload and views (one view per step, views 3-5 after 3 untimed, as the
-    reference arm's default warm-up gives), so that the two agree; this
-    process's GPU work and its threads stay out of the timing."""
-    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", args.workload,
-           "--steps", "3", "--warmup", "3"]
+def oracle_child(workload_name, steps=3, warmup=3):
+    """`bench.py --impl reference` on a workload, in a child process with no GPU
+    visible; its cpu_baseline object, or an error object."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", workload_name,
+           "--steps", str(steps), "--warmup", str(warmup)]
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
     line = next((json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")), None)
@@ -268,6 +267,46 @@ def cpu_baseline(args):
     cb = dict(line["cpu_baseline"])
     cb["sample"] += "; run as a child process, as the reference arm"
     return cb
+
+
+def tiny_line(with_oracle):
+    """The tiny mask workload (20k uniform Gaussians, 8 views of 128x128, D = 1
+    float32 sphere masks): latency-bound, so the figure is microseconds per
+    call of the whole 8-view uplift (CUDA events over 50 calls after 5 warm-up
+    calls, features resident), beside the oracle's views*ch/s on the host."""
+    import torch
+    from paper_2410_14462_gb300 import ludvig
+    wl = workload("tiny")
+    V, H, W = wl.cams.v, wl.cams.height, wl.cams.width
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    feats = torch.stack([wl.features(v, device="cuda") for v in range(V)]).float().contiguous()   # [V,H,W,1]
+    out = torch.empty((sc.n, 1), device="cuda")
+    beta = torch.empty((sc.n,), device="cuda")
+    for _ in range(5):
+        ludvig.uplift(sc, wl.cams.params, W, H, feats, out, beta)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    calls = 50
+    e0.record()
+    for _ in range(calls):
+        ludvig.uplift(sc, wl.cams.params, W, H, feats, out, beta)
+    e1.record()
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / calls
+    line = {"workload": wl.name, "us_per_call": us, "value": V * 1 / (us / 1e6), "unit": UNIT,
+            "bound": "latency (launches and the D-independent walk; 0.5 MB of features)"}
+    if with_oracle:
+        line["cpu_baseline"] = oracle_child("tiny")
+    return line
+
+
+def cpu_baseline(args):
+    """The oracle on the host cores, timed exactly as the reference arm times
+    it: a child process running `bench.py --impl reference` on the same
+    workload and views (one view per step, views 3-5 after 3 untimed, as the
+    reference arm's default warm-up gives), so that the two agree; this
+    process's GPU work and its threads stay out of the timing."""
+    return oracle_child(args.workload)
 
 
 # DRAM bytes (read + write) of one k_aggregate_tc launch, from the ncu capture in
@@ -609,8 +648,13 @@ def count_normalised_line(sc, wl, feats):
     finally:
         ludvig.set_option(ludvig.OPT_COUNT_NORMALISE, 0)
     ms = e0.elapsed_time(e1)
+    contrib = float(cnt.double().sum().item())   # sum over views and pixels of the w > 0 contributors
     return {"ms": ms, "value": V * D / (ms / 1e3), "unit": UNIT,
-            "max_count": float(cnt.max().item()), "gaussians_counted": int((cnt > 0).sum().item())}
+            "max_count": float(cnt.max().item()), "gaussians_counted": int((cnt > 0).sum().item()),
+            "contributions": contrib,
+            "aggregation_algorithmic_tflop": (2 * D + 1) * contrib / 1e12,
+            "note": ("contributions = sum_i count_i = sum over (view, pixel) of the Gaussians with w > 0; "
+                     "the aggregation's algorithmic work is 2 D flops per contribution (+1 for den)")}
 
 
 def batched_form(pools, cams, slots=6):
@@ -954,6 +998,8 @@ def run_ours(args):
             line["serving"] = serving_form(pools, fcams)
         pools = None
         torch.cuda.empty_cache()
+    if rank == 0 and args.workload == "paper":
+        line["tiny_config"] = tiny_line(world == 1 and not args.no_cpu_baseline)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         del feats
         torch.cuda.empty_cache()
