@@ -172,10 +172,11 @@ __device__ __forceinline__ Projected project_gaussian(const float* m, const floa
     o.mx = __fadd_rn(__fdiv_rn(__fmul_rn(c.fx, tx), tz), c.cx);
     o.my = __fadd_rn(__fdiv_rn(__fmul_rn(c.fy, ty), tz), c.cy);
     o.radius = rad;
-    const float fx0 = floorf(__fdiv_rn(__fsub_rn(o.mx, rad), 16.0f));
-    const float fx1 = __fadd_rn(floorf(__fdiv_rn(__fadd_rn(o.mx, rad), 16.0f)), 1.0f);
-    const float fy0 = floorf(__fdiv_rn(__fsub_rn(o.my, rad), 16.0f));
-    const float fy1 = __fadd_rn(floorf(__fdiv_rn(__fadd_rn(o.my, rad), 16.0f)), 1.0f);
+    // x / 16 and x * 2^-4 round the same exact value: identical results
+    const float fx0 = floorf(__fmul_rn(__fsub_rn(o.mx, rad), 0.0625f));
+    const float fx1 = __fadd_rn(floorf(__fmul_rn(__fadd_rn(o.mx, rad), 0.0625f)), 1.0f);
+    const float fy0 = floorf(__fmul_rn(__fsub_rn(o.my, rad), 0.0625f));
+    const float fy1 = __fadd_rn(floorf(__fmul_rn(__fadd_rn(o.my, rad), 0.0625f)), 1.0f);
     o.x0 = (int)clampf_rule(fx0, 0.0f, (float)TX);
     o.x1 = (int)clampf_rule(fx1, 0.0f, (float)TX);
     o.y0 = (int)clampf_rule(fy0, 0.0f, (float)TY);
@@ -274,8 +275,13 @@ __device__ __forceinline__ float block_y0(int ty, int w) { return (float)(ty * k
 // inside, else an end point (the upper boundary is concave in dy), and likewise
 // for the smallest.  Both ranges are widened for rounding (thr itself carries
 // the slack of reach_prep), so a pixel that the float32 per-pixel test of
-// Eq. 1 can give alpha >= 1/255 lies inside.  Every rounding is explicit:
-// k_project and k_emit_pairs must take the same tile decisions.
+// Eq. 1 can give alpha >= 1/255 lies inside.  The square roots and quotients
+// are the hardware approximations (a few ulp, far inside the widening); every
+// product and sum is rounded explicitly, so that no call site fuses them
+// differently: k_project (the count) and k_emit_pairs (the emission) must take
+// the same tile decisions.
+__device__ __forceinline__ float sqrt_fast(float x) { return x > 0.0f ? __fmul_rn(x, rsqrtf(x)) : 0.0f; }
+
 struct EllipseX {
     float b, det, thra, umax, wmax, ws, inv_a, epsx;
     int state;   // 0: reaches nothing, 1: ranges valid, 2: degenerate (take everything)
@@ -292,12 +298,12 @@ __device__ __forceinline__ EllipseX ellipse_prep(const Reach& R, float a, float 
         return E;
     }
     E.state = 1;
-    E.inv_a = __frcp_rn(a);
-    E.umax = __fsqrt_rn(__fdiv_rn(__fmul_rn(thr, c), E.det));
-    E.wmax = __fadd_rn(__fmul_rn(__fsqrt_rn(__fdiv_rn(__fmul_rn(thr, a), E.det)), 1.0001f), 0.02f);
-    E.ws = __fdiv_rn(__fmul_rn(-b, E.umax), c);
+    E.inv_a = __fdividef(1.0f, a);
+    E.umax = sqrt_fast(__fdividef(__fmul_rn(thr, c), E.det));
+    E.wmax = __fadd_rn(__fmul_rn(sqrt_fast(__fdividef(__fmul_rn(thr, a), E.det)), 1.0002f), 0.05f);
+    E.ws = __fdividef(__fmul_rn(-b, E.umax), c);
     E.thra = __fmul_rn(thr, a);
-    E.epsx = __fadd_rn(__fmul_rn(1e-3f, __fadd_rn(E.umax, 1.0f)), 0.02f);
+    E.epsx = __fadd_rn(__fmul_rn(2e-3f, __fadd_rn(E.umax, 1.0f)), 0.05f);
     return E;
 }
 
@@ -306,8 +312,8 @@ __device__ __forceinline__ bool ellipse_x_range(const EllipseX& E, float mx, flo
                                                 float& xl, float& xr) {
     const float w0 = fmaxf(__fsub_rn(my, yhi), -E.wmax), w1 = fminf(__fsub_rn(my, ylo), E.wmax);
     if (w0 > w1) return false;
-    const float s0 = __fsqrt_rn(fmaxf(__fsub_rn(E.thra, __fmul_rn(E.det, __fmul_rn(w0, w0))), 0.0f));
-    const float s1 = __fsqrt_rn(fmaxf(__fsub_rn(E.thra, __fmul_rn(E.det, __fmul_rn(w1, w1))), 0.0f));
+    const float s0 = sqrt_fast(__fsub_rn(E.thra, __fmul_rn(E.det, __fmul_rn(w0, w0))));
+    const float s1 = sqrt_fast(__fsub_rn(E.thra, __fmul_rn(E.det, __fmul_rn(w1, w1))));
     const float bw0 = __fmul_rn(-E.b, w0), bw1 = __fmul_rn(-E.b, w1);
     const float hi = (E.ws >= w0 && E.ws <= w1)
                          ? E.umax
