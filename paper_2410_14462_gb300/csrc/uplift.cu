@@ -1223,6 +1223,20 @@ ludvig_status uplift_group(ludvig_scene* ctx, const GroupViews& g, int width, in
         fextent = nv;
         for (int k = 0; k < nv; ++k) av.fview[k] = k;
     }
+    if (padded && tc_direct_supported(src.d)) {
+        // a few channels: the weights pass adds each row's W^T F and den into
+        // the (padded) numerator itself; no weight rows, no aggregation
+        int* cnt = nullptr;
+        LV_TRY(tc_weights_direct(fe.L, nv, width, height, fdt == LUDVIG_F32 ? 2 : 1, src.d, kPadD, f, fdt, av, s->ws,
+                                 p, s->dstat, !ex.async, sf, &cnt));
+        if (ex.async) {
+            LV_CUDA(cudaMemcpyAsync(&ex.diag->chunks, cnt, sizeof(int), cudaMemcpyDeviceToDevice, sf));
+            LV_CUDA(cudaEventRecord(s->ev_front[p], sf));
+            LV_CUDA(cudaStreamWaitEvent(sa, s->ev_front[p], 0));
+            LV_CUDA(cudaEventRecord(s->ev_agg[p], sa));
+        }
+        return LUDVIG_OK;
+    }
     if (padded) {
         const int64_t npx = (int64_t)nv * width * height;
         const size_t pes = fdt == LUDVIG_F32 ? 4 : 2;
@@ -1343,14 +1357,15 @@ ludvig_status reserve_async(ludvig_scene* s, int nv, int ng, int64_t n, int widt
     const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
     const bool padded = src_padded(src);
     const int fdt = src.kind == 2 ? LUDVIG_BF16 : src.dtype;
-    LV_TRY(tc_reserve(ws, fdt == LUDVIG_F32 ? 2 : 1, nv * TX * TY, s->tc_chunk_cap));
+    const bool direct = padded && tc_direct_supported(src.d);   // no weight rows, no padded copy
+    if (!direct) LV_TRY(tc_reserve(ws, fdt == LUDVIG_F32 ? 2 : 1, nv * TX * TY, s->tc_chunk_cap));
     const int64_t npx = (int64_t)nv * width * height;
     for (int p = 0; p < 2; ++p) {
         static const char* const kFb[2] = {"fp8.bf16.0", "fp8.bf16.1"};
         static const char* const kPad[2] = {"pad.feats.0", "pad.feats.1"};
         if (src.kind == 2 && (padded || !tc_e4m3_supported(src.d) || (reinterpret_cast<uintptr_t>(src.feats) & 15)))
             LV_TRY(ws.get(kFb[p], 2 * (size_t)npx * src.d, &q));
-        if (padded) LV_TRY(ws.get(kPad[p], (size_t)npx * kPadD * (fdt == LUDVIG_F32 ? 4 : 2), &q));
+        if (padded && !direct) LV_TRY(ws.get(kPad[p], (size_t)npx * kPadD * (fdt == LUDVIG_F32 ? 4 : 2), &q));
     }
     return LUDVIG_OK;
 }

@@ -124,6 +124,10 @@ inline bool tc_e4m3_supported(int d) { return d >= 32 && d <= 512 && d % 16 == 0
 // are aggregated).  checked: the chunk count is read back (synchronises `st`)
 // and the pass re-run with more chunks until they fit.  Otherwise it runs once
 // with *chunk_cap chunks and the aggregation checks the count on the device.
+bool tc_direct_supported(int d);
+ludvig_status tc_weights_direct(const GroupLists& L, int nv, int width, int height, int NT, int d, int num_stride,
+                                const void* feats, int feat_dtype, const AggViews& av, Arena& ws, int parity,
+                                int* status, bool checked, cudaStream_t st, int** counter);
 ludvig_status tc_weights(const GroupLists& L, int nv, int width, int height, int NT, Arena& ws, int parity,
                          int* status, int64_t* chunk_cap, bool checked, cudaStream_t st, TileWeights* tw);
 

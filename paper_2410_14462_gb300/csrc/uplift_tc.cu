@@ -102,14 +102,30 @@ struct WeightsArgs {
     int cap;
     float* chunk_den;       // [cap][128][NT]: each row's sum of its weight term (rewritten on a re-run)
     int count_den;          // chunk_den holds each row's count of non-zero weights (term 0; term 1: 0)
+    // direct accumulation (k_weights<NT, true>, few channels): each new row's
+    // sum_p w F[p, c] and its den go straight into the view's num and den
+    // (atomic adds); no weight rows, chunks or plan are written
+    int direct_d;           // channels, 1 .. kDirectMaxD
+    int num_stride;         // floats per Gaussian in num
+    const void* feats;      // [.., H, W, direct_d] float32 or bfloat16, views at views.fview
+    int feat_bf16;
+    AggViews views;
 };
 
+constexpr int kDirectMaxD = 4;
+
 template <int NT>
-struct WeightsSmem {
+struct WeightsSmemBase {
     alignas(16) PairRec rec[kRing][kTcBatch];
     alignas(16) uint8_t stage[NT][kTcBatch * kRowBytes];   // [term][j][256 pixels]
     uint32_t rowmask[2];
     int cur_chunk, cur_start, next_chunk;
+};
+template <int NT, bool DIRECT>
+struct WeightsSmem : WeightsSmemBase<NT> {};
+template <int NT>
+struct WeightsSmem<NT, true> : WeightsSmemBase<NT> {
+    alignas(16) float feat[kDirectMaxD][256];   // the tile's features by channel and pixel (0 off the image)
 };
 
 // A weight row's contribution to den, from its 256 bfloat16 values (8 per
@@ -137,9 +153,9 @@ __device__ __forceinline__ void finish_chunk(const WeightsArgs& a, int c, int ro
     }
 }
 
-template <int NT>
-__global__ void __launch_bounds__(256, 5) k_weights(WeightsArgs a) {
-    __shared__ WeightsSmem<NT> S;
+template <int NT, bool DIRECT>
+__global__ void __launch_bounds__(256, 5) k_weights(const __grid_constant__ WeightsArgs a) {
+    __shared__ WeightsSmem<NT, DIRECT> S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
     const int item = blockIdx.x;
@@ -163,6 +179,20 @@ __global__ void __launch_bounds__(256, 5) k_weights(WeightsArgs a) {
     }
     for (int e = tid; e < (int)(NT * kTcBatch * kRowBytes / 16); e += 256)
         reinterpret_cast<uint4*>(&S.stage[0][0])[e] = make_uint4(0u, 0u, 0u, 0u);
+    if constexpr (DIRECT) {
+        // this thread's pixel's channels (zero off the image: no weight there)
+        const bool in_img = px < a.width && py < a.height;
+        const size_t pidx = ((size_t)a.views.fview[v] * a.height + (in_img ? py : 0)) * a.width + (in_img ? px : 0);
+#pragma unroll
+        for (int c = 0; c < kDirectMaxD; ++c) {
+            float x = 0.f;
+            if (in_img && c < a.direct_d)
+                x = a.feat_bf16
+                        ? __bfloat162float(static_cast<const __nv_bfloat16*>(a.feats)[pidx * a.direct_d + c])
+                        : static_cast<const float*>(a.feats)[pidx * a.direct_d + c];
+            S.feat[c][pix] = x;
+        }
+    }
     __syncthreads();
 
     // batch k of the list goes to ring slot k % kRing.  Warp 0, lane j gathers
@@ -215,7 +245,7 @@ __global__ void __launch_bounds__(256, 5) k_weights(WeightsArgs a) {
             issue_records(k + kRing - 1, next_rank);
             next_rank = rank_of(k + kRing);
         }
-        if (tid == 0) {
+        if (!DIRECT && tid == 0) {
             // rows [nrows, nrows + 32) must have chunks; a chunk filled to
             // exactly 128 rows may not have its successor yet
             if (nrows >= S.cur_start + kCRows) {
@@ -289,7 +319,51 @@ __global__ void __launch_bounds__(256, 5) k_weights(WeightsArgs a) {
         // rows), 16 bytes per lane, one warp per row and term; the staging row
         // is cleared behind, the row's sum of each term (the bfloat16 values the
         // product uses) is kept for den, and the Gaussian id is recorded
-        if constexpr (NT == 2) {
+        if constexpr (DIRECT) {
+            // warp i % 8 takes row i: its weights w = W1 (+ W2), 8 pixels per
+            // lane, dotted with the tile's channels; the staging row is cleared
+            float* const vnum = a.views.num[v];
+            float* const vden = a.views.den[v];
+            uint32_t m = rowmask;
+            for (int i = 0; m != 0u; ++i, m &= m - 1u) {
+                if ((i & 7) != warp) continue;
+                const int j = __ffs(m) - 1;
+                float w[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float sden = 0.f;
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    uint4* src = reinterpret_cast<uint4*>(&S.stage[t][j * kRowBytes + lane * 16]);
+                    const uint4 v4 = *src;
+                    *src = make_uint4(0u, 0u, 0u, 0u);
+                    const uint32_t wv[4] = {v4.x, v4.y, v4.z, v4.w};
+                    sden += row_den(wv, a.count_den, t);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        w[2 * k] += __uint_as_float(wv[k] << 16);
+                        w[2 * k + 1] += __uint_as_float(wv[k] & 0xffff0000u);
+                    }
+                }
+                const uint32_t gid = rec[j].gid;
+#pragma unroll
+                for (int c = 0; c < kDirectMaxD; ++c) {
+                    if (c >= a.direct_d) break;
+                    const float4 f0 = *reinterpret_cast<const float4*>(&S.feat[c][lane * 8]);
+                    const float4 f1 = *reinterpret_cast<const float4*>(&S.feat[c][lane * 8 + 4]);
+                    float sc = w[0] * f0.x;
+                    sc = fmaf(w[1], f0.y, sc);
+                    sc = fmaf(w[2], f0.z, sc);
+                    sc = fmaf(w[3], f0.w, sc);
+                    sc = fmaf(w[4], f1.x, sc);
+                    sc = fmaf(w[5], f1.y, sc);
+                    sc = fmaf(w[6], f1.z, sc);
+                    sc = fmaf(w[7], f1.w, sc);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) sc += __shfl_xor_sync(0xffffffffu, sc, o);
+                    if (lane == 0) atomicAdd(vnum + (size_t)gid * a.num_stride + c, sc);
+                }
+                if (lane == 0) atomicAdd(vden + gid, sden);
+            }
+        } else if constexpr (NT == 2) {
             // warp i % 8 takes row i, both terms
             uint32_t m = rowmask;
             for (int i = 0; m != 0u; ++i, m &= m - 1u) {
@@ -350,7 +424,7 @@ __global__ void __launch_bounds__(256, 5) k_weights(WeightsArgs a) {
     // gathers issued past an early stop still land before the CTA exits
     if (warp == 0) cp_async_wait<0>();
     __syncthreads();
-    if (tid == 0) {
+    if (!DIRECT && tid == 0) {
         const int cur = S.cur_chunk, cstart = S.cur_start, nxt = S.next_chunk;
         if (nrows > cstart + kCRows) {   // the last batch spilled into nxt
             finish_chunk(a, cur, kCRows, nxt);
@@ -1516,9 +1590,9 @@ ludvig_status tc_weights(const GroupLists& L, int nv, int width, int height, int
         w.count_den = option_count_normalise() ? 1 : 0;
         const int tslot = trace_on() ? trace_begin(LUDVIG_STAGE_WEIGHTS, st) : -1;
         if (NT == 2)
-            k_weights<2><<<nitems, 256, 0, st>>>(w);
+            k_weights<2, false><<<nitems, 256, 0, st>>>(w);
         else
-            k_weights<1><<<nitems, 256, 0, st>>>(w);
+            k_weights<1, false><<<nitems, 256, 0, st>>>(w);
         LV_LAUNCH();
         trace_end(tslot, st);
         if (!checked) break;
@@ -1552,6 +1626,63 @@ ludvig_status tc_weights(const GroupLists& L, int nv, int width, int height, int
     t.cap = cap;
     *chunk_cap = cap;
     *tw = t;
+    return LUDVIG_OK;
+}
+
+// The weights pass with direct accumulation for d <= kDirectMaxD channels:
+// num (row stride num_stride) and den of each view take every row's
+// contribution as the row is made, so no weight rows, chunk plan or
+// aggregation launch exist for the group.  The chunk counter stays 0.
+bool tc_direct_supported(int d) { return d >= 1 && d <= kDirectMaxD; }
+
+ludvig_status tc_weights_direct(const GroupLists& L, int nv, int width, int height, int NT, int d, int num_stride,
+                                const void* feats, int feat_dtype, const AggViews& av, Arena& ws, int parity,
+                                int* status, bool checked, cudaStream_t st, int** counter) {
+    if (!tc_direct_supported(d) || nv < 1 || nv > kMaxGroupViews) {
+        set_error("direct accumulation takes 1 to %d channels and 1 to %d views", kDirectMaxD, kMaxGroupViews);
+        return LUDVIG_ERR_INTERNAL;
+    }
+    const int p = parity & 1;
+    const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
+    const int nitems = nv * TX * TY;
+    int* cnt;
+    LV_TRY(ws.get(kWsCounter[p], 1, &cnt));
+    LV_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), st));
+    WeightsArgs w{};
+    w.rank = L.rank;
+    w.srec = L.srec;
+    w.npad = L.npad;
+    w.ranges = L.ranges;
+    w.ntiles = TX * TY;
+    w.TX = TX;
+    w.width = width;
+    w.height = height;
+    w.chunk_counter = cnt;
+    w.count_den = option_count_normalise() ? 1 : 0;
+    w.direct_d = d;
+    w.num_stride = num_stride;
+    w.feats = feats;
+    w.feat_bf16 = feat_dtype == LUDVIG_BF16 ? 1 : 0;
+    w.views = av;
+    const int tslot = trace_on() ? trace_begin(LUDVIG_STAGE_WEIGHTS, st) : -1;
+    if (NT == 2)
+        k_weights<2, true><<<nitems, 256, 0, st>>>(w);
+    else
+        k_weights<1, true><<<nitems, 256, 0, st>>>(w);
+    LV_LAUNCH();
+    trace_end(tslot, st);
+    if (checked) {
+        void* hp;
+        LV_TRY(ws.pinned("tc.host", 16, &hp));
+        int* host = static_cast<int*>(hp);
+        LV_CUDA(cudaMemcpyAsync(host + 1, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LV_CUDA(cudaStreamSynchronize(st));
+        if (host[1] != 0) {
+            set_error("tile weights: a bounded wait expired");
+            return (ludvig_status)host[1];
+        }
+    }
+    if (counter) *counter = cnt;
     return LUDVIG_OK;
 }
 
