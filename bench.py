@@ -289,12 +289,26 @@ def tiny_line(with_oracle):
     calls = 50
     e0.record()
     for _ in range(calls):
-        ludvig.uplift(sc, wl.cams.params, W, H, feats, out, beta)
+        ludvig.uplift(sc, wl.cams.params, W, H, feats, out, beta)   # ends with ludvig_sync
     e1.record()
     torch.cuda.synchronize()
     us = e0.elapsed_time(e1) * 1e3 / calls
+    # the same calls enqueued back to back (one ludvig_sync at the end), and
+    # the host time of one enqueue
+    e0.record()
+    t0 = time.perf_counter()
+    for _ in range(calls):
+        ludvig.uplift(sc, wl.cams.params, W, H, feats, out, beta, sync=False)
+    host_us = (time.perf_counter() - t0) * 1e6 / calls
+    sc.sync()
+    e1.record()
+    torch.cuda.synchronize()
+    us_async = e0.elapsed_time(e1) * 1e3 / calls
     line = {"workload": wl.name, "us_per_call": us, "value": V * 1 / (us / 1e6), "unit": UNIT,
-            "bound": "latency (launches and the D-independent walk; 0.5 MB of features)"}
+            "us_per_call_back_to_back": us_async, "host_enqueue_us_per_call": host_us,
+            "bound": "latency (launches and the D-independent walk; 0.5 MB of features)",
+            "timing": "us_per_call: each call ends with ludvig_sync (call to result); back to back: "
+                      "50 calls enqueued without a wait, one ludvig_sync after them"}
     if with_oracle:
         line["cpu_baseline"] = oracle_child("tiny")
     return line
