@@ -1143,6 +1143,8 @@ ludvig_status composite_cc(ludvig_scene* s, const FrontEnd& fe, int nv, int widt
 // ---------------------------------------------------------------- group pipeline
 
 bool src_padded(const FeatSrc& f) { return f.kind == 1 || (f.kind == 2 && f.d < kPadD); }
+// A few channels: the weights pass accumulates itself (no weight rows or chunk capacity).
+bool src_direct(const FeatSrc& f) { return src_padded(f) && tc_direct_supported(f.d); }
 
 // How a group's work is ordered.
 struct Exec {
@@ -1223,7 +1225,7 @@ ludvig_status uplift_group(ludvig_scene* ctx, const GroupViews& g, int width, in
         fextent = nv;
         for (int k = 0; k < nv; ++k) av.fview[k] = k;
     }
-    if (padded && tc_direct_supported(src.d)) {
+    if (src_direct(src)) {
         // a few channels: the weights pass adds each row's W^T F and den into
         // the (padded) numerator itself; no weight rows, no aggregation
         int* cnt = nullptr;
@@ -1357,7 +1359,7 @@ ludvig_status reserve_async(ludvig_scene* s, int nv, int ng, int64_t n, int widt
     const int TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
     const bool padded = src_padded(src);
     const int fdt = src.kind == 2 ? LUDVIG_BF16 : src.dtype;
-    const bool direct = padded && tc_direct_supported(src.d);   // no weight rows, no padded copy
+    const bool direct = src_direct(src);   // no weight rows, no padded copy
     if (!direct) LV_TRY(tc_reserve(ws, fdt == LUDVIG_F32 ? 2 : 1, nv * TX * TY, s->tc_chunk_cap));
     const int64_t npx = (int64_t)nv * width * height;
     for (int p = 0; p < 2; ++p) {
@@ -1526,7 +1528,7 @@ ludvig_status size_for_async(ludvig_scene* s, const std::vector<GroupViews>& gro
                              const FeatSrc& src, bool tc, bool always, cudaStream_t st, size_t* first) {
     *first = 0;
     if (groups.empty()) return LUDVIG_OK;
-    if (always || s->pair_cap == 0 || (tc && s->tc_chunk_cap == 0)) {
+    if (always || s->pair_cap == 0 || (tc && !src_direct(src) && s->tc_chunk_cap == 0)) {
         const int64_t pc0 = s->pair_cap, cc0 = s->tc_chunk_cap;
         LV_TRY(run_checked(s, groups[0], width, height, src, st));
         if (s->pair_cap > pc0) s->pair_cap = round_up(s->pair_cap + s->pair_cap / 4, kRadixTile);
