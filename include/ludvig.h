@@ -73,13 +73,16 @@ typedef enum {
 } ludvig_status;
 
 typedef enum {
-    LUDVIG_F32 = 0,              /* float32 features.  d < 32, or 32 <= d <= 512 with d % 8 == 0:
-                                    tensor-core aggregation with features and weights split into
-                                    two bfloat16 terms each (float32-level accuracy); otherwise,
-                                    or with LUDVIG_OPT_F32_TENSOR_CORES = 0, CUDA-core FFMA */
-    LUDVIG_BF16 = 1              /* bfloat16 features.  d < 32, or 32 <= d <= 512 with d % 8 == 0:
-                                    tensor-core aggregation with bfloat16 weights; otherwise CUDA
-                                    cores with float32 weights */
+    LUDVIG_F32 = 0,              /* float32 features.  4 < d < 32, or 32 <= d <= 512 with
+                                    d % 8 == 0: tensor-core aggregation with features and weights
+                                    split into two bfloat16 terms each (float32-level accuracy);
+                                    d <= 4: the same weight terms summed in the compositing pass;
+                                    otherwise, or with LUDVIG_OPT_F32_TENSOR_CORES = 0, CUDA-core
+                                    FFMA */
+    LUDVIG_BF16 = 1              /* bfloat16 features.  4 < d < 32, or 32 <= d <= 512 with
+                                    d % 8 == 0: tensor-core aggregation with bfloat16 weights;
+                                    d <= 4: bfloat16 weights summed in the compositing pass;
+                                    otherwise CUDA cores with float32 weights */
 } ludvig_dtype;
 
 /* Process-wide options (ludvig_set_option / ludvig_get_option). */
@@ -193,14 +196,16 @@ int64_t ludvig_scene_workspace_bytes(ludvig_scene_t scene);
  * partial sums over disjoint view sets can be merged by addition (view
  * sharding, checkpoint/resume).  Summation order on the GPU is not fixed
  * (atomics), so results are reproducible only to rounding.
- * Where the products run: d < 32, or 32 <= d <= 512 with d % 8 == 0, on the
- * tensor cores (d < 32 on features the library zero-pads to 32 channels in
- * its workspace), float32 features as split-bfloat16 terms (float32-level
- * accuracy; LUDVIG_OPT_F32_TENSOR_CORES = 0 moves them to CUDA cores),
- * bfloat16 features with the weights rounded to bfloat16 for the product;
- * any other d on CUDA cores with float32 weights.
+ * Where the products run: d <= 4 in the compositing pass itself (each weight
+ * row, split into bfloat16 terms as below, is dotted with the tile's features
+ * on CUDA cores as it is made); 4 < d < 32, or 32 <= d <= 512 with d % 8 == 0,
+ * on the tensor cores (4 < d < 32 on features the library zero-pads to 32
+ * channels in its workspace), float32 features as split-bfloat16 terms
+ * (float32-level accuracy; LUDVIG_OPT_F32_TENSOR_CORES = 0 moves them, and
+ * float32 d <= 4, to CUDA cores), bfloat16 features with the weights rounded
+ * to bfloat16 for the product; any other d on CUDA cores with float32 weights.
  * Asynchronous: num/den are complete once ludvig_sync(scene) has returned
- * LUDVIG_OK (the views run in groups of up to 16; a group's projection, sorts
+ * LUDVIG_OK (the views run in groups of up to 128; a group's projection, sorts
  * and weights overlap the previous group's products on two internal streams
  * that are joined back into `stream`). */
 ludvig_status ludvig_uplift_accumulate(ludvig_scene_t scene, const ludvig_camera* cams,
@@ -254,7 +259,7 @@ ludvig_status ludvig_fp8_quantize(const void* feats, int32_t dtype, int32_t n_vi
  * bfloat16 path, so results carry the bfloat16 bar on the decoded values.
  * With d % 16 == 0, 32 <= d <= 512 and q 16-byte aligned the aggregation
  * reads the codes themselves and decodes them in shared memory (one byte
- * per value crosses DRAM); otherwise each group of up to 16 views is decoded
+ * per value crosses DRAM); otherwise each group of views (up to 128) is decoded
  * into the scene's workspace first.  out, beta as for ludvig_uplift. */
 ludvig_status ludvig_uplift_fp8(ludvig_scene_t scene, const ludvig_camera* cams, int32_t n_views,
                                 int32_t width, int32_t height, const uint8_t* q, const float* scales,
