@@ -953,6 +953,10 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs (features) larger than L2; no flush"},
             "stages_ms_per_step": {k: v / args.steps for k, v in tr["ms"].items()},
+            "stages_note": ("device-event intervals on the stream that runs each stage; a group's front end "
+                            "(project, depth sort) is enqueued while the previous group's aggregation holds "
+                            "every SM, so those intervals include the wait for SMs; the kernel times are in "
+                            "the ncu launch list"),
             "gpu_launches": tr["kernel_launches"],
             "roofline": roof, "clocks": clk}
 
