@@ -1724,13 +1724,19 @@ ludvig_status uplift_packed(ludvig_scene* ctx, const PackedJob* jobs, int njobs,
         LV_CUDA(cudaMemsetAsync(den[j], 0, sizeof(float) * (size_t)n, st));
         if (padded) LV_CUDA(cudaMemsetAsync(acc[j], 0, sizeof(float) * (size_t)n * kPadD, st));
     }
-    // the groups: every job's views in job order; a group closes at kMaxViews
-    // views, at group_pixels(group_bytes) pixels, or when one more view would
-    // take its Gaussian scratch past the budget
+    // the groups: every job's views, the jobs taken by decreasing scene size
+    // (a group's views are projected and depth-sorted at its largest scene's
+    // size, so views of similar scenes share groups); a group closes at
+    // kMaxViews views, at group_pixels(group_bytes) pixels, or when one more
+    // view would take its Gaussian scratch past the budget
     const int64_t max_views = std::max<int64_t>(1, packed_pixels(group_bytes, dtype) / ((int64_t)width * height));
+    std::vector<int> order(njobs);
+    for (int j = 0; j < njobs; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return jobs[x].scene->n > jobs[y].scene->n; });
     std::vector<GroupViews> groups;
     GroupViews cur;
-    for (int j = 0; j < njobs; ++j) {
+    for (int j : order) {
         const ludvig_scene* sc = jobs[j].scene;
         if (sc->n == 0) continue;
         for (int v = 0; v < jobs[j].n_views; ++v) {
