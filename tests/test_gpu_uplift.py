@@ -435,3 +435,72 @@ def test_log_scale_scene_input():
     torch.cuda.synchronize()
     va, vb = ra[0].cpu().numpy(), rb[0].cpu().numpy()
     assert np.allclose(va, vb, rtol=1e-4, atol=1e-4)
+
+
+def _wide_workload(d=4):
+    """One camera (320x240, fx = fy = 200) looking down +z at 400 large
+    Gaussians in front (standard deviations 0.1-0.5 at depths 1.5-2.5: radii
+    of tens to hundreds of pixels, up to the whole image of 300 tiles) and
+    6000 small ones behind.  The large ones lead the depth order, so a warp's
+    32 consecutive Gaussians emit thousands of (tile, Gaussian) pairs: the
+    emission fills its range in several shared-memory windows."""
+    rng = np.random.default_rng(31)
+    nb, ns = 400, 6000
+    z = np.concatenate([rng.uniform(1.5, 2.5, nb), rng.uniform(3.0, 5.0, ns)])
+    u = rng.uniform(-40, 360, nb + ns)
+    v = rng.uniform(-40, 280, nb + ns)
+    means = np.stack([(u - 160) * z / 200, (v - 120) * z / 200, z], 1)
+    scales = np.concatenate([rng.uniform(0.1, 0.5, (nb, 3)), np.exp(rng.normal(-4, 0.5, (ns, 3)))])
+    q = rng.normal(size=(nb + ns, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    opac = np.concatenate([rng.uniform(0.05, 0.3, nb), rng.uniform(0.2, 0.99, ns)])
+    scene = inputs.Scene(means.astype(np.float32), scales.astype(np.float32), q.astype(np.float32),
+                         opac.astype(np.float32))
+    params = np.zeros((1, 16), np.float32)
+    params[0, :9] = np.eye(3).reshape(-1)
+    params[0, 12:16] = (200.0, 200.0, 160.0, 120.0)
+    return inputs.Workload("wide", scene, inputs.Cameras(params, 320, 240), d, 13, "field")
+
+
+@pytest.mark.parametrize("d", [4, 48])
+def test_wide_footprints_many_pairs_per_warp(d):
+    """Tile lists (unpruned: the binning rule) bit-exact, pruned lists a
+    contributor-keeping sub-sequence, and the float32 uplift within 1e-5 of
+    the float64 oracle (d = 4: accumulated by the weights pass; d = 48: the
+    tensor-core aggregation), on a scene whose warps emit many windows."""
+    wl = _wide_workload(d)
+    sc = ludvig.Scene.from_inputs(wl.scene)
+    W, H = wl.cams.width, wl.cams.height
+    cam = wl.cams.params[0]
+    ranges, lst = ludvig.debug_tile_lists(sc, cam, W, H)
+    r_ref, l_ref = oracle.tile_lists(wl.scene, cam, W, H)
+    ranges, lst = ranges.cpu().numpy(), lst.cpu().numpy()
+    assert np.array_equal(ranges[:, 1] - ranges[:, 0], r_ref[:, 1] - r_ref[:, 0])
+    for t in range(r_ref.shape[0]):
+        assert np.array_equal(lst[ranges[t, 0]:ranges[t, 1]], l_ref[r_ref[t, 0]:r_ref[t, 1]]), f"tile {t}"
+    pr = oracle.project(wl.scene, cam, W, H)
+    rect = pr["rect"].astype(np.int64)
+    area = (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1]) * pr["visible"]
+    order = np.lexsort((np.arange(wl.scene.n), pr["p32"][:, 2]))
+    per_warp = np.add.reduceat(area[order][pr["visible"][order]], np.arange(0, int(pr["visible"].sum()), 32))
+    print(f"wide d={d}: {len(l_ref)} pairs, largest warp range {per_warp.max()} pairs")
+    assert per_warp.max() > 4 * 1024
+    TX = (W + 15) // 16
+    pr_ranges, pr_lst = ludvig.debug_tile_lists(sc, cam, W, H, pruned=True)
+    pr_ranges, pr_lst = pr_ranges.cpu().numpy(), pr_lst.cpu().numpy()
+    res = oracle.view_uplift(wl.scene, cam, W, H, triplets=True)
+    tile_of = (res["pix"] // W // 16) * TX + (res["pix"] % W) // 16
+    for t in range(r_ref.shape[0]):
+        a = pr_lst[pr_ranges[t, 0]:pr_ranges[t, 1]].tolist()
+        b = l_ref[r_ref[t, 0]:r_ref[t, 1]].tolist()
+        pos = {g: k for k, g in enumerate(b)}
+        idx = [pos[g] for g in a]
+        assert idx == sorted(idx) and len(set(idx)) == len(idx), f"tile {t}"
+        assert set(res["gid"][tile_of == t].tolist()) <= set(a), f"tile {t}: contributor pruned"
+    out, beta, _ = _gpu_uplift(wl, [0])
+    f_ref, b_ref = oracle.uplift(wl.scene, wl.cams, lambda v: wl.features(v))
+    pos = b_ref > 0
+    e = rel_l2(out, f_ref, pos)
+    print(f"wide d={d}: float32 uplift rel L2 vs float64 oracle {e:.2e}")
+    assert np.array_equal(beta > 0, pos)
+    assert e <= 1e-5
