@@ -100,8 +100,8 @@ def test_poisoned_request_leaves_the_others_intact(world):
 
 def test_admission_rejects_requests_over_budget(world):
     """The budget covers the server's replicas and the live workspaces besides
-    the outputs: with room for the workspaces (already grown by the earlier
-    requests on these scenes), one small output and 2 MB, the large request
+    the outputs: with room for the workspaces (grown first by two requests of the
+    small requests' shape), one small output and 2 MB, the large request
     on scene 0 is rejected and the small ones on scene 1 are served."""
     srv = _server(world, 1 << 40, slots=2)
     res_bytes = srv.resident_bytes()
@@ -109,6 +109,9 @@ def test_admission_rejects_requests_over_budget(world):
     assert res_bytes >= sum(sc.workspace_bytes() for sc in world["scenes"]) > 0
     srv.close()
     srv = _server(world, 1 << 40, slots=1)
+    # the small requests' shape once, so that the replica's workspace already
+    # holds what they need (a workspace grows to the largest request it served)
+    assert all(r.ok for r in srv.run([serve.Request(0, 0.0, 1, 8, 0, 4), serve.Request(1, 0.0, 1, 8, 4, 4)]))
     srv.budget = srv.resident_bytes() + serve.request_bytes(world["scenes"][1].n, 8) + (2 << 20)
     assert serve.request_bytes(world["scenes"][0].n, 48) > serve.request_bytes(world["scenes"][1].n, 8) + (2 << 20)
     reqs = [serve.Request(0, 0.0, 0, 48, 0, 4), serve.Request(1, 0.0, 1, 8, 0, 4),
