@@ -5,12 +5,18 @@
 //        = min_k 1 / (1 + exp(T (s_ik - s_iq))).
 //
 // The work streams the feature rows once and does m = queries + phrases dot
-// products per row: memory-bound, so CUDA cores, not a GEMM.  One thread per
-// row keeps the row's m dots in registers (no cross-lane reductions): a warp
-// takes 32 rows and walks their channels 32 at a time, staging each 32 x 32
-// slab through shared memory (coalesced 128-byte row loads in, one padded row
-// per thread out); the embeddings sit normalised and transposed in shared
-// memory ([channel][M]), so every thread reads the same values (broadcast).
+// products of length d per row: a skinny product S = F Phi^T (n x d times
+// d x m) with its epilogue.  A CTA takes 128 rows and computes their 128 x M
+// block of S on CUDA cores with register tiles: thread (row group, query
+// group) holds 4 rows x M/8 queries, and per channel reads 4 features of its
+// rows (one 16-byte load of the chunk staged transposed in shared memory) and
+// M/8 normalised embedding values (one or two 16-byte loads, the same for the
+// whole warp), for 4 M/8 fused multiply-adds.  Channels are
+// staged 32 at a time, the next chunk's global loads in flight while the
+// current one is used.  The feature norms are summed from the staged chunks
+// (two threads per row, each over half of every chunk).  Each dot product is
+// one fmaf chain over the channels in order.  The epilogue writes the block of S to shared memory and takes
+// the minimum over the phrases for every (row, query).
 #include <algorithm>
 
 #include "common.cuh"
@@ -20,15 +26,21 @@ namespace ludvig {
 namespace {
 
 constexpr int kRelMaxM = 64;                   // queries + phrases
-constexpr int kRelMaxSmemFloats = 40 * 1024;   // transposed embeddings in shared memory (160 KB)
+constexpr int kRelMaxSmemFloats = 40 * 1024;   // normalised embeddings in shared memory (160 KB)
+constexpr int kRelRows = 128;                  // rows per CTA
+constexpr int kRelPitch = kRelRows + 4;        // transposed chunk: [channel][row], 16-byte aligned rows
 
 template <int M>
-__global__ void __launch_bounds__(256) k_relevancy(const float* __restrict__ f, int64_t n, int d,
+__global__ void __launch_bounds__(256, M == 32 ? 3 : 2) k_relevancy(const float* __restrict__ f, int64_t n, int d,
                                                    const float* __restrict__ phi, int nq, int m, float T,
                                                    float* __restrict__ r) {
-    extern __shared__ float smem[];
-    float* sphi = smem;                            // [d][M], rows of phi normalised, zero past m
-    float (*tile)[32 * 33] = reinterpret_cast<float (*)[32 * 33]>(smem + (size_t)d * M);   // per warp
+    constexpr int QPT = M / 8;                 // queries per thread
+    constexpr int kStage = 32 * kRelPitch > kRelRows * (M + 1) ? 32 * kRelPitch : kRelRows * (M + 1);
+    extern __shared__ __align__(16) float smem[];
+    float* sphi = smem;                                        // [d][M], normalised, zero past m
+    float* As = sphi + (size_t)d * M;                          // [32][kRelPitch]
+    float* Cs = As;                                            // epilogue: [kRelRows][M + 1], in As's place
+    float* nrm = As + kStage;                                  // [kRelRows] squared norms
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = warp; e < M; e += 8) {
         float s = 0.f;
@@ -42,58 +54,100 @@ __global__ void __launch_bounds__(256) k_relevancy(const float* __restrict__ f, 
         const float inv = s > 0.f ? 1.0f / sqrtf(s) : 0.f;
         for (int c = lane; c < d; c += 32) sphi[c * M + e] = e < m ? phi[(int64_t)e * d + c] * inv : 0.f;
     }
-    __syncthreads();
-    float* t = tile[warp];
-    for (int64_t base = ((int64_t)blockIdx.x * 8 + warp) * 32; base < n; base += (int64_t)gridDim.x * 256) {
-        const int64_t i = base + lane;
-        const int rows = (int)(n - base < 32 ? n - base : 32);
-        float acc[M];
+    // query group (QPT queries, the same for a warp: its embedding loads are
+    // broadcasts) and row group (4 rows; a warp's 32 groups read one 512-byte
+    // run of the staged chunk)
+    const int qg = tid >> 5, rg = tid & 31;
+    const int64_t base = (int64_t)blockIdx.x * kRelRows;
+    // staging: element t + 256 j of a chunk is row (t + 256 j) / 32, channel lane
+    const int64_t stride8 = 8 * (int64_t)d;                       // 8 rows
+    const float* frow = f + (base + (tid >> 5)) * (int64_t)d + lane;   // row warp, channel lane
+    const int64_t rows_left = n - base - (tid >> 5);                   // rows warp + 8 jj exist for 8 jj < this
+    auto load_chunk = [&](int c0, float* v) {
+        const bool cin = c0 + lane < d;
+        const float* p = frow + c0;
 #pragma unroll
-        for (int e = 0; e < M; ++e) acc[e] = 0.f;
-        float nn = 0.f;
-        for (int c0 = 0; c0 < d; c0 += 32) {
-            // slab: rows base .. base + 31, channels c0 .. c0 + 31 (lane = channel)
-            const int c = c0 + lane;
-            float v[32];   // all 32 row loads in flight before the stores
+        for (int jj = 0; jj < 16; ++jj) v[jj] = (cin && 8 * jj < rows_left) ? p[jj * stride8] : 0.f;
+    };
+    float v[16];
+    load_chunk(0, v);
+    float acc[4][QPT];
 #pragma unroll
-            for (int rr = 0; rr < 32; ++rr) v[rr] = (rr < rows && c < d) ? f[(base + rr) * d + c] : 0.f;
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int rr = 0; rr < 32; ++rr) t[rr * 33 + lane] = v[rr];
-            __syncwarp();
-            const int cw = min(32, d - c0);
-            for (int cc = 0; cc < cw; ++cc) {
-                const float x = t[lane * 33 + cc];
+        for (int b = 0; b < QPT; ++b) acc[a][b] = 0.f;
+    float nn = 0.f;   // row (tid % 128)'s squared norm over half of each chunk's channels
+    for (int c0 = 0; c0 < d; c0 += 32) {
+        __syncthreads();   // the previous chunk is consumed (and sphi is written, first time)
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) As[lane * kRelPitch + (tid >> 5) + 8 * jj] = v[jj];
+        __syncthreads();
+        if (c0 + 32 < d) load_chunk(c0 + 32, v);   // in flight during this chunk
+        const int cw = min(32, d - c0);
+        {
+            // this thread's half of row (tid % 128)'s channels in the chunk
+            const int h0 = 16 * (tid >> 7), h1 = min(cw, h0 + 16);
+            for (int cc = h0; cc < h1; ++cc) {
+                const float x = As[cc * kRelPitch + (tid & (kRelRows - 1))];
                 nn = fmaf(x, x, nn);
-                const float4* p = reinterpret_cast<const float4*>(sphi + (size_t)(c0 + cc) * M);
+            }
+        }
+        auto step = [&](int cc) {
+            const float4 a4 = *reinterpret_cast<const float4*>(&As[cc * kRelPitch + 4 * rg]);
+            const float* pr = sphi + (size_t)(c0 + cc) * M + QPT * qg;
+            float bq[QPT];
+            if constexpr (QPT >= 4) {
 #pragma unroll
-                for (int e4 = 0; e4 < M / 4; ++e4) {
-                    const float4 ph = p[e4];
-                    acc[4 * e4] = fmaf(x, ph.x, acc[4 * e4]);
-                    acc[4 * e4 + 1] = fmaf(x, ph.y, acc[4 * e4 + 1]);
-                    acc[4 * e4 + 2] = fmaf(x, ph.z, acc[4 * e4 + 2]);
-                    acc[4 * e4 + 3] = fmaf(x, ph.w, acc[4 * e4 + 3]);
+                for (int b = 0; b < QPT; b += 4) {
+                    const float4 p4 = *reinterpret_cast<const float4*>(pr + b);
+                    bq[b] = p4.x;
+                    bq[b + 1] = p4.y;
+                    bq[b + 2] = p4.z;
+                    bq[b + 3] = p4.w;
                 }
-            }
-            __syncwarp();
-        }
-        if (lane >= rows) continue;
-        const float inv = nn > 0.f ? 1.0f / sqrtf(nn) : 0.f;
+            } else {
 #pragma unroll
-        for (int q = 0; q < M; ++q) {
-            if (q < nq) {
-                float best = 1.f;
-#pragma unroll
-                for (int e = 0; e < M; ++e)
-                    if (e >= nq && e < m) best = fminf(best, 1.0f / (1.0f + expf(T * inv * (acc[e] - acc[q]))));
-                r[i * nq + q] = best;
+                for (int b = 0; b < QPT; ++b) bq[b] = pr[b];
             }
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < QPT; ++b) acc[a][b] = fmaf(av[a], bq[b], acc[a][b]);
+        };
+        if (cw == 32) {
+#pragma unroll 8
+            for (int cc = 0; cc < 32; ++cc) step(cc);
+        } else {
+            for (int cc = 0; cc < cw; ++cc) step(cc);
         }
+    }
+    __syncthreads();   // As is free: the block of S goes to Cs
+    if (tid < kRelRows) nrm[tid] = nn;   // first halves; the second halves are added below
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < QPT; ++b) Cs[(4 * rg + a) * (M + 1) + QPT * qg + b] = acc[a][b];
+    __syncthreads();
+    if (tid >= kRelRows) nrm[tid - kRelRows] += nn;
+    __syncthreads();
+    const int rows = n - base < kRelRows ? (int)(n - base) : kRelRows;
+    for (int o = tid; o < rows * nq; o += 256) {
+        const int row = o / nq, q = o - row * nq;
+        const float* cr = Cs + row * (M + 1);
+        const float nsq = nrm[row];
+        const float inv = nsq > 0.f ? 1.0f / sqrtf(nsq) : 0.f;
+        float best = 1.f;
+        for (int e = nq; e < m; ++e) best = fminf(best, 1.0f / (1.0f + expf(T * inv * (cr[e] - cr[q]))));
+        r[(base + row) * nq + q] = best;
     }
 }
 
 template <int M>
 size_t relevancy_smem(int d) {
-    return sizeof(float) * ((size_t)d * M + 8 * 32 * 33);
+    // embeddings, then the chunk [32][kRelPitch] (or the epilogue's [128][M + 1]), then the norms
+    const size_t stage = std::max<size_t>((size_t)32 * kRelPitch, (size_t)kRelRows * (M + 1));
+    return sizeof(float) * ((size_t)d * M + stage + kRelRows);
 }
 
 template <int M>
@@ -104,11 +158,7 @@ ludvig_status launch_relevancy(const float* f, int64_t n, int d, const float* ph
     static const cudaError_t configured =
         cudaFuncSetAttribute(k_relevancy<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)relevancy_smem<M>(kRelMaxSmemFloats / M));
     LV_CUDA(configured);
-    int dev = 0, sms = 0;
-    LV_CUDA(cudaGetDevice(&dev));
-    LV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t want = ceil_div(n, 256);
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 4));
+    const unsigned grid = (unsigned)ceil_div(n, kRelRows);
     k_relevancy<M><<<grid, 256, smem, st>>>(f, n, d, phi, nq, m, T, r);
     LV_LAUNCH();
     return LUDVIG_OK;
