@@ -1260,17 +1260,23 @@ __global__ void k_reach_init(const float* __restrict__ g0, int64_t n, int dx, ui
     s[i] = b;
 }
 
+// Eight lanes per row (a row holds k to 2k entries): four rows per warp are in
+// flight at once, since each row is a short chain of dependent loads (row
+// pointer, entries, the neighbours' bits).
+constexpr int kReachLanes = 8;
+
 __global__ void __launch_bounds__(256) k_reach_step(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                                     const float* __restrict__ val, const uint32_t* __restrict__ s,
                                                     int64_t n, uint32_t* __restrict__ s2) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * 8 + warp;
-    if (i >= n) return;
+    const int sub = threadIdx.x & (kReachLanes - 1);
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kReachLanes;
     uint32_t b = 0u;
-    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += 32)
-        if (val[e] > 0.f) b |= s[col[e]];
-    b = __reduce_or_sync(0xffffffffu, b);
-    if (lane == 0) s2[i] = b;
+    if (i < n)
+        for (int64_t e = rp[i] + sub, e1 = rp[i + 1]; e < e1; e += kReachLanes)
+            if (val[e] > 0.f) b |= s[col[e]];
+#pragma unroll
+    for (int o = kReachLanes / 2; o > 0; o >>= 1) b |= __shfl_xor_sync(0xffffffffu, b, o);
+    if (i < n && sub == 0) s2[i] = b;
 }
 
 __global__ void k_reach_out(const uint32_t* __restrict__ s, const float* __restrict__ P, int64_t n, int dx,
@@ -1447,7 +1453,8 @@ extern "C" ludvig_status ludvig_reach_weight(ludvig_graph_t graph, const float* 
     k_reach_init<<<grid_for(n, 256), 256, 0, st>>>(g0, n, dx, s0);
     LV_LAUNCH();
     for (int t = 0; t < steps; ++t) {
-        k_reach_step<<<grid_for(n, 8), 256, 0, st>>>(graph->row_ptr, graph->col, graph->val, s0, n, s1);
+        k_reach_step<<<grid_for(n * kReachLanes, 256), 256, 0, st>>>(graph->row_ptr, graph->col, graph->val, s0, n,
+                                                                      s1);
         LV_LAUNCH();
         std::swap(s0, s1);
     }
