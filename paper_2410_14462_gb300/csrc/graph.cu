@@ -483,9 +483,9 @@ __global__ void k_colnorm2(const float* __restrict__ x, int64_t n, int dx, doubl
     }
 }
 
-// y = A (x / ||x||).  dx == 1: groups of kLanes lanes per row over a
-// grid-stride range of rows; dx > 1: warp per row, lane = column.  ||y||^2 per
-// column is reduced in the block and added once per block (float64).
+// y = A (x / ||x||) for one column (dx == 1, the CSR form): groups of kLanes
+// lanes per row over a grid-stride range of rows.  ||y||^2 is reduced in the
+// block and added once per block (float64).
 template <int kLanes>
 __global__ void __launch_bounds__(256) k_spmv_scaled(const int64_t* __restrict__ rp,
                                                     const int32_t* __restrict__ col,
@@ -495,56 +495,85 @@ __global__ void __launch_bounds__(256) k_spmv_scaled(const int64_t* __restrict__
                                                     float* __restrict__ y, double* __restrict__ n2_out) {
     __shared__ double part[8][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (kLanes == 1) {
-        double mine = 0.0;
-        const double nn = lane < dx ? n2_in[lane] : 0.0;
-        const float s = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.f;
-        for (int64_t i = (int64_t)blockIdx.x * 8 + warp; i < n; i += (int64_t)gridDim.x * 8) {
-            if (lane < dx) {
-                float acc = 0.f;
-                for (int64_t e = rp[i]; e < rp[i + 1]; ++e) acc = fmaf(val[e], x[(int64_t)col[e] * dx + lane], acc);
-                acc *= s;
-                y[i * dx + lane] = acc;
-                mine += (double)acc * acc;
-            }
-        }
-        part[warp][lane] = mine;
-        __syncthreads();
-        if (threadIdx.x < dx) {
-            double t = 0.0;
-            for (int w = 0; w < 8; ++w) t += part[w][threadIdx.x];
-            atomicAdd(n2_out + threadIdx.x, t);
-        }
-    } else {
-        const int sub = lane % kLanes;
-        const double nn = n2_in[0];
-        const float s = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.f;
-        double mine = 0.0;
-        const int64_t groups = (int64_t)gridDim.x * (blockDim.x / kLanes);
-        const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kLanes;
-        for (int64_t base = 0; base < n; base += groups) {
-            const int64_t i = base + g0;
-            float acc = 0.f;
-            if (i < n)
-                for (int64_t e = rp[i] + sub; e < rp[i + 1]; e += kLanes) acc = fmaf(val[e], x[col[e]], acc);
+    const int sub = lane % kLanes;
+    const double nn = n2_in[0];
+    const float s = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.f;
+    double mine = 0.0;
+    const int64_t groups = (int64_t)gridDim.x * (blockDim.x / kLanes);
+    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kLanes;
+    for (int64_t base = 0; base < n; base += groups) {
+        const int64_t i = base + g0;
+        float acc = 0.f;
+        if (i < n)
+            for (int64_t e = rp[i] + sub; e < rp[i + 1]; e += kLanes) acc = fmaf(val[e], x[col[e]], acc);
 #pragma unroll
-            for (int o = kLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (i < n && sub == 0) {
-                acc *= s;
-                y[i] = acc;
-                mine += (double)acc * acc;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-        if (lane == 0) part[warp][0] = mine;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < 8; ++w) t += part[w][0];
-            atomicAdd(n2_out, t);
+        for (int o = kLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (i < n && sub == 0) {
+            acc *= s;
+            y[i] = acc;
+            mine += (double)acc * acc;
         }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if (lane == 0) part[warp][0] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += part[w][0];
+        atomicAdd(n2_out, t);
+    }
+}
+
+// Several columns (2 <= dx <= 32): L = ceil(dx / 4) lanes per row, each
+// owning 4 consecutive columns, so a warp works on 32 / L rows at once (a row
+// is a chain of dependent loads: its pointer, then per entry the column and
+// the x values).  Each (row, column) sum is one fmaf chain over the row's
+// entries in order, then the column's scale; the columns' squared norms are
+// summed per block in shared memory, then added to n2_out.
+__global__ void __launch_bounds__(256) k_spmv_cols(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                   const float* __restrict__ val, const float* __restrict__ x,
+                                                   int64_t n, int dx, const double* __restrict__ n2_in,
+                                                   float* __restrict__ y, double* __restrict__ n2_out) {
+    __shared__ double colsum[32];
+    const int L = (dx + 3) >> 2, G = 32 / L;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane / L, c0 = 4 * (lane - grp * L);
+    const bool act = grp < G;
+    if (threadIdx.x < 32) colsum[threadIdx.x] = 0.0;
+    __syncthreads();
+    float sc[4];
+    double mine[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const double nn = (act && c0 + q < dx) ? n2_in[c0 + q] : 0.0;
+        sc[q] = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.f;
+    }
+    const int64_t nw = (int64_t)gridDim.x * 8;
+    for (int64_t base = ((int64_t)blockIdx.x * 8 + warp) * G; base < n; base += nw * G) {
+        const int64_t i = base + grp;
+        if (!act || i >= n) continue;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int64_t e = rp[i], e1 = rp[i + 1]; e < e1; ++e) {
+            const float v = val[e];
+            const float* xr = x + (int64_t)col[e] * dx + c0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (c0 + q < dx) acc[q] = fmaf(v, xr[q], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (c0 + q < dx) {
+                const float a = acc[q] * sc[q];
+                y[i * dx + c0 + q] = a;
+                mine[q] += (double)a * a;
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (act && c0 + q < dx) atomicAdd(&colsum[c0 + q], mine[q]);
+    __syncthreads();
+    if (threadIdx.x < dx) atomicAdd(n2_out + threadIdx.x, colsum[threadIdx.x]);
 }
 
 // Sliced copy of the matrix for single-column diffusion: slices of 32
@@ -1015,8 +1044,8 @@ extern "C" ludvig_status ludvig_diffuse(ludvig_graph_t g, const float* x0, int32
             k_spmv_scaled<8><<<blocks, 256, 0, st>>>(g->row_ptr, g->col, g->val, xin, n, 1, n2 + 32 * t, y,
                                                      n2 + 32 * (t + 1));
         else
-            k_spmv_scaled<1><<<blocks, 256, 0, st>>>(g->row_ptr, g->col, g->val, xin, n, dx, n2 + 32 * t, y,
-                                                     n2 + 32 * (t + 1));
+            k_spmv_cols<<<blocks, 256, 0, st>>>(g->row_ptr, g->col, g->val, xin, n, dx, n2 + 32 * t, y,
+                                                n2 + 32 * (t + 1));
         LV_LAUNCH();
         xin = y;
     }
@@ -1103,8 +1132,8 @@ extern "C" ludvig_status ludvig_diffuse_noalloc(ludvig_graph_t g, const float* x
             k_spmv_scaled<8><<<blocks, 256, 0, st>>>(g->row_ptr, g->col, g->val, xin, n, 1, n2 + 32 * t, y,
                                                      n2 + 32 * (t + 1));
         else
-            k_spmv_scaled<1><<<blocks, 256, 0, st>>>(g->row_ptr, g->col, g->val, xin, n, dx, n2 + 32 * t, y,
-                                                     n2 + 32 * (t + 1));
+            k_spmv_cols<<<blocks, 256, 0, st>>>(g->row_ptr, g->col, g->val, xin, n, dx, n2 + 32 * t, y,
+                                                n2 + 32 * (t + 1));
         LV_LAUNCH();
         xin = y;
     }
