@@ -350,15 +350,23 @@ def uplift_finalize(num, den, out=None, beta=None, stream=None):
     return out
 
 
-def uplift_host(scene: Scene, cams_params, width, height, feats: torch.Tensor, stream=None):
-    """The same uplift from host (CPU, ideally pinned) features; returns CPU tensors."""
+def uplift_host(scene: Scene, cams_params, width, height, feats: torch.Tensor, out=None, beta=None, stream=None):
+    """The same uplift from host (CPU, ideally pinned) features into host
+    outputs: out [N, D] and beta [N] float32 CPU tensors (pinned ones are
+    copied at the full link rate), allocated pinned here when not given;
+    returns (out, beta)."""
     L = load()
     if feats.is_cuda or not feats.is_contiguous():
         raise LudvigError("feats must be a contiguous CPU tensor")
     cams, nv = cameras_struct(cams_params)
     d = int(feats.shape[-1])
-    out = torch.empty((scene.n, d), dtype=torch.float32, pin_memory=True)
-    beta = torch.empty((scene.n,), dtype=torch.float32, pin_memory=True)
+    if out is None:
+        out = torch.empty((scene.n, d), dtype=torch.float32, pin_memory=True)
+    if beta is None:
+        beta = torch.empty((scene.n,), dtype=torch.float32, pin_memory=True)
+    for t, shape, name in ((out, (scene.n, d), "out"), (beta, (scene.n,), "beta")):
+        if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != shape:
+            raise LudvigError(f"{name} must be a contiguous float32 CPU tensor of shape {shape}")
     _check(L.ludvig_uplift_host(scene.handle, cams, nv, width, height, ctypes.c_void_p(feats.data_ptr()),
                                 _dtype_code(feats), d, ctypes.c_void_p(out.data_ptr()),
                                 ctypes.c_void_p(beta.data_ptr()), _stream(stream)), "ludvig_uplift_host")

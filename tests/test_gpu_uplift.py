@@ -182,6 +182,15 @@ def test_accumulate_split_equals_whole_and_host_path():
     hout, hbeta = ludvig.uplift_host(sc, wl.cams.params, W, H, F.cpu().pin_memory())
     assert rel_l2(hout.numpy(), whole.cpu().numpy()) < 1e-6
     assert rel_l2(hbeta.numpy(), beta.cpu().numpy()) < 1e-6
+    # into result buffers the caller owns (pinned and pageable), filled in place
+    for pin in (True, False):
+        o = torch.full((sc.n, 16), float("nan"), pin_memory=pin)
+        b2 = torch.full((sc.n,), float("nan"), pin_memory=pin)
+        r = ludvig.uplift_host(sc, wl.cams.params, W, H, F.cpu().contiguous(), out=o, beta=b2)
+        assert r[0] is o and r[1] is b2
+        assert rel_l2(o.numpy(), whole.cpu().numpy()) < 1e-6 and rel_l2(b2.numpy(), beta.cpu().numpy()) < 1e-6
+    with pytest.raises(ludvig.LudvigError):
+        ludvig.uplift_host(sc, wl.cams.params, W, H, F.cpu().contiguous(), out=torch.empty((sc.n, 15)))
 
 
 def test_edge_cases():
