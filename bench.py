@@ -316,11 +316,11 @@ def tiny_line(with_oracle):
 
 def cpu_baseline(args):
     """The oracle on the host cores, timed exactly as the reference arm times
-    it: a child process running `bench.py --impl reference` on the same
-    workload and views (one view per step, views 3-5 after 3 untimed, as the
-    reference arm's default warm-up gives), so that the two agree; this
-    process's GPU work and its threads stay out of the timing."""
-    return oracle_child(args.workload)
+    it: a child process running `bench.py --impl reference` with this run's
+    workload, steps and warm-up (at most 8 and 5: one view per step, so the
+    same views as the reference arm of the same command), so that the two
+    agree; this process's GPU work and its threads stay out of the timing."""
+    return oracle_child(args.workload, steps=max(1, min(8, args.steps)), warmup=max(0, min(5, args.warmup)))
 
 
 # DRAM bytes (read + write) of one k_aggregate_tc launch, from the ncu capture in
