@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form line")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-form line")
     ap.add_argument("--profile-case", default=None,
-                    choices=["tc2views", "render2views", "render16views", "uplift16views", "batch8"],
+                    choices=["tc2views", "render2views", "render16views", "uplift16views", "batch8", "tinymask"],
                     help="run a small fixed case for an ncu capture and exit (no JSON line)")
     return ap.parse_args()
 
@@ -1040,7 +1040,9 @@ def profile_case(name):
     the render kernels), three times.  uplift16views: float32 uplift of
     views 0-15 (one full launch of the aggregation, 13 GB of features), three
     times.  batch8: the first 8 jobs of the
-    32-job batched mix through one ludvig_uplift_batch call (6 slots)."""
+    32-job batched mix through one ludvig_uplift_batch call (6 slots).
+    tinymask: the tiny mask workload (20k Gaussians, 8 views of 128x128,
+    D = 1 float32), uplifted four times."""
     import torch
     from paper_2410_14462_gb300 import build, inputs, ludvig
     build.build()
@@ -1055,6 +1057,14 @@ def profile_case(name):
         res = serve.run_batch(jobs, pools, cams.params, cams.width, cams.height, slots=6)
         torch.cuda.synchronize()
         return 1 if res["errors"] else 0
+    if name == "tinymask":
+        wl = inputs.tiny_mask_workload()
+        sc = ludvig.Scene.from_inputs(wl.scene)
+        F = torch.stack([wl.features(v, device="cuda") for v in range(wl.cams.v)]).float().contiguous()
+        for _ in range(4):
+            ludvig.uplift(sc, wl.cams.params, wl.cams.width, wl.cams.height, F)
+        torch.cuda.synchronize()
+        return 0
     wl = inputs.paper_scale_workload(views=16 if name in ("render16views", "uplift16views") else 2, d=384)
     sc = ludvig.Scene.from_inputs(wl.scene)
     W, H = wl.cams.width, wl.cams.height
