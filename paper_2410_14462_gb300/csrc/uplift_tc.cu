@@ -100,8 +100,9 @@ struct WeightsArgs {
     int* item_first;        // [nitems]: the tile's first chunk, or -1 (set to -1 before the launch)
     int* chunk_counter;
     int cap;
-    float* chunk_den;       // [cap][128][NT]: each row's sum of its weight term (rewritten on a re-run)
-    int count_den;          // chunk_den holds each row's count of non-zero weights (term 0; term 1: 0)
+    float* chunk_den;       // [cap][128][NT]: each row's den, the sum of its weight terms, in term 0's
+                            // slot (term 1's: 0); rewritten on a re-run
+    int count_den;          // chunk_den holds each row's count of non-zero weights instead
     // direct accumulation (k_weights<NT, true>, few channels): each new row's
     // sum_p w F[p, c] and its den go straight into the view's num and den
     // (atomic adds); no weight rows, chunks or plan are written
@@ -132,7 +133,7 @@ struct WeightsSmem<NT, true> : WeightsSmemBase<NT> {
 // lane, packed in wv), summed over the warp: the sum of the term's values, or
 // with count_den the number of non-zero weights (counted on term 0; a weight
 // w > 0 is at least 1/255 * 1e-4, far above the smallest bfloat16).
-__device__ __forceinline__ float row_den(const uint32_t* wv, int count_den, int term) {
+__device__ __forceinline__ float lane_den(const uint32_t* wv, int count_den, int term) {
     float s = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -141,9 +142,17 @@ __device__ __forceinline__ float row_den(const uint32_t* wv, int count_den, int 
         else
             s += __uint_as_float(wv[k] << 16) + __uint_as_float(wv[k] & 0xffff0000u);
     }
+    return s;
+}
+
+__device__ __forceinline__ float warp_sum(float s) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
+}
+
+__device__ __forceinline__ float row_den(const uint32_t* wv, int count_den, int term) {
+    return warp_sum(lane_den(wv, count_den, term));
 }
 
 __device__ __forceinline__ void finish_chunk(const WeightsArgs& a, int c, int rows, int next) {
@@ -336,13 +345,14 @@ __global__ void __launch_bounds__(256, 5) k_weights(const __grid_constant__ Weig
                     const uint4 v4 = *src;
                     *src = make_uint4(0u, 0u, 0u, 0u);
                     const uint32_t wv[4] = {v4.x, v4.y, v4.z, v4.w};
-                    sden += row_den(wv, a.count_den, t);
+                    sden += lane_den(wv, a.count_den, t);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         w[2 * k] += __uint_as_float(wv[k] << 16);
                         w[2 * k + 1] += __uint_as_float(wv[k] & 0xffff0000u);
                     }
                 }
+                sden = warp_sum(sden);   // the row's den over both terms
                 const uint32_t gid = rec[j].gid;
 #pragma unroll
                 for (int c = 0; c < kDirectMaxD; ++c) {
@@ -375,6 +385,7 @@ __global__ void __launch_bounds__(256, 5) k_weights(const __grid_constant__ Weig
                     ch = nxt;
                 }
                 const bool keep = ch >= 0 && ch < a.cap;
+                float sden = 0.f;   // this lane's part of the row's den, both terms
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
                     uint4* src = reinterpret_cast<uint4*>(&S.stage[t][j * kRowBytes + lane * 16]);
@@ -385,10 +396,15 @@ __global__ void __launch_bounds__(256, 5) k_weights(const __grid_constant__ Weig
                     }
                     *src = make_uint4(0u, 0u, 0u, 0u);
                     const uint32_t wv[4] = {v4.x, v4.y, v4.z, v4.w};
-                    const float sden = row_den(wv, a.count_den, t);
-                    if (lane == 0 && keep) a.chunk_den[((size_t)ch * kCRows + local) * NT + t] = sden;
+                    sden += lane_den(wv, a.count_den, t);
                 }
-                if (lane == 0 && keep) a.chunk_gid[(size_t)ch * kCRows + local] = rec[j].gid;
+                sden = warp_sum(sden);
+                if (lane == 0 && keep) {
+                    // the row's den in term 0's slot (the aggregation adds the slots)
+                    a.chunk_den[((size_t)ch * kCRows + local) * NT] = sden;
+                    a.chunk_den[((size_t)ch * kCRows + local) * NT + 1] = 0.f;
+                    a.chunk_gid[(size_t)ch * kCRows + local] = rec[j].gid;
+                }
             }
         } else {
             // warp w takes row w (row i of the 32 at most: warp i % 8 on pass i / 8)
