@@ -108,12 +108,20 @@ __global__ void k_scene_init(const float* __restrict__ means, const float* __res
 
 // ------------------------------------------------------------ 1. project
 
+// One projected Gaussian of one view, as k_project writes it: mean, conic,
+// opacity and the tile rectangle (x0 | y0 << 16, x1 | y1 << 16) in 32 bytes.
+struct __align__(16) ProjRec {
+    float4 a;      // mx, my, conic a, conic b
+    float2 b;      // conic c, opacity
+    uint2 rect;
+};
+static_assert(sizeof(ProjRec) == 32, "ProjRec is 32 bytes");
+
 // View v projects the sb.n[v] Gaussians of its own scene; the records of the
 // group have a stride of n (the largest scene) per view.
 __global__ void __launch_bounds__(256) k_project(const __grid_constant__ SceneBatch sb, int64_t n, int64_t npad,
                           int nv, const __grid_constant__ CamBatch cb, int width, int height,
-                          float4* __restrict__ rec_a, float2* __restrict__ rec_b, uint2* __restrict__ rect,
-                          uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                          ProjRec* __restrict__ prec, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                           uint32_t* __restrict__ ntile, float* __restrict__ dbg_rec,
                           int32_t* __restrict__ dbg_rect, int prune) {
     // every block is full and lies in one view: npad is a multiple of the
@@ -146,11 +154,13 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ SceneBa
         P = project_gaussian(m, S6, cam, width, height);
         op = g.w;
         const int64_t o = (int64_t)v * n + i;
-        rec_a[o] = make_float4(P.mx, P.my, P.ca, P.cb);
-        rec_b[o] = make_float2(P.cc, g.w);
-        rect[o] = P.visible ? make_uint2((uint32_t)P.x0 | ((uint32_t)P.y0 << 16),
+        ProjRec pr;
+        pr.a = make_float4(P.mx, P.my, P.ca, P.cb);
+        pr.b = make_float2(P.cc, g.w);
+        pr.rect = P.visible ? make_uint2((uint32_t)P.x0 | ((uint32_t)P.y0 << 16),
                                          (uint32_t)P.x1 | ((uint32_t)P.y1 << 16))
                             : make_uint2(0u, 0u);
+        prec[o] = pr;
     }
     const bool vis = real && P.visible;
     const uint32_t area = vis ? (uint32_t)((P.x1 - P.x0) * (P.y1 - P.y0)) : 0u;
@@ -199,10 +209,9 @@ __device__ __forceinline__ bool pairs_fit(uint64_t np, uint64_t cap) {
 // The projected records in depth order, one per (view, rank): mean, conic,
 // opacity and index in a 32-byte record (its mask word unused) plus the tile
 // rectangle, and the number of tiles each reaches (0 for the culled ones,
-// whose records are never read).
+// whose records are never read).  A record is gathered in one 32-byte sector.
 __global__ void k_sorted_records(const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ svals,
-                                 const uint32_t* __restrict__ ntile, const float4* __restrict__ rec_a,
-                                 const float2* __restrict__ rec_b, const uint2* __restrict__ rect, int64_t n,
+                                 const uint32_t* __restrict__ ntile, const ProjRec* __restrict__ prec, int64_t n,
                                  int64_t npad, int64_t total, uint32_t* __restrict__ cnt, PairRec* __restrict__ srec,
                                  uint2* __restrict__ srect) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -213,8 +222,9 @@ __global__ void k_sorted_records(const uint32_t* __restrict__ skeys, const uint3
     }
     const int64_t v = idx / npad;
     const uint32_t i = svals[idx];
-    const float4 ra = rec_a[v * n + i];
-    const float2 rb = rec_b[v * n + i];
+    const ProjRec pr = prec[v * n + i];
+    const float4 ra = pr.a;
+    const float2 rb = pr.b;
     cnt[idx] = ntile[v * npad + i];
     PairRec r;
     r.mx = ra.x;
@@ -226,7 +236,7 @@ __global__ void k_sorted_records(const uint32_t* __restrict__ skeys, const uint3
     r.gid = i;
     r.mask = 0u;
     srec[idx] = r;
-    srect[idx] = rect[v * n + i];
+    srect[idx] = pr.rect;
 }
 
 // One (view * tiles + tile, rank) pair per tile a Gaussian reaches, written in
@@ -937,9 +947,8 @@ bool single_call(const GroupViews& g) {
 // The per-view Gaussian scratch of a group of nv views of up to n Gaussians
 // (about 120 bytes per view and Gaussian).
 struct FrontBufs {
-    float4* rec_a;
-    float2* rec_b;
-    uint2 *rect, *srect;
+    ProjRec* prec;
+    uint2* srect;
     uint32_t *keys, *vals, *keys2, *vals2, *ntile, *cnt, *off;
     PairRec* srec;
     uint64_t* total;
@@ -947,9 +956,7 @@ struct FrontBufs {
 
 ludvig_status front_buffers(Arena& ws, int nv, int64_t n, FrontBufs* b) {
     const int64_t nG = (int64_t)nv * round_up(std::max<int64_t>(n, 1), kRadixTile);
-    LV_TRY(ws.get("up.rec_a", (size_t)nv * n, &b->rec_a));
-    LV_TRY(ws.get("up.rec_b", (size_t)nv * n, &b->rec_b));
-    LV_TRY(ws.get("up.rect", (size_t)nv * n, &b->rect));
+    LV_TRY(ws.get("up.prec", (size_t)nv * n, &b->prec));
     LV_TRY(ws.get("up.keys", (size_t)nG, &b->keys));
     LV_TRY(ws.get("up.vals", (size_t)nG, &b->vals));
     LV_TRY(ws.get("up.keys2", (size_t)nG, &b->keys2));
@@ -982,9 +989,8 @@ ludvig_status front_end(ludvig_scene* ctx, const GroupViews& g, int width, int h
 
     FrontBufs b;
     LV_TRY(front_buffers(ws, nv, n, &b));
-    float4* rec_a = b.rec_a;
-    float2* rec_b = b.rec_b;
-    uint2 *rect = b.rect, *srect = b.srect;
+    ProjRec* prec = b.prec;
+    uint2* srect = b.srect;
     uint32_t *keys = b.keys, *vals = b.vals, *keys2 = b.keys2, *vals2 = b.vals2, *ntile = b.ntile, *cnt = b.cnt,
              *off = b.off;
     PairRec* srec = b.srec;
@@ -1011,7 +1017,7 @@ ludvig_status front_end(ludvig_scene* ctx, const GroupViews& g, int width, int h
         sb.n[v] = vs->n;
     }
     int tslot = trace_on() ? trace_begin(LUDVIG_STAGE_PROJECT, st) : -1;
-    k_project<<<grid_for(nG, 256), 256, 0, st>>>(sb, n, npad, nv, cb, width, height, rec_a, rec_b, rect, keys,
+    k_project<<<grid_for(nG, 256), 256, 0, st>>>(sb, n, npad, nv, cb, width, height, prec, keys,
                                                   vals, ntile, dbg ? dbg->rec : nullptr, dbg ? dbg->rect : nullptr,
                                                   prune);
     LV_LAUNCH();
@@ -1028,7 +1034,7 @@ ludvig_status front_end(ludvig_scene* ctx, const GroupViews& g, int width, int h
         LV_TRY(radix_sort_pairs(&sk, &sv, keys2, vals2, nv, npad, 32, ws, st));
     trace_end(tslot, st);
     tslot = trace_on() ? trace_begin(LUDVIG_STAGE_BIN, st) : -1;
-    k_sorted_records<<<grid_for(nG, 256), 256, 0, st>>>(sk, sv, ntile, rec_a, rec_b, rect, n, npad, nG, cnt, srec,
+    k_sorted_records<<<grid_for(nG, 256), 256, 0, st>>>(sk, sv, ntile, prec, n, npad, nG, cnt, srec,
                                                         srect);
     LV_LAUNCH();
     LV_TRY(scan_exclusive_u32(cnt, off, nG, total_d, ws, st));
