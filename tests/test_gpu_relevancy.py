@@ -29,7 +29,7 @@ def _lib():
     ludvig.load()
 
 
-@pytest.mark.parametrize("n,d,nq", [(5003, 512, 1), (4000, 512, 21), (777, 48, 40), (100, 1024, 20)])
+@pytest.mark.parametrize("n,d,nq", [(5003, 512, 1), (4000, 512, 21), (777, 48, 40), (100, 1024, 20), (1500, 200, 10)])
 def test_relevancy_matches_oracle(n, d, nq):
     rng = np.random.default_rng(n + d + nq)
     f = rng.normal(size=(n, d)).astype(np.float32)
