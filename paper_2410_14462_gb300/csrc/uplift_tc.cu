@@ -18,11 +18,15 @@
 //  per warp.  Warp 0 gathers the batches' projected records (from the
 //  depth-ordered record array, by the ranks the list holds) with cp.async
 //  kRing - 1 batches ahead, and computes each entry's 8x4 block mask once its
-//  record has landed; only the batches the walk reaches are gathered.  The batch's weights go to 32 staging rows in shared memory; the
-//  Gaussians with a non-zero weight somewhere in the tile are then appended,
-//  as dense bfloat16 rows of 256 pixels, to the tile's "chunks" of 128 rows in
-//  global memory (chunk ids from an atomic counter; row count, Gaussian ids
-//  and the tile's next chunk recorded per chunk, the first chunk per tile).
+//  record has landed (the next batch's masks after its own compositing of
+//  the current one); only the batches the walk reaches are gathered.  The
+//  batch's weights go to 32 staging rows in shared memory; the Gaussians with
+//  a non-zero weight somewhere in the tile are then appended, as dense
+//  bfloat16 rows of 256 pixels, to the tile's "chunks" of 128 rows in global
+//  memory (chunk ids from an atomic counter; row count, Gaussian ids, den and
+//  the tile's next chunk recorded per chunk, the first chunk per tile).  For
+//  d <= 4 (k_weights<NT, true>) each new row is instead dotted with the
+//  tile's features and added to num and den on the spot.
 //
 //  k_aggregate_tc (one persistent CTA per SM, warp-specialised, tiles taken
 //  round-robin with each tile's chunks back to back).  Per chunk the K loop is
